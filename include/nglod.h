@@ -1,0 +1,217 @@
+/*
+ * libnglod -- C ABI of the Neural Geometric LOD rendering hot path on GB300.
+ *
+ * The method (Takikawa et al., "Neural Geometric Level of Detail", CVPR 2021)
+ * stores a neural SDF as a sparse voxel octree (SVO) over [-1,1]^3 whose
+ * voxels carry a feature vector at each of their 8 corners (shared between
+ * neighbours), with one small MLP decoder per level of detail (Sec. 3.2).
+ * Rendering intersects rays with the octree level by level (Sec. 3.4,
+ * Algorithm 1; supplementary Sec. C) and then sphere-traces each ray through
+ * its depth-ordered voxel list (Sec. 3.4, "Adaptive Ray Stepping").
+ *
+ * Conventions shared by every call:
+ *  - Octree depth dp has resolution 2^dp; LOD l lives at depth l + 2
+ *    (r_l = 4 * 2^l, supplementary Sec. A.1).  Depths 0..2 carry no features.
+ *  - Voxel (i,j,k) at depth dp has the Morton key with bit b of i, j, k at
+ *    bits 3b, 3b+1, 3b+2; a voxel id is the index of its key in the sorted key
+ *    array of its depth.
+ *  - Corner id: rank of the corner's Morton key (lattice (2^dp+1)^3) among the
+ *    unique corner keys of that depth, ascending.  Features of LOD l are
+ *    row-major [C_l, m] in corner-id order.
+ *  - Pointers are DEVICE pointers unless their name starts with h_.  Every
+ *    call is ordered on the given CUDA stream (a cudaStream_t passed as void*;
+ *    NULL is the legacy default stream) and returns an int status; nothing
+ *    throws across the ABI, nothing traps, and every device-side wait is
+ *    bounded.  The text of the last error of the calling thread is returned
+ *    by nglod_last_error().
+ *  - Features and decoder weights are caller-owned.  The SVO handle owns its
+ *    structure arrays.  Outputs are caller-owned with explicit capacities.
+ */
+#ifndef NGLOD_H
+#define NGLOD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+enum {
+    NGLOD_OK = 0,
+    NGLOD_ERR_INVALID_ARG = 1,   /* bad pointer, size, LOD or octree         */
+    NGLOD_ERR_CAPACITY = 2,      /* an output or workspace is too small      */
+    NGLOD_ERR_CUDA = 3,          /* a CUDA runtime call failed               */
+    NGLOD_ERR_OOM = 4,           /* device allocation failed                 */
+    NGLOD_ERR_TIMEOUT = 5,       /* a bounded device-side wait expired       */
+    NGLOD_ERR_NOT_SUPPORTED = 6  /* shape or dtype outside what is built     */
+};
+
+/* Element types of features / decode arithmetic. */
+enum { NGLOD_F32 = 0, NGLOD_F16 = 1, NGLOD_BF16 = 2 };
+
+typedef struct nglod_svo nglod_svo;   /* opaque octree handle */
+
+/* Corner features of LODs 1..num_lods (Sec. 3.2: z_V^(j) in R^m, shared). */
+typedef struct {
+    const void* feats[8];  /* feats[l-1]: [C_l, m] row-major, dtype below   */
+    int dtype;             /* NGLOD_F32 or NGLOD_F16                         */
+    int m;                 /* feature dimension; only 32 is built            */
+    int num_lods;          /* number of valid entries in feats               */
+} nglod_features;
+
+/* One LOD's decoder (Eq. 2): d = W2 . relu(W1 v + b1) + b2 with
+ * v = [x, z] (in_dim = m + 3) or v = z (in_dim = m).  FP32 master weights;
+ * the BF16 decode rounds W1 and z to bf16 (round-to-nearest-even) and
+ * accumulates in FP32.
+ * The FP32 decode keeps the whole decoder (19 KB) in the kernel-parameter
+ * constant bank, read as broadcast operands; it takes the weights from the
+ * optional HOST mirrors h_W1/h_b1/h_W2 (same layout and values as W1/b1/W2).
+ * Without them the call copies the device weights to the host first, which
+ * synchronises the stream. */
+typedef struct {
+    const float* W1;       /* [hidden, in_dim] row-major (device)             */
+    const float* b1;       /* [hidden] (device)                               */
+    const float* W2;       /* [hidden] (device)                               */
+    float b2;
+    int in_dim;            /* 32 or 35                                        */
+    int hidden;            /* only 128 is built                               */
+    const float* h_W1;     /* optional host mirrors (nullable)                */
+    const float* h_b1;
+    const float* h_W2;
+} nglod_decoder;
+
+/* Sphere-tracing parameters (supplementary Sec. A.4). */
+typedef struct {
+    float eps;             /* stop when d < eps (the paper uses 3e-4)         */
+    float far_t;           /* miss when t > far_t (the paper uses 5)          */
+    int max_steps;         /* miss after this many decodes (paper: 200)       */
+    int osc_check;         /* 1: also stop when |d_k - d_(k-1)| < 6 eps; the
+                              ray is then a hit iff |d_k| < 6 eps             */
+    int decode_dtype;      /* NGLOD_F32 (CUDA cores) or NGLOD_BF16 (tcgen05)  */
+    int want_normals;      /* 1: write normals of hit rays                    */
+} nglod_trace_params;
+
+/* Text of the calling thread's last error ("" if none). */
+const char* nglod_last_error(void);
+
+/* svo_build -- Sec. 3.2 (SVO over [-1,1]^3, corner features shared between
+ * neighbours) and Sec. 3.4 ("pointers ... precalculated in an initialization
+ * step by iterating over all voxels").
+ *   h_keys[dp]   host array of h_counts[dp] Morton keys of depth dp, strictly
+ *                increasing; depth 0 must be exactly {0}; every key's parent
+ *                (key >> 3) must exist at depth dp-1.
+ *   num_depths   Dmax + 1, with 4 <= num_depths <= 11 (LOD 1..8).
+ * Builds on the device: per-voxel packed coordinates, parent index, child
+ * mask and first-child index, and for depths >= 3 the 8 corner ids per voxel
+ * (deduplicated corners).  On success *out owns that memory (svo_free).
+ * Errors: NGLOD_ERR_INVALID_ARG for a malformed octree (nothing allocated
+ * survives), NGLOD_ERR_OOM / NGLOD_ERR_CUDA.  Synchronises the stream. */
+int svo_build(const uint64_t* const* h_keys, const int64_t* h_counts,
+              int num_depths, void* stream, nglod_svo** out);
+
+/* Sizes of a built octree: h_voxels[dp] for dp < num_depths and
+ * h_corners[l-1] for LOD l = 1..num_depths-3 (either array may be NULL). */
+int svo_info(const nglod_svo* svo, int* h_num_depths, int64_t* h_voxels,
+             int64_t* h_corners);
+
+/* Device arrays owned by the handle, for inspection: per voxel of depth dp,
+ * Node {uint32 ijk packed i | j<<10 | k<<20, int32 childbase, uint32
+ * childmask, int32 parent} (16 B each) and, for dp >= 3, int32 corner ids
+ * [V, 8] (corner c = cx | cy<<1 | cz<<2).  Pointers stay valid until
+ * svo_free.  corners is set to NULL for dp < 3. */
+int svo_device_arrays(const nglod_svo* svo, int dp, const void** node,
+                      const int32_t** corners);
+
+/* Copies depth dp's arrays to host memory (synchronous): h_node [V, 4] int32
+ * Node records as above, h_corners [V, 8] and h_anc [V, 8] int32 (the voxel
+ * ids at depths 3..dp containing each voxel, -1 beyond dp; dp >= 3 only).
+ * Any output may be NULL. */
+int svo_read_arrays(const nglod_svo* svo, int dp, void* h_node, int32_t* h_corners,
+                    int32_t* h_anc);
+
+/* Releases the handle and its device memory (NULL is allowed). */
+void svo_free(nglod_svo* svo);
+
+/* Workspace bytes svo_trace_rays needs for R rays and intermediate ray/voxel
+ * lists of up to pair_capacity entries per level. */
+size_t svo_trace_rays_workspace(int64_t R, int64_t pair_capacity);
+
+/* svo_trace_rays -- Algorithm 1 (RayTraceOctree) with Decide, ExclusiveSum,
+ * Subdivide and Compactify of supplementary Sec. C, level by level from the
+ * root down to depth target_lod + 2.  Front-to-back child order: rank
+ * r = 0..7 visits child slot r XOR o, o = octant of the ray origin relative to
+ * the voxel centre (bit a set iff origin_a >= centre_a).  Slab tests are FP32
+ * round-to-nearest without contraction; a box is hit iff
+ * max(t_near, 0) <= t_far (closed intervals).  A ray with a NaN/Inf component
+ * or an all-zero direction hits nothing; a direction component below FLT_MIN
+ * in magnitude makes that axis parallel.
+ *   o, d          [R, 3] float32 origins / directions (device).
+ *   work          device workspace of work_bytes >= svo_trace_rays_workspace(
+ *                 R, pair_capacity); contents are scratch.
+ * Outputs (CSR over rays, grouped by ray, front to back within a ray):
+ *   ray_offsets   [R + 1] int32; hits of ray i are [ray_offsets[i],
+ *                 ray_offsets[i+1]).
+ *   voxel_id      [hit_capacity] int32 voxel ids at the target depth.
+ *   t_range       [hit_capacity, 2] float32 (t_enter, t_exit) per hit.
+ *   h_stats       host int64[2] (nullable): [0] = total hits H, [1] = largest
+ *                 intermediate list (pairs) seen.
+ * Errors: NGLOD_ERR_CAPACITY if H > hit_capacity or a list exceeds
+ * pair_capacity (h_stats then holds the sizes needed so far; outputs are
+ * unspecified); NGLOD_ERR_INVALID_ARG; NGLOD_ERR_TIMEOUT if the scan's
+ * bounded look-back wait expired.  Synchronises the stream (to read H). */
+int svo_trace_rays(const nglod_svo* svo, const float* o, const float* d, int64_t R,
+                   int target_lod, void* work, size_t work_bytes, int64_t pair_capacity,
+                   int32_t* ray_offsets, int32_t* voxel_id, float* t_range,
+                   int64_t hit_capacity, int64_t* h_stats, void* stream);
+
+/* sdf_query -- Sec. 3.2 and Eq. 2: for each point x, the voxels containing it
+ * at depths 3..lod+2 (found from the root through the child masks using
+ * q = fl32(x + 1), ijk = clamp(floor(q 2^(dp-1)), 0, 2^dp - 1)); per level the
+ * trilinear interpolation psi of the 8 corner features with weights from
+ * u = clamp(q 2^(dp-1) - ijk, 0, 1); z = sum of psi over levels; then the
+ * decoder of that LOD.  A level whose voxel is absent (and every deeper one)
+ * contributes 0; points outside [-1,1]^3 see z = 0.
+ *   x         [Q, 3] float32.   sdf  [Q] float32 output.
+ *   deepest   [Q] int8 (nullable): deepest LOD with a containing voxel (0 none).
+ *   grad      [Q, 3] float32 (nullable): analytic d sdf / dx (FP32 decode).
+ *   decode_dtype  NGLOD_F32 or NGLOD_BF16.
+ * Errors: NGLOD_ERR_INVALID_ARG (lod outside 1..num_depths-3, missing
+ * features), NGLOD_ERR_NOT_SUPPORTED (m != 32, hidden != 128, in_dim not 32 or
+ * 35, grad with BF16 decode).  Does not synchronise. */
+int sdf_query(const nglod_svo* svo, const nglod_features* feats,
+              const nglod_decoder* dec, const float* x, int64_t Q, int lod,
+              int decode_dtype, float* sdf, int8_t* deepest, float* grad,
+              void* stream);
+
+/* Workspace bytes sphere_trace needs for R rays. */
+size_t sphere_trace_workspace(int64_t R);
+
+/* sphere_trace -- Sec. 3.4 (Adaptive Ray Stepping) with the stopping rules
+ * of supplementary Sec. A.4.  Per ray, with its list from svo_trace_rays at
+ * the same LOD: t starts at the first entry; each iteration advances the
+ * list cursor past entries with t_exit < t (the ray misses when the list runs
+ * out), moves t up to the current entry's t_enter, queries the SDF at
+ * x = o + t d from that voxel and its ancestors, and counts one step; d < eps
+ * is a hit, otherwise t += d; t > far_t or max_steps reached is a miss.
+ *   o, d, R, lod        as for svo_trace_rays (same rays, same LOD).
+ *   ray_offsets, voxel_id, t_range   the CSR lists of svo_trace_rays.
+ *   work                device workspace >= sphere_trace_workspace(R).
+ * Outputs: t_hit [R] (+inf on miss), hit [R] uint8, steps [R] int32
+ * (nullable: decodes taken), normal [R, 3] (nullable; normalised analytic
+ * gradient of the decoded SDF at the hit point in FP32, zero on miss).
+ * Errors: as sdf_query, plus NGLOD_ERR_INVALID_ARG for bad params.  Does not
+ * synchronise. */
+int sphere_trace(const nglod_svo* svo, const nglod_features* feats,
+                 const nglod_decoder* dec, const float* o, const float* d, int64_t R,
+                 int lod, const nglod_trace_params* params, const int32_t* ray_offsets,
+                 const int32_t* voxel_id, const float* t_range, void* work,
+                 size_t work_bytes, float* t_hit, uint8_t* hit, int32_t* steps,
+                 float* normal, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NGLOD_H */

@@ -1,0 +1,509 @@
+// sdf_query, sphere_trace (FP32 decode) and the analytic-gradient kernel.
+//
+// Decoder (Eq. 2) on CUDA cores: one thread per query evaluates the whole
+// 35(32) -> 128 -> 1 MLP.  The decoder's 4737 (4608) parameters are passed as
+// the kernel's parameter block, which lives in the constant bank: with the
+// loops fully unrolled every weight is an immediate constant-bank operand of
+// its FFMA, broadcast to the warp, so the decode issues no shared- or
+// global-memory loads at all.
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "nglod_internal.cuh"
+#include "query_common.cuh"
+#include "trace_common.cuh"
+
+namespace nglod {
+
+int fill_tables(const nglod_svo* svo, const nglod_features* f, int lod, Tables& tb) {
+    const int D = lod + kFirstFeatureDepth - 1;
+    if (!f) return fail(NGLOD_ERR_INVALID_ARG, "NULL features");
+    if (f->m != kFeatDim) return fail(NGLOD_ERR_NOT_SUPPORTED, "only m = 32 features are built");
+    if (f->dtype != NGLOD_F32 && f->dtype != NGLOD_F16)
+        return fail(NGLOD_ERR_NOT_SUPPORTED, "features must be F32 or F16");
+    if (f->num_lods < lod) return fail(NGLOD_ERR_INVALID_ARG, "features do not cover the requested LOD");
+    for (int l = 0; l < kMaxLods; ++l) tb.feats[l] = nullptr;
+    for (int l = 1; l <= lod; ++l) {
+        if (!f->feats[l - 1]) return fail(NGLOD_ERR_INVALID_ARG, "NULL feature table for a LOD <= lod");
+        tb.feats[l - 1] = f->feats[l - 1];
+    }
+    for (int d = 0; d <= kMaxDepth; ++d) {
+        const bool ok = d < svo->num_depths && d <= D;
+        tb.node[d] = ok ? svo->node[d] : nullptr;
+        tb.corners[d] = ok ? svo->corners[d] : nullptr;
+        tb.anc[d] = ok ? svo->anc[d] : nullptr;
+    }
+    return NGLOD_OK;
+}
+
+int fill_dec_params(const nglod_decoder* dec, DecParams& P, cudaStream_t st) {
+    if (!dec) return fail(NGLOD_ERR_INVALID_ARG, "NULL decoder");
+    if (dec->hidden != kHidden) return fail(NGLOD_ERR_NOT_SUPPORTED, "only hidden = 128 is built");
+    if (dec->in_dim != 32 && dec->in_dim != 35) return fail(NGLOD_ERR_NOT_SUPPORTED, "in_dim must be 32 or 35");
+    const int n1 = kHidden * dec->in_dim;
+    if (dec->h_W1 && dec->h_b1 && dec->h_W2) {
+        std::copy(dec->h_W1, dec->h_W1 + n1, P.W1);
+        std::copy(dec->h_b1, dec->h_b1 + kHidden, P.b1);
+        std::copy(dec->h_W2, dec->h_W2 + kHidden, P.W2);
+    } else {
+        if (!dec->W1 || !dec->b1 || !dec->W2) return fail(NGLOD_ERR_INVALID_ARG, "NULL decoder weights");
+        NGLOD_CUDA(cudaMemcpyAsync(P.W1, dec->W1, sizeof(float) * n1, cudaMemcpyDeviceToHost, st));
+        NGLOD_CUDA(cudaMemcpyAsync(P.b1, dec->b1, sizeof(float) * kHidden, cudaMemcpyDeviceToHost, st));
+        NGLOD_CUDA(cudaMemcpyAsync(P.W2, dec->W2, sizeof(float) * kHidden, cudaMemcpyDeviceToHost, st));
+        NGLOD_CUDA(cudaStreamSynchronize(st));
+    }
+    P.b2 = dec->b2;
+    return NGLOD_OK;
+}
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+
+// ---------------------------------------------------------------------------
+// sdf_query (FP32 decode)
+// ---------------------------------------------------------------------------
+template <typename T, int IN>
+__global__ void __launch_bounds__(kThreads) k_sdf_query(const __grid_constant__ DecParams P,
+                                                        const Tables tb, const float* __restrict__ x,
+                                                        long long Q, int D, float* __restrict__ sdf,
+                                                        int8_t* __restrict__ deepest) {
+    __shared__ __align__(16) float zbuf[kWarps][32 * kZStride];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = lane >> 3, l = lane & 7, gbase = g << 3;
+    const unsigned gmask = 0xffu << gbase;
+    float* zb = zbuf[warp];
+    for (long long base = ((long long)blockIdx.x * kWarps + warp) * 32; base < Q;
+         base += (long long)gridDim.x * kWarps * 32) {
+        const long long qi = base + lane;
+        const bool act = qi < Q;
+        float x0 = 0.f, x1 = 0.f, x2 = 0.f;
+        if (act) {
+            x0 = x[3 * qi];
+            x1 = x[3 * qi + 1];
+            x2 = x[3 * qi + 2];
+        }
+        int vox;
+        uint32_t ijk;
+        const int dd = act ? locate_descend(tb, D, x0, x1, x2, vox, ijk) : -1;
+        const float q0 = __fadd_rn(x0, 1.0f), q1 = __fadd_rn(x1, 1.0f), q2 = __fadd_rn(x2, 1.0f);
+#pragma unroll 1
+        for (int r = 0; r < 8; ++r) {
+            const int s = r * 4 + g;
+            const int sdd = __shfl_sync(0xffffffffu, dd, s);
+            const int svox = __shfl_sync(0xffffffffu, vox, s);
+            const uint32_t sijk = __shfl_sync(0xffffffffu, ijk, s);
+            const float s0 = __shfl_sync(0xffffffffu, q0, s);
+            const float s1 = __shfl_sync(0xffffffffu, q1, s);
+            const float s2 = __shfl_sync(0xffffffffu, q2, s);
+            float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (sdd >= kFirstFeatureDepth) z = gather_slot<T>(tb, sdd, svox, sijk, s0, s1, s2, gmask, gbase, l);
+            *reinterpret_cast<float4*>(zb + s * kZStride + 4 * l) = z;
+        }
+        __syncwarp();
+        const float out = mlp_f32<IN>(P, zb + lane * kZStride, x0, x1, x2);
+        if (act) {
+            sdf[qi] = out;
+            if (deepest) deepest[qi] = (int8_t)(dd >= kFirstFeatureDepth ? dd - kFirstFeatureDepth + 1 : 0);
+        }
+        __syncwarp();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Analytic gradient d sdf / dx (FP32): sdf_query(grad) and trace normals.
+// One group of 8 lanes per item; decoder weights staged in shared memory
+// (W1 transposed, [in][128]) so lane l reads hidden units 32i + 4l + j.
+// ---------------------------------------------------------------------------
+struct GradArgs {
+    const float* x;        // mode 0: [Q, 3] points
+    const float* o;        // mode 1: rays
+    const float* d;
+    const float* t_hit;
+    const uint8_t* hit;
+    const int32_t* hit_vox;
+    long long n;
+    int D;
+    int mode;              // 0 query gradient, 1 normalised trace normal
+    float* out;            // [n, 3]
+};
+
+template <typename T, int IN>
+__global__ void __launch_bounds__(kThreads) k_grad(const float* __restrict__ W1, const float* __restrict__ b1,
+                                                   const float* __restrict__ W2, const Tables tb,
+                                                   const GradArgs A) {
+    __shared__ __align__(16) float sW1T[IN][kHidden];
+    __shared__ __align__(16) float sb1[kHidden];
+    __shared__ __align__(16) float sW2[kHidden];
+    for (int i = threadIdx.x; i < IN * kHidden; i += blockDim.x) {
+        const int h = i / IN, k = i - h * IN;
+        sW1T[k][h] = W1[i];
+    }
+    for (int i = threadIdx.x; i < kHidden; i += blockDim.x) {
+        sb1[i] = b1[i];
+        sW2[i] = W2[i];
+    }
+    __syncthreads();
+    constexpr int OFF = IN - kFeatDim;
+    const int lane = threadIdx.x & 31, g = lane >> 3, l = lane & 7, gbase = (threadIdx.x & ~31) + (g << 3);
+    const int wbase = gbase & 31;
+    const unsigned gmask = 0xffu << wbase;
+    const long long groups = (long long)gridDim.x * (blockDim.x / 8);
+    for (long long it = (long long)blockIdx.x * (blockDim.x / 8) + (threadIdx.x >> 3); it < A.n; it += groups) {
+        float x[3];
+        int dd, vox;
+        uint32_t ijk;
+        if (A.mode == 1) {
+            if (!A.hit[it]) {
+                if (l < 3) A.out[3 * it + l] = 0.0f;
+                continue;
+            }
+            const float t = A.t_hit[it];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) x[a] = fmaf(t, A.d[3 * it + a], A.o[3 * it + a]);
+            dd = A.D;
+            vox = A.hit_vox[it];
+            ijk = tb.node[dd][vox].ijk;
+        } else {
+#pragma unroll
+            for (int a = 0; a < 3; ++a) x[a] = A.x[3 * it + a];
+            dd = locate_descend(tb, A.D, x[0], x[1], x[2], vox, ijk);
+        }
+        const float q[3] = {__fadd_rn(x[0], 1.0f), __fadd_rn(x[1], 1.0f), __fadd_rn(x[2], 1.0f)};
+        // z and dz/dx for this lane's 4 channels
+        float z[4] = {0.f, 0.f, 0.f, 0.f};
+        float jz[4][3] = {};
+        if (dd >= kFirstFeatureDepth) {
+            const int a = (l <= dd - kFirstFeatureDepth) ? __ldg(tb.anc[dd] + (size_t)vox * 8 + l) : -1;
+            for (int dp = kFirstFeatureDepth; dp <= dd; ++dp) {
+                const int v = __shfl_sync(gmask, a, wbase + dp - kFirstFeatureDepth);
+                const int cid = __ldg(tb.corners[dp] + (size_t)v * 8 + l);
+                const int sh = dd - dp;
+                const float sc = pow2f(dp - 1);
+                const uint32_t cc[3] = {unpack_i(ijk) >> sh, unpack_j(ijk) >> sh, unpack_k(ijk) >> sh};
+                float u[3];
+#pragma unroll
+                for (int aa = 0; aa < 3; ++aa) u[aa] = clamp01(__fsub_rn(__fmul_rn(q[aa], sc), (float)cc[aa]));
+                const void* fb = tb.feats[dp - kFirstFeatureDepth];
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    const float4 r = FeatLoad<T>::load(fb, __shfl_sync(gmask, cid, wbase + c), l);
+                    float f[3], df[3];
+#pragma unroll
+                    for (int aa = 0; aa < 3; ++aa) {
+                        const bool up = (c >> aa) & 1;
+                        f[aa] = up ? u[aa] : 1.0f - u[aa];
+                        df[aa] = up ? sc : -sc;
+                    }
+                    const float w = f[0] * f[1] * f[2];
+                    const float dw[3] = {df[0] * f[1] * f[2], f[0] * df[1] * f[2], f[0] * f[1] * df[2]};
+                    const float rv[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        z[j] = fmaf(w, rv[j], z[j]);
+#pragma unroll
+                        for (int aa = 0; aa < 3; ++aa) jz[j][aa] = fmaf(dw[aa], rv[j], jz[j][aa]);
+                    }
+                }
+            }
+        }
+        // pre-activations of this lane's 16 hidden units h = 32 i + 4 l + j
+        float pre[16];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const float4 b = *reinterpret_cast<const float4*>(&sb1[32 * i + 4 * l]);
+            pre[4 * i] = b.x; pre[4 * i + 1] = b.y; pre[4 * i + 2] = b.z; pre[4 * i + 3] = b.w;
+        }
+        auto accum_pre = [&](int k, float vk) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const float4 w = *reinterpret_cast<const float4*>(&sW1T[k][32 * i + 4 * l]);
+                pre[4 * i] = fmaf(w.x, vk, pre[4 * i]);
+                pre[4 * i + 1] = fmaf(w.y, vk, pre[4 * i + 1]);
+                pre[4 * i + 2] = fmaf(w.z, vk, pre[4 * i + 2]);
+                pre[4 * i + 3] = fmaf(w.w, vk, pre[4 * i + 3]);
+            }
+        };
+#pragma unroll
+        for (int k = 0; k < OFF; ++k) accum_pre(k, x[k]);
+#pragma unroll 1
+        for (int sl = 0; sl < 8; ++sl) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) accum_pre(OFF + 4 * sl + j, __shfl_sync(gmask, z[j], wbase + sl));
+        }
+        float gh[16];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const float4 w = *reinterpret_cast<const float4*>(&sW2[32 * i + 4 * l]);
+            gh[4 * i] = pre[4 * i] > 0.f ? w.x : 0.f;
+            gh[4 * i + 1] = pre[4 * i + 1] > 0.f ? w.y : 0.f;
+            gh[4 * i + 2] = pre[4 * i + 2] > 0.f ? w.z : 0.f;
+            gh[4 * i + 3] = pre[4 * i + 3] > 0.f ? w.w : 0.f;
+        }
+        float gx[3] = {0.f, 0.f, 0.f};
+        float gz[4] = {0.f, 0.f, 0.f, 0.f};
+        auto back_k = [&](int k) {
+            float p = 0.f;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const float4 w = *reinterpret_cast<const float4*>(&sW1T[k][32 * i + 4 * l]);
+                p = fmaf(gh[4 * i], w.x, p);
+                p = fmaf(gh[4 * i + 1], w.y, p);
+                p = fmaf(gh[4 * i + 2], w.z, p);
+                p = fmaf(gh[4 * i + 3], w.w, p);
+            }
+            p += __shfl_xor_sync(gmask, p, 1);
+            p += __shfl_xor_sync(gmask, p, 2);
+            p += __shfl_xor_sync(gmask, p, 4);
+            return p;
+        };
+#pragma unroll
+        for (int k = 0; k < OFF; ++k) gx[k] = back_k(k);
+#pragma unroll 1
+        for (int sl = 0; sl < 8; ++sl) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const float p = back_k(OFF + 4 * sl + j);
+                if (sl == l) gz[j] = p;
+            }
+        }
+        float part[3];
+#pragma unroll
+        for (int aa = 0; aa < 3; ++aa) {
+            part[aa] = gz[0] * jz[0][aa] + gz[1] * jz[1][aa] + gz[2] * jz[2][aa] + gz[3] * jz[3][aa];
+            part[aa] += __shfl_xor_sync(gmask, part[aa], 1);
+            part[aa] += __shfl_xor_sync(gmask, part[aa], 2);
+            part[aa] += __shfl_xor_sync(gmask, part[aa], 4);
+            gx[aa] += part[aa];
+        }
+        if (A.mode == 1) {
+            const float nn = sqrtf(gx[0] * gx[0] + gx[1] * gx[1] + gx[2] * gx[2]);
+            const float inv = nn > 0.f ? 1.0f / nn : 0.f;
+#pragma unroll
+            for (int aa = 0; aa < 3; ++aa) gx[aa] *= inv;
+        }
+        if (l < 3) A.out[3 * it + l] = l == 0 ? gx[0] : (l == 1 ? gx[1] : gx[2]);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Sphere tracing with adaptive stepping, FP32 decode (Sec. 3.4, A.4)
+// ---------------------------------------------------------------------------
+template <typename T, int IN>
+__global__ void __launch_bounds__(kThreads) k_trace_f32(const __grid_constant__ DecParams P,
+                                                        const Tables tb, const TraceArgs A) {
+    __shared__ __align__(16) float zbuf[kWarps][32 * kZStride];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = lane >> 3, l = lane & 7, gbase = g << 3;
+    const unsigned gmask = 0xffu << gbase;
+    float* zb = zbuf[warp];
+    RaySlot S;
+    S.ray = -1;
+    RayQueue Qu;
+    Qu.init();
+    for (;;) {
+        refill(S, Qu, A, tb, lane);
+        if (__ballot_sync(0xffffffffu, S.ray >= 0) == 0u) break;
+        const bool act = S.ray >= 0;
+        const float x0 = fmaf(S.t, S.dx, S.ox), x1 = fmaf(S.t, S.dy, S.oy), x2 = fmaf(S.t, S.dz, S.oz);
+        const float q0 = __fadd_rn(x0, 1.0f), q1 = __fadd_rn(x1, 1.0f), q2 = __fadd_rn(x2, 1.0f);
+#pragma unroll 1
+        for (int r = 0; r < 8; ++r) {
+            const int s = r * 4 + g;
+            const int sact = __shfl_sync(0xffffffffu, act ? 1 : 0, s);
+            const int svox = __shfl_sync(0xffffffffu, S.vox, s);
+            const uint32_t sijk = __shfl_sync(0xffffffffu, S.ijk, s);
+            const float s0 = __shfl_sync(0xffffffffu, q0, s);
+            const float s1 = __shfl_sync(0xffffffffu, q1, s);
+            const float s2 = __shfl_sync(0xffffffffu, q2, s);
+            float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (sact) z = gather_slot<T>(tb, A.D, svox, sijk, s0, s1, s2, gmask, gbase, l);
+            *reinterpret_cast<float4*>(zb + s * kZStride + 4 * l) = z;
+        }
+        __syncwarp();
+        const float dhat = mlp_f32<IN>(P, zb + lane * kZStride, x0, x1, x2);
+        __syncwarp();
+        if (act) step_update(S, dhat, A, tb);
+    }
+}
+
+template <typename T, int IN>
+void launch_trace_f32(const DecParams& P, const Tables& tb, const TraceArgs& A, int grid, cudaStream_t st) {
+    k_trace_f32<T, IN><<<grid, kThreads, 0, st>>>(P, tb, A);
+}
+
+template <typename T, int IN>
+void launch_query(const DecParams& P, const Tables& tb, const float* x, long long Q, int D, float* sdf,
+                  int8_t* deepest, int grid, cudaStream_t st) {
+    k_sdf_query<T, IN><<<grid, kThreads, 0, st>>>(P, tb, x, Q, D, sdf, deepest);
+}
+
+template <typename T, int IN>
+void launch_grad(const nglod_decoder* dec, const Tables& tb, const GradArgs& A, int grid, cudaStream_t st) {
+    k_grad<T, IN><<<grid, kThreads, 0, st>>>(dec->W1, dec->b1, dec->W2, tb, A);
+}
+
+int grid_items(long long n, int per_cta, int sms, int ctas_per_sm) {
+    const long long g = (n + per_cta - 1) / per_cta;
+    return (int)std::max<long long>(1, std::min<long long>(g, (long long)sms * ctas_per_sm));
+}
+
+int run_grad(const nglod_decoder* dec, const Tables& tb, const GradArgs& A, bool f16, int sms,
+             cudaStream_t st) {
+    const int grid = grid_items(A.n, kThreads / 8, sms, 8);
+    if (dec->in_dim == 35) {
+        if (f16) launch_grad<__half, 35>(dec, tb, A, grid, st); else launch_grad<float, 35>(dec, tb, A, grid, st);
+    } else {
+        if (f16) launch_grad<__half, 32>(dec, tb, A, grid, st); else launch_grad<float, 32>(dec, tb, A, grid, st);
+    }
+    NGLOD_CUDA(cudaGetLastError());
+    return NGLOD_OK;
+}
+
+}  // namespace
+
+int launch_trace_fp32(const nglod_decoder* dec, const DecParams& P, const Tables& tb, const TraceArgs& A,
+                      bool f16, int sms, cudaStream_t st) {
+    const int grid = sms * 3;
+    if (dec->in_dim == 35) {
+        if (f16) launch_trace_f32<__half, 35>(P, tb, A, grid, st); else launch_trace_f32<float, 35>(P, tb, A, grid, st);
+    } else {
+        if (f16) launch_trace_f32<__half, 32>(P, tb, A, grid, st); else launch_trace_f32<float, 32>(P, tb, A, grid, st);
+    }
+    NGLOD_CUDA(cudaGetLastError());
+    return NGLOD_OK;
+}
+
+int launch_normals(const nglod_decoder* dec, const Tables& tb, const TraceArgs& A, float* normal, bool f16,
+                   int sms, cudaStream_t st) {
+    GradArgs G{};
+    G.o = A.o;
+    G.d = A.d;
+    G.t_hit = A.t_hit;
+    G.hit = A.hit;
+    G.hit_vox = A.hit_vox;
+    G.n = A.R;
+    G.D = A.D;
+    G.mode = 1;
+    G.out = normal;
+    return run_grad(dec, tb, G, f16, sms, st);
+}
+
+}  // namespace nglod
+
+using namespace nglod;
+
+extern "C" int sdf_query(const nglod_svo* svo, const nglod_features* feats, const nglod_decoder* dec,
+                         const float* x, int64_t Q, int lod, int decode_dtype, float* sdf, int8_t* deepest,
+                         float* grad, void* stream) {
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!svo) return fail(NGLOD_ERR_INVALID_ARG, "sdf_query: NULL octree");
+    const int D = lod + kFirstFeatureDepth - 1;
+    if (lod < 1 || D >= svo->num_depths) return fail(NGLOD_ERR_INVALID_ARG, "sdf_query: lod out of range");
+    if (Q < 0) return fail(NGLOD_ERR_INVALID_ARG, "sdf_query: Q < 0");
+    if (Q == 0) return NGLOD_OK;
+    if (!x || !sdf) return fail(NGLOD_ERR_INVALID_ARG, "sdf_query: NULL x or sdf");
+    Tables tb;
+    int rc = fill_tables(svo, feats, lod, tb);
+    if (rc) return rc;
+    const bool f16 = feats->dtype == NGLOD_F16;
+    if (decode_dtype == NGLOD_BF16) {
+        if (grad) return fail(NGLOD_ERR_NOT_SUPPORTED, "sdf_query: grad needs the FP32 decode");
+        rc = launch_query_bf16(svo, tb, dec, x, Q, D, sdf, deepest, f16, st);
+        if (rc) return rc;
+        return NGLOD_OK;
+    }
+    if (decode_dtype != NGLOD_F32) return fail(NGLOD_ERR_NOT_SUPPORTED, "sdf_query: decode_dtype");
+    DecParams P;
+    rc = fill_dec_params(dec, P, st);
+    if (rc) return rc;
+    const int grid = grid_items(Q, kThreads, svo->num_sms, 4);
+    if (dec->in_dim == 35) {
+        if (f16) launch_query<__half, 35>(P, tb, x, Q, D, sdf, deepest, grid, st);
+        else launch_query<float, 35>(P, tb, x, Q, D, sdf, deepest, grid, st);
+    } else {
+        if (f16) launch_query<__half, 32>(P, tb, x, Q, D, sdf, deepest, grid, st);
+        else launch_query<float, 32>(P, tb, x, Q, D, sdf, deepest, grid, st);
+    }
+    NGLOD_CUDA(cudaGetLastError());
+    if (grad) {
+        GradArgs G{};
+        G.x = x;
+        G.n = Q;
+        G.D = D;
+        G.mode = 0;
+        G.out = grad;
+        rc = run_grad(dec, tb, G, f16, svo->num_sms, st);
+        if (rc) return rc;
+    }
+    return NGLOD_OK;
+}
+
+extern "C" size_t sphere_trace_workspace(int64_t R) {
+    if (R < 0) return 0;
+    return 256 + ((sizeof(int32_t) * (size_t)R + 255) / 256) * 256;
+}
+
+extern "C" int sphere_trace(const nglod_svo* svo, const nglod_features* feats, const nglod_decoder* dec,
+                            const float* o, const float* d, int64_t R, int lod,
+                            const nglod_trace_params* params, const int32_t* ray_offsets,
+                            const int32_t* voxel_id, const float* t_range, void* work, size_t work_bytes,
+                            float* t_hit, uint8_t* hit, int32_t* steps, float* normal, void* stream) {
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!svo || !params) return fail(NGLOD_ERR_INVALID_ARG, "sphere_trace: NULL octree or params");
+    const int D = lod + kFirstFeatureDepth - 1;
+    if (lod < 1 || D >= svo->num_depths) return fail(NGLOD_ERR_INVALID_ARG, "sphere_trace: lod out of range");
+    if (R < 0 || R >= (1ll << 31) - 64) return fail(NGLOD_ERR_INVALID_ARG, "sphere_trace: bad R");
+    if (!(params->eps > 0.0f) || !(params->far_t > 0.0f) || params->max_steps < 1)
+        return fail(NGLOD_ERR_INVALID_ARG, "sphere_trace: eps, far_t and max_steps must be positive");
+    if (R == 0) return NGLOD_OK;
+    if (!o || !d || !ray_offsets || !t_hit || !hit || !work)
+        return fail(NGLOD_ERR_INVALID_ARG, "sphere_trace: NULL argument");
+    if (work_bytes < sphere_trace_workspace(R)) return fail(NGLOD_ERR_CAPACITY, "sphere_trace: workspace too small");
+    if (((uintptr_t)work & 255u) != 0) return fail(NGLOD_ERR_INVALID_ARG, "sphere_trace: work must be 256-B aligned");
+    Tables tb;
+    int rc = fill_tables(svo, feats, lod, tb);
+    if (rc) return rc;
+    if (!dec || dec->hidden != kHidden || (dec->in_dim != 32 && dec->in_dim != 35))
+        return fail(NGLOD_ERR_NOT_SUPPORTED, "sphere_trace: decoder must be 32|35 -> 128 -> 1");
+    const bool f16 = feats->dtype == NGLOD_F16;
+    TraceArgs A;
+    A.o = o;
+    A.d = d;
+    A.R = R;
+    A.D = D;
+    A.eps = params->eps;
+    A.far_t = params->far_t;
+    A.max_steps = params->max_steps;
+    A.osc = params->osc_check;
+    A.offs = ray_offsets;
+    A.vid = voxel_id;
+    A.tr = (const float2*)t_range;
+    A.t_hit = t_hit;
+    A.hit = hit;
+    A.steps = steps;
+    A.queue = (int*)work;
+    A.hit_vox = (int32_t*)((char*)work + 256);
+    NGLOD_CUDA(cudaMemsetAsync(work, 0, 256, st));
+    if (params->decode_dtype == NGLOD_F32) {
+        DecParams P;
+        rc = fill_dec_params(dec, P, st);
+        if (rc) return rc;
+        rc = launch_trace_fp32(dec, P, tb, A, f16, svo->num_sms, st);
+    } else if (params->decode_dtype == NGLOD_BF16) {
+        rc = launch_trace_bf16(svo, dec, tb, A, f16, st);
+    } else {
+        return fail(NGLOD_ERR_NOT_SUPPORTED, "sphere_trace: decode_dtype must be F32 or BF16");
+    }
+    if (rc) return rc;
+    if (normal && params->want_normals) {
+        rc = launch_normals(dec, tb, A, normal, f16, svo->num_sms, st);
+        if (rc) return rc;
+    }
+    return NGLOD_OK;
+}

@@ -1,0 +1,373 @@
+// svo_trace_rays: level-synchronous ray/octree intersection.
+//
+// Algorithm 1 of the paper runs, per octree level, Decide (one thread per
+// ray/voxel pair), ExclusiveSum of the decisions, then Subdivide (write the
+// hit voxels' occupied children, front to back) or, at the target level,
+// Compactify (keep the hit pairs).  Here the three steps of one level are a
+// single kernel: each CTA takes the next tile of the pair list (tiles are
+// handed out in order by an atomic counter), decides its pairs, scans the
+// decisions inside the CTA, obtains the tile's global offset with a
+// decoupled look-back over the preceding tiles' published sums, and writes
+// its children (or compacted hits) straight to their final positions.  The
+// decisions and their prefix sums never touch memory, the list sizes stay on
+// the device, and no host round trip happens between levels.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <string>
+
+#include "nglod_internal.cuh"
+
+namespace nglod {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kItems = 4;
+constexpr int kTile = kThreads * kItems;
+constexpr int kCtasPerSm = 6;
+constexpr unsigned long long kFlagAgg = 1ull << 62;
+constexpr unsigned long long kFlagPre = 2ull << 62;
+constexpr unsigned long long kValMask = (1ull << 62) - 1;
+constexpr long kSpinLimit = 1l << 22;   // ~0.1-1 s of waiting, then time out
+
+struct Counters {
+    long long count[kMaxDepth + 2];   // list length entering each depth
+    long long max_pairs;
+    int tile_ctr[kMaxDepth + 2];
+    int status;                        // kStatus*
+};
+
+struct LevelParams {
+    const RayPrep* rays;
+    const Node* node;                  // voxels of depth dp
+    const int2* in;                    // pairs entering depth dp (NULL at dp 0)
+    int2* out;                         // children (dp < D)
+    long long out_cap;
+    int32_t* voxel_id;                 // dp == D outputs
+    float2* t_range;
+    int32_t* out_ray;
+    long long hit_cap;
+    Counters* ctr;
+    unsigned long long* tile_state;
+    int dp, D;
+};
+
+__device__ __forceinline__ void st_release(unsigned long long* p, unsigned long long v) {
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Exclusive prefix of this tile among all tiles (decoupled look-back).
+// Called by one thread.  Every wait is bounded; on expiry the status word
+// records a timeout and the (then meaningless) partial prefix is returned.
+__device__ long long tile_prefix(unsigned long long* state, long long tile, long long agg, int* status) {
+    if (tile == 0) {
+        st_release(state, kFlagPre | (unsigned long long)agg);
+        return 0;
+    }
+    st_release(state + tile, kFlagAgg | (unsigned long long)agg);
+    long long excl = 0;
+    long long j = tile - 1;
+    long spins = 0;
+    while (j >= 0) {
+        const unsigned long long s = ld_acquire(state + j);
+        const unsigned long long flag = s & ~kValMask;
+        if (flag == 0ull) {
+            if (++spins > kSpinLimit) {
+                atomicExch(status, kStatusTimeout);
+                break;
+            }
+            if (spins > 64) __nanosleep(64);
+            continue;
+        }
+        excl += (long long)(s & kValMask);
+        if (flag == kFlagPre) break;
+        --j;
+    }
+    st_release(state + tile, kFlagPre | (unsigned long long)(excl + agg));
+    return excl;
+}
+
+__device__ __forceinline__ int block_exclusive_sum(int v, int* warp_sums, int& total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) warp_sums[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        const int s = lane < kThreads / 32 ? warp_sums[lane] : 0;
+        int si = s;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, si, o);
+            if (lane >= o) si += y;
+        }
+        if (lane < kThreads / 32) warp_sums[lane] = si - s;
+        if (lane == kThreads / 32 - 1) warp_sums[kThreads / 32] = si;
+    }
+    __syncthreads();
+    total = warp_sums[kThreads / 32];
+    return warp_sums[warp] + incl - v;
+}
+
+__global__ void __launch_bounds__(kThreads) k_prep_rays(const float* __restrict__ o,
+                                                        const float* __restrict__ d, long long R,
+                                                        RayPrep* __restrict__ rays, Counters* ctr) {
+    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < R;
+         r += (long long)gridDim.x * blockDim.x) {
+        RayPrep p;
+        p.ox = o[3 * r];
+        p.oy = o[3 * r + 1];
+        p.oz = o[3 * r + 2];
+        const float dd[3] = {d[3 * r], d[3 * r + 1], d[3 * r + 2]};
+        const float oo[3] = {p.ox, p.oy, p.oz};
+        int ok = 1, par = 0;
+        float inv[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            if (!isfinite(oo[a]) || !isfinite(dd[a])) ok = 0;
+            const bool pa = fabsf(dd[a]) < 1.17549435e-38f;
+            par |= pa ? (1 << a) : 0;
+            inv[a] = pa ? 0.0f : __fdiv_rn(1.0f, dd[a]);
+        }
+        if (par == 7) ok = 0;
+        p.ix = inv[0];
+        p.iy = inv[1];
+        p.iz = inv[2];
+        p.par = par;
+        p.valid = ok;
+        rays[r] = p;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) ctr->count[0] = R;
+}
+
+__global__ void __launch_bounds__(kThreads) k_level(const LevelParams p) {
+    __shared__ int warp_sums[kThreads / 32 + 1];
+    __shared__ long long s_tile;
+    __shared__ long long s_prefix;
+    if (p.ctr->status != kStatusOk) return;
+    const long long n = p.ctr->count[p.dp];
+    const long long ntiles = (n + kTile - 1) / kTile;
+    const bool final_level = p.dp == p.D;
+    for (;;) {
+        if (threadIdx.x == 0) s_tile = atomicAdd(&p.ctr->tile_ctr[p.dp], 1);
+        __syncthreads();
+        const long long tile = s_tile;
+        if (tile >= ntiles) break;
+        const long long base = tile * kTile + (long long)threadIdx.x * kItems;
+
+        int2 pr[kItems];
+        int cnt[kItems];
+        uint32_t aux[kItems];      // dp < D: childmask | octant << 8 ; dp == D: unused
+        int32_t cb[kItems];        // dp < D: childbase
+        float tin[kItems], tout[kItems];
+        int sum = 0;
+        if (p.dp > 0 && base + kItems <= n) {
+            const int4* src = reinterpret_cast<const int4*>(p.in + base);
+            const int4 a = src[0], b = src[1];
+            pr[0] = make_int2(a.x, a.y);
+            pr[1] = make_int2(a.z, a.w);
+            pr[2] = make_int2(b.x, b.y);
+            pr[3] = make_int2(b.z, b.w);
+        } else {
+#pragma unroll
+            for (int i = 0; i < kItems; ++i) {
+                const long long idx = base + i;
+                pr[i] = idx < n ? (p.dp == 0 ? make_int2((int)idx, 0) : p.in[idx]) : make_int2(-1, -1);
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < kItems; ++i) {
+            cnt[i] = 0;
+            aux[i] = 0;
+            cb[i] = 0;
+            tin[i] = tout[i] = 0.0f;
+            if (pr[i].x >= 0) {
+                const RayPrep ray = p.rays[pr[i].x];
+                const Node nd = p.node[pr[i].y];
+                float a0, a1;
+                if (ray.valid && slab_test(ray, nd.ijk, p.dp, a0, a1)) {
+                    if (final_level) {
+                        cnt[i] = 1;
+                        tin[i] = a0;
+                        tout[i] = a1;
+                    } else {
+                        cnt[i] = __popc(nd.childmask);
+                        aux[i] = nd.childmask | (origin_octant(ray, nd.ijk, p.dp) << 8);
+                        cb[i] = nd.childbase;
+                    }
+                }
+            }
+            sum += cnt[i];
+        }
+        int tile_total;
+        const int excl = block_exclusive_sum(sum, warp_sums, tile_total);
+        if (threadIdx.x == 0) {
+            const long long pre = tile_prefix(p.tile_state, tile, tile_total, &p.ctr->status);
+            s_prefix = pre;
+            if (tile == ntiles - 1) {
+                const long long total = pre + tile_total;
+                p.ctr->count[p.dp + 1] = total;
+                if (total > p.ctr->max_pairs) p.ctr->max_pairs = total;
+                if (total > (final_level ? p.hit_cap : p.out_cap))
+                    atomicCAS(&p.ctr->status, kStatusOk, kStatusOverflow);
+            }
+        }
+        __syncthreads();
+        long long off = s_prefix + excl;
+        if (final_level) {
+#pragma unroll
+            for (int i = 0; i < kItems; ++i) {
+                if (cnt[i] && off < p.hit_cap) {
+                    p.voxel_id[off] = pr[i].y;
+                    p.t_range[off] = make_float2(tin[i], tout[i]);
+                    p.out_ray[off] = pr[i].x;
+                }
+                off += cnt[i];
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < kItems; ++i) {
+                if (cnt[i]) {
+                    const uint32_t mask = aux[i] & 0xffu, oct = aux[i] >> 8;
+#pragma unroll
+                    for (uint32_t r = 0; r < 8; ++r) {
+                        const uint32_t c = r ^ oct;
+                        if ((mask >> c) & 1u) {
+                            if (off < p.out_cap)
+                                p.out[off] = make_int2(pr[i].x, cb[i] + __popc(mask & ((1u << c) - 1u)));
+                            ++off;
+                        }
+                    }
+                }
+            }
+        }
+        __syncthreads();   // s_tile / s_prefix / warp_sums reuse
+    }
+}
+
+// ray_offsets[r] = first list position whose ray is >= r (binary search).
+__global__ void __launch_bounds__(kThreads) k_ray_offsets(const int32_t* __restrict__ out_ray,
+                                                          const Counters* __restrict__ ctr, int D,
+                                                          long long R, int32_t* __restrict__ offs) {
+    const long long H = ctr->count[D + 1];
+    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r <= R;
+         r += (long long)gridDim.x * blockDim.x) {
+        long long lo = 0, hi = H;
+        while (lo < hi) {
+            const long long mid = lo + ((hi - lo) >> 1);
+            if (out_ray[mid] < r) lo = mid + 1; else hi = mid;
+        }
+        offs[r] = (int32_t)lo;
+    }
+}
+
+size_t align_up(size_t v, size_t a = 256) { return (v + a - 1) / a * a; }
+
+long long max_tiles(long long R, long long cap) {
+    return (std::max(R, cap) + kTile - 1) / kTile + 1;
+}
+
+}  // namespace
+}  // namespace nglod
+
+using namespace nglod;
+
+extern "C" size_t svo_trace_rays_workspace(int64_t R, int64_t pair_capacity) {
+    if (R < 0 || pair_capacity < 0) return 0;
+    return align_up(sizeof(Counters)) + align_up(sizeof(RayPrep) * (size_t)R) +
+           2 * align_up(sizeof(int2) * (size_t)pair_capacity) +
+           align_up(sizeof(unsigned long long) * (size_t)max_tiles(R, pair_capacity));
+}
+
+extern "C" int svo_trace_rays(const nglod_svo* svo, const float* o, const float* d, int64_t R,
+                              int target_lod, void* work, size_t work_bytes, int64_t pair_capacity,
+                              int32_t* ray_offsets, int32_t* voxel_id, float* t_range,
+                              int64_t hit_capacity, int64_t* h_stats, void* stream) {
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!svo) return fail(NGLOD_ERR_INVALID_ARG, "svo_trace_rays: NULL octree");
+    const int D = target_lod + kFirstFeatureDepth - 1;
+    if (target_lod < 1 || D >= svo->num_depths)
+        return fail(NGLOD_ERR_INVALID_ARG, "svo_trace_rays: target_lod outside 1.." +
+                                               std::to_string(svo->num_depths - kFirstFeatureDepth));
+    if (R < 0 || R >= (1ll << 31) - 1 || pair_capacity < 0 || hit_capacity < 0)
+        return fail(NGLOD_ERR_INVALID_ARG, "svo_trace_rays: bad R or capacity");
+    if (!ray_offsets) return fail(NGLOD_ERR_INVALID_ARG, "svo_trace_rays: NULL ray_offsets");
+    if (h_stats) h_stats[0] = h_stats[1] = 0;
+    if (R == 0) {
+        NGLOD_CUDA(cudaMemsetAsync(ray_offsets, 0, sizeof(int32_t), st));
+        return NGLOD_OK;
+    }
+    if (!o || !d || !work) return fail(NGLOD_ERR_INVALID_ARG, "svo_trace_rays: NULL input or workspace");
+    if ((hit_capacity > 0 && (!voxel_id || !t_range)))
+        return fail(NGLOD_ERR_INVALID_ARG, "svo_trace_rays: NULL voxel_id / t_range");
+    if (work_bytes < svo_trace_rays_workspace(R, pair_capacity))
+        return fail(NGLOD_ERR_CAPACITY, "svo_trace_rays: workspace smaller than svo_trace_rays_workspace()");
+    if (((uintptr_t)work & 255u) != 0) return fail(NGLOD_ERR_INVALID_ARG, "svo_trace_rays: work must be 256-B aligned");
+
+    char* w = (char*)work;
+    Counters* ctr = (Counters*)w;
+    w += align_up(sizeof(Counters));
+    RayPrep* rays = (RayPrep*)w;
+    w += align_up(sizeof(RayPrep) * (size_t)R);
+    int2* buf[2];
+    buf[0] = (int2*)w;
+    w += align_up(sizeof(int2) * (size_t)pair_capacity);
+    buf[1] = (int2*)w;
+    w += align_up(sizeof(int2) * (size_t)pair_capacity);
+    unsigned long long* tile_state = (unsigned long long*)w;
+    const long long ntiles_max = max_tiles(R, pair_capacity);
+
+    const int sms = svo->num_sms;
+    NGLOD_CUDA(cudaMemsetAsync(ctr, 0, sizeof(Counters), st));
+    k_prep_rays<<<std::min<long long>((R + kThreads - 1) / kThreads, (long long)sms * 16), kThreads, 0, st>>>(
+        o, d, R, rays, ctr);
+    for (int dp = 0; dp <= D; ++dp) {
+        NGLOD_CUDA(cudaMemsetAsync(tile_state, 0, sizeof(unsigned long long) * ntiles_max, st));
+        LevelParams lp;
+        lp.rays = rays;
+        lp.node = svo->node[dp];
+        lp.in = dp == 0 ? nullptr : buf[dp & 1];
+        lp.out = buf[(dp + 1) & 1];
+        lp.out_cap = pair_capacity;
+        lp.voxel_id = voxel_id;
+        lp.t_range = (float2*)t_range;
+        lp.out_ray = (int32_t*)buf[(dp + 1) & 1];
+        lp.hit_cap = std::min<long long>(hit_capacity, pair_capacity);
+        lp.ctr = ctr;
+        lp.tile_state = tile_state;
+        lp.dp = dp;
+        lp.D = D;
+        const long long grid = std::min<long long>(ntiles_max, (long long)sms * kCtasPerSm);
+        k_level<<<(unsigned)grid, kThreads, 0, st>>>(lp);
+    }
+    k_ray_offsets<<<std::min<long long>((R + kThreads) / kThreads, (long long)sms * 16), kThreads, 0, st>>>(
+        (const int32_t*)buf[(D + 1) & 1], ctr, D, R, ray_offsets);
+    NGLOD_CUDA(cudaGetLastError());
+    Counters h;
+    NGLOD_CUDA(cudaMemcpyAsync(&h, ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
+    NGLOD_CUDA(cudaStreamSynchronize(st));
+    const long long H = h.count[D + 1];
+    if (h_stats) {
+        h_stats[0] = h.status == kStatusOk || H > 0 ? H : 0;
+        h_stats[1] = h.max_pairs;
+    }
+    if (h.status == kStatusTimeout)
+        return fail(NGLOD_ERR_TIMEOUT, "svo_trace_rays: scan look-back wait expired");
+    if (h.status == kStatusOverflow) {
+        long long need = 0;
+        for (int dp = 1; dp <= D; ++dp) need = std::max(need, h.count[dp]);
+        if (h_stats) h_stats[1] = std::max<long long>(need, h.max_pairs);
+        return fail(NGLOD_ERR_CAPACITY, "svo_trace_rays: list larger than capacity (pairs " +
+                                            std::to_string(need) + ", hits " + std::to_string(H) + ")");
+    }
+    return NGLOD_OK;
+}

@@ -1,0 +1,296 @@
+"""Thin Python binding of libnglod (include/nglod.h) for torch CUDA tensors.
+
+Argument marshalling only: every step of the rendering path runs in the CUDA
+library.  The functions keep the C names (svo_build, svo_trace_rays,
+sdf_query, sphere_trace, ...).  If libnglod.so is missing, or no CUDA device
+is present, calls raise -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libnglod.so")
+
+NGLOD_OK, ERR_INVALID_ARG, ERR_CAPACITY, ERR_CUDA, ERR_OOM, ERR_TIMEOUT, ERR_NOT_SUPPORTED = range(7)
+F32, F16, BF16 = 0, 1, 2
+FIRST_FEATURE_DEPTH = 3
+
+EXPORTS = ["nglod_last_error", "svo_build", "svo_info", "svo_device_arrays", "svo_read_arrays", "svo_free",
+           "svo_trace_rays_workspace", "svo_trace_rays", "sdf_query", "sphere_trace_workspace",
+           "sphere_trace"]
+
+
+class NglodError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"[nglod status {code}] {msg}")
+        self.code = code
+
+
+class _Features(C.Structure):
+    _fields_ = [("feats", C.c_void_p * 8), ("dtype", C.c_int), ("m", C.c_int), ("num_lods", C.c_int)]
+
+
+class _Decoder(C.Structure):
+    _fields_ = [("W1", C.c_void_p), ("b1", C.c_void_p), ("W2", C.c_void_p), ("b2", C.c_float),
+                ("in_dim", C.c_int), ("hidden", C.c_int), ("h_W1", C.c_void_p), ("h_b1", C.c_void_p),
+                ("h_W2", C.c_void_p)]
+
+
+class _TraceParams(C.Structure):
+    _fields_ = [("eps", C.c_float), ("far_t", C.c_float), ("max_steps", C.c_int), ("osc_check", C.c_int),
+                ("decode_dtype", C.c_int), ("want_normals", C.c_int)]
+
+
+_lib = None
+
+
+def lib():
+    """Loads libnglod.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "`python -m paper_2101_10994_gb300.build` (no CPU fallback exists)")
+        L = C.CDLL(LIB_PATH)
+        P, i64, i32, sz = C.c_void_p, C.c_int64, C.c_int, C.c_size_t
+        L.nglod_last_error.restype = C.c_char_p
+        L.svo_build.argtypes = [P, P, i32, P, P]
+        L.svo_info.argtypes = [P, P, P, P]
+        L.svo_device_arrays.argtypes = [P, i32, P, P]
+        L.svo_read_arrays.argtypes = [P, i32, P, P, P]
+        L.svo_free.argtypes = [P]
+        L.svo_free.restype = None
+        L.svo_trace_rays_workspace.restype = sz
+        L.svo_trace_rays_workspace.argtypes = [i64, i64]
+        L.svo_trace_rays.argtypes = [P, P, P, i64, i32, P, sz, i64, P, P, P, i64, P, P]
+        L.sdf_query.argtypes = [P, P, P, P, i64, i32, i32, P, P, P, P]
+        L.sphere_trace_workspace.restype = sz
+        L.sphere_trace_workspace.argtypes = [i64]
+        L.sphere_trace.argtypes = [P, P, P, P, P, i64, i32, P, P, P, P, P, sz, P, P, P, P, P]
+        _lib = L
+    return _lib
+
+
+def _check(rc: int):
+    if rc != NGLOD_OK:
+        raise NglodError(rc, lib().nglod_last_error().decode())
+
+
+def _stream(stream=None) -> int:
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def _ptr(t) -> int:
+    return 0 if t is None else t.data_ptr()
+
+
+def _require_cuda(*tensors):
+    for t in tensors:
+        if t is not None and not t.is_cuda:
+            raise ValueError("nglod operates on CUDA tensors only")
+
+
+# ----------------------------------------------------------------------------
+# Octree
+# ----------------------------------------------------------------------------
+class SVO:
+    """Device octree built by svo_build; owns the C handle."""
+
+    def __init__(self, handle: int, keys):
+        self.h = C.c_void_p(handle)
+        n = C.c_int(0)
+        vox = (C.c_int64 * 16)()
+        cor = (C.c_int64 * 16)()
+        _check(lib().svo_info(self.h, C.byref(n), vox, cor))
+        self.num_depths = n.value
+        self.voxels = [vox[i] for i in range(self.num_depths)]
+        self.corners = [cor[i] for i in range(self.num_depths - FIRST_FEATURE_DEPTH)]
+        self.max_lod = self.num_depths - FIRST_FEATURE_DEPTH
+        self._cap = {}
+
+    def free(self):
+        if self.h is not None and self.h.value:
+            lib().svo_free(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    def read_arrays(self, dp: int):
+        """(node [V,4] int32, corners [V,8] int32, anc [V,8] int32) on the host.
+
+        corners / anc are None for the structural depths 0..2."""
+        V = self.voxels[dp]
+        nb = np.empty((V, 4), np.int32)
+        feat = dp >= FIRST_FEATURE_DEPTH
+        cb = np.empty((V, 8), np.int32) if feat else None
+        ab = np.empty((V, 8), np.int32) if feat else None
+        _check(lib().svo_read_arrays(self.h, dp, nb.ctypes.data, cb.ctypes.data if feat else None,
+                                     ab.ctypes.data if feat else None))
+        return nb, cb, ab
+
+
+def svo_build(keys_per_depth, stream=None) -> SVO:
+    keys = [np.ascontiguousarray(k, dtype=np.uint64) for k in keys_per_depth]
+    arr = (C.c_void_p * len(keys))(*[k.ctypes.data for k in keys])
+    counts = np.array([k.shape[0] for k in keys], np.int64)
+    out = C.c_void_p()
+    _check(lib().svo_build(arr, counts.ctypes.data, len(keys), C.c_void_p(_stream(stream)), C.byref(out)))
+    return SVO(out.value, keys)
+
+
+# ----------------------------------------------------------------------------
+# Parameters on the device
+# ----------------------------------------------------------------------------
+class Features:
+    """Corner feature tables of LODs 1..L on the device (float32 or float16)."""
+
+    def __init__(self, tables, dtype: str = "f32", device="cuda"):
+        import torch
+        tdt = {"f32": torch.float32, "f16": torch.float16}[dtype]
+        self.dtype = dtype
+        self.tables = [torch.as_tensor(np.asarray(t)).to(device=device, dtype=tdt).contiguous()
+                       for t in tables]
+        self.m = int(self.tables[0].shape[1])
+
+    def c(self) -> _Features:
+        f = _Features()
+        for i, t in enumerate(self.tables[:8]):
+            f.feats[i] = t.data_ptr()
+        f.dtype = F32 if self.dtype == "f32" else F16
+        f.m = self.m
+        f.num_lods = len(self.tables)
+        return f
+
+
+class DecoderDev:
+    """One LOD's decoder on the device plus its host mirror (FP32 weights)."""
+
+    def __init__(self, W1, b1, W2, b2, device="cuda"):
+        import torch
+        self.h_W1 = np.ascontiguousarray(W1, np.float32)
+        self.h_b1 = np.ascontiguousarray(b1, np.float32)
+        self.h_W2 = np.ascontiguousarray(W2, np.float32)
+        self.b2 = float(b2)
+        self.W1 = torch.from_numpy(self.h_W1).to(device)
+        self.b1 = torch.from_numpy(self.h_b1).to(device)
+        self.W2 = torch.from_numpy(self.h_W2).to(device)
+        self.in_dim = int(self.h_W1.shape[1])
+        self.hidden = int(self.h_W1.shape[0])
+
+    @classmethod
+    def from_decoder(cls, dec, device="cuda"):
+        return cls(dec.W1, dec.b1, dec.W2, dec.b2, device)
+
+    def c(self) -> _Decoder:
+        d = _Decoder()
+        d.W1, d.b1, d.W2 = self.W1.data_ptr(), self.b1.data_ptr(), self.W2.data_ptr()
+        d.b2 = self.b2
+        d.in_dim, d.hidden = self.in_dim, self.hidden
+        d.h_W1, d.h_b1, d.h_W2 = self.h_W1.ctypes.data, self.h_b1.ctypes.data, self.h_W2.ctypes.data
+        return d
+
+
+# ----------------------------------------------------------------------------
+# Calls
+# ----------------------------------------------------------------------------
+@dataclass
+class RayLists:
+    ray_offsets: object      # int32 [R + 1]
+    voxel_id: object         # int32 [H]
+    t_range: object          # float32 [H, 2]
+    max_pairs: int
+    lod: int
+
+
+def svo_trace_rays(svo: SVO, o, d, lod: int, stream=None, pair_capacity: int | None = None,
+                   workspace=None) -> RayLists:
+    """Per-ray front-to-back voxel lists at LOD ``lod`` (CSR).
+
+    Grows the intermediate-list capacity and retries when the library reports
+    NGLOD_ERR_CAPACITY; the capacity that worked is remembered per (R, lod).
+    """
+    import torch
+    _require_cuda(o, d)
+    o = o.contiguous()
+    d = d.contiguous()
+    R = int(o.shape[0])
+    key = (R, lod)
+    cap = pair_capacity or svo._cap.get(key, max(1 << 20, 16 * R))
+    L = lib()
+    stats = (C.c_int64 * 2)()
+    for _ in range(8):
+        wbytes = L.svo_trace_rays_workspace(R, cap)
+        if workspace is not None and workspace.numel() >= wbytes:
+            work = workspace
+        else:
+            work = torch.empty(max(wbytes, 1), dtype=torch.uint8, device=o.device)
+        offs = torch.empty(R + 1, dtype=torch.int32, device=o.device)
+        vid = torch.empty(max(cap, 1), dtype=torch.int32, device=o.device)
+        tr = torch.empty((max(cap, 1), 2), dtype=torch.float32, device=o.device)
+        rc = L.svo_trace_rays(svo.h, o.data_ptr(), d.data_ptr(), R, lod, work.data_ptr(), wbytes, cap,
+                              offs.data_ptr(), vid.data_ptr(), tr.data_ptr(), cap, stats,
+                              C.c_void_p(_stream(stream)))
+        if rc == ERR_CAPACITY:
+            cap = int(max(2 * cap, 1.25 * max(stats[0], stats[1])))
+            continue
+        _check(rc)
+        svo._cap[key] = cap
+        H = int(stats[0])
+        return RayLists(offs, vid[:H], tr[:H], int(stats[1]), lod)
+    raise NglodError(ERR_CAPACITY, "svo_trace_rays: capacity growth did not converge")
+
+
+def sdf_query(svo: SVO, feats: Features, dec: DecoderDev, x, lod: int, decode: str = "f32",
+              grad: bool = False, deepest: bool = False, stream=None):
+    import torch
+    _require_cuda(x)
+    x = x.contiguous()
+    Q = int(x.shape[0])
+    sdf = torch.empty(Q, dtype=torch.float32, device=x.device)
+    dp = torch.empty(Q, dtype=torch.int8, device=x.device) if deepest else None
+    g = torch.empty((Q, 3), dtype=torch.float32, device=x.device) if grad else None
+    fc, dc = feats.c(), dec.c()
+    _check(lib().sdf_query(svo.h, C.byref(fc), C.byref(dc), x.data_ptr(), Q, lod,
+                           {"f32": F32, "bf16": BF16}[decode], sdf.data_ptr(), _ptr(dp), _ptr(g),
+                           C.c_void_p(_stream(stream))))
+    out = [sdf]
+    if deepest:
+        out.append(dp)
+    if grad:
+        out.append(g)
+    return out[0] if len(out) == 1 else tuple(out)
+
+
+def sphere_trace(svo: SVO, feats: Features, dec: DecoderDev, o, d, lists: RayLists, eps: float = 1e-3,
+                 far: float = 5.0, max_steps: int = 128, osc: bool = False, decode: str = "f32",
+                 normals: bool = True, stream=None, out=None):
+    """Sphere-traces every ray through its voxel list; returns a dict of tensors."""
+    import torch
+    _require_cuda(o, d)
+    R = int(o.shape[0])
+    dev = o.device
+    if out is None:
+        out = dict(t=torch.empty(R, dtype=torch.float32, device=dev),
+                   hit=torch.empty(R, dtype=torch.uint8, device=dev),
+                   steps=torch.empty(R, dtype=torch.int32, device=dev),
+                   normal=torch.empty((R, 3), dtype=torch.float32, device=dev) if normals else None,
+                   work=torch.empty(max(lib().sphere_trace_workspace(R), 1), dtype=torch.uint8, device=dev))
+    p = _TraceParams(eps, far, max_steps, int(osc), {"f32": F32, "bf16": BF16}[decode], int(normals))
+    fc, dc = feats.c(), dec.c()
+    _check(lib().sphere_trace(svo.h, C.byref(fc), C.byref(dc), o.data_ptr(), d.data_ptr(), R, lists.lod,
+                              C.byref(p), lists.ray_offsets.data_ptr(), lists.voxel_id.data_ptr(),
+                              lists.t_range.data_ptr(), out["work"].data_ptr(), out["work"].numel(),
+                              out["t"].data_ptr(), out["hit"].data_ptr(), _ptr(out["steps"]),
+                              _ptr(out["normal"]), C.c_void_p(_stream(stream))))
+    return out

@@ -17,3 +17,13 @@ def oracle_mod():
     from oracle import oracle
     oracle.build()
     return oracle
+
+
+@pytest.fixture(scope="session")
+def ng():
+    """The CUDA library binding (built in-tree first); GPU tests only."""
+    import torch
+    from paper_2101_10994_gb300 import build, nglod
+    build.build()
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    return nglod

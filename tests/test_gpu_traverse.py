@@ -1,0 +1,106 @@
+"""svo_trace_rays (Algorithm 1 on the GPU) vs the oracle's brute-force lists:
+bit-exact voxel ids, order and FP32 (t_enter, t_exit) bits."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2101_10994_gb300 import scenes as S
+
+pytestmark = pytest.mark.gpu
+
+
+def gpu_lists(ng, svo, o, d, lod, **kw):
+    to = torch.from_numpy(np.ascontiguousarray(o, np.float32)).cuda()
+    td = torch.from_numpy(np.ascontiguousarray(d, np.float32)).cuda()
+    L = ng.svo_trace_rays(svo, to, td, lod, **kw)
+    return (L.ray_offsets.cpu().numpy().astype(np.int64), L.voxel_id.cpu().numpy(),
+            L.t_range.cpu().numpy(), L)
+
+
+def assert_same_lists(g, o):
+    np.testing.assert_array_equal(g[0], o[0])
+    np.testing.assert_array_equal(g[1], o[1])
+    np.testing.assert_array_equal(g[2].view(np.uint32), o[2].view(np.uint32))
+
+
+@pytest.mark.parametrize("lod", [1, 2, 3])
+def test_plain_sphere_128(ng, oracle_mod, lod):
+    sc, oc = S.plain_sphere(3)
+    svo = ng.svo_build(oc.keys)
+    ora = oracle_mod.OracleSVO(oc.keys)
+    o, d, _ = S.camera_rays(128, 128)
+    assert_same_lists(gpu_lists(ng, svo, o, d, lod), ora.trace_rays(o, d, lod))
+
+
+def test_axis_aligned_view_and_ties(ng, oracle_mod):
+    # eye on the z axis: many rays run exactly along octree centre planes
+    sc, oc = S.csg_workload(16, seed=2, max_lod=3)
+    svo = ng.svo_build(oc.keys)
+    ora = oracle_mod.OracleSVO(oc.keys)
+    o, d, _ = S.camera_rays(65, 65, eye=(0.0, 0.0, 2.5))
+    assert_same_lists(gpu_lists(ng, svo, o, d, 3), ora.trace_rays(o, d, 3))
+    dense = S.full_octree(4)
+    svo2 = ng.svo_build(dense.keys)
+    ora2 = oracle_mod.OracleSVO(dense.keys)
+    ys = np.linspace(-1, 1, 17)
+    oo = np.array([[-3.0, y, z] for y in ys for z in ys], np.float32)
+    dd = np.tile(np.array([[1.0, 0.0, 0.0]], np.float32), (len(oo), 1))
+    assert_same_lists(gpu_lists(ng, svo2, oo, dd, 2), ora2.trace_rays(oo, dd, 2))
+
+
+def test_degenerate_rays_and_empty(ng, oracle_mod):
+    sc, oc = S.plain_sphere(3)
+    svo = ng.svo_build(oc.keys)
+    ora = oracle_mod.OracleSVO(oc.keys)
+    o = np.array([[np.nan, 0, 0], [-3, 0.1, 0.1], [-3, 0.1, 0.1], [-3, 5.0, 0.1], [0.3, 0.05, 0.05],
+                  [0.0, 0.0, 0.0], [3, 3, 3], [-2, 0.2, 0.1]], np.float32)
+    d = np.array([[1, 0, 0], [0, 0, 0], [np.nan, 0, 0], [1, 0, 0], [0, 0, 1], [1, 1e-39, 0],
+                  [1, 0, 0], [1, 1e-30, -1e-30]], np.float32)
+    assert_same_lists(gpu_lists(ng, svo, o, d, 3), ora.trace_rays(o, d, 3))
+    g = gpu_lists(ng, svo, np.zeros((0, 3), np.float32), np.zeros((0, 3), np.float32), 2)
+    assert g[0].tolist() == [0] and g[1].size == 0
+
+
+def test_capacity_growth(ng, oracle_mod):
+    sc, oc = S.csg_workload(16, seed=4, max_lod=3)
+    svo = ng.svo_build(oc.keys)
+    ora = oracle_mod.OracleSVO(oc.keys)
+    o, d, _ = S.camera_rays(64, 48)
+    to = torch.from_numpy(o).cuda()
+    td = torch.from_numpy(d).cuda()
+    with pytest.raises(ng.NglodError) as e:
+        import ctypes
+        L = ng.lib()
+        cap = 64
+        work = torch.empty(L.svo_trace_rays_workspace(len(o), cap), dtype=torch.uint8, device="cuda")
+        offs = torch.empty(len(o) + 1, dtype=torch.int32, device="cuda")
+        vid = torch.empty(cap, dtype=torch.int32, device="cuda")
+        tr = torch.empty((cap, 2), dtype=torch.float32, device="cuda")
+        stats = (ctypes.c_int64 * 2)()
+        ng._check(L.svo_trace_rays(svo.h, to.data_ptr(), td.data_ptr(), len(o), 3, work.data_ptr(),
+                                   work.numel(), cap, offs.data_ptr(), vid.data_ptr(), tr.data_ptr(), cap,
+                                   stats, ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)))
+    assert e.value.code == ng.ERR_CAPACITY
+    # the binding grows the capacity and the result is exact
+    assert_same_lists(gpu_lists(ng, svo, o, d, 3, pair_capacity=64), ora.trace_rays(o, d, 3))
+
+
+def test_full_size_1080p_lod5_sampled(ng, oracle_mod):
+    # the benchmark's workload: CSG-64, LOD 5, 1920x1080, in its launch setup
+    sc, oc = S.csg_workload(64, seed=0, max_lod=5)
+    svo = ng.svo_build(oc.keys)
+    o, d, _ = S.camera_rays(1920, 1080, tile=8)
+    g = gpu_lists(ng, svo, o, d, 5)
+    ora = oracle_mod.OracleSVO(oc.keys)
+    rng = np.random.default_rng(0)
+    hit_rays = np.nonzero(np.diff(g[0]) > 0)[0]
+    pick = np.concatenate([rng.choice(hit_rays, 300, replace=False), rng.choice(len(o), 100, replace=False)])
+    offs, vid, tr = ora.trace_rays(o[pick], d[pick], 5)
+    for n, r in enumerate(pick):
+        a, b = g[0][r], g[0][r + 1]
+        np.testing.assert_array_equal(g[1][a:b], vid[offs[n]:offs[n + 1]])
+        np.testing.assert_array_equal(g[2][a:b].view(np.uint32), tr[offs[n]:offs[n + 1]].view(np.uint32))
+    # invariants over every ray: CSR monotone, ids in range, t_enter <= t_exit
+    assert np.all(np.diff(g[0]) >= 0) and g[0][-1] == len(g[1])
+    assert g[1].min() >= 0 and g[1].max() < oc.counts()[7]
+    assert np.all(g[2][:, 0] <= g[2][:, 1])
