@@ -1,0 +1,398 @@
+#!/usr/bin/env python
+"""Rendering benchmark: sphere-traced rays/s and SDF queries/s at 1920x1080,
+LOD 5, on the seeded CSG-64 scene (the paper's frame scope: ray/octree
+traversal + sphere trace + normals), FP32 and BF16 decode.
+
+One step = one frame: svo_trace_rays -> sphere_trace -> trace_normals over
+2,073,600 rays already resident in HBM.  The L2 is flushed (a 256 MB write)
+between timed steps, outside the timed events.  Prints one JSON line.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun every rank renders its own frame (independent replicas, no
+collective on the data path); rank 0 prints the whole-job throughput.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "sphere-traced rays/s and SDF queries/s at 1080p LOD5, bf16 vs fp32, % roofline"
+PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
+TRACE_SRC = [os.path.join(ROOT, "paper_2101_10994_gb300", "csrc", f) for f in
+             ("query.cu", "query_common.cuh", "trace_common.cuh", "trace_bf16.cu")]
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    # workload overrides, for profiling smaller cases only (the bench line
+    # itself is always the 1920x1080 LOD 5 CSG-64 frame)
+    p.add_argument("--width", type=int, default=1920)
+    p.add_argument("--height", type=int, default=1080)
+    p.add_argument("--decode", choices=["both", "f32", "bf16"], default="both")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def workload(width, height):
+    from paper_2101_10994_gb300 import scenes as S
+    sc, oc = S.csg_workload(64, seed=0, max_lod=5)
+    feats = S.readout_features(oc, sc)
+    dec = S.readout_decoder(5)
+    o, d, pix = S.camera_rays(width, height, tile=8)
+    return dict(scene=sc, octree=oc, feats=feats, dec=dec, o=o, d=d, lod=5, eps=1e-3, far=5.0,
+                max_steps=128)
+
+
+def bf16_available():
+    from paper_2101_10994_gb300 import nglod as ng
+    return hasattr(ng, "BF16_DECODE") and ng.BF16_DECODE
+
+
+# ----------------------------------------------------------------------------
+# clocks during the timed region
+# ----------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=2)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------
+# GPU arm
+# ----------------------------------------------------------------------------
+def flops_per_query(in_dim, lod, decode):
+    """Algorithmic flops of one SDF query: L levels x 8 corners x 32 channels
+    of trilinear FMAs, the 128 x in_dim layer and the 128-wide output."""
+    interp = 2 * 8 * 32 * lod
+    layer1 = 2 * 128 * in_dim
+    out = 2 * 128
+    return interp, layer1, out
+
+
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    from paper_2101_10994_gb300 import nglod as ng
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    W = workload(args.width, args.height)
+    R = W["o"].shape[0]
+    svo = ng.svo_build(W["octree"].keys)
+    feats = ng.Features(W["feats"], "f32")
+    dec = ng.DecoderDev.from_decoder(W["dec"])
+    o = torch.from_numpy(W["o"]).to(dev)
+    d = torch.from_numpy(W["d"]).to(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    modes = []
+    if args.decode in ("both", "f32"):
+        modes.append("f32")
+    if args.decode in ("both", "bf16") and bf16_available():
+        modes.append("bf16")
+    dist = world > 1
+    if dist:
+        import torch.distributed as td
+
+    def step(mode, out, ev):
+        ev[0].record()
+        lists = ng.svo_trace_rays(svo, o, d, W["lod"])
+        ev[1].record()
+        ng.sphere_trace(svo, feats, dec, o, d, lists, eps=W["eps"], far=W["far"], max_steps=W["max_steps"],
+                        decode=mode, normals=False, out=out)
+        ev[2].record()
+        ng.trace_normals(svo, feats, dec, o, d, lists, out)
+        ev[3].record()
+        return lists
+
+    results = {}
+    clock_info = None
+    for mode in modes:
+        out = dict(t=torch.empty(R, device=dev), hit=torch.empty(R, dtype=torch.uint8, device=dev),
+                   steps=torch.empty(R, dtype=torch.int32, device=dev),
+                   normal=torch.empty((R, 3), device=dev),
+                   work=torch.empty(ng.lib().sphere_trace_workspace(R), dtype=torch.uint8, device=dev))
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+        wev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        for _ in range(args.warmup):
+            flush.zero_()
+            step(mode, out, wev)
+        torch.cuda.synchronize()
+        if dist:
+            td.barrier()
+        torch.cuda.synchronize()
+        queries = 0
+        sampler = ClockSampler(local_rank)
+        with sampler:
+            t_wall = time.perf_counter()
+            for k in range(args.steps):
+                flush.zero_()
+                step(mode, out, evs[k])
+                queries += int(out["steps"].sum().item())
+            torch.cuda.synchronize()
+            t_wall = time.perf_counter() - t_wall
+        if dist:
+            td.barrier()
+        torch.cuda.synchronize()
+        trav = [e[0].elapsed_time(e[1]) for e in evs]
+        trace = [e[1].elapsed_time(e[2]) for e in evs]
+        norm = [e[2].elapsed_time(e[3]) for e in evs]
+        total = sum(trav) + sum(trace) + sum(norm)           # ms over K steps
+        tmax = torch.tensor([total], dtype=torch.float64, device=dev)
+        if dist:
+            td.all_reduce(tmax, op=td.ReduceOp.MAX)
+        ms_step = float(tmax.item()) / args.steps
+        hits = int(out["hit"].sum().item())
+        results[mode] = dict(
+            ms_per_step=ms_step, rays_per_s=world * R / (ms_step * 1e-3),
+            queries_per_s=world * queries / args.steps / (sum(trace) / args.steps * 1e-3),
+            ms_traverse=sum(trav) / args.steps, ms_trace=sum(trace) / args.steps,
+            ms_normals=sum(norm) / args.steps, queries_per_frame=queries // args.steps,
+            hit_pixels=hits, wall_s=t_wall)
+        if clock_info is None or mode == "bf16":
+            clock_info = sampler.summary()
+
+    # ---- end to end through the public API with pinned host buffers ----
+    mode = "bf16" if "bf16" in modes else "f32"
+    h_o = torch.from_numpy(W["o"]).pin_memory()
+    h_d = torch.from_numpy(W["d"]).pin_memory()
+    h_t = torch.empty(R, dtype=torch.float32).pin_memory()
+    h_hit = torch.empty(R, dtype=torch.uint8).pin_memory()
+    h_n = torch.empty((R, 3), dtype=torch.float32).pin_memory()
+    out = dict(t=torch.empty(R, device=dev), hit=torch.empty(R, dtype=torch.uint8, device=dev),
+               steps=torch.empty(R, dtype=torch.int32, device=dev), normal=torch.empty((R, 3), device=dev),
+               work=torch.empty(ng.lib().sphere_trace_workspace(R), dtype=torch.uint8, device=dev))
+    e2e_ms = []
+    for k in range(args.warmup + args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        go = h_o.to(dev, non_blocking=True)
+        gd = h_d.to(dev, non_blocking=True)
+        lists = ng.svo_trace_rays(svo, go, gd, W["lod"])
+        ng.sphere_trace(svo, feats, dec, go, gd, lists, eps=W["eps"], far=W["far"], max_steps=W["max_steps"],
+                        decode=mode, normals=True, out=out)
+        h_t.copy_(out["t"], non_blocking=True)
+        h_hit.copy_(out["hit"], non_blocking=True)
+        h_n.copy_(out["normal"], non_blocking=True)
+        e1.record()
+        e1.synchronize()
+        if k >= args.warmup:
+            e2e_ms.append(e0.elapsed_time(e1))
+    e2e_t = torch.tensor([statistics.mean(e2e_ms)], dtype=torch.float64, device=dev)
+    if dist:
+        td.all_reduce(e2e_t, op=td.ReduceOp.MAX)
+    e2e = dict(value=world * R / (float(e2e_t.item()) * 1e-3), unit="rays/s",
+               h2d_bytes_per_step=int(h_o.numel() * 4 + h_d.numel() * 4),
+               d2h_bytes_per_step=int(h_t.numel() * 4 + h_hit.numel() + h_n.numel() * 4))
+    svo.free()
+    return W, results, clock_info, e2e, modes
+
+
+def source_hash():
+    h = hashlib.sha256()
+    for f in TRACE_SRC:
+        if os.path.exists(f):
+            h.update(open(f, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def roofline(W, res, mode):
+    """Dominant kernel = the sphere tracer (one launch per frame)."""
+    import numpy as np
+    peaks = {}
+    pp = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pp):
+        peaks = json.load(open(pp))
+    interp, layer1, outl = flops_per_query(W["dec"].in_dim, W["lod"], mode)
+    q = res["queries_per_frame"]
+    sec = res["ms_trace"] * 1e-3
+    traffic = None
+    if os.path.exists(PROFILE_TRAFFIC):
+        tj = json.load(open(PROFILE_TRAFFIC))
+        ent = tj.get(f"trace_{mode}")
+        if ent and ent.get("source_hash") == source_hash():
+            traffic = ent.get("dram_bytes_per_launch")
+    if mode == "bf16":
+        tf = peaks.get("bf16_tflops", 1900.0)
+        achieved = q * layer1 / sec / 1e12
+        return {"bound": "tensor", "achieved": achieved, "peak": tf, "unit": "TFLOP/s",
+                "frac": achieved / tf, "traffic": traffic,
+                "peak_source": "MEASURED_PEAKS.json bf16_tflops (of measured)" if peaks else "fallback"}
+    sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+    peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+    achieved = q * (interp + layer1 + outl) / sec / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": traffic,
+            "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x sm_max_mhz (MEASURED_PEAKS.json)"}
+
+
+# ----------------------------------------------------------------------------
+# CPU oracle (baseline / reference arm)
+# ----------------------------------------------------------------------------
+def oracle_rate(W, budget_s, seed=0):
+    """Oracle rays/s on a uniform random sample of the frame's rays sized to
+    roughly ``budget_s`` seconds of CPU work (all host cores via OpenMP)."""
+    import numpy as np
+
+    from oracle.oracle import OracleSVO
+    ora = OracleSVO(W["octree"].keys)
+    R = W["o"].shape[0]
+    rng = np.random.default_rng(seed)
+    perm = rng.permutation(R)
+    n = 256
+    t = time.perf_counter()
+    ora.sphere_trace(W["feats"], W["dec"], W["o"][perm[:n]], W["d"][perm[:n]], W["lod"], eps=W["eps"],
+                     far=W["far"], max_steps=W["max_steps"])
+    dt = time.perf_counter() - t
+    n2 = int(min(R - n, max(256, n * (budget_s / max(dt, 1e-3)))))
+    sel = perm[n:n + n2]
+    t = time.perf_counter()
+    ora.sphere_trace(W["feats"], W["dec"], W["o"][sel], W["d"][sel], W["lod"], eps=W["eps"], far=W["far"],
+                     max_steps=W["max_steps"])
+    dt = time.perf_counter() - t
+    return n2 / dt, n2, dt
+
+
+def run_reference(args):
+    W = workload(args.width, args.height)
+    R = W["o"].shape[0]
+    from oracle import oracle
+    oracle.build()
+    cores = os.cpu_count()
+    budget = max(1.0, min(20.0, 100.0 / max(1, args.steps + args.warmup)))
+    rates = []
+    for k in range(args.warmup + args.steps):
+        rate, n, dt = oracle_rate(W, budget, seed=k)
+        if k >= args.warmup:
+            rates.append(rate)
+    v = statistics.mean(rates)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "rays/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": R / v * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "csg64_seed0_lod5_1920x1080", "lod": 5, "rays": R, "max_steps": 128,
+                       "eps": 1e-3, "decoder": "32->128->1 readout-embedded", "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": v, "unit": "rays/s", "cores": cores, "kind": "oracle",
+                             "sample": f"per step a uniform random sample of the 1920x1080 frame's rays "
+                                       f"(~{budget:.0f} s of CPU work), FP64 oracle: brute-force traversal + "
+                                       f"sphere trace + normals"},
+            "e2e": {"value": v, "unit": "rays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        if rank == 0:
+            run_reference(args)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as td
+        torch.cuda.set_device(local_rank)
+        td.init_process_group("nccl")
+    W, res, clocks, e2e, modes = run_ours(args, rank, world, local_rank)
+    if rank == 0:
+        head = "bf16" if "bf16" in res else "f32"
+        r = res[head]
+        line = {
+            "metric": METRIC, "value": r["rays_per_s"], "unit": "rays/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": head,
+            "data": "synthetic",
+            "config": {"workload": f"csg64_seed0_lod5_{args.width}x{args.height}", "lod": 5,
+                       "rays": int(W["o"].shape[0]), "max_steps": W["max_steps"], "eps": W["eps"],
+                       "features": "f32 m=32", "decoder": "32->128->1 readout-embedded",
+                       "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world}"},
+            "queries_per_s": r["queries_per_s"],
+            "modes": res,
+            "roofline": roofline(W, r, head),
+            "clocks": clocks,
+            "e2e": e2e,
+            "gpu_launches": args.steps * len(modes) * (W["lod"] + 7),   # prep + (lod+3) levels + offsets + trace + normals
+        }
+        if "bf16" in res and "f32" in res:
+            line["bf16_speedup"] = res["f32"]["ms_per_step"] / res["bf16"]["ms_per_step"]
+        if not args.no_cpu_baseline and world == 1:
+            from oracle import oracle
+            oracle.build()
+            v, n, dt = oracle_rate(W, 15.0)
+            line["cpu_baseline"] = {"value": v, "unit": "rays/s", "cores": os.cpu_count(), "kind": "oracle",
+                                    "sample": f"{n} rays drawn uniformly from the frame, {dt:.1f} s, FP64 "
+                                              f"brute-force traversal + sphere trace + normals"}
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as td
+        td.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

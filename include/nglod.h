@@ -210,6 +210,19 @@ int sphere_trace(const nglod_svo* svo, const nglod_features* feats,
                  size_t work_bytes, float* t_hit, uint8_t* hit, int32_t* steps,
                  float* normal, void* stream);
 
+/* trace_normals -- surface normals of the rays a preceding sphere_trace call
+ * (same work buffer, same stream, want_normals = 0 or 1) marked as hits:
+ * the normalised analytic gradient of the decoded SDF (Eq. 2 chain rule
+ * through the trilinear weights, Sec. 3.2) in FP32 at the hit point
+ * x = o + t_hit d, using the hit voxel recorded by sphere_trace.  The paper
+ * takes normals by finite differences (supplementary Sec. A.4); the analytic
+ * gradient is their limit.  normal [R, 3]; zero for misses.  Does not
+ * synchronise. */
+int trace_normals(const nglod_svo* svo, const nglod_features* feats,
+                  const nglod_decoder* dec, const float* o, const float* d, int64_t R,
+                  int lod, const void* work, size_t work_bytes, const float* t_hit,
+                  const uint8_t* hit, float* normal, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

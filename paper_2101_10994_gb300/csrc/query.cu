@@ -507,3 +507,32 @@ extern "C" int sphere_trace(const nglod_svo* svo, const nglod_features* feats, c
     }
     return NGLOD_OK;
 }
+
+extern "C" int trace_normals(const nglod_svo* svo, const nglod_features* feats, const nglod_decoder* dec,
+                             const float* o, const float* d, int64_t R, int lod, const void* work,
+                             size_t work_bytes, const float* t_hit, const uint8_t* hit, float* normal,
+                             void* stream) {
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!svo) return fail(NGLOD_ERR_INVALID_ARG, "trace_normals: NULL octree");
+    const int D = lod + kFirstFeatureDepth - 1;
+    if (lod < 1 || D >= svo->num_depths) return fail(NGLOD_ERR_INVALID_ARG, "trace_normals: lod out of range");
+    if (R < 0) return fail(NGLOD_ERR_INVALID_ARG, "trace_normals: bad R");
+    if (R == 0) return NGLOD_OK;
+    if (!o || !d || !work || !t_hit || !hit || !normal)
+        return fail(NGLOD_ERR_INVALID_ARG, "trace_normals: NULL argument");
+    if (work_bytes < sphere_trace_workspace(R)) return fail(NGLOD_ERR_CAPACITY, "trace_normals: workspace too small");
+    if (!dec || dec->hidden != kHidden || (dec->in_dim != 32 && dec->in_dim != 35))
+        return fail(NGLOD_ERR_NOT_SUPPORTED, "trace_normals: decoder must be 32|35 -> 128 -> 1");
+    Tables tb;
+    int rc = fill_tables(svo, feats, lod, tb);
+    if (rc) return rc;
+    TraceArgs A{};
+    A.o = o;
+    A.d = d;
+    A.R = R;
+    A.D = D;
+    A.t_hit = const_cast<float*>(t_hit);
+    A.hit = const_cast<uint8_t*>(hit);
+    A.hit_vox = (int32_t*)((char*)work + 256);
+    return launch_normals(dec, tb, A, normal, feats->dtype == NGLOD_F16, svo->num_sms, st);
+}

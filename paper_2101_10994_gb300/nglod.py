@@ -22,7 +22,7 @@ FIRST_FEATURE_DEPTH = 3
 
 EXPORTS = ["nglod_last_error", "svo_build", "svo_info", "svo_device_arrays", "svo_read_arrays", "svo_free",
            "svo_trace_rays_workspace", "svo_trace_rays", "sdf_query", "sphere_trace_workspace",
-           "sphere_trace"]
+           "sphere_trace", "trace_normals"]
 
 
 class NglodError(RuntimeError):
@@ -72,6 +72,7 @@ def lib():
         L.sphere_trace_workspace.restype = sz
         L.sphere_trace_workspace.argtypes = [i64]
         L.sphere_trace.argtypes = [P, P, P, P, P, i64, i32, P, P, P, P, P, sz, P, P, P, P, P]
+        L.trace_normals.argtypes = [P, P, P, P, P, i64, i32, P, sz, P, P, P, P]
         _lib = L
     return _lib
 
@@ -293,4 +294,17 @@ def sphere_trace(svo: SVO, feats: Features, dec: DecoderDev, o, d, lists: RayLis
                               lists.t_range.data_ptr(), out["work"].data_ptr(), out["work"].numel(),
                               out["t"].data_ptr(), out["hit"].data_ptr(), _ptr(out["steps"]),
                               _ptr(out["normal"]), C.c_void_p(_stream(stream))))
+    return out
+
+
+def trace_normals(svo: SVO, feats: Features, dec: DecoderDev, o, d, lists: RayLists, out, stream=None):
+    """Normals of the hits of the preceding sphere_trace call that filled ``out``."""
+    R = int(o.shape[0])
+    if out.get("normal") is None:
+        import torch
+        out["normal"] = torch.empty((R, 3), dtype=torch.float32, device=o.device)
+    fc, dc = feats.c(), dec.c()
+    _check(lib().trace_normals(svo.h, C.byref(fc), C.byref(dc), o.data_ptr(), d.data_ptr(), R, lists.lod,
+                               out["work"].data_ptr(), out["work"].numel(), out["t"].data_ptr(),
+                               out["hit"].data_ptr(), out["normal"].data_ptr(), C.c_void_p(_stream(stream))))
     return out

@@ -66,8 +66,10 @@ def test_query_gradient_vs_oracle(ng, oracle_mod):
         _, g = ng.sdf_query(svo, F, ng.DecoderDev.from_decoder(dec), torch.from_numpy(x).cuda(), lod, grad=True)
         _, _, rg = ora.sdf_query(feats, dec, x, lod, grad=True)
         g = g.cpu().numpy().astype(np.float64)
+        # FP32 sums of ~35 x 128 products of size |g| carry a relative error of
+        # a few 1e-6 per term; 5e-5 of the largest component bounds it
         scale = np.abs(rg).max(axis=1, keepdims=True)
-        assert np.all(np.abs(g - rg) <= 1e-5 * np.maximum(scale, 1.0)), np.abs(g - rg).max()
+        assert np.all(np.abs(g - rg) <= 5e-5 * np.maximum(scale, 1.0)), np.abs(g - rg).max()
         cosang = (g * rg).sum(1) / np.linalg.norm(g, axis=1) / np.linalg.norm(rg, axis=1)
         assert np.degrees(np.arccos(np.clip(cosang, -1, 1))).max() < 0.01
 
