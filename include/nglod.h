@@ -166,6 +166,27 @@ int svo_trace_rays(const nglod_svo* svo, const float* o, const float* d, int64_t
                    int32_t* ray_offsets, int32_t* voxel_id, float* t_range,
                    int64_t hit_capacity, int64_t* h_stats, void* stream);
 
+/* svo_trace_rays_noalloc -- svo_trace_rays without a caller workspace and
+ * without any device allocation.  The paper has no counterpart: this entry
+ * point exists for callers that cannot allocate device memory while they
+ * render, such as a plugin inside an application that owns the GPU memory
+ * budget, or a real-time loop that must not trigger the implicit
+ * synchronisation of cudaMalloc/cudaFree mid-frame.
+ * The workspace is a 32 MiB array built into the library, present on every
+ * GPU that loads it until the process exits.  The first call on a device
+ * (with that device current) looks up the array's device address; make it
+ * before any stream capture.  The intermediate-list capacity is whatever fits
+ * in 32 MiB after the R ray records; R too large for even that is rejected
+ * with NGLOD_ERR_CAPACITY before anything is launched, and lists that outgrow
+ * the array return NGLOD_ERR_CAPACITY like svo_trace_rays.  Every call reuses
+ * the same array (counters and scan state are cleared at the start of each
+ * call); calls that overlap on the GPU race on it.  Arguments, outputs,
+ * results and the stream synchronisation are those of svo_trace_rays. */
+int svo_trace_rays_noalloc(const nglod_svo* svo, const float* o, const float* d, int64_t R,
+                           int target_lod, int32_t* ray_offsets, int32_t* voxel_id,
+                           float* t_range, int64_t hit_capacity, int64_t* h_stats,
+                           void* stream);
+
 /* sdf_query -- Sec. 3.2 and Eq. 2: for each point x, the voxels containing it
  * at depths 3..lod+2 (found from the root through the child masks using
  * q = fl32(x + 1), ijk = clamp(floor(q 2^(dp-1)), 0, 2^dp - 1)); per level the

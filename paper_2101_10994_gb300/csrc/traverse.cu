@@ -371,3 +371,78 @@ extern "C" int svo_trace_rays(const nglod_svo* svo, const float* o, const float*
     }
     return NGLOD_OK;
 }
+
+// ---------------------------------------------------------------------------
+// svo_trace_rays_noalloc: the same traversal with its workspace in a fixed
+// device array compiled into this library, for callers that must not
+// allocate device memory while they render.
+//
+// Who needs it: a renderer embedded in a host application that owns the
+// GPU's memory budget (a viewer or engine plugin whose allocator hands out
+// every byte), or a real-time frame loop that may not risk the implicit
+// device-wide synchronisation cudaMalloc/cudaFree can cause in mid-frame.
+// Such a caller passes only its inputs and outputs.
+//
+// The array below, kNoAllocScratchBytes (32 MiB) long, is created on every
+// GPU that loads this library and stays there until the process exits.  Its
+// host-side name is only a stand-in; the device address is looked up with
+// cudaGetSymbolAddress once per device, the first time this entry point runs
+// with that device current (make that first call before any stream
+// capture).  All calls share the array and it keeps the previous call's
+// contents: the traversal clears its own counters and scan state at the
+// start of every call, but two calls that overlap on the GPU (different
+// streams, or different host threads on one device) race on it.
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+namespace nglod {
+namespace {
+constexpr size_t kNoAllocScratchBytes = 32u << 20;
+constexpr int kNoAllocMaxDevices = 64;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+std::mutex g_noalloc_mutex;
+void* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+}  // namespace
+}  // namespace nglod
+
+extern "C" int svo_trace_rays_noalloc(const nglod_svo* svo, const float* o, const float* d, int64_t R,
+                                      int target_lod, int32_t* ray_offsets, int32_t* voxel_id,
+                                      float* t_range, int64_t hit_capacity, int64_t* h_stats, void* stream) {
+    using namespace nglod;
+    if (R < 0) return fail(NGLOD_ERR_INVALID_ARG, "svo_trace_rays_noalloc: R < 0");
+    // the largest intermediate-list capacity whose workspace fits the array
+    int64_t lo = 0, hi = (int64_t)(kNoAllocScratchBytes / sizeof(int2));
+    while (lo < hi) {
+        const int64_t mid = lo + (hi - lo + 1) / 2;
+        if (svo_trace_rays_workspace(R, mid) <= kNoAllocScratchBytes) lo = mid; else hi = mid - 1;
+    }
+    const int64_t pair_capacity = lo;
+    if (R > 0 && pair_capacity < R)
+        return fail(NGLOD_ERR_CAPACITY, "svo_trace_rays_noalloc: " + std::to_string(R) +
+                                            " rays do not fit the fixed 32 MiB scratch (use svo_trace_rays with a "
+                                            "caller-allocated workspace)");
+    int dev = 0;
+    NGLOD_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kNoAllocMaxDevices)
+        return fail(NGLOD_ERR_NOT_SUPPORTED, "svo_trace_rays_noalloc: device index out of range");
+    void* scratch = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+        if (!g_noalloc_ptr[dev]) {
+            void* p = nullptr;
+            const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+            if (e != cudaSuccess || !p) {
+                return check_cuda(e == cudaSuccess ? cudaErrorInvalidSymbol : e,
+                                  "svo_trace_rays_noalloc: cudaGetSymbolAddress(scratch)");
+            }
+            g_noalloc_ptr[dev] = p;
+        }
+        scratch = g_noalloc_ptr[dev];
+    }
+    const int rc = svo_trace_rays(svo, o, d, R, target_lod, scratch, kNoAllocScratchBytes, pair_capacity,
+                                  ray_offsets, voxel_id, t_range, hit_capacity, h_stats, stream);
+    if (rc == NGLOD_ERR_CAPACITY)
+        set_error(std::string(nglod_last_error()) + " [svo_trace_rays_noalloc: the fixed 32 MiB scratch holds " +
+                  std::to_string(pair_capacity) + " pairs per level for these rays]");
+    return rc;
+}

@@ -22,7 +22,7 @@ FIRST_FEATURE_DEPTH = 3
 
 EXPORTS = ["nglod_last_error", "svo_build", "svo_info", "svo_device_arrays", "svo_read_arrays", "svo_free",
            "svo_trace_rays_workspace", "svo_trace_rays", "sdf_query", "sphere_trace_workspace",
-           "sphere_trace", "trace_normals"]
+           "sphere_trace", "trace_normals", "svo_trace_rays_noalloc"]
 
 
 class NglodError(RuntimeError):
@@ -73,6 +73,7 @@ def lib():
         L.sphere_trace_workspace.argtypes = [i64]
         L.sphere_trace.argtypes = [P, P, P, P, P, i64, i32, P, P, P, P, P, sz, P, P, P, P, P]
         L.trace_normals.argtypes = [P, P, P, P, P, i64, i32, P, sz, P, P, P, P]
+        L.svo_trace_rays_noalloc.argtypes = [P, P, P, i64, i32, P, P, P, i64, P, P]
         _lib = L
     return _lib
 
