@@ -64,12 +64,7 @@ typedef struct {
 /* One LOD's decoder (Eq. 2): d = W2 . relu(W1 v + b1) + b2 with
  * v = [x, z] (in_dim = m + 3) or v = z (in_dim = m).  FP32 master weights;
  * the BF16 decode rounds W1 and z to bf16 (round-to-nearest-even) and
- * accumulates in FP32.
- * The FP32 decode keeps the whole decoder (19 KB) in the kernel-parameter
- * constant bank, read as broadcast operands; it takes the weights from the
- * optional HOST mirrors h_W1/h_b1/h_W2 (same layout and values as W1/b1/W2).
- * Without them the call copies the device weights to the host first, which
- * synchronises the stream. */
+ * accumulates in FP32. */
 typedef struct {
     const float* W1;       /* [hidden, in_dim] row-major (device)             */
     const float* b1;       /* [hidden] (device)                               */
@@ -77,9 +72,6 @@ typedef struct {
     float b2;
     int in_dim;            /* 32 or 35                                        */
     int hidden;            /* only 128 is built                               */
-    const float* h_W1;     /* optional host mirrors (nullable)                */
-    const float* h_b1;
-    const float* h_W2;
 } nglod_decoder;
 
 /* Sphere-tracing parameters (supplementary Sec. A.4). */
@@ -197,10 +189,14 @@ int svo_trace_rays_noalloc(const nglod_svo* svo, const float* o, const float* d,
  *   x         [Q, 3] float32.   sdf  [Q] float32 output.
  *   deepest   [Q] int8 (nullable): deepest LOD with a containing voxel (0 none).
  *   grad      [Q, 3] float32 (nullable): analytic d sdf / dx (FP32 decode).
- *   decode_dtype  NGLOD_F32 or NGLOD_BF16.
+ *   decode_dtype  NGLOD_F32 (CUDA cores) or NGLOD_BF16 (tensor cores: z and
+ *                 W1's z columns rounded to bf16, FP32 accumulation; the
+ *                 x columns, biases and W2 stay FP32).
  * Errors: NGLOD_ERR_INVALID_ARG (lod outside 1..num_depths-3, missing
  * features), NGLOD_ERR_NOT_SUPPORTED (m != 32, hidden != 128, in_dim not 32 or
- * 35, grad with BF16 decode).  Does not synchronise. */
+ * 35, grad with BF16 decode), NGLOD_ERR_TIMEOUT (a bounded tensor-core wait
+ * expired).  The FP32 decode does not synchronise; the BF16 decode
+ * synchronises the stream to read its status. */
 int sdf_query(const nglod_svo* svo, const nglod_features* feats,
               const nglod_decoder* dec, const float* x, int64_t Q, int lod,
               int decode_dtype, float* sdf, int8_t* deepest, float* grad,
@@ -230,6 +226,12 @@ int sphere_trace(const nglod_svo* svo, const nglod_features* feats,
                  const int32_t* voxel_id, const float* t_range, void* work,
                  size_t work_bytes, float* t_hit, uint8_t* hit, int32_t* steps,
                  float* normal, void* stream);
+
+/* sphere_trace_status -- synchronises the stream and reports whether the
+ * last sphere_trace that used this workspace completed: NGLOD_OK, or
+ * NGLOD_ERR_TIMEOUT if a bounded tensor-core wait of the BF16 decode expired
+ * (its outputs are then invalid). */
+int sphere_trace_status(const void* work, void* stream);
 
 /* trace_normals -- surface normals of the rays a preceding sphere_trace call
  * (same work buffer, same stream, want_normals = 0 or 1) marked as hits:

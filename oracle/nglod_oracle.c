@@ -621,3 +621,17 @@ void or_sdf_backward(const or_svo *s, const double *const *feats, int m,
     }
     free(z); free(pre); free(gz);
 }
+
+/* z(x; L) = sum over levels of the trilinear feature interpolation (Sec. 3.2)
+ * for Q points, [Q, m] FP64 -- the decoder input, exposed so tests can bound
+ * the effect of rounding z (e.g. to bf16) on the decoded distance. */
+void or_feature_sum(const or_svo *s, const double *const *feats, int m, const float *x, int64_t Q,
+                    int lod, double *z) {
+    int D = lod + FIRST_FEATURE_DEPTH - 1;
+    for (int64_t q = 0; q < Q; ++q) {
+        int64_t vids[MAX_DEPTH + 1], ijks[MAX_DEPTH + 1][3];
+        locate32(s, x + 3 * q, D, vids, ijks);
+        double xd[3] = {x[3 * q], x[3 * q + 1], x[3 * q + 2]};
+        feature_sum(s, feats, m, D, vids, ijks, xd, z + (size_t)q * (size_t)m, NULL);
+    }
+}

@@ -59,6 +59,7 @@ def _load():
                                      P, P, P, i32]
         lib.or_sphere_trace.argtypes = [P, P, i32, P, P, P, f64, i32, i32, P, P, i64,
                                         i32, f64, f64, i32, i32, P, P, P, P, P, i32]
+        lib.or_feature_sum.argtypes = [P, P, i32, P, i64, i32, P]
         lib.or_sdf_backward.argtypes = [P, P, i32, P, P, P, P, i32, i32, P, i64, P, i32,
                                         P, P, P, P, P, P, P]
         _lib = lib
@@ -161,6 +162,15 @@ class OracleSVO:
                              _ptr(x), Q, lod, _ptr(sdf), _ptr(deep),
                              _ptr(g) if grad else None, nthreads)
         return (sdf, deep, g) if grad else (sdf, deep)
+
+    def feature_sum(self, feats, x, lod: int):
+        """z(x; lod) in FP64, [Q, m] (the decoder input of Eq. 2)."""
+        fs = _PtrArray([_f64(f) for f in feats])
+        m = int(fs.arrays[0].shape[1])
+        x = np.ascontiguousarray(x, np.float32).reshape(-1, 3)
+        z = np.zeros((x.shape[0], m))
+        _load().or_feature_sum(self.h, fs.p, m, _ptr(x), x.shape[0], lod, _ptr(z))
+        return z
 
     def sphere_trace(self, feats, dec, o, d, lod: int, eps: float = 1e-3,
                      far: float = 5.0, max_steps: int = 32, osc: bool = False,

@@ -39,6 +39,7 @@ struct nglod_svo {
     // anc[d][8 v + i] = id of the depth-(3 + i) voxel containing voxel v of
     // depth d, for i = 0..d-3 (i = d-3 is v itself); unused entries are -1.
     int32_t* anc[nglod::kMaxDepth + 1] = {};
+    int* dstatus = nullptr;                               // device status word
     int device = 0;
     int num_sms = 0;
 };
@@ -83,21 +84,28 @@ struct __align__(16) RayPrep {
 };
 
 // FP32 slab test of a prepared ray against voxel (i,j,k) at depth dp, all in
-// round-to-nearest with no contraction.  Voxel bounds -1 + i 2^(1-dp) are
-// exact.  hit iff max(t_near, 0) <= t_far; [tin, tout] = [max(t_near,0),
-// t_far].  Written to agree bit-for-bit with any IEEE implementation of the
-// same formula.
-__device__ __forceinline__ bool slab_test(const RayPrep& r, uint32_t ijk, int dp,
-                                          float& tin, float& tout) {
+// round-to-nearest with no contraction of the rounded steps.  Voxel bounds
+// lo = -1 + i 2^(1-dp) and hi = lo + 2^(1-dp) are exact (a single fused
+// multiply-add of exact terms rounds nothing), as is the centre lo + 2^(-dp).
+// Per axis t0 = (lo - o) * inv, t1 = (hi - o) * inv, each rounded after the
+// subtraction and after the product.  hit iff max(t_near, 0) <= t_far;
+// [tin, tout] = [max(t_near, 0), t_far].  *oct (if non-null) receives the
+// origin octant relative to the voxel centre (bit a set iff o_a >= centre_a),
+// which orders the children front to back: rank r visits slot r ^ oct.
+__device__ __forceinline__ bool slab_test(const RayPrep& r, uint32_t ijk, int dp, float& tin, float& tout,
+                                          uint32_t* oct = nullptr) {
     const float s = pow2f(1 - dp);
+    const float hs = pow2f(-dp);
     float tn = -INFINITY, tf = INFINITY;
     const float o[3] = {r.ox, r.oy, r.oz};
     const float inv[3] = {r.ix, r.iy, r.iz};
     const uint32_t c[3] = {unpack_i(ijk), unpack_j(ijk), unpack_k(ijk)};
+    uint32_t octant = 0;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        const float lo = __fsub_rn(__fmul_rn((float)c[a], s), 1.0f);
-        const float hi = __fsub_rn(__fmul_rn((float)(c[a] + 1u), s), 1.0f);
+        const float lo = __fmaf_rn((float)c[a], s, -1.0f);
+        const float hi = __fadd_rn(lo, s);
+        if (oct) octant |= (o[a] >= __fadd_rn(lo, hs)) ? (1u << a) : 0u;
         if ((r.par >> a) & 1) {
             if (!(lo <= o[a] && o[a] <= hi)) return false;
             continue;
@@ -113,18 +121,18 @@ __device__ __forceinline__ bool slab_test(const RayPrep& r, uint32_t ijk, int dp
     if (!(te <= tf)) return false;
     tin = te;
     tout = tf;
+    if (oct) *oct = octant;
     return true;
 }
 
-// Octant of the ray origin relative to the centre of voxel (i,j,k) at depth
-// dp: bit a set iff o_a >= centre_a.  The front-to-back rank of child slot c
-// is c ^ octant (ordering depends only on the origin octant).
-__device__ __forceinline__ uint32_t origin_octant(const RayPrep& r, uint32_t ijk, int dp) {
-    const float h = pow2f(-dp);
-    const float cx = __fsub_rn(__fmul_rn((float)(2u * unpack_i(ijk) + 1u), h), 1.0f);
-    const float cy = __fsub_rn(__fmul_rn((float)(2u * unpack_j(ijk) + 1u), h), 1.0f);
-    const float cz = __fsub_rn(__fmul_rn((float)(2u * unpack_k(ijk) + 1u), h), 1.0f);
-    return (r.ox >= cx ? 1u : 0u) | (r.oy >= cy ? 2u : 0u) | (r.oz >= cz ? 4u : 0u);
+// Child-slot mask re-indexed by front-to-back rank: bit r is set iff slot
+// r ^ oct is occupied (an XOR permutation of the 8 bits, by conditional swaps
+// of adjacent bits, bit pairs and nibbles).
+__device__ __forceinline__ uint32_t rank_mask(uint32_t m, uint32_t oct) {
+    if (oct & 1u) m = ((m & 0x55u) << 1) | ((m >> 1) & 0x55u);
+    if (oct & 2u) m = ((m & 0x33u) << 2) | ((m >> 2) & 0x33u);
+    if (oct & 4u) m = ((m & 0x0fu) << 4) | ((m >> 4) & 0x0fu);
+    return m;
 }
 
 // Kernel-side error status words (device memory, caller workspace).

@@ -1,11 +1,9 @@
 // sdf_query, sphere_trace (FP32 decode) and the analytic-gradient kernel.
 //
 // Decoder (Eq. 2) on CUDA cores: one thread per query evaluates the whole
-// 35(32) -> 128 -> 1 MLP.  The decoder's 4737 (4608) parameters are passed as
-// the kernel's parameter block, which lives in the constant bank: with the
-// loops fully unrolled every weight is an immediate constant-bank operand of
-// its FFMA, broadcast to the warp, so the decode issues no shared- or
-// global-memory loads at all.
+// 35(32) -> 128 -> 1 MLP with the decoder staged once per CTA in shared
+// memory; all lanes of a warp read the same weight row, so the loads are
+// broadcasts and each 16-byte load feeds four FFMAs.
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
@@ -40,23 +38,11 @@ int fill_tables(const nglod_svo* svo, const nglod_features* f, int lod, Tables& 
     return NGLOD_OK;
 }
 
-int fill_dec_params(const nglod_decoder* dec, DecParams& P, cudaStream_t st) {
+int check_decoder(const nglod_decoder* dec) {
     if (!dec) return fail(NGLOD_ERR_INVALID_ARG, "NULL decoder");
     if (dec->hidden != kHidden) return fail(NGLOD_ERR_NOT_SUPPORTED, "only hidden = 128 is built");
     if (dec->in_dim != 32 && dec->in_dim != 35) return fail(NGLOD_ERR_NOT_SUPPORTED, "in_dim must be 32 or 35");
-    const int n1 = kHidden * dec->in_dim;
-    if (dec->h_W1 && dec->h_b1 && dec->h_W2) {
-        std::copy(dec->h_W1, dec->h_W1 + n1, P.W1);
-        std::copy(dec->h_b1, dec->h_b1 + kHidden, P.b1);
-        std::copy(dec->h_W2, dec->h_W2 + kHidden, P.W2);
-    } else {
-        if (!dec->W1 || !dec->b1 || !dec->W2) return fail(NGLOD_ERR_INVALID_ARG, "NULL decoder weights");
-        NGLOD_CUDA(cudaMemcpyAsync(P.W1, dec->W1, sizeof(float) * n1, cudaMemcpyDeviceToHost, st));
-        NGLOD_CUDA(cudaMemcpyAsync(P.b1, dec->b1, sizeof(float) * kHidden, cudaMemcpyDeviceToHost, st));
-        NGLOD_CUDA(cudaMemcpyAsync(P.W2, dec->W2, sizeof(float) * kHidden, cudaMemcpyDeviceToHost, st));
-        NGLOD_CUDA(cudaStreamSynchronize(st));
-    }
-    P.b2 = dec->b2;
+    if (!dec->W1 || !dec->b1 || !dec->W2) return fail(NGLOD_ERR_INVALID_ARG, "NULL decoder weights");
     return NGLOD_OK;
 }
 
@@ -68,12 +54,21 @@ constexpr int kWarps = kThreads / 32;
 // ---------------------------------------------------------------------------
 // sdf_query (FP32 decode)
 // ---------------------------------------------------------------------------
+struct DecPtrs {
+    const float* W1;
+    const float* b1;
+    const float* W2;
+    float b2;
+};
+
 template <typename T, int IN>
-__global__ void __launch_bounds__(kThreads) k_sdf_query(const __grid_constant__ DecParams P,
-                                                        const Tables tb, const float* __restrict__ x,
-                                                        long long Q, int D, float* __restrict__ sdf,
-                                                        int8_t* __restrict__ deepest) {
+__global__ void __launch_bounds__(kThreads) k_sdf_query(const DecPtrs dp, const Tables tb,
+                                                        const float* __restrict__ x, long long Q, int D,
+                                                        float* __restrict__ sdf, int8_t* __restrict__ deepest) {
     __shared__ __align__(16) float zbuf[kWarps][32 * kZStride];
+    __shared__ __align__(16) SmemDecoder sd;
+    stage_decoder<IN>(sd, dp.W1, dp.b1, dp.W2);
+    __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int g = lane >> 3, l = lane & 7, gbase = g << 3;
     const unsigned gmask = 0xffu << gbase;
@@ -106,7 +101,7 @@ __global__ void __launch_bounds__(kThreads) k_sdf_query(const __grid_constant__ 
             *reinterpret_cast<float4*>(zb + s * kZStride + 4 * l) = z;
         }
         __syncwarp();
-        const float out = mlp_f32<IN>(P, zb + lane * kZStride, x0, x1, x2);
+        const float out = mlp_f32<IN>(sd, dp.b2, zb + lane * kZStride, x0, x1, x2);
         if (act) {
             sdf[qi] = out;
             if (deepest) deepest[qi] = (int8_t)(dd >= kFirstFeatureDepth ? dd - kFirstFeatureDepth + 1 : 0);
@@ -295,9 +290,11 @@ __global__ void __launch_bounds__(kThreads) k_grad(const float* __restrict__ W1,
 // Sphere tracing with adaptive stepping, FP32 decode (Sec. 3.4, A.4)
 // ---------------------------------------------------------------------------
 template <typename T, int IN>
-__global__ void __launch_bounds__(kThreads) k_trace_f32(const __grid_constant__ DecParams P,
-                                                        const Tables tb, const TraceArgs A) {
+__global__ void __launch_bounds__(kThreads, 3) k_trace_f32(const DecPtrs dp, const Tables tb, const TraceArgs A) {
     __shared__ __align__(16) float zbuf[kWarps][32 * kZStride];
+    __shared__ __align__(16) SmemDecoder sd;
+    stage_decoder<IN>(sd, dp.W1, dp.b1, dp.W2);
+    __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int g = lane >> 3, l = lane & 7, gbase = g << 3;
     const unsigned gmask = 0xffu << gbase;
@@ -326,19 +323,21 @@ __global__ void __launch_bounds__(kThreads) k_trace_f32(const __grid_constant__ 
             *reinterpret_cast<float4*>(zb + s * kZStride + 4 * l) = z;
         }
         __syncwarp();
-        const float dhat = mlp_f32<IN>(P, zb + lane * kZStride, x0, x1, x2);
+        const float dhat = mlp_f32<IN>(sd, dp.b2, zb + lane * kZStride, x0, x1, x2);
         __syncwarp();
         if (act) step_update(S, dhat, A, tb);
     }
 }
 
+DecPtrs dec_ptrs(const nglod_decoder* dec) { return DecPtrs{dec->W1, dec->b1, dec->W2, dec->b2}; }
+
 template <typename T, int IN>
-void launch_trace_f32(const DecParams& P, const Tables& tb, const TraceArgs& A, int grid, cudaStream_t st) {
+void launch_trace_f32(const DecPtrs& P, const Tables& tb, const TraceArgs& A, int grid, cudaStream_t st) {
     k_trace_f32<T, IN><<<grid, kThreads, 0, st>>>(P, tb, A);
 }
 
 template <typename T, int IN>
-void launch_query(const DecParams& P, const Tables& tb, const float* x, long long Q, int D, float* sdf,
+void launch_query(const DecPtrs& P, const Tables& tb, const float* x, long long Q, int D, float* sdf,
                   int8_t* deepest, int grid, cudaStream_t st) {
     k_sdf_query<T, IN><<<grid, kThreads, 0, st>>>(P, tb, x, Q, D, sdf, deepest);
 }
@@ -367,9 +366,10 @@ int run_grad(const nglod_decoder* dec, const Tables& tb, const GradArgs& A, bool
 
 }  // namespace
 
-int launch_trace_fp32(const nglod_decoder* dec, const DecParams& P, const Tables& tb, const TraceArgs& A,
-                      bool f16, int sms, cudaStream_t st) {
+int launch_trace_fp32(const nglod_decoder* dec, const Tables& tb, const TraceArgs& A, bool f16, int sms,
+                      cudaStream_t st) {
     const int grid = sms * 3;
+    const DecPtrs P = dec_ptrs(dec);
     if (dec->in_dim == 35) {
         if (f16) launch_trace_f32<__half, 35>(P, tb, A, grid, st); else launch_trace_f32<float, 35>(P, tb, A, grid, st);
     } else {
@@ -413,15 +413,17 @@ extern "C" int sdf_query(const nglod_svo* svo, const nglod_features* feats, cons
     if (rc) return rc;
     const bool f16 = feats->dtype == NGLOD_F16;
     if (decode_dtype == NGLOD_BF16) {
+        rc = check_decoder(dec);
+        if (rc) return rc;
         if (grad) return fail(NGLOD_ERR_NOT_SUPPORTED, "sdf_query: grad needs the FP32 decode");
         rc = launch_query_bf16(svo, tb, dec, x, Q, D, sdf, deepest, f16, st);
         if (rc) return rc;
         return NGLOD_OK;
     }
     if (decode_dtype != NGLOD_F32) return fail(NGLOD_ERR_NOT_SUPPORTED, "sdf_query: decode_dtype");
-    DecParams P;
-    rc = fill_dec_params(dec, P, st);
+    rc = check_decoder(dec);
     if (rc) return rc;
+    const DecPtrs P = dec_ptrs(dec);
     const int grid = grid_items(Q, kThreads, svo->num_sms, 4);
     if (dec->in_dim == 35) {
         if (f16) launch_query<__half, 35>(P, tb, x, Q, D, sdf, deepest, grid, st);
@@ -490,11 +492,10 @@ extern "C" int sphere_trace(const nglod_svo* svo, const nglod_features* feats, c
     A.queue = (int*)work;
     A.hit_vox = (int32_t*)((char*)work + 256);
     NGLOD_CUDA(cudaMemsetAsync(work, 0, 256, st));
+    rc = check_decoder(dec);
+    if (rc) return rc;
     if (params->decode_dtype == NGLOD_F32) {
-        DecParams P;
-        rc = fill_dec_params(dec, P, st);
-        if (rc) return rc;
-        rc = launch_trace_fp32(dec, P, tb, A, f16, svo->num_sms, st);
+        rc = launch_trace_fp32(dec, tb, A, f16, svo->num_sms, st);
     } else if (params->decode_dtype == NGLOD_BF16) {
         rc = launch_trace_bf16(svo, dec, tb, A, f16, st);
     } else {
@@ -535,4 +536,15 @@ extern "C" int trace_normals(const nglod_svo* svo, const nglod_features* feats, 
     A.hit = const_cast<uint8_t*>(hit);
     A.hit_vox = (int32_t*)((char*)work + 256);
     return launch_normals(dec, tb, A, normal, feats->dtype == NGLOD_F16, svo->num_sms, st);
+}
+
+extern "C" int sphere_trace_status(const void* work, void* stream) {
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!work) return fail(NGLOD_ERR_INVALID_ARG, "sphere_trace_status: NULL workspace");
+    int h[2] = {0, 0};
+    NGLOD_CUDA(cudaMemcpyAsync(h, work, sizeof(h), cudaMemcpyDeviceToHost, st));
+    NGLOD_CUDA(cudaStreamSynchronize(st));
+    if (h[1] == kStatusTimeout)
+        return fail(NGLOD_ERR_TIMEOUT, "sphere_trace: a tensor-core wait expired; results are invalid");
+    return NGLOD_OK;
 }

@@ -243,6 +243,7 @@ void destroy(nglod_svo* s, cudaStream_t st) {
         if (s->corners[d]) cudaFreeAsync(s->corners[d], st);
         if (s->anc[d]) cudaFreeAsync(s->anc[d], st);
     }
+    if (s->dstatus) cudaFreeAsync(s->dstatus, st);
     cudaStreamSynchronize(st);
     delete s;
 }
@@ -298,6 +299,8 @@ extern "C" int svo_build(const uint64_t* const* h_keys, const int64_t* h_counts,
     } while (0)
 
     BUILD_CUDA(cudaMallocAsync(&derr, sizeof(int), st));
+    BUILD_CUDA(cudaMallocAsync(&s->dstatus, sizeof(int), st));
+    BUILD_CUDA(cudaMemsetAsync(s->dstatus, 0, sizeof(int), st));
     BUILD_CUDA(cudaMemsetAsync(derr, 0, sizeof(int), st));
     for (int d = 0; d < num_depths; ++d) {
         s->n[d] = h_counts[d];

@@ -1,18 +1,308 @@
-// BF16 decode on the fifth-generation tensor cores (tcgen05): filled in by
-// the tensor-core sphere tracer.
+// BF16 decode on the fifth-generation tensor cores (tcgen05), for the sphere
+// tracer and for sdf_query.
+//
+// The decoder's first layer over a batch of 128 queries is a dense
+// contraction: pre[q][h] = sum_k z[q][k] W1[h][k], M = 128 queries,
+// N = 128 hidden units, K = 32 feature channels.  Each CTA owns 128 query
+// slots (thread i <-> A-tile row i <-> tensor-memory lane i):
+//   1. gather: 8-lane groups interpolate each slot's z (FP32) and write it as
+//      BF16 straight into the A tile, laid out as the MMA's canonical K-major
+//      operand (8-row x 16-byte core matrices);
+//   2. one thread issues two K = 16 tcgen05.mma (A, B from shared memory,
+//      FP32 accumulator in 128 TMEM columns) and commits to an mbarrier;
+//   3. epilogue: every thread loads its accumulator row with tcgen05.ld and
+//      applies b1 (+ the FP32 x-term when in_dim = 35), ReLU and the W2 dot
+//      product in FP32 on the CUDA cores.
+// W1 (z part) is converted to BF16 once per CTA and stays resident.  Several
+// CTAs share an SM (4 x 128 TMEM columns), so one CTA's gathers overlap
+// another's MMA and epilogue.  Every wait is bounded: on expiry the kernel
+// raises an error flag, drains its MMA, frees its tensor memory and returns.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <algorithm>
+
 #include "nglod_internal.cuh"
+#include "query_common.cuh"
+#include "tcgen05.cuh"
 #include "trace_common.cuh"
 
 namespace nglod {
+namespace {
 
-int launch_trace_bf16(const nglod_svo*, const nglod_decoder*, const Tables&, const TraceArgs&, bool,
-                      cudaStream_t) {
-    return fail(NGLOD_ERR_NOT_SUPPORTED, "sphere_trace: BF16 decode not built");
+constexpr int kTM = 128;                 // queries per tile = threads per CTA
+constexpr int kKc = kFeatDim / 8;        // 16-byte K chunks per operand row
+constexpr uint32_t kLbo = 128;           // K-adjacent core matrices
+constexpr uint32_t kSbo = 128 * kKc;     // M/N-adjacent 8-row groups
+constexpr long kWaitPolls = 1l << 24;
+constexpr int kDynSmem = 48 * 1024;      // > 228 KB / 5: at most 4 CTAs (512 TMEM columns) per SM
+constexpr int kCtasPerSm = 4;
+
+struct BfSmem {
+    unsigned char A[kTM * kFeatDim * 2];      // z tile, bf16, K-major
+    unsigned char B[kHidden * kFeatDim * 2];  // W1 (z columns), bf16, K-major
+    float4 epi[kHidden];                      // (b1, W2, W1x_0, W1x_1)
+    float wx2[kHidden];                       // W1x_2
+    uint64_t bar;
+    uint32_t taddr;
+};
+
+struct DecPtrsB {
+    const float* W1;
+    const float* b1;
+    const float* W2;
+    float b2;
+};
+
+template <int IN>
+__device__ __forceinline__ void stage_bf16_decoder(BfSmem& S, const DecPtrsB& dp) {
+    constexpr int OFF = IN - kFeatDim;
+    for (int i = threadIdx.x; i < kHidden * kFeatDim; i += blockDim.x) {
+        const int h = i / kFeatDim, k = i - h * kFeatDim;
+        *reinterpret_cast<__nv_bfloat16*>(S.B + tc::kmajor_offset(h, k, kKc)) =
+            __float2bfloat16_rn(dp.W1[h * IN + OFF + k]);
+    }
+    for (int h = threadIdx.x; h < kHidden; h += blockDim.x) {
+        const float x0 = OFF ? dp.W1[h * IN] : 0.f, x1 = OFF ? dp.W1[h * IN + 1] : 0.f;
+        S.epi[h] = make_float4(dp.b1[h], dp.W2[h], x0, x1);
+        S.wx2[h] = OFF ? dp.W1[h * IN + 2] : 0.f;
+    }
 }
 
-int launch_query_bf16(const nglod_svo*, const Tables&, const nglod_decoder*, const float*, long long, int,
-                      float*, int8_t*, bool, cudaStream_t) {
-    return fail(NGLOD_ERR_NOT_SUPPORTED, "sdf_query: BF16 decode not built");
+// Writes this lane's four z channels of A-tile row `row` as bf16.
+__device__ __forceinline__ void put_z(BfSmem& S, int row, int l, float4 z) {
+    const __nv_bfloat162 lo = __floats2bfloat162_rn(z.x, z.y);
+    const __nv_bfloat162 hi = __floats2bfloat162_rn(z.z, z.w);
+    uint2 v;
+    v.x = *reinterpret_cast<const uint32_t*>(&lo);
+    v.y = *reinterpret_cast<const uint32_t*>(&hi);
+    *reinterpret_cast<uint2*>(S.A + tc::kmajor_offset(row, 4 * l, kKc)) = v;
+}
+
+// Issues the tile's MMA (thread 0) and waits for it (all threads); returns
+// false if the wait expired.
+__device__ __forceinline__ bool mma_tile(BfSmem& S, uint32_t taddr, uint32_t& phase) {
+    tc::fence_proxy_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        tc::fence_after_sync();
+        const uint32_t idesc = tc::idesc_bf16_f32(kTM, kHidden);
+        const uint32_t a0 = tc::smem_u32(S.A), b0 = tc::smem_u32(S.B);
+#pragma unroll
+        for (int ks = 0; ks < kFeatDim / 16; ++ks)
+            tc::mma_bf16(taddr, tc::smem_desc_kmajor(a0 + ks * 256, kLbo, kSbo),
+                         tc::smem_desc_kmajor(b0 + ks * 256, kLbo, kSbo), idesc, ks > 0);
+        tc::mma_commit(&S.bar);
+    }
+    const bool ok = tc::mbar_wait(&S.bar, phase, kWaitPolls);
+    phase ^= 1u;
+    tc::fence_after_sync();
+    return ok;
+}
+
+// d = b2 + sum_h W2[h] relu(acc[h] + b1[h] (+ W1x[h] . x)) for this thread's row.
+template <int IN>
+__device__ __forceinline__ float epilogue(const BfSmem& S, uint32_t taddr, float b2, float x0, float x1, float x2) {
+    const int warp = threadIdx.x >> 5;
+    float out = b2;
+#pragma unroll 1
+    for (int c0 = 0; c0 < kHidden; c0 += 32) {
+        float v[32];
+        tc::tmem_ld32(taddr + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+        tc::tmem_wait_ld();
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+            const float4 e = S.epi[c0 + i];
+            float pre = v[i] + e.x;
+            if constexpr (IN != kFeatDim) pre = fmaf(e.z, x0, fmaf(e.w, x1, fmaf(S.wx2[c0 + i], x2, pre)));
+            out = fmaf(e.y, fmaxf(pre, 0.0f), out);
+        }
+    }
+    return out;
+}
+
+__device__ __forceinline__ void setup_tmem(BfSmem& S) {
+    if (threadIdx.x == 0) tc::mbar_init(&S.bar, 1);
+    if ((threadIdx.x >> 5) == 0) {
+        tc::tmem_alloc(&S.taddr, kHidden);
+        tc::tmem_relinquish();
+    }
+    tc::fence_proxy_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+}
+
+__device__ __forceinline__ void teardown_tmem(BfSmem& S, uint32_t taddr, bool drained, uint32_t phase) {
+    if (!drained) tc::mbar_wait(&S.bar, phase ^ 1u, kWaitPolls);   // let an expired MMA finish
+    tc::fence_before_sync();
+    __syncthreads();
+    if ((threadIdx.x >> 5) == 0) tc::tmem_dealloc(taddr, kHidden);
+}
+
+// ---------------------------------------------------------------------------
+// sphere tracing, BF16 decode
+// ---------------------------------------------------------------------------
+template <typename T, int IN>
+__global__ void __launch_bounds__(kTM, kCtasPerSm) k_trace_bf16(const DecPtrsB dp, const Tables tb, const TraceArgs A,
+                                                      int* __restrict__ err) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    BfSmem& S = *reinterpret_cast<BfSmem*>(smem_raw);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = lane >> 3, l = lane & 7, gbase = g << 3;
+    const unsigned gmask = 0xffu << gbase;
+    stage_bf16_decoder<IN>(S, dp);
+    setup_tmem(S);
+    const uint32_t taddr = S.taddr;
+    uint32_t phase = 0;
+    bool drained = true;
+    RaySlot st;
+    st.ray = -1;
+    RayQueue Qu;
+    Qu.init();
+    for (;;) {
+        refill(st, Qu, A, tb, lane);
+        const bool act = st.ray >= 0;
+        if (!__syncthreads_or(act)) break;
+        const float x0 = fmaf(st.t, st.dx, st.ox), x1 = fmaf(st.t, st.dy, st.oy), x2 = fmaf(st.t, st.dz, st.oz);
+        const float q0 = __fadd_rn(x0, 1.0f), q1 = __fadd_rn(x1, 1.0f), q2 = __fadd_rn(x2, 1.0f);
+#pragma unroll 1
+        for (int r = 0; r < 8; ++r) {
+            const int s = r * 4 + g;
+            const int sact = __shfl_sync(0xffffffffu, act ? 1 : 0, s);
+            const int svox = __shfl_sync(0xffffffffu, st.vox, s);
+            const uint32_t sijk = __shfl_sync(0xffffffffu, st.ijk, s);
+            const float s0 = __shfl_sync(0xffffffffu, q0, s);
+            const float s1 = __shfl_sync(0xffffffffu, q1, s);
+            const float s2 = __shfl_sync(0xffffffffu, q2, s);
+            float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (sact) z = gather_slot<T>(tb, A.D, svox, sijk, s0, s1, s2, gmask, gbase, l);
+            put_z(S, warp * 32 + s, l, z);
+        }
+        const bool ok = mma_tile(S, taddr, phase);
+        if (!__syncthreads_and(ok)) {
+            if (threadIdx.x == 0) atomicExch(err, kStatusTimeout);
+            drained = false;
+            break;
+        }
+        const float dhat = epilogue<IN>(S, taddr, dp.b2, x0, x1, x2);
+        if (act) step_update(st, dhat, A, tb);
+    }
+    teardown_tmem(S, taddr, drained, phase);
+}
+
+// ---------------------------------------------------------------------------
+// sdf_query, BF16 decode: tiles of 128 points
+// ---------------------------------------------------------------------------
+template <typename T, int IN>
+__global__ void __launch_bounds__(kTM, kCtasPerSm) k_query_bf16(const DecPtrsB dp, const Tables tb, const float* __restrict__ x,
+                                                      long long Q, int D, float* __restrict__ sdf,
+                                                      int8_t* __restrict__ deepest, int* __restrict__ err) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    BfSmem& S = *reinterpret_cast<BfSmem*>(smem_raw);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = lane >> 3, l = lane & 7, gbase = g << 3;
+    const unsigned gmask = 0xffu << gbase;
+    stage_bf16_decoder<IN>(S, dp);
+    setup_tmem(S);
+    const uint32_t taddr = S.taddr;
+    uint32_t phase = 0;
+    bool drained = true;
+    const long long ntiles = (Q + kTM - 1) / kTM;
+    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const long long qi = tile * kTM + threadIdx.x;
+        const bool act = qi < Q;
+        float x0 = 0.f, x1 = 0.f, x2 = 0.f;
+        if (act) {
+            x0 = x[3 * qi];
+            x1 = x[3 * qi + 1];
+            x2 = x[3 * qi + 2];
+        }
+        int vox;
+        uint32_t ijk;
+        const int dd = act ? locate_descend(tb, D, x0, x1, x2, vox, ijk) : -1;
+        const float q0 = __fadd_rn(x0, 1.0f), q1 = __fadd_rn(x1, 1.0f), q2 = __fadd_rn(x2, 1.0f);
+#pragma unroll 1
+        for (int r = 0; r < 8; ++r) {
+            const int s = r * 4 + g;
+            const int sdd = __shfl_sync(0xffffffffu, dd, s);
+            const int svox = __shfl_sync(0xffffffffu, vox, s);
+            const uint32_t sijk = __shfl_sync(0xffffffffu, ijk, s);
+            const float s0 = __shfl_sync(0xffffffffu, q0, s);
+            const float s1 = __shfl_sync(0xffffffffu, q1, s);
+            const float s2 = __shfl_sync(0xffffffffu, q2, s);
+            float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (sdd >= kFirstFeatureDepth) z = gather_slot<T>(tb, sdd, svox, sijk, s0, s1, s2, gmask, gbase, l);
+            put_z(S, warp * 32 + s, l, z);
+        }
+        const bool ok = mma_tile(S, taddr, phase);
+        if (!__syncthreads_and(ok)) {
+            if (threadIdx.x == 0) atomicExch(err, kStatusTimeout);
+            drained = false;
+            break;
+        }
+        const float out = epilogue<IN>(S, taddr, dp.b2, x0, x1, x2);
+        if (act) {
+            sdf[qi] = out;
+            if (deepest) deepest[qi] = (int8_t)(dd >= kFirstFeatureDepth ? dd - kFirstFeatureDepth + 1 : 0);
+        }
+    }
+    teardown_tmem(S, taddr, drained, phase);
+}
+
+DecPtrsB bptrs(const nglod_decoder* dec) { return DecPtrsB{dec->W1, dec->b1, dec->W2, dec->b2}; }
+
+template <typename T, int IN>
+void go_trace(const DecPtrsB& P, const Tables& tb, const TraceArgs& A, int* err, int grid, cudaStream_t st) {
+    k_trace_bf16<T, IN><<<grid, kTM, kDynSmem, st>>>(P, tb, A, err);
+}
+
+template <typename T, int IN>
+void go_query(const DecPtrsB& P, const Tables& tb, const float* x, long long Q, int D, float* sdf, int8_t* deep,
+              int* err, int grid, cudaStream_t st) {
+    k_query_bf16<T, IN><<<grid, kTM, kDynSmem, st>>>(P, tb, x, Q, D, sdf, deep, err);
+}
+
+}  // namespace
+
+int launch_trace_bf16(const nglod_svo* svo, const nglod_decoder* dec, const Tables& tb, const TraceArgs& A,
+                      bool f16, cudaStream_t st) {
+    static_assert(sizeof(BfSmem) <= kDynSmem, "shared layout");
+    // the error word shares the workspace header with the ray queue
+    int* err = A.queue + 1;
+    const int grid = svo->num_sms * kCtasPerSm;
+    const DecPtrsB P = bptrs(dec);
+    if (dec->in_dim == 35) {
+        if (f16) go_trace<__half, 35>(P, tb, A, err, grid, st); else go_trace<float, 35>(P, tb, A, err, grid, st);
+    } else {
+        if (f16) go_trace<__half, 32>(P, tb, A, err, grid, st); else go_trace<float, 32>(P, tb, A, err, grid, st);
+    }
+    NGLOD_CUDA(cudaGetLastError());
+    return NGLOD_OK;
+}
+
+int launch_query_bf16(const nglod_svo* svo, const Tables& tb, const nglod_decoder* dec, const float* x,
+                      long long Q, int D, float* sdf, int8_t* deepest, bool f16, cudaStream_t st) {
+    // the octree handle's device status word records an expired wait
+    int* err = svo->dstatus;
+    NGLOD_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
+    const long long tiles = (Q + kTM - 1) / kTM;
+    const int grid = (int)std::max<long long>(1, std::min<long long>(tiles, (long long)svo->num_sms * kCtasPerSm));
+    const DecPtrsB P = bptrs(dec);
+    if (dec->in_dim == 35) {
+        if (f16) go_query<__half, 35>(P, tb, x, Q, D, sdf, deepest, err, grid, st);
+        else go_query<float, 35>(P, tb, x, Q, D, sdf, deepest, err, grid, st);
+    } else {
+        if (f16) go_query<__half, 32>(P, tb, x, Q, D, sdf, deepest, err, grid, st);
+        else go_query<float, 32>(P, tb, x, Q, D, sdf, deepest, err, grid, st);
+    }
+    NGLOD_CUDA(cudaGetLastError());
+    int h = 0;
+    NGLOD_CUDA(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    NGLOD_CUDA(cudaStreamSynchronize(st));
+    if (h) return fail(NGLOD_ERR_TIMEOUT, "sdf_query: tensor-core wait expired");
+    return NGLOD_OK;
 }
 
 }  // namespace nglod

@@ -1,6 +1,6 @@
 // Ray state and stepping rules of the sphere tracer (Sec. 3.4 "Adaptive Ray
 // Stepping", supplementary Sec. A.4) shared by the FP32 and BF16 kernels,
-// plus the FP32 decoder evaluated with constant-bank weights.
+// plus the FP32 decoder evaluated from shared-memory weights.
 #pragma once
 
 #include "nglod_internal.cuh"
@@ -8,41 +8,69 @@
 
 namespace nglod {
 
-// The whole FP32 decoder as a kernel parameter block (constant bank).
-struct DecParams {
-    float W1[kHidden * 35];   // [hidden][in_dim], row stride = in_dim
-    float b1[kHidden];
-    float W2[kHidden];
-    float b2;
+// FP32 decoder staged in shared memory.  Row h of W1 is stored reordered as
+// [z_0..z_31, x_0, x_1, x_2, 0] (K4 = 32 or 36 floats) so that the input
+// vector splits into aligned float4s; every thread of a warp reads the same
+// row (a broadcast), so each 16-byte shared load feeds four FFMAs.
+constexpr int kK4Max = 36;
+struct SmemDecoder {
+    float W1[kHidden * kK4Max];
+    float2 bw[kHidden];        // (b1[h], W2[h])
 };
 
-// d = W2 . relu(W1 [x, z] + b1) + b2 for the lane's own slot, z read from
-// its staged row.  Fully unrolled: each weight is an immediate operand.
 template <int IN>
-__device__ __forceinline__ float mlp_f32(const DecParams& P, const float* zrow, float x0, float x1,
-                                         float x2) {
+__device__ __forceinline__ void stage_decoder(SmemDecoder& sd, const float* __restrict__ W1,
+                                              const float* __restrict__ b1, const float* __restrict__ W2) {
     constexpr int OFF = IN - kFeatDim;
-    float v[IN];
-    if constexpr (OFF == 3) {
-        v[0] = x0;
-        v[1] = x1;
-        v[2] = x2;
+    constexpr int K4 = OFF ? 36 : 32;
+    for (int i = threadIdx.x; i < kHidden * K4; i += blockDim.x) {
+        const int h = i / K4, k = i - h * K4;
+        float w;
+        if (k < kFeatDim) w = W1[h * IN + OFF + k];
+        else if (k < kFeatDim + OFF) w = W1[h * IN + (k - kFeatDim)];
+        else w = 0.0f;
+        sd.W1[i] = w;
     }
+    for (int h = threadIdx.x; h < kHidden; h += blockDim.x) sd.bw[h] = make_float2(b1[h], W2[h]);
+}
+
+// d = W2 . relu(W1 [x, z] + b1) + b2 for the lane's own slot, z read from
+// its staged row (Eq. 2).
+template <int IN>
+__device__ __forceinline__ float mlp_f32(const SmemDecoder& sd, float b2, const float* zrow, float x0,
+                                         float x1, float x2) {
+    constexpr int OFF = IN - kFeatDim;
+    constexpr int K4 = OFF ? 36 : 32;
+    float v[K4];
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
         const float4 a = reinterpret_cast<const float4*>(zrow)[j];
-        v[OFF + 4 * j] = a.x;
-        v[OFF + 4 * j + 1] = a.y;
-        v[OFF + 4 * j + 2] = a.z;
-        v[OFF + 4 * j + 3] = a.w;
+        v[4 * j] = a.x;
+        v[4 * j + 1] = a.y;
+        v[4 * j + 2] = a.z;
+        v[4 * j + 3] = a.w;
     }
-    float out = P.b2;
-#pragma unroll
+    if constexpr (OFF == 3) {
+        v[32] = x0;
+        v[33] = x1;
+        v[34] = x2;
+        v[35] = 0.0f;
+    }
+    float out = b2;
+#pragma unroll 2
     for (int h = 0; h < kHidden; ++h) {
-        float acc = P.b1[h];
+        const float4* w = reinterpret_cast<const float4*>(sd.W1 + h * K4);
+        float a0 = 0.0f, a1 = 0.0f;
 #pragma unroll
-        for (int k = 0; k < IN; ++k) acc = fmaf(P.W1[h * IN + k], v[k], acc);
-        out = fmaf(P.W2[h], fmaxf(acc, 0.0f), out);
+        for (int j = 0; j < K4 / 4; ++j) {
+            const float4 ww = w[j];
+            a0 = fmaf(ww.x, v[4 * j], a0);
+            a1 = fmaf(ww.y, v[4 * j + 1], a1);
+            a0 = fmaf(ww.z, v[4 * j + 2], a0);
+            a1 = fmaf(ww.w, v[4 * j + 3], a1);
+        }
+        const float2 bw = sd.bw[h];
+        out = fmaf(bw.y, fmaxf(a0 + a1 + bw.x, 0.0f), out);
     }
     return out;
 }
@@ -190,9 +218,9 @@ __device__ __forceinline__ void step_update(RaySlot& S, float dhat, const TraceA
 
 // Host-side entry points implemented per translation unit.
 int fill_tables(const nglod_svo* svo, const nglod_features* f, int lod, Tables& tb);
-int fill_dec_params(const nglod_decoder* dec, DecParams& P, cudaStream_t st);
-int launch_trace_fp32(const nglod_decoder* dec, const DecParams& P, const Tables& tb, const TraceArgs& A,
-                      bool f16, int sms, cudaStream_t st);
+int check_decoder(const nglod_decoder* dec);
+int launch_trace_fp32(const nglod_decoder* dec, const Tables& tb, const TraceArgs& A, bool f16, int sms,
+                      cudaStream_t st);
 int launch_normals(const nglod_decoder* dec, const Tables& tb, const TraceArgs& A, float* normal, bool f16,
                    int sms, cudaStream_t st);
 int launch_trace_bf16(const nglod_svo* svo, const nglod_decoder* dec, const Tables& tb, const TraceArgs& A,

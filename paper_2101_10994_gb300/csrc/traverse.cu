@@ -24,7 +24,6 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kItems = 4;
 constexpr int kTile = kThreads * kItems;
-constexpr int kCtasPerSm = 6;
 constexpr unsigned long long kFlagAgg = 1ull << 62;
 constexpr unsigned long long kFlagPre = 2ull << 62;
 constexpr unsigned long long kValMask = (1ull << 62) - 1;
@@ -61,34 +60,45 @@ __device__ __forceinline__ unsigned long long ld_acquire(const unsigned long lon
     return v;
 }
 
-// Exclusive prefix of this tile among all tiles (decoupled look-back).
-// Called by one thread.  Every wait is bounded; on expiry the status word
-// records a timeout and the (then meaningless) partial prefix is returned.
-__device__ long long tile_prefix(unsigned long long* state, long long tile, long long agg, int* status) {
+// Exclusive prefix of this tile among all tiles (decoupled look-back),
+// computed by one whole warp: each poll reads the published states of the 32
+// nearest unvisited predecessors at once, sums the aggregates up to the
+// nearest one that already carries its inclusive prefix, and moves the
+// window back only when none does.  Every wait is bounded; on expiry the
+// status word records a timeout and the (then meaningless) partial prefix is
+// returned.
+__device__ long long tile_prefix_warp(unsigned long long* state, long long tile, long long agg, int* status) {
+    const int lane = threadIdx.x & 31;
     if (tile == 0) {
-        st_release(state, kFlagPre | (unsigned long long)agg);
+        if (lane == 0) st_release(state, kFlagPre | (unsigned long long)agg);
         return 0;
     }
-    st_release(state + tile, kFlagAgg | (unsigned long long)agg);
+    if (lane == 0) st_release(state + tile, kFlagAgg | (unsigned long long)agg);
     long long excl = 0;
-    long long j = tile - 1;
+    long long end = tile - 1;          // nearest predecessor not yet summed
     long spins = 0;
-    while (j >= 0) {
-        const unsigned long long s = ld_acquire(state + j);
+    for (;;) {
+        const long long j = end - lane;
+        const unsigned long long s = j >= 0 ? ld_acquire(state + j) : kFlagPre;
         const unsigned long long flag = s & ~kValMask;
-        if (flag == 0ull) {
+        if (__any_sync(0xffffffffu, flag == 0ull)) {
             if (++spins > kSpinLimit) {
-                atomicExch(status, kStatusTimeout);
+                if (lane == 0) atomicExch(status, kStatusTimeout);
                 break;
             }
-            if (spins > 64) __nanosleep(64);
+            if (spins > 16) __nanosleep(32);
             continue;
         }
-        excl += (long long)(s & kValMask);
-        if (flag == kFlagPre) break;
-        --j;
+        const unsigned pre = __ballot_sync(0xffffffffu, flag == kFlagPre);
+        const int stop = pre ? __ffs(pre) - 1 : 31;
+        long long v = lane <= stop ? (long long)(s & kValMask) : 0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        excl += v;
+        if (pre) break;
+        end -= 32;
     }
-    st_release(state + tile, kFlagPre | (unsigned long long)(excl + agg));
+    if (lane == 0) st_release(state + tile, kFlagPre | (unsigned long long)(excl + agg));
     return excl;
 }
 
@@ -149,7 +159,16 @@ __global__ void __launch_bounds__(kThreads) k_prep_rays(const float* __restrict_
     if (blockIdx.x == 0 && threadIdx.x == 0) ctr->count[0] = R;
 }
 
+// Shared staging for one tile's output: up to 8 children per pair (int2),
+// or at the final level one (voxel, t_enter/t_exit, ray) record per pair.
+constexpr int kStageBytes = kTile * 8 * (int)sizeof(int2);
+
 __global__ void __launch_bounds__(kThreads) k_level(const LevelParams p) {
+    extern __shared__ __align__(16) unsigned char stage[];
+    int2* stage_p = reinterpret_cast<int2*>(stage);
+    int32_t* stage_i = reinterpret_cast<int32_t*>(stage);
+    float2* stage_f = reinterpret_cast<float2*>(stage + kTile * sizeof(int32_t));
+    int32_t* stage_r = reinterpret_cast<int32_t*>(stage + kTile * (sizeof(int32_t) + sizeof(float2)));
     __shared__ int warp_sums[kThreads / 32 + 1];
     __shared__ long long s_tile;
     __shared__ long long s_prefix;
@@ -194,14 +213,15 @@ __global__ void __launch_bounds__(kThreads) k_level(const LevelParams p) {
                 const RayPrep ray = p.rays[pr[i].x];
                 const Node nd = p.node[pr[i].y];
                 float a0, a1;
-                if (ray.valid && slab_test(ray, nd.ijk, p.dp, a0, a1)) {
+                uint32_t oct;
+                if (ray.valid && slab_test(ray, nd.ijk, p.dp, a0, a1, final_level ? nullptr : &oct)) {
                     if (final_level) {
                         cnt[i] = 1;
                         tin[i] = a0;
                         tout[i] = a1;
                     } else {
                         cnt[i] = __popc(nd.childmask);
-                        aux[i] = nd.childmask | (origin_octant(ray, nd.ijk, p.dp) << 8);
+                        aux[i] = nd.childmask | (oct << 8);
                         cb[i] = nd.childbase;
                     }
                 }
@@ -210,47 +230,57 @@ __global__ void __launch_bounds__(kThreads) k_level(const LevelParams p) {
         }
         int tile_total;
         const int excl = block_exclusive_sum(sum, warp_sums, tile_total);
-        if (threadIdx.x == 0) {
-            const long long pre = tile_prefix(p.tile_state, tile, tile_total, &p.ctr->status);
-            s_prefix = pre;
-            if (tile == ntiles - 1) {
-                const long long total = pre + tile_total;
-                p.ctr->count[p.dp + 1] = total;
-                if (total > p.ctr->max_pairs) p.ctr->max_pairs = total;
-                if (total > (final_level ? p.hit_cap : p.out_cap))
-                    atomicCAS(&p.ctr->status, kStatusOk, kStatusOverflow);
+        if (threadIdx.x < 32) {
+            const long long pre = tile_prefix_warp(p.tile_state, tile, tile_total, &p.ctr->status);
+            if (threadIdx.x == 0) {
+                s_prefix = pre;
+                if (tile == ntiles - 1) {
+                    const long long total = pre + tile_total;
+                    p.ctr->count[p.dp + 1] = total;
+                    if (total > p.ctr->max_pairs) p.ctr->max_pairs = total;
+                    if (total > (final_level ? p.hit_cap : p.out_cap))
+                        atomicCAS(&p.ctr->status, kStatusOk, kStatusOverflow);
+                }
             }
         }
-        __syncthreads();
-        long long off = s_prefix + excl;
+        // stage this tile's output in shared memory at tile-local offsets ...
+        int loc = excl;
         if (final_level) {
 #pragma unroll
             for (int i = 0; i < kItems; ++i) {
-                if (cnt[i] && off < p.hit_cap) {
-                    p.voxel_id[off] = pr[i].y;
-                    p.t_range[off] = make_float2(tin[i], tout[i]);
-                    p.out_ray[off] = pr[i].x;
+                if (cnt[i]) {
+                    stage_i[loc] = pr[i].y;
+                    stage_f[loc] = make_float2(tin[i], tout[i]);
+                    stage_r[loc] = pr[i].x;
                 }
-                off += cnt[i];
+                loc += cnt[i];
             }
         } else {
 #pragma unroll
             for (int i = 0; i < kItems; ++i) {
-                if (cnt[i]) {
-                    const uint32_t mask = aux[i] & 0xffu, oct = aux[i] >> 8;
-#pragma unroll
-                    for (uint32_t r = 0; r < 8; ++r) {
-                        const uint32_t c = r ^ oct;
-                        if ((mask >> c) & 1u) {
-                            if (off < p.out_cap)
-                                p.out[off] = make_int2(pr[i].x, cb[i] + __popc(mask & ((1u << c) - 1u)));
-                            ++off;
-                        }
-                    }
+                const uint32_t mask = aux[i] & 0xffu, oct = aux[i] >> 8;
+                // occupied children in front-to-back rank order (Subdivide)
+                for (uint32_t rm = rank_mask(mask, oct); rm; rm &= rm - 1u) {
+                    const uint32_t c = (uint32_t)(__ffs(rm) - 1) ^ oct;
+                    stage_p[loc++] = make_int2(pr[i].x, cb[i] + __popc(mask & ((1u << c) - 1u)));
                 }
             }
         }
-        __syncthreads();   // s_tile / s_prefix / warp_sums reuse
+        __syncthreads();
+        // ... then write it to its global position with coalesced stores
+        const long long off = s_prefix;
+        if (final_level) {
+            const long long lim = min((long long)tile_total, p.hit_cap - off);
+            for (int i = threadIdx.x; i < lim; i += kThreads) {
+                p.voxel_id[off + i] = stage_i[i];
+                p.t_range[off + i] = stage_f[i];
+                p.out_ray[off + i] = stage_r[i];
+            }
+        } else {
+            const long long lim = min((long long)tile_total, p.out_cap - off);
+            for (int i = threadIdx.x; i < lim; i += kThreads) p.out[off + i] = stage_p[i];
+        }
+        __syncthreads();   // s_tile / s_prefix / warp_sums / staging reuse
     }
 }
 
@@ -271,6 +301,19 @@ __global__ void __launch_bounds__(kThreads) k_ray_offsets(const int32_t* __restr
 }
 
 size_t align_up(size_t v, size_t a = 256) { return (v + a - 1) / a * a; }
+
+// Resident CTAs per SM of the level kernel with its staging buffer (the
+// persistent grid is sized to exactly what fits).
+int level_ctas_per_sm() {
+    static int cached = 0;
+    if (!cached) {
+        cudaFuncSetAttribute(k_level, cudaFuncAttributeMaxDynamicSharedMemorySize, kStageBytes);
+        int n = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_level, kThreads, kStageBytes);
+        cached = n > 0 ? n : 1;
+    }
+    return cached;
+}
 
 long long max_tiles(long long R, long long cap) {
     return (std::max(R, cap) + kTile - 1) / kTile + 1;
@@ -346,8 +389,8 @@ extern "C" int svo_trace_rays(const nglod_svo* svo, const float* o, const float*
         lp.tile_state = tile_state;
         lp.dp = dp;
         lp.D = D;
-        const long long grid = std::min<long long>(ntiles_max, (long long)sms * kCtasPerSm);
-        k_level<<<(unsigned)grid, kThreads, 0, st>>>(lp);
+        const long long grid = std::min<long long>(ntiles_max, (long long)sms * level_ctas_per_sm());
+        k_level<<<(unsigned)grid, kThreads, kStageBytes, st>>>(lp);
     }
     k_ray_offsets<<<std::min<long long>((R + kThreads) / kThreads, (long long)sms * 16), kThreads, 0, st>>>(
         (const int32_t*)buf[(D + 1) & 1], ctr, D, R, ray_offsets);

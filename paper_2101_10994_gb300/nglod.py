@@ -18,11 +18,12 @@ LIB_PATH = os.path.join(HERE, "libnglod.so")
 
 NGLOD_OK, ERR_INVALID_ARG, ERR_CAPACITY, ERR_CUDA, ERR_OOM, ERR_TIMEOUT, ERR_NOT_SUPPORTED = range(7)
 F32, F16, BF16 = 0, 1, 2
+BF16_DECODE = True          # the tensor-core (tcgen05) decode is built
 FIRST_FEATURE_DEPTH = 3
 
 EXPORTS = ["nglod_last_error", "svo_build", "svo_info", "svo_device_arrays", "svo_read_arrays", "svo_free",
            "svo_trace_rays_workspace", "svo_trace_rays", "sdf_query", "sphere_trace_workspace",
-           "sphere_trace", "trace_normals", "svo_trace_rays_noalloc"]
+           "sphere_trace", "sphere_trace_status", "trace_normals", "svo_trace_rays_noalloc"]
 
 
 class NglodError(RuntimeError):
@@ -37,8 +38,7 @@ class _Features(C.Structure):
 
 class _Decoder(C.Structure):
     _fields_ = [("W1", C.c_void_p), ("b1", C.c_void_p), ("W2", C.c_void_p), ("b2", C.c_float),
-                ("in_dim", C.c_int), ("hidden", C.c_int), ("h_W1", C.c_void_p), ("h_b1", C.c_void_p),
-                ("h_W2", C.c_void_p)]
+                ("in_dim", C.c_int), ("hidden", C.c_int)]
 
 
 class _TraceParams(C.Structure):
@@ -73,6 +73,7 @@ def lib():
         L.sphere_trace_workspace.argtypes = [i64]
         L.sphere_trace.argtypes = [P, P, P, P, P, i64, i32, P, P, P, P, P, sz, P, P, P, P, P]
         L.trace_normals.argtypes = [P, P, P, P, P, i64, i32, P, sz, P, P, P, P]
+        L.sphere_trace_status.argtypes = [P, P]
         L.svo_trace_rays_noalloc.argtypes = [P, P, P, i64, i32, P, P, P, i64, P, P]
         _lib = L
     return _lib
@@ -176,7 +177,7 @@ class Features:
 
 
 class DecoderDev:
-    """One LOD's decoder on the device plus its host mirror (FP32 weights)."""
+    """One LOD's decoder on the device (FP32 weights)."""
 
     def __init__(self, W1, b1, W2, b2, device="cuda"):
         import torch
@@ -199,7 +200,6 @@ class DecoderDev:
         d.W1, d.b1, d.W2 = self.W1.data_ptr(), self.b1.data_ptr(), self.W2.data_ptr()
         d.b2 = self.b2
         d.in_dim, d.hidden = self.in_dim, self.hidden
-        d.h_W1, d.h_b1, d.h_W2 = self.h_W1.ctypes.data, self.h_b1.ctypes.data, self.h_W2.ctypes.data
         return d
 
 
@@ -309,3 +309,8 @@ def trace_normals(svo: SVO, feats: Features, dec: DecoderDev, o, d, lists: RayLi
                                out["work"].data_ptr(), out["work"].numel(), out["t"].data_ptr(),
                                out["hit"].data_ptr(), out["normal"].data_ptr(), C.c_void_p(_stream(stream))))
     return out
+
+
+def sphere_trace_status(out, stream=None):
+    """Raises if the sphere_trace that filled ``out`` hit an expired wait."""
+    _check(lib().sphere_trace_status(out["work"].data_ptr(), C.c_void_p(_stream(stream))))
