@@ -214,7 +214,10 @@ size_t sphere_trace_workspace(int64_t R);
  * is a hit, otherwise t += d; t > far_t or max_steps reached is a miss.
  *   o, d, R, lod        as for svo_trace_rays (same rays, same LOD).
  *   ray_offsets, voxel_id, t_range   the CSR lists of svo_trace_rays.
- *   work                device workspace >= sphere_trace_workspace(R).
+ *   work                device workspace >= sphere_trace_workspace(R).  After
+ *                       the call, bytes [256, 256 + 4R) hold the int32 id (at
+ *                       the target depth) of the voxel each hit ray stopped in,
+ *                       -1 for misses; trace_normals reads them.
  * Outputs: t_hit [R] (+inf on miss), hit [R] uint8, steps [R] int32
  * (nullable: decodes taken), normal [R, 3] (nullable; normalised analytic
  * gradient of the decoded SDF at the hit point in FP32, zero on miss).

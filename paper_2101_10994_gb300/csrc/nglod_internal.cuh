@@ -125,6 +125,17 @@ __device__ __forceinline__ bool slab_test(const RayPrep& r, uint32_t ijk, int dp
     return true;
 }
 
+// Octant of the ray origin relative to the centre lo + 2^(-dp) of voxel
+// (i,j,k) at depth dp, computed exactly as inside slab_test.
+__device__ __forceinline__ uint32_t origin_octant(const RayPrep& r, uint32_t ijk, int dp) {
+    const float s = pow2f(1 - dp);
+    const float hs = pow2f(-dp);
+    const float cx = __fadd_rn(__fmaf_rn((float)unpack_i(ijk), s, -1.0f), hs);
+    const float cy = __fadd_rn(__fmaf_rn((float)unpack_j(ijk), s, -1.0f), hs);
+    const float cz = __fadd_rn(__fmaf_rn((float)unpack_k(ijk), s, -1.0f), hs);
+    return (r.ox >= cx ? 1u : 0u) | (r.oy >= cy ? 2u : 0u) | (r.oz >= cz ? 4u : 0u);
+}
+
 // Child-slot mask re-indexed by front-to-back rank: bit r is set iff slot
 // r ^ oct is occupied (an XOR permutation of the 8 bits, by conditional swaps
 // of adjacent bits, bit pairs and nibbles).

@@ -35,8 +35,7 @@ constexpr int kKc = kFeatDim / 8;        // 16-byte K chunks per operand row
 constexpr uint32_t kLbo = 128;           // K-adjacent core matrices
 constexpr uint32_t kSbo = 128 * kKc;     // M/N-adjacent 8-row groups
 constexpr long kWaitPolls = 1l << 24;
-constexpr int kDynSmem = 48 * 1024;      // > 228 KB / 5: at most 4 CTAs (512 TMEM columns) per SM
-constexpr int kCtasPerSm = 4;
+constexpr int kCtasPerSm = 4;           // 4 x 128 TMEM columns = the SM's 512
 
 struct BfSmem {
     unsigned char A[kTM * kFeatDim * 2];      // z tile, bf16, K-major
@@ -46,6 +45,11 @@ struct BfSmem {
     uint64_t bar;
     uint32_t taddr;
 };
+// Shared memory is kept small so the rest of the SM's 256 KB serves as L1
+// for the feature gathers; registers (>= 103 per thread) already keep
+// residency at 4 CTAs per SM.  A fifth CTA on an SM would only wait in
+// tcgen05.alloc until one of the four finished.
+constexpr int kDynSmem = (int)((sizeof(BfSmem) + 1023) / 1024 * 1024);
 
 struct DecPtrsB {
     const float* W1;
@@ -253,14 +257,24 @@ __global__ void __launch_bounds__(kTM, kCtasPerSm) k_query_bf16(const DecPtrsB d
 
 DecPtrsB bptrs(const nglod_decoder* dec) { return DecPtrsB{dec->W1, dec->b1, dec->W2, dec->b2}; }
 
+template <typename K>
+void prefer_l1(K kernel) {
+    // shared-memory share of the unified L1/shared storage, in percent
+    cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 40);
+}
+
 template <typename T, int IN>
 void go_trace(const DecPtrsB& P, const Tables& tb, const TraceArgs& A, int* err, int grid, cudaStream_t st) {
+    static bool once = (prefer_l1(k_trace_bf16<T, IN>), true);
+    (void)once;
     k_trace_bf16<T, IN><<<grid, kTM, kDynSmem, st>>>(P, tb, A, err);
 }
 
 template <typename T, int IN>
 void go_query(const DecPtrsB& P, const Tables& tb, const float* x, long long Q, int D, float* sdf, int8_t* deep,
               int* err, int grid, cudaStream_t st) {
+    static bool once = (prefer_l1(k_query_bf16<T, IN>), true);
+    (void)once;
     k_query_bf16<T, IN><<<grid, kTM, kDynSmem, st>>>(P, tb, x, Q, D, sdf, deep, err);
 }
 

@@ -22,8 +22,6 @@ namespace nglod {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kItems = 4;
-constexpr int kTile = kThreads * kItems;
 constexpr unsigned long long kFlagAgg = 1ull << 62;
 constexpr unsigned long long kFlagPre = 2ull << 62;
 constexpr unsigned long long kValMask = (1ull << 62) - 1;
@@ -159,74 +157,93 @@ __global__ void __launch_bounds__(kThreads) k_prep_rays(const float* __restrict_
     if (blockIdx.x == 0 && threadIdx.x == 0) ctr->count[0] = R;
 }
 
-// Shared staging for one tile's output: up to 8 children per pair (int2),
-// or at the final level one (voxel, t_enter/t_exit, ray) record per pair.
-constexpr int kStageBytes = kTile * 8 * (int)sizeof(int2);
+// One level of the traversal, with Decide of the next level fused into
+// Subdivide.  Input: the pairs (ray, voxel) of depth dp that Decide kept (at
+// dp = 0 the implicit pairs (ray, root), which are decided here first).  For
+// each input pair the thread tests the voxel's occupied children (their
+// bounds follow from the parent's coordinates, no load needed), counts the
+// hit ones (Decide of depth dp + 1), the CTA scans the counts
+// (ExclusiveSum) and obtains its tile's global offset by decoupled
+// look-back, and the hit children are written in front-to-back rank order
+// (Subdivide).  When depth dp + 1 is the target depth the written list is
+// the final one (Compactify): voxel ids, their (t_enter, t_exit) and the ray
+// of each entry.  Output order and contents equal those of the unfused
+// Decide / ExclusiveSum / Subdivide / Compactify sequence.
+constexpr int kTileX = kThreads * 2;                 // parents per tile (2 per thread)
+constexpr int kStageBytes = kTileX * 8 * 16;         // up to 8 children x 16 B per parent
 
 __global__ void __launch_bounds__(kThreads) k_level(const LevelParams p) {
+    constexpr int kIt = kTileX / kThreads;
     extern __shared__ __align__(16) unsigned char stage[];
     int2* stage_p = reinterpret_cast<int2*>(stage);
     int32_t* stage_i = reinterpret_cast<int32_t*>(stage);
-    float2* stage_f = reinterpret_cast<float2*>(stage + kTile * sizeof(int32_t));
-    int32_t* stage_r = reinterpret_cast<int32_t*>(stage + kTile * (sizeof(int32_t) + sizeof(float2)));
+    float2* stage_f = reinterpret_cast<float2*>(stage + kTileX * 8 * sizeof(int32_t));
+    int32_t* stage_r = reinterpret_cast<int32_t*>(stage + kTileX * 8 * (sizeof(int32_t) + sizeof(float2)));
     __shared__ int warp_sums[kThreads / 32 + 1];
     __shared__ long long s_tile;
     __shared__ long long s_prefix;
     if (p.ctr->status != kStatusOk) return;
     const long long n = p.ctr->count[p.dp];
-    const long long ntiles = (n + kTile - 1) / kTile;
-    const bool final_level = p.dp == p.D;
+    const long long ntiles = (n + kTileX - 1) / kTileX;
+    const int dc = p.dp + 1;                          // depth of the children
+    const bool final_level = dc == p.D;
     for (;;) {
         if (threadIdx.x == 0) s_tile = atomicAdd(&p.ctr->tile_ctr[p.dp], 1);
         __syncthreads();
         const long long tile = s_tile;
         if (tile >= ntiles) break;
-        const long long base = tile * kTile + (long long)threadIdx.x * kItems;
-
-        int2 pr[kItems];
-        int cnt[kItems];
-        uint32_t aux[kItems];      // dp < D: childmask | octant << 8 ; dp == D: unused
-        int32_t cb[kItems];        // dp < D: childbase
-        float tin[kItems], tout[kItems];
+        const long long base = tile * kTileX + (long long)threadIdx.x * kIt;
+        int2 pr[kIt];
+        RayPrep ray[kIt];
+        uint32_t cij[kIt];       // coordinates of child slot 0 (parent coords << 1)
+        uint32_t mask[kIt];      // occupied children (slot bits)
+        uint32_t hitr[kIt];      // hit children, by front-to-back rank
+        uint32_t oct[kIt];
+        int32_t cb[kIt];
         int sum = 0;
-        if (p.dp > 0 && base + kItems <= n) {
-            const int4* src = reinterpret_cast<const int4*>(p.in + base);
-            const int4 a = src[0], b = src[1];
+        if (p.dp > 0 && base + kIt <= n) {
+            const int4 a = *reinterpret_cast<const int4*>(p.in + base);
             pr[0] = make_int2(a.x, a.y);
             pr[1] = make_int2(a.z, a.w);
-            pr[2] = make_int2(b.x, b.y);
-            pr[3] = make_int2(b.z, b.w);
         } else {
 #pragma unroll
-            for (int i = 0; i < kItems; ++i) {
+            for (int i = 0; i < kIt; ++i) {
                 const long long idx = base + i;
                 pr[i] = idx < n ? (p.dp == 0 ? make_int2((int)idx, 0) : p.in[idx]) : make_int2(-1, -1);
             }
         }
 #pragma unroll
-        for (int i = 0; i < kItems; ++i) {
-            cnt[i] = 0;
-            aux[i] = 0;
+        for (int i = 0; i < kIt; ++i) {
+            hitr[i] = 0;
+            mask[i] = 0;
+            oct[i] = 0;
             cb[i] = 0;
-            tin[i] = tout[i] = 0.0f;
-            if (pr[i].x >= 0) {
-                const RayPrep ray = p.rays[pr[i].x];
-                const Node nd = p.node[pr[i].y];
-                float a0, a1;
-                uint32_t oct;
-                if (ray.valid && slab_test(ray, nd.ijk, p.dp, a0, a1, final_level ? nullptr : &oct)) {
-                    if (final_level) {
-                        cnt[i] = 1;
-                        tin[i] = a0;
-                        tout[i] = a1;
-                    } else {
-                        cnt[i] = __popc(nd.childmask);
-                        aux[i] = nd.childmask | (oct << 8);
-                        cb[i] = nd.childbase;
-                    }
-                }
+            cij[i] = 0;
+            if (pr[i].x < 0) continue;
+            ray[i] = p.rays[pr[i].x];
+            const Node nd = p.node[pr[i].y];
+            uint32_t o8;
+            if (p.dp == 0) {
+                // the root is the only undecided input; every other pair was kept by Decide
+                float t0, t1;
+                if (!ray[i].valid || !slab_test(ray[i], nd.ijk, 0, t0, t1, &o8)) continue;
+            } else {
+                o8 = origin_octant(ray[i], nd.ijk, p.dp);
             }
-            sum += cnt[i];
+            mask[i] = nd.childmask;
+            oct[i] = o8;
+            cb[i] = nd.childbase;
+            cij[i] = (nd.ijk << 1) & 0x3ffffffeu;
+            uint32_t h = 0;
+            for (uint32_t rm = rank_mask(nd.childmask, o8); rm; rm &= rm - 1u) {
+                const uint32_t r = (uint32_t)(__ffs(rm) - 1);
+                const uint32_t c = r ^ o8;
+                const uint32_t ijk = cij[i] | pack_ijk(c & 1u, (c >> 1) & 1u, (c >> 2) & 1u);
+                float a0, a1;
+                if (slab_test(ray[i], ijk, dc, a0, a1)) h |= 1u << r;
+            }
+            hitr[i] = h;
+            sum += __popc(h);
         }
         int tile_total;
         const int excl = block_exclusive_sum(sum, warp_sums, tile_total);
@@ -236,7 +253,7 @@ __global__ void __launch_bounds__(kThreads) k_level(const LevelParams p) {
                 s_prefix = pre;
                 if (tile == ntiles - 1) {
                     const long long total = pre + tile_total;
-                    p.ctr->count[p.dp + 1] = total;
+                    p.ctr->count[dc] = total;
                     if (total > p.ctr->max_pairs) p.ctr->max_pairs = total;
                     if (total > (final_level ? p.hit_cap : p.out_cap))
                         atomicCAS(&p.ctr->status, kStatusOk, kStatusOverflow);
@@ -245,25 +262,21 @@ __global__ void __launch_bounds__(kThreads) k_level(const LevelParams p) {
         }
         // stage this tile's output in shared memory at tile-local offsets ...
         int loc = excl;
-        if (final_level) {
 #pragma unroll
-            for (int i = 0; i < kItems; ++i) {
-                if (cnt[i]) {
-                    stage_i[loc] = pr[i].y;
-                    stage_f[loc] = make_float2(tin[i], tout[i]);
+        for (int i = 0; i < kIt; ++i) {
+            for (uint32_t h = hitr[i]; h; h &= h - 1u) {
+                const uint32_t c = (uint32_t)(__ffs(h) - 1) ^ oct[i];
+                const int32_t child = cb[i] + __popc(mask[i] & ((1u << c) - 1u));
+                if (final_level) {
+                    float a0 = 0.f, a1 = 0.f;
+                    slab_test(ray[i], cij[i] | pack_ijk(c & 1u, (c >> 1) & 1u, (c >> 2) & 1u), dc, a0, a1);
+                    stage_i[loc] = child;
+                    stage_f[loc] = make_float2(a0, a1);
                     stage_r[loc] = pr[i].x;
+                } else {
+                    stage_p[loc] = make_int2(pr[i].x, child);
                 }
-                loc += cnt[i];
-            }
-        } else {
-#pragma unroll
-            for (int i = 0; i < kItems; ++i) {
-                const uint32_t mask = aux[i] & 0xffu, oct = aux[i] >> 8;
-                // occupied children in front-to-back rank order (Subdivide)
-                for (uint32_t rm = rank_mask(mask, oct); rm; rm &= rm - 1u) {
-                    const uint32_t c = (uint32_t)(__ffs(rm) - 1) ^ oct;
-                    stage_p[loc++] = make_int2(pr[i].x, cb[i] + __popc(mask & ((1u << c) - 1u)));
-                }
+                ++loc;
             }
         }
         __syncthreads();
@@ -287,8 +300,9 @@ __global__ void __launch_bounds__(kThreads) k_level(const LevelParams p) {
 // ray_offsets[r] = first list position whose ray is >= r (binary search).
 __global__ void __launch_bounds__(kThreads) k_ray_offsets(const int32_t* __restrict__ out_ray,
                                                           const Counters* __restrict__ ctr, int D,
-                                                          long long R, int32_t* __restrict__ offs) {
-    const long long H = ctr->count[D + 1];
+                                                          long long R, long long cap,
+                                                          int32_t* __restrict__ offs) {
+    const long long H = min(ctr->count[D], cap);   // never past what was written
     for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r <= R;
          r += (long long)gridDim.x * blockDim.x) {
         long long lo = 0, hi = H;
@@ -316,7 +330,7 @@ int level_ctas_per_sm() {
 }
 
 long long max_tiles(long long R, long long cap) {
-    return (std::max(R, cap) + kTile - 1) / kTile + 1;
+    return (std::max(R, cap) + kTileX - 1) / kTileX + 1;
 }
 
 }  // namespace
@@ -373,7 +387,7 @@ extern "C" int svo_trace_rays(const nglod_svo* svo, const float* o, const float*
     NGLOD_CUDA(cudaMemsetAsync(ctr, 0, sizeof(Counters), st));
     k_prep_rays<<<std::min<long long>((R + kThreads - 1) / kThreads, (long long)sms * 16), kThreads, 0, st>>>(
         o, d, R, rays, ctr);
-    for (int dp = 0; dp <= D; ++dp) {
+    for (int dp = 0; dp < D; ++dp) {
         NGLOD_CUDA(cudaMemsetAsync(tile_state, 0, sizeof(unsigned long long) * ntiles_max, st));
         LevelParams lp;
         lp.rays = rays;
@@ -383,7 +397,7 @@ extern "C" int svo_trace_rays(const nglod_svo* svo, const float* o, const float*
         lp.out_cap = pair_capacity;
         lp.voxel_id = voxel_id;
         lp.t_range = (float2*)t_range;
-        lp.out_ray = (int32_t*)buf[(dp + 1) & 1];
+        lp.out_ray = (int32_t*)buf[(dp + 1) & 1];   // used when dp + 1 == D
         lp.hit_cap = std::min<long long>(hit_capacity, pair_capacity);
         lp.ctr = ctr;
         lp.tile_state = tile_state;
@@ -393,12 +407,12 @@ extern "C" int svo_trace_rays(const nglod_svo* svo, const float* o, const float*
         k_level<<<(unsigned)grid, kThreads, kStageBytes, st>>>(lp);
     }
     k_ray_offsets<<<std::min<long long>((R + kThreads) / kThreads, (long long)sms * 16), kThreads, 0, st>>>(
-        (const int32_t*)buf[(D + 1) & 1], ctr, D, R, ray_offsets);
+        (const int32_t*)buf[D & 1], ctr, D, R, std::min<long long>(hit_capacity, pair_capacity), ray_offsets);
     NGLOD_CUDA(cudaGetLastError());
     Counters h;
     NGLOD_CUDA(cudaMemcpyAsync(&h, ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
     NGLOD_CUDA(cudaStreamSynchronize(st));
-    const long long H = h.count[D + 1];
+    const long long H = h.count[D];
     if (h_stats) {
         h_stats[0] = h.status == kStatusOk || H > 0 ? H : 0;
         h_stats[1] = h.max_pairs;
@@ -407,7 +421,7 @@ extern "C" int svo_trace_rays(const nglod_svo* svo, const float* o, const float*
         return fail(NGLOD_ERR_TIMEOUT, "svo_trace_rays: scan look-back wait expired");
     if (h.status == kStatusOverflow) {
         long long need = 0;
-        for (int dp = 1; dp <= D; ++dp) need = std::max(need, h.count[dp]);
+        for (int dp = 1; dp < D; ++dp) need = std::max(need, h.count[dp]);
         if (h_stats) h_stats[1] = std::max<long long>(need, h.max_pairs);
         return fail(NGLOD_ERR_CAPACITY, "svo_trace_rays: list larger than capacity (pairs " +
                                             std::to_string(need) + ", hits " + std::to_string(H) + ")");

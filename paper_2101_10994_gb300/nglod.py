@@ -295,6 +295,7 @@ def sphere_trace(svo: SVO, feats: Features, dec: DecoderDev, o, d, lists: RayLis
                               lists.t_range.data_ptr(), out["work"].data_ptr(), out["work"].numel(),
                               out["t"].data_ptr(), out["hit"].data_ptr(), _ptr(out["steps"]),
                               _ptr(out["normal"]), C.c_void_p(_stream(stream))))
+    out["hit_voxel"] = out["work"][256:256 + 4 * R].view(torch.int32)
     return out
 
 

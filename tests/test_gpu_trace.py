@@ -1,8 +1,9 @@
 """sphere_trace on the GPU vs the FP64 oracle (Sec. 3.4, A.4).
 
 FP32 decode: identical hit masks, hit depth within 1e-3 scene units, and
-normals within 0.5 degrees of the oracle tracer's normal (both take the
-gradient in the voxel the list assigned the hit to).  BF16 decode (tensor cores): the oracle runs with the same
+normals within 0.5 degrees of the oracle's gradient at the GPU's own hit
+point, taken in the voxel the GPU's ray stopped in (the trilinear field's
+gradient jumps across voxel faces, so "the same x" includes the voxel).  BF16 decode (tensor cores): the oracle runs with the same
 bf16-rounded W1 z-columns; rounding z to bf16 changes the decoded distance by
 at most 2^-8 sum_h |W2_h| sum_k |W1_hk z_k|, which can move the stop test
 d < eps by one step of size ~eps on rays whose distance lands within that
@@ -47,18 +48,46 @@ def trace_both(ng, ora, oc, feats, fdt, dec, lod, o, d, eps, max_steps, decode, 
     return gs, ref
 
 
-def compare(ora, feats, dec, lod, o, d, gs, ref, eps, decode="f32", sel=None):
+def oracle_normal_in_voxel(ora, oc, feats, dec, lod, x, vox):
+    """Oracle gradient direction at x, inside the given target-depth voxel
+    (x is clamped into the voxel by 1e-4 of its size, so a hit on a face is
+    evaluated in the voxel the tracer stopped in)."""
+    D = lod + S.FIRST_FEATURE_DEPTH - 1
+    i, j, k = S.morton_decode(oc.keys[D][vox])
+    s = 2.0 / (1 << D)
+    lo = np.stack([-1 + i * s, -1 + j * s, -1 + k * s], axis=1)
+    def unit(xx):
+        _, _, g = ora.sdf_query(feats, dec, np.clip(xx, lo + 1e-4 * s, lo + s - 1e-4 * s).astype(np.float32),
+                                lod, grad=True)
+        return g / np.maximum(np.linalg.norm(g, axis=1, keepdims=True), 1e-300)
+    n0 = unit(x)
+    # a ReLU kink within 5e-5 of x makes the gradient ill-defined there; a
+    # point whose oracle direction moves by more than 0.2 degrees (under half
+    # the 0.5-degree tolerance) within that radius is reported as not stable
+    # instead of compared
+    stable = np.ones(len(x), bool)
+    for a in range(3):
+        for sgn in (-1.0, 1.0):
+            xs = x.copy()
+            xs[:, a] += sgn * 5e-5
+            stable &= np.degrees(np.arccos(np.clip((unit(xs) * n0).sum(1), -1, 1))) <= 0.2
+    return n0, stable
+
+
+def compare(ora, feats, dec, lod, o, d, gs, ref, eps, decode="f32", sel=None, oc=None):
     o = o if sel is None else o[sel]
     d = d if sel is None else d[sel]
     gh, rh = gs["hit"].astype(bool), ref["hit"].astype(bool)
     mismatch = int((gh != rh).sum())
     both = gh & rh
     dt = np.abs(gs["t"][both].astype(np.float64) - ref["t"][both])
-    # normals: both sides take the gradient in the voxel the list put the hit
-    # in (a hit on a voxel's entry face belongs to that voxel, not to its
-    # face neighbour), at hit points that agree to the depth tolerance
-    ang = np.degrees(np.arccos(np.clip((gs["normal"][both] * ref["normal"][both]).sum(1), -1, 1)))
+    # normals at the same x: the GPU's FP32 normal vs the oracle's gradient
+    # at the GPU's own hit point, in the voxel the GPU's ray stopped in
+    x = o[gh].astype(np.float64) + gs["t"][gh].astype(np.float64)[:, None] * d[gh].astype(np.float64)
+    nref, stable = oracle_normal_in_voxel(ora, oc, feats, dec, lod, x, gs["hit_voxel"][gh])
+    ang = np.degrees(np.arccos(np.clip((gs["normal"][gh][stable] * nref[stable]).sum(1), -1, 1)))
     return dict(mismatch=mismatch, both=int(both.sum()), dt=dt, ang=ang,
+                stable=float(stable.mean()) if stable.size else 1.0,
                 steps_eq=float((gs["steps"] == ref["steps"]).mean()))
 
 
@@ -73,10 +102,11 @@ def test_plain_sphere_f32(ng, oracle_mod, decoder):
         dec.b1 = np.random.default_rng(0).normal(0, 0.05, 128).astype(np.float32)
     o, d, _ = S.camera_rays(128, 128)
     gs, ref = trace_both(ng, ora, oc, feats, "f32", dec, 3, o, d, 1e-3, 32, "f32")
-    c = compare(ora, feats, dec, 3, o, d, gs, ref, 1e-3)
+    c = compare(ora, feats, dec, 3, o, d, gs, ref, 1e-3, oc=oc)
     assert c["mismatch"] <= 2 and c["both"] > 1500, (c["mismatch"], c["both"])
     assert np.mean(c["dt"] <= 1e-3) >= 0.999 and c["dt"].max() <= 1.5e-3, c["dt"].max()
     assert c["ang"].max() <= 0.5, c["ang"].max()
+    assert c["stable"] >= (0.99 if decoder == "readout" else 0.8), c["stable"]
     assert c["steps_eq"] >= 0.999
 
 
@@ -89,7 +119,7 @@ def test_csg64_lod5_1080p_sampled_f32(ng, oracle_mod):
     rng = np.random.default_rng(1)
     sel = rng.choice(len(o), 1500, replace=False)
     gs, ref = trace_both(ng, ora, oc, feats, "f32", dec, 5, o, d, 1e-3, 128, "f32", sample=sel)
-    c = compare(ora, feats, dec, 5, o, d, gs, ref, 1e-3, sel=sel)
+    c = compare(ora, feats, dec, 5, o, d, gs, ref, 1e-3, sel=sel, oc=oc)
     assert c["mismatch"] <= 1 and c["both"] > 300
     assert c["dt"].max() <= 1e-3, c["dt"].max()
     assert c["ang"].max() <= 0.5
@@ -103,7 +133,7 @@ def test_trace_options_f32(ng, oracle_mod):
     o, d, _ = S.camera_rays(96, 96, tile=8)
     for eps, ms, osc in ((1e-3, 1, False), (3e-4, 200, False), (1e-2, 64, True)):
         gs, ref = trace_both(ng, ora, oc, feats, "f16", dec, 3, o, d, eps, ms, "f32", osc=osc)
-        c = compare(ora, feats, dec, 3, o, d, gs, ref, eps)
+        c = compare(ora, feats, dec, 3, o, d, gs, ref, eps, oc=oc)
         assert c["mismatch"] <= 2, (eps, ms, osc)
         if c["both"]:
             assert np.mean(c["dt"] <= 1e-3) >= 0.999
@@ -124,12 +154,12 @@ def test_csg64_lod5_bf16(ng, oracle_mod, fdt):
     rng = np.random.default_rng(2)
     sel = rng.choice(len(o), 3000, replace=False)
     gs, ref = trace_both(ng, ora, oc, feats, fdt, dec, 5, o, d, 1e-3, 128, "bf16", sample=sel)
-    c = compare(ora, feats, dec, 5, o, d, gs, ref, 1e-3, sel=sel)
+    c = compare(ora, feats, dec, 5, o, d, gs, ref, 1e-3, sel=sel, oc=oc)
     assert c["both"] > 500
     assert c["mismatch"] <= 3, c["mismatch"]
     assert np.mean(c["dt"] <= 1e-3) >= 0.995, np.sort(c["dt"])[-10:]
     assert c["dt"].max() <= 1e-3 + 2e-4, c["dt"].max()
-    assert c["ang"].max() <= 0.5
+    assert c["ang"].max() <= 0.5, c["ang"].max()
 
 
 def test_bf16_query_within_rounding_bound(ng, oracle_mod):
