@@ -30,8 +30,11 @@ sys.path.insert(0, ROOT)
 
 METRIC = "sphere-traced rays/s and SDF queries/s at 1080p LOD5, bf16 vs fp32, % roofline"
 PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
-TRACE_SRC = [os.path.join(ROOT, "paper_2101_10994_gb300", "csrc", f) for f in
-             ("query.cu", "query_common.cuh", "trace_common.cuh", "trace_bf16.cu")]
+CSRC = os.path.join(ROOT, "paper_2101_10994_gb300", "csrc")
+KERNEL_SRC = {"k_level": ["traverse.cu", "nglod_internal.cuh"],
+              "k_trace_f32": ["query.cu", "query_common.cuh", "trace_common.cuh", "nglod_internal.cuh"],
+              "k_trace_bf16": ["trace_bf16.cu", "query_common.cuh", "trace_common.cuh", "tcgen05.cuh",
+                               "nglod_internal.cuh"]}
 
 
 def parse():
@@ -208,7 +211,9 @@ def run_ours(args, rank, world, local_rank):
             td.all_reduce(tmax, op=td.ReduceOp.MAX)
         ms_step = float(tmax.item()) / args.steps
         hits = int(out["hit"].sum().item())
-        results[mode] = dict(
+        lists = step(mode, out, wev)
+        sizes = lists.level_sizes()
+        results[mode] = dict(level_sizes=sizes,
             ms_per_step=ms_step, rays_per_s=world * R / (ms_step * 1e-3),
             queries_per_s=world * queries / args.steps / (sum(trace) / args.steps * 1e-3),
             ms_traverse=sum(trav) / args.steps, ms_trace=sum(trace) / args.steps,
@@ -254,42 +259,73 @@ def run_ours(args, rank, world, local_rank):
     return W, results, clock_info, e2e, modes
 
 
-def source_hash():
+def source_hash(kernel):
+    """Hash of the sources a kernel is built from (stale traffic is dropped)."""
     h = hashlib.sha256()
-    for f in TRACE_SRC:
-        if os.path.exists(f):
-            h.update(open(f, "rb").read())
+    for f in KERNEL_SRC[kernel]:
+        p = os.path.join(CSRC, f)
+        if os.path.exists(p):
+            h.update(open(p, "rb").read())
     return h.hexdigest()[:16]
 
 
-def roofline(W, res, mode):
-    """Dominant kernel = the sphere tracer (one launch per frame)."""
-    import numpy as np
-    peaks = {}
-    pp = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    if os.path.exists(pp):
-        peaks = json.load(open(pp))
+def profiled_traffic(kernel):
+    if os.path.exists(PROFILE_TRAFFIC):
+        ent = json.load(open(PROFILE_TRAFFIC)).get(kernel)
+        if ent and ent.get("source_hash") == source_hash(kernel):
+            return ent.get("dram_bytes_per_launch")
+    return None
+
+
+def traversal_bytes(W, sizes):
+    """Algorithmic bytes of one frame's level kernels (depths 0..D-1): each
+    level reads its pair list (8 B/pair; implicit at the root), the node
+    records of its depth (16 B/voxel) and the ray records (32 B/ray), and
+    writes the next list (8 B/pair) or, at the last level, the final entries
+    (voxel id 4 B + t range 8 B + ray 4 B)."""
+    oc = W["octree"]
+    R = sizes[0]
+    D = len(sizes) - 1
+    total = 0
+    for dp in range(D):
+        total += (8 * sizes[dp] if dp > 0 else 0) + 16 * oc.counts()[dp] + 32 * R
+        total += 16 * sizes[dp + 1] if dp + 1 == D else 8 * sizes[dp + 1]
+    return total, D
+
+
+def roofline(W, res, mode, peaks):
+    """Dominant kernel = k_level: the traversal's level kernel takes the
+    largest share of the frame (one launch per depth)."""
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    nbytes, launches = traversal_bytes(W, res["level_sizes"])
+    sec = res["ms_traverse"] * 1e-3
+    achieved = nbytes / sec / 1e9
+    return {"bound": "hbm", "kernel": "k_level", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+            "frac": achieved / hbm, "traffic": profiled_traffic("k_level"),
+            "bytes_per_launch": nbytes / launches, "launches_per_frame": launches,
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in peaks else "fallback",
+            "timing": "CUDA events around svo_trace_rays (level kernels + ray prep + offsets + H readback)"}
+
+
+def trace_roofline(W, res, mode, peaks):
+    """Secondary: the sphere tracer's decode against its own unit."""
     interp, layer1, outl = flops_per_query(W["dec"].in_dim, W["lod"], mode)
     q = res["queries_per_frame"]
     sec = res["ms_trace"] * 1e-3
-    traffic = None
-    if os.path.exists(PROFILE_TRAFFIC):
-        tj = json.load(open(PROFILE_TRAFFIC))
-        ent = tj.get(f"trace_{mode}")
-        if ent and ent.get("source_hash") == source_hash():
-            traffic = ent.get("dram_bytes_per_launch")
+    kern = "k_trace_bf16" if mode == "bf16" else "k_trace_f32"
     if mode == "bf16":
         tf = peaks.get("bf16_tflops", 1900.0)
         achieved = q * layer1 / sec / 1e12
-        return {"bound": "tensor", "achieved": achieved, "peak": tf, "unit": "TFLOP/s",
-                "frac": achieved / tf, "traffic": traffic,
-                "peak_source": "MEASURED_PEAKS.json bf16_tflops (of measured)" if peaks else "fallback"}
+        return {"bound": "tensor", "kernel": kern, "achieved": achieved, "peak": tf, "unit": "TFLOP/s",
+                "frac": achieved / tf, "traffic": profiled_traffic(kern),
+                "gather_bytes_per_query": 8 * 32 * 4 * W["lod"],
+                "gather_GBps": q * 8 * 32 * 4 * W["lod"] / sec / 1e9}
     sm_mhz = peaks.get("sm_max_mhz", 2070.0)
     peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
     achieved = q * (interp + layer1 + outl) / sec / 1e12
-    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": traffic,
-            "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x sm_max_mhz (MEASURED_PEAKS.json)"}
+    return {"bound": "alu", "kernel": kern, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": profiled_traffic(kern),
+            "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x sm_max_mhz"}
 
 
 # ----------------------------------------------------------------------------
@@ -361,6 +397,10 @@ def main():
         td.init_process_group("nccl")
     W, res, clocks, e2e, modes = run_ours(args, rank, world, local_rank)
     if rank == 0:
+        peaks = {}
+        pp = os.path.join(ROOT, "MEASURED_PEAKS.json")
+        if os.path.exists(pp):
+            peaks = json.load(open(pp))
         head = "bf16" if "bf16" in res else "f32"
         r = res[head]
         line = {
@@ -374,7 +414,8 @@ def main():
                        "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world}"},
             "queries_per_s": r["queries_per_s"],
             "modes": res,
-            "roofline": roofline(W, r, head),
+            "roofline": roofline(W, r, head, peaks),
+            "trace_roofline": trace_roofline(W, r, head, peaks),
             "clocks": clocks,
             "e2e": e2e,
             "gpu_launches": args.steps * len(modes) * (W["lod"] + 7),   # prep + (lod+3) levels + offsets + trace + normals

@@ -179,6 +179,13 @@ int svo_trace_rays_noalloc(const nglod_svo* svo, const float* o, const float* d,
                            float* t_range, int64_t hit_capacity, int64_t* h_stats,
                            void* stream);
 
+/* svo_trace_rays_sizes -- list sizes of the last svo_trace_rays that used this
+ * workspace (synchronises the stream): h_sizes[dp] for dp = 0..n-1 is the
+ * number of ray/voxel pairs at depth dp that Decide kept (dp = 0: rays whose
+ * ray hits the root is not yet tested, i.e. R), the last entry being the
+ * final hit count.  n <= 12. */
+int svo_trace_rays_sizes(const void* work, int64_t* h_sizes, int n, void* stream);
+
 /* sdf_query -- Sec. 3.2 and Eq. 2: for each point x, the voxels containing it
  * at depths 3..lod+2 (found from the root through the child masks using
  * q = fl32(x + 1), ijk = clamp(floor(q 2^(dp-1)), 0, 2^dp - 1)); per level the

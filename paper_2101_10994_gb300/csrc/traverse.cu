@@ -30,7 +30,6 @@ constexpr long kSpinLimit = 1l << 22;   // ~0.1-1 s of waiting, then time out
 struct Counters {
     long long count[kMaxDepth + 2];   // list length entering each depth
     long long max_pairs;
-    int tile_ctr[kMaxDepth + 2];
     int status;                        // kStatus*
 };
 
@@ -45,60 +44,8 @@ struct LevelParams {
     int32_t* out_ray;
     long long hit_cap;
     Counters* ctr;
-    unsigned long long* tile_state;
     int dp, D;
 };
-
-__device__ __forceinline__ void st_release(unsigned long long* p, unsigned long long v) {
-    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
-__device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long* p) {
-    unsigned long long v;
-    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
-}
-
-// Exclusive prefix of this tile among all tiles (decoupled look-back),
-// computed by one whole warp: each poll reads the published states of the 32
-// nearest unvisited predecessors at once, sums the aggregates up to the
-// nearest one that already carries its inclusive prefix, and moves the
-// window back only when none does.  Every wait is bounded; on expiry the
-// status word records a timeout and the (then meaningless) partial prefix is
-// returned.
-__device__ long long tile_prefix_warp(unsigned long long* state, long long tile, long long agg, int* status) {
-    const int lane = threadIdx.x & 31;
-    if (tile == 0) {
-        if (lane == 0) st_release(state, kFlagPre | (unsigned long long)agg);
-        return 0;
-    }
-    if (lane == 0) st_release(state + tile, kFlagAgg | (unsigned long long)agg);
-    long long excl = 0;
-    long long end = tile - 1;          // nearest predecessor not yet summed
-    long spins = 0;
-    for (;;) {
-        const long long j = end - lane;
-        const unsigned long long s = j >= 0 ? ld_acquire(state + j) : kFlagPre;
-        const unsigned long long flag = s & ~kValMask;
-        if (__any_sync(0xffffffffu, flag == 0ull)) {
-            if (++spins > kSpinLimit) {
-                if (lane == 0) atomicExch(status, kStatusTimeout);
-                break;
-            }
-            if (spins > 16) __nanosleep(32);
-            continue;
-        }
-        const unsigned pre = __ballot_sync(0xffffffffu, flag == kFlagPre);
-        const int stop = pre ? __ffs(pre) - 1 : 31;
-        long long v = lane <= stop ? (long long)(s & kValMask) : 0;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        excl += v;
-        if (pre) break;
-        end -= 32;
-    }
-    if (lane == 0) st_release(state + tile, kFlagPre | (unsigned long long)(excl + agg));
-    return excl;
-}
 
 __device__ __forceinline__ int block_exclusive_sum(int v, int* warp_sums, int& total) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -159,20 +106,60 @@ __global__ void __launch_bounds__(kThreads) k_prep_rays(const float* __restrict_
 
 // One level of the traversal, with Decide of the next level fused into
 // Subdivide.  Input: the pairs (ray, voxel) of depth dp that Decide kept (at
-// dp = 0 the implicit pairs (ray, root), which are decided here first).  For
-// each input pair the thread tests the voxel's occupied children (their
-// bounds follow from the parent's coordinates, no load needed), counts the
-// hit ones (Decide of depth dp + 1), the CTA scans the counts
-// (ExclusiveSum) and obtains its tile's global offset by decoupled
-// look-back, and the hit children are written in front-to-back rank order
-// (Subdivide).  When depth dp + 1 is the target depth the written list is
-// the final one (Compactify): voxel ids, their (t_enter, t_exit) and the ray
-// of each entry.  Output order and contents equal those of the unfused
-// Decide / ExclusiveSum / Subdivide / Compactify sequence.
+// dp = 0 the implicit pairs (ray, root), decided here first).  For each input
+// pair a thread tests the voxel's occupied children (their bounds follow
+// from the parent's coordinates, no load needed) and records which ones the
+// ray hits (Decide of depth dp + 1).  The exclusive sum of the hit counts
+// gives every pair its output position, and the hit children are written in
+// front-to-back rank order (Subdivide); when depth dp + 1 is the target
+// depth the written list is the final one (Compactify): voxel ids, their
+// (t_enter, t_exit) and the ray of each entry.  Output order and contents
+// equal those of the unfused Decide / ExclusiveSum / Subdivide / Compactify
+// sequence.
+//
+// Scan structure: the launch is cooperative (every CTA resident) and each
+// CTA owns one contiguous chunk of the input list.
+//   pass 1  decide the chunk, store a 16-bit record per pair (hit children
+//           by rank | octant << 8) and the chunk's hit count;
+//   barrier one bounded grid-wide barrier; each CTA then sums the counts of
+//           the chunks before it (the ExclusiveSum at chunk granularity);
+//   pass 2  re-read the chunk (now L2-resident), scan inside each tile and
+//           write the children at their final positions through shared
+//           memory, coalesced.
+// No CTA ever waits on another except at the single barrier.
 constexpr int kTileX = kThreads * 2;                 // parents per tile (2 per thread)
 constexpr int kStageBytes = kTileX * 8 * 16;         // up to 8 children x 16 B per parent
 
-__global__ void __launch_bounds__(kThreads) k_level(const LevelParams p) {
+struct LevelScratch {
+    uint16_t* rec;          // [input pairs] hit-by-rank | octant << 8
+    long long* chunk_cnt;   // [grid]
+    unsigned* arrive;       // grid barrier counter (zeroed per level)
+};
+
+__device__ __forceinline__ bool grid_barrier(unsigned* arrive, unsigned nblocks, int* status) {
+    __syncthreads();
+    bool ok = true;
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(arrive, 1u);
+        long spins = 0;
+        for (;;) {
+            unsigned v;
+            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(arrive) : "memory");
+            if (v >= nblocks) break;
+            if (++spins > kSpinLimit) {
+                atomicExch(status, kStatusTimeout);
+                ok = false;
+                break;
+            }
+            if (spins > 32) __nanosleep(64);
+        }
+    }
+    __syncthreads();
+    return ok;
+}
+
+__global__ void __launch_bounds__(kThreads) k_level(const LevelParams p, const LevelScratch x) {
     constexpr int kIt = kTileX / kThreads;
     extern __shared__ __align__(16) unsigned char stage[];
     int2* stage_p = reinterpret_cast<int2*>(stage);
@@ -180,108 +167,124 @@ __global__ void __launch_bounds__(kThreads) k_level(const LevelParams p) {
     float2* stage_f = reinterpret_cast<float2*>(stage + kTileX * 8 * sizeof(int32_t));
     int32_t* stage_r = reinterpret_cast<int32_t*>(stage + kTileX * 8 * (sizeof(int32_t) + sizeof(float2)));
     __shared__ int warp_sums[kThreads / 32 + 1];
-    __shared__ long long s_tile;
     __shared__ long long s_prefix;
-    if (p.ctr->status != kStatusOk) return;
-    const long long n = p.ctr->count[p.dp];
+    const bool skip = p.ctr->status != kStatusOk;     // uniform: earlier level failed
+    const long long n = skip ? 0 : p.ctr->count[p.dp];
     const long long ntiles = (n + kTileX - 1) / kTileX;
+    const long long per = (ntiles + gridDim.x - 1) / gridDim.x;
+    const long long t_begin = min((long long)blockIdx.x * per, ntiles);
+    const long long t_end = min(t_begin + per, ntiles);
     const int dc = p.dp + 1;                          // depth of the children
     const bool final_level = dc == p.D;
-    for (;;) {
-        if (threadIdx.x == 0) s_tile = atomicAdd(&p.ctr->tile_ctr[p.dp], 1);
-        __syncthreads();
-        const long long tile = s_tile;
-        if (tile >= ntiles) break;
+
+    // ---- pass 1: Decide the children of every pair of the chunk ----
+    long long mine = 0;
+    for (long long tile = t_begin; tile < t_end; ++tile) {
         const long long base = tile * kTileX + (long long)threadIdx.x * kIt;
-        int2 pr[kIt];
-        RayPrep ray[kIt];
-        uint32_t cij[kIt];       // coordinates of child slot 0 (parent coords << 1)
-        uint32_t mask[kIt];      // occupied children (slot bits)
-        uint32_t hitr[kIt];      // hit children, by front-to-back rank
-        uint32_t oct[kIt];
-        int32_t cb[kIt];
-        int sum = 0;
-        if (p.dp > 0 && base + kIt <= n) {
-            const int4 a = *reinterpret_cast<const int4*>(p.in + base);
-            pr[0] = make_int2(a.x, a.y);
-            pr[1] = make_int2(a.z, a.w);
-        } else {
-#pragma unroll
-            for (int i = 0; i < kIt; ++i) {
-                const long long idx = base + i;
-                pr[i] = idx < n ? (p.dp == 0 ? make_int2((int)idx, 0) : p.in[idx]) : make_int2(-1, -1);
-            }
-        }
 #pragma unroll
         for (int i = 0; i < kIt; ++i) {
-            hitr[i] = 0;
-            mask[i] = 0;
-            oct[i] = 0;
-            cb[i] = 0;
-            cij[i] = 0;
-            if (pr[i].x < 0) continue;
-            ray[i] = p.rays[pr[i].x];
-            const Node nd = p.node[pr[i].y];
-            uint32_t o8;
+            const long long idx = base + i;
+            if (idx >= n) continue;
+            const int2 pr = p.dp == 0 ? make_int2((int)idx, 0) : p.in[idx];
+            const RayPrep ray = p.rays[pr.x];
+            const Node nd = p.node[pr.y];
+            uint32_t o8, h = 0;
+            bool live = true;
             if (p.dp == 0) {
-                // the root is the only undecided input; every other pair was kept by Decide
-                float t0, t1;
-                if (!ray[i].valid || !slab_test(ray[i], nd.ijk, 0, t0, t1, &o8)) continue;
+                float t0, t1;   // the root is the only undecided input
+                live = ray.valid && slab_test(ray, nd.ijk, 0, t0, t1, &o8);
             } else {
-                o8 = origin_octant(ray[i], nd.ijk, p.dp);
+                o8 = origin_octant(ray, nd.ijk, p.dp);
             }
-            mask[i] = nd.childmask;
-            oct[i] = o8;
-            cb[i] = nd.childbase;
-            cij[i] = (nd.ijk << 1) & 0x3ffffffeu;
-            uint32_t h = 0;
-            for (uint32_t rm = rank_mask(nd.childmask, o8); rm; rm &= rm - 1u) {
-                const uint32_t r = (uint32_t)(__ffs(rm) - 1);
-                const uint32_t c = r ^ o8;
-                const uint32_t ijk = cij[i] | pack_ijk(c & 1u, (c >> 1) & 1u, (c >> 2) & 1u);
-                float a0, a1;
-                if (slab_test(ray[i], ijk, dc, a0, a1)) h |= 1u << r;
-            }
-            hitr[i] = h;
-            sum += __popc(h);
-        }
-        int tile_total;
-        const int excl = block_exclusive_sum(sum, warp_sums, tile_total);
-        if (threadIdx.x < 32) {
-            const long long pre = tile_prefix_warp(p.tile_state, tile, tile_total, &p.ctr->status);
-            if (threadIdx.x == 0) {
-                s_prefix = pre;
-                if (tile == ntiles - 1) {
-                    const long long total = pre + tile_total;
-                    p.ctr->count[dc] = total;
-                    if (total > p.ctr->max_pairs) p.ctr->max_pairs = total;
-                    if (total > (final_level ? p.hit_cap : p.out_cap))
-                        atomicCAS(&p.ctr->status, kStatusOk, kStatusOverflow);
+            if (live) {
+                const uint32_t cij = (nd.ijk << 1) & 0x3ffffffeu;
+                for (uint32_t rm = rank_mask(nd.childmask, o8); rm; rm &= rm - 1u) {
+                    const uint32_t r = (uint32_t)(__ffs(rm) - 1);
+                    const uint32_t c = r ^ o8;
+                    float a0, a1;
+                    if (slab_test(ray, cij | pack_ijk(c & 1u, (c >> 1) & 1u, (c >> 2) & 1u), dc, a0, a1))
+                        h |= 1u << r;
                 }
             }
+            x.rec[idx] = (uint16_t)(h | (live ? (o8 << 8) : 0u));
+            mine += __popc(h);
         }
-        // stage this tile's output in shared memory at tile-local offsets ...
-        int loc = excl;
+    }
+    // chunk total -> scan of chunk totals (one bounded grid barrier)
+    {
+        int total;
+        block_exclusive_sum((int)mine, warp_sums, total);
+        if (threadIdx.x == 0) {
+            asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(x.chunk_cnt + blockIdx.x),
+                         "l"((unsigned long long)total)
+                         : "memory");
+        }
+    }
+    if (!grid_barrier(x.arrive, gridDim.x, &p.ctr->status)) return;
+    if (threadIdx.x < 32) {
+        long long acc = 0;
+        for (unsigned b = threadIdx.x; b < blockIdx.x; b += 32) {
+            unsigned long long v;
+            asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(x.chunk_cnt + b) : "memory");
+            acc += (long long)v;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (threadIdx.x == 0) {
+            s_prefix = acc;
+            if (blockIdx.x == gridDim.x - 1 && !skip) {
+                unsigned long long mine_tot;
+                asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(mine_tot) : "l"(x.chunk_cnt + blockIdx.x) : "memory");
+                const long long total = acc + (long long)mine_tot;
+                p.ctr->count[dc] = total;
+                if (total > p.ctr->max_pairs) p.ctr->max_pairs = total;
+                if (total > (final_level ? p.hit_cap : p.out_cap))
+                    atomicCAS(&p.ctr->status, kStatusOk, kStatusOverflow);
+            }
+        }
+    }
+    __syncthreads();
+    long long off = s_prefix;
+
+    // ---- pass 2: positions inside each tile, then Subdivide / Compactify ----
+    for (long long tile = t_begin; tile < t_end; ++tile) {
+        const long long base = tile * kTileX + (long long)threadIdx.x * kIt;
+        uint32_t rec[kIt];
+        int cnt = 0;
 #pragma unroll
         for (int i = 0; i < kIt; ++i) {
-            for (uint32_t h = hitr[i]; h; h &= h - 1u) {
-                const uint32_t c = (uint32_t)(__ffs(h) - 1) ^ oct[i];
-                const int32_t child = cb[i] + __popc(mask[i] & ((1u << c) - 1u));
+            rec[i] = base + i < n ? x.rec[base + i] : 0u;
+            cnt += __popc(rec[i] & 0xffu);
+        }
+        int tile_total;
+        int loc = block_exclusive_sum(cnt, warp_sums, tile_total);
+#pragma unroll
+        for (int i = 0; i < kIt; ++i) {
+            const uint32_t h0 = rec[i] & 0xffu;
+            if (!h0) continue;
+            const long long idx = base + i;
+            const int2 pr = p.dp == 0 ? make_int2((int)idx, 0) : p.in[idx];
+            const Node nd = p.node[pr.y];
+            const uint32_t o8 = rec[i] >> 8;
+            const uint32_t cij = (nd.ijk << 1) & 0x3ffffffeu;
+            RayPrep ray;
+            if (final_level) ray = p.rays[pr.x];
+            for (uint32_t h = h0; h; h &= h - 1u) {
+                const uint32_t c = (uint32_t)(__ffs(h) - 1) ^ o8;
+                const int32_t child = nd.childbase + __popc(nd.childmask & ((1u << c) - 1u));
                 if (final_level) {
                     float a0 = 0.f, a1 = 0.f;
-                    slab_test(ray[i], cij[i] | pack_ijk(c & 1u, (c >> 1) & 1u, (c >> 2) & 1u), dc, a0, a1);
+                    slab_test(ray, cij | pack_ijk(c & 1u, (c >> 1) & 1u, (c >> 2) & 1u), dc, a0, a1);
                     stage_i[loc] = child;
                     stage_f[loc] = make_float2(a0, a1);
-                    stage_r[loc] = pr[i].x;
+                    stage_r[loc] = pr.x;
                 } else {
-                    stage_p[loc] = make_int2(pr[i].x, child);
+                    stage_p[loc] = make_int2(pr.x, child);
                 }
                 ++loc;
             }
         }
         __syncthreads();
-        // ... then write it to its global position with coalesced stores
-        const long long off = s_prefix;
         if (final_level) {
             const long long lim = min((long long)tile_total, p.hit_cap - off);
             for (int i = threadIdx.x; i < lim; i += kThreads) {
@@ -293,7 +296,8 @@ __global__ void __launch_bounds__(kThreads) k_level(const LevelParams p) {
             const long long lim = min((long long)tile_total, p.out_cap - off);
             for (int i = threadIdx.x; i < lim; i += kThreads) p.out[off + i] = stage_p[i];
         }
-        __syncthreads();   // s_tile / s_prefix / warp_sums / staging reuse
+        off += tile_total;
+        __syncthreads();   // staging and warp_sums reuse
     }
 }
 
@@ -316,6 +320,8 @@ __global__ void __launch_bounds__(kThreads) k_ray_offsets(const int32_t* __restr
 
 size_t align_up(size_t v, size_t a = 256) { return (v + a - 1) / a * a; }
 
+constexpr int kMaxGrid = 4096;   // chunk-count slots (>= resident CTAs of the level kernel)
+
 // Resident CTAs per SM of the level kernel with its staging buffer (the
 // persistent grid is sized to exactly what fits).
 int level_ctas_per_sm() {
@@ -329,9 +335,6 @@ int level_ctas_per_sm() {
     return cached;
 }
 
-long long max_tiles(long long R, long long cap) {
-    return (std::max(R, cap) + kTileX - 1) / kTileX + 1;
-}
 
 }  // namespace
 }  // namespace nglod
@@ -340,9 +343,11 @@ using namespace nglod;
 
 extern "C" size_t svo_trace_rays_workspace(int64_t R, int64_t pair_capacity) {
     if (R < 0 || pair_capacity < 0) return 0;
+    const size_t n_in = (size_t)std::max<int64_t>(R, pair_capacity);
     return align_up(sizeof(Counters)) + align_up(sizeof(RayPrep) * (size_t)R) +
            2 * align_up(sizeof(int2) * (size_t)pair_capacity) +
-           align_up(sizeof(unsigned long long) * (size_t)max_tiles(R, pair_capacity));
+           align_up(sizeof(unsigned long long) * kMaxGrid) + align_up(sizeof(unsigned) * (kMaxDepth + 2)) +
+           align_up(sizeof(uint16_t) * n_in);
 }
 
 extern "C" int svo_trace_rays(const nglod_svo* svo, const float* o, const float* d, int64_t R,
@@ -380,15 +385,19 @@ extern "C" int svo_trace_rays(const nglod_svo* svo, const float* o, const float*
     w += align_up(sizeof(int2) * (size_t)pair_capacity);
     buf[1] = (int2*)w;
     w += align_up(sizeof(int2) * (size_t)pair_capacity);
-    unsigned long long* tile_state = (unsigned long long*)w;
-    const long long ntiles_max = max_tiles(R, pair_capacity);
+    long long* chunk_cnt = (long long*)w;
+    w += align_up(sizeof(unsigned long long) * kMaxGrid);
+    unsigned* arrive = (unsigned*)w;
+    w += align_up(sizeof(unsigned) * (kMaxDepth + 2));
+    uint16_t* rec = (uint16_t*)w;
 
     const int sms = svo->num_sms;
+    const int grid = std::min(sms * level_ctas_per_sm(), kMaxGrid);
     NGLOD_CUDA(cudaMemsetAsync(ctr, 0, sizeof(Counters), st));
+    NGLOD_CUDA(cudaMemsetAsync(arrive, 0, sizeof(unsigned) * (kMaxDepth + 2), st));
     k_prep_rays<<<std::min<long long>((R + kThreads - 1) / kThreads, (long long)sms * 16), kThreads, 0, st>>>(
         o, d, R, rays, ctr);
     for (int dp = 0; dp < D; ++dp) {
-        NGLOD_CUDA(cudaMemsetAsync(tile_state, 0, sizeof(unsigned long long) * ntiles_max, st));
         LevelParams lp;
         lp.rays = rays;
         lp.node = svo->node[dp];
@@ -400,11 +409,15 @@ extern "C" int svo_trace_rays(const nglod_svo* svo, const float* o, const float*
         lp.out_ray = (int32_t*)buf[(dp + 1) & 1];   // used when dp + 1 == D
         lp.hit_cap = std::min<long long>(hit_capacity, pair_capacity);
         lp.ctr = ctr;
-        lp.tile_state = tile_state;
         lp.dp = dp;
         lp.D = D;
-        const long long grid = std::min<long long>(ntiles_max, (long long)sms * level_ctas_per_sm());
-        k_level<<<(unsigned)grid, kThreads, kStageBytes, st>>>(lp);
+        LevelScratch xs;
+        xs.rec = rec;
+        xs.chunk_cnt = chunk_cnt;
+        xs.arrive = arrive + dp;
+        void* args[] = {(void*)&lp, (void*)&xs};
+        NGLOD_CUDA(cudaLaunchCooperativeKernel((const void*)k_level, dim3(grid), dim3(kThreads), args,
+                                               (size_t)kStageBytes, st));
     }
     k_ray_offsets<<<std::min<long long>((R + kThreads) / kThreads, (long long)sms * 16), kThreads, 0, st>>>(
         (const int32_t*)buf[D & 1], ctr, D, R, std::min<long long>(hit_capacity, pair_capacity), ray_offsets);
@@ -426,6 +439,17 @@ extern "C" int svo_trace_rays(const nglod_svo* svo, const float* o, const float*
         return fail(NGLOD_ERR_CAPACITY, "svo_trace_rays: list larger than capacity (pairs " +
                                             std::to_string(need) + ", hits " + std::to_string(H) + ")");
     }
+    return NGLOD_OK;
+}
+
+extern "C" int svo_trace_rays_sizes(const void* work, int64_t* h_sizes, int n, void* stream) {
+    using namespace nglod;
+    if (!work || !h_sizes || n < 1 || n > kMaxDepth + 2)
+        return fail(NGLOD_ERR_INVALID_ARG, "svo_trace_rays_sizes: bad arguments");
+    Counters h;
+    NGLOD_CUDA(cudaMemcpyAsync(&h, work, sizeof(Counters), cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+    NGLOD_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    for (int i = 0; i < n; ++i) h_sizes[i] = h.count[i];
     return NGLOD_OK;
 }
 

@@ -23,7 +23,8 @@ FIRST_FEATURE_DEPTH = 3
 
 EXPORTS = ["nglod_last_error", "svo_build", "svo_info", "svo_device_arrays", "svo_read_arrays", "svo_free",
            "svo_trace_rays_workspace", "svo_trace_rays", "sdf_query", "sphere_trace_workspace",
-           "sphere_trace", "sphere_trace_status", "trace_normals", "svo_trace_rays_noalloc"]
+           "sphere_trace", "sphere_trace_status", "trace_normals", "svo_trace_rays_noalloc",
+           "svo_trace_rays_sizes"]
 
 
 class NglodError(RuntimeError):
@@ -74,6 +75,7 @@ def lib():
         L.sphere_trace.argtypes = [P, P, P, P, P, i64, i32, P, P, P, P, P, sz, P, P, P, P, P]
         L.trace_normals.argtypes = [P, P, P, P, P, i64, i32, P, sz, P, P, P, P]
         L.sphere_trace_status.argtypes = [P, P]
+        L.svo_trace_rays_sizes.argtypes = [P, P, i32, P]
         L.svo_trace_rays_noalloc.argtypes = [P, P, P, i64, i32, P, P, P, i64, P, P]
         _lib = L
     return _lib
@@ -213,6 +215,14 @@ class RayLists:
     t_range: object          # float32 [H, 2]
     max_pairs: int
     lod: int
+    work: object = None      # the workspace the lists were built in
+
+    def level_sizes(self, stream=None):
+        """Pairs kept by Decide at each depth 0..target (entry 0 = R)."""
+        D = self.lod + FIRST_FEATURE_DEPTH - 1
+        out = (C.c_int64 * (D + 1))()
+        _check(lib().svo_trace_rays_sizes(self.work.data_ptr(), out, D + 1, C.c_void_p(_stream(stream))))
+        return [int(v) for v in out]
 
 
 def svo_trace_rays(svo: SVO, o, d, lod: int, stream=None, pair_capacity: int | None = None,
@@ -249,7 +259,7 @@ def svo_trace_rays(svo: SVO, o, d, lod: int, stream=None, pair_capacity: int | N
         _check(rc)
         svo._cap[key] = cap
         H = int(stats[0])
-        return RayLists(offs, vid[:H], tr[:H], int(stats[1]), lod)
+        return RayLists(offs, vid[:H], tr[:H], int(stats[1]), lod, work)
     raise NglodError(ERR_CAPACITY, "svo_trace_rays: capacity growth did not converge")
 
 
