@@ -224,7 +224,9 @@ size_t sphere_trace_workspace(int64_t R);
  *   work                device workspace >= sphere_trace_workspace(R).  After
  *                       the call, bytes [256, 256 + 4R) hold the int32 id (at
  *                       the target depth) of the voxel each hit ray stopped in,
- *                       -1 for misses; trace_normals reads them.
+ *                       -1 for misses, and int32 word 2 counts the hit rays,
+ *                       whose ids follow (in no particular order) from byte
+ *                       256 + 4R rounded up to 256; trace_normals reads them.
  * Outputs: t_hit [R] (+inf on miss), hit [R] uint8, steps [R] int32
  * (nullable: decodes taken), normal [R, 3] (nullable; normalised analytic
  * gradient of the decoded SDF at the hit point in FP32, zero on miss).

@@ -136,6 +136,68 @@ __device__ __forceinline__ uint32_t origin_octant(const RayPrep& r, uint32_t ijk
     return (r.ox >= cx ? 1u : 0u) | (r.oy >= cy ? 2u : 0u) | (r.oz >= cz ? 4u : 0u);
 }
 
+// Slab tests of all 8 children of voxel (i,j,k) at depth dp at once.  A
+// child's bounds along axis a are (lo, mid) or (mid, hi) with lo, mid, hi the
+// parent's low face, centre and high face -- the very values slab_test
+// computes for the child (lo = fma(2i, 2^-dp, -1) = parent lo, hi = lo +
+// 2^-dp), so each crossing t = (plane - o) * inv is computed once per plane
+// and the results equal eight separate slab_test calls bit for bit.
+// Returns the hit mask by child slot; tin/tout[c] hold the hit intervals.
+struct ChildSlabs {
+    float tn[3][2], tf[3][2];   // per axis, per side (0 low child, 1 high child)
+    bool in[3][2];              // parallel axes: origin inside that side's slab
+};
+
+__device__ __forceinline__ void child_slabs(const RayPrep& r, uint32_t ijk, int dp, ChildSlabs& cs) {
+    const float s = pow2f(1 - dp);
+    const float hs = pow2f(-dp);
+    const float o[3] = {r.ox, r.oy, r.oz};
+    const float inv[3] = {r.ix, r.iy, r.iz};
+    const uint32_t c[3] = {unpack_i(ijk), unpack_j(ijk), unpack_k(ijk)};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float lo = __fmaf_rn((float)c[a], s, -1.0f);
+        const float mid = __fadd_rn(lo, hs);
+        const float hi = __fadd_rn(mid, hs);
+        if ((r.par >> a) & 1) {
+            cs.in[a][0] = lo <= o[a] && o[a] <= mid;
+            cs.in[a][1] = mid <= o[a] && o[a] <= hi;
+            cs.tn[a][0] = cs.tn[a][1] = -INFINITY;
+            cs.tf[a][0] = cs.tf[a][1] = INFINITY;
+            continue;
+        }
+        cs.in[a][0] = cs.in[a][1] = true;
+        const float t_lo = __fmul_rn(__fsub_rn(lo, o[a]), inv[a]);
+        const float t_mid = __fmul_rn(__fsub_rn(mid, o[a]), inv[a]);
+        const float t_hi = __fmul_rn(__fsub_rn(hi, o[a]), inv[a]);
+        cs.tn[a][0] = t_lo < t_mid ? t_lo : t_mid;
+        cs.tf[a][0] = t_lo < t_mid ? t_mid : t_lo;
+        cs.tn[a][1] = t_mid < t_hi ? t_mid : t_hi;
+        cs.tf[a][1] = t_mid < t_hi ? t_hi : t_mid;
+    }
+}
+
+// Hit test of child slot c from its per-axis intervals (same max / min and
+// closed-interval rule as slab_test).
+__device__ __forceinline__ bool child_hit(const ChildSlabs& cs, uint32_t c, float& tin, float& tout) {
+    const bool x = c & 1u, y = (c >> 1) & 1u, z = (c >> 2) & 1u;
+    if (!((x ? cs.in[0][1] : cs.in[0][0]) && (y ? cs.in[1][1] : cs.in[1][0]) && (z ? cs.in[2][1] : cs.in[2][0])))
+        return false;
+    float tn = x ? cs.tn[0][1] : cs.tn[0][0];
+    float tf = x ? cs.tf[0][1] : cs.tf[0][0];
+    const float tn1 = y ? cs.tn[1][1] : cs.tn[1][0], tf1 = y ? cs.tf[1][1] : cs.tf[1][0];
+    const float tn2 = z ? cs.tn[2][1] : cs.tn[2][0], tf2 = z ? cs.tf[2][1] : cs.tf[2][0];
+    if (tn1 > tn) tn = tn1;
+    if (tf1 < tf) tf = tf1;
+    if (tn2 > tn) tn = tn2;
+    if (tf2 < tf) tf = tf2;
+    const float te = tn > 0.0f ? tn : 0.0f;
+    if (!(te <= tf)) return false;
+    tin = te;
+    tout = tf;
+    return true;
+}
+
 // Child-slot mask re-indexed by front-to-back rank: bit r is set iff slot
 // r ^ oct is occupied (an XOR permutation of the 8 bits, by conditional swaps
 // of adjacent bits, bit pairs and nibbles).

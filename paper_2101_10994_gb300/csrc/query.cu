@@ -112,177 +112,199 @@ __global__ void __launch_bounds__(kThreads) k_sdf_query(const DecPtrs dp, const 
 
 // ---------------------------------------------------------------------------
 // Analytic gradient d sdf / dx (FP32): sdf_query(grad) and trace normals.
-// One group of 8 lanes per item; decoder weights staged in shared memory
-// (W1 transposed, [in][128]) so lane l reads hidden units 32i + 4l + j.
+//
+// d sdf/dx = W1x^T g + J^T W1z^T g with g_h = W2_h [pre_h > 0] and J = dz/dx
+// (chain rule through Eq. 2 and the trilinear weights of Sec. 3.2).  Per warp
+// of 32 items: (A) 8-lane groups gather z into shared memory; (B) each lane
+// runs its item's forward pass and accumulates v = sum_h g_h W1[h] in the
+// same loop over hidden units (each W1 row read once as broadcast 16-byte
+// loads); (C) groups apply the trilinear derivative weights to v's z part,
+// corner by corner, and reduce.  The trace normals run over the compact list
+// of hit rays the tracer recorded.
 // ---------------------------------------------------------------------------
 struct GradArgs {
     const float* x;        // mode 0: [Q, 3] points
     const float* o;        // mode 1: rays
     const float* d;
     const float* t_hit;
-    const uint8_t* hit;
     const int32_t* hit_vox;
-    long long n;
+    const int* hit_count;  // mode 1: number of entries in hit_list
+    const int32_t* hit_list;
+    long long n;           // mode 0: Q
     int D;
     int mode;              // 0 query gradient, 1 normalised trace normal
-    float* out;            // [n, 3]
+    float* out;            // [n, 3] (mode 1: indexed by ray)
 };
 
 template <typename T, int IN>
-__global__ void __launch_bounds__(kThreads) k_grad(const float* __restrict__ W1, const float* __restrict__ b1,
-                                                   const float* __restrict__ W2, const Tables tb,
-                                                   const GradArgs A) {
-    __shared__ __align__(16) float sW1T[IN][kHidden];
-    __shared__ __align__(16) float sb1[kHidden];
-    __shared__ __align__(16) float sW2[kHidden];
-    for (int i = threadIdx.x; i < IN * kHidden; i += blockDim.x) {
-        const int h = i / IN, k = i - h * IN;
-        sW1T[k][h] = W1[i];
-    }
-    for (int i = threadIdx.x; i < kHidden; i += blockDim.x) {
-        sb1[i] = b1[i];
-        sW2[i] = W2[i];
-    }
-    __syncthreads();
+__global__ void __launch_bounds__(kThreads) k_grad(const DecPtrs dp, const Tables tb, const GradArgs A) {
     constexpr int OFF = IN - kFeatDim;
-    const int lane = threadIdx.x & 31, g = lane >> 3, l = lane & 7, gbase = (threadIdx.x & ~31) + (g << 3);
-    const int wbase = gbase & 31;
-    const unsigned gmask = 0xffu << wbase;
-    const long long groups = (long long)gridDim.x * (blockDim.x / 8);
-    for (long long it = (long long)blockIdx.x * (blockDim.x / 8) + (threadIdx.x >> 3); it < A.n; it += groups) {
-        float x[3];
-        int dd, vox;
-        uint32_t ijk;
-        if (A.mode == 1) {
-            if (!A.hit[it]) {
-                if (l < 3) A.out[3 * it + l] = 0.0f;
-                continue;
+    constexpr int K4 = OFF ? 36 : 32;
+    __shared__ __align__(16) float zbuf[kWarps][32 * kZStride];
+    __shared__ __align__(16) float gxs[kWarps][32 * 4];
+    __shared__ __align__(16) SmemDecoder sd;
+    stage_decoder<IN>(sd, dp.W1, dp.b1, dp.W2);
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = lane >> 3, l = lane & 7, gbase = g << 3;
+    const unsigned gmask = 0xffu << gbase;
+    float* zb = zbuf[warp];
+    float* gb = gxs[warp];
+    const long long n = A.mode == 1 ? (long long)*A.hit_count : A.n;
+    for (long long base = ((long long)blockIdx.x * kWarps + warp) * 32; base < n;
+         base += (long long)gridDim.x * kWarps * 32) {
+        const long long it = base + lane;
+        const bool act = it < n;
+        float x0 = 0.f, x1 = 0.f, x2 = 0.f;
+        int dd = -1, vox = -1, ray = -1;
+        uint32_t ijk = 0;
+        if (act) {
+            if (A.mode == 1) {
+                ray = A.hit_list[it];
+                const float t = A.t_hit[ray];
+                x0 = fmaf(t, A.d[3 * ray], A.o[3 * ray]);
+                x1 = fmaf(t, A.d[3 * ray + 1], A.o[3 * ray + 1]);
+                x2 = fmaf(t, A.d[3 * ray + 2], A.o[3 * ray + 2]);
+                dd = A.D;
+                vox = A.hit_vox[ray];
+                ijk = tb.node[dd][vox].ijk;
+            } else {
+                x0 = A.x[3 * it];
+                x1 = A.x[3 * it + 1];
+                x2 = A.x[3 * it + 2];
+                dd = locate_descend(tb, A.D, x0, x1, x2, vox, ijk);
             }
-            const float t = A.t_hit[it];
-#pragma unroll
-            for (int a = 0; a < 3; ++a) x[a] = fmaf(t, A.d[3 * it + a], A.o[3 * it + a]);
-            dd = A.D;
-            vox = A.hit_vox[it];
-            ijk = tb.node[dd][vox].ijk;
-        } else {
-#pragma unroll
-            for (int a = 0; a < 3; ++a) x[a] = A.x[3 * it + a];
-            dd = locate_descend(tb, A.D, x[0], x[1], x[2], vox, ijk);
         }
-        const float q[3] = {__fadd_rn(x[0], 1.0f), __fadd_rn(x[1], 1.0f), __fadd_rn(x[2], 1.0f)};
-        // z and dz/dx for this lane's 4 channels
-        float z[4] = {0.f, 0.f, 0.f, 0.f};
-        float jz[4][3] = {};
-        if (dd >= kFirstFeatureDepth) {
-            const int a = (l <= dd - kFirstFeatureDepth) ? __ldg(tb.anc[dd] + (size_t)vox * 8 + l) : -1;
-            for (int dp = kFirstFeatureDepth; dp <= dd; ++dp) {
-                const int v = __shfl_sync(gmask, a, wbase + dp - kFirstFeatureDepth);
-                const int cid = __ldg(tb.corners[dp] + (size_t)v * 8 + l);
-                const int sh = dd - dp;
-                const float sc = pow2f(dp - 1);
-                const uint32_t cc[3] = {unpack_i(ijk) >> sh, unpack_j(ijk) >> sh, unpack_k(ijk) >> sh};
-                float u[3];
+        const float q0 = __fadd_rn(x0, 1.0f), q1 = __fadd_rn(x1, 1.0f), q2 = __fadd_rn(x2, 1.0f);
+        // (A) z of the 32 items
+#pragma unroll 1
+        for (int r = 0; r < 8; ++r) {
+            const int s = r * 4 + g;
+            const int sdd = __shfl_sync(0xffffffffu, dd, s);
+            const int svox = __shfl_sync(0xffffffffu, vox, s);
+            const uint32_t sijk = __shfl_sync(0xffffffffu, ijk, s);
+            const float s0 = __shfl_sync(0xffffffffu, q0, s);
+            const float s1 = __shfl_sync(0xffffffffu, q1, s);
+            const float s2 = __shfl_sync(0xffffffffu, q2, s);
+            float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (sdd >= kFirstFeatureDepth) z = gather_slot<T>(tb, sdd, svox, sijk, s0, s1, s2, gmask, gbase, l);
+            *reinterpret_cast<float4*>(zb + s * kZStride + 4 * l) = z;
+        }
+        __syncwarp();
+        // (B) forward pass and v = sum_h W2_h [pre_h > 0] W1[h] for this lane's item
+        float v[K4], gv[K4];
 #pragma unroll
-                for (int aa = 0; aa < 3; ++aa) u[aa] = clamp01(__fsub_rn(__fmul_rn(q[aa], sc), (float)cc[aa]));
-                const void* fb = tb.feats[dp - kFirstFeatureDepth];
+        for (int j = 0; j < 8; ++j) {
+            const float4 a = reinterpret_cast<const float4*>(zb + lane * kZStride)[j];
+            v[4 * j] = a.x; v[4 * j + 1] = a.y; v[4 * j + 2] = a.z; v[4 * j + 3] = a.w;
+        }
+        if constexpr (OFF == 3) {
+            v[32] = x0; v[33] = x1; v[34] = x2; v[35] = 0.0f;
+        }
 #pragma unroll
-                for (int c = 0; c < 8; ++c) {
-                    const float4 r = FeatLoad<T>::load(fb, __shfl_sync(gmask, cid, wbase + c), l);
-                    float f[3], df[3];
+        for (int k = 0; k < K4; ++k) gv[k] = 0.0f;
+#pragma unroll 1
+        for (int h = 0; h < kHidden; ++h) {
+            const float4* w = reinterpret_cast<const float4*>(sd.W1 + h * K4);
+            float a0 = 0.0f, a1 = 0.0f;
 #pragma unroll
-                    for (int aa = 0; aa < 3; ++aa) {
-                        const bool up = (c >> aa) & 1;
-                        f[aa] = up ? u[aa] : 1.0f - u[aa];
-                        df[aa] = up ? sc : -sc;
-                    }
-                    const float w = f[0] * f[1] * f[2];
-                    const float dw[3] = {df[0] * f[1] * f[2], f[0] * df[1] * f[2], f[0] * f[1] * df[2]};
-                    const float rv[4] = {r.x, r.y, r.z, r.w};
+            for (int j = 0; j < K4 / 4; ++j) {
+                const float4 ww = w[j];
+                a0 = fmaf(ww.x, v[4 * j], a0);
+                a1 = fmaf(ww.y, v[4 * j + 1], a1);
+                a0 = fmaf(ww.z, v[4 * j + 2], a0);
+                a1 = fmaf(ww.w, v[4 * j + 3], a1);
+            }
+            const float2 bw = sd.bw[h];
+            const float gh = (a0 + a1 + bw.x) > 0.0f ? bw.y : 0.0f;
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        z[j] = fmaf(w, rv[j], z[j]);
+            for (int j = 0; j < K4 / 4; ++j) {
+                const float4 ww = w[j];
+                gv[4 * j] = fmaf(gh, ww.x, gv[4 * j]);
+                gv[4 * j + 1] = fmaf(gh, ww.y, gv[4 * j + 1]);
+                gv[4 * j + 2] = fmaf(gh, ww.z, gv[4 * j + 2]);
+                gv[4 * j + 3] = fmaf(gh, ww.w, gv[4 * j + 3]);
+            }
+        }
+        __syncwarp();
 #pragma unroll
-                        for (int aa = 0; aa < 3; ++aa) jz[j][aa] = fmaf(dw[aa], rv[j], jz[j][aa]);
+        for (int j = 0; j < 8; ++j)
+            reinterpret_cast<float4*>(zb + lane * kZStride)[j] =
+                make_float4(gv[4 * j], gv[4 * j + 1], gv[4 * j + 2], gv[4 * j + 3]);
+        __syncwarp();
+        // (C) J^T v_z: the trilinear derivative weights of every level and corner
+#pragma unroll 1
+        for (int r = 0; r < 8; ++r) {
+            const int s = r * 4 + g;
+            const int sdd = __shfl_sync(0xffffffffu, dd, s);
+            const int svox = __shfl_sync(0xffffffffu, vox, s);
+            const uint32_t sijk = __shfl_sync(0xffffffffu, ijk, s);
+            const float sq[3] = {__shfl_sync(0xffffffffu, q0, s), __shfl_sync(0xffffffffu, q1, s),
+                                 __shfl_sync(0xffffffffu, q2, s)};
+            float part[3] = {0.f, 0.f, 0.f};
+            if (sdd >= kFirstFeatureDepth) {
+                const float4 gz = *reinterpret_cast<const float4*>(zb + s * kZStride + 4 * l);
+                const int a = (l <= sdd - kFirstFeatureDepth) ? __ldg(tb.anc[sdd] + (size_t)svox * 8 + l) : -1;
+                for (int dp2 = kFirstFeatureDepth; dp2 <= sdd; ++dp2) {
+                    const int vv = __shfl_sync(gmask, a, gbase + dp2 - kFirstFeatureDepth);
+                    const int cid = __ldg(tb.corners[dp2] + (size_t)vv * 8 + l);
+                    const int sh = sdd - dp2;
+                    const float sc = pow2f(dp2 - 1);
+                    const uint32_t cc[3] = {unpack_i(sijk) >> sh, unpack_j(sijk) >> sh, unpack_k(sijk) >> sh};
+                    float u[3];
+#pragma unroll
+                    for (int aa = 0; aa < 3; ++aa) u[aa] = clamp01(__fsub_rn(__fmul_rn(sq[aa], sc), (float)cc[aa]));
+                    const void* fb = tb.feats[dp2 - kFirstFeatureDepth];
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) {
+                        const float4 row = FeatLoad<T>::load(fb, __shfl_sync(gmask, cid, gbase + c), l);
+                        const float pc = row.x * gz.x + row.y * gz.y + row.z * gz.z + row.w * gz.w;
+                        float f[3], df[3];
+#pragma unroll
+                        for (int aa = 0; aa < 3; ++aa) {
+                            const bool up = (c >> aa) & 1;
+                            f[aa] = up ? u[aa] : 1.0f - u[aa];
+                            df[aa] = up ? sc : -sc;
+                        }
+                        part[0] = fmaf(df[0] * f[1] * f[2], pc, part[0]);
+                        part[1] = fmaf(f[0] * df[1] * f[2], pc, part[1]);
+                        part[2] = fmaf(f[0] * f[1] * df[2], pc, part[2]);
                     }
                 }
             }
-        }
-        // pre-activations of this lane's 16 hidden units h = 32 i + 4 l + j
-        float pre[16];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const float4 b = *reinterpret_cast<const float4*>(&sb1[32 * i + 4 * l]);
-            pre[4 * i] = b.x; pre[4 * i + 1] = b.y; pre[4 * i + 2] = b.z; pre[4 * i + 3] = b.w;
-        }
-        auto accum_pre = [&](int k, float vk) {
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const float4 w = *reinterpret_cast<const float4*>(&sW1T[k][32 * i + 4 * l]);
-                pre[4 * i] = fmaf(w.x, vk, pre[4 * i]);
-                pre[4 * i + 1] = fmaf(w.y, vk, pre[4 * i + 1]);
-                pre[4 * i + 2] = fmaf(w.z, vk, pre[4 * i + 2]);
-                pre[4 * i + 3] = fmaf(w.w, vk, pre[4 * i + 3]);
+            for (int aa = 0; aa < 3; ++aa) {
+                part[aa] += __shfl_xor_sync(0xffffffffu, part[aa], 1);
+                part[aa] += __shfl_xor_sync(0xffffffffu, part[aa], 2);
+                part[aa] += __shfl_xor_sync(0xffffffffu, part[aa], 4);
             }
-        };
-#pragma unroll
-        for (int k = 0; k < OFF; ++k) accum_pre(k, x[k]);
-#pragma unroll 1
-        for (int sl = 0; sl < 8; ++sl) {
-#pragma unroll
-            for (int j = 0; j < 4; ++j) accum_pre(OFF + 4 * sl + j, __shfl_sync(gmask, z[j], wbase + sl));
-        }
-        float gh[16];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const float4 w = *reinterpret_cast<const float4*>(&sW2[32 * i + 4 * l]);
-            gh[4 * i] = pre[4 * i] > 0.f ? w.x : 0.f;
-            gh[4 * i + 1] = pre[4 * i + 1] > 0.f ? w.y : 0.f;
-            gh[4 * i + 2] = pre[4 * i + 2] > 0.f ? w.z : 0.f;
-            gh[4 * i + 3] = pre[4 * i + 3] > 0.f ? w.w : 0.f;
-        }
-        float gx[3] = {0.f, 0.f, 0.f};
-        float gz[4] = {0.f, 0.f, 0.f, 0.f};
-        auto back_k = [&](int k) {
-            float p = 0.f;
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const float4 w = *reinterpret_cast<const float4*>(&sW1T[k][32 * i + 4 * l]);
-                p = fmaf(gh[4 * i], w.x, p);
-                p = fmaf(gh[4 * i + 1], w.y, p);
-                p = fmaf(gh[4 * i + 2], w.z, p);
-                p = fmaf(gh[4 * i + 3], w.w, p);
-            }
-            p += __shfl_xor_sync(gmask, p, 1);
-            p += __shfl_xor_sync(gmask, p, 2);
-            p += __shfl_xor_sync(gmask, p, 4);
-            return p;
-        };
-#pragma unroll
-        for (int k = 0; k < OFF; ++k) gx[k] = back_k(k);
-#pragma unroll 1
-        for (int sl = 0; sl < 8; ++sl) {
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const float p = back_k(OFF + 4 * sl + j);
-                if (sl == l) gz[j] = p;
+            if (l == 0) {
+                gb[s * 4] = part[0];
+                gb[s * 4 + 1] = part[1];
+                gb[s * 4 + 2] = part[2];
             }
         }
-        float part[3];
-#pragma unroll
-        for (int aa = 0; aa < 3; ++aa) {
-            part[aa] = gz[0] * jz[0][aa] + gz[1] * jz[1][aa] + gz[2] * jz[2][aa] + gz[3] * jz[3][aa];
-            part[aa] += __shfl_xor_sync(gmask, part[aa], 1);
-            part[aa] += __shfl_xor_sync(gmask, part[aa], 2);
-            part[aa] += __shfl_xor_sync(gmask, part[aa], 4);
-            gx[aa] += part[aa];
+        __syncwarp();
+        if (act) {
+            float gx[3] = {gb[lane * 4], gb[lane * 4 + 1], gb[lane * 4 + 2]};
+            if constexpr (OFF == 3) {
+                gx[0] += gv[32];
+                gx[1] += gv[33];
+                gx[2] += gv[34];
+            }
+            const long long oi = A.mode == 1 ? (long long)ray : it;
+            if (A.mode == 1) {
+                const float nn = sqrtf(gx[0] * gx[0] + gx[1] * gx[1] + gx[2] * gx[2]);
+                const float inv = nn > 0.f ? 1.0f / nn : 0.f;
+                gx[0] *= inv;
+                gx[1] *= inv;
+                gx[2] *= inv;
+            }
+            A.out[3 * oi] = gx[0];
+            A.out[3 * oi + 1] = gx[1];
+            A.out[3 * oi + 2] = gx[2];
         }
-        if (A.mode == 1) {
-            const float nn = sqrtf(gx[0] * gx[0] + gx[1] * gx[1] + gx[2] * gx[2]);
-            const float inv = nn > 0.f ? 1.0f / nn : 0.f;
-#pragma unroll
-            for (int aa = 0; aa < 3; ++aa) gx[aa] *= inv;
-        }
-        if (l < 3) A.out[3 * it + l] = l == 0 ? gx[0] : (l == 1 ? gx[1] : gx[2]);
+        __syncwarp();
     }
 }
 
@@ -301,6 +323,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_trace_f32(const DecPtrs dp, con
     float* zb = zbuf[warp];
     RaySlot S;
     S.ray = -1;
+    S.hit_ray = -1;
     RayQueue Qu;
     Qu.init();
     for (;;) {
@@ -326,6 +349,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_trace_f32(const DecPtrs dp, con
         const float dhat = mlp_f32<IN>(sd, dp.b2, zb + lane * kZStride, x0, x1, x2);
         __syncwarp();
         if (act) step_update(S, dhat, A, tb);
+        publish_hits(S, A, lane);
     }
 }
 
@@ -344,7 +368,7 @@ void launch_query(const DecPtrs& P, const Tables& tb, const float* x, long long 
 
 template <typename T, int IN>
 void launch_grad(const nglod_decoder* dec, const Tables& tb, const GradArgs& A, int grid, cudaStream_t st) {
-    k_grad<T, IN><<<grid, kThreads, 0, st>>>(dec->W1, dec->b1, dec->W2, tb, A);
+    k_grad<T, IN><<<grid, kThreads, 0, st>>>(dec_ptrs(dec), tb, A);
 }
 
 int grid_items(long long n, int per_cta, int sms, int ctas_per_sm) {
@@ -354,7 +378,7 @@ int grid_items(long long n, int per_cta, int sms, int ctas_per_sm) {
 
 int run_grad(const nglod_decoder* dec, const Tables& tb, const GradArgs& A, bool f16, int sms,
              cudaStream_t st) {
-    const int grid = grid_items(A.n, kThreads / 8, sms, 8);
+    const int grid = grid_items(A.n, kThreads, sms, 2);
     if (dec->in_dim == 35) {
         if (f16) launch_grad<__half, 35>(dec, tb, A, grid, st); else launch_grad<float, 35>(dec, tb, A, grid, st);
     } else {
@@ -381,12 +405,15 @@ int launch_trace_fp32(const nglod_decoder* dec, const Tables& tb, const TraceArg
 
 int launch_normals(const nglod_decoder* dec, const Tables& tb, const TraceArgs& A, float* normal, bool f16,
                    int sms, cudaStream_t st) {
+    // misses get zero normals; the kernel writes the hits from the hit list
+    NGLOD_CUDA(cudaMemsetAsync(normal, 0, sizeof(float) * 3 * (size_t)A.R, st));
     GradArgs G{};
     G.o = A.o;
     G.d = A.d;
     G.t_hit = A.t_hit;
-    G.hit = A.hit;
     G.hit_vox = A.hit_vox;
+    G.hit_count = A.hit_count;
+    G.hit_list = A.hit_list;
     G.n = A.R;
     G.D = A.D;
     G.mode = 1;
@@ -448,7 +475,7 @@ extern "C" int sdf_query(const nglod_svo* svo, const nglod_features* feats, cons
 
 extern "C" size_t sphere_trace_workspace(int64_t R) {
     if (R < 0) return 0;
-    return 256 + ((sizeof(int32_t) * (size_t)R + 255) / 256) * 256;
+    return trace_ws_hit_list_offset(R) + ((sizeof(int32_t) * (size_t)R + 255) / 256) * 256;
 }
 
 extern "C" int sphere_trace(const nglod_svo* svo, const nglod_features* feats, const nglod_decoder* dec,
@@ -490,7 +517,9 @@ extern "C" int sphere_trace(const nglod_svo* svo, const nglod_features* feats, c
     A.hit = hit;
     A.steps = steps;
     A.queue = (int*)work;
-    A.hit_vox = (int32_t*)((char*)work + 256);
+    A.hit_count = (int*)work + 2;
+    A.hit_vox = (int32_t*)((char*)work + trace_ws_hit_vox_offset());
+    A.hit_list = (int32_t*)((char*)work + trace_ws_hit_list_offset(R));
     NGLOD_CUDA(cudaMemsetAsync(work, 0, 256, st));
     rc = check_decoder(dec);
     if (rc) return rc;
@@ -534,7 +563,9 @@ extern "C" int trace_normals(const nglod_svo* svo, const nglod_features* feats, 
     A.D = D;
     A.t_hit = const_cast<float*>(t_hit);
     A.hit = const_cast<uint8_t*>(hit);
-    A.hit_vox = (int32_t*)((char*)work + 256);
+    A.hit_count = (int*)const_cast<void*>(work) + 2;
+    A.hit_vox = (int32_t*)((char*)work + trace_ws_hit_vox_offset());
+    A.hit_list = (int32_t*)((char*)work + trace_ws_hit_list_offset(R));
     return launch_normals(dec, tb, A, normal, feats->dtype == NGLOD_F16, svo->num_sms, st);
 }
 

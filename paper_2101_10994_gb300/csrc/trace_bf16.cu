@@ -163,6 +163,7 @@ __global__ void __launch_bounds__(kTM, kCtasPerSm) k_trace_bf16(const DecPtrsB d
     bool drained = true;
     RaySlot st;
     st.ray = -1;
+    st.hit_ray = -1;
     RayQueue Qu;
     Qu.init();
     for (;;) {
@@ -192,6 +193,7 @@ __global__ void __launch_bounds__(kTM, kCtasPerSm) k_trace_bf16(const DecPtrsB d
         }
         const float dhat = epilogue<IN>(S, taddr, dp.b2, x0, x1, x2);
         if (act) step_update(st, dhat, A, tb);
+        publish_hits(st, A, lane);
     }
     teardown_tmem(S, taddr, drained, phase);
 }

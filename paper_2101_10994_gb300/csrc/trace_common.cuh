@@ -90,6 +90,8 @@ struct TraceArgs {
     int32_t* steps;       // nullable
     int32_t* hit_vox;     // workspace: voxel of the hit (for normals)
     int* queue;           // workspace: next unstarted ray
+    int* hit_count;       // workspace: number of rays in hit_list
+    int32_t* hit_list;    // workspace: ids of the rays that hit (any order)
 };
 
 // One ray being traced: its list cursor [cur, end) with the current entry's
@@ -97,6 +99,7 @@ struct TraceArgs {
 // previous distance (oscillation rule).
 struct RaySlot {
     int ray;
+    int hit_ray;          // id of a ray this slot just finished as a hit, else -1
     float ox, oy, oz, dx, dy, dz;
     float t, tin, tout, dprev;
     int cur, end, k, vox;
@@ -118,7 +121,21 @@ __device__ __forceinline__ void finish(RaySlot& S, const TraceArgs& A, bool hit)
     A.hit[S.ray] = hit ? 1 : 0;
     if (A.steps) A.steps[S.ray] = S.k;
     A.hit_vox[S.ray] = hit ? S.vox : -1;
+    if (hit) S.hit_ray = S.ray;
     S.ray = -1;
+}
+
+// Appends the rays this warp just finished as hits to the hit list (one
+// atomic per warp and step).  Called by the whole warp, converged.
+__device__ __forceinline__ void publish_hits(RaySlot& S, const TraceArgs& A, int lane) {
+    const unsigned m = __ballot_sync(0xffffffffu, S.hit_ray >= 0);
+    if (m) {
+        int base = 0;
+        if (lane == 0) base = atomicAdd(A.hit_count, __popc(m));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (S.hit_ray >= 0) A.hit_list[base + __popc(m & ((1u << lane) - 1u))] = S.hit_ray;
+    }
+    S.hit_ray = -1;
 }
 
 // Moves the cursor past entries that end before t (the ray is discarded when
@@ -223,6 +240,10 @@ int launch_trace_fp32(const nglod_decoder* dec, const Tables& tb, const TraceArg
                       cudaStream_t st);
 int launch_normals(const nglod_decoder* dec, const Tables& tb, const TraceArgs& A, float* normal, bool f16,
                    int sms, cudaStream_t st);
+// Workspace layout of sphere_trace: [0, 256) header {queue, status, hit
+// count}, then int32 hit voxel per ray, then int32 hit list.
+inline size_t trace_ws_hit_vox_offset() { return 256; }
+inline size_t trace_ws_hit_list_offset(long long R) { return 256 + ((sizeof(int32_t) * (size_t)R + 255) / 256) * 256; }
 int launch_trace_bf16(const nglod_svo* svo, const nglod_decoder* dec, const Tables& tb, const TraceArgs& A,
                       bool f16, cudaStream_t st);
 int launch_query_bf16(const nglod_svo* svo, const Tables& tb, const nglod_decoder* dec, const float* x,

@@ -196,15 +196,16 @@ __global__ void __launch_bounds__(kThreads) k_level(const LevelParams p, const L
             } else {
                 o8 = origin_octant(ray, nd.ijk, p.dp);
             }
-            if (live) {
-                const uint32_t cij = (nd.ijk << 1) & 0x3ffffffeu;
-                for (uint32_t rm = rank_mask(nd.childmask, o8); rm; rm &= rm - 1u) {
-                    const uint32_t r = (uint32_t)(__ffs(rm) - 1);
-                    const uint32_t c = r ^ o8;
+            if (live && nd.childmask) {
+                ChildSlabs cs;
+                child_slabs(ray, nd.ijk, p.dp, cs);
+                uint32_t hs = 0;   // by slot, all 8 tested without branches
+#pragma unroll
+                for (uint32_t c = 0; c < 8; ++c) {
                     float a0, a1;
-                    if (slab_test(ray, cij | pack_ijk(c & 1u, (c >> 1) & 1u, (c >> 2) & 1u), dc, a0, a1))
-                        h |= 1u << r;
+                    hs |= child_hit(cs, c, a0, a1) ? (1u << c) : 0u;
                 }
+                h = rank_mask(hs & nd.childmask, o8);
             }
             x.rec[idx] = (uint16_t)(h | (live ? (o8 << 8) : 0u));
             mine += __popc(h);
@@ -266,15 +267,14 @@ __global__ void __launch_bounds__(kThreads) k_level(const LevelParams p, const L
             const int2 pr = p.dp == 0 ? make_int2((int)idx, 0) : p.in[idx];
             const Node nd = p.node[pr.y];
             const uint32_t o8 = rec[i] >> 8;
-            const uint32_t cij = (nd.ijk << 1) & 0x3ffffffeu;
-            RayPrep ray;
-            if (final_level) ray = p.rays[pr.x];
+            ChildSlabs cs;
+            if (final_level) child_slabs(p.rays[pr.x], nd.ijk, p.dp, cs);
             for (uint32_t h = h0; h; h &= h - 1u) {
                 const uint32_t c = (uint32_t)(__ffs(h) - 1) ^ o8;
                 const int32_t child = nd.childbase + __popc(nd.childmask & ((1u << c) - 1u));
                 if (final_level) {
                     float a0 = 0.f, a1 = 0.f;
-                    slab_test(ray, cij | pack_ijk(c & 1u, (c >> 1) & 1u, (c >> 2) & 1u), dc, a0, a1);
+                    child_hit(cs, c, a0, a1);
                     stage_i[loc] = child;
                     stage_f[loc] = make_float2(a0, a1);
                     stage_r[loc] = pr.x;
