@@ -239,6 +239,49 @@ int sphere_trace(const nglod_svo* svo, const nglod_features* feats,
                  size_t work_bytes, float* t_hit, uint8_t* hit, int32_t* steps,
                  float* normal, void* stream);
 
+/* sdf_backward -- gradients of  sum_i sum_q grad_sdf[i][q] * sdf_(L_i)(x_q),
+ * the adjoint of the per-LOD sum of Eq. 4 (Sec. 3.3: "summing them across
+ * levels" trains every LOD's decoder and the shared features jointly), for
+ * the LODs L_1 < L_2 < ... selected by lod_mask (bit L-1 selects LOD L).
+ *   decs          host array of num_lods decoders (index L-1; only the
+ *                 selected ones are read), FP32 weights on the device.
+ *   x             [Q, 3] points; grad_sdf [popcount(lod_mask), Q] (row i for
+ *                 the i-th selected LOD, increasing).
+ *   h_grad_feats  host array of device pointers, [C_l, 32] FP32 per LOD
+ *                 l = 1..highest selected LOD; ACCUMULATED (+=).
+ *   h_grad_W1/_b1/_W2  host arrays (index L-1) of device pointers, shapes as
+ *                 the decoder, accumulated; grad_b2 device [num_lods], acc.
+ *   grad_x        [Q, 3] accumulated, nullable.
+ *   deterministic must be 0 (the ordered scatter is not built); feature and
+ *                 weight gradients are summed with FP32 atomics, so their
+ *                 rounding order varies between runs.
+ * Interpolation weights are recomputed from x, never stored.  Errors as
+ * sdf_query.  Does not synchronise. */
+int sdf_backward(const nglod_svo* svo, const nglod_features* feats, const nglod_decoder* decs,
+                 const float* x, int64_t Q, uint32_t lod_mask, const float* grad_sdf,
+                 float* const* h_grad_feats, float* const* h_grad_W1, float* const* h_grad_b1,
+                 float* const* h_grad_W2, float* grad_b2, float* grad_x, int deterministic,
+                 void* stream);
+
+/* sdf_l2_backward -- one training step's gradients for the loss of Eq. 4,
+ * J = loss_scale * sum_L sum_q (sdf_L(x_q) - target_q)^2 over the LODs in
+ * lod_mask, computed in one pass per LOD (prediction, residual and adjoint
+ * together; no separate forward launch).  loss (device [num_lods], nullable)
+ * accumulates sum_q (sdf_L(x_q) - target_q)^2 per LOD.  Gradient buffers and
+ * errors as sdf_backward (no x gradient).  Does not synchronise. */
+int sdf_l2_backward(const nglod_svo* svo, const nglod_features* feats, const nglod_decoder* decs,
+                    const float* x, const float* target, int64_t Q, uint32_t lod_mask,
+                    float loss_scale, float* loss, float* const* h_grad_feats,
+                    float* const* h_grad_W1, float* const* h_grad_b1, float* const* h_grad_W2,
+                    float* grad_b2, void* stream);
+
+/* nglod_adam_step -- Adam (the optimiser of supplementary Sec. A.3) on n FP32
+ * parameters: m = b1 m + (1-b1) g, v = b2 v + (1-b2) g^2,
+ * p -= lr (m / (1-b1^step)) / (sqrt(v / (1-b2^step)) + eps); grad is then
+ * zeroed.  step counts from 1.  Does not synchronise. */
+int nglod_adam_step(float* param, float* grad, float* m, float* v, int64_t n, float lr,
+                    float beta1, float beta2, float eps, int step, void* stream);
+
 /* sphere_trace_status -- synchronises the stream and reports whether the
  * last sphere_trace that used this workspace completed: NGLOD_OK, or
  * NGLOD_ERR_TIMEOUT if a bounded tensor-core wait of the BF16 decode expired

@@ -127,8 +127,11 @@ __global__ void __launch_bounds__(kThreads) k_prep_rays(const float* __restrict_
 //           write the children at their final positions through shared
 //           memory, coalesced.
 // No CTA ever waits on another except at the single barrier.
-constexpr int kTileX = kThreads * 2;                 // parents per tile (2 per thread)
-constexpr int kStageBytes = kTileX * 8 * 16;         // up to 8 children x 16 B per parent
+constexpr int kTileX = kThreads * 2;                 // parents per pass-2 tile (2 per thread)
+constexpr int kPass1 = 4;                            // parents per thread per pass-1 step
+// staging: up to 8 children per parent, 8 B (pair) or 16 B (final entry) each
+template <bool FINAL>
+constexpr int stage_bytes() { return kTileX * 8 * (FINAL ? 16 : 8); }
 
 struct LevelScratch {
     uint16_t* rec;          // [input pairs] hit-by-rank | octant << 8
@@ -159,6 +162,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned* arrive, unsigned nblocks,
     return ok;
 }
 
+template <bool FINAL>
 __global__ void __launch_bounds__(kThreads) k_level(const LevelParams p, const LevelScratch x) {
     constexpr int kIt = kTileX / kThreads;
     extern __shared__ __align__(16) unsigned char stage[];
@@ -175,16 +179,16 @@ __global__ void __launch_bounds__(kThreads) k_level(const LevelParams p, const L
     const long long t_begin = min((long long)blockIdx.x * per, ntiles);
     const long long t_end = min(t_begin + per, ntiles);
     const int dc = p.dp + 1;                          // depth of the children
-    const bool final_level = dc == p.D;
+    constexpr bool final_level = FINAL;
 
     // ---- pass 1: Decide the children of every pair of the chunk ----
     long long mine = 0;
-    for (long long tile = t_begin; tile < t_end; ++tile) {
-        const long long base = tile * kTileX + (long long)threadIdx.x * kIt;
+    const long long c_lo = t_begin * kTileX, c_hi = min(t_end * kTileX, n);
+    for (long long base = c_lo + (long long)threadIdx.x * kPass1; base < c_hi; base += (long long)kThreads * kPass1) {
 #pragma unroll
-        for (int i = 0; i < kIt; ++i) {
+        for (int i = 0; i < kPass1; ++i) {
             const long long idx = base + i;
-            if (idx >= n) continue;
+            if (idx >= c_hi) continue;
             const int2 pr = p.dp == 0 ? make_int2((int)idx, 0) : p.in[idx];
             const RayPrep ray = p.rays[pr.x];
             const Node nd = p.node[pr.y];
@@ -324,12 +328,13 @@ constexpr int kMaxGrid = 4096;   // chunk-count slots (>= resident CTAs of the l
 
 // Resident CTAs per SM of the level kernel with its staging buffer (the
 // persistent grid is sized to exactly what fits).
+template <bool FINAL>
 int level_ctas_per_sm() {
     static int cached = 0;
     if (!cached) {
-        cudaFuncSetAttribute(k_level, cudaFuncAttributeMaxDynamicSharedMemorySize, kStageBytes);
+        cudaFuncSetAttribute(k_level<FINAL>, cudaFuncAttributeMaxDynamicSharedMemorySize, stage_bytes<FINAL>());
         int n = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_level, kThreads, kStageBytes);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_level<FINAL>, kThreads, stage_bytes<FINAL>());
         cached = n > 0 ? n : 1;
     }
     return cached;
@@ -392,7 +397,6 @@ extern "C" int svo_trace_rays(const nglod_svo* svo, const float* o, const float*
     uint16_t* rec = (uint16_t*)w;
 
     const int sms = svo->num_sms;
-    const int grid = std::min(sms * level_ctas_per_sm(), kMaxGrid);
     NGLOD_CUDA(cudaMemsetAsync(ctr, 0, sizeof(Counters), st));
     NGLOD_CUDA(cudaMemsetAsync(arrive, 0, sizeof(unsigned) * (kMaxDepth + 2), st));
     k_prep_rays<<<std::min<long long>((R + kThreads - 1) / kThreads, (long long)sms * 16), kThreads, 0, st>>>(
@@ -416,8 +420,15 @@ extern "C" int svo_trace_rays(const nglod_svo* svo, const float* o, const float*
         xs.chunk_cnt = chunk_cnt;
         xs.arrive = arrive + dp;
         void* args[] = {(void*)&lp, (void*)&xs};
-        NGLOD_CUDA(cudaLaunchCooperativeKernel((const void*)k_level, dim3(grid), dim3(kThreads), args,
-                                               (size_t)kStageBytes, st));
+        if (dp + 1 == D) {
+            const int grid = std::min(sms * level_ctas_per_sm<true>(), kMaxGrid);
+            NGLOD_CUDA(cudaLaunchCooperativeKernel((const void*)k_level<true>, dim3(grid), dim3(kThreads), args,
+                                                   (size_t)stage_bytes<true>(), st));
+        } else {
+            const int grid = std::min(sms * level_ctas_per_sm<false>(), kMaxGrid);
+            NGLOD_CUDA(cudaLaunchCooperativeKernel((const void*)k_level<false>, dim3(grid), dim3(kThreads), args,
+                                                   (size_t)stage_bytes<false>(), st));
+        }
     }
     k_ray_offsets<<<std::min<long long>((R + kThreads) / kThreads, (long long)sms * 16), kThreads, 0, st>>>(
         (const int32_t*)buf[D & 1], ctr, D, R, std::min<long long>(hit_capacity, pair_capacity), ray_offsets);

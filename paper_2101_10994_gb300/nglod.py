@@ -24,7 +24,7 @@ FIRST_FEATURE_DEPTH = 3
 EXPORTS = ["nglod_last_error", "svo_build", "svo_info", "svo_device_arrays", "svo_read_arrays", "svo_free",
            "svo_trace_rays_workspace", "svo_trace_rays", "sdf_query", "sphere_trace_workspace",
            "sphere_trace", "sphere_trace_status", "trace_normals", "svo_trace_rays_noalloc",
-           "svo_trace_rays_sizes"]
+           "svo_trace_rays_sizes", "sdf_backward", "sdf_l2_backward", "nglod_adam_step"]
 
 
 class NglodError(RuntimeError):
@@ -76,6 +76,9 @@ def lib():
         L.trace_normals.argtypes = [P, P, P, P, P, i64, i32, P, sz, P, P, P, P]
         L.sphere_trace_status.argtypes = [P, P]
         L.svo_trace_rays_sizes.argtypes = [P, P, i32, P]
+        L.sdf_backward.argtypes = [P, P, P, P, i64, C.c_uint32, P, P, P, P, P, P, P, i32, P]
+        L.sdf_l2_backward.argtypes = [P, P, P, P, P, i64, C.c_uint32, C.c_float, P, P, P, P, P, P, P]
+        L.nglod_adam_step.argtypes = [P, P, P, P, i64, C.c_float, C.c_float, C.c_float, C.c_float, i32, P]
         L.svo_trace_rays_noalloc.argtypes = [P, P, P, i64, i32, P, P, P, i64, P, P]
         _lib = L
     return _lib
@@ -325,3 +328,67 @@ def trace_normals(svo: SVO, feats: Features, dec: DecoderDev, o, d, lists: RayLi
 def sphere_trace_status(out, stream=None):
     """Raises if the sphere_trace that filled ``out`` hit an expired wait."""
     _check(lib().sphere_trace_status(out["work"].data_ptr(), C.c_void_p(_stream(stream))))
+
+
+def new_grads(svo: SVO, decs, device="cuda"):
+    """Zeroed gradient buffers matching the features and decoders."""
+    import torch
+    return dict(feats=[torch.zeros((c, 32), dtype=torch.float32, device=device) for c in svo.corners],
+                W1=[torch.zeros_like(d.W1) for d in decs], b1=[torch.zeros_like(d.b1) for d in decs],
+                W2=[torch.zeros_like(d.W2) for d in decs],
+                b2=torch.zeros(len(decs), dtype=torch.float32, device=device))
+
+
+def sdf_backward(svo: SVO, feats: Features, decs, x, lods, grad_sdf, grads=None, grad_x=None, stream=None):
+    """Accumulates the gradients of sum_i grad_sdf[i] . sdf_{lods[i]}(x) into ``grads``.
+
+    ``decs`` lists every LOD's decoder (index lod - 1); ``lods`` the
+    increasing LODs whose outputs carry gradient (rows of ``grad_sdf``)."""
+    _require_cuda(x, grad_sdf)
+    x = x.contiguous()
+    grad_sdf = grad_sdf.contiguous()
+    Q = int(x.shape[0])
+    if grads is None:
+        grads = new_grads(svo, decs, x.device)
+    mask = 0
+    for l in lods:
+        mask |= 1 << (int(l) - 1)
+    dec_arr = (_Decoder * len(decs))(*[d.c() for d in decs])
+    fc = feats.c()
+    P = C.c_void_p
+
+    def parr(ts):
+        return (P * len(ts))(*[t.data_ptr() for t in ts])
+
+    _check(lib().sdf_backward(svo.h, C.byref(fc), dec_arr, x.data_ptr(), Q, mask, grad_sdf.data_ptr(),
+                              parr(grads["feats"]), parr(grads["W1"]), parr(grads["b1"]), parr(grads["W2"]),
+                              grads["b2"].data_ptr(), _ptr(grad_x), 0, C.c_void_p(_stream(stream))))
+    return grads
+
+
+def sdf_l2_backward(svo: SVO, feats: Features, decs, x, target, lods, loss_scale: float, grads, loss=None,
+                    stream=None):
+    """Gradients of loss_scale * sum_L sum_q (sdf_L(x_q) - target_q)^2 (Eq. 4), accumulated into ``grads``."""
+    _require_cuda(x, target)
+    mask = 0
+    for l in lods:
+        mask |= 1 << (int(l) - 1)
+    dec_arr = (_Decoder * len(decs))(*[d.c() for d in decs])
+    fc = feats.c()
+    P = C.c_void_p
+
+    def parr(ts):
+        return (P * len(ts))(*[t.data_ptr() for t in ts])
+
+    _check(lib().sdf_l2_backward(svo.h, C.byref(fc), dec_arr, x.data_ptr(), target.data_ptr(), int(x.shape[0]),
+                                 mask, float(loss_scale), _ptr(loss), parr(grads["feats"]), parr(grads["W1"]),
+                                 parr(grads["b1"]), parr(grads["W2"]), grads["b2"].data_ptr(),
+                                 C.c_void_p(_stream(stream))))
+    return grads
+
+
+def adam_step(param, grad, m, v, lr, step, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    """In-place Adam update of one FP32 tensor (grad is zeroed)."""
+    _check(lib().nglod_adam_step(param.data_ptr(), grad.data_ptr(), m.data_ptr(), v.data_ptr(), param.numel(),
+                                 float(lr), float(beta1), float(beta2), float(eps), int(step),
+                                 C.c_void_p(_stream(stream))))

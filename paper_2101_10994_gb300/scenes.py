@@ -382,3 +382,77 @@ def points_in_voxels(octree: Octree, dp: int, n: int, seed: int,
     p = np.stack([-1.0 + (i + u[:, 0]) * s, -1.0 + (j + u[:, 1]) * s,
                   -1.0 + (k + u[:, 2]) * s], axis=1)
     return p.astype(np.float32)
+
+
+# ----------------------------------------------------------------------------
+# Training samples (inputs of the summed per-LOD L2 loss)
+# ----------------------------------------------------------------------------
+def _primitive_surface(scene: Scene, p: int, n: int, rng) -> np.ndarray:
+    """n points uniformly distributed on primitive p's surface."""
+    t, c, q = scene.types[p], scene.centers[p], scene.params[p]
+    if t == PRIM_SPHERE:
+        v = rng.normal(size=(n, 3))
+        return c + q[0] * v / np.linalg.norm(v, axis=1, keepdims=True)
+    if t == PRIM_BOX:
+        h = q[0:3]
+        areas = np.array([h[1] * h[2], h[0] * h[2], h[0] * h[1]] * 2)
+        face = rng.choice(6, n, p=areas / areas.sum())
+        u = rng.uniform(-1.0, 1.0, (n, 3)) * h
+        axis = face % 3
+        sign = np.where(face < 3, 1.0, -1.0)
+        u[np.arange(n), axis] = sign * h[axis]
+        return c + u
+    h, r = q[0:3], q[3]
+    L = 2.0 * np.linalg.norm(h)
+    axis = h / np.linalg.norm(h)
+    side = rng.uniform(size=n) < (2 * np.pi * r * L) / (2 * np.pi * r * L + 4 * np.pi * r * r)
+    v = rng.normal(size=(n, 3))
+    v /= np.linalg.norm(v, axis=1, keepdims=True)
+    perp = v - (v @ axis)[:, None] * axis
+    perp /= np.maximum(np.linalg.norm(perp, axis=1, keepdims=True), 1e-12)
+    s = rng.uniform(-0.5 * L, 0.5 * L, n)
+    cyl = c + s[:, None] * axis + r * perp
+    cap = c + np.where((v @ axis)[:, None] >= 0, h, -h) + r * v
+    return np.where(side[:, None], cyl, cap)
+
+
+def surface_samples(scene: Scene, n: int, seed: int) -> np.ndarray:
+    """Points on the union's surface: primitives chosen in proportion to their
+    area, points on them drawn uniformly, and points inside another primitive
+    (union SDF < -1e-7) rejected."""
+    rng = np.random.default_rng(seed)
+    areas = []
+    for t, q in zip(scene.types, scene.params):
+        if t == PRIM_SPHERE:
+            areas.append(4 * np.pi * q[0] ** 2)
+        elif t == PRIM_BOX:
+            areas.append(8 * (q[0] * q[1] + q[1] * q[2] + q[0] * q[2]))
+        else:
+            L = 2.0 * np.linalg.norm(q[0:3])
+            areas.append(2 * np.pi * q[3] * L + 4 * np.pi * q[3] ** 2)
+    areas = np.array(areas)
+    out = []
+    have = 0
+    while have < n:
+        m = int((n - have) * 1.5) + 64
+        which = rng.choice(scene.n, m, p=areas / areas.sum())
+        pts = np.empty((m, 3))
+        for p in np.unique(which):
+            sel = which == p
+            pts[sel] = _primitive_surface(scene, int(p), int(sel.sum()), rng)
+        keep = scene_sdf(scene, pts) >= -1e-7
+        keep &= np.all(np.abs(pts) <= 1.0, axis=1)
+        out.append(pts[keep])
+        have += int(keep.sum())
+    return np.concatenate(out)[:n]
+
+
+def training_batch(scene: Scene, n: int, seed: int, sigma: float = 0.01):
+    """Half near-surface (surface + N(0, sigma^2)), half uniform in [-1,1]^3,
+    with float32 targets from the exact scene SDF (Sec. 3.3 sampling)."""
+    rng = np.random.default_rng(seed + 7919)
+    n_near = n // 2
+    near = surface_samples(scene, n_near, seed) + rng.normal(0.0, sigma, (n_near, 3))
+    uni = rng.uniform(-1.0, 1.0, (n - n_near, 3))
+    x = np.clip(np.concatenate([near, uni]), -1.0, 1.0).astype(np.float32)
+    return x, scene_sdf(scene, x.astype(np.float64)).astype(np.float32)

@@ -1,0 +1,54 @@
+"""Training of the octree features and per-LOD decoders on the GPU (Eq. 4).
+
+Each step runs, per LOD, the fused prediction + L2 residual + adjoint kernel
+(sdf_l2_backward) over one batch, then the Adam kernel over every parameter
+tensor (features of every level, each decoder's W1, b1, W2, b2).  Only the
+library's kernels touch the parameters; PyTorch holds the buffers.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import nglod as ng
+
+
+class Trainer:
+    def __init__(self, svo: ng.SVO, feats, decoders, lr: float = 1e-3, device="cuda"):
+        import torch
+        self.torch = torch
+        self.svo = svo
+        self.F = ng.Features(feats, "f32", device)
+        self.D = [ng.DecoderDev.from_decoder(d, device) for d in decoders]
+        self.b2 = torch.tensor([d.b2 for d in self.D], dtype=torch.float32, device=device)
+        self.grads = ng.new_grads(svo, self.D, device)
+        self.params = (list(self.F.tables) + [d.W1 for d in self.D] + [d.b1 for d in self.D] +
+                       [d.W2 for d in self.D] + [self.b2])
+        self.gparams = (list(self.grads["feats"]) + self.grads["W1"] + self.grads["b1"] + self.grads["W2"] +
+                        [self.grads["b2"]])
+        self.m = [torch.zeros_like(p) for p in self.params]
+        self.v = [torch.zeros_like(p) for p in self.params]
+        self.lr = lr
+        self.t = 0
+        self.L = len(self.D)
+
+    def step(self, x, target, lods=None):
+        """One Adam step on a batch; returns the per-LOD mean squared error."""
+        torch = self.torch
+        lods = lods or list(range(1, self.L + 1))
+        loss = torch.zeros(self.L, dtype=torch.float32, device=x.device)
+        Q = int(x.shape[0])
+        ng.sdf_l2_backward(self.svo, self.F, self.D, x, target, lods, 1.0 / Q, self.grads, loss)
+        self.t += 1
+        for p, g, m, v in zip(self.params, self.gparams, self.m, self.v):
+            ng.adam_step(p, g, m, v, self.lr, self.t)
+        b2 = self.b2.cpu().numpy()
+        for d, b in zip(self.D, b2):
+            d.b2 = float(b)
+        return loss / Q
+
+    def export(self):
+        """Current parameters as numpy (features per LOD, scenes.Decoder list)."""
+        from .scenes import Decoder
+        feats = [t.cpu().numpy() for t in self.F.tables]
+        decs = [Decoder(d.W1.cpu().numpy(), d.b1.cpu().numpy(), d.W2.cpu().numpy(), d.b2, d.in_dim) for d in self.D]
+        return feats, decs
