@@ -47,7 +47,7 @@ def parse():
     # itself is always the 1920x1080 LOD 5 CSG-64 frame)
     p.add_argument("--width", type=int, default=1920)
     p.add_argument("--height", type=int, default=1080)
-    p.add_argument("--decode", choices=["both", "f32", "bf16"], default="both")
+    p.add_argument("--decode", choices=["both", "all", "f32", "bf16", "fp8"], default="all")
     p.add_argument("--no-cpu-baseline", action="store_true")
     return p.parse_args()
 
@@ -154,10 +154,13 @@ def run_ours(args, rank, world, local_rank):
     d = torch.from_numpy(W["d"]).to(dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     modes = []
-    if args.decode in ("both", "f32"):
+    if args.decode in ("both", "all", "f32"):
         modes.append("f32")
-    if args.decode in ("both", "bf16") and bf16_available():
+    if args.decode in ("both", "all", "bf16") and bf16_available():
         modes.append("bf16")
+    if args.decode in ("all", "fp8") and bf16_available():
+        modes.append("fp8")
+        feats.set_fp8_bound(svo, W["lod"])
     dist = world > 1
     if dist:
         import torch.distributed as td
@@ -223,7 +226,7 @@ def run_ours(args, rank, world, local_rank):
             clock_info = sampler.summary()
 
     # ---- end to end through the public API with pinned host buffers ----
-    mode = "bf16" if "bf16" in modes else "f32"
+    mode = "bf16" if "bf16" in modes else modes[0]
     h_o = torch.from_numpy(W["o"]).pin_memory()
     h_d = torch.from_numpy(W["d"]).pin_memory()
     h_t = torch.empty(R, dtype=torch.float32).pin_memory()
@@ -313,8 +316,8 @@ def trace_roofline(W, res, mode, peaks):
     interp, layer1, outl = flops_per_query(W["dec"].in_dim, W["lod"], mode)
     q = res["queries_per_frame"]
     sec = res["ms_trace"] * 1e-3
-    kern = "k_trace_bf16" if mode == "bf16" else "k_trace_f32"
-    if mode == "bf16":
+    kern = "k_trace_f32" if mode == "f32" else "k_trace_bf16"
+    if mode != "f32":
         tf = peaks.get("bf16_tflops", 1900.0)
         achieved = q * layer1 / sec / 1e12
         return {"bound": "tensor", "kernel": kern, "achieved": achieved, "peak": tf, "unit": "TFLOP/s",
@@ -405,7 +408,7 @@ def main():
         pp = os.path.join(ROOT, "MEASURED_PEAKS.json")
         if os.path.exists(pp):
             peaks = json.load(open(pp))
-        head = "bf16" if "bf16" in res else "f32"
+        head = "bf16" if "bf16" in res else list(res)[0]
         r = res[head]
         line = {
             "metric": METRIC, "value": r["rays_per_s"], "unit": "rays/s", "n_gpus": world,

@@ -49,7 +49,7 @@ enum {
 };
 
 /* Element types of features / decode arithmetic. */
-enum { NGLOD_F32 = 0, NGLOD_F16 = 1, NGLOD_BF16 = 2 };
+enum { NGLOD_F32 = 0, NGLOD_F16 = 1, NGLOD_BF16 = 2, NGLOD_FP8E4M3 = 3 };
 
 typedef struct nglod_svo nglod_svo;   /* opaque octree handle */
 
@@ -59,6 +59,9 @@ typedef struct {
     int dtype;             /* NGLOD_F32 or NGLOD_F16                         */
     int m;                 /* feature dimension; only 32 is built            */
     int num_lods;          /* number of valid entries in feats               */
+    float fp8_z_absmax;    /* FP8 decode only: a bound on |z| (e.g. from
+                              nglod_features_absmax); z is scaled so this
+                              bound maps to 448, the largest e4m3 value     */
 } nglod_features;
 
 /* One LOD's decoder (Eq. 2): d = W2 . relu(W1 v + b1) + b2 with
@@ -81,9 +84,17 @@ typedef struct {
     int max_steps;         /* miss after this many decodes (paper: 200)       */
     int osc_check;         /* 1: also stop when |d_k - d_(k-1)| < 6 eps; the
                               ray is then a hit iff |d_k| < 6 eps             */
-    int decode_dtype;      /* NGLOD_F32 (CUDA cores) or NGLOD_BF16 (tcgen05)  */
+    int decode_dtype;      /* NGLOD_F32 (CUDA cores), NGLOD_BF16 or
+                              NGLOD_FP8E4M3 (tcgen05; see sdf_query)         */
     int want_normals;      /* 1: write normals of hit rays                    */
 } nglod_trace_params;
+
+/* nglod_features_absmax -- the sum over LODs 1..lod of each feature table's
+ * largest |value|, written to *h_out (synchronises).  The trilinear weights
+ * are non-negative and sum to 1, so this bounds every |z_k(x; lod)|: the
+ * natural fp8_z_absmax for decoding at that LOD. */
+int nglod_features_absmax(const nglod_svo* svo, const nglod_features* feats, int lod, float* h_out,
+                          void* stream);
 
 /* Text of the calling thread's last error ("" if none). */
 const char* nglod_last_error(void);
@@ -198,7 +209,11 @@ int svo_trace_rays_sizes(const void* work, int64_t* h_sizes, int n, void* stream
  *   grad      [Q, 3] float32 (nullable): analytic d sdf / dx (FP32 decode).
  *   decode_dtype  NGLOD_F32 (CUDA cores) or NGLOD_BF16 (tensor cores: z and
  *                 W1's z columns rounded to bf16, FP32 accumulation; the
- *                 x columns, biases and W2 stay FP32).
+ *                 x columns, biases and W2 stay FP32) or NGLOD_FP8E4M3
+ *                 (tensor cores: z scaled by 448 / feats->fp8_z_absmax and
+ *                 W1's z columns by 448 / their largest |value| (a per-LOD
+ *                 scale), both rounded to e4m3, FP32 accumulation, scales
+ *                 undone before the bias).
  * Errors: NGLOD_ERR_INVALID_ARG (lod outside 1..num_depths-3, missing
  * features), NGLOD_ERR_NOT_SUPPORTED (m != 32, hidden != 128, in_dim not 32 or
  * 35, grad with BF16 decode), NGLOD_ERR_TIMEOUT (a bounded tensor-core wait

@@ -40,6 +40,7 @@ struct nglod_svo {
     // depth d, for i = 0..d-3 (i = d-3 is v itself); unused entries are -1.
     int32_t* anc[nglod::kMaxDepth + 1] = {};
     int* dstatus = nullptr;                               // device status word
+    unsigned* dscratch = nullptr;                         // 16 device words (reductions)
     int device = 0;
     int num_sms = 0;
 };

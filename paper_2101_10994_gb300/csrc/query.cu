@@ -8,6 +8,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstring>
 #include <string>
 #include <vector>
 
@@ -439,11 +440,14 @@ extern "C" int sdf_query(const nglod_svo* svo, const nglod_features* feats, cons
     int rc = fill_tables(svo, feats, lod, tb);
     if (rc) return rc;
     const bool f16 = feats->dtype == NGLOD_F16;
-    if (decode_dtype == NGLOD_BF16) {
+    if (decode_dtype == NGLOD_BF16 || decode_dtype == NGLOD_FP8E4M3) {
         rc = check_decoder(dec);
         if (rc) return rc;
         if (grad) return fail(NGLOD_ERR_NOT_SUPPORTED, "sdf_query: grad needs the FP32 decode");
-        rc = launch_query_bf16(svo, tb, dec, x, Q, D, sdf, deepest, f16, st);
+        const bool fp8 = decode_dtype == NGLOD_FP8E4M3;
+        if (fp8 && !(feats->fp8_z_absmax > 0.0f))
+            return fail(NGLOD_ERR_INVALID_ARG, "sdf_query: the FP8 decode needs feats->fp8_z_absmax > 0");
+        rc = launch_query_bf16(svo, tb, dec, x, Q, D, sdf, deepest, f16, fp8 ? feats->fp8_z_absmax : 0.0f, st);
         if (rc) return rc;
         return NGLOD_OK;
     }
@@ -525,10 +529,13 @@ extern "C" int sphere_trace(const nglod_svo* svo, const nglod_features* feats, c
     if (rc) return rc;
     if (params->decode_dtype == NGLOD_F32) {
         rc = launch_trace_fp32(dec, tb, A, f16, svo->num_sms, st);
-    } else if (params->decode_dtype == NGLOD_BF16) {
-        rc = launch_trace_bf16(svo, dec, tb, A, f16, st);
+    } else if (params->decode_dtype == NGLOD_BF16 || params->decode_dtype == NGLOD_FP8E4M3) {
+        const bool fp8 = params->decode_dtype == NGLOD_FP8E4M3;
+        if (fp8 && !(feats->fp8_z_absmax > 0.0f))
+            return fail(NGLOD_ERR_INVALID_ARG, "sphere_trace: the FP8 decode needs feats->fp8_z_absmax > 0");
+        rc = launch_trace_bf16(svo, dec, tb, A, f16, fp8 ? feats->fp8_z_absmax : 0.0f, st);
     } else {
-        return fail(NGLOD_ERR_NOT_SUPPORTED, "sphere_trace: decode_dtype must be F32 or BF16");
+        return fail(NGLOD_ERR_NOT_SUPPORTED, "sphere_trace: decode_dtype must be F32, BF16 or FP8E4M3");
     }
     if (rc) return rc;
     if (normal && params->want_normals) {
@@ -577,5 +584,50 @@ extern "C" int sphere_trace_status(const void* work, void* stream) {
     NGLOD_CUDA(cudaStreamSynchronize(st));
     if (h[1] == kStatusTimeout)
         return fail(NGLOD_ERR_TIMEOUT, "sphere_trace: a tensor-core wait expired; results are invalid");
+    return NGLOD_OK;
+}
+
+namespace nglod {
+namespace {
+template <typename T>
+__global__ void k_absmax(const T* __restrict__ a, long long n, unsigned* __restrict__ out) {
+    float m = 0.0f;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        m = fmaxf(m, fabsf((float)a[i]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));   // non-negative: bit order = value order
+}
+}  // namespace
+}  // namespace nglod
+
+extern "C" int nglod_features_absmax(const nglod_svo* svo, const nglod_features* feats, int lod, float* h_out,
+                                     void* stream) {
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!svo || !feats || !h_out || lod < 1 || lod > feats->num_lods || lod > svo->num_depths - kFirstFeatureDepth)
+        return fail(NGLOD_ERR_INVALID_ARG, "nglod_features_absmax: bad arguments");
+    if (feats->dtype != NGLOD_F32 && feats->dtype != NGLOD_F16)
+        return fail(NGLOD_ERR_NOT_SUPPORTED, "nglod_features_absmax: features must be F32 or F16");
+    NGLOD_CUDA(cudaMemsetAsync(svo->dscratch, 0, sizeof(unsigned) * 16, st));
+    for (int l = 1; l <= lod; ++l) {
+        if (!feats->feats[l - 1]) return fail(NGLOD_ERR_INVALID_ARG, "nglod_features_absmax: NULL table");
+        const long long n = svo->nc[l + kFirstFeatureDepth - 1] * (long long)feats->m;
+        const int grid = (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, (long long)svo->num_sms * 8));
+        if (feats->dtype == NGLOD_F16)
+            k_absmax<__half><<<grid, 256, 0, st>>>((const __half*)feats->feats[l - 1], n, svo->dscratch + l);
+        else
+            k_absmax<float><<<grid, 256, 0, st>>>((const float*)feats->feats[l - 1], n, svo->dscratch + l);
+    }
+    NGLOD_CUDA(cudaGetLastError());
+    unsigned h[16];
+    NGLOD_CUDA(cudaMemcpyAsync(h, svo->dscratch, sizeof(h), cudaMemcpyDeviceToHost, st));
+    NGLOD_CUDA(cudaStreamSynchronize(st));
+    float sum = 0.0f;
+    for (int l = 1; l <= lod; ++l) {
+        float v;
+        memcpy(&v, &h[l], sizeof(float));
+        sum += v;
+    }
+    *h_out = sum;
     return NGLOD_OK;
 }

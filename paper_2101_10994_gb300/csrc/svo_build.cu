@@ -244,6 +244,7 @@ void destroy(nglod_svo* s, cudaStream_t st) {
         if (s->anc[d]) cudaFreeAsync(s->anc[d], st);
     }
     if (s->dstatus) cudaFreeAsync(s->dstatus, st);
+    if (s->dscratch) cudaFreeAsync(s->dscratch, st);
     cudaStreamSynchronize(st);
     delete s;
 }
@@ -301,6 +302,7 @@ extern "C" int svo_build(const uint64_t* const* h_keys, const int64_t* h_counts,
     BUILD_CUDA(cudaMallocAsync(&derr, sizeof(int), st));
     BUILD_CUDA(cudaMallocAsync(&s->dstatus, sizeof(int), st));
     BUILD_CUDA(cudaMemsetAsync(s->dstatus, 0, sizeof(int), st));
+    BUILD_CUDA(cudaMallocAsync(&s->dscratch, sizeof(unsigned) * 16, st));
     BUILD_CUDA(cudaMemsetAsync(derr, 0, sizeof(int), st));
     for (int d = 0; d < num_depths; ++d) {
         s->n[d] = h_counts[d];

@@ -71,6 +71,13 @@ __host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
+// Instruction descriptor of kind::f8f6f4 with A and B = E4M3 (format 0 at
+// bits 7-9 and 10-12), D = F32, both K-major; N >> 3 at bits 17-22, M >> 4 at
+// bits 24-28.  One instruction covers K = 32 eight-bit elements.
+__host__ __device__ constexpr uint32_t idesc_e4m3_f32(int M, int N) {
+    return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
 // Shared-memory matrix descriptor, K-major without swizzle: the operand is
 // made of 8-row x 16-byte core matrices (128 contiguous bytes each); lbo =
 // byte distance between core matrices adjacent along K, sbo = between
@@ -91,6 +98,17 @@ __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64
         "{\n\t.reg .pred p;\n\t"
         "setp.ne.b32 p, %4, 0;\n\t"
         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+        ::"r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate ? 1u : 0u)
+        : "memory");
+}
+
+// D[tmem] (+)= A[smem] * B[smem]^T with E4M3 operands, issued by one thread.
+__device__ __forceinline__ void mma_e4m3(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         bool accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}"
         ::"r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate ? 1u : 0u)
         : "memory");
 }
@@ -122,6 +140,12 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// Byte offset of element (row, k) of a K-major no-swizzle 8-bit operand with
+// kc_per_row 16-byte K chunks per 8-row group (16 elements per chunk).
+__host__ __device__ __forceinline__ uint32_t kmajor_offset8(int row, int k, int kc_per_row) {
+    return (uint32_t)(((row >> 3) * kc_per_row + (k >> 4)) * 128 + (row & 7) * 16 + (k & 15));
+}
 
 // Byte offset of element (row, k) of a K-major no-swizzle bf16 operand with
 // kc_per_row 16-byte K chunks per 8-row group: core matrix (row/8, k/8) at

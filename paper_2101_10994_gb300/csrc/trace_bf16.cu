@@ -19,6 +19,7 @@
 // raises an error flag, drains its MMA, frees its tensor memory and returns.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
+#include <cuda_fp8.h>
 
 #include <algorithm>
 
@@ -38,13 +39,16 @@ constexpr long kWaitPolls = 1l << 24;
 constexpr int kCtasPerSm = 4;           // 4 x 128 TMEM columns = the SM's 512
 
 struct BfSmem {
-    unsigned char A[kTM * kFeatDim * 2];      // z tile, bf16, K-major
-    unsigned char B[kHidden * kFeatDim * 2];  // W1 (z columns), bf16, K-major
+    unsigned char A[kTM * kFeatDim * 2];      // z tile, bf16 or e4m3, K-major
+    unsigned char B[kHidden * kFeatDim * 2];  // W1 (z columns), bf16 or e4m3, K-major
     float4 epi[kHidden];                      // (b1, W2, W1x_0, W1x_1)
     float wx2[kHidden];                       // W1x_2
+    float amax[kTM / 32];                     // FP8: per-warp |W1z| maxima
+    float acc_scale;                          // FP8: 1 / (W1 scale * z scale)
     uint64_t bar;
     uint32_t taddr;
 };
+constexpr float kE4M3Max = 448.0f;
 // Shared memory is kept small so the rest of the SM's 256 KB serves as L1
 // for the feature gathers; registers (>= 103 per thread) already keep
 // residency at 4 CTAs per SM.  A fifth CTA on an SM would only wait in
@@ -56,15 +60,38 @@ struct DecPtrsB {
     const float* b1;
     const float* W2;
     float b2;
+    float z_scale;     // FP8: z is multiplied by this before rounding to e4m3
 };
 
-template <int IN>
+template <int IN, bool FP8>
 __device__ __forceinline__ void stage_bf16_decoder(BfSmem& S, const DecPtrsB& dp) {
     constexpr int OFF = IN - kFeatDim;
-    for (int i = threadIdx.x; i < kHidden * kFeatDim; i += blockDim.x) {
-        const int h = i / kFeatDim, k = i - h * kFeatDim;
-        *reinterpret_cast<__nv_bfloat16*>(S.B + tc::kmajor_offset(h, k, kKc)) =
-            __float2bfloat16_rn(dp.W1[h * IN + OFF + k]);
+    if constexpr (FP8) {
+        // per-LOD weight scale: the largest |W1| of the z columns maps to 448
+        float m = 0.0f;
+        for (int i = threadIdx.x; i < kHidden * kFeatDim; i += blockDim.x)
+            m = fmaxf(m, fabsf(dp.W1[(i / kFeatDim) * IN + OFF + i % kFeatDim]));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if ((threadIdx.x & 31) == 0) S.amax[threadIdx.x >> 5] = m;
+        __syncthreads();
+        float wmax = 0.0f;
+#pragma unroll
+        for (int w = 0; w < kTM / 32; ++w) wmax = fmaxf(wmax, S.amax[w]);
+        const float ws = wmax > 0.0f ? kE4M3Max / wmax : 1.0f;
+        if (threadIdx.x == 0) S.acc_scale = 1.0f / (ws * dp.z_scale);
+        for (int i = threadIdx.x; i < kHidden * kFeatDim; i += blockDim.x) {
+            const int h = i / kFeatDim, k = i - h * kFeatDim;
+            const __nv_fp8_e4m3 q(dp.W1[h * IN + OFF + k] * ws);
+            S.B[tc::kmajor_offset8(h, k, kFeatDim / 16)] = *reinterpret_cast<const unsigned char*>(&q);
+        }
+    } else {
+        for (int i = threadIdx.x; i < kHidden * kFeatDim; i += blockDim.x) {
+            const int h = i / kFeatDim, k = i - h * kFeatDim;
+            *reinterpret_cast<__nv_bfloat16*>(S.B + tc::kmajor_offset(h, k, kKc)) =
+                __float2bfloat16_rn(dp.W1[h * IN + OFF + k]);
+        }
+        if (threadIdx.x == 0) S.acc_scale = 1.0f;
     }
     for (int h = threadIdx.x; h < kHidden; h += blockDim.x) {
         const float x0 = OFF ? dp.W1[h * IN] : 0.f, x1 = OFF ? dp.W1[h * IN + 1] : 0.f;
@@ -73,30 +100,46 @@ __device__ __forceinline__ void stage_bf16_decoder(BfSmem& S, const DecPtrsB& dp
     }
 }
 
-// Writes this lane's four z channels of A-tile row `row` as bf16.
-__device__ __forceinline__ void put_z(BfSmem& S, int row, int l, float4 z) {
-    const __nv_bfloat162 lo = __floats2bfloat162_rn(z.x, z.y);
-    const __nv_bfloat162 hi = __floats2bfloat162_rn(z.z, z.w);
-    uint2 v;
-    v.x = *reinterpret_cast<const uint32_t*>(&lo);
-    v.y = *reinterpret_cast<const uint32_t*>(&hi);
-    *reinterpret_cast<uint2*>(S.A + tc::kmajor_offset(row, 4 * l, kKc)) = v;
+// Writes this lane's four z channels of A-tile row `row` as bf16 or, scaled,
+// as e4m3 (round to nearest, saturating at +-448).
+template <bool FP8>
+__device__ __forceinline__ void put_z(BfSmem& S, int row, int l, float4 z, float zs) {
+    if constexpr (FP8) {
+        const __nv_fp8x4_e4m3 q(make_float4(z.x * zs, z.y * zs, z.z * zs, z.w * zs));
+        *reinterpret_cast<uint32_t*>(S.A + tc::kmajor_offset8(row, 4 * l, kFeatDim / 16)) =
+            *reinterpret_cast<const uint32_t*>(&q);
+    } else {
+        const __nv_bfloat162 lo = __floats2bfloat162_rn(z.x, z.y);
+        const __nv_bfloat162 hi = __floats2bfloat162_rn(z.z, z.w);
+        uint2 v;
+        v.x = *reinterpret_cast<const uint32_t*>(&lo);
+        v.y = *reinterpret_cast<const uint32_t*>(&hi);
+        *reinterpret_cast<uint2*>(S.A + tc::kmajor_offset(row, 4 * l, kKc)) = v;
+    }
 }
 
 // Issues the tile's MMA (thread 0) and waits for it (all threads); returns
 // false if the wait expired.
+template <bool FP8>
 __device__ __forceinline__ bool mma_tile(BfSmem& S, uint32_t taddr, uint32_t& phase) {
     tc::fence_proxy_async_smem();
     tc::fence_before_sync();
     __syncthreads();
     if (threadIdx.x == 0) {
         tc::fence_after_sync();
-        const uint32_t idesc = tc::idesc_bf16_f32(kTM, kHidden);
         const uint32_t a0 = tc::smem_u32(S.A), b0 = tc::smem_u32(S.B);
+        if constexpr (FP8) {
+            // K = 32 e4m3 elements = 2 chunks of 16 B per row: one instruction
+            constexpr uint32_t sbo8 = 128 * (kFeatDim / 16);
+            tc::mma_e4m3(taddr, tc::smem_desc_kmajor(a0, kLbo, sbo8), tc::smem_desc_kmajor(b0, kLbo, sbo8),
+                         tc::idesc_e4m3_f32(kTM, kHidden), false);
+        } else {
+            const uint32_t idesc = tc::idesc_bf16_f32(kTM, kHidden);
 #pragma unroll
-        for (int ks = 0; ks < kFeatDim / 16; ++ks)
-            tc::mma_bf16(taddr, tc::smem_desc_kmajor(a0 + ks * 256, kLbo, kSbo),
-                         tc::smem_desc_kmajor(b0 + ks * 256, kLbo, kSbo), idesc, ks > 0);
+            for (int ks = 0; ks < kFeatDim / 16; ++ks)
+                tc::mma_bf16(taddr, tc::smem_desc_kmajor(a0 + ks * 256, kLbo, kSbo),
+                             tc::smem_desc_kmajor(b0 + ks * 256, kLbo, kSbo), idesc, ks > 0);
+        }
         tc::mma_commit(&S.bar);
     }
     const bool ok = tc::mbar_wait(&S.bar, phase, kWaitPolls);
@@ -118,7 +161,7 @@ __device__ __forceinline__ float epilogue(const BfSmem& S, uint32_t taddr, float
 #pragma unroll
         for (int i = 0; i < 32; ++i) {
             const float4 e = S.epi[c0 + i];
-            float pre = v[i] + e.x;
+            float pre = fmaf(v[i], S.acc_scale, e.x);
             if constexpr (IN != kFeatDim) pre = fmaf(e.z, x0, fmaf(e.w, x1, fmaf(S.wx2[c0 + i], x2, pre)));
             out = fmaf(e.y, fmaxf(pre, 0.0f), out);
         }
@@ -148,7 +191,7 @@ __device__ __forceinline__ void teardown_tmem(BfSmem& S, uint32_t taddr, bool dr
 // ---------------------------------------------------------------------------
 // sphere tracing, BF16 decode
 // ---------------------------------------------------------------------------
-template <typename T, int IN>
+template <typename T, int IN, bool FP8>
 __global__ void __launch_bounds__(kTM, kCtasPerSm) k_trace_bf16(const DecPtrsB dp, const Tables tb, const TraceArgs A,
                                                       int* __restrict__ err) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -156,7 +199,7 @@ __global__ void __launch_bounds__(kTM, kCtasPerSm) k_trace_bf16(const DecPtrsB d
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int g = lane >> 3, l = lane & 7, gbase = g << 3;
     const unsigned gmask = 0xffu << gbase;
-    stage_bf16_decoder<IN>(S, dp);
+    stage_bf16_decoder<IN, FP8>(S, dp);
     setup_tmem(S);
     const uint32_t taddr = S.taddr;
     uint32_t phase = 0;
@@ -183,9 +226,9 @@ __global__ void __launch_bounds__(kTM, kCtasPerSm) k_trace_bf16(const DecPtrsB d
             const float s2 = __shfl_sync(0xffffffffu, q2, s);
             float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
             if (sact) z = gather_slot<T>(tb, A.D, svox, sijk, s0, s1, s2, gmask, gbase, l);
-            put_z(S, warp * 32 + s, l, z);
+            put_z<FP8>(S, warp * 32 + s, l, z, dp.z_scale);
         }
-        const bool ok = mma_tile(S, taddr, phase);
+        const bool ok = mma_tile<FP8>(S, taddr, phase);
         if (!__syncthreads_and(ok)) {
             if (threadIdx.x == 0) atomicExch(err, kStatusTimeout);
             drained = false;
@@ -201,7 +244,7 @@ __global__ void __launch_bounds__(kTM, kCtasPerSm) k_trace_bf16(const DecPtrsB d
 // ---------------------------------------------------------------------------
 // sdf_query, BF16 decode: tiles of 128 points
 // ---------------------------------------------------------------------------
-template <typename T, int IN>
+template <typename T, int IN, bool FP8>
 __global__ void __launch_bounds__(kTM, kCtasPerSm) k_query_bf16(const DecPtrsB dp, const Tables tb, const float* __restrict__ x,
                                                       long long Q, int D, float* __restrict__ sdf,
                                                       int8_t* __restrict__ deepest, int* __restrict__ err) {
@@ -210,7 +253,7 @@ __global__ void __launch_bounds__(kTM, kCtasPerSm) k_query_bf16(const DecPtrsB d
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int g = lane >> 3, l = lane & 7, gbase = g << 3;
     const unsigned gmask = 0xffu << gbase;
-    stage_bf16_decoder<IN>(S, dp);
+    stage_bf16_decoder<IN, FP8>(S, dp);
     setup_tmem(S);
     const uint32_t taddr = S.taddr;
     uint32_t phase = 0;
@@ -240,9 +283,9 @@ __global__ void __launch_bounds__(kTM, kCtasPerSm) k_query_bf16(const DecPtrsB d
             const float s2 = __shfl_sync(0xffffffffu, q2, s);
             float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
             if (sdd >= kFirstFeatureDepth) z = gather_slot<T>(tb, sdd, svox, sijk, s0, s1, s2, gmask, gbase, l);
-            put_z(S, warp * 32 + s, l, z);
+            put_z<FP8>(S, warp * 32 + s, l, z, dp.z_scale);
         }
-        const bool ok = mma_tile(S, taddr, phase);
+        const bool ok = mma_tile<FP8>(S, taddr, phase);
         if (!__syncthreads_and(ok)) {
             if (threadIdx.x == 0) atomicExch(err, kStatusTimeout);
             drained = false;
@@ -257,7 +300,9 @@ __global__ void __launch_bounds__(kTM, kCtasPerSm) k_query_bf16(const DecPtrsB d
     teardown_tmem(S, taddr, drained, phase);
 }
 
-DecPtrsB bptrs(const nglod_decoder* dec) { return DecPtrsB{dec->W1, dec->b1, dec->W2, dec->b2}; }
+DecPtrsB bptrs(const nglod_decoder* dec, float z_scale) {
+    return DecPtrsB{dec->W1, dec->b1, dec->W2, dec->b2, z_scale};
+}
 
 template <typename K>
 void prefer_l1(K kernel) {
@@ -265,53 +310,71 @@ void prefer_l1(K kernel) {
     cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 40);
 }
 
-template <typename T, int IN>
-void go_trace(const DecPtrsB& P, const Tables& tb, const TraceArgs& A, int* err, int grid, cudaStream_t st) {
-    static bool once = (prefer_l1(k_trace_bf16<T, IN>), true);
+template <typename T, int IN, bool FP8>
+void go_trace1(const DecPtrsB& P, const Tables& tb, const TraceArgs& A, int* err, int grid, cudaStream_t st) {
+    static bool once = (prefer_l1(k_trace_bf16<T, IN, FP8>), true);
     (void)once;
-    k_trace_bf16<T, IN><<<grid, kTM, kDynSmem, st>>>(P, tb, A, err);
+    k_trace_bf16<T, IN, FP8><<<grid, kTM, kDynSmem, st>>>(P, tb, A, err);
+}
+
+template <typename T, int IN>
+void go_trace(const DecPtrsB& P, const Tables& tb, const TraceArgs& A, int* err, int grid, bool fp8, cudaStream_t st) {
+    if (fp8) go_trace1<T, IN, true>(P, tb, A, err, grid, st);
+    else go_trace1<T, IN, false>(P, tb, A, err, grid, st);
+}
+
+template <typename T, int IN, bool FP8>
+void go_query1(const DecPtrsB& P, const Tables& tb, const float* x, long long Q, int D, float* sdf, int8_t* deep,
+               int* err, int grid, cudaStream_t st) {
+    static bool once = (prefer_l1(k_query_bf16<T, IN, FP8>), true);
+    (void)once;
+    k_query_bf16<T, IN, FP8><<<grid, kTM, kDynSmem, st>>>(P, tb, x, Q, D, sdf, deep, err);
 }
 
 template <typename T, int IN>
 void go_query(const DecPtrsB& P, const Tables& tb, const float* x, long long Q, int D, float* sdf, int8_t* deep,
-              int* err, int grid, cudaStream_t st) {
-    static bool once = (prefer_l1(k_query_bf16<T, IN>), true);
-    (void)once;
-    k_query_bf16<T, IN><<<grid, kTM, kDynSmem, st>>>(P, tb, x, Q, D, sdf, deep, err);
+              int* err, int grid, bool fp8, cudaStream_t st) {
+    if (fp8) go_query1<T, IN, true>(P, tb, x, Q, D, sdf, deep, err, grid, st);
+    else go_query1<T, IN, false>(P, tb, x, Q, D, sdf, deep, err, grid, st);
 }
 
 }  // namespace
 
 int launch_trace_bf16(const nglod_svo* svo, const nglod_decoder* dec, const Tables& tb, const TraceArgs& A,
-                      bool f16, cudaStream_t st) {
+                      bool f16, float fp8_z_absmax, cudaStream_t st) {
+    const bool fp8 = fp8_z_absmax > 0.0f;
     static_assert(sizeof(BfSmem) <= kDynSmem, "shared layout");
     // the error word shares the workspace header with the ray queue
     int* err = A.queue + 1;
     const int grid = svo->num_sms * kCtasPerSm;
-    const DecPtrsB P = bptrs(dec);
+    const DecPtrsB P = bptrs(dec, fp8 ? kE4M3Max / fp8_z_absmax : 1.0f);
     if (dec->in_dim == 35) {
-        if (f16) go_trace<__half, 35>(P, tb, A, err, grid, st); else go_trace<float, 35>(P, tb, A, err, grid, st);
+        if (f16) go_trace<__half, 35>(P, tb, A, err, grid, fp8, st);
+        else go_trace<float, 35>(P, tb, A, err, grid, fp8, st);
     } else {
-        if (f16) go_trace<__half, 32>(P, tb, A, err, grid, st); else go_trace<float, 32>(P, tb, A, err, grid, st);
+        if (f16) go_trace<__half, 32>(P, tb, A, err, grid, fp8, st);
+        else go_trace<float, 32>(P, tb, A, err, grid, fp8, st);
     }
     NGLOD_CUDA(cudaGetLastError());
     return NGLOD_OK;
 }
 
 int launch_query_bf16(const nglod_svo* svo, const Tables& tb, const nglod_decoder* dec, const float* x,
-                      long long Q, int D, float* sdf, int8_t* deepest, bool f16, cudaStream_t st) {
+                      long long Q, int D, float* sdf, int8_t* deepest, bool f16, float fp8_z_absmax,
+                      cudaStream_t st) {
+    const bool fp8 = fp8_z_absmax > 0.0f;
     // the octree handle's device status word records an expired wait
     int* err = svo->dstatus;
     NGLOD_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
     const long long tiles = (Q + kTM - 1) / kTM;
     const int grid = (int)std::max<long long>(1, std::min<long long>(tiles, (long long)svo->num_sms * kCtasPerSm));
-    const DecPtrsB P = bptrs(dec);
+    const DecPtrsB P = bptrs(dec, fp8 ? kE4M3Max / fp8_z_absmax : 1.0f);
     if (dec->in_dim == 35) {
-        if (f16) go_query<__half, 35>(P, tb, x, Q, D, sdf, deepest, err, grid, st);
-        else go_query<float, 35>(P, tb, x, Q, D, sdf, deepest, err, grid, st);
+        if (f16) go_query<__half, 35>(P, tb, x, Q, D, sdf, deepest, err, grid, fp8, st);
+        else go_query<float, 35>(P, tb, x, Q, D, sdf, deepest, err, grid, fp8, st);
     } else {
-        if (f16) go_query<__half, 32>(P, tb, x, Q, D, sdf, deepest, err, grid, st);
-        else go_query<float, 32>(P, tb, x, Q, D, sdf, deepest, err, grid, st);
+        if (f16) go_query<__half, 32>(P, tb, x, Q, D, sdf, deepest, err, grid, fp8, st);
+        else go_query<float, 32>(P, tb, x, Q, D, sdf, deepest, err, grid, fp8, st);
     }
     NGLOD_CUDA(cudaGetLastError());
     int h = 0;

@@ -245,8 +245,9 @@ int launch_normals(const nglod_decoder* dec, const Tables& tb, const TraceArgs& 
 inline size_t trace_ws_hit_vox_offset() { return 256; }
 inline size_t trace_ws_hit_list_offset(long long R) { return 256 + ((sizeof(int32_t) * (size_t)R + 255) / 256) * 256; }
 int launch_trace_bf16(const nglod_svo* svo, const nglod_decoder* dec, const Tables& tb, const TraceArgs& A,
-                      bool f16, cudaStream_t st);
+                      bool f16, float fp8_z_absmax, cudaStream_t st);
 int launch_query_bf16(const nglod_svo* svo, const Tables& tb, const nglod_decoder* dec, const float* x,
-                      long long Q, int D, float* sdf, int8_t* deepest, bool f16, cudaStream_t st);
+                      long long Q, int D, float* sdf, int8_t* deepest, bool f16, float fp8_z_absmax,
+                      cudaStream_t st);
 
 }  // namespace nglod

@@ -17,14 +17,15 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libnglod.so")
 
 NGLOD_OK, ERR_INVALID_ARG, ERR_CAPACITY, ERR_CUDA, ERR_OOM, ERR_TIMEOUT, ERR_NOT_SUPPORTED = range(7)
-F32, F16, BF16 = 0, 1, 2
+F32, F16, BF16, FP8 = 0, 1, 2, 3
 BF16_DECODE = True          # the tensor-core (tcgen05) decode is built
 FIRST_FEATURE_DEPTH = 3
 
 EXPORTS = ["nglod_last_error", "svo_build", "svo_info", "svo_device_arrays", "svo_read_arrays", "svo_free",
            "svo_trace_rays_workspace", "svo_trace_rays", "sdf_query", "sphere_trace_workspace",
            "sphere_trace", "sphere_trace_status", "trace_normals", "svo_trace_rays_noalloc",
-           "svo_trace_rays_sizes", "sdf_backward", "sdf_l2_backward", "nglod_adam_step"]
+           "svo_trace_rays_sizes", "sdf_backward", "sdf_l2_backward", "nglod_adam_step",
+           "nglod_features_absmax"]
 
 
 class NglodError(RuntimeError):
@@ -34,7 +35,8 @@ class NglodError(RuntimeError):
 
 
 class _Features(C.Structure):
-    _fields_ = [("feats", C.c_void_p * 8), ("dtype", C.c_int), ("m", C.c_int), ("num_lods", C.c_int)]
+    _fields_ = [("feats", C.c_void_p * 8), ("dtype", C.c_int), ("m", C.c_int), ("num_lods", C.c_int),
+                ("fp8_z_absmax", C.c_float)]
 
 
 class _Decoder(C.Structure):
@@ -78,6 +80,7 @@ def lib():
         L.svo_trace_rays_sizes.argtypes = [P, P, i32, P]
         L.sdf_backward.argtypes = [P, P, P, P, i64, C.c_uint32, P, P, P, P, P, P, P, i32, P]
         L.sdf_l2_backward.argtypes = [P, P, P, P, P, i64, C.c_uint32, C.c_float, P, P, P, P, P, P, P]
+        L.nglod_features_absmax.argtypes = [P, P, i32, P, P]
         L.nglod_adam_step.argtypes = [P, P, P, P, i64, C.c_float, C.c_float, C.c_float, C.c_float, i32, P]
         L.svo_trace_rays_noalloc.argtypes = [P, P, P, i64, i32, P, P, P, i64, P, P]
         _lib = L
@@ -170,6 +173,15 @@ class Features:
         self.tables = [torch.as_tensor(np.asarray(t)).to(device=device, dtype=tdt).contiguous()
                        for t in tables]
         self.m = int(self.tables[0].shape[1])
+        self.z_absmax = 0.0
+
+    def set_fp8_bound(self, svo, lod: int, stream=None):
+        """Computes the |z| bound the FP8 decode scales by (library reduction)."""
+        out = C.c_float(0.0)
+        fc = self.c()
+        _check(lib().nglod_features_absmax(svo.h, C.byref(fc), int(lod), C.byref(out), C.c_void_p(_stream(stream))))
+        self.z_absmax = float(out.value)
+        return self.z_absmax
 
     def c(self) -> _Features:
         f = _Features()
@@ -178,6 +190,7 @@ class Features:
         f.dtype = F32 if self.dtype == "f32" else F16
         f.m = self.m
         f.num_lods = len(self.tables)
+        f.fp8_z_absmax = getattr(self, "z_absmax", 0.0)
         return f
 
 
@@ -277,7 +290,7 @@ def sdf_query(svo: SVO, feats: Features, dec: DecoderDev, x, lod: int, decode: s
     g = torch.empty((Q, 3), dtype=torch.float32, device=x.device) if grad else None
     fc, dc = feats.c(), dec.c()
     _check(lib().sdf_query(svo.h, C.byref(fc), C.byref(dc), x.data_ptr(), Q, lod,
-                           {"f32": F32, "bf16": BF16}[decode], sdf.data_ptr(), _ptr(dp), _ptr(g),
+                           {"f32": F32, "bf16": BF16, "fp8": FP8}[decode], sdf.data_ptr(), _ptr(dp), _ptr(g),
                            C.c_void_p(_stream(stream))))
     out = [sdf]
     if deepest:
@@ -301,7 +314,7 @@ def sphere_trace(svo: SVO, feats: Features, dec: DecoderDev, o, d, lists: RayLis
                    steps=torch.empty(R, dtype=torch.int32, device=dev),
                    normal=torch.empty((R, 3), dtype=torch.float32, device=dev) if normals else None,
                    work=torch.empty(max(lib().sphere_trace_workspace(R), 1), dtype=torch.uint8, device=dev))
-    p = _TraceParams(eps, far, max_steps, int(osc), {"f32": F32, "bf16": BF16}[decode], int(normals))
+    p = _TraceParams(eps, far, max_steps, int(osc), {"f32": F32, "bf16": BF16, "fp8": FP8}[decode], int(normals))
     fc, dc = feats.c(), dec.c()
     _check(lib().sphere_trace(svo.h, C.byref(fc), C.byref(dc), o.data_ptr(), d.data_ptr(), R, lists.lod,
                               C.byref(p), lists.ray_offsets.data_ptr(), lists.voxel_id.data_ptr(),
