@@ -8,6 +8,8 @@ One step = one frame: svo_trace_rays -> sphere_trace -> trace_normals over
 between timed steps, outside the timed events.  Prints one JSON line.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+    python bench.py --workload batch     # many scenes per frame: per-scene calls vs one
+                                         # persistent launch vs its CUDA graph
 
 Under torchrun every rank renders its own frame (independent replicas, no
 collective on the data path); rank 0 prints the whole-job throughput.
@@ -49,6 +51,9 @@ def parse():
     p.add_argument("--height", type=int, default=1080)
     p.add_argument("--decode", choices=["both", "all", "f32", "bf16", "fp8"], default="all")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--workload", choices=["frame", "batch"], default="frame",
+                   help="frame: the 1080p LOD5 CSG-64 frame (default); batch: 32 seeded CSG scenes of "
+                        "U{8..256} primitives at LOD U{3..6}, images U{128..1024} a side, BF16 decode")
     return p.parse_args()
 
 
@@ -397,6 +402,10 @@ def main():
         if rank == 0:
             run_reference(args)
         return
+    if args.workload == "batch":
+        if rank == 0:
+            run_batch(args)
+        return
     if world > 1:
         import torch
         import torch.distributed as td
@@ -425,7 +434,7 @@ def main():
             "traversal_roofline": traversal_roofline(W, r, head, peaks),
             "clocks": clocks,
             "e2e": e2e,
-            "gpu_launches": args.steps * len(modes) * (W["lod"] + 7),   # prep + (lod+3) levels + offsets + trace + normals
+            "gpu_launches": args.steps * len(modes) * (W["lod"] + 6),   # prep + (lod+2) levels + offsets + trace + normals
         }
         if "bf16" in res and "f32" in res:
             line["bf16_speedup"] = res["f32"]["ms_per_step"] / res["bf16"]["ms_per_step"]

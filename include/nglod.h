@@ -190,6 +190,22 @@ int svo_trace_rays_noalloc(const nglod_svo* svo, const float* o, const float* d,
                            float* t_range, int64_t hit_capacity, int64_t* h_stats,
                            void* stream);
 
+/* svo_trace_rays_async -- svo_trace_rays without the final host read-back,
+ * so the whole traversal is enqueued on the stream and can be captured in a
+ * CUDA graph.  The caller sizes pair_capacity and hit_capacity (e.g. from an
+ * earlier svo_trace_rays of the same frame); overflow or an expired wait is
+ * recorded in the workspace and reported by svo_trace_rays_check, and the
+ * outputs are then unspecified.  Arguments as svo_trace_rays. */
+int svo_trace_rays_async(const nglod_svo* svo, const float* o, const float* d, int64_t R,
+                         int target_lod, void* work, size_t work_bytes, int64_t pair_capacity,
+                         int32_t* ray_offsets, int32_t* voxel_id, float* t_range,
+                         int64_t hit_capacity, void* stream);
+
+/* svo_trace_rays_check -- synchronises and reports the status of the last
+ * traversal enqueued in this workspace (as svo_trace_rays would have): OK,
+ * NGLOD_ERR_CAPACITY (h_stats = sizes needed) or NGLOD_ERR_TIMEOUT. */
+int svo_trace_rays_check(const void* work, int target_lod, int64_t* h_stats, void* stream);
+
 /* svo_trace_rays_sizes -- list sizes of the last svo_trace_rays that used this
  * workspace (synchronises the stream): h_sizes[dp] for dp = 0..n-1 is the
  * number of ray/voxel pairs at depth dp that Decide kept (dp = 0: rays whose
@@ -302,6 +318,52 @@ int nglod_adam_step(float* param, float* grad, float* m, float* v, int64_t n, fl
  * NGLOD_ERR_TIMEOUT if a bounded tensor-core wait of the BF16 decode expired
  * (its outputs are then invalid). */
 int sphere_trace_status(const void* work, void* stream);
+
+/* One image of a batch: an octree with its features and the decoder of the
+ * LOD it is traced at, its rays and their lists (svo_trace_rays at that LOD),
+ * a trace workspace (>= sphere_trace_workspace(R)) and its outputs. */
+typedef struct {
+    const nglod_svo* svo;
+    nglod_features feats;
+    nglod_decoder dec;        /* jobs with the same dec.W1 pointer share one group */
+    int lod;
+    const float* o;
+    const float* d;
+    int64_t R;
+    const int32_t* ray_offsets;
+    const int32_t* voxel_id;
+    const float* t_range;
+    void* work;
+    size_t work_bytes;
+    float* t_hit;
+    uint8_t* hit;
+    int32_t* steps;           /* nullable */
+    float* normal;            /* nullable */
+} nglod_trace_job;
+
+typedef struct nglod_batch nglod_batch;   /* opaque */
+
+/* sphere_trace_batch_create -- fixes a batch of jobs (their buffers must stay
+ * valid) for tracing many scenes and images of uneven size in ONE persistent
+ * launch (the same stepping rules as sphere_trace, Sec. 3.4 / A.4).  Jobs are
+ * grouped by decoder; within a group one ray queue spans all jobs' rays.
+ * All jobs share params, in_dim and the feature dtype.  ctas_per_sm: resident
+ * CTAs per SM of the trace kernel (0 = default; 1..4 tensor-core, 1..3 FP32),
+ * the knob the autotuner sets.  Uploads the job table (synchronises). */
+int sphere_trace_batch_create(const nglod_trace_job* jobs, int num_jobs,
+                              const nglod_trace_params* params, int ctas_per_sm, void* stream,
+                              nglod_batch** out);
+
+/* sphere_trace_batch_run -- enqueues one batched trace (reset, the persistent
+ * trace kernel, then each job's normals if requested); no host
+ * synchronisation, so it can be captured in a CUDA graph. */
+int sphere_trace_batch_run(nglod_batch* batch, void* stream);
+
+/* sphere_trace_batch_status -- synchronises; NGLOD_ERR_TIMEOUT if a bounded
+ * tensor-core wait of the last run expired. */
+int sphere_trace_batch_status(nglod_batch* batch, void* stream);
+
+void sphere_trace_batch_free(nglod_batch* batch);
 
 /* trace_normals -- surface normals of the rays a preceding sphere_trace call
  * (same work buffer, same stream, want_normals = 0 or 1) marked as hits:

@@ -356,6 +356,57 @@ __global__ void __launch_bounds__(kThreads, 3) k_trace_f32(const DecPtrs dp, con
 
 DecPtrs dec_ptrs(const nglod_decoder* dec) { return DecPtrs{dec->W1, dec->b1, dec->W2, dec->b2}; }
 
+// Batched tracing, FP32 decode: groups of jobs sharing a decoder, each warp
+// drains a group's ray queue independently (no CTA-wide barrier inside a group).
+template <typename T, int IN>
+__global__ void __launch_bounds__(kThreads, 3) k_trace_batch_f32(const TraceJob* __restrict__ jobs,
+                                                                  const JobGroup* __restrict__ groups, int ngroups) {
+    __shared__ __align__(16) float zbuf[kWarps][32 * kZStride];
+    __shared__ __align__(16) SmemDecoder sd;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = lane >> 3, l = lane & 7, gbase = g << 3;
+    const unsigned gmask = 0xffu << gbase;
+    float* zb = zbuf[warp];
+    for (int gi = 0; gi < ngroups; ++gi) {
+        const JobGroup G = groups[gi];
+        __syncthreads();
+        stage_decoder<IN>(sd, G.W1, G.b1, G.W2);
+        __syncthreads();
+        RaySlot S;
+        S.ray = -1;
+        S.hit_ray = -1;
+        S.job = G.j0;
+        RayQueue Qu;
+        Qu.init();
+        for (;;) {
+            refill_batch(S, Qu, G, jobs, lane);
+            if (__ballot_sync(0xffffffffu, S.ray >= 0) == 0u) break;
+            const bool act = S.ray >= 0;
+            const float x0 = fmaf(S.t, S.dx, S.ox), x1 = fmaf(S.t, S.dy, S.oy), x2 = fmaf(S.t, S.dz, S.oz);
+            const float q0 = __fadd_rn(x0, 1.0f), q1 = __fadd_rn(x1, 1.0f), q2 = __fadd_rn(x2, 1.0f);
+#pragma unroll 1
+            for (int r = 0; r < 8; ++r) {
+                const int s = r * 4 + g;
+                const int sact = __shfl_sync(0xffffffffu, act ? 1 : 0, s);
+                const int sjob = __shfl_sync(0xffffffffu, S.job, s);
+                const int svox = __shfl_sync(0xffffffffu, S.vox, s);
+                const uint32_t sijk = __shfl_sync(0xffffffffu, S.ijk, s);
+                const float s0 = __shfl_sync(0xffffffffu, q0, s);
+                const float s1 = __shfl_sync(0xffffffffu, q1, s);
+                const float s2 = __shfl_sync(0xffffffffu, q2, s);
+                float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (sact) z = gather_slot<T>(jobs[sjob].tb, jobs[sjob].A.D, svox, sijk, s0, s1, s2, gmask, gbase, l);
+                *reinterpret_cast<float4*>(zb + s * kZStride + 4 * l) = z;
+            }
+            __syncwarp();
+            const float dhat = mlp_f32<IN>(sd, G.b2, zb + lane * kZStride, x0, x1, x2);
+            __syncwarp();
+            if (act) step_update(S, dhat, jobs[S.job].A, jobs[S.job].tb);
+            publish_hits_batch(S, jobs);
+        }
+    }
+}
+
 template <typename T, int IN>
 void launch_trace_f32(const DecPtrs& P, const Tables& tb, const TraceArgs& A, int grid, cudaStream_t st) {
     k_trace_f32<T, IN><<<grid, kThreads, 0, st>>>(P, tb, A);
@@ -399,6 +450,20 @@ int launch_trace_fp32(const nglod_decoder* dec, const Tables& tb, const TraceArg
         if (f16) launch_trace_f32<__half, 35>(P, tb, A, grid, st); else launch_trace_f32<float, 35>(P, tb, A, grid, st);
     } else {
         if (f16) launch_trace_f32<__half, 32>(P, tb, A, grid, st); else launch_trace_f32<float, 32>(P, tb, A, grid, st);
+    }
+    NGLOD_CUDA(cudaGetLastError());
+    return NGLOD_OK;
+}
+
+int launch_trace_batch_f32(const TraceJob* jobs, const JobGroup* groups, int ngroups, int in_dim, bool f16,
+                           int ctas_per_sm, int sms, cudaStream_t st) {
+    const int grid = sms * std::max(1, std::min(ctas_per_sm > 0 ? ctas_per_sm : 3, 3));
+    if (in_dim == 35) {
+        if (f16) k_trace_batch_f32<__half, 35><<<grid, kThreads, 0, st>>>(jobs, groups, ngroups);
+        else k_trace_batch_f32<float, 35><<<grid, kThreads, 0, st>>>(jobs, groups, ngroups);
+    } else {
+        if (f16) k_trace_batch_f32<__half, 32><<<grid, kThreads, 0, st>>>(jobs, groups, ngroups);
+        else k_trace_batch_f32<float, 32><<<grid, kThreads, 0, st>>>(jobs, groups, ngroups);
     }
     NGLOD_CUDA(cudaGetLastError());
     return NGLOD_OK;

@@ -300,6 +300,87 @@ __global__ void __launch_bounds__(kTM, kCtasPerSm) k_query_bf16(const DecPtrsB d
     teardown_tmem(S, taddr, drained, phase);
 }
 
+template <typename K>
+void prefer_l1(K kernel);
+
+// ---------------------------------------------------------------------------
+// batched sphere tracing (tensor-core decode): groups of jobs, one decoder
+// per group, one persistent launch
+// ---------------------------------------------------------------------------
+template <typename T, int IN, bool FP8>
+__global__ void __launch_bounds__(kTM, kCtasPerSm) k_trace_batch(const TraceJob* __restrict__ jobs,
+                                                               const JobGroup* __restrict__ groups, int ngroups,
+                                                               int* __restrict__ err) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    BfSmem& S = *reinterpret_cast<BfSmem*>(smem_raw);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g8 = lane >> 3, l = lane & 7, gbase = g8 << 3;
+    const unsigned gmask = 0xffu << gbase;
+    if (threadIdx.x == 0) tc::mbar_init(&S.bar, 1);
+    if (warp == 0) {
+        tc::tmem_alloc(&S.taddr, kHidden);
+        tc::tmem_relinquish();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t taddr = S.taddr;
+    uint32_t phase = 0;
+    bool drained = true;
+    for (int gi = 0; gi < ngroups && drained; ++gi) {
+        const JobGroup G = groups[gi];
+        const DecPtrsB dp{G.W1, G.b1, G.W2, G.b2, G.z_scale};
+        __syncthreads();                      // the previous group's epilogues are done
+        stage_bf16_decoder<IN, FP8>(S, dp);
+        tc::fence_proxy_async_smem();
+        __syncthreads();
+        RaySlot st;
+        st.ray = -1;
+        st.hit_ray = -1;
+        st.job = G.j0;
+        RayQueue Qu;
+        Qu.init();
+        for (;;) {
+            refill_batch(st, Qu, G, jobs, lane);
+            const bool act = st.ray >= 0;
+            if (!__syncthreads_or(act)) break;
+            const float x0 = fmaf(st.t, st.dx, st.ox), x1 = fmaf(st.t, st.dy, st.oy), x2 = fmaf(st.t, st.dz, st.oz);
+            const float q0 = __fadd_rn(x0, 1.0f), q1 = __fadd_rn(x1, 1.0f), q2 = __fadd_rn(x2, 1.0f);
+#pragma unroll 1
+            for (int r = 0; r < 8; ++r) {
+                const int s = r * 4 + g8;
+                const int sact = __shfl_sync(0xffffffffu, act ? 1 : 0, s);
+                const int sjob = __shfl_sync(0xffffffffu, st.job, s);
+                const int svox = __shfl_sync(0xffffffffu, st.vox, s);
+                const uint32_t sijk = __shfl_sync(0xffffffffu, st.ijk, s);
+                const float s0 = __shfl_sync(0xffffffffu, q0, s);
+                const float s1 = __shfl_sync(0xffffffffu, q1, s);
+                const float s2 = __shfl_sync(0xffffffffu, q2, s);
+                float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (sact) z = gather_slot<T>(jobs[sjob].tb, jobs[sjob].A.D, svox, sijk, s0, s1, s2, gmask, gbase, l);
+                put_z<FP8>(S, warp * 32 + s, l, z, dp.z_scale);
+            }
+            const bool ok = mma_tile<FP8>(S, taddr, phase);
+            if (!__syncthreads_and(ok)) {
+                if (threadIdx.x == 0) atomicExch(err, kStatusTimeout);
+                drained = false;
+                break;
+            }
+            const float dhat = epilogue<IN>(S, taddr, dp.b2, x0, x1, x2);
+            if (act) step_update(st, dhat, jobs[st.job].A, jobs[st.job].tb);
+            publish_hits_batch(st, jobs);
+        }
+    }
+    teardown_tmem(S, taddr, drained, phase);
+}
+
+template <typename T, int IN, bool FP8>
+void go_batch1(const TraceJob* jobs, const JobGroup* groups, int ngroups, int* err, int grid, cudaStream_t st) {
+    static bool once = (prefer_l1(k_trace_batch<T, IN, FP8>), true);
+    (void)once;
+    k_trace_batch<T, IN, FP8><<<grid, kTM, kDynSmem, st>>>(jobs, groups, ngroups, err);
+}
+
 DecPtrsB bptrs(const nglod_decoder* dec, float z_scale) {
     return DecPtrsB{dec->W1, dec->b1, dec->W2, dec->b2, z_scale};
 }
@@ -384,4 +465,22 @@ int launch_query_bf16(const nglod_svo* svo, const Tables& tb, const nglod_decode
     return NGLOD_OK;
 }
 
+}  // namespace nglod
+
+namespace nglod {
+int launch_trace_batch_tc(const TraceJob* jobs, const JobGroup* groups, int ngroups, int in_dim, bool f16, bool fp8,
+                          int ctas_per_sm, int sms, int* err, cudaStream_t st) {
+    const int grid = sms * std::max(1, std::min(ctas_per_sm > 0 ? ctas_per_sm : kCtasPerSm, kCtasPerSm));
+#define NGLOD_GO(T, I, F) go_batch1<T, I, F>(jobs, groups, ngroups, err, grid, st)
+    if (in_dim == 35) {
+        if (f16) { if (fp8) NGLOD_GO(__half, 35, true); else NGLOD_GO(__half, 35, false); }
+        else { if (fp8) NGLOD_GO(float, 35, true); else NGLOD_GO(float, 35, false); }
+    } else {
+        if (f16) { if (fp8) NGLOD_GO(__half, 32, true); else NGLOD_GO(__half, 32, false); }
+        else { if (fp8) NGLOD_GO(float, 32, true); else NGLOD_GO(float, 32, false); }
+    }
+#undef NGLOD_GO
+    NGLOD_CUDA(cudaGetLastError());
+    return NGLOD_OK;
+}
 }  // namespace nglod

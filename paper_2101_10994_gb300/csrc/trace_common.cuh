@@ -100,6 +100,7 @@ struct TraceArgs {
 struct RaySlot {
     int ray;
     int hit_ray;          // id of a ray this slot just finished as a hit, else -1
+    int job;              // batched tracing: the job the ray belongs to
     float ox, oy, oz, dx, dy, dz;
     float t, tin, tout, dprev;
     int cur, end, k, vox;
@@ -233,6 +234,72 @@ __device__ __forceinline__ void step_update(RaySlot& S, float dhat, const TraceA
     advance(S, A, tb);
 }
 
+// ---------------------------------------------------------------------------
+// Batched tracing: many (octree, features, rays) jobs in one persistent
+// launch.  Jobs sharing a decoder form a group; the kernel traces the groups
+// one after another (staging each group's decoder once), and inside a group
+// one ray queue spans all of its jobs' rays.
+// ---------------------------------------------------------------------------
+struct TraceJob {
+    TraceArgs A;             // per-job rays, lists, outputs, workspace words
+    Tables tb;               // per-job octree and feature tables
+    long long ray_base;      // index of the job's first ray in its group's queue
+};
+
+struct JobGroup {
+    int j0, j1;              // jobs [j0, j1)
+    long long nrays;
+    const float* W1;
+    const float* b1;
+    const float* W2;
+    float b2;
+    float z_scale;           // FP8 decode
+    int* queue;
+};
+
+// Gives every idle lane the next ray of the group (finishing empty-list rays
+// on the spot); a lane's job is found by binary search over the jobs' bases.
+__device__ __forceinline__ void refill_batch(RaySlot& S, RayQueue& Qu, const JobGroup& G,
+                                             const TraceJob* __restrict__ jobs, int lane) {
+    for (;;) {
+        const unsigned need = __ballot_sync(0xffffffffu, S.ray < 0);
+        if (need == 0u || Qu.exhausted) return;
+        if (Qu.next >= Qu.end) {
+            int s = 0;
+            if (lane == 0) s = atomicAdd(G.queue, 32);
+            s = __shfl_sync(0xffffffffu, s, 0);
+            if ((long long)s >= G.nrays) {
+                Qu.exhausted = true;
+                return;
+            }
+            Qu.next = s;
+            Qu.end = (int)min((long long)s + 32, G.nrays);
+        }
+        const int rank = __popc(need & ((1u << lane) - 1u));
+        const int avail = Qu.end - Qu.next;
+        if (S.ray < 0 && rank < avail) {
+            const long long gi = Qu.next + rank;
+            int lo = G.j0, hi = G.j1 - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (jobs[mid].ray_base <= gi) lo = mid; else hi = mid - 1;
+            }
+            S.job = lo;
+            start_ray(S, (int)(gi - jobs[lo].ray_base), jobs[lo].A, jobs[lo].tb);
+        }
+        Qu.next += min(__popc(need), avail);
+    }
+}
+
+// Appends finished hits to their own job's hit list.
+__device__ __forceinline__ void publish_hits_batch(RaySlot& S, const TraceJob* __restrict__ jobs) {
+    if (S.hit_ray >= 0) {
+        const TraceArgs& A = jobs[S.job].A;
+        A.hit_list[atomicAdd(A.hit_count, 1)] = S.hit_ray;
+    }
+    S.hit_ray = -1;
+}
+
 // Host-side entry points implemented per translation unit.
 int fill_tables(const nglod_svo* svo, const nglod_features* f, int lod, Tables& tb);
 int check_decoder(const nglod_decoder* dec);
@@ -249,5 +316,9 @@ int launch_trace_bf16(const nglod_svo* svo, const nglod_decoder* dec, const Tabl
 int launch_query_bf16(const nglod_svo* svo, const Tables& tb, const nglod_decoder* dec, const float* x,
                       long long Q, int D, float* sdf, int8_t* deepest, bool f16, float fp8_z_absmax,
                       cudaStream_t st);
+int launch_trace_batch_tc(const TraceJob* jobs, const JobGroup* groups, int ngroups, int in_dim, bool f16, bool fp8,
+                          int ctas_per_sm, int sms, int* err, cudaStream_t st);
+int launch_trace_batch_f32(const TraceJob* jobs, const JobGroup* groups, int ngroups, int in_dim, bool f16,
+                           int ctas_per_sm, int sms, cudaStream_t st);
 
 }  // namespace nglod

@@ -355,46 +355,50 @@ extern "C" size_t svo_trace_rays_workspace(int64_t R, int64_t pair_capacity) {
            align_up(sizeof(uint16_t) * n_in);
 }
 
-extern "C" int svo_trace_rays(const nglod_svo* svo, const float* o, const float* d, int64_t R,
-                              int target_lod, void* work, size_t work_bytes, int64_t pair_capacity,
-                              int32_t* ray_offsets, int32_t* voxel_id, float* t_range,
-                              int64_t hit_capacity, int64_t* h_stats, void* stream) {
-    cudaStream_t st = (cudaStream_t)stream;
-    if (!svo) return fail(NGLOD_ERR_INVALID_ARG, "svo_trace_rays: NULL octree");
+namespace nglod {
+namespace {
+
+// Enqueues the whole traversal on the stream (no host synchronisation).
+int enqueue_traversal(const nglod_svo* svo, const float* o, const float* d, int64_t R, int target_lod, void* work,
+                      size_t work_bytes, int64_t pair_capacity, int32_t* ray_offsets, int32_t* voxel_id,
+                      float* t_range, int64_t hit_capacity, cudaStream_t st, const char* who) {
+    const std::string w(who);
+    if (!svo) return fail(NGLOD_ERR_INVALID_ARG, w + ": NULL octree");
     const int D = target_lod + kFirstFeatureDepth - 1;
     if (target_lod < 1 || D >= svo->num_depths)
-        return fail(NGLOD_ERR_INVALID_ARG, "svo_trace_rays: target_lod outside 1.." +
+        return fail(NGLOD_ERR_INVALID_ARG, w + ": target_lod outside 1.." +
                                                std::to_string(svo->num_depths - kFirstFeatureDepth));
     if (R < 0 || R >= (1ll << 31) - 1 || pair_capacity < 0 || hit_capacity < 0)
-        return fail(NGLOD_ERR_INVALID_ARG, "svo_trace_rays: bad R or capacity");
-    if (!ray_offsets) return fail(NGLOD_ERR_INVALID_ARG, "svo_trace_rays: NULL ray_offsets");
-    if (h_stats) h_stats[0] = h_stats[1] = 0;
+        return fail(NGLOD_ERR_INVALID_ARG, w + ": bad R or capacity");
+    if (!ray_offsets) return fail(NGLOD_ERR_INVALID_ARG, w + ": NULL ray_offsets");
+    if (!work) return fail(NGLOD_ERR_INVALID_ARG, w + ": NULL workspace");
+    if (work_bytes < svo_trace_rays_workspace(R, pair_capacity))
+        return fail(NGLOD_ERR_CAPACITY, w + ": workspace smaller than svo_trace_rays_workspace()");
+    if (((uintptr_t)work & 255u) != 0) return fail(NGLOD_ERR_INVALID_ARG, w + ": work must be 256-B aligned");
+    Counters* ctr = (Counters*)work;
     if (R == 0) {
+        NGLOD_CUDA(cudaMemsetAsync(ctr, 0, sizeof(Counters), st));
         NGLOD_CUDA(cudaMemsetAsync(ray_offsets, 0, sizeof(int32_t), st));
         return NGLOD_OK;
     }
-    if (!o || !d || !work) return fail(NGLOD_ERR_INVALID_ARG, "svo_trace_rays: NULL input or workspace");
+    if (!o || !d) return fail(NGLOD_ERR_INVALID_ARG, w + ": NULL rays");
     if ((hit_capacity > 0 && (!voxel_id || !t_range)))
-        return fail(NGLOD_ERR_INVALID_ARG, "svo_trace_rays: NULL voxel_id / t_range");
-    if (work_bytes < svo_trace_rays_workspace(R, pair_capacity))
-        return fail(NGLOD_ERR_CAPACITY, "svo_trace_rays: workspace smaller than svo_trace_rays_workspace()");
-    if (((uintptr_t)work & 255u) != 0) return fail(NGLOD_ERR_INVALID_ARG, "svo_trace_rays: work must be 256-B aligned");
+        return fail(NGLOD_ERR_INVALID_ARG, w + ": NULL voxel_id / t_range");
 
-    char* w = (char*)work;
-    Counters* ctr = (Counters*)w;
-    w += align_up(sizeof(Counters));
-    RayPrep* rays = (RayPrep*)w;
-    w += align_up(sizeof(RayPrep) * (size_t)R);
+    char* wp = (char*)work;
+    wp += align_up(sizeof(Counters));
+    RayPrep* rays = (RayPrep*)wp;
+    wp += align_up(sizeof(RayPrep) * (size_t)R);
     int2* buf[2];
-    buf[0] = (int2*)w;
-    w += align_up(sizeof(int2) * (size_t)pair_capacity);
-    buf[1] = (int2*)w;
-    w += align_up(sizeof(int2) * (size_t)pair_capacity);
-    long long* chunk_cnt = (long long*)w;
-    w += align_up(sizeof(unsigned long long) * kMaxGrid);
-    unsigned* arrive = (unsigned*)w;
-    w += align_up(sizeof(unsigned) * (kMaxDepth + 2));
-    uint16_t* rec = (uint16_t*)w;
+    buf[0] = (int2*)wp;
+    wp += align_up(sizeof(int2) * (size_t)pair_capacity);
+    buf[1] = (int2*)wp;
+    wp += align_up(sizeof(int2) * (size_t)pair_capacity);
+    long long* chunk_cnt = (long long*)wp;
+    wp += align_up(sizeof(unsigned long long) * kMaxGrid);
+    unsigned* arrive = (unsigned*)wp;
+    wp += align_up(sizeof(unsigned) * (kMaxDepth + 2));
+    uint16_t* rec = (uint16_t*)wp;
 
     const int sms = svo->num_sms;
     NGLOD_CUDA(cudaMemsetAsync(ctr, 0, sizeof(Counters), st));
@@ -419,38 +423,80 @@ extern "C" int svo_trace_rays(const nglod_svo* svo, const float* o, const float*
         xs.rec = rec;
         xs.chunk_cnt = chunk_cnt;
         xs.arrive = arrive + dp;
-        void* args[] = {(void*)&lp, (void*)&xs};
-        if (dp + 1 == D) {
-            const int grid = std::min(sms * level_ctas_per_sm<true>(), kMaxGrid);
-            NGLOD_CUDA(cudaLaunchCooperativeKernel((const void*)k_level<true>, dim3(grid), dim3(kThreads), args,
-                                                   (size_t)stage_bytes<true>(), st));
+        const bool fin = dp + 1 == D;
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeCooperative;   // every CTA resident (one grid barrier)
+        attr[0].val.cooperative = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        cfg.blockDim = dim3(kThreads);
+        cfg.stream = st;
+        if (fin) {
+            cfg.gridDim = dim3(std::min(sms * level_ctas_per_sm<true>(), kMaxGrid));
+            cfg.dynamicSmemBytes = stage_bytes<true>();
+            NGLOD_CUDA(cudaLaunchKernelEx(&cfg, k_level<true>, lp, xs));
         } else {
-            const int grid = std::min(sms * level_ctas_per_sm<false>(), kMaxGrid);
-            NGLOD_CUDA(cudaLaunchCooperativeKernel((const void*)k_level<false>, dim3(grid), dim3(kThreads), args,
-                                                   (size_t)stage_bytes<false>(), st));
+            cfg.gridDim = dim3(std::min(sms * level_ctas_per_sm<false>(), kMaxGrid));
+            cfg.dynamicSmemBytes = stage_bytes<false>();
+            NGLOD_CUDA(cudaLaunchKernelEx(&cfg, k_level<false>, lp, xs));
         }
     }
     k_ray_offsets<<<std::min<long long>((R + kThreads) / kThreads, (long long)sms * 16), kThreads, 0, st>>>(
         (const int32_t*)buf[D & 1], ctr, D, R, std::min<long long>(hit_capacity, pair_capacity), ray_offsets);
     NGLOD_CUDA(cudaGetLastError());
+    return NGLOD_OK;
+}
+
+// Reads the counters of a finished traversal and maps them to a status.
+int read_traversal(const void* work, int D, int64_t* h_stats, cudaStream_t st, const char* who) {
     Counters h;
-    NGLOD_CUDA(cudaMemcpyAsync(&h, ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
+    NGLOD_CUDA(cudaMemcpyAsync(&h, work, sizeof(Counters), cudaMemcpyDeviceToHost, st));
     NGLOD_CUDA(cudaStreamSynchronize(st));
     const long long H = h.count[D];
     if (h_stats) {
-        h_stats[0] = h.status == kStatusOk || H > 0 ? H : 0;
+        h_stats[0] = H;
         h_stats[1] = h.max_pairs;
     }
     if (h.status == kStatusTimeout)
-        return fail(NGLOD_ERR_TIMEOUT, "svo_trace_rays: scan look-back wait expired");
+        return fail(NGLOD_ERR_TIMEOUT, std::string(who) + ": grid barrier wait expired");
     if (h.status == kStatusOverflow) {
         long long need = 0;
         for (int dp = 1; dp < D; ++dp) need = std::max(need, h.count[dp]);
         if (h_stats) h_stats[1] = std::max<long long>(need, h.max_pairs);
-        return fail(NGLOD_ERR_CAPACITY, "svo_trace_rays: list larger than capacity (pairs " +
+        return fail(NGLOD_ERR_CAPACITY, std::string(who) + ": list larger than capacity (pairs " +
                                             std::to_string(need) + ", hits " + std::to_string(H) + ")");
     }
     return NGLOD_OK;
+}
+
+}  // namespace
+}  // namespace nglod
+
+extern "C" int svo_trace_rays(const nglod_svo* svo, const float* o, const float* d, int64_t R, int target_lod,
+                              void* work, size_t work_bytes, int64_t pair_capacity, int32_t* ray_offsets,
+                              int32_t* voxel_id, float* t_range, int64_t hit_capacity, int64_t* h_stats,
+                              void* stream) {
+    cudaStream_t st = (cudaStream_t)stream;
+    if (h_stats) h_stats[0] = h_stats[1] = 0;
+    int rc = enqueue_traversal(svo, o, d, R, target_lod, work, work_bytes, pair_capacity, ray_offsets, voxel_id,
+                               t_range, hit_capacity, st, "svo_trace_rays");
+    if (rc || R == 0) return rc;
+    return read_traversal(work, target_lod + kFirstFeatureDepth - 1, h_stats, st, "svo_trace_rays");
+}
+
+extern "C" int svo_trace_rays_async(const nglod_svo* svo, const float* o, const float* d, int64_t R, int target_lod,
+                                    void* work, size_t work_bytes, int64_t pair_capacity, int32_t* ray_offsets,
+                                    int32_t* voxel_id, float* t_range, int64_t hit_capacity, void* stream) {
+    return enqueue_traversal(svo, o, d, R, target_lod, work, work_bytes, pair_capacity, ray_offsets, voxel_id,
+                             t_range, hit_capacity, (cudaStream_t)stream, "svo_trace_rays_async");
+}
+
+extern "C" int svo_trace_rays_check(const void* work, int target_lod, int64_t* h_stats, void* stream) {
+    if (!work || target_lod < 1 || target_lod + kFirstFeatureDepth - 1 > kMaxDepth)
+        return fail(NGLOD_ERR_INVALID_ARG, "svo_trace_rays_check: bad arguments");
+    return read_traversal(work, target_lod + kFirstFeatureDepth - 1, h_stats, (cudaStream_t)stream,
+                          "svo_trace_rays_check");
 }
 
 extern "C" int svo_trace_rays_sizes(const void* work, int64_t* h_sizes, int n, void* stream) {

@@ -25,7 +25,9 @@ EXPORTS = ["nglod_last_error", "svo_build", "svo_info", "svo_device_arrays", "sv
            "svo_trace_rays_workspace", "svo_trace_rays", "sdf_query", "sphere_trace_workspace",
            "sphere_trace", "sphere_trace_status", "trace_normals", "svo_trace_rays_noalloc",
            "svo_trace_rays_sizes", "sdf_backward", "sdf_l2_backward", "nglod_adam_step",
-           "nglod_features_absmax"]
+           "nglod_features_absmax", "svo_trace_rays_async", "svo_trace_rays_check",
+           "sphere_trace_batch_create", "sphere_trace_batch_run", "sphere_trace_batch_status",
+           "sphere_trace_batch_free"]
 
 
 class NglodError(RuntimeError):
@@ -42,6 +44,13 @@ class _Features(C.Structure):
 class _Decoder(C.Structure):
     _fields_ = [("W1", C.c_void_p), ("b1", C.c_void_p), ("W2", C.c_void_p), ("b2", C.c_float),
                 ("in_dim", C.c_int), ("hidden", C.c_int)]
+
+
+class _TraceJob(C.Structure):
+    _fields_ = [("svo", C.c_void_p), ("feats", _Features), ("dec", _Decoder), ("lod", C.c_int),
+                ("o", C.c_void_p), ("d", C.c_void_p), ("R", C.c_int64), ("ray_offsets", C.c_void_p),
+                ("voxel_id", C.c_void_p), ("t_range", C.c_void_p), ("work", C.c_void_p), ("work_bytes", C.c_size_t),
+                ("t_hit", C.c_void_p), ("hit", C.c_void_p), ("steps", C.c_void_p), ("normal", C.c_void_p)]
 
 
 class _TraceParams(C.Structure):
@@ -81,6 +90,13 @@ def lib():
         L.sdf_backward.argtypes = [P, P, P, P, i64, C.c_uint32, P, P, P, P, P, P, P, i32, P]
         L.sdf_l2_backward.argtypes = [P, P, P, P, P, i64, C.c_uint32, C.c_float, P, P, P, P, P, P, P]
         L.nglod_features_absmax.argtypes = [P, P, i32, P, P]
+        L.svo_trace_rays_async.argtypes = [P, P, P, i64, i32, P, sz, i64, P, P, P, i64, P]
+        L.svo_trace_rays_check.argtypes = [P, i32, P, P]
+        L.sphere_trace_batch_create.argtypes = [P, i32, P, i32, P, P]
+        L.sphere_trace_batch_run.argtypes = [P, P]
+        L.sphere_trace_batch_status.argtypes = [P, P]
+        L.sphere_trace_batch_free.argtypes = [P]
+        L.sphere_trace_batch_free.restype = None
         L.nglod_adam_step.argtypes = [P, P, P, P, i64, C.c_float, C.c_float, C.c_float, C.c_float, i32, P]
         L.svo_trace_rays_noalloc.argtypes = [P, P, P, i64, i32, P, P, P, i64, P, P]
         _lib = L

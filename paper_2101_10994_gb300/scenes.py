@@ -124,28 +124,82 @@ def csg_scene(n: int, seed: int = 0) -> Scene:
     return Scene(types, centers, params, name=f"csg{n}_s{seed}")
 
 
-def scene_sdf(scene: Scene, pts: np.ndarray, chunk: int = 1 << 16) -> np.ndarray:
-    """Exact CSG signed distance (min over primitive SDFs), float64 [N]."""
+def _bound_radius(scene: Scene) -> np.ndarray:
+    """Radius of a sphere about each primitive's centre that contains it."""
+    rb = np.empty(scene.n)
+    for p, (t, q) in enumerate(zip(scene.types, scene.params)):
+        if t == PRIM_SPHERE:
+            rb[p] = q[0]
+        elif t == PRIM_BOX:
+            rb[p] = math.sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2])
+        else:
+            rb[p] = math.sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2]) + q[3]
+    return rb
+
+
+def _primitive_sdf(t: int, c: np.ndarray, q: np.ndarray, p: np.ndarray) -> np.ndarray:
+    """SDF of one primitive type at points p [n, 3]; c and q are one
+    primitive's centre and params ([3], [4]) or one row per point ([n, 3],
+    [n, 4])."""
+    d = p - c
+    if t == PRIM_SPHERE:
+        return np.sqrt(d[:, 0] * d[:, 0] + d[:, 1] * d[:, 1] + d[:, 2] * d[:, 2]) - q[..., 0]
+    if t == PRIM_BOX:
+        a = np.abs(d) - q[..., 0:3]
+        e = np.maximum(a, 0.0)
+        return (np.sqrt(e[:, 0] * e[:, 0] + e[:, 1] * e[:, 1] + e[:, 2] * e[:, 2])
+                + np.minimum(np.maximum(np.maximum(a[:, 0], a[:, 1]), a[:, 2]), 0.0))
+    h = q[..., 0:3]
+    pa = d + h                      # segment from c - h to c + h
+    ba = 2.0 * h
+    tt = np.clip((pa[:, 0] * ba[..., 0] + pa[:, 1] * ba[..., 1] + pa[:, 2] * ba[..., 2])
+                 / (ba[..., 0] * ba[..., 0] + ba[..., 1] * ba[..., 1] + ba[..., 2] * ba[..., 2]), 0.0, 1.0)
+    e = pa - tt[:, None] * ba
+    return np.sqrt(e[:, 0] * e[:, 0] + e[:, 1] * e[:, 1] + e[:, 2] * e[:, 2]) - q[..., 3]
+
+
+def _pair_sdf(scene: Scene, prim: np.ndarray, pts: np.ndarray) -> np.ndarray:
+    """SDF of primitive prim[i] at pts[i], for every pair i."""
+    out = np.empty(prim.shape[0])
+    ty = scene.types[prim]
+    for t in (PRIM_SPHERE, PRIM_BOX, PRIM_CAPSULE):
+        sel = np.flatnonzero(ty == t)
+        if sel.size:
+            pr = prim[sel]
+            out[sel] = _primitive_sdf(t, scene.centers[pr], scene.params[pr], pts[sel])
+    return out
+
+
+def scene_sdf(scene: Scene, pts: np.ndarray, cap=None, chunk: int = 1 << 13) -> np.ndarray:
+    """Exact CSG signed distance (min over primitive SDFs), float64 [N].
+
+    Every primitive SDF here is 1-Lipschitz and <= 0 at the primitive's
+    centre, so |x - c_p| bounds it from above, and |x - c_p| - rb_p (rb_p =
+    bounding radius) from below.  A primitive whose lower bound exceeds the
+    smallest upper bound (plus 1e-9 for rounding) cannot be the minimum and
+    is skipped; the result is the same min.  With ``cap`` (scalar or [N]),
+    values >= cap are only guaranteed to stay >= cap (primitives whose lower
+    bound exceeds cap are skipped too; such points may return +inf).
+    """
     pts = np.asarray(pts, dtype=np.float64).reshape(-1, 3)
     out = np.empty(pts.shape[0])
+    rb = _bound_radius(scene)
+    cen = scene.centers
     for s in range(0, pts.shape[0], chunk):
         p = pts[s:s + chunk]
+        dv = p[:, None, :] - cen[None, :, :]
+        dist = np.sqrt(dv[..., 0] * dv[..., 0] + dv[..., 1] * dv[..., 1] + dv[..., 2] * dv[..., 2])
+        lim = dist.min(axis=1)
+        if cap is not None:
+            cp = np.broadcast_to(np.asarray(cap, np.float64), (pts.shape[0],))[s:s + chunk]
+            lim = np.minimum(lim, cp)
+        live = (dist - rb[None, :]) <= (lim + 1e-9)[:, None]
         best = np.full(p.shape[0], np.inf)
-        for t, c, q in zip(scene.types, scene.centers, scene.params):
-            d = p - c
-            if t == PRIM_SPHERE:
-                v = np.linalg.norm(d, axis=1) - q[0]
-            elif t == PRIM_BOX:
-                a = np.abs(d) - q[0:3]
-                v = (np.linalg.norm(np.maximum(a, 0.0), axis=1)
-                     + np.minimum(a.max(axis=1), 0.0))
-            else:
-                h = q[0:3]
-                pa = d + h                      # segment from c - h to c + h
-                ba = 2.0 * h
-                tt = np.clip(pa @ ba / (ba @ ba), 0.0, 1.0)
-                v = np.linalg.norm(pa - tt[:, None] * ba, axis=1) - q[3]
-            best = np.minimum(best, v)
+        for k in range(scene.n):
+            rows = np.flatnonzero(live[:, k])
+            if rows.size:
+                best[rows] = np.minimum(best[rows], _primitive_sdf(int(scene.types[k]), cen[k],
+                                                                   scene.params[k], p[rows]))
         out[s:s + chunk] = best
     return out
 
@@ -159,6 +213,7 @@ class Octree:
     keys: list                                   # list[np.ndarray uint64]
     scene: Scene | None = None
     corner_keys: list = field(default_factory=list)   # per feature depth
+    prim_pairs: list | None = None               # per depth (voxel index, primitive) candidates
 
     @property
     def max_depth(self) -> int:
@@ -193,19 +248,78 @@ def unique_corner_keys(keys: np.ndarray) -> np.ndarray:
 
 
 def build_octree(scene: Scene, max_depth: int) -> Octree:
-    """Top-down occupancy: keep a voxel iff |sdf(centre)| < half diagonal."""
+    """Top-down occupancy: keep a voxel iff |sdf(centre)| < half diagonal.
+
+    The min over primitives is taken over each voxel's candidate set
+    rel(v) = {p : |centre(v) - c_p| - rb_p <= 3 hd_v} (hd_v = half diagonal,
+    rb_p = bounding radius).  A child's set is inside its parent's (child
+    centres lie hd_child from the parent's, and hd_parent = 2 hd_child), so
+    the sets are built top-down from pairs.  The minimising primitive of any
+    point within 2 hd_v of the centre with |sdf| < 2 hd_v lies in rel(v)
+    (its lower bound is at most its value), so the keep decision and the
+    corner distances of kept voxels are the exact min; the sets are kept on
+    the octree (``prim_pairs``) for the corner distances.
+    """
+    rb = _bound_radius(scene)
     keys = [np.zeros(1, np.uint64)]
+    pv = np.zeros(scene.n, np.int64)                 # pair -> voxel index at this depth
+    pp = np.arange(scene.n, dtype=np.int64)          # pair -> primitive
+    pairs = [(pv, pp)]
     for dp in range(1, max_depth + 1):
         parents = keys[-1]
         cand = (parents[:, None] * np.uint64(8)
                 + np.arange(8, dtype=np.uint64)[None, :]).reshape(-1)
         half_diag = math.sqrt(3.0) * (2.0 / (1 << dp)) * 0.5
-        sd = scene_sdf(scene, voxel_centers(cand, dp))
-        keys.append(np.sort(cand[np.abs(sd) < half_diag]))
+        cc = voxel_centers(cand, dp)
+        ci = (pv[:, None] * 8 + np.arange(8)[None, :]).reshape(-1)
+        cp = np.repeat(pp, 8)
+        dv = cc[ci] - scene.centers[cp]
+        lb = np.sqrt(dv[:, 0] * dv[:, 0] + dv[:, 1] * dv[:, 1] + dv[:, 2] * dv[:, 2]) - rb[cp]
+        live = lb <= 3.0 * half_diag + 1e-9
+        ci, cp = ci[live], cp[live]
+        best = np.full(cand.shape[0], np.inf)
+        np.minimum.at(best, ci, _pair_sdf(scene, cp, cc[ci]))
+        keep = np.abs(best) < half_diag
+        newidx = np.cumsum(keep) - 1
+        sel = keep[ci]
+        pv, pp = newidx[ci[sel]], cp[sel]
+        keys.append(cand[keep])                      # parents sorted => candidates sorted
+        pairs.append((pv, pp))
     oct_ = Octree(keys=keys, scene=scene)
+    oct_.prim_pairs = pairs
     oct_.corner_keys = [unique_corner_keys(keys[dp])
                         for dp in range(FIRST_FEATURE_DEPTH, max_depth + 1)]
     return oct_
+
+
+def corner_sdf(octree: Octree, scene: Scene, li: int) -> np.ndarray:
+    """Exact scene SDF at the corners of feature level li (depth 3 + li),
+    from the candidate sets of build_octree (min over a voxel's set)."""
+    dp = FIRST_FEATURE_DEPTH + li
+    ck = octree.corner_keys[li]
+    pairs = getattr(octree, "prim_pairs", None)
+    if pairs is None or octree.scene is not scene:
+        return scene_sdf(scene, corner_positions(ck, dp))
+    pv, pp = pairs[dp]
+    keys = octree.keys[dp]
+    i, j, k = morton_decode(keys)
+    owner = np.empty(ck.shape[0], np.int64)
+    for c in range(8):
+        ckey = morton_encode(i + (c & 1), j + ((c >> 1) & 1), k + ((c >> 2) & 1))
+        owner[np.searchsorted(ck, ckey)] = np.arange(keys.shape[0])
+    order = np.argsort(pv, kind="stable")
+    pv, pp = pv[order], pp[order]
+    start = np.searchsorted(pv, np.arange(keys.shape[0]))
+    cnt = np.searchsorted(pv, np.arange(keys.shape[0]), side="right") - start
+    n = cnt[owner]
+    corner = np.repeat(np.arange(ck.shape[0]), n)
+    first = np.repeat(start[owner], n)
+    within = np.arange(corner.shape[0]) - np.repeat(np.cumsum(n) - n, n)
+    prim = pp[first + within]
+    pos = corner_positions(ck, dp)
+    out = np.full(ck.shape[0], np.inf)
+    np.minimum.at(out, corner, _pair_sdf(scene, prim, pos[corner]))
+    return out
 
 
 def full_octree(max_depth: int) -> Octree:
@@ -252,7 +366,7 @@ def readout_features(octree: Octree, scene: Scene, m: int = 32, seed: int = 0,
         dp = FIRST_FEATURE_DEPTH + li
         f = rng.normal(0.0, sigma, (ck.shape[0], m))
         f[:, :L] = 0.0
-        f[:, li] = scene_sdf(scene, corner_positions(ck, dp))
+        f[:, li] = corner_sdf(octree, scene, li)
         feats.append(f.astype(np.float32))
     return feats
 
@@ -456,3 +570,37 @@ def training_batch(scene: Scene, n: int, seed: int, sigma: float = 0.01):
     uni = rng.uniform(-1.0, 1.0, (n - n_near, 3))
     x = np.clip(np.concatenate([near, uni]), -1.0, 1.0).astype(np.float32)
     return x, scene_sdf(scene, x.astype(np.float64)).astype(np.float32)
+
+
+def _batch_item(args):
+    s, n, lod, w, h, readout = args
+    sc = csg_scene(n, s)
+    oc = build_octree(sc, lod + FIRST_FEATURE_DEPTH - 1)
+    feats = readout_features(oc, sc) if readout else None
+    oc.prim_pairs = None                         # not needed past the build; keeps the pickle small
+    return sc, oc, lod, w, h, feats
+
+
+def batching_workload(n_scenes: int = 32, seed: int = 0, min_prims: int = 8, max_prims: int = 256,
+                      min_lod: int = 3, max_lod: int = 6, min_side: int = 128, max_side: int = 1024,
+                      readout: bool = True, workers: int = 1):
+    """Seeded multi-scene workload: scene s = CSG(U{min_prims..max_prims},
+    seed s), octree to LOD U{min_lod..max_lod}, image U{min_side..max_side}
+    wide and high (one draw each per scene, in that order, from
+    default_rng(seed)).  Returns (scene, octree, lod, width, height, readout
+    features or None) per scene; ``workers`` > 1 builds them in a spawned
+    process pool."""
+    rng = np.random.default_rng(seed)
+    items = []
+    for s in range(n_scenes):
+        n = int(rng.integers(min_prims, max_prims + 1))
+        lod = int(rng.integers(min_lod, max_lod + 1))
+        w = int(rng.integers(min_side, max_side + 1))
+        h = int(rng.integers(min_side, max_side + 1))
+        items.append((s, n, lod, w, h, readout))
+    if workers <= 1:
+        return [_batch_item(a) for a in items]
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    with cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+        return list(ex.map(_batch_item, items))
