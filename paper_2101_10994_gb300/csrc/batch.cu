@@ -144,6 +144,12 @@ extern "C" int sphere_trace_batch_create(const nglod_trace_job* jobs, int num_jo
             b->h_decs.push_back(J.dec);
             b->normals.push_back(J.normal);
         }
+        if (rc) break;
+        // the group queue is a 32-bit counter that runs up to nrays + 32 per warp
+        if (base > (1ll << 31) - (1ll << 24)) {
+            rc = fail(NGLOD_ERR_NOT_SUPPORTED, "sphere_trace_batch_create: more than 2^31 - 2^24 rays per decoder group");
+            break;
+        }
         gr.j1 = (int)b->h_jobs.size();
         gr.nrays = base;
         const nglod_trace_job& J0 = jobs[members[g][0]];
