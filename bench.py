@@ -393,6 +393,81 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+# ----------------------------------------------------------------------------
+# batching: many scenes and images of uneven size per frame
+# ----------------------------------------------------------------------------
+def run_batch(args):
+    from paper_2101_10994_gb300 import scenes as S
+    items = S.batching_workload(32, seed=0, workers=min(16, os.cpu_count() or 1))
+    import torch
+
+    from paper_2101_10994_gb300 import batch as B
+    from paper_2101_10994_gb300 import nglod as ng
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    decs = {}
+    jobs = []
+    for sc, oc, lod, w, h, feats in items:
+        if lod not in decs:
+            decs[lod] = ng.DecoderDev.from_decoder(S.readout_decoder(lod))
+        o, d, _ = S.camera_rays(w, h, tile=8)
+        jobs.append(B.Job(ng.svo_build(oc.keys), ng.Features(feats, "f32"), decs[lod], lod,
+                          torch.from_numpy(o).to(dev), torch.from_numpy(d).to(dev)))
+    R = sum(j.R for j in jobs)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def timed(fn, n):
+        ts = []
+        for _ in range(n):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts)
+
+    def per_scene():
+        B.per_scene_frame(jobs, decode="bf16")
+
+    rnd = B.BatchRenderer(jobs, decode="bf16")
+    best, tune = B.autotune(rnd, reps=3)
+    rnd.frame()
+    rnd.check()
+    rnd.capture()
+    for _ in range(args.warmup):
+        per_scene()
+        rnd.frame()
+        rnd.replay()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(0)
+    with sampler:
+        ms_scene = timed(per_scene, args.steps)
+        ms_batch = timed(rnd.frame, args.steps)
+        ms_graph = timed(rnd.replay, args.steps)
+    rnd.check()
+    hits = sum(int(rnd.outputs(k)["hit"].sum().item()) for k in range(len(jobs)))
+    line = {
+        "metric": "batched sphere-traced rays/s (traversal + trace + normals), 32 scenes per frame",
+        "value": R / (ms_graph * 1e-3), "unit": "rays/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_graph, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+        "config": {"workload": "batch32_csg_u8-256_lod_u3-6_side_u128-1024_seed0", "rays": R,
+                   "scenes": len(jobs), "decoder_groups": len(decs), "max_steps": 128, "eps": 1e-3,
+                   "l2": "flushed between steps (256 MB write)", "parallelism": "single GPU"},
+        "schedules_ms": {"per_scene_calls": ms_scene, "persistent_launch": ms_batch, "graph_replay": ms_graph},
+        "speedup_vs_per_scene": ms_scene / ms_graph,
+        "autotune": {"best_ctas_per_sm": best, "ms": tune},
+        "hit_pixels": hits,
+        "clocks": sampler.summary(),
+        # per graph replay: each job's traversal (prep + lod+2 levels + offsets), the reset and
+        # the persistent trace kernel, each job's normals
+        "gpu_launches": args.steps * (sum(j.lod + 4 for j in jobs) + 2 + len(jobs)),
+    }
+    print(json.dumps(line))
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
