@@ -20,6 +20,7 @@
  *   - feature query: Sec. 3.2 (trilinear psi per level, summed over levels);
  *   - decoder: Eq. 2 (one hidden layer, ReLU, linear output, Sec. A.1);
  *   - sphere tracing with adaptive stepping: Sec. 3.4 and Sec. A.4;
+ *   - level blending of two consecutive LODs: Sec. 3.2, Eq. 3;
  *   - input gradient (normals) and parameter gradients of Eq. 4: chain rule.
  *
  * Parity status: every function here is pinned by tests/test_oracle_*.py
@@ -486,14 +487,18 @@ void or_sdf_query(const or_svo *s, const double *const *feats, int m,
  *   also stops the ray, as a hit iff |d_k| < 6 eps.
  * Outputs: t_hit (+inf on miss), hit, steps, x_hit (last query point),
  * normal = normalised analytic gradient at x_hit (0 on miss). */
-void or_sphere_trace(const or_svo *s, const double *const *feats, int m,
-                     const double *W1, const double *b1, const double *W2, double b2,
-                     int in_dim, int hidden, const float *o, const float *dir,
-                     int64_t R, int lod, double eps, double far_, int max_steps, int osc,
-                     double *t_hit, uint8_t *hit, int32_t *steps, double *x_hit,
-                     double *normal, int nthreads) {
+/* The tracer of or_sphere_trace and or_sphere_trace_blend.  With lo == NULL
+ * the distance is the decoder `hi` at LOD `lod`; otherwise it is Eq. 3's
+ * blend (1 - alpha) d_lo + alpha d_hi, where d_lo decodes the feature sum
+ * over depths 3..D-1 with `lo` and d_hi the sum over 3..D with `hi`, both at
+ * the same point, and the normal is the normalised blend of their
+ * gradients. */
+static void trace_impl(const or_svo *s, const double *const *feats, int m, const or_dec *hi,
+                       const or_dec *lo, double alpha, const float *o, const float *dir,
+                       int64_t R, int lod, double eps, double far_, int max_steps, int osc,
+                       double *t_hit, uint8_t *hit, int32_t *steps, double *x_hit,
+                       double *normal, int nthreads) {
     int D = lod + FIRST_FEATURE_DEPTH - 1;
-    or_dec dec = mkdec(W1, b1, W2, b2, in_dim, hidden);
 #ifdef _OPENMP
     if (nthreads > 0) omp_set_num_threads(nthreads);
 #pragma omp parallel for schedule(dynamic, 4)
@@ -503,8 +508,10 @@ void or_sphere_trace(const or_svo *s, const double *const *feats, int m,
         int64_t n = ray_hits(s, D, o + 3 * r, dir + 3 * r, &lst);
         double oo[3] = {o[3 * r], o[3 * r + 1], o[3 * r + 2]};
         double dd[3] = {dir[3 * r], dir[3 * r + 1], dir[3 * r + 2]};
-        double *z = (double *)malloc(sizeof(double) * (size_t)m * 4);
+        double *z = (double *)malloc(sizeof(double) * (size_t)m * 8);
         double *jz = z + m;
+        double *zl = z + 4 * m;
+        double *jzl = zl + m;
         int64_t vids[MAX_DEPTH + 1], ijks[MAX_DEPTH + 1][3];
         int k = 0, is_hit = 0;
         double t = n > 0 ? (double)lst[0].tin : INFINITY;
@@ -526,7 +533,11 @@ void or_sphere_trace(const or_svo *s, const double *const *feats, int m,
                 ijks[d][0] = i >> sh; ijks[d][1] = j >> sh; ijks[d][2] = kk >> sh;
             }
             feature_sum(s, feats, m, D, vids, ijks, x, z, NULL);
-            double dk = decode(&dec, x, z, m, NULL);
+            double dk = decode(hi, x, z, m, NULL);
+            if (lo) {
+                feature_sum(s, feats, m, D - 1, vids, ijks, x, zl, NULL);
+                dk = (1.0 - alpha) * decode(lo, x, zl, m, NULL) + alpha * dk;
+            }
             ++k;
             if (dk < eps) { is_hit = 1; break; }
             if (osc && k > 1 && fabs(dk - dprev) < 6.0 * eps) {
@@ -548,7 +559,13 @@ void or_sphere_trace(const or_svo *s, const double *const *feats, int m,
         if (is_hit) {
             feature_sum(s, feats, m, D, vids, ijks, x, z, jz);
             double g[3];
-            decode_grad_x(&dec, x, z, jz, m, g);
+            decode_grad_x(hi, x, z, jz, m, g);
+            if (lo) {
+                double gl[3];
+                feature_sum(s, feats, m, D - 1, vids, ijks, x, zl, jzl);
+                decode_grad_x(lo, x, zl, jzl, m, gl);
+                for (int a = 0; a < 3; ++a) g[a] = (1.0 - alpha) * gl[a] + alpha * g[a];
+            }
             double nn = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
             if (nn > 0.0)
                 for (int a = 0; a < 3; ++a) normal[3 * r + a] = g[a] / nn;
@@ -556,6 +573,34 @@ void or_sphere_trace(const or_svo *s, const double *const *feats, int m,
         free(z);
         free(lst);
     }
+}
+
+void or_sphere_trace(const or_svo *s, const double *const *feats, int m,
+                     const double *W1, const double *b1, const double *W2, double b2,
+                     int in_dim, int hidden, const float *o, const float *dir,
+                     int64_t R, int lod, double eps, double far_, int max_steps, int osc,
+                     double *t_hit, uint8_t *hit, int32_t *steps, double *x_hit,
+                     double *normal, int nthreads) {
+    or_dec dec = mkdec(W1, b1, W2, b2, in_dim, hidden);
+    trace_impl(s, feats, m, &dec, NULL, 0.0, o, dir, R, lod, eps, far_, max_steps, osc, t_hit, hit,
+               steps, x_hit, normal, nthreads);
+}
+
+/* Level blending (Sec. 3.2, Eq. 3) while sphere tracing: rays walk their
+ * lists at LOD lod_hi = L* + 1 and every step decodes
+ * (1 - alpha) d_{L*}(x) + alpha d_{L*+1}(x), alpha in [0, 1]; decoder "lo"
+ * is LOD L*'s, "hi" is LOD L*+1's.  Outputs as or_sphere_trace. */
+void or_sphere_trace_blend(const or_svo *s, const double *const *feats, int m,
+                           const double *W1lo, const double *b1lo, const double *W2lo, double b2lo,
+                           const double *W1hi, const double *b1hi, const double *W2hi, double b2hi,
+                           int in_dim, int hidden, const float *o, const float *dir, int64_t R,
+                           int lod_hi, double alpha, double eps, double far_, int max_steps, int osc,
+                           double *t_hit, uint8_t *hit, int32_t *steps, double *x_hit,
+                           double *normal, int nthreads) {
+    or_dec lo = mkdec(W1lo, b1lo, W2lo, b2lo, in_dim, hidden);
+    or_dec hi = mkdec(W1hi, b1hi, W2hi, b2hi, in_dim, hidden);
+    trace_impl(s, feats, m, &hi, &lo, alpha, o, dir, R, lod_hi, eps, far_, max_steps, osc, t_hit, hit,
+               steps, x_hit, normal, nthreads);
 }
 
 /* ------------------------------------------------------------------------ */

@@ -59,6 +59,8 @@ def _load():
                                      P, P, P, i32]
         lib.or_sphere_trace.argtypes = [P, P, i32, P, P, P, f64, i32, i32, P, P, i64,
                                         i32, f64, f64, i32, i32, P, P, P, P, P, i32]
+        lib.or_sphere_trace_blend.argtypes = [P, P, i32, P, P, P, f64, P, P, P, f64, i32, i32, P, P,
+                                              i64, i32, f64, f64, f64, i32, i32, P, P, P, P, P, i32]
         lib.or_feature_sum.argtypes = [P, P, i32, P, i64, i32, P]
         lib.or_sdf_backward.argtypes = [P, P, i32, P, P, P, P, i32, i32, P, i64, P, i32,
                                         P, P, P, P, P, P, P]
@@ -189,6 +191,52 @@ class OracleSVO:
                                 _ptr(out["x"]), _ptr(out["normal"]), nthreads)
         return out
 
+    # -- level blending (Sec. 3.2, Eq. 3) ----------------------------------
+    @staticmethod
+    def split_lod(lod_tilde: float):
+        """L* = floor(L~) and alpha = L~ - L* (Eq. 3)."""
+        lstar = int(np.floor(lod_tilde))
+        return lstar, float(lod_tilde) - lstar
+
+    def sdf_query_blend(self, feats, dec_lo, dec_hi, x, lod_tilde: float):
+        """Eq. 3 at the points x: (1 - alpha) sdf_{L*}(x) + alpha sdf_{L*+1}(x),
+        each term the plain LOD query (dec_lo = LOD L*'s decoder, dec_hi =
+        LOD L*+1's; alpha = 0 needs no dec_hi)."""
+        lstar, alpha = self.split_lod(lod_tilde)
+        lo, _ = self.sdf_query(feats, dec_lo, x, lstar)
+        if alpha == 0.0:
+            return lo
+        hi, _ = self.sdf_query(feats, dec_hi, x, lstar + 1)
+        return (1.0 - alpha) * lo + alpha * hi
+
+    def sphere_trace_blend(self, feats, dec_lo, dec_hi, o, d, lod_tilde: float, eps: float = 1e-3,
+                           far: float = 5.0, max_steps: int = 32, osc: bool = False, alpha=None,
+                           nthreads: int = 0):
+        """Sphere tracing of the Eq. 3 blend.  With alpha = 0 this is the
+        plain trace at L*; otherwise rays walk their lists at L* + 1 and
+        each step decodes both LODs at the same point.  ``alpha`` overrides
+        the fractional part (the tests use alpha = 1 with L~ = L*)."""
+        lstar, a = self.split_lod(lod_tilde)
+        a = a if alpha is None else float(alpha)
+        if a == 0.0:
+            return self.sphere_trace(feats, dec_lo, o, d, lstar, eps=eps, far=far, max_steps=max_steps, osc=osc,
+                                     nthreads=nthreads)
+        fs = _PtrArray([_f64(f) for f in feats])
+        m = int(fs.arrays[0].shape[1])
+        W1l, b1l, W2l, b2l, ind, hid = self._dec(dec_lo)
+        W1h, b1h, W2h, b2h, ind2, hid2 = self._dec(dec_hi)
+        assert (ind, hid) == (ind2, hid2)
+        o = np.ascontiguousarray(o, np.float32).reshape(-1, 3)
+        d = np.ascontiguousarray(d, np.float32).reshape(-1, 3)
+        R = o.shape[0]
+        out = dict(t=np.zeros(R), hit=np.zeros(R, np.uint8), steps=np.zeros(R, np.int32),
+                   x=np.zeros((R, 3)), normal=np.zeros((R, 3)))
+        _load().or_sphere_trace_blend(self.h, fs.p, m, _ptr(W1l), _ptr(b1l), _ptr(W2l), b2l, _ptr(W1h),
+                                      _ptr(b1h), _ptr(W2h), b2h, ind, hid, _ptr(o), _ptr(d), R, lstar + 1, a,
+                                      eps, far, max_steps, int(osc), _ptr(out["t"]), _ptr(out["hit"]),
+                                      _ptr(out["steps"]), _ptr(out["x"]), _ptr(out["normal"]), nthreads)
+        return out
+
     def sdf_backward(self, feats, decs, x, lods, grad_sdf):
         """Gradients of sum_i sum_q grad_sdf[i, q] * sdf_{lods[i]}(x_q).
 
@@ -219,6 +267,14 @@ class OracleSVO:
                                 _ptr(x), Q, _ptr(lods), len(lods), _ptr(gs), GF.p,
                                 GW1.p, GB1.p, GW2.p, _ptr(gb2), _ptr(gx))
         return dict(feats=gf, W1=gW1, b1=gb1, W2=gW2, b2=gb2, x=gx)
+
+
+def lod_select(distance, d_near: float, d_far: float, lod_near: float, lod_far: float):
+    """LOD selection of Sec. 3.4: the continuous LOD moves linearly from
+    lod_near (distance <= d_near) to lod_far (distance >= d_far)."""
+    dist = np.asarray(distance, np.float64)
+    s = np.clip((dist - d_near) / (d_far - d_near), 0.0, 1.0)
+    return lod_near + s * (lod_far - lod_near)
 
 
 if __name__ == "__main__":
