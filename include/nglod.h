@@ -319,6 +319,49 @@ int nglod_adam_step(float* param, float* grad, float* m, float* v, int64_t n, fl
  * (its outputs are then invalid). */
 int sphere_trace_status(const void* work, void* stream);
 
+/* ---- Continuous LOD: level blending (Sec. 3.2, Eq. 3) ---------------------
+ * For a continuous LOD L~ in [1, max lod], L* = floor(L~) and
+ * alpha = L~ - L* (exact in FP32); the blended distance is
+ *   d_L~(x) = (1 - alpha) d_L*(x) + alpha d_(L*+1)(x),
+ * each term the query of sdf_query at that LOD (feature sum over the depths
+ * 3..L+2 that contain x, absent levels contributing 0, then that LOD's
+ * decoder).  dec_lo is LOD L*'s decoder, dec_hi LOD L*+1's (same in_dim;
+ * dec_hi is not read when alpha = 0).  alpha = 0 is exactly the plain call
+ * at L*.  Blending runs with decode_dtype NGLOD_F32 or NGLOD_BF16 (the
+ * FP8 decode only at alpha = 0). */
+
+/* sdf_query_blend -- d_L~ at Q points x [Q, 3] into sdf [Q].  Errors as
+ * sdf_query, plus NGLOD_ERR_INVALID_ARG for L~ outside [1, max lod] and
+ * NGLOD_ERR_NOT_SUPPORTED for decoders of different in_dim.  The FP32
+ * decode does not synchronise; the BF16 decode synchronises to read its
+ * status. */
+int sdf_query_blend(const nglod_svo* svo, const nglod_features* feats,
+                    const nglod_decoder* dec_lo, const nglod_decoder* dec_hi,
+                    const float* x, int64_t Q, float lod_tilde, int decode_dtype,
+                    float* sdf, void* stream);
+
+/* sphere_trace_blend -- sphere_trace (Sec. 3.4 / A.4 stepping) of the
+ * blended field d_L~.  The lists (ray_offsets, voxel_id, t_range) are those
+ * of svo_trace_rays at LOD ceil(L~): at L* + 1 when alpha > 0 (rays walk the
+ * finer voxels, inside which both terms are defined; every step decodes
+ * both LODs at the same point), at L* when alpha = 0 (the plain trace).
+ * normal: the normalised blend (1 - alpha) grad d_L* + alpha grad d_(L*+1)
+ * at the hit point.  Other arguments, outputs, workspace layout and errors
+ * as sphere_trace.  Does not synchronise. */
+int sphere_trace_blend(const nglod_svo* svo, const nglod_features* feats,
+                       const nglod_decoder* dec_lo, const nglod_decoder* dec_hi,
+                       const float* o, const float* d, int64_t R, float lod_tilde,
+                       const nglod_trace_params* params, const int32_t* ray_offsets,
+                       const int32_t* voxel_id, const float* t_range, void* work,
+                       size_t work_bytes, float* t_hit, uint8_t* hit, int32_t* steps,
+                       float* normal, void* stream);
+
+/* nglod_lod_select -- the LOD selection of Sec. 3.4: L~ moves linearly
+ * with the distance to the object, from lod_near at distance <= d_near to
+ * lod_far at distance >= d_far (clamped outside; a step at d_near when
+ * d_far <= d_near).  Host function, no device work. */
+float nglod_lod_select(float distance, float d_near, float d_far, float lod_near, float lod_far);
+
 /* One image of a batch: an octree with its features and the decoder of the
  * LOD it is traced at, its rays and their lists (svo_trace_rays at that LOD),
  * a trace workspace (>= sphere_trace_workspace(R)) and its outputs. */

@@ -133,8 +133,10 @@ struct GradArgs {
     const int32_t* hit_list;
     long long n;           // mode 0: Q
     int D;
-    int mode;              // 0 query gradient, 1 normalised trace normal
-    float* out;            // [n, 3] (mode 1: indexed by ray)
+    int mode;              // 0 query gradient, 1 normalised trace normal, 2 out[ray] += w * gradient
+    float* out;            // [n, 3] (modes 1, 2: indexed by ray)
+    int dcap;              // > 0: only depths 3..dcap enter z (level blending, Eq. 3)
+    float w;               // mode 2 weight
 };
 
 template <typename T, int IN>
@@ -151,7 +153,8 @@ __global__ void __launch_bounds__(kThreads) k_grad(const DecPtrs dp, const Table
     const unsigned gmask = 0xffu << gbase;
     float* zb = zbuf[warp];
     float* gb = gxs[warp];
-    const long long n = A.mode == 1 ? (long long)*A.hit_count : A.n;
+    const long long n = A.mode >= 1 ? (long long)*A.hit_count : A.n;
+    const int dcap = A.dcap > 0 ? A.dcap : kMaxDepth;
     for (long long base = ((long long)blockIdx.x * kWarps + warp) * 32; base < n;
          base += (long long)gridDim.x * kWarps * 32) {
         const long long it = base + lane;
@@ -160,7 +163,7 @@ __global__ void __launch_bounds__(kThreads) k_grad(const DecPtrs dp, const Table
         int dd = -1, vox = -1, ray = -1;
         uint32_t ijk = 0;
         if (act) {
-            if (A.mode == 1) {
+            if (A.mode >= 1) {
                 ray = A.hit_list[it];
                 const float t = A.t_hit[ray];
                 x0 = fmaf(t, A.d[3 * ray], A.o[3 * ray]);
@@ -188,7 +191,9 @@ __global__ void __launch_bounds__(kThreads) k_grad(const DecPtrs dp, const Table
             const float s1 = __shfl_sync(0xffffffffu, q1, s);
             const float s2 = __shfl_sync(0xffffffffu, q2, s);
             float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (sdd >= kFirstFeatureDepth) z = gather_slot<T>(tb, sdd, svox, sijk, s0, s1, s2, gmask, gbase, l);
+            if (sdd >= kFirstFeatureDepth)
+                z = gather_levels<T>(tb, sdd, kFirstFeatureDepth, min(sdd, dcap), svox, sijk, s0, s1, s2, gmask,
+                                     gbase, l);
             *reinterpret_cast<float4*>(zb + s * kZStride + 4 * l) = z;
         }
         __syncwarp();
@@ -246,7 +251,7 @@ __global__ void __launch_bounds__(kThreads) k_grad(const DecPtrs dp, const Table
             if (sdd >= kFirstFeatureDepth) {
                 const float4 gz = *reinterpret_cast<const float4*>(zb + s * kZStride + 4 * l);
                 const int a = (l <= sdd - kFirstFeatureDepth) ? __ldg(tb.anc[sdd] + (size_t)svox * 8 + l) : -1;
-                for (int dp2 = kFirstFeatureDepth; dp2 <= sdd; ++dp2) {
+                for (int dp2 = kFirstFeatureDepth; dp2 <= min(sdd, dcap); ++dp2) {
                     const int vv = __shfl_sync(gmask, a, gbase + dp2 - kFirstFeatureDepth);
                     const int cid = __ldg(tb.corners[dp2] + (size_t)vv * 8 + l);
                     const int sh = sdd - dp2;
@@ -293,17 +298,23 @@ __global__ void __launch_bounds__(kThreads) k_grad(const DecPtrs dp, const Table
                 gx[1] += gv[33];
                 gx[2] += gv[34];
             }
-            const long long oi = A.mode == 1 ? (long long)ray : it;
-            if (A.mode == 1) {
-                const float nn = sqrtf(gx[0] * gx[0] + gx[1] * gx[1] + gx[2] * gx[2]);
-                const float inv = nn > 0.f ? 1.0f / nn : 0.f;
-                gx[0] *= inv;
-                gx[1] *= inv;
-                gx[2] *= inv;
+            const long long oi = A.mode >= 1 ? (long long)ray : it;
+            if (A.mode == 2) {
+                A.out[3 * oi] += A.w * gx[0];
+                A.out[3 * oi + 1] += A.w * gx[1];
+                A.out[3 * oi + 2] += A.w * gx[2];
+            } else {
+                if (A.mode == 1) {
+                    const float nn = sqrtf(gx[0] * gx[0] + gx[1] * gx[1] + gx[2] * gx[2]);
+                    const float inv = nn > 0.f ? 1.0f / nn : 0.f;
+                    gx[0] *= inv;
+                    gx[1] *= inv;
+                    gx[2] *= inv;
+                }
+                A.out[3 * oi] = gx[0];
+                A.out[3 * oi + 1] = gx[1];
+                A.out[3 * oi + 2] = gx[2];
             }
-            A.out[3 * oi] = gx[0];
-            A.out[3 * oi + 1] = gx[1];
-            A.out[3 * oi + 2] = gx[2];
         }
         __syncwarp();
     }
@@ -440,6 +451,183 @@ int run_grad(const nglod_decoder* dec, const Tables& tb, const GradArgs& A, bool
     return NGLOD_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Level blending (Sec. 3.2, Eq. 3), FP32 decode.  The slots' z over depths
+// 3..D-1 is decoded with LOD L*'s decoder; then the depth-D level is added
+// to the staged rows and decoded with LOD L*+1's; the result is
+// (1 - alpha) d_lo + alpha d_hi.  Two staged decoders do not fit beside the
+// z rows in static shared memory, so both live in dynamic shared memory.
+// ---------------------------------------------------------------------------
+constexpr size_t kBlendF32Smem = 2 * sizeof(SmemDecoder) + sizeof(float) * kWarps * 32 * kZStride;
+
+template <typename T, int IN>
+__global__ void __launch_bounds__(kThreads, 2) k_trace_blend_f32(const DecPtrs lo, const DecPtrs hi, float alpha,
+                                                                  const Tables tb, const TraceArgs A) {
+    extern __shared__ __align__(16) unsigned char blend_smem[];
+    SmemDecoder& slo = *reinterpret_cast<SmemDecoder*>(blend_smem);
+    SmemDecoder& shi = *reinterpret_cast<SmemDecoder*>(blend_smem + sizeof(SmemDecoder));
+    stage_decoder<IN>(slo, lo.W1, lo.b1, lo.W2);
+    stage_decoder<IN>(shi, hi.W1, hi.b1, hi.W2);
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = lane >> 3, l = lane & 7, gbase = g << 3;
+    const unsigned gmask = 0xffu << gbase;
+    float* zb = reinterpret_cast<float*>(blend_smem + 2 * sizeof(SmemDecoder)) + warp * 32 * kZStride;
+    RaySlot S;
+    S.ray = -1;
+    S.hit_ray = -1;
+    RayQueue Qu;
+    Qu.init();
+    for (;;) {
+        refill(S, Qu, A, tb, lane);
+        if (__ballot_sync(0xffffffffu, S.ray >= 0) == 0u) break;
+        const bool act = S.ray >= 0;
+        const float x0 = fmaf(S.t, S.dx, S.ox), x1 = fmaf(S.t, S.dy, S.oy), x2 = fmaf(S.t, S.dz, S.oz);
+        const float q0 = __fadd_rn(x0, 1.0f), q1 = __fadd_rn(x1, 1.0f), q2 = __fadd_rn(x2, 1.0f);
+        float dlo = 0.0f, dhi = 0.0f;
+#pragma unroll 1
+        for (int pass = 0; pass < 2; ++pass) {
+            // pass 0: depths 3..D-1 into the rows; pass 1: add depth D
+            const int d0 = pass ? A.D : kFirstFeatureDepth, d1 = pass ? A.D : A.D - 1;
+#pragma unroll 1
+            for (int r = 0; r < 8; ++r) {
+                const int s = r * 4 + g;
+                const int sact = __shfl_sync(0xffffffffu, act ? 1 : 0, s);
+                const int svox = __shfl_sync(0xffffffffu, S.vox, s);
+                const uint32_t sijk = __shfl_sync(0xffffffffu, S.ijk, s);
+                const float s0 = __shfl_sync(0xffffffffu, q0, s);
+                const float s1 = __shfl_sync(0xffffffffu, q1, s);
+                const float s2 = __shfl_sync(0xffffffffu, q2, s);
+                float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (sact) z = gather_levels<T>(tb, A.D, d0, d1, svox, sijk, s0, s1, s2, gmask, gbase, l);
+                float4* row = reinterpret_cast<float4*>(zb + s * kZStride + 4 * l);
+                if (pass) {
+                    const float4 p = *row;
+                    z = make_float4(p.x + z.x, p.y + z.y, p.z + z.z, p.w + z.w);
+                }
+                *row = z;
+            }
+            __syncwarp();
+            const float dv = mlp_f32<IN>(pass ? shi : slo, pass ? hi.b2 : lo.b2, zb + lane * kZStride, x0, x1, x2);
+            if (pass) dhi = dv;
+            else dlo = dv;
+            __syncwarp();
+        }
+        const float dhat = fmaf(alpha, dhi - dlo, dlo);
+        if (act) step_update(S, dhat, A, tb);
+        publish_hits(S, A, lane);
+    }
+}
+
+template <typename T, int IN>
+__global__ void __launch_bounds__(kThreads, 2) k_query_blend_f32(const DecPtrs lo, const DecPtrs hi, float alpha,
+                                                                  const Tables tb, const float* __restrict__ x,
+                                                                  long long Q, int D, float* __restrict__ sdf) {
+    extern __shared__ __align__(16) unsigned char blend_smem[];
+    SmemDecoder& slo = *reinterpret_cast<SmemDecoder*>(blend_smem);
+    SmemDecoder& shi = *reinterpret_cast<SmemDecoder*>(blend_smem + sizeof(SmemDecoder));
+    stage_decoder<IN>(slo, lo.W1, lo.b1, lo.W2);
+    stage_decoder<IN>(shi, hi.W1, hi.b1, hi.W2);
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = lane >> 3, l = lane & 7, gbase = g << 3;
+    const unsigned gmask = 0xffu << gbase;
+    float* zb = reinterpret_cast<float*>(blend_smem + 2 * sizeof(SmemDecoder)) + warp * 32 * kZStride;
+    for (long long base = ((long long)blockIdx.x * kWarps + warp) * 32; base < Q;
+         base += (long long)gridDim.x * kWarps * 32) {
+        const long long qi = base + lane;
+        const bool act = qi < Q;
+        float x0 = 0.f, x1 = 0.f, x2 = 0.f;
+        if (act) {
+            x0 = x[3 * qi];
+            x1 = x[3 * qi + 1];
+            x2 = x[3 * qi + 2];
+        }
+        int vox;
+        uint32_t ijk;
+        const int dd = act ? locate_descend(tb, D, x0, x1, x2, vox, ijk) : -1;
+        const float q0 = __fadd_rn(x0, 1.0f), q1 = __fadd_rn(x1, 1.0f), q2 = __fadd_rn(x2, 1.0f);
+        float dlo = 0.0f, dhi = 0.0f;
+#pragma unroll 1
+        for (int pass = 0; pass < 2; ++pass) {
+#pragma unroll 1
+            for (int r = 0; r < 8; ++r) {
+                const int s = r * 4 + g;
+                const int sdd = __shfl_sync(0xffffffffu, dd, s);
+                const int svox = __shfl_sync(0xffffffffu, vox, s);
+                const uint32_t sijk = __shfl_sync(0xffffffffu, ijk, s);
+                const float s0 = __shfl_sync(0xffffffffu, q0, s);
+                const float s1 = __shfl_sync(0xffffffffu, q1, s);
+                const float s2 = __shfl_sync(0xffffffffu, q2, s);
+                float4* row = reinterpret_cast<float4*>(zb + s * kZStride + 4 * l);
+                if (pass == 0) {
+                    float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (sdd >= kFirstFeatureDepth)
+                        z = gather_levels<T>(tb, sdd, kFirstFeatureDepth, min(sdd, D - 1), svox, sijk, s0, s1, s2,
+                                             gmask, gbase, l);
+                    *row = z;
+                } else if (sdd == D) {
+                    // the depth-D level exists only where x's depth-D voxel does
+                    const float4 z = gather_levels<T>(tb, sdd, D, D, svox, sijk, s0, s1, s2, gmask, gbase, l);
+                    const float4 p = *row;
+                    *row = make_float4(p.x + z.x, p.y + z.y, p.z + z.z, p.w + z.w);
+                }
+            }
+            __syncwarp();
+            const float dv = mlp_f32<IN>(pass ? shi : slo, pass ? hi.b2 : lo.b2, zb + lane * kZStride, x0, x1, x2);
+            if (pass) dhi = dv;
+            else dlo = dv;
+            __syncwarp();
+        }
+        if (act) sdf[qi] = fmaf(alpha, dhi - dlo, dlo);
+    }
+}
+
+template <typename K>
+void allow_blend_smem(K kernel) {
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBlendF32Smem);
+}
+
+template <typename T, int IN>
+void go_blend_f32(bool trace, const DecPtrs& lo, const DecPtrs& hi, float alpha, const Tables& tb,
+                  const TraceArgs* A, const float* x, long long Q, int D, float* sdf, int grid, cudaStream_t st) {
+    if (trace) {
+        static bool once = (allow_blend_smem(k_trace_blend_f32<T, IN>), true);
+        (void)once;
+        k_trace_blend_f32<T, IN><<<grid, kThreads, kBlendF32Smem, st>>>(lo, hi, alpha, tb, *A);
+    } else {
+        static bool once = (allow_blend_smem(k_query_blend_f32<T, IN>), true);
+        (void)once;
+        k_query_blend_f32<T, IN><<<grid, kThreads, kBlendF32Smem, st>>>(lo, hi, alpha, tb, x, Q, D, sdf);
+    }
+}
+
+void go_blend_f32_any(bool trace, int in_dim, bool f16, const DecPtrs& lo, const DecPtrs& hi, float alpha,
+                      const Tables& tb, const TraceArgs* A, const float* x, long long Q, int D, float* sdf,
+                      int grid, cudaStream_t st) {
+    if (in_dim == 35) {
+        if (f16) go_blend_f32<__half, 35>(trace, lo, hi, alpha, tb, A, x, Q, D, sdf, grid, st);
+        else go_blend_f32<float, 35>(trace, lo, hi, alpha, tb, A, x, Q, D, sdf, grid, st);
+    } else {
+        if (f16) go_blend_f32<__half, 32>(trace, lo, hi, alpha, tb, A, x, Q, D, sdf, grid, st);
+        else go_blend_f32<float, 32>(trace, lo, hi, alpha, tb, A, x, Q, D, sdf, grid, st);
+    }
+}
+
+// Normalises the accumulated blended gradients of the hit rays.
+__global__ void k_normalise_hits(const int* __restrict__ hit_count, const int32_t* __restrict__ hit_list,
+                                 float* __restrict__ normal) {
+    const long long n = *hit_count;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        float* v = normal + 3 * (size_t)hit_list[i];
+        const float nn = sqrtf(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+        const float inv = nn > 0.f ? 1.0f / nn : 0.f;
+        v[0] *= inv;
+        v[1] *= inv;
+        v[2] *= inv;
+    }
+}
+
 }  // namespace
 
 int launch_trace_fp32(const nglod_decoder* dec, const Tables& tb, const TraceArgs& A, bool f16, int sms,
@@ -485,6 +673,52 @@ int launch_normals(const nglod_decoder* dec, const Tables& tb, const TraceArgs& 
     G.mode = 1;
     G.out = normal;
     return run_grad(dec, tb, G, f16, sms, st);
+}
+
+int launch_trace_blend_f32(const nglod_decoder* lo, const nglod_decoder* hi, float alpha, const Tables& tb,
+                           const TraceArgs& A, bool f16, int sms, cudaStream_t st) {
+    go_blend_f32_any(true, lo->in_dim, f16, dec_ptrs(lo), dec_ptrs(hi), alpha, tb, &A, nullptr, 0, A.D, nullptr,
+                     sms * 2, st);
+    NGLOD_CUDA(cudaGetLastError());
+    return NGLOD_OK;
+}
+
+int launch_query_blend_f32(const nglod_decoder* lo, const nglod_decoder* hi, float alpha, const Tables& tb,
+                           const float* x, long long Q, int D, float* sdf, bool f16, int sms, cudaStream_t st) {
+    go_blend_f32_any(false, lo->in_dim, f16, dec_ptrs(lo), dec_ptrs(hi), alpha, tb, nullptr, x, Q, D, sdf,
+                     grid_items(Q, kThreads, sms, 2), st);
+    NGLOD_CUDA(cudaGetLastError());
+    return NGLOD_OK;
+}
+
+// Normals of the blended field: the normalised (1 - alpha) grad d_lo +
+// alpha grad d_hi at each hit point (d_lo over depths 3..D-1 of the hit
+// voxel's ancestors, d_hi over 3..D).
+int launch_normals_blend(const nglod_decoder* lo, const nglod_decoder* hi, float alpha, const Tables& tb,
+                         const TraceArgs& A, float* normal, bool f16, int sms, cudaStream_t st) {
+    NGLOD_CUDA(cudaMemsetAsync(normal, 0, sizeof(float) * 3 * (size_t)A.R, st));
+    GradArgs G{};
+    G.o = A.o;
+    G.d = A.d;
+    G.t_hit = A.t_hit;
+    G.hit_vox = A.hit_vox;
+    G.hit_count = A.hit_count;
+    G.hit_list = A.hit_list;
+    G.n = A.R;
+    G.D = A.D;
+    G.mode = 2;
+    G.out = normal;
+    G.dcap = A.D - 1;
+    G.w = 1.0f - alpha;
+    int rc = run_grad(lo, tb, G, f16, sms, st);
+    if (rc) return rc;
+    G.dcap = A.D;
+    G.w = alpha;
+    if ((rc = run_grad(hi, tb, G, f16, sms, st))) return rc;
+    k_normalise_hits<<<std::max(1, (int)std::min<long long>((A.R + 255) / 256, (long long)sms * 8)), 256, 0, st>>>(
+        A.hit_count, A.hit_list, normal);
+    NGLOD_CUDA(cudaGetLastError());
+    return NGLOD_OK;
 }
 
 }  // namespace nglod

@@ -484,3 +484,233 @@ int launch_trace_batch_tc(const TraceJob* jobs, const JobGroup* groups, int ngro
     return NGLOD_OK;
 }
 }  // namespace nglod
+
+// ---------------------------------------------------------------------------
+// Level blending (Sec. 3.2, Eq. 3), BF16 decode: every slot decodes the
+// feature sum up to depth D-1 with LOD L*'s decoder and the sum up to D with
+// LOD L*+1's, and takes (1 - alpha) d_lo + alpha d_hi.  One gather pass fills
+// both A tiles (the second only adds the deepest level); the two MMAs run
+// one after the other through the same 128 TMEM columns, so residency stays
+// at 4 CTAs per SM.
+// ---------------------------------------------------------------------------
+namespace nglod {
+namespace {
+
+struct BlendSmem {
+    // each: its decoder's B tile and epilogue terms, its own A tile and mbarrier
+    alignas(1024) BfSmem lo;
+    alignas(1024) BfSmem hi;
+};
+constexpr int kBlendSmem = (int)((sizeof(BlendSmem) + 1023) / 1024 * 1024);
+
+__device__ __forceinline__ void setup_blend(BlendSmem& S) {
+    if (threadIdx.x == 0) {
+        tc::mbar_init(&S.lo.bar, 1);
+        tc::mbar_init(&S.hi.bar, 1);
+    }
+    if ((threadIdx.x >> 5) == 0) {
+        tc::tmem_alloc(&S.lo.taddr, kHidden);
+        tc::tmem_relinquish();
+    }
+    tc::fence_proxy_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+}
+
+// Group-cooperative: this lane's channels of z_lo (depths 3..dd-1 of a
+// depth-dd voxel) and z_hi = z_lo + psi_dd.
+template <typename T>
+__device__ __forceinline__ void gather_pair(const Tables& tb, int dd, int dlo, int vox, uint32_t ijk, float q0,
+                                            float q1, float q2, unsigned gmask, int gbase, int l, float4& zl,
+                                            float4& zh) {
+    zl = gather_levels<T>(tb, dd, kFirstFeatureDepth, min(dd, dlo), vox, ijk, q0, q1, q2, gmask, gbase, l);
+    zh = zl;
+    if (dd > dlo) {
+        const float4 p = gather_levels<T>(tb, dd, dd, dd, vox, ijk, q0, q1, q2, gmask, gbase, l);
+        zh = make_float4(zl.x + p.x, zl.y + p.y, zl.z + p.z, zl.w + p.w);
+    }
+}
+
+// Both MMAs and epilogues of a tile; returns 0 or which wait expired (1, 2).
+template <int IN>
+__device__ __forceinline__ int blend_decode(BlendSmem& S, uint32_t taddr, uint32_t& ph_lo, uint32_t& ph_hi,
+                                            float b2lo, float b2hi, float alpha, float x0, float x1, float x2,
+                                            float& dhat) {
+    if (!__syncthreads_and(mma_tile<false>(S.lo, taddr, ph_lo))) return 1;
+    const float dlo = epilogue<IN>(S.lo, taddr, b2lo, x0, x1, x2);
+    if (!__syncthreads_and(mma_tile<false>(S.hi, taddr, ph_hi))) return 2;
+    const float dhi = epilogue<IN>(S.hi, taddr, b2hi, x0, x1, x2);
+    dhat = fmaf(alpha, dhi - dlo, dlo);
+    return 0;
+}
+
+__device__ __forceinline__ void teardown_blend(BlendSmem& S, uint32_t taddr, int failed, uint32_t ph_lo,
+                                               uint32_t ph_hi) {
+    if (failed == 2) teardown_tmem(S.hi, taddr, false, ph_hi);
+    else teardown_tmem(S.lo, taddr, failed == 0, ph_lo);
+}
+
+template <typename T, int IN>
+__global__ void __launch_bounds__(kTM, kCtasPerSm) k_trace_blend_bf16(const DecPtrsB plo, const DecPtrsB phi,
+                                                                     float alpha, const Tables tb, const TraceArgs A,
+                                                                     int* __restrict__ err) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    BlendSmem& S = *reinterpret_cast<BlendSmem*>(smem_raw);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = lane >> 3, l = lane & 7, gbase = g << 3;
+    const unsigned gmask = 0xffu << gbase;
+    stage_bf16_decoder<IN, false>(S.lo, plo);
+    stage_bf16_decoder<IN, false>(S.hi, phi);
+    setup_blend(S);
+    const uint32_t taddr = S.lo.taddr;
+    uint32_t ph_lo = 0, ph_hi = 0;
+    int failed = 0;
+    RaySlot st;
+    st.ray = -1;
+    st.hit_ray = -1;
+    RayQueue Qu;
+    Qu.init();
+    for (;;) {
+        refill(st, Qu, A, tb, lane);
+        const bool act = st.ray >= 0;
+        if (!__syncthreads_or(act)) break;
+        const float x0 = fmaf(st.t, st.dx, st.ox), x1 = fmaf(st.t, st.dy, st.oy), x2 = fmaf(st.t, st.dz, st.oz);
+        const float q0 = __fadd_rn(x0, 1.0f), q1 = __fadd_rn(x1, 1.0f), q2 = __fadd_rn(x2, 1.0f);
+#pragma unroll 1
+        for (int r = 0; r < 8; ++r) {
+            const int s = r * 4 + g;
+            const int sact = __shfl_sync(0xffffffffu, act ? 1 : 0, s);
+            const int svox = __shfl_sync(0xffffffffu, st.vox, s);
+            const uint32_t sijk = __shfl_sync(0xffffffffu, st.ijk, s);
+            const float s0 = __shfl_sync(0xffffffffu, q0, s);
+            const float s1 = __shfl_sync(0xffffffffu, q1, s);
+            const float s2 = __shfl_sync(0xffffffffu, q2, s);
+            float4 zl = make_float4(0.f, 0.f, 0.f, 0.f), zh = zl;
+            if (sact) gather_pair<T>(tb, A.D, A.D - 1, svox, sijk, s0, s1, s2, gmask, gbase, l, zl, zh);
+            put_z<false>(S.lo, warp * 32 + s, l, zl, 1.0f);
+            put_z<false>(S.hi, warp * 32 + s, l, zh, 1.0f);
+        }
+        float dhat = 0.0f;
+        failed = blend_decode<IN>(S, taddr, ph_lo, ph_hi, plo.b2, phi.b2, alpha, x0, x1, x2, dhat);
+        if (failed) {
+            if (threadIdx.x == 0) atomicExch(err, kStatusTimeout);
+            break;
+        }
+        if (act) step_update(st, dhat, A, tb);
+        publish_hits(st, A, lane);
+    }
+    teardown_blend(S, taddr, failed, ph_lo, ph_hi);
+}
+
+template <typename T, int IN>
+__global__ void __launch_bounds__(kTM, kCtasPerSm) k_query_blend_bf16(const DecPtrsB plo, const DecPtrsB phi,
+                                                                     float alpha, const Tables tb,
+                                                                     const float* __restrict__ x, long long Q, int D,
+                                                                     float* __restrict__ sdf, int* __restrict__ err) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    BlendSmem& S = *reinterpret_cast<BlendSmem*>(smem_raw);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = lane >> 3, l = lane & 7, gbase = g << 3;
+    const unsigned gmask = 0xffu << gbase;
+    stage_bf16_decoder<IN, false>(S.lo, plo);
+    stage_bf16_decoder<IN, false>(S.hi, phi);
+    setup_blend(S);
+    const uint32_t taddr = S.lo.taddr;
+    uint32_t ph_lo = 0, ph_hi = 0;
+    int failed = 0;
+    const long long ntiles = (Q + kTM - 1) / kTM;
+    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const long long qi = tile * kTM + threadIdx.x;
+        const bool act = qi < Q;
+        float x0 = 0.f, x1 = 0.f, x2 = 0.f;
+        if (act) {
+            x0 = x[3 * qi];
+            x1 = x[3 * qi + 1];
+            x2 = x[3 * qi + 2];
+        }
+        int vox;
+        uint32_t ijk;
+        const int dd = act ? locate_descend(tb, D, x0, x1, x2, vox, ijk) : -1;
+        const float q0 = __fadd_rn(x0, 1.0f), q1 = __fadd_rn(x1, 1.0f), q2 = __fadd_rn(x2, 1.0f);
+#pragma unroll 1
+        for (int r = 0; r < 8; ++r) {
+            const int s = r * 4 + g;
+            const int sdd = __shfl_sync(0xffffffffu, dd, s);
+            const int svox = __shfl_sync(0xffffffffu, vox, s);
+            const uint32_t sijk = __shfl_sync(0xffffffffu, ijk, s);
+            const float s0 = __shfl_sync(0xffffffffu, q0, s);
+            const float s1 = __shfl_sync(0xffffffffu, q1, s);
+            const float s2 = __shfl_sync(0xffffffffu, q2, s);
+            float4 zl = make_float4(0.f, 0.f, 0.f, 0.f), zh = zl;
+            if (sdd >= kFirstFeatureDepth)
+                gather_pair<T>(tb, sdd, D - 1, svox, sijk, s0, s1, s2, gmask, gbase, l, zl, zh);
+            put_z<false>(S.lo, warp * 32 + s, l, zl, 1.0f);
+            put_z<false>(S.hi, warp * 32 + s, l, zh, 1.0f);
+        }
+        float out = 0.0f;
+        failed = blend_decode<IN>(S, taddr, ph_lo, ph_hi, plo.b2, phi.b2, alpha, x0, x1, x2, out);
+        if (failed) {
+            if (threadIdx.x == 0) atomicExch(err, kStatusTimeout);
+            break;
+        }
+        if (act) sdf[qi] = out;
+    }
+    teardown_blend(S, taddr, failed, ph_lo, ph_hi);
+}
+
+template <typename T, int IN>
+void go_blend(bool trace, const DecPtrsB& lo, const DecPtrsB& hi, float alpha, const Tables& tb, const TraceArgs* A,
+              const float* x, long long Q, int D, float* sdf, int* err, int grid, cudaStream_t st) {
+    static_assert(sizeof(BlendSmem) <= kBlendSmem && kBlendSmem <= 48 * 1024, "shared layout");
+    if (trace) {
+        static bool once = (prefer_l1(k_trace_blend_bf16<T, IN>), true);
+        (void)once;
+        k_trace_blend_bf16<T, IN><<<grid, kTM, kBlendSmem, st>>>(lo, hi, alpha, tb, *A, err);
+    } else {
+        static bool once = (prefer_l1(k_query_blend_bf16<T, IN>), true);
+        (void)once;
+        k_query_blend_bf16<T, IN><<<grid, kTM, kBlendSmem, st>>>(lo, hi, alpha, tb, x, Q, D, sdf, err);
+    }
+}
+
+void go_blend_any(bool trace, int in_dim, bool f16, const DecPtrsB& lo, const DecPtrsB& hi, float alpha,
+                  const Tables& tb, const TraceArgs* A, const float* x, long long Q, int D, float* sdf, int* err,
+                  int grid, cudaStream_t st) {
+    if (in_dim == 35) {
+        if (f16) go_blend<__half, 35>(trace, lo, hi, alpha, tb, A, x, Q, D, sdf, err, grid, st);
+        else go_blend<float, 35>(trace, lo, hi, alpha, tb, A, x, Q, D, sdf, err, grid, st);
+    } else {
+        if (f16) go_blend<__half, 32>(trace, lo, hi, alpha, tb, A, x, Q, D, sdf, err, grid, st);
+        else go_blend<float, 32>(trace, lo, hi, alpha, tb, A, x, Q, D, sdf, err, grid, st);
+    }
+}
+
+}  // namespace
+
+int launch_trace_blend_bf16(const nglod_svo* svo, const nglod_decoder* lo, const nglod_decoder* hi, float alpha,
+                            const Tables& tb, const TraceArgs& A, bool f16, cudaStream_t st) {
+    int* err = A.queue + 1;      // the workspace header's status word
+    go_blend_any(true, lo->in_dim, f16, bptrs(lo, 1.0f), bptrs(hi, 1.0f), alpha, tb, &A, nullptr, 0, A.D, nullptr,
+                 err, svo->num_sms * kCtasPerSm, st);
+    NGLOD_CUDA(cudaGetLastError());
+    return NGLOD_OK;
+}
+
+int launch_query_blend_bf16(const nglod_svo* svo, const nglod_decoder* lo, const nglod_decoder* hi, float alpha,
+                            const Tables& tb, const float* x, long long Q, int D, float* sdf, bool f16,
+                            cudaStream_t st) {
+    int* err = svo->dstatus;
+    NGLOD_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
+    const long long tiles = (Q + kTM - 1) / kTM;
+    const int grid = (int)std::max<long long>(1, std::min<long long>(tiles, (long long)svo->num_sms * kCtasPerSm));
+    go_blend_any(false, lo->in_dim, f16, bptrs(lo, 1.0f), bptrs(hi, 1.0f), alpha, tb, nullptr, x, Q, D, sdf, err,
+                 grid, st);
+    NGLOD_CUDA(cudaGetLastError());
+    int h = 0;
+    NGLOD_CUDA(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    NGLOD_CUDA(cudaStreamSynchronize(st));
+    if (h) return fail(NGLOD_ERR_TIMEOUT, "sdf_query_blend: tensor-core wait expired");
+    return NGLOD_OK;
+}
+}  // namespace nglod

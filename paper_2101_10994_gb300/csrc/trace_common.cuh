@@ -318,6 +318,17 @@ int launch_query_bf16(const nglod_svo* svo, const Tables& tb, const nglod_decode
                       cudaStream_t st);
 int launch_trace_batch_tc(const TraceJob* jobs, const JobGroup* groups, int ngroups, int in_dim, bool f16, bool fp8,
                           int ctas_per_sm, int sms, int* err, cudaStream_t st);
+int launch_trace_blend_f32(const nglod_decoder* lo, const nglod_decoder* hi, float alpha, const Tables& tb,
+                           const TraceArgs& A, bool f16, int sms, cudaStream_t st);
+int launch_query_blend_f32(const nglod_decoder* lo, const nglod_decoder* hi, float alpha, const Tables& tb,
+                           const float* x, long long Q, int D, float* sdf, bool f16, int sms, cudaStream_t st);
+int launch_normals_blend(const nglod_decoder* lo, const nglod_decoder* hi, float alpha, const Tables& tb,
+                         const TraceArgs& A, float* normal, bool f16, int sms, cudaStream_t st);
+int launch_trace_blend_bf16(const nglod_svo* svo, const nglod_decoder* lo, const nglod_decoder* hi, float alpha,
+                            const Tables& tb, const TraceArgs& A, bool f16, cudaStream_t st);
+int launch_query_blend_bf16(const nglod_svo* svo, const nglod_decoder* lo, const nglod_decoder* hi, float alpha,
+                            const Tables& tb, const float* x, long long Q, int D, float* sdf, bool f16,
+                            cudaStream_t st);
 int launch_trace_batch_f32(const TraceJob* jobs, const JobGroup* groups, int ngroups, int in_dim, bool f16,
                            int ctas_per_sm, int sms, cudaStream_t st);
 

@@ -27,7 +27,7 @@ EXPORTS = ["nglod_last_error", "svo_build", "svo_info", "svo_device_arrays", "sv
            "svo_trace_rays_sizes", "sdf_backward", "sdf_l2_backward", "nglod_adam_step",
            "nglod_features_absmax", "svo_trace_rays_async", "svo_trace_rays_check",
            "sphere_trace_batch_create", "sphere_trace_batch_run", "sphere_trace_batch_status",
-           "sphere_trace_batch_free"]
+           "sphere_trace_batch_free", "sdf_query_blend", "sphere_trace_blend", "nglod_lod_select"]
 
 
 class NglodError(RuntimeError):
@@ -97,6 +97,10 @@ def lib():
         L.sphere_trace_batch_status.argtypes = [P, P]
         L.sphere_trace_batch_free.argtypes = [P]
         L.sphere_trace_batch_free.restype = None
+        L.sdf_query_blend.argtypes = [P, P, P, P, P, i64, C.c_float, i32, P, P]
+        L.sphere_trace_blend.argtypes = [P, P, P, P, P, P, i64, C.c_float, P, P, P, P, P, sz, P, P, P, P, P]
+        L.nglod_lod_select.argtypes = [C.c_float] * 5
+        L.nglod_lod_select.restype = C.c_float
         L.nglod_adam_step.argtypes = [P, P, P, P, i64, C.c_float, C.c_float, C.c_float, C.c_float, i32, P]
         L.svo_trace_rays_noalloc.argtypes = [P, P, P, i64, i32, P, P, P, i64, P, P]
         _lib = L
@@ -357,6 +361,63 @@ def trace_normals(svo: SVO, feats: Features, dec: DecoderDev, o, d, lists: RayLi
 def sphere_trace_status(out, stream=None):
     """Raises if the sphere_trace that filled ``out`` hit an expired wait."""
     _check(lib().sphere_trace_status(out["work"].data_ptr(), C.c_void_p(_stream(stream))))
+
+
+# ----------------------------------------------------------------------------
+# Continuous LOD (level blending, Eq. 3) and LOD selection
+# ----------------------------------------------------------------------------
+def lod_select(distance: float, d_near: float, d_far: float, lod_near: float, lod_far: float) -> float:
+    """Continuous LOD moving linearly with the distance to the object."""
+    return float(lib().nglod_lod_select(distance, d_near, d_far, lod_near, lod_far))
+
+
+def blend_lists_lod(lod_tilde: float) -> int:
+    """The LOD whose ray lists sphere_trace_blend walks: ceil(L~)."""
+    import math
+    return int(math.ceil(float(np.float32(lod_tilde))))
+
+
+def sdf_query_blend(svo: SVO, feats: Features, dec_lo: DecoderDev, dec_hi: DecoderDev | None, x, lod_tilde: float,
+                    decode: str = "f32", stream=None):
+    import torch
+    _require_cuda(x)
+    x = x.contiguous()
+    Q = int(x.shape[0])
+    out = torch.empty(Q, dtype=torch.float32, device=x.device)
+    fc, lo = feats.c(), dec_lo.c()
+    hi = (dec_hi or dec_lo).c()
+    _check(lib().sdf_query_blend(svo.h, C.byref(fc), C.byref(lo), C.byref(hi), x.data_ptr(), Q, lod_tilde,
+                                 {"f32": F32, "bf16": BF16, "fp8": FP8}[decode], out.data_ptr(),
+                                 C.c_void_p(_stream(stream))))
+    return out
+
+
+def sphere_trace_blend(svo: SVO, feats: Features, dec_lo: DecoderDev, dec_hi: DecoderDev | None, o, d,
+                       lists: RayLists, lod_tilde: float, eps: float = 1e-3, far: float = 5.0, max_steps: int = 128,
+                       osc: bool = False, decode: str = "f32", normals: bool = True, stream=None, out=None):
+    """Sphere-traces the Eq. 3 blend; ``lists`` must be at LOD ceil(L~)."""
+    import torch
+    _require_cuda(o, d)
+    if lists.lod != blend_lists_lod(lod_tilde):
+        raise ValueError("sphere_trace_blend: lists must be traced at LOD ceil(lod_tilde)")
+    R = int(o.shape[0])
+    dev = o.device
+    if out is None:
+        out = dict(t=torch.empty(R, dtype=torch.float32, device=dev),
+                   hit=torch.empty(R, dtype=torch.uint8, device=dev),
+                   steps=torch.empty(R, dtype=torch.int32, device=dev),
+                   normal=torch.empty((R, 3), dtype=torch.float32, device=dev) if normals else None,
+                   work=torch.empty(max(lib().sphere_trace_workspace(R), 1), dtype=torch.uint8, device=dev))
+    p = _TraceParams(eps, far, max_steps, int(osc), {"f32": F32, "bf16": BF16, "fp8": FP8}[decode], int(normals))
+    fc, lo = feats.c(), dec_lo.c()
+    hi = (dec_hi or dec_lo).c()
+    _check(lib().sphere_trace_blend(svo.h, C.byref(fc), C.byref(lo), C.byref(hi), o.data_ptr(), d.data_ptr(), R,
+                                    lod_tilde, C.byref(p), lists.ray_offsets.data_ptr(), lists.voxel_id.data_ptr(),
+                                    lists.t_range.data_ptr(), out["work"].data_ptr(), out["work"].numel(),
+                                    out["t"].data_ptr(), out["hit"].data_ptr(), _ptr(out["steps"]),
+                                    _ptr(out["normal"]), C.c_void_p(_stream(stream))))
+    out["hit_voxel"] = out["work"][256:256 + 4 * R].view(torch.int32)
+    return out
 
 
 def new_grads(svo: SVO, decs, device="cuda"):
