@@ -63,7 +63,8 @@ def workload(width, height):
     feats = S.readout_features(oc, sc)
     dec = S.readout_decoder(5)
     o, d, pix = S.camera_rays(width, height, tile=8)
-    return dict(scene=sc, octree=oc, feats=feats, dec=dec, o=o, d=d, lod=5, eps=1e-3, far=5.0,
+    return dict(scene=sc, octree=oc, feats=feats, dec=dec, dec_lo=S.readout_decoder(4), o=o, d=d, lod=5, eps=1e-3,
+                far=5.0,
                 max_steps=128)
 
 
@@ -229,6 +230,32 @@ def run_ours(args, rank, world, local_rank):
             hit_pixels=hits, wall_s=t_wall)
         if clock_info is None or mode == "bf16":
             clock_info = sampler.summary()
+
+    # ---- continuous LOD (Eq. 3): the same frame at L~ = lod - 0.5, BF16 ----
+    if "bf16" in modes and W["lod"] >= 2:
+        lt = W["lod"] - 0.5
+        dlo = ng.DecoderDev.from_decoder(W["dec_lo"])
+        out = dict(t=torch.empty(R, device=dev), hit=torch.empty(R, dtype=torch.uint8, device=dev),
+                   steps=torch.empty(R, dtype=torch.int32, device=dev), normal=torch.empty((R, 3), device=dev),
+                   work=torch.empty(ng.lib().sphere_trace_workspace(R), dtype=torch.uint8, device=dev))
+        bl = []
+        for k in range(args.warmup + args.steps):
+            flush.zero_()
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            e[0].record()
+            lists = ng.svo_trace_rays(svo, o, d, ng.blend_lists_lod(lt))
+            e[1].record()
+            ng.sphere_trace_blend(svo, feats, dlo, dec, o, d, lists, lt, eps=W["eps"], far=W["far"],
+                                  max_steps=W["max_steps"], decode="bf16", normals=True, out=out)
+            e[2].record()
+            e[2].synchronize()
+            if k >= args.warmup:
+                bl.append((e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2]), int(out["steps"].sum().item())))
+        ms = statistics.mean(a + b for a, b, _ in bl)
+        results["bf16_blend"] = dict(lod_tilde=lt, ms_per_step=ms, rays_per_s=world * R / (ms * 1e-3),
+                                     ms_traverse=statistics.mean(a for a, _, _ in bl),
+                                     ms_trace_and_normals=statistics.mean(b for _, b, _ in bl),
+                                     queries_per_frame=bl[-1][2], hit_pixels=int(out["hit"].sum().item()))
 
     # ---- end to end through the public API with pinned host buffers ----
     mode = "bf16" if "bf16" in modes else modes[0]
@@ -509,7 +536,9 @@ def main():
             "traversal_roofline": traversal_roofline(W, r, head, peaks),
             "clocks": clocks,
             "e2e": e2e,
-            "gpu_launches": args.steps * len(modes) * (W["lod"] + 6),   # prep + (lod+2) levels + offsets + trace + normals
+            # per frame: prep + (lod+2) levels + offsets + trace + normals; the blended frame adds
+            # a second gradient pass and the normalisation
+            "gpu_launches": args.steps * (len(modes) * (W["lod"] + 6) + ("bf16_blend" in res) * (W["lod"] + 8)),
         }
         if "bf16" in res and "f32" in res:
             line["bf16_speedup"] = res["f32"]["ms_per_step"] / res["bf16"]["ms_per_step"]
