@@ -324,9 +324,10 @@ __global__ void __launch_bounds__(kThreads) k_grad(const DecPtrs dp, const Table
 // Sphere tracing with adaptive stepping, FP32 decode (Sec. 3.4, A.4)
 // ---------------------------------------------------------------------------
 template <typename T, int IN>
-__global__ void __launch_bounds__(kThreads, 3) k_trace_f32(const DecPtrs dp, const Tables tb, const TraceArgs A) {
+__global__ void __launch_bounds__(kThreads, 2) k_trace_f32(const DecPtrs dp, const Tables tb, const TraceArgs A) {
     __shared__ __align__(16) float zbuf[kWarps][32 * kZStride];
     __shared__ __align__(16) SmemDecoder sd;
+    __shared__ __align__(16) int cidbuf[kWarps][kCidBufInts];
     stage_decoder<IN>(sd, dp.W1, dp.b1, dp.W2);
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -344,19 +345,20 @@ __global__ void __launch_bounds__(kThreads, 3) k_trace_f32(const DecPtrs dp, con
         const bool act = S.ray >= 0;
         const float x0 = fmaf(S.t, S.dx, S.ox), x1 = fmaf(S.t, S.dy, S.oy), x2 = fmaf(S.t, S.dz, S.oz);
         const float q0 = __fadd_rn(x0, 1.0f), q1 = __fadd_rn(x1, 1.0f), q2 = __fadd_rn(x2, 1.0f);
-#pragma unroll 1
-        for (int r = 0; r < 8; ++r) {
-            const int s = r * 4 + g;
-            const int sact = __shfl_sync(0xffffffffu, act ? 1 : 0, s);
-            const int svox = __shfl_sync(0xffffffffu, S.vox, s);
-            const uint32_t sijk = __shfl_sync(0xffffffffu, S.ijk, s);
-            const float s0 = __shfl_sync(0xffffffffu, q0, s);
-            const float s1 = __shfl_sync(0xffffffffu, q1, s);
-            const float s2 = __shfl_sync(0xffffffffu, q2, s);
-            float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (sact) z = gather_slot<T>(tb, A.D, svox, sijk, s0, s1, s2, gmask, gbase, l);
-            *reinterpret_cast<float4*>(zb + s * kZStride + 4 * l) = z;
-        }
+        auto slot = [&](int s) {
+            GSlot G;
+            G.dd = __shfl_sync(0xffffffffu, act ? A.D : -1, s);
+            G.vox = __shfl_sync(0xffffffffu, S.vox, s);
+            G.ijk = __shfl_sync(0xffffffffu, S.ijk, s);
+            G.q0 = __shfl_sync(0xffffffffu, q0, s);
+            G.q1 = __shfl_sync(0xffffffffu, q1, s);
+            G.q2 = __shfl_sync(0xffffffffu, q2, s);
+            return G;
+        };
+        auto store = [&](int r, float4, float4 z) {
+            *reinterpret_cast<float4*>(zb + (r * 4 + g) * kZStride + 4 * l) = z;
+        };
+        gather_warp<T>(tb, kMaxDepth, kMaxDepth, cidbuf[warp], slot, store, gmask, gbase, g, l);
         __syncwarp();
         const float dhat = mlp_f32<IN>(sd, dp.b2, zb + lane * kZStride, x0, x1, x2);
         __syncwarp();
@@ -632,7 +634,7 @@ __global__ void k_normalise_hits(const int* __restrict__ hit_count, const int32_
 
 int launch_trace_fp32(const nglod_decoder* dec, const Tables& tb, const TraceArgs& A, bool f16, int sms,
                       cudaStream_t st) {
-    const int grid = sms * 3;
+    const int grid = sms * 2;
     const DecPtrs P = dec_ptrs(dec);
     if (dec->in_dim == 35) {
         if (f16) launch_trace_f32<__half, 35>(P, tb, A, grid, st); else launch_trace_f32<float, 35>(P, tb, A, grid, st);
