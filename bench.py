@@ -33,7 +33,7 @@ sys.path.insert(0, ROOT)
 METRIC = "sphere-traced rays/s and SDF queries/s at 1080p LOD5, bf16 vs fp32, % roofline"
 PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
 CSRC = os.path.join(ROOT, "paper_2101_10994_gb300", "csrc")
-KERNEL_SRC = {"k_level": ["traverse.cu", "nglod_internal.cuh"],
+KERNEL_SRC = {"k_traverse": ["traverse.cu", "nglod_internal.cuh"],
               "k_trace_f32": ["query.cu", "query_common.cuh", "trace_common.cuh", "nglod_internal.cuh"],
               "k_trace_bf16": ["trace_bf16.cu", "query_common.cuh", "trace_common.cuh", "tcgen05.cuh",
                                "nglod_internal.cuh"]}
@@ -313,32 +313,32 @@ def profiled_traffic(kernel):
 
 
 def traversal_bytes(W, sizes):
-    """Algorithmic bytes of one frame's level kernels (depths 0..D-1): each
-    level reads its pair list (8 B/pair; implicit at the root), the node
-    records of its depth (16 B/voxel) and the ray records (32 B/ray), and
-    writes the next list (8 B/pair) or, at the last level, the final entries
-    (voxel id 4 B + t range 8 B + ray 4 B)."""
-    oc = W["octree"]
+    """Algorithmic bytes of one frame's traversal as this design runs it
+    (tiles of rays swept level by level on chip): every ray read once (24 B)
+    with its count written and read back and its CSR offset written
+    (3 x 4 B); one node record (16 B) per ray/voxel pair Decide visits at
+    depths 0..D-1; every final entry (voxel id 4 B + t range 8 B) staged,
+    read back and written to its final position (3 x 12 B)."""
     R = sizes[0]
     D = len(sizes) - 1
-    total = 0
-    for dp in range(D):
-        total += (8 * sizes[dp] if dp > 0 else 0) + 16 * oc.counts()[dp] + 32 * R
-        total += 16 * sizes[dp + 1] if dp + 1 == D else 8 * sizes[dp + 1]
-    return total, D
+    H = sizes[D]
+    visits = sum(sizes[:D])
+    return 36 * R + 16 * visits + 36 * H
 
 
 def traversal_roofline(W, res, mode, peaks):
-    """The traversal's level kernel (one launch per depth) against HBM."""
+    """The traversal (k_traverse + tile scan + placement, 3 launches) against
+    HBM; it is issue-bound on the slab tests, so this fraction is low."""
     hbm = peaks.get("hbm_gbs", 6800.0)
-    nbytes, launches = traversal_bytes(W, res["level_sizes"])
+    nbytes = traversal_bytes(W, res["level_sizes"])
     sec = res["ms_traverse"] * 1e-3
     achieved = nbytes / sec / 1e9
-    return {"bound": "hbm", "kernel": "k_level", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-            "frac": achieved / hbm, "traffic": profiled_traffic("k_level"),
-            "bytes_per_launch": nbytes / launches, "launches_per_frame": launches,
+    return {"bound": "hbm", "kernel": "k_traverse", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+            "frac": achieved / hbm, "traffic": profiled_traffic("k_traverse"),
+            "bytes_per_frame": nbytes, "launches_per_frame": 3,
             "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in peaks else "fallback",
-            "timing": "CUDA events around svo_trace_rays (level kernels + ray prep + offsets + H readback)"}
+            "timing": "CUDA events around svo_trace_rays (3 launches + the H read-back)",
+            "note": "issue-bound on the 8-child slab tests (ncu: ~64 % issue active); node records hit L1/L2"}
 
 
 def trace_roofline(W, res, mode, peaks):
@@ -488,9 +488,9 @@ def run_batch(args):
         "autotune": {"best_ctas_per_sm": best, "ms": tune},
         "hit_pixels": hits,
         "clocks": sampler.summary(),
-        # per graph replay: each job's traversal (prep + lod+2 levels + offsets), the reset and
-        # the persistent trace kernel, each job's normals
-        "gpu_launches": args.steps * (sum(j.lod + 4 for j in jobs) + 2 + len(jobs)),
+        # per graph replay: each job's traversal (3 launches), the reset and the persistent
+        # trace kernel, each job's normals
+        "gpu_launches": args.steps * (3 * len(jobs) + 2 + len(jobs)),
     }
     print(json.dumps(line))
 
@@ -536,9 +536,9 @@ def main():
             "traversal_roofline": traversal_roofline(W, r, head, peaks),
             "clocks": clocks,
             "e2e": e2e,
-            # per frame: prep + (lod+2) levels + offsets + trace + normals; the blended frame adds
-            # a second gradient pass and the normalisation
-            "gpu_launches": args.steps * (len(modes) * (W["lod"] + 6) + ("bf16_blend" in res) * (W["lod"] + 8)),
+            # per frame: traversal (tiles, tile scan, placement) + trace + normals; the blended
+            # frame adds a second gradient pass and the normalisation
+            "gpu_launches": args.steps * (len(modes) * 5 + ("bf16_blend" in res) * 7),
         }
         if "bf16" in res and "f32" in res:
             line["bf16_speedup"] = res["f32"]["ms_per_step"] / res["bf16"]["ms_per_step"]

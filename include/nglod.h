@@ -137,8 +137,10 @@ int svo_read_arrays(const nglod_svo* svo, int dp, void* h_node, int32_t* h_corne
 /* Releases the handle and its device memory (NULL is allowed). */
 void svo_free(nglod_svo* svo);
 
-/* Workspace bytes svo_trace_rays needs for R rays and intermediate ray/voxel
- * lists of up to pair_capacity entries per level. */
+/* Workspace bytes svo_trace_rays needs for R rays and a staging list of
+ * pair_capacity entries: a counter block, a 16-byte record per tile of 128
+ * rays, one count per ray and 12 bytes per staged entry (the intermediate
+ * per-level ray/voxel lists never leave on-chip memory). */
 size_t svo_trace_rays_workspace(int64_t R, int64_t pair_capacity);
 
 /* svo_trace_rays -- Algorithm 1 (RayTraceOctree) with Decide, ExclusiveSum,
@@ -150,20 +152,27 @@ size_t svo_trace_rays_workspace(int64_t R, int64_t pair_capacity);
  * max(t_near, 0) <= t_far (closed intervals).  A ray with a NaN/Inf component
  * or an all-zero direction hits nothing; a direction component below FLT_MIN
  * in magnitude makes that axis parallel.
+ * The levels run per tile of 128 consecutive rays inside one persistent
+ * kernel, each tile's frontier in shared memory (Decide, the block-wide
+ * ExclusiveSum and Subdivide on chip; a tile whose frontier outgrows it is
+ * re-run over halves of its rays).  Tiles stage their entries in any order;
+ * a scan of the tile counts then places them in ray order, so the result
+ * equals the global level-by-level sequence entry for entry.
  *   o, d          [R, 3] float32 origins / directions (device).
  *   work          device workspace of work_bytes >= svo_trace_rays_workspace(
  *                 R, pair_capacity); contents are scratch.
+ *   pair_capacity staging-list capacity (entries); must be >= H.
  * Outputs (CSR over rays, grouped by ray, front to back within a ray):
  *   ray_offsets   [R + 1] int32; hits of ray i are [ray_offsets[i],
  *                 ray_offsets[i+1]).
  *   voxel_id      [hit_capacity] int32 voxel ids at the target depth.
  *   t_range       [hit_capacity, 2] float32 (t_enter, t_exit) per hit.
  *   h_stats       host int64[2] (nullable): [0] = total hits H, [1] = largest
- *                 intermediate list (pairs) seen.
- * Errors: NGLOD_ERR_CAPACITY if H > hit_capacity or a list exceeds
- * pair_capacity (h_stats then holds the sizes needed so far; outputs are
- * unspecified); NGLOD_ERR_INVALID_ARG; NGLOD_ERR_TIMEOUT if the scan's
- * bounded look-back wait expired.  Synchronises the stream (to read H). */
+ *                 number of pairs Decide kept at any depth.
+ * Errors: NGLOD_ERR_CAPACITY if H > hit_capacity or H > pair_capacity
+ * (h_stats[0] then holds the H needed; outputs are unspecified);
+ * NGLOD_ERR_INVALID_ARG.  No kernel waits on another.  Synchronises the
+ * stream (to read H). */
 int svo_trace_rays(const nglod_svo* svo, const float* o, const float* d, int64_t R,
                    int target_lod, void* work, size_t work_bytes, int64_t pair_capacity,
                    int32_t* ray_offsets, int32_t* voxel_id, float* t_range,
@@ -178,10 +187,12 @@ int svo_trace_rays(const nglod_svo* svo, const float* o, const float* d, int64_t
  * The workspace is a 32 MiB array built into the library, present on every
  * GPU that loads it until the process exits.  The first call on a device
  * (with that device current) looks up the array's device address; make it
- * before any stream capture.  The intermediate-list capacity is whatever fits
- * in 32 MiB after the R ray records; R too large for even that is rejected
- * with NGLOD_ERR_CAPACITY before anything is launched, and lists that outgrow
- * the array return NGLOD_ERR_CAPACITY like svo_trace_rays.  Every call reuses
+ * before any stream capture.  The staging capacity is whatever fits in
+ * 32 MiB after the per-ray and per-tile records (about 2.1 M entries at
+ * 2 M rays); R whose records alone exceed it is rejected with
+ * NGLOD_ERR_CAPACITY before anything is read or launched, and more entries
+ * than the staging capacity return NGLOD_ERR_CAPACITY like svo_trace_rays.
+ * Every call reuses
  * the same array (counters and scan state are cleared at the start of each
  * call); calls that overlap on the GPU race on it.  Arguments, outputs,
  * results and the stream synchronisation are those of svo_trace_rays. */
@@ -192,8 +203,8 @@ int svo_trace_rays_noalloc(const nglod_svo* svo, const float* o, const float* d,
 
 /* svo_trace_rays_async -- svo_trace_rays without the final host read-back,
  * so the whole traversal is enqueued on the stream and can be captured in a
- * CUDA graph.  The caller sizes pair_capacity and hit_capacity (e.g. from an
- * earlier svo_trace_rays of the same frame); overflow or an expired wait is
+ * CUDA graph.  The caller sizes pair_capacity and hit_capacity (e.g. from
+ * an earlier svo_trace_rays of the same frame); overflow is
  * recorded in the workspace and reported by svo_trace_rays_check, and the
  * outputs are then unspecified.  Arguments as svo_trace_rays. */
 int svo_trace_rays_async(const nglod_svo* svo, const float* o, const float* d, int64_t R,

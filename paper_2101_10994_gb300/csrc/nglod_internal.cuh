@@ -199,6 +199,70 @@ __device__ __forceinline__ bool child_hit(const ChildSlabs& cs, uint32_t c, floa
     return true;
 }
 
+// All 8 children of voxel (i,j,k) at depth dp in one pass: the same values
+// and comparisons as child_slabs + child_hit (hence as 8 slab_test calls),
+// with the per-axis near/far terms combined pairwise -- the (x, y) pair once
+// for both z sides -- in the order child_hit uses (x, then y, then z; a later
+// axis replaces the running value only when strictly larger / smaller, so
+// even the sign of a zero result is the same).  Returns the hit mask by slot
+// and the origin octant (as origin_octant); with WANT_T the hit children's
+// (t_enter, t_exit) land in tin / tout by slot.
+template <bool WANT_T>
+__device__ __forceinline__ uint32_t child_hits8(const RayPrep& r, uint32_t ijk, int dp, uint32_t& oct,
+                                                float* tin = nullptr, float* tout = nullptr) {
+    const float s = pow2f(1 - dp);
+    const float hs = pow2f(-dp);
+    const float o[3] = {r.ox, r.oy, r.oz};
+    const float inv[3] = {r.ix, r.iy, r.iz};
+    const uint32_t c[3] = {unpack_i(ijk), unpack_j(ijk), unpack_k(ijk)};
+    float nr[3][2], fr[3][2];
+    uint32_t allow = 0xffu;
+    oct = 0;
+    constexpr uint32_t kSide[3][2] = {{0x55u, 0xaau}, {0x33u, 0xccu}, {0x0fu, 0xf0u}};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float lo = __fmaf_rn((float)c[a], s, -1.0f);
+        const float mid = __fadd_rn(lo, hs);
+        const float hi = __fadd_rn(mid, hs);
+        oct |= (o[a] >= mid) ? (1u << a) : 0u;
+        if ((r.par >> a) & 1) {
+            allow &= ((lo <= o[a] && o[a] <= mid) ? kSide[a][0] : 0u) | ((mid <= o[a] && o[a] <= hi) ? kSide[a][1] : 0u);
+            nr[a][0] = nr[a][1] = -INFINITY;
+            fr[a][0] = fr[a][1] = INFINITY;
+            continue;
+        }
+        const float t_lo = __fmul_rn(__fsub_rn(lo, o[a]), inv[a]);
+        const float t_mid = __fmul_rn(__fsub_rn(mid, o[a]), inv[a]);
+        const float t_hi = __fmul_rn(__fsub_rn(hi, o[a]), inv[a]);
+        nr[a][0] = t_lo < t_mid ? t_lo : t_mid;
+        fr[a][0] = t_lo < t_mid ? t_mid : t_lo;
+        nr[a][1] = t_mid < t_hi ? t_mid : t_hi;
+        fr[a][1] = t_mid < t_hi ? t_hi : t_mid;
+    }
+    uint32_t hit = 0;
+#pragma unroll
+    for (int xy = 0; xy < 4; ++xy) {
+        const int x = xy & 1, y = xy >> 1;
+        float n2 = nr[0][x], f2 = fr[0][x];
+        if (nr[1][y] > n2) n2 = nr[1][y];
+        if (fr[1][y] < f2) f2 = fr[1][y];
+#pragma unroll
+        for (int z = 0; z < 2; ++z) {
+            float tn = n2, tf = f2;
+            if (nr[2][z] > tn) tn = nr[2][z];
+            if (fr[2][z] < tf) tf = fr[2][z];
+            const float te = tn > 0.0f ? tn : 0.0f;
+            const int slot = xy | (z << 2);
+            if (te <= tf) hit |= 1u << slot;
+            if (WANT_T) {
+                tin[slot] = te;
+                tout[slot] = tf;
+            }
+        }
+    }
+    return hit & allow;
+}
+
 // Child-slot mask re-indexed by front-to-back rank: bit r is set iff slot
 // r ^ oct is occupied (an XOR permutation of the 8 bits, by conditional swaps
 // of adjacent bits, bit pairs and nibbles).

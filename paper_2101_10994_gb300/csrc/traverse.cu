@@ -1,16 +1,29 @@
-// svo_trace_rays: level-synchronous ray/octree intersection.
+// svo_trace_rays: ray/octree intersection (Algorithm 1 of the paper).
 //
-// Algorithm 1 of the paper runs, per octree level, Decide (one thread per
-// ray/voxel pair), ExclusiveSum of the decisions, then Subdivide (write the
-// hit voxels' occupied children, front to back) or, at the target level,
-// Compactify (keep the hit pairs).  Here the three steps of one level are a
-// single kernel: each CTA takes the next tile of the pair list (tiles are
-// handed out in order by an atomic counter), decides its pairs, scans the
-// decisions inside the CTA, obtains the tile's global offset with a
-// decoupled look-back over the preceding tiles' published sums, and writes
-// its children (or compacted hits) straight to their final positions.  The
-// decisions and their prefix sums never touch memory, the list sizes stay on
-// the device, and no host round trip happens between levels.
+// Algorithm 1 runs, per octree level, Decide (one thread per ray/voxel
+// pair), ExclusiveSum of the decisions, then Subdivide (write the hit
+// voxels' occupied children, front to back) or, at the target level,
+// Compactify (keep the hit pairs).  Rays are independent, so the same
+// level-by-level sweep is run here per tile of kTR consecutive rays, with
+// the whole frontier of the tile kept in shared memory: Decide, the
+// exclusive sum (a block scan) and Subdivide of every level happen on chip,
+// and only the final, compacted entries ever reach device memory.
+//   k_traverse  one persistent kernel takes tiles from an atomic ticket,
+//               sweeps their levels and appends each tile's entries (in
+//               ray order, front to back per ray) to a staging list at a
+//               slot reserved with one atomic; it also stores the tile's
+//               entry count and each ray's count;
+//   k_tile_scan the exclusive sum of the tile counts (one CTA);
+//   k_place     moves every tile's entries to their final CSR positions and
+//               writes its rays' offsets.
+// No CTA ever waits for another.  The output equals the global
+// level-synchronous sequence entry for entry: within a tile the per-level
+// scans keep pairs in (ray, front to back) order, and tiles are placed in
+// ray order.
+//
+// A tile whose frontier would outgrow shared memory at some level is
+// re-run over halves of its rays (recursively); a single ray always fits,
+// since a ray crosses at most 3 * 2^dp - 2 voxels of depth dp.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -22,29 +35,52 @@ namespace nglod {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr unsigned long long kFlagAgg = 1ull << 62;
-constexpr unsigned long long kFlagPre = 2ull << 62;
-constexpr unsigned long long kValMask = (1ull << 62) - 1;
-constexpr long kSpinLimit = 1l << 22;   // ~0.1-1 s of waiting, then time out
+constexpr int kTR = 128;                 // rays per tile
+constexpr int kFCap = 4096;              // frontier capacity (pairs) of one buffer
+static_assert(kFCap >= 3 * (1 << (kMaxDepth - 1)), "one ray's frontier must fit");
+constexpr int kScanThreads = 1024;
 
 struct Counters {
-    long long count[kMaxDepth + 2];   // list length entering each depth
-    long long max_pairs;
+    long long count[kMaxDepth + 2];   // pairs kept at each depth (count[0] = R)
+    long long max_pairs;               // filled on the host
+    unsigned long long next_tile;      // tile ticket
+    unsigned long long stage_top;      // staging slots handed out
     int status;                        // kStatus*
 };
 
-struct LevelParams {
-    const RayPrep* rays;
-    const Node* node;                  // voxels of depth dp
-    const int2* in;                    // pairs entering depth dp (NULL at dp 0)
-    int2* out;                         // children (dp < D)
-    long long out_cap;
-    int32_t* voxel_id;                 // dp == D outputs
-    float2* t_range;
-    int32_t* out_ray;
-    long long hit_cap;
+struct TileInfo {
+    long long stage;                   // first staging slot of the tile's entries
+    long long count;                   // entries of the tile
+};
+
+struct NodeTab {
+    const Node* node[kMaxDepth + 1];
+};
+
+struct TileParams {
+    NodeTab nt;
+    const float* o;
+    const float* d;
+    long long R, ntiles, stage_cap;
+    int D;
+    int32_t* ray_cnt;                  // [R] entries per ray (k_place turns them into offsets)
+    int32_t* stage_vid;                // [stage_cap] staged entries
+    float2* stage_tr;
+    TileInfo* tiles;                   // [ntiles]
     Counters* ctr;
-    int dp, D;
+};
+
+struct TileSmem {
+    RayPrep ray[kTR];
+    int32_t vox[2][kFCap];             // frontier: voxel ids at the current depth
+    uint8_t rl[2][kFCap];              // ... and the tile-local ray of each pair
+    uint16_t rec[kFCap];               // decisions: hit children by rank | octant << 8
+    int ray_cnt[kTR];                  // entries per ray at the target depth
+    long long lvl[kMaxDepth + 2];      // level sizes of the current pass
+    int sub_len[kTR];                  // fallback: lengths of the sub-ranges run
+    int warp_sums[kThreads / 32 + 1];
+    long long tile;
+    long long stage;
 };
 
 __device__ __forceinline__ int block_exclusive_sum(int v, int* warp_sums, int& total) {
@@ -70,276 +106,339 @@ __device__ __forceinline__ int block_exclusive_sum(int v, int* warp_sums, int& t
     }
     __syncthreads();
     total = warp_sums[kThreads / 32];
-    return warp_sums[warp] + incl - v;
+    const int r = warp_sums[warp] + incl - v;
+    __syncthreads();                   // warp_sums may be reused right away
+    return r;
 }
 
-__global__ void __launch_bounds__(kThreads) k_prep_rays(const float* __restrict__ o,
-                                                        const float* __restrict__ d, long long R,
-                                                        RayPrep* __restrict__ rays, Counters* ctr) {
-    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < R;
-         r += (long long)gridDim.x * blockDim.x) {
-        RayPrep p;
-        p.ox = o[3 * r];
-        p.oy = o[3 * r + 1];
-        p.oz = o[3 * r + 2];
-        const float dd[3] = {d[3 * r], d[3 * r + 1], d[3 * r + 2]};
-        const float oo[3] = {p.ox, p.oy, p.oz};
-        int ok = 1, par = 0;
-        float inv[3];
+__device__ __forceinline__ RayPrep prep_ray(const float* o, const float* d, long long r) {
+    RayPrep p;
+    p.ox = o[3 * r];
+    p.oy = o[3 * r + 1];
+    p.oz = o[3 * r + 2];
+    const float dd[3] = {d[3 * r], d[3 * r + 1], d[3 * r + 2]};
+    const float oo[3] = {p.ox, p.oy, p.oz};
+    int ok = 1, par = 0;
+    float inv[3];
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            if (!isfinite(oo[a]) || !isfinite(dd[a])) ok = 0;
-            const bool pa = fabsf(dd[a]) < 1.17549435e-38f;
-            par |= pa ? (1 << a) : 0;
-            inv[a] = pa ? 0.0f : __fdiv_rn(1.0f, dd[a]);
-        }
-        if (par == 7) ok = 0;
-        p.ix = inv[0];
-        p.iy = inv[1];
-        p.iz = inv[2];
-        p.par = par;
-        p.valid = ok;
-        rays[r] = p;
+    for (int a = 0; a < 3; ++a) {
+        if (!isfinite(oo[a]) || !isfinite(dd[a])) ok = 0;
+        const bool pa = fabsf(dd[a]) < 1.17549435e-38f;
+        par |= pa ? (1 << a) : 0;
+        inv[a] = pa ? 0.0f : __fdiv_rn(1.0f, dd[a]);
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) ctr->count[0] = R;
+    if (par == 7) ok = 0;
+    p.ix = inv[0];
+    p.iy = inv[1];
+    p.iz = inv[2];
+    p.par = par;
+    p.valid = ok;
+    return p;
 }
 
-// One level of the traversal, with Decide of the next level fused into
-// Subdivide.  Input: the pairs (ray, voxel) of depth dp that Decide kept (at
-// dp = 0 the implicit pairs (ray, root), decided here first).  For each input
-// pair a thread tests the voxel's occupied children (their bounds follow
-// from the parent's coordinates, no load needed) and records which ones the
-// ray hits (Decide of depth dp + 1).  The exclusive sum of the hit counts
-// gives every pair its output position, and the hit children are written in
-// front-to-back rank order (Subdivide); when depth dp + 1 is the target
-// depth the written list is the final one (Compactify): voxel ids, their
-// (t_enter, t_exit) and the ray of each entry.  Output order and contents
-// equal those of the unfused Decide / ExclusiveSum / Subdivide / Compactify
-// sequence.
-//
-// Scan structure: the launch is cooperative (every CTA resident) and each
-// CTA owns one contiguous chunk of the input list.
-//   pass 1  decide the chunk, store a 16-bit record per pair (hit children
-//           by rank | octant << 8) and the chunk's hit count;
-//   barrier one bounded grid-wide barrier; each CTA then sums the counts of
-//           the chunks before it (the ExclusiveSum at chunk granularity);
-//   pass 2  re-read the chunk (now L2-resident), scan inside each tile and
-//           write the children at their final positions through shared
-//           memory, coalesced.
-// No CTA ever waits on another except at the single barrier.
-constexpr int kTileX = kThreads * 2;                 // parents per pass-2 tile (2 per thread)
-constexpr int kPass1 = 4;                            // parents per thread per pass-1 step
-// staging: up to 8 children per parent, 8 B (pair) or 16 B (final entry) each
-template <bool FINAL>
-constexpr int stage_bytes() { return kTileX * 8 * (FINAL ? 16 : 8); }
-
-struct LevelScratch {
-    uint16_t* rec;          // [input pairs] hit-by-rank | octant << 8
-    long long* chunk_cnt;   // [grid]
-    unsigned* arrive;       // grid barrier counter (zeroed per level)
-};
-
-__device__ __forceinline__ bool grid_barrier(unsigned* arrive, unsigned nblocks, int* status) {
-    __syncthreads();
-    bool ok = true;
-    if (threadIdx.x == 0) {
-        __threadfence();
-        atomicAdd(arrive, 1u);
-        long spins = 0;
-        for (;;) {
-            unsigned v;
-            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(arrive) : "memory");
-            if (v >= nblocks) break;
-            if (++spins > kSpinLimit) {
-                atomicExch(status, kStatusTimeout);
-                ok = false;
-                break;
-            }
-            if (spins > 32) __nanosleep(64);
-        }
-    }
-    __syncthreads();
-    return ok;
-}
-
-template <bool FINAL>
-__global__ void __launch_bounds__(kThreads) k_level(const LevelParams p, const LevelScratch x) {
-    constexpr int kIt = kTileX / kThreads;
-    extern __shared__ __align__(16) unsigned char stage[];
-    int2* stage_p = reinterpret_cast<int2*>(stage);
-    int32_t* stage_i = reinterpret_cast<int32_t*>(stage);
-    float2* stage_f = reinterpret_cast<float2*>(stage + kTileX * 8 * sizeof(int32_t));
-    int32_t* stage_r = reinterpret_cast<int32_t*>(stage + kTileX * 8 * (sizeof(int32_t) + sizeof(float2)));
-    __shared__ int warp_sums[kThreads / 32 + 1];
-    __shared__ long long s_prefix;
-    const bool skip = p.ctr->status != kStatusOk;     // uniform: earlier level failed
-    const long long n = skip ? 0 : p.ctr->count[p.dp];
-    const long long ntiles = (n + kTileX - 1) / kTileX;
-    const long long per = (ntiles + gridDim.x - 1) / gridDim.x;
-    const long long t_begin = min((long long)blockIdx.x * per, ntiles);
-    const long long t_end = min(t_begin + per, ntiles);
-    const int dc = p.dp + 1;                          // depth of the children
-    constexpr bool final_level = FINAL;
-
-    // ---- pass 1: Decide the children of every pair of the chunk ----
-    long long mine = 0;
-    const long long c_lo = t_begin * kTileX, c_hi = min(t_end * kTileX, n);
-    for (long long base = c_lo + (long long)threadIdx.x * kPass1; base < c_hi; base += (long long)kThreads * kPass1) {
-#pragma unroll
-        for (int i = 0; i < kPass1; ++i) {
-            const long long idx = base + i;
-            if (idx >= c_hi) continue;
-            const int2 pr = p.dp == 0 ? make_int2((int)idx, 0) : p.in[idx];
-            const RayPrep ray = p.rays[pr.x];
-            const Node nd = p.node[pr.y];
+// Decide at depth dp for the n pairs of frontier buffer `cur`: each pair's
+// occupied children are slab-tested (all 8 from the 3 shared plane crossings
+// per axis) and recorded by front-to-back rank.  Thread t owns the pairs
+// [c0, c1) (contiguous, so the block scan keeps list order); `base` is its
+// first output position.  Returns the number of children hit.
+__device__ __forceinline__ int decide(TileSmem& S, const TileParams& p, int dp, int cur, int n, bool per_ray,
+                                      int& c0, int& c1, int& base) {
+    const int k = (n + kThreads - 1) / kThreads;
+    c0 = min((int)threadIdx.x * k, n);
+    c1 = min(c0 + k, n);
+    int cnt = 0;
+    const Node* nodes = p.nt.node[dp];
+    for (int i0 = c0; i0 < c1; i0 += 4) {
+        // the next four pairs' nodes are loaded together, then decided one
+        // after the other (one copy of the decision code)
+        Node nd0 = nodes[S.vox[cur][i0]];
+        Node nd1 = nodes[S.vox[cur][min(i0 + 1, c1 - 1)]];
+        Node nd2 = nodes[S.vox[cur][min(i0 + 2, c1 - 1)]];
+        Node nd3 = nodes[S.vox[cur][min(i0 + 3, c1 - 1)]];
+        const int iend = min(i0 + 4, c1);
+#pragma unroll 1
+        for (int i = i0; i < iend; ++i) {
+            const int rl = S.rl[cur][i];
+            const RayPrep ray = S.ray[rl];
             uint32_t o8, h = 0;
             bool live = true;
-            if (p.dp == 0) {
+            if (dp == 0) {
                 float t0, t1;   // the root is the only undecided input
-                live = ray.valid && slab_test(ray, nd.ijk, 0, t0, t1, &o8);
-            } else {
-                o8 = origin_octant(ray, nd.ijk, p.dp);
+                live = ray.valid && slab_test(ray, nd0.ijk, 0, t0, t1, &o8);
             }
-            if (live && nd.childmask) {
-                ChildSlabs cs;
-                child_slabs(ray, nd.ijk, p.dp, cs);
-                uint32_t hs = 0;   // by slot, all 8 tested without branches
-#pragma unroll
-                for (uint32_t c = 0; c < 8; ++c) {
-                    float a0, a1;
-                    hs |= child_hit(cs, c, a0, a1) ? (1u << c) : 0u;
-                }
-                h = rank_mask(hs & nd.childmask, o8);
+            if (live && nd0.childmask) {
+                uint32_t oc;
+                const uint32_t hs = child_hits8<false>(ray, nd0.ijk, dp, oc);
+                o8 = oc;
+                h = rank_mask(hs & nd0.childmask, o8);
+            } else if (dp != 0) {
+                o8 = origin_octant(ray, nd0.ijk, dp);
             }
-            x.rec[idx] = (uint16_t)(h | (live ? (o8 << 8) : 0u));
-            mine += __popc(h);
+            S.rec[i] = (uint16_t)(h | (live ? (o8 << 8) : 0u));
+            cnt += __popc(h);
+            if (per_ray && h) atomicAdd(&S.ray_cnt[rl], __popc(h));
+            nd0 = nd1;
+            nd1 = nd2;
+            nd2 = nd3;
         }
     }
-    // chunk total -> scan of chunk totals (one bounded grid barrier)
-    {
-        int total;
-        block_exclusive_sum((int)mine, warp_sums, total);
-        if (threadIdx.x == 0) {
-            asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(x.chunk_cnt + blockIdx.x),
-                         "l"((unsigned long long)total)
-                         : "memory");
-        }
-    }
-    if (!grid_barrier(x.arrive, gridDim.x, &p.ctr->status)) return;
-    if (threadIdx.x < 32) {
-        long long acc = 0;
-        for (unsigned b = threadIdx.x; b < blockIdx.x; b += 32) {
-            unsigned long long v;
-            asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(x.chunk_cnt + b) : "memory");
-            acc += (long long)v;
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (threadIdx.x == 0) {
-            s_prefix = acc;
-            if (blockIdx.x == gridDim.x - 1 && !skip) {
-                unsigned long long mine_tot;
-                asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(mine_tot) : "l"(x.chunk_cnt + blockIdx.x) : "memory");
-                const long long total = acc + (long long)mine_tot;
-                p.ctr->count[dc] = total;
-                if (total > p.ctr->max_pairs) p.ctr->max_pairs = total;
-                if (total > (final_level ? p.hit_cap : p.out_cap))
-                    atomicCAS(&p.ctr->status, kStatusOk, kStatusOverflow);
-            }
-        }
-    }
-    __syncthreads();
-    long long off = s_prefix;
+    int total;
+    base = block_exclusive_sum(cnt, S.warp_sums, total);
+    return total;
+}
 
-    // ---- pass 2: positions inside each tile, then Subdivide / Compactify ----
-    for (long long tile = t_begin; tile < t_end; ++tile) {
-        const long long base = tile * kTileX + (long long)threadIdx.x * kIt;
-        uint32_t rec[kIt];
-        int cnt = 0;
-#pragma unroll
-        for (int i = 0; i < kIt; ++i) {
-            rec[i] = base + i < n ? x.rec[base + i] : 0u;
-            cnt += __popc(rec[i] & 0xffu);
+// Subdivide: the hit children of the owned pairs, front to back, into `nxt`.
+__device__ __forceinline__ void subdivide(TileSmem& S, const TileParams& p, int dp, int cur, int c0, int c1,
+                                          int base) {
+    const Node* nodes = p.nt.node[dp];
+    int pos = base;
+    for (int i = c0; i < c1; ++i) {
+        const uint32_t h0 = S.rec[i] & 0xffu;
+        if (!h0) continue;
+        const Node nd = nodes[S.vox[cur][i]];
+        const uint32_t o8 = S.rec[i] >> 8;
+        const uint8_t rl = S.rl[cur][i];
+        for (uint32_t h = h0; h; h &= h - 1u) {
+            const uint32_t c = (uint32_t)(__ffs(h) - 1) ^ o8;
+            S.vox[cur ^ 1][pos] = nd.childbase + __popc(nd.childmask & ((1u << c) - 1u));
+            S.rl[cur ^ 1][pos] = rl;
+            ++pos;
         }
-        int tile_total;
-        int loc = block_exclusive_sum(cnt, warp_sums, tile_total);
-#pragma unroll
-        for (int i = 0; i < kIt; ++i) {
-            const uint32_t h0 = rec[i] & 0xffu;
-            if (!h0) continue;
-            const long long idx = base + i;
-            const int2 pr = p.dp == 0 ? make_int2((int)idx, 0) : p.in[idx];
-            const Node nd = p.node[pr.y];
-            const uint32_t o8 = rec[i] >> 8;
-            ChildSlabs cs;
-            if (final_level) child_slabs(p.rays[pr.x], nd.ijk, p.dp, cs);
-            for (uint32_t h = h0; h; h &= h - 1u) {
-                const uint32_t c = (uint32_t)(__ffs(h) - 1) ^ o8;
-                const int32_t child = nd.childbase + __popc(nd.childmask & ((1u << c) - 1u));
-                if (final_level) {
-                    float a0 = 0.f, a1 = 0.f;
-                    child_hit(cs, c, a0, a1);
-                    stage_i[loc] = child;
-                    stage_f[loc] = make_float2(a0, a1);
-                    stage_r[loc] = pr.x;
-                } else {
-                    stage_p[loc] = make_int2(pr.x, child);
-                }
-                ++loc;
-            }
-        }
-        __syncthreads();
-        if (final_level) {
-            const long long lim = min((long long)tile_total, p.hit_cap - off);
-            for (int i = threadIdx.x; i < lim; i += kThreads) {
-                p.voxel_id[off + i] = stage_i[i];
-                p.t_range[off + i] = stage_f[i];
-                p.out_ray[off + i] = stage_r[i];
-            }
-        } else {
-            const long long lim = min((long long)tile_total, p.out_cap - off);
-            for (int i = threadIdx.x; i < lim; i += kThreads) p.out[off + i] = stage_p[i];
-        }
-        off += tile_total;
-        __syncthreads();   // staging and warp_sums reuse
     }
 }
 
-// ray_offsets[r] = first list position whose ray is >= r (binary search).
-__global__ void __launch_bounds__(kThreads) k_ray_offsets(const int32_t* __restrict__ out_ray,
-                                                          const Counters* __restrict__ ctr, int D,
-                                                          long long R, long long cap,
-                                                          int32_t* __restrict__ offs) {
-    const long long H = min(ctr->count[D], cap);   // never past what was written
-    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r <= R;
-         r += (long long)gridDim.x * blockDim.x) {
-        long long lo = 0, hi = H;
-        while (lo < hi) {
-            const long long mid = lo + ((hi - lo) >> 1);
-            if (out_ray[mid] < r) lo = mid + 1; else hi = mid;
+// Compactify at the target depth: the hit children of the owned pairs with
+// their (t_enter, t_exit), written to their final list positions.
+__device__ __forceinline__ void write_final(TileSmem& S, const TileParams& p, int dp, int cur, int c0, int c1,
+                                            long long pos) {
+    const Node* nodes = p.nt.node[dp];
+    for (int i = c0; i < c1; ++i) {
+        const uint32_t h0 = S.rec[i] & 0xffu;
+        if (!h0) continue;
+        const Node nd = nodes[S.vox[cur][i]];
+        const uint32_t o8 = S.rec[i] >> 8;
+        float tn[8], tf[8];
+        uint32_t oc;
+        child_hits8<true>(S.ray[S.rl[cur][i]], nd.ijk, dp, oc, tn, tf);
+        for (uint32_t h = h0; h; h &= h - 1u) {
+            const uint32_t c = (uint32_t)(__ffs(h) - 1) ^ o8;
+            if (pos < p.stage_cap) {
+                p.stage_vid[pos] = nd.childbase + __popc(nd.childmask & ((1u << c) - 1u));
+                p.stage_tr[pos] = make_float2(tn[c], tf[c]);
+            }
+            ++pos;
         }
-        offs[r] = (int32_t)lo;
+    }
+}
+
+// Levels 0..D-1 for the tile-local rays [r0, r0 + nr).  Returns false if a
+// frontier would exceed kFCap (block-uniform).  On success the target
+// depth's decisions stay in S.rec with the thread's chunk [c0, c1) and
+// output base, and `total` is the number of entries; S.lvl holds the level
+// sizes of this pass.
+__device__ bool run_levels(TileSmem& S, const TileParams& p, int r0, int nr, bool per_ray, int& cur, int& c0,
+                           int& c1, int& base, int& total) {
+    for (int i = threadIdx.x; i < nr; i += kThreads) {
+        S.vox[0][i] = 0;
+        S.rl[0][i] = (uint8_t)(r0 + i);
+    }
+    if (threadIdx.x <= kMaxDepth + 1) S.lvl[threadIdx.x] = 0;
+    __syncthreads();
+    cur = 0;
+    int n = nr;
+    for (int dp = 0; dp < p.D; ++dp) {
+        const bool fin = dp + 1 == p.D;
+        total = decide(S, p, dp, cur, n, fin && per_ray, c0, c1, base);
+        if (threadIdx.x == 0) S.lvl[dp + 1] = total;
+        if (fin) break;
+        if (total > kFCap) return false;
+        subdivide(S, p, dp, cur, c0, c1, base);
+        __syncthreads();
+        cur ^= 1;
+        n = total;
+    }
+    __syncthreads();
+    return true;
+}
+
+__device__ __forceinline__ void commit_levels(TileSmem& S, const TileParams& p) {
+    if (threadIdx.x >= 1 && threadIdx.x <= p.D && S.lvl[threadIdx.x])
+        atomicAdd((unsigned long long*)&p.ctr->count[threadIdx.x], (unsigned long long)S.lvl[threadIdx.x]);
+}
+
+__global__ void __launch_bounds__(kThreads, 4) k_traverse(const TileParams p) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    TileSmem& S = *reinterpret_cast<TileSmem*>(smem_raw);
+    if (blockIdx.x == 0 && threadIdx.x == 0) p.ctr->count[0] = p.R;
+    for (;;) {
+        if (threadIdx.x == 0) S.tile = (long long)atomicAdd(&p.ctr->next_tile, 1ull);
+        __syncthreads();
+        const long long t = S.tile;
+        if (t >= p.ntiles) break;
+        const long long ra = t * kTR;
+        const int nr = (int)min((long long)kTR, p.R - ra);
+        for (int i = threadIdx.x; i < kTR; i += kThreads) {
+            if (i < nr) S.ray[i] = prep_ray(p.o, p.d, ra + i);
+            S.ray_cnt[i] = 0;
+        }
+        __syncthreads();
+        int cur, c0, c1, base, total;
+        const bool whole = run_levels(S, p, 0, nr, true, cur, c0, c1, base, total);
+        long long tile_total = 0;
+        int nsub = 0;
+        if (whole) {
+            commit_levels(S, p);
+            tile_total = total;
+        } else {
+            // halve until every sub-range fits; per-ray counts accumulate
+            int r = 0, len = nr / 2;
+            while (r < nr) {
+                const int l = min(len, nr - r);
+                int cu2, a0, a1, b2, tot2;
+                if (!run_levels(S, p, r, l, true, cu2, a0, a1, b2, tot2)) {
+                    len = max(1, l / 2);
+                    continue;
+                }
+                commit_levels(S, p);
+                if (threadIdx.x == 0) S.sub_len[nsub] = l;
+                ++nsub;
+                tile_total += tot2;
+                r += l;
+            }
+        }
+        if (threadIdx.x == 0) {
+            const long long st = (long long)atomicAdd(&p.ctr->stage_top, (unsigned long long)tile_total);
+            S.stage = st;
+            p.tiles[t] = TileInfo{st, tile_total};
+            if (st + tile_total > p.stage_cap) atomicCAS(&p.ctr->status, kStatusOk, kStatusOverflow);
+        }
+        if ((int)threadIdx.x < nr) p.ray_cnt[ra + threadIdx.x] = S.ray_cnt[threadIdx.x];
+        __syncthreads();
+        const long long st = S.stage;
+        if (whole) {
+            write_final(S, p, p.D - 1, cur, c0, c1, st + base);
+        } else {
+            long long run = st;
+            int r = 0;
+            for (int k = 0; k < nsub; ++k) {
+                const int l = S.sub_len[k];
+                int cu2, a0, a1, b2, tot2;
+                run_levels(S, p, r, l, false, cu2, a0, a1, b2, tot2);
+                write_final(S, p, p.D - 1, cu2, a0, a1, run + b2);
+                __syncthreads();
+                run += tot2;
+                r += l;
+            }
+        }
+        __syncthreads();   // shared state is reused by the next tile
+    }
+}
+
+// Exclusive sum of the tile counts, in place over TileInfo::count (one CTA);
+// the grand total is the hit count H.
+__global__ void __launch_bounds__(kScanThreads) k_tile_scan(TileInfo* __restrict__ tiles, long long ntiles,
+                                                            Counters* __restrict__ ctr, long long hit_cap, int D) {
+    __shared__ long long warp_sums[kScanThreads / 32 + 1];
+    __shared__ long long carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (long long b0 = 0; b0 < ntiles; b0 += kScanThreads) {
+        const long long i = b0 + threadIdx.x;
+        const long long v = i < ntiles ? tiles[i].count : 0;
+        long long incl = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane == 31) warp_sums[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            const long long s = warp_sums[lane];
+            long long si = s;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const long long y = __shfl_up_sync(0xffffffffu, si, o);
+                if (lane >= o) si += y;
+            }
+            warp_sums[lane] = si - s;
+            if (lane == 31) warp_sums[32] = si;
+        }
+        __syncthreads();
+        if (i < ntiles) tiles[i].count = carry + warp_sums[warp] + incl - v;   // now the exclusive prefix
+        __syncthreads();
+        if (threadIdx.x == 0) carry += warp_sums[32];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        if (carry != ctr->count[D]) atomicCAS(&ctr->status, kStatusOk, kStatusBadIndex);
+        if (carry > hit_cap) atomicCAS(&ctr->status, kStatusOk, kStatusOverflow);
+    }
+}
+
+// One CTA per tile: its rays' CSR offsets (exclusive sum of their counts
+// after the tile's prefix) and its staged entries copied to their final
+// positions (coalesced).
+__global__ void __launch_bounds__(kTR) k_place(const TileInfo* __restrict__ tiles, const TileParams p,
+                                              const int32_t* __restrict__ ray_cnt, int32_t* __restrict__ ray_offsets,
+                                              int32_t* __restrict__ voxel_id, float2* __restrict__ t_range,
+                                              long long hit_cap) {
+    __shared__ int warp_sums[kTR / 32 + 1];
+    if (p.ctr->status != kStatusOk) return;
+    for (long long t = blockIdx.x; t < p.ntiles; t += gridDim.x) {
+        const long long ra = t * kTR;
+        const int nr = (int)min((long long)kTR, p.R - ra);
+        const long long off = tiles[t].count;           // exclusive prefix (k_tile_scan)
+        const int v = (int)threadIdx.x < nr ? ray_cnt[ra + threadIdx.x] : 0;
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        int incl = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane == 31) warp_sums[warp] = incl;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int a = 0;
+            for (int w = 0; w < kTR / 32; ++w) {
+                const int x = warp_sums[w];
+                warp_sums[w] = a;
+                a += x;
+            }
+            warp_sums[kTR / 32] = a;
+        }
+        __syncthreads();
+        if ((int)threadIdx.x < nr) ray_offsets[ra + threadIdx.x] = (int32_t)(off + warp_sums[warp] + incl - v);
+        const int cnt = warp_sums[kTR / 32];
+        if (t == p.ntiles - 1 && threadIdx.x == 0) ray_offsets[p.R] = (int32_t)(off + cnt);
+        // staged entries -> final positions (within both capacities: the
+        // status checked above covers the staging list and H <= hit_cap)
+        __syncthreads();
+        const long long st = p.tiles[t].stage;
+        for (int i = threadIdx.x; i < cnt; i += kTR) {
+            voxel_id[off + i] = p.stage_vid[st + i];
+            t_range[off + i] = p.stage_tr[st + i];
+        }
+        __syncthreads();
     }
 }
 
 size_t align_up(size_t v, size_t a = 256) { return (v + a - 1) / a * a; }
 
-constexpr int kMaxGrid = 4096;   // chunk-count slots (>= resident CTAs of the level kernel)
+long long num_tiles(long long R) { return (R + kTR - 1) / kTR; }
 
-// Resident CTAs per SM of the level kernel with its staging buffer (the
-// persistent grid is sized to exactly what fits).
-template <bool FINAL>
-int level_ctas_per_sm() {
+int traverse_ctas_per_sm() {
     static int cached = 0;
     if (!cached) {
-        cudaFuncSetAttribute(k_level<FINAL>, cudaFuncAttributeMaxDynamicSharedMemorySize, stage_bytes<FINAL>());
+        cudaFuncSetAttribute(k_traverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TileSmem));
         int n = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_level<FINAL>, kThreads, stage_bytes<FINAL>());
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_traverse, kThreads, sizeof(TileSmem));
         cached = n > 0 ? n : 1;
     }
     return cached;
 }
-
 
 }  // namespace
 }  // namespace nglod
@@ -348,11 +447,9 @@ using namespace nglod;
 
 extern "C" size_t svo_trace_rays_workspace(int64_t R, int64_t pair_capacity) {
     if (R < 0 || pair_capacity < 0) return 0;
-    const size_t n_in = (size_t)std::max<int64_t>(R, pair_capacity);
-    return align_up(sizeof(Counters)) + align_up(sizeof(RayPrep) * (size_t)R) +
-           2 * align_up(sizeof(int2) * (size_t)pair_capacity) +
-           align_up(sizeof(unsigned long long) * kMaxGrid) + align_up(sizeof(unsigned) * (kMaxDepth + 2)) +
-           align_up(sizeof(uint16_t) * n_in);
+    return align_up(sizeof(Counters)) + align_up(sizeof(TileInfo) * (size_t)(num_tiles(R) + 1)) +
+           align_up(sizeof(int32_t) * (size_t)(R + 1)) + align_up(sizeof(int32_t) * (size_t)pair_capacity) +
+           align_up(sizeof(float2) * (size_t)pair_capacity);
 }
 
 namespace nglod {
@@ -385,65 +482,35 @@ int enqueue_traversal(const nglod_svo* svo, const float* o, const float* d, int6
     if ((hit_capacity > 0 && (!voxel_id || !t_range)))
         return fail(NGLOD_ERR_INVALID_ARG, w + ": NULL voxel_id / t_range");
 
-    char* wp = (char*)work;
-    wp += align_up(sizeof(Counters));
-    RayPrep* rays = (RayPrep*)wp;
-    wp += align_up(sizeof(RayPrep) * (size_t)R);
-    int2* buf[2];
-    buf[0] = (int2*)wp;
-    wp += align_up(sizeof(int2) * (size_t)pair_capacity);
-    buf[1] = (int2*)wp;
-    wp += align_up(sizeof(int2) * (size_t)pair_capacity);
-    long long* chunk_cnt = (long long*)wp;
-    wp += align_up(sizeof(unsigned long long) * kMaxGrid);
-    unsigned* arrive = (unsigned*)wp;
-    wp += align_up(sizeof(unsigned) * (kMaxDepth + 2));
-    uint16_t* rec = (uint16_t*)wp;
-
-    const int sms = svo->num_sms;
+    const long long ntiles = num_tiles(R);
+    char* wp = (char*)work + align_up(sizeof(Counters));
+    TileInfo* tiles = (TileInfo*)wp;
+    wp += align_up(sizeof(TileInfo) * (size_t)(ntiles + 1));
+    int32_t* ray_cnt = (int32_t*)wp;
+    wp += align_up(sizeof(int32_t) * (size_t)(R + 1));
+    int32_t* stage_vid = (int32_t*)wp;
+    wp += align_up(sizeof(int32_t) * (size_t)pair_capacity);
+    float2* stage_tr = (float2*)wp;
     NGLOD_CUDA(cudaMemsetAsync(ctr, 0, sizeof(Counters), st));
-    NGLOD_CUDA(cudaMemsetAsync(arrive, 0, sizeof(unsigned) * (kMaxDepth + 2), st));
-    k_prep_rays<<<std::min<long long>((R + kThreads - 1) / kThreads, (long long)sms * 16), kThreads, 0, st>>>(
-        o, d, R, rays, ctr);
-    for (int dp = 0; dp < D; ++dp) {
-        LevelParams lp;
-        lp.rays = rays;
-        lp.node = svo->node[dp];
-        lp.in = dp == 0 ? nullptr : buf[dp & 1];
-        lp.out = buf[(dp + 1) & 1];
-        lp.out_cap = pair_capacity;
-        lp.voxel_id = voxel_id;
-        lp.t_range = (float2*)t_range;
-        lp.out_ray = (int32_t*)buf[(dp + 1) & 1];   // used when dp + 1 == D
-        lp.hit_cap = std::min<long long>(hit_capacity, pair_capacity);
-        lp.ctr = ctr;
-        lp.dp = dp;
-        lp.D = D;
-        LevelScratch xs;
-        xs.rec = rec;
-        xs.chunk_cnt = chunk_cnt;
-        xs.arrive = arrive + dp;
-        const bool fin = dp + 1 == D;
-        cudaLaunchConfig_t cfg = {};
-        cudaLaunchAttribute attr[1];
-        attr[0].id = cudaLaunchAttributeCooperative;   // every CTA resident (one grid barrier)
-        attr[0].val.cooperative = 1;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
-        cfg.blockDim = dim3(kThreads);
-        cfg.stream = st;
-        if (fin) {
-            cfg.gridDim = dim3(std::min(sms * level_ctas_per_sm<true>(), kMaxGrid));
-            cfg.dynamicSmemBytes = stage_bytes<true>();
-            NGLOD_CUDA(cudaLaunchKernelEx(&cfg, k_level<true>, lp, xs));
-        } else {
-            cfg.gridDim = dim3(std::min(sms * level_ctas_per_sm<false>(), kMaxGrid));
-            cfg.dynamicSmemBytes = stage_bytes<false>();
-            NGLOD_CUDA(cudaLaunchKernelEx(&cfg, k_level<false>, lp, xs));
-        }
-    }
-    k_ray_offsets<<<std::min<long long>((R + kThreads) / kThreads, (long long)sms * 16), kThreads, 0, st>>>(
-        (const int32_t*)buf[D & 1], ctr, D, R, std::min<long long>(hit_capacity, pair_capacity), ray_offsets);
+    TileParams p;
+    for (int dp = 0; dp <= kMaxDepth; ++dp) p.nt.node[dp] = dp < svo->num_depths ? svo->node[dp] : nullptr;
+    p.o = o;
+    p.d = d;
+    p.R = R;
+    p.ntiles = ntiles;
+    p.stage_cap = pair_capacity;
+    p.D = D;
+    p.ray_cnt = ray_cnt;
+    p.stage_vid = stage_vid;
+    p.stage_tr = stage_tr;
+    p.tiles = tiles;
+    p.ctr = ctr;
+    const int sms = svo->num_sms;
+    const long long grid = std::min<long long>(ntiles, (long long)sms * traverse_ctas_per_sm());
+    k_traverse<<<(unsigned)grid, kThreads, sizeof(TileSmem), st>>>(p);
+    k_tile_scan<<<1, kScanThreads, 0, st>>>(tiles, ntiles, ctr, hit_capacity, D);
+    k_place<<<(unsigned)std::min<long long>(ntiles, (long long)sms * 16), kTR, 0, st>>>(
+        tiles, p, ray_cnt, ray_offsets, voxel_id, (float2*)t_range, hit_capacity);
     NGLOD_CUDA(cudaGetLastError());
     return NGLOD_OK;
 }
@@ -454,19 +521,17 @@ int read_traversal(const void* work, int D, int64_t* h_stats, cudaStream_t st, c
     NGLOD_CUDA(cudaMemcpyAsync(&h, work, sizeof(Counters), cudaMemcpyDeviceToHost, st));
     NGLOD_CUDA(cudaStreamSynchronize(st));
     const long long H = h.count[D];
+    long long mx = 0;
+    for (int dp = 1; dp <= D; ++dp) mx = std::max(mx, h.count[dp]);
     if (h_stats) {
         h_stats[0] = H;
-        h_stats[1] = h.max_pairs;
+        h_stats[1] = mx;
     }
-    if (h.status == kStatusTimeout)
-        return fail(NGLOD_ERR_TIMEOUT, std::string(who) + ": grid barrier wait expired");
-    if (h.status == kStatusOverflow) {
-        long long need = 0;
-        for (int dp = 1; dp < D; ++dp) need = std::max(need, h.count[dp]);
-        if (h_stats) h_stats[1] = std::max<long long>(need, h.max_pairs);
-        return fail(NGLOD_ERR_CAPACITY, std::string(who) + ": list larger than capacity (pairs " +
-                                            std::to_string(need) + ", hits " + std::to_string(H) + ")");
-    }
+    if (h.status == kStatusOverflow)
+        return fail(NGLOD_ERR_CAPACITY, std::string(who) + ": " + std::to_string(H) +
+                                            " hits exceed hit_capacity or pair_capacity");
+    if (h.status != kStatusOk)
+        return fail(NGLOD_ERR_CUDA, std::string(who) + ": inconsistent traversal counters");
     return NGLOD_OK;
 }
 
@@ -548,17 +613,18 @@ extern "C" int svo_trace_rays_noalloc(const nglod_svo* svo, const float* o, cons
                                       float* t_range, int64_t hit_capacity, int64_t* h_stats, void* stream) {
     using namespace nglod;
     if (R < 0) return fail(NGLOD_ERR_INVALID_ARG, "svo_trace_rays_noalloc: R < 0");
-    // the largest intermediate-list capacity whose workspace fits the array
-    int64_t lo = 0, hi = (int64_t)(kNoAllocScratchBytes / sizeof(int2));
+    // the fixed part of the workspace (counters, tile records, per-ray
+    // counts) must fit the array; the rest is the staging-list capacity
+    if (svo_trace_rays_workspace(R, 0) > kNoAllocScratchBytes)
+        return fail(NGLOD_ERR_CAPACITY, "svo_trace_rays_noalloc: " + std::to_string(R) +
+                                            " rays need more workspace than the fixed 32 MiB scratch (use "
+                                            "svo_trace_rays with a caller-allocated workspace)");
+    int64_t lo = 0, hi = (int64_t)(kNoAllocScratchBytes / (sizeof(int32_t) + sizeof(float2)));
     while (lo < hi) {
         const int64_t mid = lo + (hi - lo + 1) / 2;
         if (svo_trace_rays_workspace(R, mid) <= kNoAllocScratchBytes) lo = mid; else hi = mid - 1;
     }
     const int64_t pair_capacity = lo;
-    if (R > 0 && pair_capacity < R)
-        return fail(NGLOD_ERR_CAPACITY, "svo_trace_rays_noalloc: " + std::to_string(R) +
-                                            " rays do not fit the fixed 32 MiB scratch (use svo_trace_rays with a "
-                                            "caller-allocated workspace)");
     int dev = 0;
     NGLOD_CUDA(cudaGetDevice(&dev));
     if (dev < 0 || dev >= kNoAllocMaxDevices)
@@ -580,7 +646,7 @@ extern "C" int svo_trace_rays_noalloc(const nglod_svo* svo, const float* o, cons
     const int rc = svo_trace_rays(svo, o, d, R, target_lod, scratch, kNoAllocScratchBytes, pair_capacity,
                                   ray_offsets, voxel_id, t_range, hit_capacity, h_stats, stream);
     if (rc == NGLOD_ERR_CAPACITY)
-        set_error(std::string(nglod_last_error()) + " [svo_trace_rays_noalloc: the fixed 32 MiB scratch holds " +
-                  std::to_string(pair_capacity) + " pairs per level for these rays]");
+        set_error(std::string(nglod_last_error()) + " [svo_trace_rays_noalloc: the fixed 32 MiB scratch stages " +
+                  std::to_string(pair_capacity) + " entries for these rays]");
     return rc;
 }

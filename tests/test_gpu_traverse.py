@@ -104,3 +104,24 @@ def test_full_size_1080p_lod5_sampled(ng, oracle_mod):
     assert np.all(np.diff(g[0]) >= 0) and g[0][-1] == len(g[1])
     assert g[1].min() >= 0 and g[1].max() < oc.counts()[7]
     assert np.all(g[2][:, 0] <= g[2][:, 1])
+
+
+def test_dense_grid_frontier_overflow_path(ng, oracle_mod):
+    # every voxel of a dense depth-6 grid is occupied: a ray crossing the cube
+    # meets ~100-190 voxels per level, so 128 rays overflow the on-chip
+    # frontier and the traversal re-runs the tile over halves of its rays;
+    # the lists must still equal the brute-force ones bit for bit
+    dense = S.full_octree(6)
+    svo = ng.svo_build(dense.keys)
+    ora = oracle_mod.OracleSVO(dense.keys)
+    rng = np.random.default_rng(9)
+    n = 300
+    o = np.tile(np.array([[-2.5, 0.05, -0.1]], np.float32), (n, 1)) + rng.uniform(-0.3, 0.3, (n, 3)).astype(np.float32)
+    tgt = rng.uniform(-0.6, 0.6, (n, 3))
+    d = (tgt - o).astype(np.float64)
+    d = (d / np.linalg.norm(d, axis=1, keepdims=True)).astype(np.float32)
+    g = gpu_lists(ng, svo, o, d, 4)
+    assert np.diff(g[0]).mean() > 60
+    assert_same_lists(g, ora.trace_rays(o, d, 4))
+    sizes = g[3].level_sizes()
+    assert sizes[-1] == len(g[1]) and sizes[0] == n

@@ -59,12 +59,16 @@ def test_noalloc_matches_caller_workspace_twice(ng):
 def test_noalloc_rejects_rays_beyond_its_scratch(ng):
     sc, oc = S.plain_sphere(3)
     svo = ng.svo_build(oc.keys)
-    R = 2_000_000                   # 64 MB of ray records alone: more than 32 MiB
-    o = torch.zeros((R, 3), device="cuda")
-    d = torch.ones((R, 3), device="cuda")
-    offs = torch.empty(R + 1, dtype=torch.int32, device="cuda")
-    rc = ng.lib().svo_trace_rays_noalloc(svo.h, o.data_ptr(), d.data_ptr(), R, 3, offs.data_ptr(), None, None,
-                                         0, None, ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    # the fixed part of the workspace (a count per ray, a record per tile of
+    # 128 rays) for 2^31 - 2 rays is ~8.9 GB, far more than the 32 MiB array:
+    # rejected on the host before anything is read or launched (the NULL ray
+    # and offset pointers are never reached; with no size check they would be
+    # rejected as invalid arguments, also before any launch)
+    R = (1 << 31) - 2
+    assert ng.lib().svo_trace_rays_workspace(R, 0) > 32 << 20
+    assert ng.lib().svo_trace_rays_workspace(2_000_000, 0) < 32 << 20
+    rc = ng.lib().svo_trace_rays_noalloc(svo.h, None, None, R, 3, None, None, None, 0, None,
+                                         ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
     assert rc == ng.ERR_CAPACITY
     assert b"32 MiB" in ng.lib().nglod_last_error()
     svo.free()
