@@ -234,30 +234,51 @@ __device__ __forceinline__ uint32_t child_hits8(const RayPrep& r, uint32_t ijk, 
         const float t_lo = __fmul_rn(__fsub_rn(lo, o[a]), inv[a]);
         const float t_mid = __fmul_rn(__fsub_rn(mid, o[a]), inv[a]);
         const float t_hi = __fmul_rn(__fsub_rn(hi, o[a]), inv[a]);
-        nr[a][0] = t_lo < t_mid ? t_lo : t_mid;
-        fr[a][0] = t_lo < t_mid ? t_mid : t_lo;
-        nr[a][1] = t_mid < t_hi ? t_mid : t_hi;
-        fr[a][1] = t_mid < t_hi ? t_hi : t_mid;
+        if (WANT_T) {
+            nr[a][0] = t_lo < t_mid ? t_lo : t_mid;
+            fr[a][0] = t_lo < t_mid ? t_mid : t_lo;
+            nr[a][1] = t_mid < t_hi ? t_mid : t_hi;
+            fr[a][1] = t_mid < t_hi ? t_hi : t_mid;
+        } else {
+            nr[a][0] = fminf(t_lo, t_mid);
+            fr[a][0] = fmaxf(t_lo, t_mid);
+            nr[a][1] = fminf(t_mid, t_hi);
+            fr[a][1] = fmaxf(t_mid, t_hi);
+        }
     }
     uint32_t hit = 0;
+    if (WANT_T) {
 #pragma unroll
-    for (int xy = 0; xy < 4; ++xy) {
-        const int x = xy & 1, y = xy >> 1;
-        float n2 = nr[0][x], f2 = fr[0][x];
-        if (nr[1][y] > n2) n2 = nr[1][y];
-        if (fr[1][y] < f2) f2 = fr[1][y];
+        for (int xy = 0; xy < 4; ++xy) {
+            const int x = xy & 1, y = xy >> 1;
+            float n2 = nr[0][x], f2 = fr[0][x];
+            if (nr[1][y] > n2) n2 = nr[1][y];
+            if (fr[1][y] < f2) f2 = fr[1][y];
 #pragma unroll
-        for (int z = 0; z < 2; ++z) {
-            float tn = n2, tf = f2;
-            if (nr[2][z] > tn) tn = nr[2][z];
-            if (fr[2][z] < tf) tf = fr[2][z];
-            const float te = tn > 0.0f ? tn : 0.0f;
-            const int slot = xy | (z << 2);
-            if (te <= tf) hit |= 1u << slot;
-            if (WANT_T) {
+            for (int z = 0; z < 2; ++z) {
+                float tn = n2, tf = f2;
+                if (nr[2][z] > tn) tn = nr[2][z];
+                if (fr[2][z] < tf) tf = fr[2][z];
+                const float te = tn > 0.0f ? tn : 0.0f;
+                const int slot = xy | (z << 2);
+                if (te <= tf) hit |= 1u << slot;
                 tin[slot] = te;
                 tout[slot] = tf;
             }
+        }
+    } else {
+        // only the decision t_enter <= t_exit is needed: fmaxf / fminf give
+        // the same values up to the sign of a zero (no operand is NaN: every
+        // t is a finite or infinite product of finite factors), which no
+        // comparison can see; the 0 of t_enter = max(t_near, 0) joins the z
+        // terms
+        const float nz0 = fmaxf(nr[2][0], 0.0f), nz1 = fmaxf(nr[2][1], 0.0f);
+#pragma unroll
+        for (int xy = 0; xy < 4; ++xy) {
+            const int x = xy & 1, y = xy >> 1;
+            const float n2 = fmaxf(nr[0][x], nr[1][y]), f2 = fminf(fr[0][x], fr[1][y]);
+            if (fmaxf(n2, nz0) <= fminf(f2, fr[2][0])) hit |= 1u << xy;
+            if (fmaxf(n2, nz1) <= fminf(f2, fr[2][1])) hit |= 1u << (xy | 4);
         }
     }
     return hit & allow;

@@ -81,6 +81,7 @@ struct TileSmem {
     int warp_sums[kThreads / 32 + 1];
     long long tile;
     long long stage;
+    uint8_t rank_lut[8 * 256];         // rank_mask(m, oct) at [oct * 256 + m]
 };
 
 __device__ __forceinline__ int block_exclusive_sum(int v, int* warp_sums, int& total) {
@@ -167,10 +168,8 @@ __device__ __forceinline__ int decide(TileSmem& S, const TileParams& p, int dp, 
                 live = ray.valid && slab_test(ray, nd0.ijk, 0, t0, t1, &o8);
             }
             if (live && nd0.childmask) {
-                uint32_t oc;
-                const uint32_t hs = child_hits8<false>(ray, nd0.ijk, dp, oc);
-                o8 = oc;
-                h = rank_mask(hs & nd0.childmask, o8);
+                const uint32_t hs = child_hits8<false>(ray, nd0.ijk, dp, o8);
+                h = S.rank_lut[(o8 << 8) | (hs & nd0.childmask)];
             } else if (dp != 0) {
                 o8 = origin_octant(ray, nd0.ijk, dp);
             }
@@ -217,14 +216,17 @@ __device__ __forceinline__ void write_final(TileSmem& S, const TileParams& p, in
         if (!h0) continue;
         const Node nd = nodes[S.vox[cur][i]];
         const uint32_t o8 = S.rec[i] >> 8;
-        float tn[8], tf[8];
-        uint32_t oc;
-        child_hits8<true>(S.ray[S.rl[cur][i]], nd.ijk, dp, oc, tn, tf);
+        // the exact (t_enter, t_exit) of the hit children only (about one
+        // per pair at the target depth)
+        ChildSlabs cs;
+        child_slabs(S.ray[S.rl[cur][i]], nd.ijk, dp, cs);
         for (uint32_t h = h0; h; h &= h - 1u) {
             const uint32_t c = (uint32_t)(__ffs(h) - 1) ^ o8;
+            float a0 = 0.f, a1 = 0.f;
+            child_hit(cs, c, a0, a1);
             if (pos < p.stage_cap) {
                 p.stage_vid[pos] = nd.childbase + __popc(nd.childmask & ((1u << c) - 1u));
-                p.stage_tr[pos] = make_float2(tn[c], tf[c]);
+                p.stage_tr[pos] = make_float2(a0, a1);
             }
             ++pos;
         }
@@ -270,6 +272,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_traverse(const TileParams p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TileSmem& S = *reinterpret_cast<TileSmem*>(smem_raw);
     if (blockIdx.x == 0 && threadIdx.x == 0) p.ctr->count[0] = p.R;
+    for (int i = threadIdx.x; i < 8 * 256; i += kThreads) S.rank_lut[i] = (uint8_t)rank_mask(i & 255, i >> 8);
     for (;;) {
         if (threadIdx.x == 0) S.tile = (long long)atomicAdd(&p.ctr->next_tile, 1ull);
         __syncthreads();
@@ -379,47 +382,67 @@ __global__ void __launch_bounds__(kScanThreads) k_tile_scan(TileInfo* __restrict
 
 // One CTA per tile: its rays' CSR offsets (exclusive sum of their counts
 // after the tile's prefix) and its staged entries copied to their final
-// positions (coalesced).
-__global__ void __launch_bounds__(kTR) k_place(const TileInfo* __restrict__ tiles, const TileParams p,
-                                              const int32_t* __restrict__ ray_cnt, int32_t* __restrict__ ray_offsets,
-                                              int32_t* __restrict__ voxel_id, float2* __restrict__ t_range,
-                                              long long hit_cap) {
+// positions (coalesced, four independent copies in flight per thread).
+constexpr int kPlaceThreads = 256;
+
+__global__ void __launch_bounds__(kPlaceThreads) k_place(const TileInfo* __restrict__ tiles, const TileParams p,
+                                                        const int32_t* __restrict__ ray_cnt,
+                                                        int32_t* __restrict__ ray_offsets,
+                                                        int32_t* __restrict__ voxel_id, float2* __restrict__ t_range) {
     __shared__ int warp_sums[kTR / 32 + 1];
     if (p.ctr->status != kStatusOk) return;
     for (long long t = blockIdx.x; t < p.ntiles; t += gridDim.x) {
         const long long ra = t * kTR;
         const int nr = (int)min((long long)kTR, p.R - ra);
         const long long off = tiles[t].count;           // exclusive prefix (k_tile_scan)
-        const int v = (int)threadIdx.x < nr ? ray_cnt[ra + threadIdx.x] : 0;
-        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-        int incl = v;
+        const long long st = tiles[t].stage;
+        if (threadIdx.x < kTR) {
+            const int v = (int)threadIdx.x < nr ? ray_cnt[ra + threadIdx.x] : 0;
+            const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+            int incl = v;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += y;
-        }
-        if (lane == 31) warp_sums[warp] = incl;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            int a = 0;
-            for (int w = 0; w < kTR / 32; ++w) {
-                const int x = warp_sums[w];
-                warp_sums[w] = a;
-                a += x;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
             }
-            warp_sums[kTR / 32] = a;
+            if (lane == 31) warp_sums[warp] = incl;
+            asm volatile("bar.sync 1, %0;" ::"r"(kTR));   // the kTR scanning threads only
+            if (threadIdx.x == 0) {
+                int a = 0;
+                for (int w = 0; w < kTR / 32; ++w) {
+                    const int x = warp_sums[w];
+                    warp_sums[w] = a;
+                    a += x;
+                }
+                warp_sums[kTR / 32] = a;
+            }
+            asm volatile("bar.sync 1, %0;" ::"r"(kTR));
+            if ((int)threadIdx.x < nr) ray_offsets[ra + threadIdx.x] = (int32_t)(off + warp_sums[warp] + incl - v);
         }
         __syncthreads();
-        if ((int)threadIdx.x < nr) ray_offsets[ra + threadIdx.x] = (int32_t)(off + warp_sums[warp] + incl - v);
-        const int cnt = warp_sums[kTR / 32];
-        if (t == p.ntiles - 1 && threadIdx.x == 0) ray_offsets[p.R] = (int32_t)(off + cnt);
         // staged entries -> final positions (within both capacities: the
         // status checked above covers the staging list and H <= hit_cap)
-        __syncthreads();
-        const long long st = p.tiles[t].stage;
-        for (int i = threadIdx.x; i < cnt; i += kTR) {
-            voxel_id[off + i] = p.stage_vid[st + i];
-            t_range[off + i] = p.stage_tr[st + i];
+        const int cnt = warp_sums[kTR / 32];
+        if (t == p.ntiles - 1 && threadIdx.x == 0) ray_offsets[p.R] = (int32_t)(off + cnt);
+        for (int i0 = threadIdx.x; i0 < cnt; i0 += 4 * kPlaceThreads) {
+            int32_t v[4];
+            float2 tr[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int i = i0 + u * kPlaceThreads;
+                if (i < cnt) {
+                    v[u] = p.stage_vid[st + i];
+                    tr[u] = p.stage_tr[st + i];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int i = i0 + u * kPlaceThreads;
+                if (i < cnt) {
+                    voxel_id[off + i] = v[u];
+                    t_range[off + i] = tr[u];
+                }
+            }
         }
         __syncthreads();
     }
@@ -509,8 +532,8 @@ int enqueue_traversal(const nglod_svo* svo, const float* o, const float* d, int6
     const long long grid = std::min<long long>(ntiles, (long long)sms * traverse_ctas_per_sm());
     k_traverse<<<(unsigned)grid, kThreads, sizeof(TileSmem), st>>>(p);
     k_tile_scan<<<1, kScanThreads, 0, st>>>(tiles, ntiles, ctr, hit_capacity, D);
-    k_place<<<(unsigned)std::min<long long>(ntiles, (long long)sms * 16), kTR, 0, st>>>(
-        tiles, p, ray_cnt, ray_offsets, voxel_id, (float2*)t_range, hit_capacity);
+    k_place<<<(unsigned)std::min<long long>(ntiles, (long long)sms * 8), kPlaceThreads, 0, st>>>(
+        tiles, p, ray_cnt, ray_offsets, voxel_id, (float2*)t_range);
     NGLOD_CUDA(cudaGetLastError());
     return NGLOD_OK;
 }
