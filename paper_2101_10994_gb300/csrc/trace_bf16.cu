@@ -200,6 +200,8 @@ __global__ void __launch_bounds__(kTM, kCtasPerSm) k_trace_bf16(const DecPtrsB d
     const int g = lane >> 3, l = lane & 7, gbase = g << 3;
     const unsigned gmask = 0xffu << gbase;
     stage_bf16_decoder<IN, FP8>(S, dp);
+    for (int i = threadIdx.x; i < (int)(sizeof(S.A) / 16); i += blockDim.x)
+        reinterpret_cast<uint4*>(S.A)[i] = make_uint4(0u, 0u, 0u, 0u);   // rows of idle warps stay finite
     setup_tmem(S);
     const uint32_t taddr = S.taddr;
     uint32_t phase = 0;
@@ -215,18 +217,23 @@ __global__ void __launch_bounds__(kTM, kCtasPerSm) k_trace_bf16(const DecPtrsB d
         if (!__syncthreads_or(act)) break;
         const float x0 = fmaf(st.t, st.dx, st.ox), x1 = fmaf(st.t, st.dy, st.oy), x2 = fmaf(st.t, st.dz, st.oz);
         const float q0 = __fadd_rn(x0, 1.0f), q1 = __fadd_rn(x1, 1.0f), q2 = __fadd_rn(x2, 1.0f);
+        // a warp without rays (the tail of the frame) leaves its 32 A-tile
+        // rows as they are and skips its epilogue: its rows are never read
+        const bool wact = __any_sync(0xffffffffu, act);
+        if (wact) {
 #pragma unroll 1
-        for (int r = 0; r < 8; ++r) {
-            const int s = r * 4 + g;
-            const int sact = __shfl_sync(0xffffffffu, act ? 1 : 0, s);
-            const int svox = __shfl_sync(0xffffffffu, st.vox, s);
-            const uint32_t sijk = __shfl_sync(0xffffffffu, st.ijk, s);
-            const float s0 = __shfl_sync(0xffffffffu, q0, s);
-            const float s1 = __shfl_sync(0xffffffffu, q1, s);
-            const float s2 = __shfl_sync(0xffffffffu, q2, s);
-            float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (sact) z = gather_slot<T>(tb, A.D, svox, sijk, s0, s1, s2, gmask, gbase, l);
-            put_z<FP8>(S, warp * 32 + s, l, z, dp.z_scale);
+            for (int r = 0; r < 8; ++r) {
+                const int s = r * 4 + g;
+                const int sact = __shfl_sync(0xffffffffu, act ? 1 : 0, s);
+                const int svox = __shfl_sync(0xffffffffu, st.vox, s);
+                const uint32_t sijk = __shfl_sync(0xffffffffu, st.ijk, s);
+                const float s0 = __shfl_sync(0xffffffffu, q0, s);
+                const float s1 = __shfl_sync(0xffffffffu, q1, s);
+                const float s2 = __shfl_sync(0xffffffffu, q2, s);
+                float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (sact) z = gather_slot<T>(tb, A.D, svox, sijk, s0, s1, s2, gmask, gbase, l);
+                put_z<FP8>(S, warp * 32 + s, l, z, dp.z_scale);
+            }
         }
         const bool ok = mma_tile<FP8>(S, taddr, phase);
         if (!__syncthreads_and(ok)) {
@@ -234,7 +241,7 @@ __global__ void __launch_bounds__(kTM, kCtasPerSm) k_trace_bf16(const DecPtrsB d
             drained = false;
             break;
         }
-        const float dhat = epilogue<IN>(S, taddr, dp.b2, x0, x1, x2);
+        const float dhat = wact ? epilogue<IN>(S, taddr, dp.b2, x0, x1, x2) : 0.0f;
         if (act) step_update(st, dhat, A, tb);
         publish_hits(st, A, lane);
     }
@@ -316,6 +323,8 @@ __global__ void __launch_bounds__(kTM, kCtasPerSm) k_trace_batch(const TraceJob*
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int g8 = lane >> 3, l = lane & 7, gbase = g8 << 3;
     const unsigned gmask = 0xffu << gbase;
+    for (int i = threadIdx.x; i < (int)(sizeof(S.A) / 16); i += blockDim.x)
+        reinterpret_cast<uint4*>(S.A)[i] = make_uint4(0u, 0u, 0u, 0u);   // rows of idle warps stay finite
     if (threadIdx.x == 0) tc::mbar_init(&S.bar, 1);
     if (warp == 0) {
         tc::tmem_alloc(&S.taddr, kHidden);
@@ -346,8 +355,9 @@ __global__ void __launch_bounds__(kTM, kCtasPerSm) k_trace_batch(const TraceJob*
             if (!__syncthreads_or(act)) break;
             const float x0 = fmaf(st.t, st.dx, st.ox), x1 = fmaf(st.t, st.dy, st.oy), x2 = fmaf(st.t, st.dz, st.oz);
             const float q0 = __fadd_rn(x0, 1.0f), q1 = __fadd_rn(x1, 1.0f), q2 = __fadd_rn(x2, 1.0f);
+            const bool wact = __any_sync(0xffffffffu, act);   // idle warps: rows unread, no epilogue
 #pragma unroll 1
-            for (int r = 0; r < 8; ++r) {
+            for (int r = 0; r < (wact ? 8 : 0); ++r) {
                 const int s = r * 4 + g8;
                 const int sact = __shfl_sync(0xffffffffu, act ? 1 : 0, s);
                 const int sjob = __shfl_sync(0xffffffffu, st.job, s);
@@ -366,7 +376,7 @@ __global__ void __launch_bounds__(kTM, kCtasPerSm) k_trace_batch(const TraceJob*
                 drained = false;
                 break;
             }
-            const float dhat = epilogue<IN>(S, taddr, dp.b2, x0, x1, x2);
+            const float dhat = wact ? epilogue<IN>(S, taddr, dp.b2, x0, x1, x2) : 0.0f;
             if (act) step_update(st, dhat, jobs[st.job].A, jobs[st.job].tb);
             publish_hits_batch(st, jobs);
         }
@@ -504,6 +514,10 @@ struct BlendSmem {
 constexpr int kBlendSmem = (int)((sizeof(BlendSmem) + 1023) / 1024 * 1024);
 
 __device__ __forceinline__ void setup_blend(BlendSmem& S) {
+    for (int i = threadIdx.x; i < (int)(sizeof(S.lo.A) / 16); i += blockDim.x) {
+        reinterpret_cast<uint4*>(S.lo.A)[i] = make_uint4(0u, 0u, 0u, 0u);   // rows of idle warps stay finite
+        reinterpret_cast<uint4*>(S.hi.A)[i] = make_uint4(0u, 0u, 0u, 0u);
+    }
     if (threadIdx.x == 0) {
         tc::mbar_init(&S.lo.bar, 1);
         tc::mbar_init(&S.hi.bar, 1);
@@ -536,11 +550,11 @@ __device__ __forceinline__ void gather_pair(const Tables& tb, int dd, int dlo, i
 template <int IN>
 __device__ __forceinline__ int blend_decode(BlendSmem& S, uint32_t taddr, uint32_t& ph_lo, uint32_t& ph_hi,
                                             float b2lo, float b2hi, float alpha, float x0, float x1, float x2,
-                                            float& dhat) {
+                                            bool wact, float& dhat) {
     if (!__syncthreads_and(mma_tile<false>(S.lo, taddr, ph_lo))) return 1;
-    const float dlo = epilogue<IN>(S.lo, taddr, b2lo, x0, x1, x2);
+    const float dlo = wact ? epilogue<IN>(S.lo, taddr, b2lo, x0, x1, x2) : 0.0f;
     if (!__syncthreads_and(mma_tile<false>(S.hi, taddr, ph_hi))) return 2;
-    const float dhi = epilogue<IN>(S.hi, taddr, b2hi, x0, x1, x2);
+    const float dhi = wact ? epilogue<IN>(S.hi, taddr, b2hi, x0, x1, x2) : 0.0f;
     dhat = fmaf(alpha, dhi - dlo, dlo);
     return 0;
 }
@@ -592,7 +606,8 @@ __global__ void __launch_bounds__(kTM, kCtasPerSm) k_trace_blend_bf16(const DecP
             put_z<false>(S.hi, warp * 32 + s, l, zh, 1.0f);
         }
         float dhat = 0.0f;
-        failed = blend_decode<IN>(S, taddr, ph_lo, ph_hi, plo.b2, phi.b2, alpha, x0, x1, x2, dhat);
+        failed = blend_decode<IN>(S, taddr, ph_lo, ph_hi, plo.b2, phi.b2, alpha, x0, x1, x2,
+                                  __any_sync(0xffffffffu, act), dhat);
         if (failed) {
             if (threadIdx.x == 0) atomicExch(err, kStatusTimeout);
             break;
@@ -649,7 +664,8 @@ __global__ void __launch_bounds__(kTM, kCtasPerSm) k_query_blend_bf16(const DecP
             put_z<false>(S.hi, warp * 32 + s, l, zh, 1.0f);
         }
         float out = 0.0f;
-        failed = blend_decode<IN>(S, taddr, ph_lo, ph_hi, plo.b2, phi.b2, alpha, x0, x1, x2, out);
+        failed = blend_decode<IN>(S, taddr, ph_lo, ph_hi, plo.b2, phi.b2, alpha, x0, x1, x2,
+                                  __any_sync(0xffffffffu, act), out);
         if (failed) {
             if (threadIdx.x == 0) atomicExch(err, kStatusTimeout);
             break;
