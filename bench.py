@@ -74,6 +74,27 @@ def bf16_available():
 
 
 # ----------------------------------------------------------------------------
+# replicas across ranks (torchrun): no collective on the data path, only the
+# job's clock -- the slowest rank's time -- and the whole job's units
+# ----------------------------------------------------------------------------
+def max_over_ranks(value, device=None):
+    """The largest value over the ranks of the process group (the value
+    itself when no group is initialised)."""
+    import torch
+    import torch.distributed as td
+    if not (td.is_available() and td.is_initialized()):
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    td.all_reduce(t, op=td.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank, world, seconds):
+    """Whole-job throughput: the units all ranks processed over the job's time."""
+    return world * units_per_rank / seconds
+
+
+# ----------------------------------------------------------------------------
 # clocks during the timed region
 # ----------------------------------------------------------------------------
 class ClockSampler:
@@ -215,15 +236,12 @@ def run_ours(args, rank, world, local_rank):
         trace = [e[1].elapsed_time(e[2]) for e in evs]
         norm = [e[2].elapsed_time(e[3]) for e in evs]
         total = sum(trav) + sum(trace) + sum(norm)           # ms over K steps
-        tmax = torch.tensor([total], dtype=torch.float64, device=dev)
-        if dist:
-            td.all_reduce(tmax, op=td.ReduceOp.MAX)
-        ms_step = float(tmax.item()) / args.steps
+        ms_step = max_over_ranks(total, dev) / args.steps
         hits = int(out["hit"].sum().item())
         lists = step(mode, out, wev)
         sizes = lists.level_sizes()
         results[mode] = dict(level_sizes=sizes,
-            ms_per_step=ms_step, rays_per_s=world * R / (ms_step * 1e-3),
+            ms_per_step=ms_step, rays_per_s=job_rate(R, world, ms_step * 1e-3),
             queries_per_s=world * queries / args.steps / (sum(trace) / args.steps * 1e-3),
             ms_traverse=sum(trav) / args.steps, ms_trace=sum(trace) / args.steps,
             ms_normals=sum(norm) / args.steps, queries_per_frame=queries // args.steps,
@@ -284,10 +302,8 @@ def run_ours(args, rank, world, local_rank):
         e1.synchronize()
         if k >= args.warmup:
             e2e_ms.append(e0.elapsed_time(e1))
-    e2e_t = torch.tensor([statistics.mean(e2e_ms)], dtype=torch.float64, device=dev)
-    if dist:
-        td.all_reduce(e2e_t, op=td.ReduceOp.MAX)
-    e2e = dict(value=world * R / (float(e2e_t.item()) * 1e-3), unit="rays/s",
+    e2e_ms_job = max_over_ranks(statistics.mean(e2e_ms), dev)
+    e2e = dict(value=job_rate(R, world, e2e_ms_job * 1e-3), unit="rays/s",
                h2d_bytes_per_step=int(h_o.numel() * 4 + h_d.numel() * 4),
                d2h_bytes_per_step=int(h_t.numel() * 4 + h_hit.numel() + h_n.numel() * 4))
     svo.free()
