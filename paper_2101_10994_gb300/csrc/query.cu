@@ -327,7 +327,6 @@ template <typename T, int IN>
 __global__ void __launch_bounds__(kThreads, 2) k_trace_f32(const DecPtrs dp, const Tables tb, const TraceArgs A) {
     __shared__ __align__(16) float zbuf[kWarps][32 * kZStride];
     __shared__ __align__(16) SmemDecoder sd;
-    __shared__ __align__(16) int cidbuf[kWarps][kCidBufInts];
     stage_decoder<IN>(sd, dp.W1, dp.b1, dp.W2);
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -345,20 +344,25 @@ __global__ void __launch_bounds__(kThreads, 2) k_trace_f32(const DecPtrs dp, con
         const bool act = S.ray >= 0;
         const float x0 = fmaf(S.t, S.dx, S.ox), x1 = fmaf(S.t, S.dy, S.oy), x2 = fmaf(S.t, S.dz, S.oz);
         const float q0 = __fadd_rn(x0, 1.0f), q1 = __fadd_rn(x1, 1.0f), q2 = __fadd_rn(x2, 1.0f);
-        auto slot = [&](int s) {
-            GSlot G;
-            G.dd = __shfl_sync(0xffffffffu, act ? A.D : -1, s);
-            G.vox = __shfl_sync(0xffffffffu, S.vox, s);
-            G.ijk = __shfl_sync(0xffffffffu, S.ijk, s);
-            G.q0 = __shfl_sync(0xffffffffu, q0, s);
-            G.q1 = __shfl_sync(0xffffffffu, q1, s);
-            G.q2 = __shfl_sync(0xffffffffu, q2, s);
-            return G;
-        };
-        auto store = [&](int r, float4, float4 z) {
-            *reinterpret_cast<float4*>(zb + (r * 4 + g) * kZStride + 4 * l) = z;
-        };
-        gather_warp<T>(tb, kMaxDepth, kMaxDepth, cidbuf[warp], slot, store, gmask, gbase, g, l);
+        {
+            const int g4 = lane >> 2, l4 = lane & 3, gb4 = g4 << 2;
+            const unsigned gm4 = 0xfu << gb4;
+#pragma unroll 1
+            for (int r = 0; r < 4; ++r) {
+                const int s = r * 8 + g4;
+                const int sact = __shfl_sync(0xffffffffu, act ? 1 : 0, s);
+                const int svox = __shfl_sync(0xffffffffu, S.vox, s);
+                const uint32_t sijk = __shfl_sync(0xffffffffu, S.ijk, s);
+                const float s0 = __shfl_sync(0xffffffffu, q0, s);
+                const float s1 = __shfl_sync(0xffffffffu, q1, s);
+                const float s2 = __shfl_sync(0xffffffffu, q2, s);
+                float4 za = make_float4(0.f, 0.f, 0.f, 0.f), zc = za;
+                if (sact) gather_slot4<T>(tb, A.D, svox, sijk, s0, s1, s2, gm4, gb4, l4, za, zc);
+                float4* zr = reinterpret_cast<float4*>(zb + s * kZStride + 8 * l4);
+                zr[0] = za;
+                zr[1] = zc;
+            }
+        }
         __syncwarp();
         const float dhat = mlp_f32<IN>(sd, dp.b2, zb + lane * kZStride, x0, x1, x2);
         __syncwarp();

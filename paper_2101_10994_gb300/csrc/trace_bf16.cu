@@ -197,8 +197,6 @@ __global__ void __launch_bounds__(kTM, kCtasPerSm) k_trace_bf16(const DecPtrsB d
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     BfSmem& S = *reinterpret_cast<BfSmem*>(smem_raw);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int g = lane >> 3, l = lane & 7, gbase = g << 3;
-    const unsigned gmask = 0xffu << gbase;
     stage_bf16_decoder<IN, FP8>(S, dp);
     for (int i = threadIdx.x; i < (int)(sizeof(S.A) / 16); i += blockDim.x)
         reinterpret_cast<uint4*>(S.A)[i] = make_uint4(0u, 0u, 0u, 0u);   // rows of idle warps stay finite
@@ -221,18 +219,21 @@ __global__ void __launch_bounds__(kTM, kCtasPerSm) k_trace_bf16(const DecPtrsB d
         // rows as they are and skips its epilogue: its rows are never read
         const bool wact = __any_sync(0xffffffffu, act);
         if (wact) {
+            const int g4 = lane >> 2, l4 = lane & 3, gb4 = g4 << 2;
+            const unsigned gm4 = 0xfu << gb4;
 #pragma unroll 1
-            for (int r = 0; r < 8; ++r) {
-                const int s = r * 4 + g;
+            for (int r = 0; r < 4; ++r) {
+                const int s = r * 8 + g4;
                 const int sact = __shfl_sync(0xffffffffu, act ? 1 : 0, s);
                 const int svox = __shfl_sync(0xffffffffu, st.vox, s);
                 const uint32_t sijk = __shfl_sync(0xffffffffu, st.ijk, s);
                 const float s0 = __shfl_sync(0xffffffffu, q0, s);
                 const float s1 = __shfl_sync(0xffffffffu, q1, s);
                 const float s2 = __shfl_sync(0xffffffffu, q2, s);
-                float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (sact) z = gather_slot<T>(tb, A.D, svox, sijk, s0, s1, s2, gmask, gbase, l);
-                put_z<FP8>(S, warp * 32 + s, l, z, dp.z_scale);
+                float4 za = make_float4(0.f, 0.f, 0.f, 0.f), zb = za;
+                if (sact) gather_slot4<T>(tb, A.D, svox, sijk, s0, s1, s2, gm4, gb4, l4, za, zb);
+                put_z<FP8>(S, warp * 32 + s, 2 * l4, za, dp.z_scale);
+                put_z<FP8>(S, warp * 32 + s, 2 * l4 + 1, zb, dp.z_scale);
             }
         }
         const bool ok = mma_tile<FP8>(S, taddr, phase);
@@ -321,8 +322,6 @@ __global__ void __launch_bounds__(kTM, kCtasPerSm) k_trace_batch(const TraceJob*
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     BfSmem& S = *reinterpret_cast<BfSmem*>(smem_raw);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int g8 = lane >> 3, l = lane & 7, gbase = g8 << 3;
-    const unsigned gmask = 0xffu << gbase;
     for (int i = threadIdx.x; i < (int)(sizeof(S.A) / 16); i += blockDim.x)
         reinterpret_cast<uint4*>(S.A)[i] = make_uint4(0u, 0u, 0u, 0u);   // rows of idle warps stay finite
     if (threadIdx.x == 0) tc::mbar_init(&S.bar, 1);
@@ -356,9 +355,11 @@ __global__ void __launch_bounds__(kTM, kCtasPerSm) k_trace_batch(const TraceJob*
             const float x0 = fmaf(st.t, st.dx, st.ox), x1 = fmaf(st.t, st.dy, st.oy), x2 = fmaf(st.t, st.dz, st.oz);
             const float q0 = __fadd_rn(x0, 1.0f), q1 = __fadd_rn(x1, 1.0f), q2 = __fadd_rn(x2, 1.0f);
             const bool wact = __any_sync(0xffffffffu, act);   // idle warps: rows unread, no epilogue
+            const int g4 = lane >> 2, l4 = lane & 3, gb4 = g4 << 2;
+            const unsigned gm4 = 0xfu << gb4;
 #pragma unroll 1
-            for (int r = 0; r < (wact ? 8 : 0); ++r) {
-                const int s = r * 4 + g8;
+            for (int r = 0; r < (wact ? 4 : 0); ++r) {
+                const int s = r * 8 + g4;
                 const int sact = __shfl_sync(0xffffffffu, act ? 1 : 0, s);
                 const int sjob = __shfl_sync(0xffffffffu, st.job, s);
                 const int svox = __shfl_sync(0xffffffffu, st.vox, s);
@@ -366,9 +367,11 @@ __global__ void __launch_bounds__(kTM, kCtasPerSm) k_trace_batch(const TraceJob*
                 const float s0 = __shfl_sync(0xffffffffu, q0, s);
                 const float s1 = __shfl_sync(0xffffffffu, q1, s);
                 const float s2 = __shfl_sync(0xffffffffu, q2, s);
-                float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (sact) z = gather_slot<T>(jobs[sjob].tb, jobs[sjob].A.D, svox, sijk, s0, s1, s2, gmask, gbase, l);
-                put_z<FP8>(S, warp * 32 + s, l, z, dp.z_scale);
+                float4 za = make_float4(0.f, 0.f, 0.f, 0.f), zb = za;
+                if (sact)
+                    gather_slot4<T>(jobs[sjob].tb, jobs[sjob].A.D, svox, sijk, s0, s1, s2, gm4, gb4, l4, za, zb);
+                put_z<FP8>(S, warp * 32 + s, 2 * l4, za, dp.z_scale);
+                put_z<FP8>(S, warp * 32 + s, 2 * l4 + 1, zb, dp.z_scale);
             }
             const bool ok = mma_tile<FP8>(S, taddr, phase);
             if (!__syncthreads_and(ok)) {
