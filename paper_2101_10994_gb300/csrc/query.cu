@@ -149,8 +149,6 @@ __global__ void __launch_bounds__(kThreads) k_grad(const DecPtrs dp, const Table
     stage_decoder<IN>(sd, dp.W1, dp.b1, dp.W2);
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int g = lane >> 3, l = lane & 7, gbase = g << 3;
-    const unsigned gmask = 0xffu << gbase;
     float* zb = zbuf[warp];
     float* gb = gxs[warp];
     const long long n = A.mode >= 1 ? (long long)*A.hit_count : A.n;
@@ -180,21 +178,24 @@ __global__ void __launch_bounds__(kThreads) k_grad(const DecPtrs dp, const Table
             }
         }
         const float q0 = __fadd_rn(x0, 1.0f), q1 = __fadd_rn(x1, 1.0f), q2 = __fadd_rn(x2, 1.0f);
-        // (A) z of the 32 items
+        // (A) z of the 32 items (4-lane groups, 8 channels a lane)
+        const int g4 = lane >> 2, l4 = lane & 3, gb4 = g4 << 2;
+        const unsigned gm4 = 0xfu << gb4;
 #pragma unroll 1
-        for (int r = 0; r < 8; ++r) {
-            const int s = r * 4 + g;
+        for (int r = 0; r < 4; ++r) {
+            const int s = r * 8 + g4;
             const int sdd = __shfl_sync(0xffffffffu, dd, s);
             const int svox = __shfl_sync(0xffffffffu, vox, s);
             const uint32_t sijk = __shfl_sync(0xffffffffu, ijk, s);
             const float s0 = __shfl_sync(0xffffffffu, q0, s);
             const float s1 = __shfl_sync(0xffffffffu, q1, s);
             const float s2 = __shfl_sync(0xffffffffu, q2, s);
-            float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+            float4 za = make_float4(0.f, 0.f, 0.f, 0.f), zc = za;
             if (sdd >= kFirstFeatureDepth)
-                z = gather_levels<T>(tb, sdd, kFirstFeatureDepth, min(sdd, dcap), svox, sijk, s0, s1, s2, gmask,
-                                     gbase, l);
-            *reinterpret_cast<float4*>(zb + s * kZStride + 4 * l) = z;
+                gather_slot4<T>(tb, sdd, svox, sijk, s0, s1, s2, gm4, gb4, l4, za, zc, dcap);
+            float4* zr = reinterpret_cast<float4*>(zb + s * kZStride + 8 * l4);
+            zr[0] = za;
+            zr[1] = zc;
         }
         __syncwarp();
         // (B) forward pass and v = sum_h W2_h [pre_h > 0] W1[h] for this lane's item
@@ -239,9 +240,10 @@ __global__ void __launch_bounds__(kThreads) k_grad(const DecPtrs dp, const Table
                 make_float4(gv[4 * j], gv[4 * j + 1], gv[4 * j + 2], gv[4 * j + 3]);
         __syncwarp();
         // (C) J^T v_z: the trilinear derivative weights of every level and corner
+        // (4-lane groups: lane l4 dots its 8 channels of each corner row with v_z)
 #pragma unroll 1
-        for (int r = 0; r < 8; ++r) {
-            const int s = r * 4 + g;
+        for (int r = 0; r < 4; ++r) {
+            const int s = r * 8 + g4;
             const int sdd = __shfl_sync(0xffffffffu, dd, s);
             const int svox = __shfl_sync(0xffffffffu, vox, s);
             const uint32_t sijk = __shfl_sync(0xffffffffu, ijk, s);
@@ -249,22 +251,28 @@ __global__ void __launch_bounds__(kThreads) k_grad(const DecPtrs dp, const Table
                                  __shfl_sync(0xffffffffu, q2, s)};
             float part[3] = {0.f, 0.f, 0.f};
             if (sdd >= kFirstFeatureDepth) {
-                const float4 gz = *reinterpret_cast<const float4*>(zb + s * kZStride + 4 * l);
-                const int a = (l <= sdd - kFirstFeatureDepth) ? __ldg(tb.anc[sdd] + (size_t)svox * 8 + l) : -1;
+                const float4 ga = *reinterpret_cast<const float4*>(zb + s * kZStride + 8 * l4);
+                const float4 gc = *reinterpret_cast<const float4*>(zb + s * kZStride + 8 * l4 + 4);
+                int2 a = make_int2(-1, -1);
+                if (2 * l4 <= sdd - kFirstFeatureDepth)
+                    a = __ldg(reinterpret_cast<const int2*>(tb.anc[sdd] + (size_t)svox * 8) + l4);
                 for (int dp2 = kFirstFeatureDepth; dp2 <= min(sdd, dcap); ++dp2) {
-                    const int vv = __shfl_sync(gmask, a, gbase + dp2 - kFirstFeatureDepth);
-                    const int cid = __ldg(tb.corners[dp2] + (size_t)vv * 8 + l);
+                    const int i = dp2 - kFirstFeatureDepth;
+                    const int vv = __shfl_sync(gm4, (i & 1) ? a.y : a.x, gb4 + (i >> 1));
+                    const int2 cc = __ldg(reinterpret_cast<const int2*>(tb.corners[dp2] + (size_t)vv * 8) + l4);
                     const int sh = sdd - dp2;
                     const float sc = pow2f(dp2 - 1);
-                    const uint32_t cc[3] = {unpack_i(sijk) >> sh, unpack_j(sijk) >> sh, unpack_k(sijk) >> sh};
+                    const uint32_t ci[3] = {unpack_i(sijk) >> sh, unpack_j(sijk) >> sh, unpack_k(sijk) >> sh};
                     float u[3];
 #pragma unroll
-                    for (int aa = 0; aa < 3; ++aa) u[aa] = clamp01(__fsub_rn(__fmul_rn(sq[aa], sc), (float)cc[aa]));
-                    const void* fb = tb.feats[dp2 - kFirstFeatureDepth];
+                    for (int aa = 0; aa < 3; ++aa) u[aa] = clamp01(__fsub_rn(__fmul_rn(sq[aa], sc), (float)ci[aa]));
+                    const void* fb = tb.feats[i];
 #pragma unroll
                     for (int c = 0; c < 8; ++c) {
-                        const float4 row = FeatLoad<T>::load(fb, __shfl_sync(gmask, cid, gbase + c), l);
-                        const float pc = row.x * gz.x + row.y * gz.y + row.z * gz.z + row.w * gz.w;
+                        float4 ra, rc;
+                        FeatLoad8<T>::load(fb, __shfl_sync(gm4, (c & 1) ? cc.y : cc.x, gb4 + (c >> 1)), l4, ra, rc);
+                        const float pc = ra.x * ga.x + ra.y * ga.y + ra.z * ga.z + ra.w * ga.w +
+                                         rc.x * gc.x + rc.y * gc.y + rc.z * gc.z + rc.w * gc.w;
                         float f[3], df[3];
 #pragma unroll
                         for (int aa = 0; aa < 3; ++aa) {
@@ -282,9 +290,8 @@ __global__ void __launch_bounds__(kThreads) k_grad(const DecPtrs dp, const Table
             for (int aa = 0; aa < 3; ++aa) {
                 part[aa] += __shfl_xor_sync(0xffffffffu, part[aa], 1);
                 part[aa] += __shfl_xor_sync(0xffffffffu, part[aa], 2);
-                part[aa] += __shfl_xor_sync(0xffffffffu, part[aa], 4);
             }
-            if (l == 0) {
+            if (l4 == 0) {
                 gb[s * 4] = part[0];
                 gb[s * 4 + 1] = part[1];
                 gb[s * 4 + 2] = part[2];
@@ -330,8 +337,6 @@ __global__ void __launch_bounds__(kThreads, 2) k_trace_f32(const DecPtrs dp, con
     stage_decoder<IN>(sd, dp.W1, dp.b1, dp.W2);
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int g = lane >> 3, l = lane & 7, gbase = g << 3;
-    const unsigned gmask = 0xffu << gbase;
     float* zb = zbuf[warp];
     RaySlot S;
     S.ray = -1;

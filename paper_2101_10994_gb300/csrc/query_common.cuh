@@ -130,13 +130,15 @@ struct FeatLoad8<__half> {
 // in the same order as gather_slot (bit-identical result).
 template <typename T>
 __device__ __forceinline__ void gather_slot4(const Tables& tb, int dd, int vox, uint32_t ijk, float q0, float q1,
-                                             float q2, unsigned gmask, int gbase, int l4, float4& za, float4& zb) {
+                                             float q2, unsigned gmask, int gbase, int l4, float4& za, float4& zb,
+                                             int dlast = kMaxDepth) {
     za = make_float4(0.f, 0.f, 0.f, 0.f);
     zb = za;
     int2 a = make_int2(-1, -1);
     if (2 * l4 <= dd - kFirstFeatureDepth) a = __ldg(reinterpret_cast<const int2*>(tb.anc[dd] + (size_t)vox * 8) + l4);
+    const int top = min(dd, dlast);     // depths above dlast are left out (level blending, Eq. 3)
 #pragma unroll 1
-    for (int dp = kFirstFeatureDepth; dp <= dd; ++dp) {
+    for (int dp = kFirstFeatureDepth; dp <= top; ++dp) {
         const int i = dp - kFirstFeatureDepth;
         const int v = __shfl_sync(gmask, (i & 1) ? a.y : a.x, gbase + (i >> 1));
         const int2 cc = __ldg(reinterpret_cast<const int2*>(tb.corners[dp] + (size_t)v * 8) + l4);
