@@ -71,8 +71,8 @@ __global__ void __launch_bounds__(kThreads) k_sdf_query(const DecPtrs dp, const 
     stage_decoder<IN>(sd, dp.W1, dp.b1, dp.W2);
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int g = lane >> 3, l = lane & 7, gbase = g << 3;
-    const unsigned gmask = 0xffu << gbase;
+    const int g4 = lane >> 2, l4 = lane & 3, gb4 = g4 << 2;
+    const unsigned gm4 = 0xfu << gb4;
     float* zb = zbuf[warp];
     for (long long base = ((long long)blockIdx.x * kWarps + warp) * 32; base < Q;
          base += (long long)gridDim.x * kWarps * 32) {
@@ -89,17 +89,19 @@ __global__ void __launch_bounds__(kThreads) k_sdf_query(const DecPtrs dp, const 
         const int dd = act ? locate_descend(tb, D, x0, x1, x2, vox, ijk) : -1;
         const float q0 = __fadd_rn(x0, 1.0f), q1 = __fadd_rn(x1, 1.0f), q2 = __fadd_rn(x2, 1.0f);
 #pragma unroll 1
-        for (int r = 0; r < 8; ++r) {
-            const int s = r * 4 + g;
+        for (int r = 0; r < 4; ++r) {
+            const int s = r * 8 + g4;
             const int sdd = __shfl_sync(0xffffffffu, dd, s);
             const int svox = __shfl_sync(0xffffffffu, vox, s);
             const uint32_t sijk = __shfl_sync(0xffffffffu, ijk, s);
             const float s0 = __shfl_sync(0xffffffffu, q0, s);
             const float s1 = __shfl_sync(0xffffffffu, q1, s);
             const float s2 = __shfl_sync(0xffffffffu, q2, s);
-            float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (sdd >= kFirstFeatureDepth) z = gather_slot<T>(tb, sdd, svox, sijk, s0, s1, s2, gmask, gbase, l);
-            *reinterpret_cast<float4*>(zb + s * kZStride + 4 * l) = z;
+            float4 za = make_float4(0.f, 0.f, 0.f, 0.f), zc = za;
+            if (sdd >= kFirstFeatureDepth) gather_slot4<T>(tb, sdd, svox, sijk, s0, s1, s2, gm4, gb4, l4, za, zc);
+            float4* zr = reinterpret_cast<float4*>(zb + s * kZStride + 8 * l4);
+            zr[0] = za;
+            zr[1] = zc;
         }
         __syncwarp();
         const float out = mlp_f32<IN>(sd, dp.b2, zb + lane * kZStride, x0, x1, x2);
@@ -386,8 +388,8 @@ __global__ void __launch_bounds__(kThreads, 3) k_trace_batch_f32(const TraceJob*
     __shared__ __align__(16) float zbuf[kWarps][32 * kZStride];
     __shared__ __align__(16) SmemDecoder sd;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int g = lane >> 3, l = lane & 7, gbase = g << 3;
-    const unsigned gmask = 0xffu << gbase;
+    const int g4 = lane >> 2, l4 = lane & 3, gb4 = g4 << 2;
+    const unsigned gm4 = 0xfu << gb4;
     float* zb = zbuf[warp];
     for (int gi = 0; gi < ngroups; ++gi) {
         const JobGroup G = groups[gi];
@@ -407,8 +409,8 @@ __global__ void __launch_bounds__(kThreads, 3) k_trace_batch_f32(const TraceJob*
             const float x0 = fmaf(S.t, S.dx, S.ox), x1 = fmaf(S.t, S.dy, S.oy), x2 = fmaf(S.t, S.dz, S.oz);
             const float q0 = __fadd_rn(x0, 1.0f), q1 = __fadd_rn(x1, 1.0f), q2 = __fadd_rn(x2, 1.0f);
 #pragma unroll 1
-            for (int r = 0; r < 8; ++r) {
-                const int s = r * 4 + g;
+            for (int r = 0; r < 4; ++r) {
+                const int s = r * 8 + g4;
                 const int sact = __shfl_sync(0xffffffffu, act ? 1 : 0, s);
                 const int sjob = __shfl_sync(0xffffffffu, S.job, s);
                 const int svox = __shfl_sync(0xffffffffu, S.vox, s);
@@ -416,9 +418,12 @@ __global__ void __launch_bounds__(kThreads, 3) k_trace_batch_f32(const TraceJob*
                 const float s0 = __shfl_sync(0xffffffffu, q0, s);
                 const float s1 = __shfl_sync(0xffffffffu, q1, s);
                 const float s2 = __shfl_sync(0xffffffffu, q2, s);
-                float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (sact) z = gather_slot<T>(jobs[sjob].tb, jobs[sjob].A.D, svox, sijk, s0, s1, s2, gmask, gbase, l);
-                *reinterpret_cast<float4*>(zb + s * kZStride + 4 * l) = z;
+                float4 za = make_float4(0.f, 0.f, 0.f, 0.f), zc = za;
+                if (sact)
+                    gather_slot4<T>(jobs[sjob].tb, jobs[sjob].A.D, svox, sijk, s0, s1, s2, gm4, gb4, l4, za, zc);
+                float4* zr = reinterpret_cast<float4*>(zb + s * kZStride + 8 * l4);
+                zr[0] = za;
+                zr[1] = zc;
             }
             __syncwarp();
             const float dhat = mlp_f32<IN>(sd, G.b2, zb + lane * kZStride, x0, x1, x2);
@@ -481,8 +486,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_trace_blend_f32(const DecPtrs l
     stage_decoder<IN>(shi, hi.W1, hi.b1, hi.W2);
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int g = lane >> 3, l = lane & 7, gbase = g << 3;
-    const unsigned gmask = 0xffu << gbase;
+    const int g4 = lane >> 2, l4 = lane & 3, gb4 = g4 << 2;
+    const unsigned gm4 = 0xfu << gb4;
     float* zb = reinterpret_cast<float*>(blend_smem + 2 * sizeof(SmemDecoder)) + warp * 32 * kZStride;
     RaySlot S;
     S.ray = -1;
@@ -501,22 +506,24 @@ __global__ void __launch_bounds__(kThreads, 2) k_trace_blend_f32(const DecPtrs l
             // pass 0: depths 3..D-1 into the rows; pass 1: add depth D
             const int d0 = pass ? A.D : kFirstFeatureDepth, d1 = pass ? A.D : A.D - 1;
 #pragma unroll 1
-            for (int r = 0; r < 8; ++r) {
-                const int s = r * 4 + g;
+            for (int r = 0; r < 4; ++r) {
+                const int s = r * 8 + g4;
                 const int sact = __shfl_sync(0xffffffffu, act ? 1 : 0, s);
                 const int svox = __shfl_sync(0xffffffffu, S.vox, s);
                 const uint32_t sijk = __shfl_sync(0xffffffffu, S.ijk, s);
                 const float s0 = __shfl_sync(0xffffffffu, q0, s);
                 const float s1 = __shfl_sync(0xffffffffu, q1, s);
                 const float s2 = __shfl_sync(0xffffffffu, q2, s);
-                float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (sact) z = gather_levels<T>(tb, A.D, d0, d1, svox, sijk, s0, s1, s2, gmask, gbase, l);
-                float4* row = reinterpret_cast<float4*>(zb + s * kZStride + 4 * l);
+                float4 za = make_float4(0.f, 0.f, 0.f, 0.f), zc = za;
+                if (sact) gather_slot4<T>(tb, A.D, svox, sijk, s0, s1, s2, gm4, gb4, l4, za, zc, d1, d0);
+                float4* row = reinterpret_cast<float4*>(zb + s * kZStride + 8 * l4);
                 if (pass) {
-                    const float4 p = *row;
-                    z = make_float4(p.x + z.x, p.y + z.y, p.z + z.z, p.w + z.w);
+                    const float4 p = row[0], q = row[1];
+                    za = make_float4(p.x + za.x, p.y + za.y, p.z + za.z, p.w + za.w);
+                    zc = make_float4(q.x + zc.x, q.y + zc.y, q.z + zc.z, q.w + zc.w);
                 }
-                *row = z;
+                row[0] = za;
+                row[1] = zc;
             }
             __syncwarp();
             const float dv = mlp_f32<IN>(pass ? shi : slo, pass ? hi.b2 : lo.b2, zb + lane * kZStride, x0, x1, x2);
@@ -541,8 +548,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_query_blend_f32(const DecPtrs l
     stage_decoder<IN>(shi, hi.W1, hi.b1, hi.W2);
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int g = lane >> 3, l = lane & 7, gbase = g << 3;
-    const unsigned gmask = 0xffu << gbase;
+    const int g4 = lane >> 2, l4 = lane & 3, gb4 = g4 << 2;
+    const unsigned gm4 = 0xfu << gb4;
     float* zb = reinterpret_cast<float*>(blend_smem + 2 * sizeof(SmemDecoder)) + warp * 32 * kZStride;
     for (long long base = ((long long)blockIdx.x * kWarps + warp) * 32; base < Q;
          base += (long long)gridDim.x * kWarps * 32) {
@@ -562,26 +569,28 @@ __global__ void __launch_bounds__(kThreads, 2) k_query_blend_f32(const DecPtrs l
 #pragma unroll 1
         for (int pass = 0; pass < 2; ++pass) {
 #pragma unroll 1
-            for (int r = 0; r < 8; ++r) {
-                const int s = r * 4 + g;
+            for (int r = 0; r < 4; ++r) {
+                const int s = r * 8 + g4;
                 const int sdd = __shfl_sync(0xffffffffu, dd, s);
                 const int svox = __shfl_sync(0xffffffffu, vox, s);
                 const uint32_t sijk = __shfl_sync(0xffffffffu, ijk, s);
                 const float s0 = __shfl_sync(0xffffffffu, q0, s);
                 const float s1 = __shfl_sync(0xffffffffu, q1, s);
                 const float s2 = __shfl_sync(0xffffffffu, q2, s);
-                float4* row = reinterpret_cast<float4*>(zb + s * kZStride + 4 * l);
+                float4* row = reinterpret_cast<float4*>(zb + s * kZStride + 8 * l4);
                 if (pass == 0) {
-                    float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+                    float4 za = make_float4(0.f, 0.f, 0.f, 0.f), zc = za;
                     if (sdd >= kFirstFeatureDepth)
-                        z = gather_levels<T>(tb, sdd, kFirstFeatureDepth, min(sdd, D - 1), svox, sijk, s0, s1, s2,
-                                             gmask, gbase, l);
-                    *row = z;
+                        gather_slot4<T>(tb, sdd, svox, sijk, s0, s1, s2, gm4, gb4, l4, za, zc, D - 1);
+                    row[0] = za;
+                    row[1] = zc;
                 } else if (sdd == D) {
                     // the depth-D level exists only where x's depth-D voxel does
-                    const float4 z = gather_levels<T>(tb, sdd, D, D, svox, sijk, s0, s1, s2, gmask, gbase, l);
-                    const float4 p = *row;
-                    *row = make_float4(p.x + z.x, p.y + z.y, p.z + z.z, p.w + z.w);
+                    float4 za, zc;
+                    gather_slot4<T>(tb, sdd, svox, sijk, s0, s1, s2, gm4, gb4, l4, za, zc, D, D);
+                    const float4 p = row[0], q = row[1];
+                    row[0] = make_float4(p.x + za.x, p.y + za.y, p.z + za.z, p.w + za.w);
+                    row[1] = make_float4(q.x + zc.x, q.y + zc.y, q.z + zc.z, q.w + zc.w);
                 }
             }
             __syncwarp();

@@ -131,14 +131,14 @@ struct FeatLoad8<__half> {
 template <typename T>
 __device__ __forceinline__ void gather_slot4(const Tables& tb, int dd, int vox, uint32_t ijk, float q0, float q1,
                                              float q2, unsigned gmask, int gbase, int l4, float4& za, float4& zb,
-                                             int dlast = kMaxDepth) {
+                                             int dlast = kMaxDepth, int dfirst = kFirstFeatureDepth) {
     za = make_float4(0.f, 0.f, 0.f, 0.f);
     zb = za;
     int2 a = make_int2(-1, -1);
     if (2 * l4 <= dd - kFirstFeatureDepth) a = __ldg(reinterpret_cast<const int2*>(tb.anc[dd] + (size_t)vox * 8) + l4);
-    const int top = min(dd, dlast);     // depths above dlast are left out (level blending, Eq. 3)
+    const int top = min(dd, dlast);     // only depths dfirst..dlast (level blending, Eq. 3)
 #pragma unroll 1
-    for (int dp = kFirstFeatureDepth; dp <= top; ++dp) {
+    for (int dp = dfirst; dp <= top; ++dp) {
         const int i = dp - kFirstFeatureDepth;
         const int v = __shfl_sync(gmask, (i & 1) ? a.y : a.x, gbase + (i >> 1));
         const int2 cc = __ldg(reinterpret_cast<const int2*>(tb.corners[dp] + (size_t)v * 8) + l4);
@@ -168,42 +168,6 @@ __device__ __forceinline__ void gather_slot4(const Tables& tb, int dd, int vox, 
             zb.w = fmaf(w[c], rb[c].w, zb.w);
         }
     }
-}
-
-// gather_slot restricted to the levels dfirst..dlast (3 <= dfirst, dlast <=
-// dd): this lane's four channels of sum_{dp=dfirst..dlast} psi_dp(x).  Used
-// by level blending (Eq. 3), which decodes the sums up to two consecutive
-// LODs.  All 8 lanes of the group must call it together.
-template <typename T>
-__device__ __forceinline__ float4 gather_levels(const Tables& tb, int dd, int dfirst, int dlast, int vox,
-                                                uint32_t ijk, float q0, float q1, float q2, unsigned gmask,
-                                                int gbase, int l) {
-    float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-    const int a = (l <= dd - kFirstFeatureDepth) ? __ldg(tb.anc[dd] + (size_t)vox * 8 + l) : -1;
-#pragma unroll 1
-    for (int dp = dfirst; dp <= dlast; ++dp) {
-        const int v = __shfl_sync(gmask, a, gbase + dp - kFirstFeatureDepth);
-        const int cid = __ldg(tb.corners[dp] + (size_t)v * 8 + l);
-        const int sh = dd - dp;
-        const float sc = pow2f(dp - 1);
-        const float u0 = clamp01(__fsub_rn(__fmul_rn(q0, sc), (float)(unpack_i(ijk) >> sh)));
-        const float u1 = clamp01(__fsub_rn(__fmul_rn(q1, sc), (float)(unpack_j(ijk) >> sh)));
-        const float u2 = clamp01(__fsub_rn(__fmul_rn(q2, sc), (float)(unpack_k(ijk) >> sh)));
-        float w[8];
-        trilinear_weights(u0, u1, u2, w);
-        const void* fb = tb.feats[dp - kFirstFeatureDepth];
-        float4 r[8];
-#pragma unroll
-        for (int c = 0; c < 8; ++c) r[c] = FeatLoad<T>::load(fb, __shfl_sync(gmask, cid, gbase + c), l);
-#pragma unroll
-        for (int c = 0; c < 8; ++c) {
-            z.x = fmaf(w[c], r[c].x, z.x);
-            z.y = fmaf(w[c], r[c].y, z.y);
-            z.z = fmaf(w[c], r[c].z, z.z);
-            z.w = fmaf(w[c], r[c].w, z.w);
-        }
-    }
-    return z;
 }
 
 // Locates x by descending from the root through the child masks (the voxels

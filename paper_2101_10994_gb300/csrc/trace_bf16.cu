@@ -259,8 +259,8 @@ __global__ void __launch_bounds__(kTM, kCtasPerSm) k_query_bf16(const DecPtrsB d
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     BfSmem& S = *reinterpret_cast<BfSmem*>(smem_raw);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int g = lane >> 3, l = lane & 7, gbase = g << 3;
-    const unsigned gmask = 0xffu << gbase;
+    const int g4 = lane >> 2, l4 = lane & 3, gb4 = g4 << 2;
+    const unsigned gm4 = 0xfu << gb4;
     stage_bf16_decoder<IN, FP8>(S, dp);
     setup_tmem(S);
     const uint32_t taddr = S.taddr;
@@ -281,17 +281,18 @@ __global__ void __launch_bounds__(kTM, kCtasPerSm) k_query_bf16(const DecPtrsB d
         const int dd = act ? locate_descend(tb, D, x0, x1, x2, vox, ijk) : -1;
         const float q0 = __fadd_rn(x0, 1.0f), q1 = __fadd_rn(x1, 1.0f), q2 = __fadd_rn(x2, 1.0f);
 #pragma unroll 1
-        for (int r = 0; r < 8; ++r) {
-            const int s = r * 4 + g;
+        for (int r = 0; r < 4; ++r) {
+            const int s = r * 8 + g4;
             const int sdd = __shfl_sync(0xffffffffu, dd, s);
             const int svox = __shfl_sync(0xffffffffu, vox, s);
             const uint32_t sijk = __shfl_sync(0xffffffffu, ijk, s);
             const float s0 = __shfl_sync(0xffffffffu, q0, s);
             const float s1 = __shfl_sync(0xffffffffu, q1, s);
             const float s2 = __shfl_sync(0xffffffffu, q2, s);
-            float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (sdd >= kFirstFeatureDepth) z = gather_slot<T>(tb, sdd, svox, sijk, s0, s1, s2, gmask, gbase, l);
-            put_z<FP8>(S, warp * 32 + s, l, z, dp.z_scale);
+            float4 za = make_float4(0.f, 0.f, 0.f, 0.f), zb = za;
+            if (sdd >= kFirstFeatureDepth) gather_slot4<T>(tb, sdd, svox, sijk, s0, s1, s2, gm4, gb4, l4, za, zb);
+            put_z<FP8>(S, warp * 32 + s, 2 * l4, za, dp.z_scale);
+            put_z<FP8>(S, warp * 32 + s, 2 * l4 + 1, zb, dp.z_scale);
         }
         const bool ok = mma_tile<FP8>(S, taddr, phase);
         if (!__syncthreads_and(ok)) {
@@ -535,17 +536,21 @@ __device__ __forceinline__ void setup_blend(BlendSmem& S) {
     tc::fence_after_sync();
 }
 
-// Group-cooperative: this lane's channels of z_lo (depths 3..dd-1 of a
-// depth-dd voxel) and z_hi = z_lo + psi_dd.
+// Group-cooperative (4-lane groups): this lane's 8 channels of z_lo
+// (depths 3..dd-1 of a depth-dd voxel) and z_hi = z_lo + psi_dd.
 template <typename T>
 __device__ __forceinline__ void gather_pair(const Tables& tb, int dd, int dlo, int vox, uint32_t ijk, float q0,
-                                            float q1, float q2, unsigned gmask, int gbase, int l, float4& zl,
-                                            float4& zh) {
-    zl = gather_levels<T>(tb, dd, kFirstFeatureDepth, min(dd, dlo), vox, ijk, q0, q1, q2, gmask, gbase, l);
-    zh = zl;
+                                            float q1, float q2, unsigned gmask, int gbase, int l4, float4 (&zl)[2],
+                                            float4 (&zh)[2]) {
+    gather_slot4<T>(tb, dd, vox, ijk, q0, q1, q2, gmask, gbase, l4, zl[0], zl[1], min(dd, dlo));
+    zh[0] = zl[0];
+    zh[1] = zl[1];
     if (dd > dlo) {
-        const float4 p = gather_levels<T>(tb, dd, dd, dd, vox, ijk, q0, q1, q2, gmask, gbase, l);
-        zh = make_float4(zl.x + p.x, zl.y + p.y, zl.z + p.z, zl.w + p.w);
+        float4 p[2];
+        gather_slot4<T>(tb, dd, vox, ijk, q0, q1, q2, gmask, gbase, l4, p[0], p[1], dd, dd);
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+            zh[h] = make_float4(zl[h].x + p[h].x, zl[h].y + p[h].y, zl[h].z + p[h].z, zl[h].w + p[h].w);
     }
 }
 
@@ -575,8 +580,8 @@ __global__ void __launch_bounds__(kTM, kCtasPerSm) k_trace_blend_bf16(const DecP
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     BlendSmem& S = *reinterpret_cast<BlendSmem*>(smem_raw);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int g = lane >> 3, l = lane & 7, gbase = g << 3;
-    const unsigned gmask = 0xffu << gbase;
+    const int g4 = lane >> 2, l4 = lane & 3, gb4 = g4 << 2;
+    const unsigned gm4 = 0xfu << gb4;
     stage_bf16_decoder<IN, false>(S.lo, plo);
     stage_bf16_decoder<IN, false>(S.hi, phi);
     setup_blend(S);
@@ -595,18 +600,21 @@ __global__ void __launch_bounds__(kTM, kCtasPerSm) k_trace_blend_bf16(const DecP
         const float x0 = fmaf(st.t, st.dx, st.ox), x1 = fmaf(st.t, st.dy, st.oy), x2 = fmaf(st.t, st.dz, st.oz);
         const float q0 = __fadd_rn(x0, 1.0f), q1 = __fadd_rn(x1, 1.0f), q2 = __fadd_rn(x2, 1.0f);
 #pragma unroll 1
-        for (int r = 0; r < 8; ++r) {
-            const int s = r * 4 + g;
+        for (int r = 0; r < 4; ++r) {
+            const int s = r * 8 + g4;
             const int sact = __shfl_sync(0xffffffffu, act ? 1 : 0, s);
             const int svox = __shfl_sync(0xffffffffu, st.vox, s);
             const uint32_t sijk = __shfl_sync(0xffffffffu, st.ijk, s);
             const float s0 = __shfl_sync(0xffffffffu, q0, s);
             const float s1 = __shfl_sync(0xffffffffu, q1, s);
             const float s2 = __shfl_sync(0xffffffffu, q2, s);
-            float4 zl = make_float4(0.f, 0.f, 0.f, 0.f), zh = zl;
-            if (sact) gather_pair<T>(tb, A.D, A.D - 1, svox, sijk, s0, s1, s2, gmask, gbase, l, zl, zh);
-            put_z<false>(S.lo, warp * 32 + s, l, zl, 1.0f);
-            put_z<false>(S.hi, warp * 32 + s, l, zh, 1.0f);
+            float4 zl[2] = {make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f)}, zh[2] = {zl[0], zl[1]};
+            if (sact) gather_pair<T>(tb, A.D, A.D - 1, svox, sijk, s0, s1, s2, gm4, gb4, l4, zl, zh);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                put_z<false>(S.lo, warp * 32 + s, 2 * l4 + h, zl[h], 1.0f);
+                put_z<false>(S.hi, warp * 32 + s, 2 * l4 + h, zh[h], 1.0f);
+            }
         }
         float dhat = 0.0f;
         failed = blend_decode<IN>(S, taddr, ph_lo, ph_hi, plo.b2, phi.b2, alpha, x0, x1, x2,
@@ -629,8 +637,8 @@ __global__ void __launch_bounds__(kTM, kCtasPerSm) k_query_blend_bf16(const DecP
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     BlendSmem& S = *reinterpret_cast<BlendSmem*>(smem_raw);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int g = lane >> 3, l = lane & 7, gbase = g << 3;
-    const unsigned gmask = 0xffu << gbase;
+    const int g4 = lane >> 2, l4 = lane & 3, gb4 = g4 << 2;
+    const unsigned gm4 = 0xfu << gb4;
     stage_bf16_decoder<IN, false>(S.lo, plo);
     stage_bf16_decoder<IN, false>(S.hi, phi);
     setup_blend(S);
@@ -652,19 +660,22 @@ __global__ void __launch_bounds__(kTM, kCtasPerSm) k_query_blend_bf16(const DecP
         const int dd = act ? locate_descend(tb, D, x0, x1, x2, vox, ijk) : -1;
         const float q0 = __fadd_rn(x0, 1.0f), q1 = __fadd_rn(x1, 1.0f), q2 = __fadd_rn(x2, 1.0f);
 #pragma unroll 1
-        for (int r = 0; r < 8; ++r) {
-            const int s = r * 4 + g;
+        for (int r = 0; r < 4; ++r) {
+            const int s = r * 8 + g4;
             const int sdd = __shfl_sync(0xffffffffu, dd, s);
             const int svox = __shfl_sync(0xffffffffu, vox, s);
             const uint32_t sijk = __shfl_sync(0xffffffffu, ijk, s);
             const float s0 = __shfl_sync(0xffffffffu, q0, s);
             const float s1 = __shfl_sync(0xffffffffu, q1, s);
             const float s2 = __shfl_sync(0xffffffffu, q2, s);
-            float4 zl = make_float4(0.f, 0.f, 0.f, 0.f), zh = zl;
+            float4 zl[2] = {make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f)}, zh[2] = {zl[0], zl[1]};
             if (sdd >= kFirstFeatureDepth)
-                gather_pair<T>(tb, sdd, D - 1, svox, sijk, s0, s1, s2, gmask, gbase, l, zl, zh);
-            put_z<false>(S.lo, warp * 32 + s, l, zl, 1.0f);
-            put_z<false>(S.hi, warp * 32 + s, l, zh, 1.0f);
+                gather_pair<T>(tb, sdd, D - 1, svox, sijk, s0, s1, s2, gm4, gb4, l4, zl, zh);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                put_z<false>(S.lo, warp * 32 + s, 2 * l4 + h, zl[h], 1.0f);
+                put_z<false>(S.hi, warp * 32 + s, 2 * l4 + h, zh[h], 1.0f);
+            }
         }
         float out = 0.0f;
         failed = blend_decode<IN>(S, taddr, ph_lo, ph_hi, plo.b2, phi.b2, alpha, x0, x1, x2,
