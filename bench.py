@@ -3,9 +3,12 @@
 LOD 5, on the seeded CSG-64 scene (the paper's frame scope: ray/octree
 traversal + sphere trace + normals), FP32 and BF16 decode.
 
-One step = one frame: svo_trace_rays -> sphere_trace -> trace_normals over
-2,073,600 rays already resident in HBM.  The L2 is flushed (a 256 MB write)
-between timed steps, outside the timed events.  Prints one JSON line.
+One step = one frame: ray/octree traversal -> sphere trace -> normals over
+2,073,600 rays already resident in HBM, as the library's frame renderer runs
+it (two chunks of rays on two CUDA streams, so one chunk's stages overlap the
+other's); the per-stage times come from the same frame run sequentially.
+The L2 is flushed (a 256 MB write) between timed steps, outside the timed
+events.  Prints one JSON line.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
     python bench.py --workload batch     # many scenes per frame: per-scene calls vs one
@@ -31,6 +34,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "sphere-traced rays/s and SDF queries/s at 1080p LOD5, bf16 vs fp32, % roofline"
+CHUNKS = 2          # ray chunks (and streams) of the frame renderer
 PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
 CSRC = os.path.join(ROOT, "paper_2101_10994_gb300", "csrc")
 KERNEL_SRC = {"k_traverse": ["traverse.cu", "nglod_internal.cuh"],
@@ -170,6 +174,7 @@ def run_ours(args, rank, world, local_rank):
     import torch
 
     from paper_2101_10994_gb300 import nglod as ng
+    from paper_2101_10994_gb300.frame import FrameRenderer
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     W = workload(args.width, args.height)
@@ -240,7 +245,36 @@ def run_ours(args, rank, world, local_rank):
         hits = int(out["hit"].sum().item())
         lists = step(mode, out, wev)
         sizes = lists.level_sizes()
-        results[mode] = dict(level_sizes=sizes,
+        # the frame as the library's frame renderer runs it: two chunks of rays on two
+        # streams (traversal, trace and normals of one chunk overlap the other's)
+        fr = FrameRenderer(svo, feats, dec, o, d, W["lod"], chunks=CHUNKS, eps=W["eps"], far=W["far"],
+                           max_steps=W["max_steps"], decode=mode, normals=True)
+        for _ in range(args.warmup):
+            flush.zero_()
+            fr.frame()
+        fr.check()
+        fev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        if dist:
+            td.barrier()
+        torch.cuda.synchronize()
+        with sampler:
+            for k in range(args.steps):
+                flush.zero_()
+                fev[k][0].record()
+                fr.frame()
+                fev[k][1].record()
+            torch.cuda.synchronize()
+        fr.check()
+        if dist:
+            td.barrier()
+        torch.cuda.synchronize()
+        ms_seq = ms_step
+        ms_step = max_over_ranks(sum(a.elapsed_time(b) for a, b in fev), dev) / args.steps
+        assert torch.equal(fr.out["t"], out["t"]) and torch.equal(fr.out["normal"], out["normal"])
+        del fr
+        results[mode] = dict(level_sizes=sizes, schedule=f"{CHUNKS} ray chunks on {CHUNKS} streams",
+            ms_sequential=ms_seq, rays_per_s_sequential=job_rate(R, world, ms_seq * 1e-3),
             ms_per_step=ms_step, rays_per_s=job_rate(R, world, ms_step * 1e-3),
             queries_per_s=world * queries / args.steps / (sum(trace) / args.steps * 1e-3),
             ms_traverse=sum(trav) / args.steps, ms_trace=sum(trace) / args.steps,
@@ -275,37 +309,37 @@ def run_ours(args, rank, world, local_rank):
                                      ms_trace_and_normals=statistics.mean(b for _, b, _ in bl),
                                      queries_per_frame=bl[-1][2], hit_pixels=int(out["hit"].sum().item()))
 
-    # ---- end to end through the public API with pinned host buffers ----
+    # ---- end to end through the public API with pinned host buffers: each chunk's
+    # rays copied in and its t / hit / normals copied out on the chunk's stream ----
     mode = "bf16" if "bf16" in modes else modes[0]
     h_o = torch.from_numpy(W["o"]).pin_memory()
     h_d = torch.from_numpy(W["d"]).pin_memory()
-    h_t = torch.empty(R, dtype=torch.float32).pin_memory()
-    h_hit = torch.empty(R, dtype=torch.uint8).pin_memory()
-    h_n = torch.empty((R, 3), dtype=torch.float32).pin_memory()
-    out = dict(t=torch.empty(R, device=dev), hit=torch.empty(R, dtype=torch.uint8, device=dev),
-               steps=torch.empty(R, dtype=torch.int32, device=dev), normal=torch.empty((R, 3), device=dev),
-               work=torch.empty(ng.lib().sphere_trace_workspace(R), dtype=torch.uint8, device=dev))
+    h_out = {"t": torch.empty(R, dtype=torch.float32).pin_memory(),
+             "hit": torch.empty(R, dtype=torch.uint8).pin_memory(),
+             "normal": torch.empty((R, 3), dtype=torch.float32).pin_memory()}
+    # the renderer sizes its lists from the rays it is built on; every timed frame then
+    # brings its rays in from the host buffers (the device copies are cleared first)
+    fr = FrameRenderer(svo, feats, dec, o.clone(), d.clone(), W["lod"], chunks=CHUNKS, eps=W["eps"], far=W["far"],
+                       max_steps=W["max_steps"], decode=mode, normals=True)
     e2e_ms = []
     for k in range(args.warmup + args.steps):
         flush.zero_()
+        fr.o.zero_()
+        fr.d.zero_()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        go = h_o.to(dev, non_blocking=True)
-        gd = h_d.to(dev, non_blocking=True)
-        lists = ng.svo_trace_rays(svo, go, gd, W["lod"])
-        ng.sphere_trace(svo, feats, dec, go, gd, lists, eps=W["eps"], far=W["far"], max_steps=W["max_steps"],
-                        decode=mode, normals=True, out=out)
-        h_t.copy_(out["t"], non_blocking=True)
-        h_hit.copy_(out["hit"], non_blocking=True)
-        h_n.copy_(out["normal"], non_blocking=True)
+        fr.frame(h_in=(h_o, h_d), h_out=h_out)
         e1.record()
         e1.synchronize()
         if k >= args.warmup:
             e2e_ms.append(e0.elapsed_time(e1))
+    fr.check()
+    assert torch.equal(h_out["t"], fr.out["t"].cpu())
     e2e_ms_job = max_over_ranks(statistics.mean(e2e_ms), dev)
     e2e = dict(value=job_rate(R, world, e2e_ms_job * 1e-3), unit="rays/s",
                h2d_bytes_per_step=int(h_o.numel() * 4 + h_d.numel() * 4),
-               d2h_bytes_per_step=int(h_t.numel() * 4 + h_hit.numel() + h_n.numel() * 4))
+               d2h_bytes_per_step=int(sum(v.numel() * v.element_size() for v in h_out.values())),
+               schedule=f"{CHUNKS} chunks on {CHUNKS} streams, copies overlapped with the other chunks' work")
     svo.free()
     return W, results, clock_info, e2e, modes
 
@@ -552,9 +586,10 @@ def main():
             "traversal_roofline": traversal_roofline(W, r, head, peaks),
             "clocks": clocks,
             "e2e": e2e,
-            # per frame: traversal (tiles, tile scan, placement) + trace + normals; the blended
-            # frame adds a second gradient pass and the normalisation
-            "gpu_launches": args.steps * (len(modes) * 5 + ("bf16_blend" in res) * 7),
+            # per frame: traversal (tiles, tile scan, placement) + trace + normals, once in the
+            # sequential frame and once per chunk in the renderer's frame; the blended frame adds
+            # a second gradient pass and the normalisation
+            "gpu_launches": args.steps * (len(modes) * 5 * (1 + CHUNKS) + ("bf16_blend" in res) * 7),
         }
         if "bf16" in res and "f32" in res:
             line["bf16_speedup"] = res["f32"]["ms_per_step"] / res["bf16"]["ms_per_step"]

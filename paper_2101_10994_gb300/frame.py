@@ -1,0 +1,103 @@
+"""One image per frame with its stages overlapped across CUDA streams.
+
+The rays of the image are split into a few consecutive chunks; each chunk's
+traversal (svo_trace_rays_async), sphere trace and normals are enqueued on
+its own stream, so the tail of one chunk's trace -- the few long rays that
+keep a persistent launch busy while most SMs idle -- overlaps the next
+chunk's traversal and trace, and one chunk's normals overlap another's
+trace.  No kernel waits for another; the chunks only share the GPU.  The
+outputs are the single-pass frame's, bit for bit (rays are independent).
+
+With host buffers, each chunk's rays are copied in and its results copied
+out on the chunk's stream, so the copies overlap the other chunks' work.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+from . import nglod as ng
+
+
+class FrameRenderer:
+    def __init__(self, svo: ng.SVO, feats: ng.Features, dec: ng.DecoderDev, o, d, lod: int, chunks: int = 2,
+                 eps: float = 1e-3, far: float = 5.0, max_steps: int = 128, decode: str = "bf16",
+                 normals: bool = True, headroom: float = 1.25):
+        import torch
+        self.torch = torch
+        self.svo, self.feats, self.dec, self.lod = svo, feats, dec, int(lod)
+        self.o, self.d = o.contiguous(), d.contiguous()
+        self.R = R = int(self.o.shape[0])
+        self.eps, self.far, self.max_steps, self.decode, self.normals = eps, far, max_steps, decode, normals
+        dev = self.o.device
+        # chunk bounds on multiples of 128 rays (the traversal's tile)
+        n = max(1, int(chunks))
+        self.bounds = sorted(set([min(R, R * i // n // 128 * 128) for i in range(n)] + [R]))
+        if self.bounds[0] != 0:
+            self.bounds = [0] + self.bounds
+        self.out = dict(t=torch.empty(R, dtype=torch.float32, device=dev),
+                        hit=torch.empty(R, dtype=torch.uint8, device=dev),
+                        steps=torch.empty(R, dtype=torch.int32, device=dev),
+                        normal=torch.empty((R, 3), dtype=torch.float32, device=dev) if normals else None)
+        L = ng.lib()
+        self.chunks = []
+        for rs, re_ in zip(self.bounds[:-1], self.bounds[1:]):
+            m = re_ - rs
+            # sizing pass: the lists of this chunk fix its capacities
+            lists = ng.svo_trace_rays(svo, self.o[rs:re_], self.d[rs:re_], self.lod)
+            cap = int(lists.voxel_id.numel() * headroom) + 4096
+            c = dict(rs=rs, n=m, cap=cap, stream=torch.cuda.Stream(device=dev),
+                     twork=torch.empty(L.svo_trace_rays_workspace(m, cap), dtype=torch.uint8, device=dev),
+                     offs=torch.empty(m + 1, dtype=torch.int32, device=dev),
+                     vid=torch.empty(cap, dtype=torch.int32, device=dev),
+                     tr=torch.empty((cap, 2), dtype=torch.float32, device=dev),
+                     swork=torch.empty(L.sphere_trace_workspace(m), dtype=torch.uint8, device=dev))
+            c["lists"] = ng.RayLists(c["offs"], c["vid"], c["tr"], 0, self.lod, c["twork"])
+            c["outs"] = dict(t=self.out["t"][rs:re_], hit=self.out["hit"][rs:re_], steps=self.out["steps"][rs:re_],
+                             normal=self.out["normal"][rs:re_] if normals else None, work=c["swork"])
+            self.chunks.append(c)
+
+    def _enqueue(self, c):
+        L = ng.lib()
+        st = c["stream"]
+        rs, re_ = c["rs"], c["rs"] + c["n"]
+        oo, dd = self.o[rs:re_], self.d[rs:re_]
+        ng._check(L.svo_trace_rays_async(self.svo.h, oo.data_ptr(), dd.data_ptr(), c["n"], self.lod,
+                                         c["twork"].data_ptr(), c["twork"].numel(), c["cap"], c["offs"].data_ptr(),
+                                         c["vid"].data_ptr(), c["tr"].data_ptr(), c["cap"],
+                                         C.c_void_p(st.cuda_stream)))
+        ng.sphere_trace(self.svo, self.feats, self.dec, oo, dd, c["lists"], eps=self.eps, far=self.far,
+                        max_steps=self.max_steps, decode=self.decode, normals=self.normals, stream=st, out=c["outs"])
+
+    def frame(self, h_in=None, h_out=None):
+        """Enqueues one frame after the work already on the current stream,
+        which waits for it.  h_in = (o, d) pinned host arrays to copy in, h_out
+        = dict of pinned host tensors (t, hit, normal) to copy the results
+        to, chunk by chunk on the chunks' streams."""
+        torch = self.torch
+        main = torch.cuda.current_stream()
+        start = torch.cuda.Event()
+        start.record(main)
+        for c in self.chunks:
+            st = c["stream"]
+            st.wait_event(start)
+            rs, re_ = c["rs"], c["rs"] + c["n"]
+            with torch.cuda.stream(st):
+                if h_in is not None:
+                    self.o[rs:re_].copy_(h_in[0][rs:re_], non_blocking=True)
+                    self.d[rs:re_].copy_(h_in[1][rs:re_], non_blocking=True)
+                self._enqueue(c)
+                if h_out is not None:
+                    for k, v in h_out.items():
+                        v[rs:re_].copy_(self.out[k][rs:re_], non_blocking=True)
+        for c in self.chunks:
+            main.wait_stream(c["stream"])
+
+    def check(self):
+        """Synchronises; raises if a chunk's lists outgrew their capacity or a
+        bounded wait expired."""
+        L = ng.lib()
+        stats = (C.c_int64 * 2)()
+        for c in self.chunks:
+            s = C.c_void_p(c["stream"].cuda_stream)
+            ng._check(L.svo_trace_rays_check(c["twork"].data_ptr(), self.lod, stats, s))
+            ng._check(L.sphere_trace_status(c["swork"].data_ptr(), s))

@@ -1,0 +1,43 @@
+"""A frame traced as chunks on several CUDA streams (FrameRenderer) equals the
+single-pass frame output for output: rays are independent, so splitting them
+changes only which launch handles which ray."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2101_10994_gb300 import scenes as S
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("decode,chunks", [("bf16", 2), ("f32", 3), ("fp8", 2)])
+def test_chunked_frame_equals_single_pass(ng, decode, chunks):
+    from paper_2101_10994_gb300.frame import FrameRenderer
+    sc, oc = S.csg_workload(64, seed=0, max_lod=5)
+    svo = ng.svo_build(oc.keys)
+    F = ng.Features(S.readout_features(oc, sc))
+    if decode == "fp8":
+        F.set_fp8_bound(svo, 5)
+    D = ng.DecoderDev.from_decoder(S.readout_decoder(5))
+    o, d, _ = S.camera_rays(640, 360, tile=8)
+    to, td = torch.from_numpy(o).cuda(), torch.from_numpy(d).cuda()
+    lists = ng.svo_trace_rays(svo, to, td, 5)
+    ref = ng.sphere_trace(svo, F, D, to, td, lists, decode=decode, normals=True)
+    fr = FrameRenderer(svo, F, D, to, td, 5, chunks=chunks, decode=decode)
+    assert len(fr.chunks) == chunks
+    for _ in range(2):                     # a second frame reuses every buffer
+        fr.frame()
+        fr.check()
+        for k in ("t", "hit", "steps", "normal"):
+            assert torch.equal(fr.out[k], ref[k]), k
+    # rays and results through pinned host buffers, copied chunk by chunk
+    h_in = (torch.from_numpy(o).pin_memory(), torch.from_numpy(d).pin_memory())
+    h_out = {"t": torch.empty(len(o)).pin_memory(), "hit": torch.empty(len(o), dtype=torch.uint8).pin_memory(),
+             "normal": torch.empty((len(o), 3)).pin_memory()}
+    fr.o.zero_()
+    fr.frame(h_in, h_out)
+    torch.cuda.synchronize()
+    fr.check()
+    assert torch.equal(h_out["t"], ref["t"].cpu()) and torch.equal(h_out["normal"], ref["normal"].cpu())
+    assert torch.equal(h_out["hit"], ref["hit"].cpu())
+    svo.free()
