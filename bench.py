@@ -283,31 +283,29 @@ def run_ours(args, rank, world, local_rank):
         if clock_info is None or mode == "bf16":
             clock_info = sampler.summary()
 
-    # ---- continuous LOD (Eq. 3): the same frame at L~ = lod - 0.5, BF16 ----
+    # ---- continuous LOD (Eq. 3): the same frame at L~ = lod - 0.5, BF16, frame renderer ----
     if "bf16" in modes and W["lod"] >= 2:
         lt = W["lod"] - 0.5
         dlo = ng.DecoderDev.from_decoder(W["dec_lo"])
-        out = dict(t=torch.empty(R, device=dev), hit=torch.empty(R, dtype=torch.uint8, device=dev),
-                   steps=torch.empty(R, dtype=torch.int32, device=dev), normal=torch.empty((R, 3), device=dev),
-                   work=torch.empty(ng.lib().sphere_trace_workspace(R), dtype=torch.uint8, device=dev))
+        fr = FrameRenderer(svo, feats, dlo, o, d, lt, chunks=CHUNKS, eps=W["eps"], far=W["far"],
+                           max_steps=W["max_steps"], decode="bf16", normals=True, dec_hi=dec)
         bl = []
         for k in range(args.warmup + args.steps):
             flush.zero_()
-            e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
-            e[0].record()
-            lists = ng.svo_trace_rays(svo, o, d, ng.blend_lists_lod(lt))
-            e[1].record()
-            ng.sphere_trace_blend(svo, feats, dlo, dec, o, d, lists, lt, eps=W["eps"], far=W["far"],
-                                  max_steps=W["max_steps"], decode="bf16", normals=True, out=out)
-            e[2].record()
-            e[2].synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fr.frame()
+            e1.record()
+            e1.synchronize()
             if k >= args.warmup:
-                bl.append((e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2]), int(out["steps"].sum().item())))
-        ms = statistics.mean(a + b for a, b, _ in bl)
-        results["bf16_blend"] = dict(lod_tilde=lt, ms_per_step=ms, rays_per_s=world * R / (ms * 1e-3),
-                                     ms_traverse=statistics.mean(a for a, _, _ in bl),
-                                     ms_trace_and_normals=statistics.mean(b for _, b, _ in bl),
-                                     queries_per_frame=bl[-1][2], hit_pixels=int(out["hit"].sum().item()))
+                bl.append(e0.elapsed_time(e1))
+        fr.check()
+        ms = max_over_ranks(statistics.mean(bl), dev)
+        results["bf16_blend"] = dict(lod_tilde=lt, schedule=f"{CHUNKS} ray chunks on {CHUNKS} streams",
+                                     ms_per_step=ms, rays_per_s=job_rate(R, world, ms * 1e-3),
+                                     queries_per_frame=int(fr.out["steps"].sum().item()),
+                                     hit_pixels=int(fr.out["hit"].sum().item()))
+        del fr
 
     # ---- end to end through the public API with pinned host buffers: each chunk's
     # rays copied in and its t / hit / normals copied out on the chunk's stream ----
@@ -589,7 +587,7 @@ def main():
             # per frame: traversal (tiles, tile scan, placement) + trace + normals, once in the
             # sequential frame and once per chunk in the renderer's frame; the blended frame adds
             # a second gradient pass and the normalisation
-            "gpu_launches": args.steps * (len(modes) * 5 * (1 + CHUNKS) + ("bf16_blend" in res) * 7),
+            "gpu_launches": args.steps * (len(modes) * 5 * (1 + CHUNKS) + ("bf16_blend" in res) * 7 * CHUNKS),
         }
         if "bf16" in res and "f32" in res:
             line["bf16_speedup"] = res["f32"]["ms_per_step"] / res["bf16"]["ms_per_step"]

@@ -19,11 +19,19 @@ from . import nglod as ng
 
 
 class FrameRenderer:
-    def __init__(self, svo: ng.SVO, feats: ng.Features, dec: ng.DecoderDev, o, d, lod: int, chunks: int = 2,
+    def __init__(self, svo: ng.SVO, feats: ng.Features, dec: ng.DecoderDev, o, d, lod, chunks: int = 2,
                  eps: float = 1e-3, far: float = 5.0, max_steps: int = 128, decode: str = "bf16",
-                 normals: bool = True, headroom: float = 1.25):
+                 normals: bool = True, headroom: float = 1.25, dec_hi: ng.DecoderDev | None = None):
+        """lod: an integer LOD, or a continuous L~ (Eq. 3) with dec = LOD floor(L~)'s decoder and
+        dec_hi = LOD floor(L~) + 1's; rays then walk their lists at ceil(L~)."""
         import torch
         self.torch = torch
+        self.lod_tilde = float(lod)
+        self.blend = self.lod_tilde != int(self.lod_tilde)
+        self.dec_hi = dec_hi
+        if self.blend and dec_hi is None:
+            raise ValueError("FrameRenderer: a fractional LOD needs dec_hi")
+        lod = ng.blend_lists_lod(self.lod_tilde) if self.blend else int(lod)
         self.svo, self.feats, self.dec, self.lod = svo, feats, dec, int(lod)
         self.o, self.d = o.contiguous(), d.contiguous()
         self.R = R = int(self.o.shape[0])
@@ -65,8 +73,14 @@ class FrameRenderer:
                                          c["twork"].data_ptr(), c["twork"].numel(), c["cap"], c["offs"].data_ptr(),
                                          c["vid"].data_ptr(), c["tr"].data_ptr(), c["cap"],
                                          C.c_void_p(st.cuda_stream)))
-        ng.sphere_trace(self.svo, self.feats, self.dec, oo, dd, c["lists"], eps=self.eps, far=self.far,
-                        max_steps=self.max_steps, decode=self.decode, normals=self.normals, stream=st, out=c["outs"])
+        if self.blend:
+            ng.sphere_trace_blend(self.svo, self.feats, self.dec, self.dec_hi, oo, dd, c["lists"], self.lod_tilde,
+                                  eps=self.eps, far=self.far, max_steps=self.max_steps, decode=self.decode,
+                                  normals=self.normals, stream=st, out=c["outs"])
+        else:
+            ng.sphere_trace(self.svo, self.feats, self.dec, oo, dd, c["lists"], eps=self.eps, far=self.far,
+                            max_steps=self.max_steps, decode=self.decode, normals=self.normals, stream=st,
+                            out=c["outs"])
 
     def frame(self, h_in=None, h_out=None):
         """Enqueues one frame after the work already on the current stream,

@@ -41,3 +41,21 @@ def test_chunked_frame_equals_single_pass(ng, decode, chunks):
     assert torch.equal(h_out["t"], ref["t"].cpu()) and torch.equal(h_out["normal"], ref["normal"].cpu())
     assert torch.equal(h_out["hit"], ref["hit"].cpu())
     svo.free()
+
+
+def test_chunked_blended_frame_equals_single_pass(ng):
+    from paper_2101_10994_gb300.frame import FrameRenderer
+    sc, oc = S.csg_workload(64, seed=0, max_lod=5)
+    svo = ng.svo_build(oc.keys)
+    F = ng.Features(S.readout_features(oc, sc))
+    D4, D5 = ng.DecoderDev.from_decoder(S.readout_decoder(4)), ng.DecoderDev.from_decoder(S.readout_decoder(5))
+    o, d, _ = S.camera_rays(480, 270, tile=8)
+    to, td = torch.from_numpy(o).cuda(), torch.from_numpy(d).cuda()
+    lists = ng.svo_trace_rays(svo, to, td, ng.blend_lists_lod(4.5))
+    ref = ng.sphere_trace_blend(svo, F, D4, D5, to, td, lists, 4.5, decode="bf16", normals=True)
+    fr = FrameRenderer(svo, F, D4, to, td, 4.5, chunks=2, decode="bf16", dec_hi=D5)
+    fr.frame()
+    fr.check()
+    for k in ("t", "hit", "steps", "normal"):
+        assert torch.equal(fr.out[k], ref[k]), k
+    svo.free()
