@@ -26,12 +26,18 @@ class Job:
 
 class BatchRenderer:
     def __init__(self, jobs, eps=1e-3, far=5.0, max_steps=128, decode="bf16", normals=True, ctas_per_sm=0,
-                 headroom=1.25, stream=None):
+                 headroom=1.25, stream=None, traversal_streams=4):
         import torch
         self.torch = torch
         self.jobs = jobs
+        # the jobs' traversals are independent: they run on a few side streams
+        # (forked from and joined back into the frame's stream, also under graph capture)
+        self.tstreams = [torch.cuda.Stream(device=jobs[0].o.device) for _ in range(max(0, traversal_streams))]
+        # the batched trace leaves the normals to frame(), which spreads the jobs'
+        # normal kernels over the side streams
+        self.normals = bool(normals)
         self.params = ng._TraceParams(eps, far, max_steps, 0, {"f32": ng.F32, "bf16": ng.BF16, "fp8": ng.FP8}[decode],
-                                      int(normals))
+                                      0)
         self.decode = decode
         L = ng.lib()
         dev = jobs[0].o.device
@@ -90,15 +96,40 @@ class BatchRenderer:
             pass
 
     def frame(self, stream=None):
-        """Enqueues one frame: every job's traversal, then the batched trace."""
+        """Enqueues one frame: every job's traversal (spread over the
+        traversal streams), then the batched trace on the frame's stream."""
+        torch = self.torch
         L = ng.lib()
-        s = C.c_void_p(ng._stream(stream))
-        for j, b in zip(self.jobs, self.bufs):
+        main = stream if stream is not None else torch.cuda.current_stream()
+        s = C.c_void_p(main.cuda_stream)
+        if self.tstreams:
+            start = torch.cuda.Event()
+            start.record(main)
+            for st in self.tstreams:
+                st.wait_event(start)
+        for i, (j, b) in enumerate(zip(self.jobs, self.bufs)):
+            st = self.tstreams[i % len(self.tstreams)] if self.tstreams else main
             ng._check(L.svo_trace_rays_async(j.svo.h, j.o.data_ptr(), j.d.data_ptr(), j.R, j.lod,
                                              b["twork"].data_ptr(), b["twork"].numel(), b["cap"],
                                              b["offs"].data_ptr(), b["vid"].data_ptr(), b["tr"].data_ptr(),
-                                             b["hcap"], s))
+                                             b["hcap"], C.c_void_p(st.cuda_stream)))
+        for st in self.tstreams:
+            main.wait_stream(st)
         ng._check(L.sphere_trace_batch_run(self.handle, s))
+        if self.normals:
+            if self.tstreams:
+                traced = torch.cuda.Event()
+                traced.record(main)
+                for st in self.tstreams:
+                    st.wait_event(traced)
+            for i, (j, b) in enumerate(zip(self.jobs, self.bufs)):
+                st = self.tstreams[i % len(self.tstreams)] if self.tstreams else main
+                fc, dc = j.feats.c(), j.dec.c()
+                ng._check(L.trace_normals(j.svo.h, C.byref(fc), C.byref(dc), j.o.data_ptr(), j.d.data_ptr(), j.R,
+                                          j.lod, b["swork"].data_ptr(), b["swork"].numel(), b["t"].data_ptr(),
+                                          b["hit"].data_ptr(), b["normal"].data_ptr(), C.c_void_p(st.cuda_stream)))
+            for st in self.tstreams:
+                main.wait_stream(st)
 
     def check(self, stream=None):
         """Synchronises; raises if a traversal overflowed or a wait expired."""
