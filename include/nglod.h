@@ -87,7 +87,18 @@ typedef struct {
     int decode_dtype;      /* NGLOD_F32 (CUDA cores), NGLOD_BF16 or
                               NGLOD_FP8E4M3 (tcgen05; see sdf_query)         */
     int want_normals;      /* 1: write normals of hit rays                    */
+    int normal_mode;       /* NGLOD_NORMALS_ANALYTIC (0): normalised analytic
+                              gradient of the decoded SDF (FP32);
+                              NGLOD_NORMALS_FD (1): central differences, the
+                              form supplementary Sec. A.4 names -- the SDF
+                              evaluated as sdf_query does (FP32 decode) at
+                              x +- fd_h e_a and n = normalise of the three
+                              differences                                  */
+    float fd_h;            /* FD step in scene units, in (0, 1) (FD only)     */
 } nglod_trace_params;
+
+#define NGLOD_NORMALS_ANALYTIC 0
+#define NGLOD_NORMALS_FD 1
 
 /* nglod_features_absmax -- the sum over LODs 1..lod of each feature table's
  * largest |value|, written to *h_out (synchronises).  The trilinear weights
@@ -294,9 +305,18 @@ int sphere_trace(const nglod_svo* svo, const nglod_features* feats,
  *   h_grad_W1/_b1/_W2  host arrays (index L-1) of device pointers, shapes as
  *                 the decoder, accumulated; grad_b2 device [num_lods], acc.
  *   grad_x        [Q, 3] accumulated, nullable.
- *   deterministic must be 0 (the ordered scatter is not built); feature and
- *                 weight gradients are summed with FP32 atomics, so their
- *                 rounding order varies between runs.
+ *   deterministic 0: feature and weight gradients are summed with FP32
+ *                 atomics, so their rounding order varies between runs.
+ *                 1: every contribution is summed exactly in 128-bit fixed
+ *                 point (quantum 2^-64; contributions below 2^-41 in
+ *                 magnitude lose their bits under 2^-64; sums must stay
+ *                 below 2^63) and each sum is rounded once to FP32, so
+ *                 feature gradients are bit-identical between runs and
+ *                 launch shapes, and decoder gradients between runs on one
+ *                 device.  A non-finite contribution makes every gradient
+ *                 output of the call NaN.  Allocates its accumulators
+ *                 stream-ordered (16 B per gradient element) and frees
+ *                 them before returning; NGLOD_ERR_CUDA if that fails.
  * Interpolation weights are recomputed from x, never stored.  Errors as
  * sdf_query.  Does not synchronise. */
 int sdf_backward(const nglod_svo* svo, const nglod_features* feats, const nglod_decoder* decs,
@@ -431,6 +451,14 @@ int trace_normals(const nglod_svo* svo, const nglod_features* feats,
                   const nglod_decoder* dec, const float* o, const float* d, int64_t R,
                   int lod, const void* work, size_t work_bytes, const float* t_hit,
                   const uint8_t* hit, float* normal, void* stream);
+
+/* trace_normals_fd -- as trace_normals, with the normals taken by central
+ * differences of step fd_h in (0, 1) (NGLOD_NORMALS_FD of nglod_trace_params;
+ * supplementary Sec. A.4): six sdf_query-style FP32 evaluations per hit. */
+int trace_normals_fd(const nglod_svo* svo, const nglod_features* feats, const nglod_decoder* dec,
+                     const float* o, const float* d, int64_t R, int lod, const void* work,
+                     size_t work_bytes, const float* t_hit, const uint8_t* hit, float fd_h,
+                     float* normal, void* stream);
 
 #ifdef __cplusplus
 }

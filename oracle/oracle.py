@@ -209,6 +209,30 @@ class OracleSVO:
         hi, _ = self.sdf_query(feats, dec_hi, x, lstar + 1)
         return (1.0 - alpha) * lo + alpha * hi
 
+    def fd_normals(self, feats, dec, x, lod, h: float, dec_hi=None, lod_tilde=None):
+        """Normals by central differences (supplementary Sec. A.4 obtains the
+        rendered normals by finite differences; the scheme and step are not
+        given -- read here as central differences with step h): the SDF in
+        FP64 at the points x + h e_a and x - h e_a, each coordinate rounded to
+        FP32 as the points are formed, and n = the normalised vector of the
+        three differences.  With ``lod_tilde`` the SDF is the Eq. 3 blend
+        (dec = LOD floor(L~)'s decoder, dec_hi = the next one's)."""
+        x = np.ascontiguousarray(x, np.float32).reshape(-1, 3)
+        Q = x.shape[0]
+        pts = np.repeat(x[:, None, :], 6, axis=1)
+        for a in range(3):
+            pts[:, 2 * a, a] = (x[:, a] + np.float32(h)).astype(np.float32)
+            pts[:, 2 * a + 1, a] = (x[:, a] - np.float32(h)).astype(np.float32)
+        pts = pts.reshape(-1, 3)
+        if lod_tilde is None:
+            f, _ = self.sdf_query(feats, dec, pts, lod)
+        else:
+            f = self.sdf_query_blend(feats, dec, dec_hi, pts, lod_tilde)
+        f = f.reshape(Q, 6)
+        g = f[:, 0::2] - f[:, 1::2]
+        n = np.linalg.norm(g, axis=1, keepdims=True)
+        return np.where(n > 0, g / np.where(n > 0, n, 1.0), 0.0)
+
     def sphere_trace_blend(self, feats, dec_lo, dec_hi, o, d, lod_tilde: float, eps: float = 1e-3,
                            far: float = 5.0, max_steps: int = 32, osc: bool = False, alpha=None,
                            nthreads: int = 0):

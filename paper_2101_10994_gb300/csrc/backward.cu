@@ -19,6 +19,19 @@
 //   (E) optional d/dx: W1x^T dpre + J^T gz (trilinear derivative weights),
 //       added into grad_x (the launches of one call are stream-ordered).
 // Interpolation weights are recomputed, never stored.
+//
+// Deterministic mode (the same kernel, DET = true): every contribution that
+// the default mode adds with FP32 atomics -- the feature scatter of (D), the
+// per-warp dW1 rows of (C) and the per-lane db1 / dW2 / db2 sums -- is
+// converted exactly to a 128-bit two's-complement fixed-point number with
+// quantum 2^-64 and added into a device accumulator with two 64-bit integer
+// atomics (the low word's carry, read from the value the atomic returns,
+// goes into the high word).  Integer addition is associative, so the sums
+// do not depend on the order the atomics land in; a final pass rounds each
+// sum once to FP32 and adds it into the caller's gradient.  Exact for
+// contributions of magnitude >= 2^-41 (smaller ones lose the bits below
+// 2^-64); sums must stay below 2^63 in magnitude.  A non-finite
+// contribution raises a flag that turns every output of the call into NaN.
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
@@ -53,7 +66,49 @@ struct BackArgs {
     float* gW2;              // [128]
     float* gb2;              // [1]
     float* gx;               // [Q, 3] or null
+    // deterministic mode: 128-bit fixed-point accumulators (2 words each)
+    unsigned long long* fx_feat[kMaxLods];  // [C_l * 32]
+    unsigned long long* fx_W1;               // [128 * IN]
+    unsigned long long* fx_b1;               // [128]
+    unsigned long long* fx_W2;               // [128]
+    unsigned long long* fx_b2;               // [1]
+    unsigned* fx_flag;                       // non-finite contribution seen
 };
+
+// v (FP32) as a 128-bit two's-complement fixed-point number, value * 2^64
+// truncated toward zero, added into acc[0] (low word) and acc[1] (high).
+__device__ __forceinline__ void fx_add(unsigned long long* acc, float v, unsigned* flag) {
+    if (v == 0.0f) return;
+    const uint32_t b = __float_as_uint(v);
+    const int E = (int)((b >> 23) & 0xffu);
+    // value = M * 2^(max(E,1) - 150), so value * 2^64 = M << (max(E,1) - 86)
+    const int sh = (E ? E : 1) - 86;
+    if (E == 0xff || sh > 103) {  // inf / nan, or |v| >= 2^63
+        atomicOr(flag, 1u);
+        return;
+    }
+    const unsigned long long M = (b & 0x7fffffu) | (E ? 0x800000u : 0u);
+    unsigned long long lo, hi;
+    if (sh >= 64) {
+        lo = 0ull;
+        hi = M << (sh - 64);
+    } else if (sh > 0) {
+        lo = M << sh;
+        hi = M >> (64 - sh);
+    } else {
+        lo = (-sh) < 64 ? (M >> (-sh)) : 0ull;
+        hi = 0ull;
+    }
+    if (b >> 31) {  // negate: ~x + 1 over the pair
+        lo = ~lo + 1ull;
+        hi = ~hi + (lo == 0ull ? 1ull : 0ull);
+    }
+    if (lo) {
+        const unsigned long long old = atomicAdd(acc, lo);
+        hi += (old + lo < old) ? 1ull : 0ull;
+    }
+    if (hi) atomicAdd(acc + 1, hi);
+}
 
 struct BackSmem {
     SmemDecoder sd;
@@ -70,7 +125,7 @@ __device__ __forceinline__ void red_add_v4(float* addr, float4 v) {
                  : "memory");
 }
 
-template <typename T, int IN>
+template <typename T, int IN, bool DET>
 __global__ void __launch_bounds__(kThreads) k_backward(const Tables tb, const BackArgs A) {
     constexpr int OFF = IN - kFeatDim;
     constexpr int K4 = OFF ? 36 : 32;
@@ -210,8 +265,16 @@ __global__ void __launch_bounds__(kThreads) k_backward(const Tables tb, const Ba
                     accr[4 * j + 3] = fmaf(dq, a.w, accr[4 * j + 3]);
                 }
             }
+            if constexpr (DET) {
 #pragma unroll
-            for (int k = 0; k < K4; ++k) atomicAdd(&S.acc_w1[(hc + lane) * K4 + k], accr[k]);
+                for (int k = 0; k < kFeatDim + OFF; ++k) {
+                    const int col = k < kFeatDim ? OFF + k : k - kFeatDim;
+                    fx_add(A.fx_W1 + 2 * ((size_t)(hc + lane) * IN + col), accr[k], A.fx_flag);
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < K4; ++k) atomicAdd(&S.acc_w1[(hc + lane) * K4 + k], accr[k]);
+            }
             __syncwarp();
         }
         // (D) feature gradients: w_c * gz onto every level's 8 corners
@@ -249,8 +312,16 @@ __global__ void __launch_bounds__(kThreads) k_backward(const Tables tb, const Ba
 #pragma unroll
                     for (int c = 0; c < 8; ++c) {
                         const int id = __shfl_sync(gmask, cid, gbase + c);
-                        red_add_v4(gf + (size_t)id * 32 + 4 * l,
-                                   make_float4(wts[c] * gz.x, wts[c] * gz.y, wts[c] * gz.z, wts[c] * gz.w));
+                        if constexpr (DET) {
+                            unsigned long long* fa = A.fx_feat[dp2 - kFirstFeatureDepth] + 2 * ((size_t)id * 32 + 4 * l);
+                            fx_add(fa, wts[c] * gz.x, A.fx_flag);
+                            fx_add(fa + 2, wts[c] * gz.y, A.fx_flag);
+                            fx_add(fa + 4, wts[c] * gz.z, A.fx_flag);
+                            fx_add(fa + 6, wts[c] * gz.w, A.fx_flag);
+                        } else {
+                            red_add_v4(gf + (size_t)id * 32 + 4 * l,
+                                       make_float4(wts[c] * gz.x, wts[c] * gz.y, wts[c] * gz.z, wts[c] * gz.w));
+                        }
                         if (A.gx) {
                             const float4 row = FeatLoad<T>::load(fb, id, l);
                             const float pc = row.x * gz.x + row.y * gz.y + row.z * gz.z + row.w * gz.w;
@@ -297,41 +368,78 @@ __global__ void __launch_bounds__(kThreads) k_backward(const Tables tb, const Ba
         }
         __syncwarp();
     }
-    // flush: per-lane unit sums into shared, then the CTA adds once per parameter
+    if constexpr (DET) {
+        // per-lane unit sums (a fixed order of queries per lane) straight to the accumulators
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        atomicAdd(&S.acc_b1[32 * i + lane], own_b1[i]);
-        atomicAdd(&S.acc_w2[32 * i + lane], own_w2[i]);
-    }
-    {
+        for (int i = 0; i < 4; ++i) {
+            fx_add(A.fx_b1 + 2 * (32 * i + lane), own_b1[i], A.fx_flag);
+            fx_add(A.fx_W2 + 2 * (32 * i + lane), own_w2[i], A.fx_flag);
+        }
         float b2 = own_b2;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) b2 += __shfl_xor_sync(0xffffffffu, b2, o);
-        if (lane == 0) atomicAdd(&S.acc_b2, b2);
+        if (lane == 0) fx_add(A.fx_b2, b2, A.fx_flag);
+    } else {
+        // flush: per-lane unit sums into shared, then the CTA adds once per parameter
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            atomicAdd(&S.acc_b1[32 * i + lane], own_b1[i]);
+            atomicAdd(&S.acc_w2[32 * i + lane], own_w2[i]);
+        }
+        {
+            float b2 = own_b2;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) b2 += __shfl_xor_sync(0xffffffffu, b2, o);
+            if (lane == 0) atomicAdd(&S.acc_b2, b2);
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < kHidden * K4; i += blockDim.x) {
+            const int h = i / K4, k = i - h * K4;
+            int col;
+            if (k < kFeatDim) col = OFF + k;
+            else if (k < kFeatDim + OFF) col = k - kFeatDim;
+            else continue;
+            atomicAdd(&A.gW1[h * IN + col], S.acc_w1[i]);
+        }
+        for (int h = threadIdx.x; h < kHidden; h += blockDim.x) {
+            atomicAdd(&A.gb1[h], S.acc_b1[h]);
+            atomicAdd(&A.gW2[h], S.acc_w2[h]);
+        }
+        if (threadIdx.x == 0) atomicAdd(A.gb2, S.acc_b2);
     }
-    __syncthreads();
-    for (int i = threadIdx.x; i < kHidden * K4; i += blockDim.x) {
-        const int h = i / K4, k = i - h * K4;
-        int col;
-        if (k < kFeatDim) col = OFF + k;
-        else if (k < kFeatDim + OFF) col = k - kFeatDim;
-        else continue;
-        atomicAdd(&A.gW1[h * IN + col], S.acc_w1[i]);
-    }
-    for (int h = threadIdx.x; h < kHidden; h += blockDim.x) {
-        atomicAdd(&A.gb1[h], S.acc_b1[h]);
-        atomicAdd(&A.gW2[h], S.acc_w2[h]);
-    }
-    if (threadIdx.x == 0) atomicAdd(A.gb2, S.acc_b2);
 }
 
-template <typename T, int IN>
+template <typename T, int IN, bool DET>
 void launch_back(const Tables& tb, const BackArgs& A, int grid, cudaStream_t st) {
-    static bool once = (cudaFuncSetAttribute(k_backward<T, IN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    static bool once = (cudaFuncSetAttribute(k_backward<T, IN, DET>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)sizeof(BackSmem)),
                         true);
     (void)once;
-    k_backward<T, IN><<<grid, kThreads, sizeof(BackSmem), st>>>(tb, A);
+    k_backward<T, IN, DET><<<grid, kThreads, sizeof(BackSmem), st>>>(tb, A);
+}
+
+template <typename T, int IN>
+void launch_back(const Tables& tb, const BackArgs& A, int grid, bool det, cudaStream_t st) {
+    if (det) launch_back<T, IN, true>(tb, A, grid, st); else launch_back<T, IN, false>(tb, A, grid, st);
+}
+
+// out[i] += the FP32 rounding of the 128-bit fixed-point sum acc[i] * 2^-64
+// (NaN for every element if a non-finite contribution was seen).
+__global__ void k_fx_finalize(const unsigned long long* __restrict__ acc, float* __restrict__ out, long long n,
+                              const unsigned* __restrict__ flag) {
+    const bool bad = *flag != 0u;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        unsigned long long lo = acc[2 * i], hi = acc[2 * i + 1];
+        const bool neg = (hi >> 63) != 0ull;
+        if (neg) {
+            lo = ~lo + 1ull;
+            hi = ~hi + (lo == 0ull ? 1ull : 0ull);
+        }
+        // |sum| = hi + lo * 2^-64; hi < 2^63 so both conversions are in range
+        const double mag = __ull2double_rn(hi) + __ull2double_rn(lo) * 0x1p-64;
+        const float v = bad ? __int_as_float(0x7fc00000) : (float)(neg ? -mag : mag);
+        out[i] += v;
+    }
 }
 
 }  // namespace
@@ -345,7 +453,8 @@ namespace {
 int run_backward(const nglod_svo* svo, const nglod_features* feats, const nglod_decoder* decs, const float* x,
                  int64_t Q, uint32_t lod_mask, const float* grad_sdf, const float* target, float loss_scale,
                  float* loss, float* const* h_grad_feats, float* const* h_grad_W1, float* const* h_grad_b1,
-                 float* const* h_grad_W2, float* grad_b2, float* grad_x, cudaStream_t st, const char* who) {
+                 float* const* h_grad_W2, float* grad_b2, float* grad_x, bool det, cudaStream_t st,
+                 const char* who) {
     const std::string w(who);
     if (!svo || !feats || !decs) return fail(NGLOD_ERR_INVALID_ARG, w + ": NULL argument");
     if (Q < 0) return fail(NGLOD_ERR_INVALID_ARG, w + ": Q < 0");
@@ -365,6 +474,28 @@ int run_backward(const nglod_svo* svo, const nglod_features* feats, const nglod_
     for (int l = 1; l <= top; ++l)
         if (!h_grad_feats[l - 1]) return fail(NGLOD_ERR_INVALID_ARG, w + ": NULL feature gradient");
     const int grid = svo->num_sms * 2;
+    // deterministic mode: one zeroed block of fixed-point accumulators --
+    // the feature levels 1..top, then per selected LOD W1 | b1 | W2 | b2,
+    // then the flag word
+    unsigned long long* fx = nullptr;
+    size_t fx_feat_off[kMaxLods] = {}, fx_dec_off[kMaxLods] = {};
+    size_t fx_words = 0;
+    if (det) {
+        size_t n = 0;
+        for (int l = 1; l <= top; ++l) {
+            fx_feat_off[l - 1] = n;
+            n += (size_t)svo->nc[l + kFirstFeatureDepth - 1] * kFeatDim;
+        }
+        for (int lod = 1; lod <= max_lod; ++lod) {
+            if (!((lod_mask >> (lod - 1)) & 1u)) continue;
+            fx_dec_off[lod - 1] = n;
+            n += (size_t)kHidden * decs[lod - 1].in_dim + 2 * kHidden + 1;
+        }
+        fx_words = 2 * n + 2;
+        NGLOD_CUDA(cudaMallocAsync((void**)&fx, fx_words * sizeof(unsigned long long), st));
+        NGLOD_CUDA(cudaMemsetAsync(fx, 0, fx_words * sizeof(unsigned long long), st));
+    }
+    unsigned* fx_flag = det ? reinterpret_cast<unsigned*>(fx + fx_words - 2) : nullptr;
     int idx = 0;
     for (int lod = 1; lod <= max_lod; ++lod) {
         if (!((lod_mask >> (lod - 1)) & 1u)) continue;
@@ -391,15 +522,44 @@ int run_backward(const nglod_svo* svo, const nglod_features* feats, const nglod_
         A.gW2 = h_grad_W2[lod - 1];
         A.gb2 = grad_b2 + (lod - 1);
         A.gx = grad_x;
+        for (int l = 0; l < kMaxLods; ++l) A.fx_feat[l] = det && l < top ? fx + 2 * fx_feat_off[l] : nullptr;
+        if (det) {
+            A.fx_W1 = fx + 2 * fx_dec_off[lod - 1];
+            A.fx_b1 = A.fx_W1 + 2 * (size_t)kHidden * dec.in_dim;
+            A.fx_W2 = A.fx_b1 + 2 * kHidden;
+            A.fx_b2 = A.fx_W2 + 2 * kHidden;
+        } else {
+            A.fx_W1 = A.fx_b1 = A.fx_W2 = A.fx_b2 = nullptr;
+        }
+        A.fx_flag = fx_flag;
         const long long need = (Q + kThreads - 1) / kThreads;
         const int g2 = (int)std::max<long long>(1, std::min<long long>(need, grid));
         if (dec.in_dim == 35) {
-            if (f16) launch_back<__half, 35>(tb, A, g2, st); else launch_back<float, 35>(tb, A, g2, st);
+            if (f16) launch_back<__half, 35>(tb, A, g2, det, st); else launch_back<float, 35>(tb, A, g2, det, st);
         } else {
-            if (f16) launch_back<__half, 32>(tb, A, g2, st); else launch_back<float, 32>(tb, A, g2, st);
+            if (f16) launch_back<__half, 32>(tb, A, g2, det, st); else launch_back<float, 32>(tb, A, g2, det, st);
         }
         NGLOD_CUDA(cudaGetLastError());
         ++idx;
+    }
+    if (det) {
+        auto fin = [&](size_t off, float* out, long long n) {
+            const int gr = (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, (long long)grid * 8));
+            k_fx_finalize<<<gr, 256, 0, st>>>(fx + 2 * off, out, n, fx_flag);
+        };
+        for (int l = 1; l <= top; ++l)
+            fin(fx_feat_off[l - 1], h_grad_feats[l - 1], svo->nc[l + kFirstFeatureDepth - 1] * kFeatDim);
+        for (int lod = 1; lod <= max_lod; ++lod) {
+            if (!((lod_mask >> (lod - 1)) & 1u)) continue;
+            const size_t o = fx_dec_off[lod - 1];
+            const int in = decs[lod - 1].in_dim;
+            fin(o, h_grad_W1[lod - 1], (long long)kHidden * in);
+            fin(o + (size_t)kHidden * in, h_grad_b1[lod - 1], kHidden);
+            fin(o + (size_t)kHidden * in + kHidden, h_grad_W2[lod - 1], kHidden);
+            fin(o + (size_t)kHidden * in + 2 * kHidden, grad_b2 + (lod - 1), 1);
+        }
+        NGLOD_CUDA(cudaGetLastError());
+        NGLOD_CUDA(cudaFreeAsync(fx, st));
     }
     return NGLOD_OK;
 }
@@ -428,10 +588,10 @@ extern "C" int sdf_backward(const nglod_svo* svo, const nglod_features* feats, c
                             float* const* h_grad_feats, float* const* h_grad_W1, float* const* h_grad_b1,
                             float* const* h_grad_W2, float* grad_b2, float* grad_x, int deterministic,
                             void* stream) {
-    if (deterministic) return fail(NGLOD_ERR_NOT_SUPPORTED, "sdf_backward: the deterministic scatter is not built");
     if (!grad_sdf) return fail(NGLOD_ERR_INVALID_ARG, "sdf_backward: NULL grad_sdf");
     return run_backward(svo, feats, decs, x, Q, lod_mask, grad_sdf, nullptr, 0.f, nullptr, h_grad_feats, h_grad_W1,
-                        h_grad_b1, h_grad_W2, grad_b2, grad_x, (cudaStream_t)stream, "sdf_backward");
+                        h_grad_b1, h_grad_W2, grad_b2, grad_x, deterministic != 0, (cudaStream_t)stream,
+                        "sdf_backward");
 }
 
 extern "C" int sdf_l2_backward(const nglod_svo* svo, const nglod_features* feats, const nglod_decoder* decs,
@@ -440,7 +600,7 @@ extern "C" int sdf_l2_backward(const nglod_svo* svo, const nglod_features* feats
                                float* const* h_grad_b1, float* const* h_grad_W2, float* grad_b2, void* stream) {
     if (!target) return fail(NGLOD_ERR_INVALID_ARG, "sdf_l2_backward: NULL target");
     return run_backward(svo, feats, decs, x, Q, lod_mask, nullptr, target, loss_scale, loss, h_grad_feats, h_grad_W1,
-                        h_grad_b1, h_grad_W2, grad_b2, nullptr, (cudaStream_t)stream, "sdf_l2_backward");
+                        h_grad_b1, h_grad_W2, grad_b2, nullptr, false, (cudaStream_t)stream, "sdf_l2_backward");
 }
 
 extern "C" int nglod_adam_step(float* param, float* grad, float* m, float* v, int64_t n, float lr, float beta1,

@@ -24,6 +24,8 @@
 
 struct nglod_batch {
     int njobs = 0, ngroups = 0, decode = NGLOD_F32, in_dim = 32, ctas_per_sm = 0, want_normals = 0;
+    int normal_mode = NGLOD_NORMALS_ANALYTIC;
+    float fd_h = 0.f;
     bool f16 = false;
     float fp8_z = 0.f;
     nglod::TraceJob* d_jobs = nullptr;
@@ -70,11 +72,14 @@ extern "C" int sphere_trace_batch_create(const nglod_trace_job* jobs, int num_jo
     const int dec_t = params->decode_dtype;
     if (dec_t != NGLOD_F32 && dec_t != NGLOD_BF16 && dec_t != NGLOD_FP8E4M3)
         return fail(NGLOD_ERR_NOT_SUPPORTED, "sphere_trace_batch_create: decode_dtype");
+    if (int e = check_normal_params(params, "sphere_trace_batch_create")) return e;
     nglod_batch* b = new (std::nothrow) nglod_batch();
     if (!b) return fail(NGLOD_ERR_OOM, "sphere_trace_batch_create: host allocation failed");
     b->decode = dec_t;
     b->ctas_per_sm = ctas_per_sm;
     b->want_normals = params->want_normals;
+    b->normal_mode = params->normal_mode;
+    b->fd_h = params->fd_h;
     b->sms = device_sms();
     // group jobs by decoder (W1 pointer), keeping first-seen order
     std::map<const float*, int> gid;
@@ -210,7 +215,11 @@ extern "C" int sphere_trace_batch_run(nglod_batch* b, void* stream) {
     if (b->want_normals) {
         for (int j = 0; j < b->njobs; ++j) {
             if (!b->normals[j] || b->h_jobs[j].A.R == 0) continue;
-            rc = launch_normals(&b->h_decs[j], b->h_jobs[j].tb, b->h_jobs[j].A, b->normals[j], b->f16, b->sms, st);
+            rc = b->normal_mode == NGLOD_NORMALS_FD
+                     ? launch_normals_fd(&b->h_decs[j], b->h_jobs[j].tb, b->h_jobs[j].A, b->fd_h, b->normals[j],
+                                         b->f16, b->sms, st)
+                     : launch_normals(&b->h_decs[j], b->h_jobs[j].tb, b->h_jobs[j].A, b->normals[j], b->f16,
+                                      b->sms, st);
             if (rc) return rc;
         }
     }

@@ -87,6 +87,7 @@ extern "C" int sphere_trace_blend(const nglod_svo* svo, const nglod_features* fe
     if (R < 0 || R >= (1ll << 31) - 64) return fail(NGLOD_ERR_INVALID_ARG, "sphere_trace_blend: bad R");
     if (!(params->eps > 0.0f) || !(params->far_t > 0.0f) || params->max_steps < 1)
         return fail(NGLOD_ERR_INVALID_ARG, "sphere_trace_blend: eps, far_t and max_steps must be positive");
+    if ((rc = check_normal_params(params, "sphere_trace_blend"))) return rc;
     if (R == 0) return NGLOD_OK;
     if (!o || !d || !ray_offsets || !t_hit || !hit || !work)
         return fail(NGLOD_ERR_INVALID_ARG, "sphere_trace_blend: NULL argument");
@@ -125,7 +126,9 @@ extern "C" int sphere_trace_blend(const nglod_svo* svo, const nglod_features* fe
     else
         return fail(NGLOD_ERR_NOT_SUPPORTED, "sphere_trace_blend: decode_dtype must be F32 or BF16 when blending");
     if (rc) return rc;
-    if (normal && params->want_normals) return launch_normals_blend(dec_lo, dec_hi, alpha, tb, A, normal, f16,
-                                                                    svo->num_sms, st);
+    if (normal && params->want_normals)
+        return params->normal_mode == NGLOD_NORMALS_FD
+                   ? launch_normals_blend_fd(dec_lo, dec_hi, alpha, tb, A, params->fd_h, normal, f16, svo->num_sms, st)
+                   : launch_normals_blend(dec_lo, dec_hi, alpha, tb, A, normal, f16, svo->num_sms, st);
     return NGLOD_OK;
 }

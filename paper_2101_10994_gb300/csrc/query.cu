@@ -62,10 +62,63 @@ struct DecPtrs {
     float b2;
 };
 
-template <typename T, int IN>
+// Finite-difference normals (supplementary Sec. A.4 takes the normals by
+// finite differences): at each hit point x = o + t d the SDF is evaluated at
+// x + h e_a and x - h e_a (a = 0..2, FP32 coordinates), exactly as sdf_query
+// evaluates a point, and n = normalise(d(x + h e_a) - d(x - h e_a))_a.  A
+// warp holds 5 hit rays x 6 points in lanes 0..29 (lane 6 i + 2 a + s: ray
+// i, axis a, sign s) and forms the normals with shuffles.
+struct FDArgs {
+    const float* o;
+    const float* d;
+    const float* t_hit;
+    const int* hit_count;     // device: number of entries in hit_list
+    const int32_t* hit_list;  // ray ids of the hits
+    float h;
+    float* normal;            // [R, 3], indexed by ray
+};
+
+constexpr int kFDRaysPerWarp = 5;
+
+__device__ __forceinline__ bool fd_point(const FDArgs& F, long long c, int lane, long long nh, float& x0,
+                                         float& x1, float& x2, int& ray) {
+    const long long i = c * kFDRaysPerWarp + lane / 6;
+    if (lane >= 6 * kFDRaysPerWarp || i >= nh) return false;
+    ray = F.hit_list[i];
+    const float t = F.t_hit[ray];
+    x0 = fmaf(t, F.d[3 * ray], F.o[3 * ray]);
+    x1 = fmaf(t, F.d[3 * ray + 1], F.o[3 * ray + 1]);
+    x2 = fmaf(t, F.d[3 * ray + 2], F.o[3 * ray + 2]);
+    const int k = lane % 6;
+    const float dh = (k & 1) ? -F.h : F.h;
+    if (k < 2) x0 = __fadd_rn(x0, dh);
+    else if (k < 4) x1 = __fadd_rn(x1, dh);
+    else x2 = __fadd_rn(x2, dh);
+    return true;
+}
+
+__device__ __forceinline__ void fd_write(const FDArgs& F, int lane, bool act, int ray, float f) {
+    const int b = min(lane / 6, kFDRaysPerWarp - 1) * 6;
+    float g[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+        g[a] = __fsub_rn(__shfl_sync(0xffffffffu, f, b + 2 * a), __shfl_sync(0xffffffffu, f, b + 2 * a + 1));
+    if (act && lane % 6 == 0) {
+        const float nn = sqrtf(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+        const float inv = nn > 0.f ? 1.0f / nn : 0.f;
+        F.normal[3 * (size_t)ray] = g[0] * inv;
+        F.normal[3 * (size_t)ray + 1] = g[1] * inv;
+        F.normal[3 * (size_t)ray + 2] = g[2] * inv;
+    }
+}
+
+// FD = false: Q points from x.  FD = true: the points of fd_point (Q, x,
+// sdf, deepest unused) and the normals of fd_write.
+template <typename T, int IN, bool FD>
 __global__ void __launch_bounds__(kThreads) k_sdf_query(const DecPtrs dp, const Tables tb,
                                                         const float* __restrict__ x, long long Q, int D,
-                                                        float* __restrict__ sdf, int8_t* __restrict__ deepest) {
+                                                        float* __restrict__ sdf, int8_t* __restrict__ deepest,
+                                                        const FDArgs F) {
     __shared__ __align__(16) float zbuf[kWarps][32 * kZStride];
     __shared__ __align__(16) SmemDecoder sd;
     stage_decoder<IN>(sd, dp.W1, dp.b1, dp.W2);
@@ -74,15 +127,22 @@ __global__ void __launch_bounds__(kThreads) k_sdf_query(const DecPtrs dp, const 
     const int g4 = lane >> 2, l4 = lane & 3, gb4 = g4 << 2;
     const unsigned gm4 = 0xfu << gb4;
     float* zb = zbuf[warp];
-    for (long long base = ((long long)blockIdx.x * kWarps + warp) * 32; base < Q;
-         base += (long long)gridDim.x * kWarps * 32) {
-        const long long qi = base + lane;
-        const bool act = qi < Q;
+    const long long nh = FD ? (long long)*F.hit_count : 0;
+    const long long nchunks = FD ? (nh + kFDRaysPerWarp - 1) / kFDRaysPerWarp : (Q + 31) / 32;
+    for (long long c = (long long)blockIdx.x * kWarps + warp; c < nchunks; c += (long long)gridDim.x * kWarps) {
+        const long long qi = c * 32 + lane;
         float x0 = 0.f, x1 = 0.f, x2 = 0.f;
-        if (act) {
-            x0 = x[3 * qi];
-            x1 = x[3 * qi + 1];
-            x2 = x[3 * qi + 2];
+        int ray = -1;
+        bool act;
+        if constexpr (FD) {
+            act = fd_point(F, c, lane, nh, x0, x1, x2, ray);
+        } else {
+            act = qi < Q;
+            if (act) {
+                x0 = x[3 * qi];
+                x1 = x[3 * qi + 1];
+                x2 = x[3 * qi + 2];
+            }
         }
         int vox;
         uint32_t ijk;
@@ -105,7 +165,9 @@ __global__ void __launch_bounds__(kThreads) k_sdf_query(const DecPtrs dp, const 
         }
         __syncwarp();
         const float out = mlp_f32<IN>(sd, dp.b2, zb + lane * kZStride, x0, x1, x2);
-        if (act) {
+        if constexpr (FD) {
+            fd_write(F, lane, act, ray, out);
+        } else if (act) {
             sdf[qi] = out;
             if (deepest) deepest[qi] = (int8_t)(dd >= kFirstFeatureDepth ? dd - kFirstFeatureDepth + 1 : 0);
         }
@@ -442,7 +504,12 @@ void launch_trace_f32(const DecPtrs& P, const Tables& tb, const TraceArgs& A, in
 template <typename T, int IN>
 void launch_query(const DecPtrs& P, const Tables& tb, const float* x, long long Q, int D, float* sdf,
                   int8_t* deepest, int grid, cudaStream_t st) {
-    k_sdf_query<T, IN><<<grid, kThreads, 0, st>>>(P, tb, x, Q, D, sdf, deepest);
+    k_sdf_query<T, IN, false><<<grid, kThreads, 0, st>>>(P, tb, x, Q, D, sdf, deepest, FDArgs{});
+}
+
+template <typename T, int IN>
+void launch_fd(const DecPtrs& P, const Tables& tb, int D, const FDArgs& F, int grid, cudaStream_t st) {
+    k_sdf_query<T, IN, true><<<grid, kThreads, 0, st>>>(P, tb, nullptr, 0, D, nullptr, nullptr, F);
 }
 
 template <typename T, int IN>
@@ -537,10 +604,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_trace_blend_f32(const DecPtrs l
     }
 }
 
-template <typename T, int IN>
+template <typename T, int IN, bool FD>
 __global__ void __launch_bounds__(kThreads, 2) k_query_blend_f32(const DecPtrs lo, const DecPtrs hi, float alpha,
                                                                   const Tables tb, const float* __restrict__ x,
-                                                                  long long Q, int D, float* __restrict__ sdf) {
+                                                                  long long Q, int D, float* __restrict__ sdf,
+                                                                  const FDArgs F) {
     extern __shared__ __align__(16) unsigned char blend_smem[];
     SmemDecoder& slo = *reinterpret_cast<SmemDecoder*>(blend_smem);
     SmemDecoder& shi = *reinterpret_cast<SmemDecoder*>(blend_smem + sizeof(SmemDecoder));
@@ -551,15 +619,22 @@ __global__ void __launch_bounds__(kThreads, 2) k_query_blend_f32(const DecPtrs l
     const int g4 = lane >> 2, l4 = lane & 3, gb4 = g4 << 2;
     const unsigned gm4 = 0xfu << gb4;
     float* zb = reinterpret_cast<float*>(blend_smem + 2 * sizeof(SmemDecoder)) + warp * 32 * kZStride;
-    for (long long base = ((long long)blockIdx.x * kWarps + warp) * 32; base < Q;
-         base += (long long)gridDim.x * kWarps * 32) {
-        const long long qi = base + lane;
-        const bool act = qi < Q;
+    const long long nh = FD ? (long long)*F.hit_count : 0;
+    const long long nchunks = FD ? (nh + kFDRaysPerWarp - 1) / kFDRaysPerWarp : (Q + 31) / 32;
+    for (long long c = (long long)blockIdx.x * kWarps + warp; c < nchunks; c += (long long)gridDim.x * kWarps) {
+        const long long qi = c * 32 + lane;
         float x0 = 0.f, x1 = 0.f, x2 = 0.f;
-        if (act) {
-            x0 = x[3 * qi];
-            x1 = x[3 * qi + 1];
-            x2 = x[3 * qi + 2];
+        int ray = -1;
+        bool act;
+        if constexpr (FD) {
+            act = fd_point(F, c, lane, nh, x0, x1, x2, ray);
+        } else {
+            act = qi < Q;
+            if (act) {
+                x0 = x[3 * qi];
+                x1 = x[3 * qi + 1];
+                x2 = x[3 * qi + 2];
+            }
         }
         int vox;
         uint32_t ijk;
@@ -599,7 +674,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_query_blend_f32(const DecPtrs l
             else dlo = dv;
             __syncwarp();
         }
-        if (act) sdf[qi] = fmaf(alpha, dhi - dlo, dlo);
+        const float db = fmaf(alpha, dhi - dlo, dlo);
+        if constexpr (FD) fd_write(F, lane, act, ray, db);
+        else if (act) sdf[qi] = db;
     }
 }
 
@@ -610,28 +687,47 @@ void allow_blend_smem(K kernel) {
 
 template <typename T, int IN>
 void go_blend_f32(bool trace, const DecPtrs& lo, const DecPtrs& hi, float alpha, const Tables& tb,
-                  const TraceArgs* A, const float* x, long long Q, int D, float* sdf, int grid, cudaStream_t st) {
+                  const TraceArgs* A, const float* x, long long Q, int D, float* sdf, const FDArgs* F, int grid,
+                  cudaStream_t st) {
     if (trace) {
         static bool once = (allow_blend_smem(k_trace_blend_f32<T, IN>), true);
         (void)once;
         k_trace_blend_f32<T, IN><<<grid, kThreads, kBlendF32Smem, st>>>(lo, hi, alpha, tb, *A);
-    } else {
-        static bool once = (allow_blend_smem(k_query_blend_f32<T, IN>), true);
+    } else if (F) {
+        static bool once = (allow_blend_smem(k_query_blend_f32<T, IN, true>), true);
         (void)once;
-        k_query_blend_f32<T, IN><<<grid, kThreads, kBlendF32Smem, st>>>(lo, hi, alpha, tb, x, Q, D, sdf);
+        k_query_blend_f32<T, IN, true><<<grid, kThreads, kBlendF32Smem, st>>>(lo, hi, alpha, tb, nullptr, 0, D,
+                                                                                nullptr, *F);
+    } else {
+        static bool once = (allow_blend_smem(k_query_blend_f32<T, IN, false>), true);
+        (void)once;
+        k_query_blend_f32<T, IN, false><<<grid, kThreads, kBlendF32Smem, st>>>(lo, hi, alpha, tb, x, Q, D, sdf,
+                                                                                 FDArgs{});
     }
 }
 
 void go_blend_f32_any(bool trace, int in_dim, bool f16, const DecPtrs& lo, const DecPtrs& hi, float alpha,
                       const Tables& tb, const TraceArgs* A, const float* x, long long Q, int D, float* sdf,
-                      int grid, cudaStream_t st) {
+                      int grid, cudaStream_t st, const FDArgs* F = nullptr) {
     if (in_dim == 35) {
-        if (f16) go_blend_f32<__half, 35>(trace, lo, hi, alpha, tb, A, x, Q, D, sdf, grid, st);
-        else go_blend_f32<float, 35>(trace, lo, hi, alpha, tb, A, x, Q, D, sdf, grid, st);
+        if (f16) go_blend_f32<__half, 35>(trace, lo, hi, alpha, tb, A, x, Q, D, sdf, F, grid, st);
+        else go_blend_f32<float, 35>(trace, lo, hi, alpha, tb, A, x, Q, D, sdf, F, grid, st);
     } else {
-        if (f16) go_blend_f32<__half, 32>(trace, lo, hi, alpha, tb, A, x, Q, D, sdf, grid, st);
-        else go_blend_f32<float, 32>(trace, lo, hi, alpha, tb, A, x, Q, D, sdf, grid, st);
+        if (f16) go_blend_f32<__half, 32>(trace, lo, hi, alpha, tb, A, x, Q, D, sdf, F, grid, st);
+        else go_blend_f32<float, 32>(trace, lo, hi, alpha, tb, A, x, Q, D, sdf, F, grid, st);
     }
+}
+
+FDArgs fd_args(const TraceArgs& A, float h, float* normal) {
+    FDArgs F;
+    F.o = A.o;
+    F.d = A.d;
+    F.t_hit = A.t_hit;
+    F.hit_count = A.hit_count;
+    F.hit_list = A.hit_list;
+    F.h = h;
+    F.normal = normal;
+    return F;
 }
 
 // Normalises the accumulated blended gradients of the hit rays.
@@ -693,6 +789,39 @@ int launch_normals(const nglod_decoder* dec, const Tables& tb, const TraceArgs& 
     G.mode = 1;
     G.out = normal;
     return run_grad(dec, tb, G, f16, sms, st);
+}
+
+int check_normal_params(const nglod_trace_params* params, const char* who) {
+    if (params->normal_mode != NGLOD_NORMALS_ANALYTIC && params->normal_mode != NGLOD_NORMALS_FD)
+        return fail(NGLOD_ERR_INVALID_ARG, std::string(who) + ": normal_mode must be ANALYTIC or FD");
+    if (params->normal_mode == NGLOD_NORMALS_FD && !(params->fd_h > 0.0f && params->fd_h < 1.0f))
+        return fail(NGLOD_ERR_INVALID_ARG, std::string(who) + ": fd_h must lie in (0, 1)");
+    return NGLOD_OK;
+}
+
+int launch_normals_fd(const nglod_decoder* dec, const Tables& tb, const TraceArgs& A, float h, float* normal,
+                      bool f16, int sms, cudaStream_t st) {
+    NGLOD_CUDA(cudaMemsetAsync(normal, 0, sizeof(float) * 3 * (size_t)A.R, st));
+    const FDArgs F = fd_args(A, h, normal);
+    const int grid = grid_items((A.R + kFDRaysPerWarp - 1) / kFDRaysPerWarp * 32, kThreads, sms, 2);
+    const DecPtrs P = dec_ptrs(dec);
+    if (dec->in_dim == 35) {
+        if (f16) launch_fd<__half, 35>(P, tb, A.D, F, grid, st); else launch_fd<float, 35>(P, tb, A.D, F, grid, st);
+    } else {
+        if (f16) launch_fd<__half, 32>(P, tb, A.D, F, grid, st); else launch_fd<float, 32>(P, tb, A.D, F, grid, st);
+    }
+    NGLOD_CUDA(cudaGetLastError());
+    return NGLOD_OK;
+}
+
+int launch_normals_blend_fd(const nglod_decoder* lo, const nglod_decoder* hi, float alpha, const Tables& tb,
+                            const TraceArgs& A, float h, float* normal, bool f16, int sms, cudaStream_t st) {
+    NGLOD_CUDA(cudaMemsetAsync(normal, 0, sizeof(float) * 3 * (size_t)A.R, st));
+    const FDArgs F = fd_args(A, h, normal);
+    go_blend_f32_any(false, lo->in_dim, f16, dec_ptrs(lo), dec_ptrs(hi), alpha, tb, nullptr, nullptr, 0, A.D,
+                     nullptr, grid_items((A.R + kFDRaysPerWarp - 1) / kFDRaysPerWarp * 32, kThreads, sms, 2), st, &F);
+    NGLOD_CUDA(cudaGetLastError());
+    return NGLOD_OK;
 }
 
 int launch_trace_blend_f32(const nglod_decoder* lo, const nglod_decoder* hi, float alpha, const Tables& tb,
@@ -813,6 +942,7 @@ extern "C" int sphere_trace(const nglod_svo* svo, const nglod_features* feats, c
     if (R < 0 || R >= (1ll << 31) - 64) return fail(NGLOD_ERR_INVALID_ARG, "sphere_trace: bad R");
     if (!(params->eps > 0.0f) || !(params->far_t > 0.0f) || params->max_steps < 1)
         return fail(NGLOD_ERR_INVALID_ARG, "sphere_trace: eps, far_t and max_steps must be positive");
+    if (int e = check_normal_params(params, "sphere_trace")) return e;
     if (R == 0) return NGLOD_OK;
     if (!o || !d || !ray_offsets || !t_hit || !hit || !work)
         return fail(NGLOD_ERR_INVALID_ARG, "sphere_trace: NULL argument");
@@ -858,18 +988,22 @@ extern "C" int sphere_trace(const nglod_svo* svo, const nglod_features* feats, c
     }
     if (rc) return rc;
     if (normal && params->want_normals) {
-        rc = launch_normals(dec, tb, A, normal, f16, svo->num_sms, st);
+        rc = params->normal_mode == NGLOD_NORMALS_FD
+                 ? launch_normals_fd(dec, tb, A, params->fd_h, normal, f16, svo->num_sms, st)
+                 : launch_normals(dec, tb, A, normal, f16, svo->num_sms, st);
         if (rc) return rc;
     }
     return NGLOD_OK;
 }
 
-extern "C" int trace_normals(const nglod_svo* svo, const nglod_features* feats, const nglod_decoder* dec,
-                             const float* o, const float* d, int64_t R, int lod, const void* work,
-                             size_t work_bytes, const float* t_hit, const uint8_t* hit, float* normal,
-                             void* stream) {
+namespace {
+int normals_common(const nglod_svo* svo, const nglod_features* feats, const nglod_decoder* dec, const float* o,
+                   const float* d, int64_t R, int lod, const void* work, size_t work_bytes, const float* t_hit,
+                   const uint8_t* hit, float* normal, float fd_h, void* stream) {
     cudaStream_t st = (cudaStream_t)stream;
     if (!svo) return fail(NGLOD_ERR_INVALID_ARG, "trace_normals: NULL octree");
+    if (fd_h != 0.0f && !(fd_h > 0.0f && fd_h < 1.0f))
+        return fail(NGLOD_ERR_INVALID_ARG, "trace_normals_fd: fd_h must lie in (0, 1)");
     const int D = lod + kFirstFeatureDepth - 1;
     if (lod < 1 || D >= svo->num_depths) return fail(NGLOD_ERR_INVALID_ARG, "trace_normals: lod out of range");
     if (R < 0) return fail(NGLOD_ERR_INVALID_ARG, "trace_normals: bad R");
@@ -892,7 +1026,26 @@ extern "C" int trace_normals(const nglod_svo* svo, const nglod_features* feats, 
     A.hit_count = (int*)const_cast<void*>(work) + 2;
     A.hit_vox = (int32_t*)((char*)work + trace_ws_hit_vox_offset());
     A.hit_list = (int32_t*)((char*)work + trace_ws_hit_list_offset(R));
-    return launch_normals(dec, tb, A, normal, feats->dtype == NGLOD_F16, svo->num_sms, st);
+    const bool f16 = feats->dtype == NGLOD_F16;
+    return fd_h > 0.0f ? launch_normals_fd(dec, tb, A, fd_h, normal, f16, svo->num_sms, st)
+                       : launch_normals(dec, tb, A, normal, f16, svo->num_sms, st);
+}
+}  // namespace
+
+extern "C" int trace_normals(const nglod_svo* svo, const nglod_features* feats, const nglod_decoder* dec,
+                             const float* o, const float* d, int64_t R, int lod, const void* work,
+                             size_t work_bytes, const float* t_hit, const uint8_t* hit, float* normal,
+                             void* stream) {
+    return normals_common(svo, feats, dec, o, d, R, lod, work, work_bytes, t_hit, hit, normal, 0.0f, stream);
+}
+
+extern "C" int trace_normals_fd(const nglod_svo* svo, const nglod_features* feats, const nglod_decoder* dec,
+                                const float* o, const float* d, int64_t R, int lod, const void* work,
+                                size_t work_bytes, const float* t_hit, const uint8_t* hit, float fd_h,
+                                float* normal, void* stream) {
+    if (!(fd_h > 0.0f && fd_h < 1.0f))
+        return fail(NGLOD_ERR_INVALID_ARG, "trace_normals_fd: fd_h must lie in (0, 1)");
+    return normals_common(svo, feats, dec, o, d, R, lod, work, work_bytes, t_hit, hit, normal, fd_h, stream);
 }
 
 extern "C" int sphere_trace_status(const void* work, void* stream) {

@@ -307,6 +307,12 @@ int launch_trace_fp32(const nglod_decoder* dec, const Tables& tb, const TraceArg
                       cudaStream_t st);
 int launch_normals(const nglod_decoder* dec, const Tables& tb, const TraceArgs& A, float* normal, bool f16,
                    int sms, cudaStream_t st);
+// Central-difference normals of the hit rays (step h), plain and blended.
+int launch_normals_fd(const nglod_decoder* dec, const Tables& tb, const TraceArgs& A, float h, float* normal,
+                      bool f16, int sms, cudaStream_t st);
+int launch_normals_blend_fd(const nglod_decoder* lo, const nglod_decoder* hi, float alpha, const Tables& tb,
+                            const TraceArgs& A, float h, float* normal, bool f16, int sms, cudaStream_t st);
+int check_normal_params(const nglod_trace_params* params, const char* who);
 // Workspace layout of sphere_trace: [0, 256) header {queue, status, hit
 // count}, then int32 hit voxel per ray, then int32 hit list.
 inline size_t trace_ws_hit_vox_offset() { return 256; }

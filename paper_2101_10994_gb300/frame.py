@@ -21,7 +21,8 @@ from . import nglod as ng
 class FrameRenderer:
     def __init__(self, svo: ng.SVO, feats: ng.Features, dec: ng.DecoderDev, o, d, lod, chunks: int = 2,
                  eps: float = 1e-3, far: float = 5.0, max_steps: int = 128, decode: str = "bf16",
-                 normals: bool = True, headroom: float = 1.25, dec_hi: ng.DecoderDev | None = None):
+                 normals: bool = True, headroom: float = 1.25, dec_hi: ng.DecoderDev | None = None,
+                 normal_mode: str = "analytic", fd_h: float = 1e-3):
         """lod: an integer LOD, or a continuous L~ (Eq. 3) with dec = LOD floor(L~)'s decoder and
         dec_hi = LOD floor(L~) + 1's; rays then walk their lists at ceil(L~)."""
         import torch
@@ -36,6 +37,7 @@ class FrameRenderer:
         self.o, self.d = o.contiguous(), d.contiguous()
         self.R = R = int(self.o.shape[0])
         self.eps, self.far, self.max_steps, self.decode, self.normals = eps, far, max_steps, decode, normals
+        self.nopt = dict(normal_mode=normal_mode, fd_h=fd_h)
         dev = self.o.device
         # chunk bounds on multiples of 128 rays (the traversal's tile)
         n = max(1, int(chunks))
@@ -76,11 +78,11 @@ class FrameRenderer:
         if self.blend:
             ng.sphere_trace_blend(self.svo, self.feats, self.dec, self.dec_hi, oo, dd, c["lists"], self.lod_tilde,
                                   eps=self.eps, far=self.far, max_steps=self.max_steps, decode=self.decode,
-                                  normals=self.normals, stream=st, out=c["outs"])
+                                  normals=self.normals, stream=st, out=c["outs"], **self.nopt)
         else:
             ng.sphere_trace(self.svo, self.feats, self.dec, oo, dd, c["lists"], eps=self.eps, far=self.far,
                             max_steps=self.max_steps, decode=self.decode, normals=self.normals, stream=st,
-                            out=c["outs"])
+                            out=c["outs"], **self.nopt)
 
     def frame(self, h_in=None, h_out=None):
         """Enqueues one frame after the work already on the current stream,

@@ -27,7 +27,8 @@ EXPORTS = ["nglod_last_error", "svo_build", "svo_info", "svo_device_arrays", "sv
            "svo_trace_rays_sizes", "sdf_backward", "sdf_l2_backward", "nglod_adam_step",
            "nglod_features_absmax", "svo_trace_rays_async", "svo_trace_rays_check",
            "sphere_trace_batch_create", "sphere_trace_batch_run", "sphere_trace_batch_status",
-           "sphere_trace_batch_free", "sdf_query_blend", "sphere_trace_blend", "nglod_lod_select"]
+           "sphere_trace_batch_free", "sdf_query_blend", "sphere_trace_blend", "nglod_lod_select",
+           "trace_normals_fd"]
 
 
 class NglodError(RuntimeError):
@@ -55,7 +56,10 @@ class _TraceJob(C.Structure):
 
 class _TraceParams(C.Structure):
     _fields_ = [("eps", C.c_float), ("far_t", C.c_float), ("max_steps", C.c_int), ("osc_check", C.c_int),
-                ("decode_dtype", C.c_int), ("want_normals", C.c_int)]
+                ("decode_dtype", C.c_int), ("want_normals", C.c_int), ("normal_mode", C.c_int),
+                ("fd_h", C.c_float)]
+
+NORMALS = {"analytic": 0, "fd": 1}
 
 
 _lib = None
@@ -85,6 +89,7 @@ def lib():
         L.sphere_trace_workspace.argtypes = [i64]
         L.sphere_trace.argtypes = [P, P, P, P, P, i64, i32, P, P, P, P, P, sz, P, P, P, P, P]
         L.trace_normals.argtypes = [P, P, P, P, P, i64, i32, P, sz, P, P, P, P]
+        L.trace_normals_fd.argtypes = [P, P, P, P, P, i64, i32, P, sz, P, P, C.c_float, P, P]
         L.sphere_trace_status.argtypes = [P, P]
         L.svo_trace_rays_sizes.argtypes = [P, P, i32, P]
         L.sdf_backward.argtypes = [P, P, P, P, i64, C.c_uint32, P, P, P, P, P, P, P, i32, P]
@@ -195,6 +200,17 @@ class Features:
         self.m = int(self.tables[0].shape[1])
         self.z_absmax = 0.0
 
+    @classmethod
+    def from_tensors(cls, tables):
+        """A view on existing device tensors (FP32 or FP16 [C_l, 32], no copy)."""
+        import torch
+        f = cls.__new__(cls)
+        f.tables = [t.contiguous() for t in tables]
+        f.dtype = "f16" if f.tables[0].dtype == torch.float16 else "f32"
+        f.m = int(f.tables[0].shape[1])
+        f.z_absmax = 0.0
+        return f
+
     def set_fp8_bound(self, svo, lod: int, stream=None):
         """Computes the |z| bound the FP8 decode scales by (library reduction)."""
         out = C.c_float(0.0)
@@ -232,6 +248,15 @@ class DecoderDev:
     @classmethod
     def from_decoder(cls, dec, device="cuda"):
         return cls(dec.W1, dec.b1, dec.W2, dec.b2, device)
+
+    @classmethod
+    def from_tensors(cls, W1, b1, W2, b2: float):
+        """A view on existing FP32 device tensors (no copy)."""
+        d = cls.__new__(cls)
+        d.W1, d.b1, d.W2 = W1.contiguous(), b1.contiguous(), W2.contiguous()
+        d.b2 = float(b2)
+        d.in_dim, d.hidden = int(W1.shape[1]), int(W1.shape[0])
+        return d
 
     def c(self) -> _Decoder:
         d = _Decoder()
@@ -322,8 +347,11 @@ def sdf_query(svo: SVO, feats: Features, dec: DecoderDev, x, lod: int, decode: s
 
 def sphere_trace(svo: SVO, feats: Features, dec: DecoderDev, o, d, lists: RayLists, eps: float = 1e-3,
                  far: float = 5.0, max_steps: int = 128, osc: bool = False, decode: str = "f32",
-                 normals: bool = True, stream=None, out=None):
-    """Sphere-traces every ray through its voxel list; returns a dict of tensors."""
+                 normals: bool = True, stream=None, out=None, normal_mode: str = "analytic", fd_h: float = 1e-3):
+    """Sphere-traces every ray through its voxel list; returns a dict of tensors.
+
+    normal_mode "analytic" (gradient of the decoded SDF) or "fd" (central
+    differences with step fd_h, supplementary Sec. A.4)."""
     import torch
     _require_cuda(o, d)
     R = int(o.shape[0])
@@ -334,7 +362,8 @@ def sphere_trace(svo: SVO, feats: Features, dec: DecoderDev, o, d, lists: RayLis
                    steps=torch.empty(R, dtype=torch.int32, device=dev),
                    normal=torch.empty((R, 3), dtype=torch.float32, device=dev) if normals else None,
                    work=torch.empty(max(lib().sphere_trace_workspace(R), 1), dtype=torch.uint8, device=dev))
-    p = _TraceParams(eps, far, max_steps, int(osc), {"f32": F32, "bf16": BF16, "fp8": FP8}[decode], int(normals))
+    p = _TraceParams(eps, far, max_steps, int(osc), {"f32": F32, "bf16": BF16, "fp8": FP8}[decode], int(normals),
+                     NORMALS[normal_mode], fd_h)
     fc, dc = feats.c(), dec.c()
     _check(lib().sphere_trace(svo.h, C.byref(fc), C.byref(dc), o.data_ptr(), d.data_ptr(), R, lists.lod,
                               C.byref(p), lists.ray_offsets.data_ptr(), lists.voxel_id.data_ptr(),
@@ -345,16 +374,20 @@ def sphere_trace(svo: SVO, feats: Features, dec: DecoderDev, o, d, lists: RayLis
     return out
 
 
-def trace_normals(svo: SVO, feats: Features, dec: DecoderDev, o, d, lists: RayLists, out, stream=None):
+def trace_normals(svo: SVO, feats: Features, dec: DecoderDev, o, d, lists: RayLists, out, stream=None,
+                  normal_mode: str = "analytic", fd_h: float = 1e-3):
     """Normals of the hits of the preceding sphere_trace call that filled ``out``."""
     R = int(o.shape[0])
     if out.get("normal") is None:
         import torch
         out["normal"] = torch.empty((R, 3), dtype=torch.float32, device=o.device)
     fc, dc = feats.c(), dec.c()
-    _check(lib().trace_normals(svo.h, C.byref(fc), C.byref(dc), o.data_ptr(), d.data_ptr(), R, lists.lod,
-                               out["work"].data_ptr(), out["work"].numel(), out["t"].data_ptr(),
-                               out["hit"].data_ptr(), out["normal"].data_ptr(), C.c_void_p(_stream(stream))))
+    args = (svo.h, C.byref(fc), C.byref(dc), o.data_ptr(), d.data_ptr(), R, lists.lod, out["work"].data_ptr(),
+            out["work"].numel(), out["t"].data_ptr(), out["hit"].data_ptr())
+    if NORMALS[normal_mode]:
+        _check(lib().trace_normals_fd(*args, fd_h, out["normal"].data_ptr(), C.c_void_p(_stream(stream))))
+    else:
+        _check(lib().trace_normals(*args, out["normal"].data_ptr(), C.c_void_p(_stream(stream))))
     return out
 
 
@@ -394,7 +427,8 @@ def sdf_query_blend(svo: SVO, feats: Features, dec_lo: DecoderDev, dec_hi: Decod
 
 def sphere_trace_blend(svo: SVO, feats: Features, dec_lo: DecoderDev, dec_hi: DecoderDev | None, o, d,
                        lists: RayLists, lod_tilde: float, eps: float = 1e-3, far: float = 5.0, max_steps: int = 128,
-                       osc: bool = False, decode: str = "f32", normals: bool = True, stream=None, out=None):
+                       osc: bool = False, decode: str = "f32", normals: bool = True, stream=None, out=None,
+                       normal_mode: str = "analytic", fd_h: float = 1e-3):
     """Sphere-traces the Eq. 3 blend; ``lists`` must be at LOD ceil(L~)."""
     import torch
     _require_cuda(o, d)
@@ -408,7 +442,8 @@ def sphere_trace_blend(svo: SVO, feats: Features, dec_lo: DecoderDev, dec_hi: De
                    steps=torch.empty(R, dtype=torch.int32, device=dev),
                    normal=torch.empty((R, 3), dtype=torch.float32, device=dev) if normals else None,
                    work=torch.empty(max(lib().sphere_trace_workspace(R), 1), dtype=torch.uint8, device=dev))
-    p = _TraceParams(eps, far, max_steps, int(osc), {"f32": F32, "bf16": BF16, "fp8": FP8}[decode], int(normals))
+    p = _TraceParams(eps, far, max_steps, int(osc), {"f32": F32, "bf16": BF16, "fp8": FP8}[decode], int(normals),
+                     NORMALS[normal_mode], fd_h)
     fc, lo = feats.c(), dec_lo.c()
     hi = (dec_hi or dec_lo).c()
     _check(lib().sphere_trace_blend(svo.h, C.byref(fc), C.byref(lo), C.byref(hi), o.data_ptr(), d.data_ptr(), R,
@@ -429,11 +464,13 @@ def new_grads(svo: SVO, decs, device="cuda"):
                 b2=torch.zeros(len(decs), dtype=torch.float32, device=device))
 
 
-def sdf_backward(svo: SVO, feats: Features, decs, x, lods, grad_sdf, grads=None, grad_x=None, stream=None):
+def sdf_backward(svo: SVO, feats: Features, decs, x, lods, grad_sdf, grads=None, grad_x=None, stream=None,
+                 deterministic: bool = False):
     """Accumulates the gradients of sum_i grad_sdf[i] . sdf_{lods[i]}(x) into ``grads``.
 
     ``decs`` lists every LOD's decoder (index lod - 1); ``lods`` the
-    increasing LODs whose outputs carry gradient (rows of ``grad_sdf``)."""
+    increasing LODs whose outputs carry gradient (rows of ``grad_sdf``).
+    ``deterministic``: exact fixed-point sums, bit-identical between runs."""
     _require_cuda(x, grad_sdf)
     x = x.contiguous()
     grad_sdf = grad_sdf.contiguous()
@@ -452,7 +489,8 @@ def sdf_backward(svo: SVO, feats: Features, decs, x, lods, grad_sdf, grads=None,
 
     _check(lib().sdf_backward(svo.h, C.byref(fc), dec_arr, x.data_ptr(), Q, mask, grad_sdf.data_ptr(),
                               parr(grads["feats"]), parr(grads["W1"]), parr(grads["b1"]), parr(grads["W2"]),
-                              grads["b2"].data_ptr(), _ptr(grad_x), 0, C.c_void_p(_stream(stream))))
+                              grads["b2"].data_ptr(), _ptr(grad_x), int(bool(deterministic)),
+                              C.c_void_p(_stream(stream))))
     return grads
 
 

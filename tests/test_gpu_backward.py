@@ -153,3 +153,75 @@ def test_adam_step_formula(ng):
     np.testing.assert_allclose(v.cpu().numpy(), ve, rtol=1e-4, atol=1e-9)
     np.testing.assert_allclose(p.cpu().numpy(), pe, rtol=1e-5, atol=1e-6)
     assert g.abs().max().item() == 0.0
+
+
+@pytest.mark.parametrize("fdtype,in_dim", [("f32", 32), ("f16", 35)])
+def test_deterministic_backward(ng, oracle_mod, fdtype, in_dim):
+    # deterministic=1: two runs give bit-identical gradients, the feature
+    # gradients are also identical when the points come in another order,
+    # and the values agree with the FP64 oracle adjoint and the atomic path.
+    # Hidden units sit firmly on or off (biases +-1 against pre-activations
+    # of spread ~0.1), so no FP32-vs-FP64 ReLU flip among the 72k
+    # (query, LOD) pairs moves a coarse corner's summed gradient.
+    sc, oc = S.csg_workload(64, seed=0, max_lod=5)
+    feats = S.init_features(oc, seed=2, sigma=0.1)
+    decs = []
+    for lod in range(1, 6):
+        d = S.init_decoder(lod, in_dim)
+        d.b1 = np.where(np.random.default_rng(lod).random(128) < 0.5, 1.0, -1.0).astype(np.float32)
+        decs.append(d)
+    x = np.concatenate([S.points_in_voxels(oc, 7, 20000, 5), S.uniform_points(4000, 6)])
+    lods = [2, 4, 5]
+    g = np.random.default_rng(4).normal(size=(len(lods), len(x))).astype(np.float32)
+    svo = ng.svo_build(oc.keys)
+    F = ng.Features(feats, dtype=fdtype)
+    D = [ng.DecoderDev.from_decoder(d) for d in decs]
+    xt, gt = torch.from_numpy(x).cuda(), torch.from_numpy(g).cuda()
+
+    def run(det, perm=None):
+        xx, gg = (xt, gt) if perm is None else (xt[perm].contiguous(), gt[:, perm].contiguous())
+        gx = torch.zeros((len(x), 3), device="cuda")
+        gr = ng.sdf_backward(svo, F, D, xx, lods, gg, grad_x=gx, deterministic=det)
+        torch.cuda.synchronize()
+        return gr, gx
+    a, ax = run(True)
+    b, bx = run(True)
+    for k in ("W1", "b1", "W2"):
+        for i in range(5):
+            assert torch.equal(a[k][i], b[k][i]), (k, i)
+    assert torch.equal(a["b2"], b["b2"])
+    for li in range(5):
+        assert torch.equal(a["feats"][li], b["feats"][li]), li
+    assert torch.equal(ax, bx)
+    perm = torch.randperm(len(x), generator=torch.Generator().manual_seed(0)).cuda()
+    p, _ = run(True, perm)
+    for li in range(5):
+        assert torch.equal(a["feats"][li], p["feats"][li]), li
+    f, _ = run(False)
+    ffeats = [t.astype(np.float16).astype(np.float32) for t in feats] if fdtype == "f16" else feats
+    ref = oracle_mod.OracleSVO(oc.keys).sdf_backward(ffeats, decs, x, lods, g)
+    for li in range(5):
+        assert rel_err(a["feats"][li].cpu().numpy(), ref["feats"][li]) < 2e-5, li
+        assert rel_err(a["feats"][li].cpu().numpy(), f["feats"][li].cpu().numpy()) < 2e-5, li
+    for lod in lods:
+        i = lod - 1
+        for k in ("W1", "b1", "W2"):
+            assert rel_err(a[k][i].cpu().numpy(), ref[k][i]) < 2e-5, (k, lod)
+        assert abs(a["b2"][i].item() - ref["b2"][i]) < 1e-3 * max(1.0, abs(ref["b2"][i]))
+    svo.free()
+
+
+def test_deterministic_backward_nonfinite(ng):
+    # a non-finite upstream gradient turns every output of the call into NaN
+    sc, oc = S.plain_sphere(3)
+    feats = S.init_features(oc, seed=2, sigma=0.1)
+    decs = [S.init_decoder(l, 32) for l in (1, 2, 3)]
+    x = S.points_in_voxels(oc, 5, 256, 7)
+    g = np.ones((1, len(x)), np.float32)
+    g[0, 17] = np.inf
+    svo = ng.svo_build(oc.keys)
+    gr = ng.sdf_backward(svo, ng.Features(feats), [ng.DecoderDev.from_decoder(d) for d in decs],
+                         torch.from_numpy(x).cuda(), [3], torch.from_numpy(g).cuda(), deterministic=True)
+    torch.cuda.synchronize()
+    assert torch.isnan(gr["W1"][2]).all() and torch.isnan(gr["feats"][0]).all()
+    svo.free()

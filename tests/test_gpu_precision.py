@@ -1,0 +1,87 @@
+"""Per-pixel and per-query errors of the reduced-precision paths against the
+FP64 oracle of the full-precision model (Sec. 4's representation: FP32
+corner features, FP32 decoder), on CSG-256 (seed 0) at LOD 5 and LOD 6 with
+a 1920x1080 frame.
+
+Configurations: features stored FP32 or FP16 (rounded once, relative error
+<= 2^-11), decode FP32 (CUDA cores), BF16 or FP8-E4M3 (tensor cores; z and
+W1's z columns rounded to 8 or 4 significant bits).  The model is the
+read-out one (LOD L decodes the level-L trilinear interpolant of the corner
+SDF samples exactly), so the FP64 oracle of it is the ground truth; errors
+are reported per configuration (run with -s to see the table) and bounded:
+  * query: |d_gpu - d| <= e_feat + e_dec with e_feat = 2^-11 sum_levels
+    max|f| (FP16 storage) and e_dec the decode's rounding of z (2^-8 |z| for
+    BF16; 2^-4 |z| + 2^-10 B / 448 for FP8, B = the FP8 z bound);
+  * frame: a decode error e moves the stop test d < eps to a neighbouring
+    step, so hit masks differ only on rays whose closest approach lies
+    within e of eps (a small fraction), and the hit depth moves by about
+    one step (< 2 eps) on all but grazing rays.
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_2101_10994_gb300 import scenes as S
+
+pytestmark = pytest.mark.gpu
+
+EPS = 1e-3
+CONFIGS = [("f32", "f32"), ("f16", "f32"), ("f32", "bf16"), ("f16", "bf16"), ("f32", "fp8"), ("f16", "fp8")]
+
+
+@pytest.fixture(scope="module")
+def csg256():
+    sc, oc = S.csg_workload(256, seed=0, max_lod=6)
+    return sc, oc
+
+
+@pytest.mark.parametrize("lod", [5, 6])
+def test_precision_vs_fp64(ng, oracle_mod, csg256, lod):
+    sc, oc = csg256
+    ora = oracle_mod.OracleSVO(oc.keys)
+    feats, dec = S.readout_features(oc, sc), S.readout_decoder(lod)
+    svo = ng.svo_build(oc.keys)
+    D = ng.DecoderDev.from_decoder(dec)
+    o, d, _ = S.camera_rays(1920, 1080, tile=8)
+    to, td = torch.from_numpy(o).cuda(), torch.from_numpy(d).cuda()
+    lists = ng.svo_trace_rays(svo, to, td, lod)
+    sel = np.random.default_rng(lod).choice(len(o), 4000, replace=False)
+    ref = ora.sphere_trace(feats, dec, o[sel], d[sel], lod, eps=EPS, max_steps=128)
+    rh = ref["hit"].astype(bool)
+    xq = np.concatenate([S.points_in_voxels(oc, lod + S.FIRST_FEATURE_DEPTH - 1, 20000, 3),
+                         S.uniform_points(4000, 4)])
+    dq, _ = ora.sdf_query(feats, dec, xq, lod)
+    z = ora.feature_sum(feats, xq, lod)[:, lod - 1]
+    rows = []
+    for fdt, decode in CONFIGS:
+        F = ng.Features(feats, fdt)
+        B = F.set_fp8_bound(svo, lod) if decode == "fp8" else 0.0
+        got_q = ng.sdf_query(svo, F, D, torch.from_numpy(xq).cuda(), lod,
+                             decode=decode).cpu().numpy().astype(np.float64)
+        e_feat = (2.0 ** -11 * sum(np.abs(f[:, : lod]).max() for f in feats[:lod])) if fdt == "f16" else 0.0
+        e_dec = {"f32": 1e-5 + 0.0 * z, "bf16": 2.0 ** -8 * (np.abs(z) + e_feat),
+                 "fp8": 2.0 ** -4 * (np.abs(z) + e_feat) + 2.0 ** -10 * B / 448.0}[decode]
+        eq = np.abs(got_q - dq)
+        assert np.all(eq <= e_feat + e_dec + 1e-6), (fdt, decode, (eq - e_feat - e_dec).max())
+        out = ng.sphere_trace(svo, F, D, to, td, lists, eps=EPS, max_steps=128, decode=decode, normals=True)
+        ng.sphere_trace_status(out)
+        gh = out["hit"].cpu().numpy()[sel].astype(bool)
+        both = gh & rh
+        dt = np.abs(out["t"].cpu().numpy()[sel][both].astype(np.float64) - ref["t"][both])
+        nn = out["normal"].cpu().numpy()[sel][both].astype(np.float64)
+        cosang = (nn * ref["normal"][both]).sum(1) / np.maximum(np.linalg.norm(ref["normal"][both], axis=1), 1e-300)
+        ang = np.degrees(np.arccos(np.clip(cosang, -1.0, 1.0)))
+        mism = float((gh != rh).mean())
+        rows.append((fdt, decode, eq, mism, int(both.sum()), dt, ang))
+        assert mism <= (0.01 if decode == "fp8" else 0.003), (fdt, decode, mism)
+        assert np.median(dt) <= EPS and np.percentile(dt, 99) <= 2 * EPS, (fdt, decode, np.percentile(dt, 99))
+        assert np.median(ang) <= 0.5, (fdt, decode, np.median(ang))
+    print(f"\nCSG-256 seed 0, LOD {lod}, 1920x1080 ({len(sel)} sampled pixels, {int(rh.sum())} oracle hits; "
+          f"{len(xq)} queries), errors vs the FP64 oracle:")
+    print("features decode | query |dd| median p99 max | hit-mask mismatch | hit |dt| median p99 max | "
+          "normal deg median p99")
+    for fdt, decode, eq, mism, nb, dt, ang in rows:
+        print(f"PRECISION lod={lod} {fdt:>4} {decode:>5} | {np.median(eq):.2e} {np.percentile(eq, 99):.2e} "
+              f"{eq.max():.2e} | {mism * 100:.2f}% | {np.median(dt):.2e} {np.percentile(dt, 99):.2e} "
+              f"{dt.max():.2e} | {np.median(ang):.3f} {np.percentile(ang, 99):.3f}")
+    svo.free()
