@@ -584,10 +584,11 @@ def main():
             "traversal_roofline": traversal_roofline(W, r, head, peaks),
             "clocks": clocks,
             "e2e": e2e,
-            # per frame: traversal (tiles, tile scan, placement) + trace + normals, once in the
-            # sequential frame and once per chunk in the renderer's frame; the blended frame adds
-            # a second gradient pass and the normalisation
-            "gpu_launches": args.steps * (len(modes) * 5 * (1 + CHUNKS) + ("bf16_blend" in res) * 7 * CHUNKS),
+            # per frame: traversal (tiles, tile scan, placement) + ray-group order (keys, bucket
+            # scan, scatter) + trace + normals, once in the sequential frame and once per chunk in
+            # the renderer's frame; the blended frame adds a second gradient pass and the
+            # normalisation
+            "gpu_launches": args.steps * (len(modes) * 8 * (1 + CHUNKS) + ("bf16_blend" in res) * 10 * CHUNKS),
         }
         if "bf16" in res and "f32" in res:
             line["bf16_speedup"] = res["f32"]["ms_per_step"] / res["bf16"]["ms_per_step"]

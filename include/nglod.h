@@ -55,7 +55,9 @@ typedef struct nglod_svo nglod_svo;   /* opaque octree handle */
 
 /* Corner features of LODs 1..num_lods (Sec. 3.2: z_V^(j) in R^m, shared). */
 typedef struct {
-    const void* feats[8];  /* feats[l-1]: [C_l, m] row-major, dtype below   */
+    const void* feats[8];  /* feats[l-1]: [C_l, m] row-major, dtype below;
+                              32-byte aligned (FP32) or 16-byte (FP16), else
+                              NGLOD_ERR_INVALID_ARG                          */
     int dtype;             /* NGLOD_F32 or NGLOD_F16                         */
     int m;                 /* feature dimension; only 32 is built            */
     int num_lods;          /* number of valid entries in feats               */
@@ -280,9 +282,14 @@ size_t sphere_trace_workspace(int64_t R);
  *                       -1 for misses, and int32 word 2 counts the hit rays,
  *                       whose ids follow (in no particular order) from byte
  *                       256 + 4R rounded up to 256; trace_normals reads them.
+ *                       The rest holds the order in which 32-ray groups are
+ *                       handed to the persistent trace (by decreasing longest
+ *                       list, so long rays start early); it changes only the
+ *                       schedule, never a ray's outputs.
  * Outputs: t_hit [R] (+inf on miss), hit [R] uint8, steps [R] int32
  * (nullable: decodes taken), normal [R, 3] (nullable; normalised analytic
- * gradient of the decoded SDF at the hit point in FP32, zero on miss).
+ * gradient of the decoded SDF at the hit point in FP32, or its central
+ * differences with params->normal_mode = NGLOD_NORMALS_FD; zero on miss).
  * Errors: as sdf_query, plus NGLOD_ERR_INVALID_ARG for bad params.  Does not
  * synchronise. */
 int sphere_trace(const nglod_svo* svo, const nglod_features* feats,

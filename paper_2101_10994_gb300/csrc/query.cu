@@ -28,6 +28,9 @@ int fill_tables(const nglod_svo* svo, const nglod_features* f, int lod, Tables& 
     for (int l = 0; l < kMaxLods; ++l) tb.feats[l] = nullptr;
     for (int l = 1; l <= lod; ++l) {
         if (!f->feats[l - 1]) return fail(NGLOD_ERR_INVALID_ARG, "NULL feature table for a LOD <= lod");
+        // FP32 rows are read with 32-byte vector loads, FP16 rows with 16-byte ones
+        if ((reinterpret_cast<uintptr_t>(f->feats[l - 1]) & (f->dtype == NGLOD_F32 ? 31u : 15u)) != 0)
+            return fail(NGLOD_ERR_INVALID_ARG, "feature tables must be 32-byte (FP32) or 16-byte (FP16) aligned");
         tb.feats[l - 1] = f->feats[l - 1];
     }
     for (int d = 0; d <= kMaxDepth; ++d) {
@@ -925,9 +928,104 @@ extern "C" int sdf_query(const nglod_svo* svo, const nglod_features* feats, cons
     return NGLOD_OK;
 }
 
+namespace nglod {
+namespace {
+
+// Ray-group handout order of the persistent tracers.  Rays are taken from the
+// queue 32 at a time; a group whose longest voxel list is long tends to
+// hold a slot for many steps, and started last it leaves the frame with a
+// tail of nearly empty tiles.  The groups are therefore handed out by
+// decreasing longest-list length (a counting sort over kOrderBuckets
+// lengths, clamped), which changes only the schedule: every ray's outputs
+// are those of the index-order trace.
+__global__ void k_group_keys(const int32_t* __restrict__ offs, long long R, uint8_t* __restrict__ key,
+                             int* __restrict__ hist) {
+    __shared__ int h[kOrderBuckets];
+    for (int i = threadIdx.x; i < kOrderBuckets; i += blockDim.x) h[i] = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const long long G = (R + 31) / 32;
+    const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
+    for (long long g = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); g < G; g += nw) {
+        const long long r = g * 32 + lane;
+        const int len = r < R ? offs[r + 1] - offs[r] : 0;
+        const int m = __reduce_max_sync(0xffffffffu, len);
+        if (lane == 0) {
+            const int b = kOrderBuckets - 1 - min(max(m, 0), kOrderBuckets - 1);   // longest first
+            key[g] = (uint8_t)b;
+            atomicAdd(&h[b], 1);
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kOrderBuckets; i += blockDim.x)
+        if (h[i]) atomicAdd(&hist[i], h[i]);
+}
+
+// cursor[b] = sum of hist[0..b) (one block of kOrderBuckets threads).
+__global__ void k_order_scan(const int* __restrict__ hist, int* __restrict__ cursor) {
+    __shared__ int ws[kOrderBuckets / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int v = hist[threadIdx.x];
+    int incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) ws[w] = incl;
+    __syncthreads();
+    int pre = 0;
+    for (int i = 0; i < w; ++i) pre += ws[i];
+    cursor[threadIdx.x] = pre + incl - v;
+}
+
+// Places every group at its bucket's cursor; lanes of a warp with the same
+// key share one atomic (most groups fall in a few buckets).
+__global__ void k_order_scatter(const uint8_t* __restrict__ key, long long G, int* __restrict__ cursor,
+                                int32_t* __restrict__ order) {
+    const int lane = threadIdx.x & 31;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long g0 = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); g0 < G; g0 += stride) {
+        const long long g = g0 + lane;
+        const bool act = g < G;
+        const unsigned live = __ballot_sync(0xffffffffu, act);
+        if (!act) continue;
+        const int k = key[g];
+        const unsigned peers = __match_any_sync(live, k);
+        const int leader = __ffs(peers) - 1;
+        int base = 0;
+        if (lane == leader) base = atomicAdd(&cursor[k], __popc(peers));
+        base = __shfl_sync(peers, base, leader);
+        order[base + __popc(peers & ((1u << lane) - 1u))] = (int32_t)g;
+    }
+}
+
+}  // namespace
+
+int enqueue_ray_order(TraceArgs& A, void* work, cudaStream_t st) {
+    const long long R = A.R, G = (R + 31) / 32;
+    char* w = static_cast<char*>(work);
+    int32_t* order = reinterpret_cast<int32_t*>(w + trace_ws_order_offset(R));
+    uint8_t* key = reinterpret_cast<uint8_t*>(w + trace_ws_key_offset(R));
+    int* hist = reinterpret_cast<int*>(w + trace_ws_count_offset(R));
+    int* cursor = hist + kOrderBuckets;
+    NGLOD_CUDA(cudaMemsetAsync(hist, 0, kOrderBuckets * sizeof(int), st));
+    const int sms = device_sms();
+    const int gk = (int)std::max<long long>(1, std::min<long long>((G + 7) / 8, (long long)sms * 4));
+    k_group_keys<<<gk, 256, 0, st>>>(A.offs, R, key, hist);
+    k_order_scan<<<1, kOrderBuckets, 0, st>>>(hist, cursor);
+    const int gs = (int)std::max<long long>(1, std::min<long long>((G + 255) / 256, (long long)sms * 4));
+    k_order_scatter<<<gs, 256, 0, st>>>(key, G, cursor, order);
+    NGLOD_CUDA(cudaGetLastError());
+    A.order = order;
+    return NGLOD_OK;
+}
+
+}  // namespace nglod
+
 extern "C" size_t sphere_trace_workspace(int64_t R) {
     if (R < 0) return 0;
-    return trace_ws_hit_list_offset(R) + ((sizeof(int32_t) * (size_t)R + 255) / 256) * 256;
+    return trace_ws_size(R);
 }
 
 extern "C" int sphere_trace(const nglod_svo* svo, const nglod_features* feats, const nglod_decoder* dec,
@@ -976,6 +1074,7 @@ extern "C" int sphere_trace(const nglod_svo* svo, const nglod_features* feats, c
     NGLOD_CUDA(cudaMemsetAsync(work, 0, 256, st));
     rc = check_decoder(dec);
     if (rc) return rc;
+    if ((rc = enqueue_ray_order(A, work, st))) return rc;
     if (params->decode_dtype == NGLOD_F32) {
         rc = launch_trace_fp32(dec, tb, A, f16, svo->num_sms, st);
     } else if (params->decode_dtype == NGLOD_BF16 || params->decode_dtype == NGLOD_FP8E4M3) {

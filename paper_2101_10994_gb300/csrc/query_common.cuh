@@ -101,12 +101,15 @@ __device__ __forceinline__ float4 gather_slot(const Tables& tb, int dd, int vox,
 template <typename T>
 struct FeatLoad8;
 
+// FP32 rows: one 32-byte load per lane (the 4 lanes read the 128-byte row
+// with a single instruction; rows are 128-byte aligned).
 template <>
 struct FeatLoad8<float> {
     static __device__ __forceinline__ void load(const void* base, int row, int l4, float4& a, float4& b) {
-        const float4* p = reinterpret_cast<const float4*>(base) + (size_t)row * 8 + 2 * l4;
-        a = __ldg(p);
-        b = __ldg(p + 1);
+        const float* p = reinterpret_cast<const float*>(base) + (size_t)row * 32 + 8 * l4;
+        asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+            : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
+            : "l"(p));
     }
 };
 

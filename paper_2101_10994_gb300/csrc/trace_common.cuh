@@ -92,6 +92,9 @@ struct TraceArgs {
     int* queue;           // workspace: next unstarted ray
     int* hit_count;       // workspace: number of rays in hit_list
     int32_t* hit_list;    // workspace: ids of the rays that hit (any order)
+    // workspace: the order in which 32-ray groups are handed out (null:
+    // index order); longest-working groups first shortens the frame's tail
+    const int32_t* order = nullptr;
 };
 
 // One ray being traced: its list cursor [cur, end) with the current entry's
@@ -204,6 +207,7 @@ __device__ __forceinline__ void refill(RaySlot& S, RayQueue& Qu, const TraceArgs
                 Qu.exhausted = true;
                 return;
             }
+            if (A.order) s = A.order[s >> 5] << 5;
             Qu.next = s;
             Qu.end = (int)min((long long)s + 32, A.R);
         }
@@ -317,6 +321,20 @@ int check_normal_params(const nglod_trace_params* params, const char* who);
 // count}, then int32 hit voxel per ray, then int32 hit list.
 inline size_t trace_ws_hit_vox_offset() { return 256; }
 inline size_t trace_ws_hit_list_offset(long long R) { return 256 + ((sizeof(int32_t) * (size_t)R + 255) / 256) * 256; }
+// ... then the ray-group order: int32 order[G], uint8 key[G] (G = ceil(R / 32))
+// and the 2 x kOrderBuckets counters of its counting sort.
+constexpr int kOrderBuckets = 256;
+inline size_t trace_ws_align(size_t v) { return (v + 255) / 256 * 256; }
+inline size_t trace_ws_order_offset(long long R) {
+    return trace_ws_hit_list_offset(R) + trace_ws_align(sizeof(int32_t) * (size_t)R);
+}
+inline size_t trace_ws_key_offset(long long R) {
+    return trace_ws_order_offset(R) + trace_ws_align(sizeof(int32_t) * (size_t)((R + 31) / 32));
+}
+inline size_t trace_ws_count_offset(long long R) { return trace_ws_key_offset(R) + trace_ws_align((size_t)((R + 31) / 32)); }
+inline size_t trace_ws_size(long long R) { return trace_ws_count_offset(R) + 2 * kOrderBuckets * sizeof(int); }
+// Enqueues the work-ordered ray-group handout of a trace (sets A.order).
+int enqueue_ray_order(TraceArgs& A, void* work, cudaStream_t st);
 int launch_trace_bf16(const nglod_svo* svo, const nglod_decoder* dec, const Tables& tb, const TraceArgs& A,
                       bool f16, float fp8_z_absmax, cudaStream_t st);
 int launch_query_bf16(const nglod_svo* svo, const Tables& tb, const nglod_decoder* dec, const float* x,
