@@ -536,9 +536,9 @@ def run_batch(args):
         "autotune": {"best_ctas_per_sm": best, "ms": tune},
         "hit_pixels": hits,
         "clocks": sampler.summary(),
-        # per graph replay: each job's traversal (3 launches), the reset and the persistent
-        # trace kernel, each job's normals
-        "gpu_launches": args.steps * (3 * len(jobs) + 2 + len(jobs)),
+        # per graph replay: each job's traversal (3 launches), the reset, the chunk order
+        # (keys, bucket scan, scatter) and the persistent trace kernel, each job's normals
+        "gpu_launches": args.steps * (3 * len(jobs) + 5 + len(jobs)),
     }
     print(json.dumps(line))
 

@@ -30,7 +30,12 @@ struct nglod_batch {
     float fp8_z = 0.f;
     nglod::TraceJob* d_jobs = nullptr;
     nglod::JobGroup* d_groups = nullptr;
-    int* d_words = nullptr;            // [0, G) group queues, [G] status
+    int* d_words = nullptr;            // [0, G) group queues, [G] status, then G x kOrderBuckets counts
+    int32_t* d_order = nullptr;        // per group: handout order of its 32-ray chunks
+    uint8_t* d_keys = nullptr;         // per chunk: bucket of its longest list
+    long long* d_gbase = nullptr;      // [G + 1] first chunk of each group (global chunk index)
+    int* d_cursor = nullptr;           // G x kOrderBuckets
+    long long nchunks = 0;
     std::vector<nglod::TraceJob> h_jobs;
     std::vector<nglod_decoder> h_decs;
     std::vector<float*> normals;
@@ -53,7 +58,100 @@ void destroy_batch(nglod_batch* b) {
     if (b->d_jobs) cudaFree(b->d_jobs);
     if (b->d_groups) cudaFree(b->d_groups);
     if (b->d_words) cudaFree(b->d_words);
+    if (b->d_order) cudaFree(b->d_order);
+    if (b->d_keys) cudaFree(b->d_keys);
+    if (b->d_gbase) cudaFree(b->d_gbase);
+    if (b->d_cursor) cudaFree(b->d_cursor);
     delete b;
+}
+
+// Work-ordered handout inside each group (as in sphere_trace): every 32-ray
+// chunk of a group's queue is keyed by its longest voxel list, and the
+// chunks are counting-sorted longest first.  Chunk c of the batch lies in
+// group g with gbase[g] <= c < gbase[g + 1]; its rays are those of the job
+// whose (32-aligned) queue range holds it.
+constexpr int kSmemGroups = 16;    // groups whose bucket counts a block keeps in shared memory
+
+__device__ __forceinline__ int find_group(const long long* __restrict__ gbase, int G, long long c) {
+    int lo = 0, hi = G - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (gbase[mid] <= c) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void k_batch_keys(const TraceJob* __restrict__ jobs, const JobGroup* __restrict__ groups, int G,
+                             const long long* __restrict__ gbase, long long nchunks, uint8_t* __restrict__ key,
+                             int* __restrict__ hist) {
+    __shared__ int h[kSmemGroups * kOrderBuckets];
+    const int gs = min(G, kSmemGroups);
+    for (int i = threadIdx.x; i < gs * kOrderBuckets; i += blockDim.x) h[i] = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
+    for (long long c = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); c < nchunks; c += nw) {
+        const int g = find_group(gbase, G, c);
+        const long long gi = (c - gbase[g]) * 32;
+        int lo = groups[g].j0, hi = groups[g].j1 - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (jobs[mid].ray_base <= gi) lo = mid; else hi = mid - 1;
+        }
+        const TraceArgs& A = jobs[lo].A;
+        const long long r = gi - jobs[lo].ray_base + lane;
+        const int len = r < A.R ? A.offs[r + 1] - A.offs[r] : 0;
+        const int m = __reduce_max_sync(0xffffffffu, len);
+        if (lane == 0) {
+            const int b = kOrderBuckets - 1 - min(max(m, 0), kOrderBuckets - 1);
+            key[c] = (uint8_t)b;
+            if (g < kSmemGroups) atomicAdd(&h[g * kOrderBuckets + b], 1);
+            else atomicAdd(&hist[g * kOrderBuckets + b], 1);
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < gs * kOrderBuckets; i += blockDim.x)
+        if (h[i]) atomicAdd(&hist[i], h[i]);
+}
+
+// One block per group: cursor = exclusive sum of its bucket counts.
+__global__ void k_batch_order_scan(const int* __restrict__ hist, int* __restrict__ cursor) {
+    __shared__ int ws[kOrderBuckets / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int v = hist[blockIdx.x * kOrderBuckets + threadIdx.x];
+    int incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) ws[w] = incl;
+    __syncthreads();
+    int pre = 0;
+    for (int i = 0; i < w; ++i) pre += ws[i];
+    cursor[blockIdx.x * kOrderBuckets + threadIdx.x] = pre + incl - v;
+}
+
+__global__ void k_batch_order_scatter(const long long* __restrict__ gbase, int G, long long nchunks,
+                                      const uint8_t* __restrict__ key, int* __restrict__ cursor,
+                                      int32_t* __restrict__ order) {
+    const int lane = threadIdx.x & 31;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long c0 = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); c0 < nchunks; c0 += stride) {
+        const long long c = c0 + lane;
+        const bool act = c < nchunks;
+        const unsigned live = __ballot_sync(0xffffffffu, act);
+        if (!act) continue;
+        const int g = find_group(gbase, G, c);
+        const int slot = g * kOrderBuckets + key[c];
+        const unsigned peers = __match_any_sync(live, slot);
+        const int leader = __ffs(peers) - 1;
+        int base = 0;
+        if (lane == leader) base = atomicAdd(&cursor[slot], __popc(peers));
+        base = __shfl_sync(peers, base, leader);
+        // the group's order array starts at its first chunk; entries are group-local chunks
+        order[gbase[g] + base + __popc(peers & ((1u << lane) - 1u))] = (int32_t)(c - gbase[g]);
+    }
 }
 
 }  // namespace
@@ -144,7 +242,7 @@ extern "C" int sphere_trace_batch_create(const nglod_trace_job* jobs, int num_jo
             A.hit_vox = (int32_t*)((char*)J.work + trace_ws_hit_vox_offset());
             A.hit_list = (int32_t*)((char*)J.work + trace_ws_hit_list_offset(J.R));
             tj.ray_base = base;
-            base += J.R;
+            base += (J.R + 31) / 32 * 32;     // chunks of 32 never span two jobs
             b->h_jobs.push_back(tj);
             b->h_decs.push_back(J.dec);
             b->normals.push_back(J.normal);
@@ -179,17 +277,29 @@ extern "C" int sphere_trace_batch_create(const nglod_trace_job* jobs, int num_jo
     }
     b->njobs = (int)b->h_jobs.size();
     b->ngroups = G;
+    std::vector<long long> gbase(G + 1, 0);
+    for (int g = 0; g < G; ++g) gbase[g + 1] = gbase[g] + groups[g].nrays / 32;
+    b->nchunks = gbase[G];
     cudaError_t e = cudaMalloc(&b->d_jobs, sizeof(TraceJob) * b->njobs);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_groups, sizeof(JobGroup) * G);
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_words, sizeof(int) * (G + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_words, sizeof(int) * (G + 1 + (size_t)G * kOrderBuckets));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_cursor, sizeof(int) * (size_t)G * kOrderBuckets);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_gbase, sizeof(long long) * (G + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_order, sizeof(int32_t) * std::max<long long>(1, b->nchunks));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_keys, std::max<long long>(1, b->nchunks));
     if (e != cudaSuccess) {
         destroy_batch(b);
         return check_cuda(e, "sphere_trace_batch_create: cudaMalloc");
     }
-    for (int g = 0; g < G; ++g) groups[g].queue = b->d_words + g;
+    for (int g = 0; g < G; ++g) {
+        groups[g].queue = b->d_words + g;
+        groups[g].order = b->d_order + gbase[g];
+    }
     e = cudaMemcpyAsync(b->d_jobs, b->h_jobs.data(), sizeof(TraceJob) * b->njobs, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(b->d_groups, groups.data(), sizeof(JobGroup) * G, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->d_gbase, gbase.data(), sizeof(long long) * (G + 1), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) {
         destroy_batch(b);
@@ -202,9 +312,20 @@ extern "C" int sphere_trace_batch_create(const nglod_trace_job* jobs, int num_jo
 extern "C" int sphere_trace_batch_run(nglod_batch* b, void* stream) {
     cudaStream_t st = (cudaStream_t)stream;
     if (!b) return fail(NGLOD_ERR_INVALID_ARG, "sphere_trace_batch_run: NULL batch");
-    k_batch_reset<<<std::max(1, std::min((b->njobs + b->ngroups + 1 + 255) / 256, 64)), 256, 0, st>>>(
-        b->d_jobs, b->njobs, b->d_words, b->ngroups + 1);
+    const int nwords = b->ngroups + 1 + b->ngroups * kOrderBuckets;
+    k_batch_reset<<<std::max(1, std::min((b->njobs + nwords + 255) / 256, 64)), 256, 0, st>>>(
+        b->d_jobs, b->njobs, b->d_words, nwords);
     NGLOD_CUDA(cudaGetLastError());
+    if (b->nchunks > 0) {
+        int* hist = b->d_words + b->ngroups + 1;
+        const int gk = (int)std::max<long long>(1, std::min<long long>((b->nchunks + 7) / 8, (long long)b->sms * 4));
+        k_batch_keys<<<gk, 256, 0, st>>>(b->d_jobs, b->d_groups, b->ngroups, b->d_gbase, b->nchunks, b->d_keys, hist);
+        k_batch_order_scan<<<b->ngroups, kOrderBuckets, 0, st>>>(hist, b->d_cursor);
+        const int gs = (int)std::max<long long>(1, std::min<long long>((b->nchunks + 255) / 256, (long long)b->sms * 4));
+        k_batch_order_scatter<<<gs, 256, 0, st>>>(b->d_gbase, b->ngroups, b->nchunks, b->d_keys, b->d_cursor,
+                                                   b->d_order);
+        NGLOD_CUDA(cudaGetLastError());
+    }
     int rc;
     if (b->decode == NGLOD_F32)
         rc = launch_trace_batch_f32(b->d_jobs, b->d_groups, b->ngroups, b->in_dim, b->f16, b->ctas_per_sm, b->sms, st);

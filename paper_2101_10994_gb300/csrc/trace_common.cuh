@@ -247,18 +247,19 @@ __device__ __forceinline__ void step_update(RaySlot& S, float dhat, const TraceA
 struct TraceJob {
     TraceArgs A;             // per-job rays, lists, outputs, workspace words
     Tables tb;               // per-job octree and feature tables
-    long long ray_base;      // index of the job's first ray in its group's queue
+    long long ray_base;      // index of the job's first ray in its group's queue (a multiple of 32)
 };
 
 struct JobGroup {
     int j0, j1;              // jobs [j0, j1)
-    long long nrays;
+    long long nrays;         // queue length: the jobs' rays, each job padded to a multiple of 32
     const float* W1;
     const float* b1;
     const float* W2;
     float b2;
     float z_scale;           // FP8 decode
     int* queue;
+    const int32_t* order;    // handout order of the group's 32-ray chunks (longest list first)
 };
 
 // Gives every idle lane the next ray of the group (finishing empty-list rays
@@ -276,6 +277,7 @@ __device__ __forceinline__ void refill_batch(RaySlot& S, RayQueue& Qu, const Job
                 Qu.exhausted = true;
                 return;
             }
+            if (G.order) s = G.order[s >> 5] << 5;
             Qu.next = s;
             Qu.end = (int)min((long long)s + 32, G.nrays);
         }
@@ -288,8 +290,11 @@ __device__ __forceinline__ void refill_batch(RaySlot& S, RayQueue& Qu, const Job
                 const int mid = (lo + hi + 1) >> 1;
                 if (jobs[mid].ray_base <= gi) lo = mid; else hi = mid - 1;
             }
-            S.job = lo;
-            start_ray(S, (int)(gi - jobs[lo].ray_base), jobs[lo].A, jobs[lo].tb);
+            const long long local = gi - jobs[lo].ray_base;
+            if (local < jobs[lo].A.R) {      // else: the padding after the job's last ray
+                S.job = lo;
+                start_ray(S, (int)local, jobs[lo].A, jobs[lo].tb);
+            }
         }
         Qu.next += min(__popc(need), avail);
     }
