@@ -13,6 +13,7 @@ events.  Prints one JSON line.
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
     python bench.py --workload batch     # many scenes per frame: per-scene calls vs one
                                          # persistent launch vs its CUDA graph
+    python bench.py --workload train     # training steps (Eq. 4, LODs 1-5, 2^19 samples)
 
 Under torchrun every rank renders its own frame (independent replicas, no
 collective on the data path); rank 0 prints the whole-job throughput.
@@ -55,9 +56,10 @@ def parse():
     p.add_argument("--height", type=int, default=1080)
     p.add_argument("--decode", choices=["both", "all", "f32", "bf16", "fp8"], default="all")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--workload", choices=["frame", "batch"], default="frame",
+    p.add_argument("--workload", choices=["frame", "batch", "train"], default="frame",
                    help="frame: the 1080p LOD5 CSG-64 frame (default); batch: 32 seeded CSG scenes of "
-                        "U{8..256} primitives at LOD U{3..6}, images U{128..1024} a side, BF16 decode")
+                        "U{8..256} primitives at LOD U{3..6}, images U{128..1024} a side, BF16 decode; "
+                        "train: Adam steps of Eq. 4 on the LOD 1-5 CSG-64 octree, 2^19 samples per batch")
     return p.parse_args()
 
 
@@ -543,6 +545,78 @@ def run_batch(args):
     print(json.dumps(line))
 
 
+# ----------------------------------------------------------------------------
+# training: one Adam step of Eq. 4 over all LODs
+# ----------------------------------------------------------------------------
+def run_train(args):
+    """One step = the fused prediction + residual + adjoint kernel per LOD
+    (LODs 1..5 summed, Eq. 4) over a batch of 2^19 SDF samples (half near the
+    surface, half uniform) and the Adam kernel over every parameter tensor."""
+    from paper_2101_10994_gb300 import scenes as S
+    import torch
+
+    from paper_2101_10994_gb300 import nglod as ng
+    from paper_2101_10994_gb300.train import Trainer
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    sc, oc = S.csg_workload(64, seed=0, max_lod=5)
+    n = 1 << 19
+    x_h, t_h = S.training_batch(sc, n, 17)
+    x_p, t_p = torch.from_numpy(x_h).pin_memory(), torch.from_numpy(t_h).pin_memory()
+    x, t = x_p.to(dev), t_p.to(dev)
+    svo = ng.svo_build(oc.keys)
+    tr = Trainer(svo, S.init_features(oc, seed=0, sigma=0.01), [S.init_decoder(l, 32) for l in range(1, 6)])
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def timed(fn, k):
+        ts, out = [], None
+        for _ in range(k):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            out = fn()
+            e1.record()
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts), out
+
+    first = tr.step(x, t).cpu().numpy()
+    for _ in range(args.warmup):
+        tr.step(x, t)
+    torch.cuda.synchronize()
+    loss_h = torch.empty(5, dtype=torch.float32).pin_memory()
+
+    def e2e_step():
+        x.copy_(x_p, non_blocking=True)
+        t.copy_(t_p, non_blocking=True)
+        loss = tr.step(x, t)
+        loss_h.copy_(loss, non_blocking=True)
+        return loss
+
+    sampler = ClockSampler(0)
+    with sampler:
+        ms, last = timed(lambda: tr.step(x, t), args.steps)
+        ms_e2e, _ = timed(e2e_step, args.steps)
+    last = last.cpu().numpy()
+    nparam = len(tr.params)
+    line = {
+        "metric": "SDF training samples/s (Eq. 4 over LODs 1-5: fused prediction + adjoint + Adam)",
+        "value": n / (ms * 1e-3), "unit": "samples/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": "train_csg64_seed0_lod1-5_2^19_samples", "samples": n, "lods": [1, 2, 3, 4, 5],
+                   "features": "f32 m=32", "decoder": "32->128->1", "optimizer": "Adam lr 1e-3",
+                   "l2": "flushed between steps (256 MB write)", "parallelism": "single GPU"},
+        "loss_per_lod": {"first_step": [float(v) for v in first], "last_step": [float(v) for v in last]},
+        "clocks": sampler.summary(),
+        "e2e": {"value": n / (ms_e2e * 1e-3), "unit": "samples/s", "h2d_bytes_per_step": int(n * 16),
+                "d2h_bytes_per_step": 20},
+        # per step: one fused kernel per LOD, one Adam kernel per parameter tensor
+        "gpu_launches": args.steps * (5 + nparam),
+    }
+    print(json.dumps(line))
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -555,6 +629,10 @@ def main():
     if args.workload == "batch":
         if rank == 0:
             run_batch(args)
+        return
+    if args.workload == "train":
+        if rank == 0:
+            run_train(args)
         return
     if world > 1:
         import torch

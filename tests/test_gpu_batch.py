@@ -144,3 +144,21 @@ def test_batch_rejects_mixed_in_dim(ng, items):
     jobs[1].dec = ng.DecoderDev.from_decoder(S.readout_decoder(jobs[1].lod, in_dim=35))
     with pytest.raises(ng.NglodError):
         B.BatchRenderer(jobs, decode="f32")
+
+
+def test_batch_tiny_jobs_padding(ng, items):
+    # jobs of 1 and 33 rays between larger ones of the same decoder group: each
+    # job's queue range is padded to 32-ray chunks, and the padding must start
+    # no ray and disturb no neighbour
+    from paper_2101_10994_gb300 import batch as B
+    sc, oc, lod, w, h, feats = items[0]
+    tiny = [(sc, oc, lod, 1, 1, feats), (sc, oc, lod, 11, 3, feats)]
+    jobs = make_jobs(ng, [items[0]] + tiny + [items[0]], "bf16")
+    assert len({j.lod for j in jobs}) == 1
+    rnd = B.BatchRenderer(jobs, decode="bf16")
+    rnd.frame()
+    rnd.check()
+    for k, j in enumerate(jobs):
+        lists, ref = per_job(ng, j, "bf16")
+        assert_same(rnd.outputs(k), lists, ref, rnd.bufs[k])
+    rnd.free()
