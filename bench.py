@@ -551,7 +551,9 @@ def run_batch(args):
 def run_train(args):
     """One step = the fused prediction + residual + adjoint kernel per LOD
     (LODs 1..5 summed, Eq. 4) over a batch of 2^19 SDF samples (half near the
-    surface, half uniform) and the Adam kernel over every parameter tensor."""
+    surface, half uniform) and the Adam kernel over every parameter tensor;
+    the adjoint's decoder contractions in FP32 on the CUDA cores, and (the
+    reported value) in BF16 on the tensor cores."""
     from paper_2101_10994_gb300 import scenes as S
     import torch
 
@@ -565,7 +567,6 @@ def run_train(args):
     x_p, t_p = torch.from_numpy(x_h).pin_memory(), torch.from_numpy(t_h).pin_memory()
     x, t = x_p.to(dev), t_p.to(dev)
     svo = ng.svo_build(oc.keys)
-    tr = Trainer(svo, S.init_features(oc, seed=0, sigma=0.01), [S.init_decoder(l, 32) for l in range(1, 6)])
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
     def timed(fn, k):
@@ -580,36 +581,45 @@ def run_train(args):
             ts.append(e0.elapsed_time(e1))
         return statistics.median(ts), out
 
-    first = tr.step(x, t).cpu().numpy()
-    for _ in range(args.warmup):
-        tr.step(x, t)
-    torch.cuda.synchronize()
     loss_h = torch.empty(5, dtype=torch.float32).pin_memory()
-
-    def e2e_step():
-        x.copy_(x_p, non_blocking=True)
-        t.copy_(t_p, non_blocking=True)
-        loss = tr.step(x, t)
-        loss_h.copy_(loss, non_blocking=True)
-        return loss
-
+    res = {}
     sampler = ClockSampler(0)
-    with sampler:
-        ms, last = timed(lambda: tr.step(x, t), args.steps)
-        ms_e2e, _ = timed(e2e_step, args.steps)
-    last = last.cpu().numpy()
+    for mma in ("f32", "bf16"):
+        tr = Trainer(svo, S.init_features(oc, seed=0, sigma=0.01), [S.init_decoder(l, 32) for l in range(1, 6)],
+                     mma=mma)
+        first = tr.step(x, t).cpu().numpy()
+        for _ in range(args.warmup):
+            tr.step(x, t)
+        torch.cuda.synchronize()
+
+        def e2e_step():
+            x.copy_(x_p, non_blocking=True)
+            t.copy_(t_p, non_blocking=True)
+            loss = tr.step(x, t)
+            loss_h.copy_(loss, non_blocking=True)
+            return loss
+
+        with sampler:
+            ms, last = timed(lambda: tr.step(x, t), args.steps)
+            ms_e2e, _ = timed(e2e_step, args.steps)
+        res[mma] = {"ms_per_step": ms, "samples_per_s": n / (ms * 1e-3), "e2e_samples_per_s": n / (ms_e2e * 1e-3),
+                    "loss_first_step": [float(v) for v in first],
+                    "loss_after": [float(v) for v in last.cpu().numpy()], "steps_taken": 2 + args.warmup + 2 * args.steps}
     nparam = len(tr.params)
+    head = "bf16"
+    ms = res[head]["ms_per_step"]
     line = {
         "metric": "SDF training samples/s (Eq. 4 over LODs 1-5: fused prediction + adjoint + Adam)",
         "value": n / (ms * 1e-3), "unit": "samples/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": head,
         "data": "synthetic",
         "config": {"workload": "train_csg64_seed0_lod1-5_2^19_samples", "samples": n, "lods": [1, 2, 3, 4, 5],
                    "features": "f32 m=32", "decoder": "32->128->1", "optimizer": "Adam lr 1e-3",
+                   "adjoint": "bf16 tensor-core contractions, fp32 accumulation (fp32 CUDA-core adjoint in modes)",
                    "l2": "flushed between steps (256 MB write)", "parallelism": "single GPU"},
-        "loss_per_lod": {"first_step": [float(v) for v in first], "last_step": [float(v) for v in last]},
+        "modes": res,
         "clocks": sampler.summary(),
-        "e2e": {"value": n / (ms_e2e * 1e-3), "unit": "samples/s", "h2d_bytes_per_step": int(n * 16),
+        "e2e": {"value": res[head]["e2e_samples_per_s"], "unit": "samples/s", "h2d_bytes_per_step": int(n * 16),
                 "d2h_bytes_per_step": 20},
         # per step: one fused kernel per LOD, one Adam kernel per parameter tensor
         "gpu_launches": args.steps * (5 + nparam),

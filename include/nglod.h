@@ -344,6 +344,26 @@ int sdf_l2_backward(const nglod_svo* svo, const nglod_features* feats, const ngl
                     float* const* h_grad_W1, float* const* h_grad_b1, float* const* h_grad_W2,
                     float* grad_b2, void* stream);
 
+/* sdf_backward_bf16 / sdf_l2_backward_bf16 -- the gradients of sdf_backward
+ * and sdf_l2_backward (same arguments, same accumulation into the gradient
+ * buffers) with the decoder's three contractions -- the pre-activations
+ * v W1^T, gz = dpre W1 and dW1 = dpre^T v over 128-query tiles -- on the
+ * tensor cores with BF16 operands and FP32 accumulation (mixed-precision
+ * training; v = [z | x] and dpre rounded to BF16, W1's x columns, b1, W2,
+ * the ReLU masks, the loss and every sum over queries other than dW1 in
+ * FP32).  No x gradient and no deterministic mode (use sdf_backward).
+ * Synchronises the stream to read its status: NGLOD_ERR_TIMEOUT if a
+ * bounded tensor-core wait expired (the gradients are then incomplete). */
+int sdf_backward_bf16(const nglod_svo* svo, const nglod_features* feats, const nglod_decoder* decs,
+                      const float* x, int64_t Q, uint32_t lod_mask, const float* grad_sdf,
+                      float* const* h_grad_feats, float* const* h_grad_W1, float* const* h_grad_b1,
+                      float* const* h_grad_W2, float* grad_b2, void* stream);
+int sdf_l2_backward_bf16(const nglod_svo* svo, const nglod_features* feats, const nglod_decoder* decs,
+                         const float* x, const float* target, int64_t Q, uint32_t lod_mask,
+                         float loss_scale, float* loss, float* const* h_grad_feats,
+                         float* const* h_grad_W1, float* const* h_grad_b1, float* const* h_grad_W2,
+                         float* grad_b2, void* stream);
+
 /* nglod_adam_step -- Adam (the optimiser of supplementary Sec. A.3) on n FP32
  * parameters: m = b1 m + (1-b1) g, v = b2 v + (1-b2) g^2,
  * p -= lr (m / (1-b1^step)) / (sqrt(v / (1-b2^step)) + eps); grad is then

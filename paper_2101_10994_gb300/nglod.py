@@ -28,7 +28,7 @@ EXPORTS = ["nglod_last_error", "svo_build", "svo_info", "svo_device_arrays", "sv
            "nglod_features_absmax", "svo_trace_rays_async", "svo_trace_rays_check",
            "sphere_trace_batch_create", "sphere_trace_batch_run", "sphere_trace_batch_status",
            "sphere_trace_batch_free", "sdf_query_blend", "sphere_trace_blend", "nglod_lod_select",
-           "trace_normals_fd"]
+           "trace_normals_fd", "sdf_backward_bf16", "sdf_l2_backward_bf16"]
 
 
 class NglodError(RuntimeError):
@@ -94,6 +94,8 @@ def lib():
         L.svo_trace_rays_sizes.argtypes = [P, P, i32, P]
         L.sdf_backward.argtypes = [P, P, P, P, i64, C.c_uint32, P, P, P, P, P, P, P, i32, P]
         L.sdf_l2_backward.argtypes = [P, P, P, P, P, i64, C.c_uint32, C.c_float, P, P, P, P, P, P, P]
+        L.sdf_backward_bf16.argtypes = [P, P, P, P, i64, C.c_uint32, P, P, P, P, P, P, P]
+        L.sdf_l2_backward_bf16.argtypes = [P, P, P, P, P, i64, C.c_uint32, C.c_float, P, P, P, P, P, P, P]
         L.nglod_features_absmax.argtypes = [P, P, i32, P, P]
         L.svo_trace_rays_async.argtypes = [P, P, P, i64, i32, P, sz, i64, P, P, P, i64, P]
         L.svo_trace_rays_check.argtypes = [P, i32, P, P]
@@ -465,12 +467,14 @@ def new_grads(svo: SVO, decs, device="cuda"):
 
 
 def sdf_backward(svo: SVO, feats: Features, decs, x, lods, grad_sdf, grads=None, grad_x=None, stream=None,
-                 deterministic: bool = False):
+                 deterministic: bool = False, mma: str = "f32"):
     """Accumulates the gradients of sum_i grad_sdf[i] . sdf_{lods[i]}(x) into ``grads``.
 
     ``decs`` lists every LOD's decoder (index lod - 1); ``lods`` the
     increasing LODs whose outputs carry gradient (rows of ``grad_sdf``).
-    ``deterministic``: exact fixed-point sums, bit-identical between runs."""
+    ``deterministic``: exact fixed-point sums, bit-identical between runs.
+    ``mma="bf16"``: the decoder's contractions on the tensor cores (BF16
+    operands, FP32 accumulation; no grad_x, not deterministic)."""
     _require_cuda(x, grad_sdf)
     x = x.contiguous()
     grad_sdf = grad_sdf.contiguous()
@@ -487,6 +491,13 @@ def sdf_backward(svo: SVO, feats: Features, decs, x, lods, grad_sdf, grads=None,
     def parr(ts):
         return (P * len(ts))(*[t.data_ptr() for t in ts])
 
+    if mma == "bf16":
+        if grad_x is not None or deterministic:
+            raise ValueError("sdf_backward: the BF16 tensor-core adjoint has no grad_x or deterministic mode")
+        _check(lib().sdf_backward_bf16(svo.h, C.byref(fc), dec_arr, x.data_ptr(), Q, mask, grad_sdf.data_ptr(),
+                                       parr(grads["feats"]), parr(grads["W1"]), parr(grads["b1"]), parr(grads["W2"]),
+                                       grads["b2"].data_ptr(), C.c_void_p(_stream(stream))))
+        return grads
     _check(lib().sdf_backward(svo.h, C.byref(fc), dec_arr, x.data_ptr(), Q, mask, grad_sdf.data_ptr(),
                               parr(grads["feats"]), parr(grads["W1"]), parr(grads["b1"]), parr(grads["W2"]),
                               grads["b2"].data_ptr(), _ptr(grad_x), int(bool(deterministic)),
@@ -495,8 +506,10 @@ def sdf_backward(svo: SVO, feats: Features, decs, x, lods, grad_sdf, grads=None,
 
 
 def sdf_l2_backward(svo: SVO, feats: Features, decs, x, target, lods, loss_scale: float, grads, loss=None,
-                    stream=None):
-    """Gradients of loss_scale * sum_L sum_q (sdf_L(x_q) - target_q)^2 (Eq. 4), accumulated into ``grads``."""
+                    stream=None, mma: str = "f32"):
+    """Gradients of loss_scale * sum_L sum_q (sdf_L(x_q) - target_q)^2 (Eq. 4), accumulated into ``grads``.
+
+    ``mma="bf16"``: the decoder's contractions on the tensor cores (BF16 operands, FP32 accumulation)."""
     _require_cuda(x, target)
     mask = 0
     for l in lods:
@@ -508,10 +521,10 @@ def sdf_l2_backward(svo: SVO, feats: Features, decs, x, target, lods, loss_scale
     def parr(ts):
         return (P * len(ts))(*[t.data_ptr() for t in ts])
 
-    _check(lib().sdf_l2_backward(svo.h, C.byref(fc), dec_arr, x.data_ptr(), target.data_ptr(), int(x.shape[0]),
-                                 mask, float(loss_scale), _ptr(loss), parr(grads["feats"]), parr(grads["W1"]),
-                                 parr(grads["b1"]), parr(grads["W2"]), grads["b2"].data_ptr(),
-                                 C.c_void_p(_stream(stream))))
+    fn = lib().sdf_l2_backward_bf16 if mma == "bf16" else lib().sdf_l2_backward
+    _check(fn(svo.h, C.byref(fc), dec_arr, x.data_ptr(), target.data_ptr(), int(x.shape[0]),
+              mask, float(loss_scale), _ptr(loss), parr(grads["feats"]), parr(grads["W1"]),
+              parr(grads["b1"]), parr(grads["W2"]), grads["b2"].data_ptr(), C.c_void_p(_stream(stream))))
     return grads
 
 

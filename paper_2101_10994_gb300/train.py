@@ -13,7 +13,8 @@ from . import nglod as ng
 
 
 class Trainer:
-    def __init__(self, svo: ng.SVO, feats, decoders, lr: float = 1e-3, device="cuda"):
+    def __init__(self, svo: ng.SVO, feats, decoders, lr: float = 1e-3, device="cuda", mma: str = "f32"):
+        """mma = "bf16": the adjoint's decoder contractions on the tensor cores."""
         import torch
         self.torch = torch
         self.svo = svo
@@ -28,6 +29,7 @@ class Trainer:
         self.m = [torch.zeros_like(p) for p in self.params]
         self.v = [torch.zeros_like(p) for p in self.params]
         self.lr = lr
+        self.mma = mma
         self.t = 0
         self.L = len(self.D)
 
@@ -37,7 +39,7 @@ class Trainer:
         lods = lods or list(range(1, self.L + 1))
         loss = torch.zeros(self.L, dtype=torch.float32, device=x.device)
         Q = int(x.shape[0])
-        ng.sdf_l2_backward(self.svo, self.F, self.D, x, target, lods, 1.0 / Q, self.grads, loss)
+        ng.sdf_l2_backward(self.svo, self.F, self.D, x, target, lods, 1.0 / Q, self.grads, loss, mma=self.mma)
         self.t += 1
         for p, g, m, v in zip(self.params, self.gparams, self.m, self.v):
             ng.adam_step(p, g, m, v, self.lr, self.t)
