@@ -364,6 +364,20 @@ int sdf_l2_backward_bf16(const nglod_svo* svo, const nglod_features* feats, cons
                          float* const* h_grad_W1, float* const* h_grad_b1, float* const* h_grad_W2,
                          float* grad_b2, void* stream);
 
+/* nglod_sort_points -- reorders Q points by the Morton code of the depth-
+ * `depth` octree cell (1 <= depth <= 7) containing them (a counting sort;
+ * the order inside a cell is unspecified), so that neighbouring samples of
+ * a training batch share voxels and corner rows.  x [Q, 3] -> x_out; extra
+ * [Q] (nullable, e.g. the SDF targets) -> extra_out; perm [Q] (nullable)
+ * receives the source index of each output point.  Outputs must not alias
+ * inputs.  work: device buffer of nglod_sort_points_workspace(Q, depth)
+ * bytes (4 Q + 2 x 4 x 8^depth bytes and change).  Eq. 4 sums over the
+ * samples, so sorting a batch changes its gradients only by FP32 rounding
+ * order.  Does not synchronise. */
+size_t nglod_sort_points_workspace(int64_t Q, int depth);
+int nglod_sort_points(const float* x, const float* extra, int64_t Q, int depth, float* x_out,
+                      float* extra_out, int32_t* perm, void* work, size_t work_bytes, void* stream);
+
 /* nglod_adam_step -- Adam (the optimiser of supplementary Sec. A.3) on n FP32
  * parameters: m = b1 m + (1-b1) g, v = b2 v + (1-b2) g^2,
  * p -= lr (m / (1-b1^step)) / (sqrt(v / (1-b2^step)) + eps); grad is then

@@ -15,7 +15,10 @@
 //       and MMA3: dW1 += dpre^T v (A2 and A1 both read MN-major), the latter
 //       accumulating in tensor memory over all of the CTA's tiles;
 //   (E) 4-lane groups scatter w_c * gz (gz = the z part of gv) onto every
-//       level's 8 corners with 16-byte vector atomic adds.
+//       level's 8 corners with 16-byte vector atomic adds; the groups of a
+//       warp whose slots share a voxel at a level first sum their
+//       contributions (a butterfly over the groups), so spatially sorted
+//       points (nglod_sort_points) need one atomic per corner and block.
 // One tile layout serves each operand both ways: an MN-major view of a
 // K-major tile takes LBO = the stride between core matrices adjacent along
 // K and SBO = the stride between those adjacent along M/N.  The x columns
@@ -100,32 +103,84 @@ __device__ __forceinline__ float reduce_scatter32(float (&v)[32], int lane) {
 }
 
 // Adds w_c * gz (this lane's 8 channels ga | gb) onto the 8 corners of
-// every level 3..dd of the slot's voxel (the interpolation of gather_slot4,
-// run backwards).  The whole 4-lane group calls it together.
-__device__ __forceinline__ void scatter_slot4(const Tables& tb, float* const* gfeat, int dd, int vox, uint32_t ijk,
-                                              float q0, float q1, float q2, unsigned gmask, int gbase, int l4,
-                                              float4 ga, float4 gb) {
+// every level 3..D of the slots of one round (8 slots, one per 4-lane
+// group).  Groups whose slots lie in the same voxel at a level first sum
+// their contributions pairwise over the groups (xor 4, 8, 16 in lanes) as
+// long as the merged block of groups shares that voxel, so one atomic per
+// corner serves the block.  Called by the whole warp.
+__device__ __forceinline__ void scatter_round(const Tables& tb, float* const* gfeat, int D, int dd, int vox,
+                                              uint32_t ijk, float q0, float q1, float q2, int lane, float4 ga,
+                                              float4 gb) {
+    const int l4 = lane & 3, g4 = lane >> 2, gbase = g4 << 2;
     int2 a = make_int2(-1, -1);
-    if (2 * l4 <= dd - kFirstFeatureDepth) a = __ldg(reinterpret_cast<const int2*>(tb.anc[dd] + (size_t)vox * 8) + l4);
+    if (dd >= kFirstFeatureDepth && 2 * l4 <= dd - kFirstFeatureDepth)
+        a = __ldg(reinterpret_cast<const int2*>(tb.anc[dd] + (size_t)vox * 8) + l4);
 #pragma unroll 1
-    for (int dp = kFirstFeatureDepth; dp <= dd; ++dp) {
+    for (int dp = kFirstFeatureDepth; dp <= D; ++dp) {
         const int i = dp - kFirstFeatureDepth;
-        const int v = __shfl_sync(gmask, (i & 1) ? a.y : a.x, gbase + (i >> 1));
-        const int2 cc = __ldg(reinterpret_cast<const int2*>(tb.corners[dp] + (size_t)v * 8) + l4);
-        const int sh = dd - dp;
-        const float sc = pow2f(dp - 1);
-        const float u0 = clamp01(__fsub_rn(__fmul_rn(q0, sc), (float)(unpack_i(ijk) >> sh)));
-        const float u1 = clamp01(__fsub_rn(__fmul_rn(q1, sc), (float)(unpack_j(ijk) >> sh)));
-        const float u2 = clamp01(__fsub_rn(__fmul_rn(q2, sc), (float)(unpack_k(ijk) >> sh)));
+        const bool act = dp <= dd;
+        const int v = __shfl_sync(0xffffffffu, (i & 1) ? a.y : a.x, gbase + (i >> 1));
+        const int key = act ? v : -1 - g4;
+        const unsigned peers = __match_any_sync(0xffffffffu, key);
+        const bool merge_any = __any_sync(0xffffffffu, __popc(peers) > 4);
+        int2 cc = make_int2(0, 0);
         float w[8];
-        trilinear_weights(u0, u1, u2, w);
-        float* gf = gfeat[i];
+        if (act) {
+            cc = __ldg(reinterpret_cast<const int2*>(tb.corners[dp] + (size_t)v * 8) + l4);
+            const int sh = dd - dp;
+            const float sc = pow2f(dp - 1);
+            const float u0 = clamp01(__fsub_rn(__fmul_rn(q0, sc), (float)(unpack_i(ijk) >> sh)));
+            const float u1 = clamp01(__fsub_rn(__fmul_rn(q1, sc), (float)(unpack_j(ijk) >> sh)));
+            const float u2 = clamp01(__fsub_rn(__fmul_rn(q2, sc), (float)(unpack_k(ijk) >> sh)));
+            trilinear_weights(u0, u1, u2, w);
+        } else {
+#pragma unroll
+            for (int c = 0; c < 8; ++c) w[c] = 0.0f;
+        }
+        // merge plan (the same for all 8 corners): which butterfly steps merge
+        bool carry = act, uni = true;
+        unsigned mstep = 0;                          // bit j: step o = 4 << j merges for this lane
+        if (merge_any) {
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                const int o = 4 << j;
+                const int pkey = __shfl_xor_sync(0xffffffffu, key, o);
+                const int puni = __shfl_xor_sync(0xffffffffu, uni ? 1 : 0, o);
+                if (uni && puni && key == pkey) {
+                    // both halves now hold the block's sum; the lower half's carrier writes it
+                    mstep |= 1u << j;
+                    if (lane & o) carry = false;
+                } else {
+                    uni = false;
+                }
+            }
+        }
+        float* gf = act ? gfeat[i] : nullptr;
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
-            const int cid = __shfl_sync(gmask, (c & 1) ? cc.y : cc.x, gbase + (c >> 1));
-            float* p = gf + (size_t)cid * 32 + 8 * l4;
-            red_add_v4(p, make_float4(w[c] * ga.x, w[c] * ga.y, w[c] * ga.z, w[c] * ga.w));
-            red_add_v4(p + 4, make_float4(w[c] * gb.x, w[c] * gb.y, w[c] * gb.z, w[c] * gb.w));
+            const int cid = __shfl_sync(0xffffffffu, (c & 1) ? cc.y : cc.x, gbase + (c >> 1));
+            float4 ra = make_float4(w[c] * ga.x, w[c] * ga.y, w[c] * ga.z, w[c] * ga.w);
+            float4 rb = make_float4(w[c] * gb.x, w[c] * gb.y, w[c] * gb.z, w[c] * gb.w);
+            if (merge_any) {
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    const int o = 4 << j;
+                    float4 pa, pb;
+                    pa.x = __shfl_xor_sync(0xffffffffu, ra.x, o); pa.y = __shfl_xor_sync(0xffffffffu, ra.y, o);
+                    pa.z = __shfl_xor_sync(0xffffffffu, ra.z, o); pa.w = __shfl_xor_sync(0xffffffffu, ra.w, o);
+                    pb.x = __shfl_xor_sync(0xffffffffu, rb.x, o); pb.y = __shfl_xor_sync(0xffffffffu, rb.y, o);
+                    pb.z = __shfl_xor_sync(0xffffffffu, rb.z, o); pb.w = __shfl_xor_sync(0xffffffffu, rb.w, o);
+                    if ((mstep >> j) & 1u) {
+                        ra = make_float4(ra.x + pa.x, ra.y + pa.y, ra.z + pa.z, ra.w + pa.w);
+                        rb = make_float4(rb.x + pb.x, rb.y + pb.y, rb.z + pb.z, rb.w + pb.w);
+                    }
+                }
+            }
+            if (carry) {
+                float* p = gf + (size_t)cid * 32 + 8 * l4;
+                red_add_v4(p, ra);
+                red_add_v4(p + 4, rb);
+            }
         }
     }
 }
@@ -319,11 +374,9 @@ __global__ void __launch_bounds__(kTQ, 2) k_backward_tc(const Tables tb, const T
             const float s0 = __shfl_sync(0xffffffffu, q0, s);
             const float s1 = __shfl_sync(0xffffffffu, q1, s);
             const float s2 = __shfl_sync(0xffffffffu, q2, s);
-            if (sdd >= kFirstFeatureDepth) {
-                const float* gr = gzs + (warp * 32 + s) * kZStride + 8 * l4;
-                scatter_slot4(tb, A.gfeat, sdd, svox, sijk, s0, s1, s2, gm4, gb4, l4,
-                              *reinterpret_cast<const float4*>(gr), *reinterpret_cast<const float4*>(gr + 4));
-            }
+            const float* gr = gzs + (warp * 32 + s) * kZStride + 8 * l4;
+            scatter_round(tb, A.gfeat, A.D, sdd, svox, sijk, s0, s1, s2, lane,
+                          *reinterpret_cast<const float4*>(gr), *reinterpret_cast<const float4*>(gr + 4));
         }
         __syncthreads();   // gz staging is A2: the next tile writes dpre there
     }

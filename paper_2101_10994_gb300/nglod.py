@@ -28,7 +28,8 @@ EXPORTS = ["nglod_last_error", "svo_build", "svo_info", "svo_device_arrays", "sv
            "nglod_features_absmax", "svo_trace_rays_async", "svo_trace_rays_check",
            "sphere_trace_batch_create", "sphere_trace_batch_run", "sphere_trace_batch_status",
            "sphere_trace_batch_free", "sdf_query_blend", "sphere_trace_blend", "nglod_lod_select",
-           "trace_normals_fd", "sdf_backward_bf16", "sdf_l2_backward_bf16"]
+           "trace_normals_fd", "sdf_backward_bf16", "sdf_l2_backward_bf16", "nglod_sort_points_workspace",
+           "nglod_sort_points"]
 
 
 class NglodError(RuntimeError):
@@ -95,6 +96,9 @@ def lib():
         L.sdf_backward.argtypes = [P, P, P, P, i64, C.c_uint32, P, P, P, P, P, P, P, i32, P]
         L.sdf_l2_backward.argtypes = [P, P, P, P, P, i64, C.c_uint32, C.c_float, P, P, P, P, P, P, P]
         L.sdf_backward_bf16.argtypes = [P, P, P, P, i64, C.c_uint32, P, P, P, P, P, P, P]
+        L.nglod_sort_points_workspace.restype = sz
+        L.nglod_sort_points_workspace.argtypes = [i64, i32]
+        L.nglod_sort_points.argtypes = [P, P, i64, i32, P, P, P, P, sz, P]
         L.sdf_l2_backward_bf16.argtypes = [P, P, P, P, P, i64, C.c_uint32, C.c_float, P, P, P, P, P, P, P]
         L.nglod_features_absmax.argtypes = [P, P, i32, P, P]
         L.svo_trace_rays_async.argtypes = [P, P, P, i64, i32, P, sz, i64, P, P, P, i64, P]
@@ -526,6 +530,30 @@ def sdf_l2_backward(svo: SVO, feats: Features, decs, x, target, lods, loss_scale
               mask, float(loss_scale), _ptr(loss), parr(grads["feats"]), parr(grads["W1"]),
               parr(grads["b1"]), parr(grads["W2"]), grads["b2"].data_ptr(), C.c_void_p(_stream(stream))))
     return grads
+
+
+def sort_points(x, extra=None, depth: int = 7, out=None, stream=None):
+    """Points (and one float per point) reordered by the Morton code of their
+    depth-``depth`` octree cell; returns (x_sorted, extra_sorted, perm).
+    ``out``: a dict of reusable buffers (x, extra, perm, work)."""
+    import torch
+    _require_cuda(x)
+    x = x.contiguous()
+    Q = int(x.shape[0])
+    dev = x.device
+    o = out if out is not None else {}
+    if o.get("x") is None or o["x"].shape[0] != Q:
+        o["x"] = torch.empty((Q, 3), dtype=torch.float32, device=dev)
+        o["extra"] = torch.empty(Q, dtype=torch.float32, device=dev)
+        o["perm"] = torch.empty(Q, dtype=torch.int32, device=dev)
+        o["work"] = torch.empty(max(1, lib().nglod_sort_points_workspace(Q, depth)), dtype=torch.uint8, device=dev)
+    if o["work"].numel() < lib().nglod_sort_points_workspace(Q, depth):
+        o["work"] = torch.empty(lib().nglod_sort_points_workspace(Q, depth), dtype=torch.uint8, device=dev)
+    e = extra.contiguous() if extra is not None else None
+    _check(lib().nglod_sort_points(x.data_ptr(), _ptr(e), Q, int(depth), o["x"].data_ptr(),
+                                   o["extra"].data_ptr() if e is not None else None, o["perm"].data_ptr(),
+                                   o["work"].data_ptr(), o["work"].numel(), C.c_void_p(_stream(stream))))
+    return o["x"], (o["extra"] if e is not None else None), o["perm"]
 
 
 def adam_step(param, grad, m, v, lr, step, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):

@@ -13,8 +13,11 @@ from . import nglod as ng
 
 
 class Trainer:
-    def __init__(self, svo: ng.SVO, feats, decoders, lr: float = 1e-3, device="cuda", mma: str = "f32"):
-        """mma = "bf16": the adjoint's decoder contractions on the tensor cores."""
+    def __init__(self, svo: ng.SVO, feats, decoders, lr: float = 1e-3, device="cuda", mma: str = "f32",
+                 sort_depth: int | None = 7):
+        """mma = "bf16": the adjoint's decoder contractions on the tensor cores.
+        sort_depth: each batch is first reordered by the Morton code of its
+        points' cells at that depth (nglod_sort_points; None: as given)."""
         import torch
         self.torch = torch
         self.svo = svo
@@ -30,6 +33,8 @@ class Trainer:
         self.v = [torch.zeros_like(p) for p in self.params]
         self.lr = lr
         self.mma = mma
+        self.sort_depth = None if sort_depth is None else min(int(sort_depth), 7)
+        self.sort_buf = {}
         self.t = 0
         self.L = len(self.D)
 
@@ -39,6 +44,8 @@ class Trainer:
         lods = lods or list(range(1, self.L + 1))
         loss = torch.zeros(self.L, dtype=torch.float32, device=x.device)
         Q = int(x.shape[0])
+        if self.sort_depth:
+            x, target, _ = ng.sort_points(x, target, self.sort_depth, out=self.sort_buf)
         ng.sdf_l2_backward(self.svo, self.F, self.D, x, target, lods, 1.0 / Q, self.grads, loss, mma=self.mma)
         self.t += 1
         for p, g, m, v in zip(self.params, self.gparams, self.m, self.v):

@@ -40,8 +40,11 @@ def close(a, b, what):
     assert np.linalg.norm(a - b) <= 2.0 ** -7 * np.linalg.norm(b), (what, np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
-@pytest.mark.parametrize("in_dim,fdt", [(32, "f32"), (35, "f16")])
-def test_tc_backward_matches_fp32(ng, in_dim, fdt):
+@pytest.mark.parametrize("in_dim,fdt,order", [(32, "f32", "given"), (35, "f16", "given"), (32, "f32", "sorted"),
+                                               (35, "f32", "sorted")])
+def test_tc_backward_matches_fp32(ng, in_dim, fdt, order):
+    # "sorted": the points reordered by their depth-7 cells, so the warps'
+    # corner updates merge (one atomic per block of samples in a voxel)
     sc, oc = S.csg_workload(64, seed=0, max_lod=5)
     feats = S.init_features(oc, seed=2, sigma=0.1)
     decs = firm_decoders(5, in_dim)
@@ -52,6 +55,9 @@ def test_tc_backward_matches_fp32(ng, in_dim, fdt):
     lods = [2, 4, 5]
     g = np.random.default_rng(4).normal(size=(len(lods), len(x))).astype(np.float32)
     xt, gt = torch.from_numpy(x).cuda(), torch.from_numpy(g).cuda()
+    if order == "sorted":
+        xt, _, perm = ng.sort_points(xt, None, 7)
+        gt = gt[:, perm.long()].contiguous()
     ref = ng.sdf_backward(svo, F, D, xt, lods, gt)
     got = ng.sdf_backward(svo, F, D, xt, lods, gt, mma="bf16")
     for li in range(5):
