@@ -284,8 +284,10 @@ size_t sphere_trace_workspace(int64_t R);
  *                       256 + 4R rounded up to 256; trace_normals reads them.
  *                       The rest holds the order in which 32-ray groups are
  *                       handed to the persistent trace (by decreasing longest
- *                       list, so long rays start early); it changes only the
- *                       schedule, never a ray's outputs.
+ *                       list, so long rays start early; it changes only the
+ *                       schedule, never a ray's outputs) and, per hit-list
+ *                       position, the ReLU mask of the hit's last decode
+ *                       (128 bits), which trace_normals reuses.
  * Outputs: t_hit [R] (+inf on miss), hit [R] uint8, steps [R] int32
  * (nullable: decodes taken), normal [R, 3] (nullable; normalised analytic
  * gradient of the decoded SDF at the hit point in FP32, or its central
@@ -481,10 +483,13 @@ int sphere_trace_batch_status(nglod_batch* batch, void* stream);
 void sphere_trace_batch_free(nglod_batch* batch);
 
 /* trace_normals -- surface normals of the rays a preceding sphere_trace call
- * (same work buffer, same stream, want_normals = 0 or 1) marked as hits:
+ * (same work buffer, same stream, same decoder and LOD, want_normals = 0 or
+ * 1) marked as hits:
  * the normalised analytic gradient of the decoded SDF (Eq. 2 chain rule
  * through the trilinear weights, Sec. 3.2) in FP32 at the hit point
- * x = o + t_hit d, using the hit voxel recorded by sphere_trace.  The paper
+ * x = o + t_hit d, using the hit voxel and the ReLU mask of the hit's last
+ * decode recorded by sphere_trace (a blended trace records no masks: the
+ * forward pass is then recomputed in FP32).  The paper
  * takes normals by finite differences (supplementary Sec. A.4); the analytic
  * gradient is their limit.  normal [R, 3]; zero for misses.  Does not
  * synchronise. */

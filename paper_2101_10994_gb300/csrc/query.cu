@@ -198,6 +198,8 @@ struct GradArgs {
     const int32_t* hit_vox;
     const int* hit_count;  // mode 1: number of entries in hit_list
     const int32_t* hit_list;
+    const uint4* hit_mask;  // mode 1: the tracer's ReLU mask per hit-list position (used if *mask_flag)
+    const int* mask_flag;
     long long n;           // mode 0: Q
     int D;
     int mode;              // 0 query gradient, 1 normalised trace normal, 2 out[ray] += w * gradient
@@ -220,6 +222,9 @@ __global__ void __launch_bounds__(kThreads) k_grad(const DecPtrs dp, const Table
     float* gb = gxs[warp];
     const long long n = A.mode >= 1 ? (long long)*A.hit_count : A.n;
     const int dcap = A.dcap > 0 ? A.dcap : kMaxDepth;
+    // trace normals after a tracer that recorded its hits' ReLU masks: no z
+    // gather and no forward pass, v = sum_h W2_h [mask_h] W1[h] directly
+    const bool use_mask = A.mode == 1 && A.hit_mask != nullptr && *A.mask_flag != 0;
     for (long long base = ((long long)blockIdx.x * kWarps + warp) * 32; base < n;
          base += (long long)gridDim.x * kWarps * 32) {
         const long long it = base + lane;
@@ -249,7 +254,7 @@ __global__ void __launch_bounds__(kThreads) k_grad(const DecPtrs dp, const Table
         const int g4 = lane >> 2, l4 = lane & 3, gb4 = g4 << 2;
         const unsigned gm4 = 0xfu << gb4;
 #pragma unroll 1
-        for (int r = 0; r < 4; ++r) {
+        for (int r = 0; r < (use_mask ? 0 : 4); ++r) {
             const int s = r * 8 + g4;
             const int sdd = __shfl_sync(0xffffffffu, dd, s);
             const int svox = __shfl_sync(0xffffffffu, vox, s);
@@ -277,8 +282,29 @@ __global__ void __launch_bounds__(kThreads) k_grad(const DecPtrs dp, const Table
         }
 #pragma unroll
         for (int k = 0; k < K4; ++k) gv[k] = 0.0f;
+        if (use_mask) {
+            const uint4 mk = act ? A.hit_mask[it] : make_uint4(0u, 0u, 0u, 0u);
 #pragma unroll 1
-        for (int h = 0; h < kHidden; ++h) {
+            for (int c = 0; c < 4; ++c) {
+                const uint32_t bits = c == 0 ? mk.x : c == 1 ? mk.y : c == 2 ? mk.z : mk.w;
+#pragma unroll 2
+                for (int hh = 0; hh < 32; ++hh) {
+                    const int h = c * 32 + hh;
+                    const float4* w = reinterpret_cast<const float4*>(sd.W1 + h * K4);
+                    const float gh = ((bits >> hh) & 1u) ? sd.bw[h].y : 0.0f;
+#pragma unroll
+                    for (int j = 0; j < K4 / 4; ++j) {
+                        const float4 ww = w[j];
+                        gv[4 * j] = fmaf(gh, ww.x, gv[4 * j]);
+                        gv[4 * j + 1] = fmaf(gh, ww.y, gv[4 * j + 1]);
+                        gv[4 * j + 2] = fmaf(gh, ww.z, gv[4 * j + 2]);
+                        gv[4 * j + 3] = fmaf(gh, ww.w, gv[4 * j + 3]);
+                    }
+                }
+            }
+        }
+#pragma unroll 1
+        for (int h = 0; h < (use_mask ? 0 : kHidden); ++h) {
             const float4* w = reinterpret_cast<const float4*>(sd.W1 + h * K4);
             float a0 = 0.0f, a1 = 0.0f;
 #pragma unroll
@@ -436,10 +462,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_trace_f32(const DecPtrs dp, con
             }
         }
         __syncwarp();
-        const float dhat = mlp_f32<IN>(sd, dp.b2, zb + lane * kZStride, x0, x1, x2);
+        uint4 mask;
+        const float dhat = mlp_f32<IN, true>(sd, dp.b2, zb + lane * kZStride, x0, x1, x2, &mask);
         __syncwarp();
         if (act) step_update(S, dhat, A, tb);
-        publish_hits(S, A, lane);
+        publish_hits(S, A, lane, mask);
     }
 }
 
@@ -491,10 +518,11 @@ __global__ void __launch_bounds__(kThreads, 3) k_trace_batch_f32(const TraceJob*
                 zr[1] = zc;
             }
             __syncwarp();
-            const float dhat = mlp_f32<IN>(sd, G.b2, zb + lane * kZStride, x0, x1, x2);
+            uint4 mask;
+            const float dhat = mlp_f32<IN, true>(sd, G.b2, zb + lane * kZStride, x0, x1, x2, &mask);
             __syncwarp();
             if (act) step_update(S, dhat, jobs[S.job].A, jobs[S.job].tb);
-            publish_hits_batch(S, jobs);
+            publish_hits_batch(S, jobs, mask);
         }
     }
 }
@@ -787,6 +815,8 @@ int launch_normals(const nglod_decoder* dec, const Tables& tb, const TraceArgs& 
     G.hit_vox = A.hit_vox;
     G.hit_count = A.hit_count;
     G.hit_list = A.hit_list;
+    G.hit_mask = A.hit_mask;
+    G.mask_flag = A.hit_count + (kWsMaskFlagWord - 2);
     G.n = A.R;
     G.D = A.D;
     G.mode = 1;
@@ -1002,6 +1032,12 @@ __global__ void k_order_scatter(const uint8_t* __restrict__ key, long long G, in
 
 }  // namespace
 
+int enable_hit_masks(TraceArgs& A, void* work, cudaStream_t st) {
+    A.hit_mask = reinterpret_cast<uint4*>(static_cast<char*>(work) + trace_ws_mask_offset(A.R));
+    NGLOD_CUDA(cudaMemsetAsync(static_cast<int*>(work) + kWsMaskFlagWord, 1, 1, st));
+    return NGLOD_OK;
+}
+
 int enqueue_ray_order(TraceArgs& A, void* work, cudaStream_t st) {
     const long long R = A.R, G = (R + 31) / 32;
     char* w = static_cast<char*>(work);
@@ -1075,6 +1111,7 @@ extern "C" int sphere_trace(const nglod_svo* svo, const nglod_features* feats, c
     rc = check_decoder(dec);
     if (rc) return rc;
     if ((rc = enqueue_ray_order(A, work, st))) return rc;
+    if ((rc = enable_hit_masks(A, work, st))) return rc;
     if (params->decode_dtype == NGLOD_F32) {
         rc = launch_trace_fp32(dec, tb, A, f16, svo->num_sms, st);
     } else if (params->decode_dtype == NGLOD_BF16 || params->decode_dtype == NGLOD_FP8E4M3) {
@@ -1125,6 +1162,7 @@ int normals_common(const nglod_svo* svo, const nglod_features* feats, const nglo
     A.hit_count = (int*)const_cast<void*>(work) + 2;
     A.hit_vox = (int32_t*)((char*)work + trace_ws_hit_vox_offset());
     A.hit_list = (int32_t*)((char*)work + trace_ws_hit_list_offset(R));
+    A.hit_mask = (uint4*)((char*)work + trace_ws_mask_offset(R));   // used if the header flag says recorded
     const bool f16 = feats->dtype == NGLOD_F16;
     return fd_h > 0.0f ? launch_normals_fd(dec, tb, A, fd_h, normal, f16, svo->num_sms, st)
                        : launch_normals(dec, tb, A, normal, f16, svo->num_sms, st);

@@ -148,24 +148,34 @@ __device__ __forceinline__ bool mma_tile(BfSmem& S, uint32_t taddr, uint32_t& ph
     return ok;
 }
 
-// d = b2 + sum_h W2[h] relu(acc[h] + b1[h] (+ W1x[h] . x)) for this thread's row.
+// d = b2 + sum_h W2[h] relu(acc[h] + b1[h] (+ W1x[h] . x)) for this thread's
+// row; with a mask pointer, also its ReLU mask (bit h: pre_h > 0).
 template <int IN>
-__device__ __forceinline__ float epilogue(const BfSmem& S, uint32_t taddr, float b2, float x0, float x1, float x2) {
+__device__ __forceinline__ float epilogue(const BfSmem& S, uint32_t taddr, float b2, float x0, float x1, float x2,
+                                          uint4* mask = nullptr) {
     const int warp = threadIdx.x >> 5;
     float out = b2;
+    uint32_t m0 = 0u, m1 = 0u, m2 = 0u, m3 = 0u;
 #pragma unroll 1
     for (int c0 = 0; c0 < kHidden; c0 += 32) {
         float v[32];
         tc::tmem_ld32(taddr + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
         tc::tmem_wait_ld();
+        uint32_t bits = 0u;
 #pragma unroll
         for (int i = 0; i < 32; ++i) {
             const float4 e = S.epi[c0 + i];
             float pre = fmaf(v[i], S.acc_scale, e.x);
             if constexpr (IN != kFeatDim) pre = fmaf(e.z, x0, fmaf(e.w, x1, fmaf(S.wx2[c0 + i], x2, pre)));
             out = fmaf(e.y, fmaxf(pre, 0.0f), out);
+            bits |= (pre > 0.0f ? 1u : 0u) << i;
         }
+        m0 = c0 == 0 ? bits : m0;
+        m1 = c0 == 32 ? bits : m1;
+        m2 = c0 == 64 ? bits : m2;
+        m3 = c0 == 96 ? bits : m3;
     }
+    if (mask) *mask = make_uint4(m0, m1, m2, m3);
     return out;
 }
 
@@ -242,9 +252,10 @@ __global__ void __launch_bounds__(kTM, kCtasPerSm) k_trace_bf16(const DecPtrsB d
             drained = false;
             break;
         }
-        const float dhat = wact ? epilogue<IN>(S, taddr, dp.b2, x0, x1, x2) : 0.0f;
+        uint4 mask = make_uint4(0u, 0u, 0u, 0u);
+        const float dhat = wact ? epilogue<IN>(S, taddr, dp.b2, x0, x1, x2, &mask) : 0.0f;
         if (act) step_update(st, dhat, A, tb);
-        publish_hits(st, A, lane);
+        publish_hits(st, A, lane, mask);
     }
     teardown_tmem(S, taddr, drained, phase);
 }
@@ -380,9 +391,10 @@ __global__ void __launch_bounds__(kTM, kCtasPerSm) k_trace_batch(const TraceJob*
                 drained = false;
                 break;
             }
-            const float dhat = wact ? epilogue<IN>(S, taddr, dp.b2, x0, x1, x2) : 0.0f;
+            uint4 mask = make_uint4(0u, 0u, 0u, 0u);
+            const float dhat = wact ? epilogue<IN>(S, taddr, dp.b2, x0, x1, x2, &mask) : 0.0f;
             if (act) step_update(st, dhat, jobs[st.job].A, jobs[st.job].tb);
-            publish_hits_batch(st, jobs);
+            publish_hits_batch(st, jobs, mask);
         }
     }
     teardown_tmem(S, taddr, drained, phase);

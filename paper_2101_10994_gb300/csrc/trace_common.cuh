@@ -36,9 +36,9 @@ __device__ __forceinline__ void stage_decoder(SmemDecoder& sd, const float* __re
 
 // d = W2 . relu(W1 [x, z] + b1) + b2 for the lane's own slot, z read from
 // its staged row (Eq. 2).
-template <int IN>
+template <int IN, bool MASK = false>
 __device__ __forceinline__ float mlp_f32(const SmemDecoder& sd, float b2, const float* zrow, float x0,
-                                         float x1, float x2) {
+                                         float x1, float x2, uint4* mask = nullptr) {
     constexpr int OFF = IN - kFeatDim;
     constexpr int K4 = OFF ? 36 : 32;
     float v[K4];
@@ -57,21 +57,36 @@ __device__ __forceinline__ float mlp_f32(const SmemDecoder& sd, float b2, const 
         v[35] = 0.0f;
     }
     float out = b2;
+    uint32_t m0 = 0u, m1 = 0u, m2 = 0u, m3 = 0u;
+#pragma unroll 1
+    for (int c = 0; c < 4; ++c) {
+        uint32_t bits = 0u;
 #pragma unroll 2
-    for (int h = 0; h < kHidden; ++h) {
-        const float4* w = reinterpret_cast<const float4*>(sd.W1 + h * K4);
-        float a0 = 0.0f, a1 = 0.0f;
+        for (int hh = 0; hh < 32; ++hh) {
+            const int h = c * 32 + hh;
+            const float4* w = reinterpret_cast<const float4*>(sd.W1 + h * K4);
+            float a0 = 0.0f, a1 = 0.0f;
 #pragma unroll
-        for (int j = 0; j < K4 / 4; ++j) {
-            const float4 ww = w[j];
-            a0 = fmaf(ww.x, v[4 * j], a0);
-            a1 = fmaf(ww.y, v[4 * j + 1], a1);
-            a0 = fmaf(ww.z, v[4 * j + 2], a0);
-            a1 = fmaf(ww.w, v[4 * j + 3], a1);
+            for (int j = 0; j < K4 / 4; ++j) {
+                const float4 ww = w[j];
+                a0 = fmaf(ww.x, v[4 * j], a0);
+                a1 = fmaf(ww.y, v[4 * j + 1], a1);
+                a0 = fmaf(ww.z, v[4 * j + 2], a0);
+                a1 = fmaf(ww.w, v[4 * j + 3], a1);
+            }
+            const float2 bw = sd.bw[h];
+            const float pre = a0 + a1 + bw.x;
+            out = fmaf(bw.y, fmaxf(pre, 0.0f), out);
+            if constexpr (MASK) bits |= (pre > 0.0f ? 1u : 0u) << hh;
         }
-        const float2 bw = sd.bw[h];
-        out = fmaf(bw.y, fmaxf(a0 + a1 + bw.x, 0.0f), out);
+        if constexpr (MASK) {
+            m0 = c == 0 ? bits : m0;
+            m1 = c == 1 ? bits : m1;
+            m2 = c == 2 ? bits : m2;
+            m3 = c == 3 ? bits : m3;
+        }
     }
+    if constexpr (MASK) *mask = make_uint4(m0, m1, m2, m3);
     return out;
 }
 
@@ -95,6 +110,10 @@ struct TraceArgs {
     // workspace: the order in which 32-ray groups are handed out (null:
     // index order); longest-working groups first shortens the frame's tail
     const int32_t* order = nullptr;
+    // workspace: the ReLU mask (bit h: pre_h > 0) of each hit's last decode,
+    // at its hit-list position (null: not recorded); the normals need no
+    // forward pass then
+    uint4* hit_mask = nullptr;
 };
 
 // One ray being traced: its list cursor [cur, end) with the current entry's
@@ -131,13 +150,18 @@ __device__ __forceinline__ void finish(RaySlot& S, const TraceArgs& A, bool hit)
 
 // Appends the rays this warp just finished as hits to the hit list (one
 // atomic per warp and step).  Called by the whole warp, converged.
-__device__ __forceinline__ void publish_hits(RaySlot& S, const TraceArgs& A, int lane) {
+__device__ __forceinline__ void publish_hits(RaySlot& S, const TraceArgs& A, int lane,
+                                             uint4 mask = make_uint4(0u, 0u, 0u, 0u)) {
     const unsigned m = __ballot_sync(0xffffffffu, S.hit_ray >= 0);
     if (m) {
         int base = 0;
         if (lane == 0) base = atomicAdd(A.hit_count, __popc(m));
         base = __shfl_sync(0xffffffffu, base, 0);
-        if (S.hit_ray >= 0) A.hit_list[base + __popc(m & ((1u << lane) - 1u))] = S.hit_ray;
+        if (S.hit_ray >= 0) {
+            const int pos = base + __popc(m & ((1u << lane) - 1u));
+            A.hit_list[pos] = S.hit_ray;
+            if (A.hit_mask) A.hit_mask[pos] = mask;
+        }
     }
     S.hit_ray = -1;
 }
@@ -301,10 +325,13 @@ __device__ __forceinline__ void refill_batch(RaySlot& S, RayQueue& Qu, const Job
 }
 
 // Appends finished hits to their own job's hit list.
-__device__ __forceinline__ void publish_hits_batch(RaySlot& S, const TraceJob* __restrict__ jobs) {
+__device__ __forceinline__ void publish_hits_batch(RaySlot& S, const TraceJob* __restrict__ jobs,
+                                                   uint4 mask = make_uint4(0u, 0u, 0u, 0u)) {
     if (S.hit_ray >= 0) {
         const TraceArgs& A = jobs[S.job].A;
-        A.hit_list[atomicAdd(A.hit_count, 1)] = S.hit_ray;
+        const int pos = atomicAdd(A.hit_count, 1);
+        A.hit_list[pos] = S.hit_ray;
+        if (A.hit_mask) A.hit_mask[pos] = mask;
     }
     S.hit_ray = -1;
 }
@@ -337,7 +364,16 @@ inline size_t trace_ws_key_offset(long long R) {
     return trace_ws_order_offset(R) + trace_ws_align(sizeof(int32_t) * (size_t)((R + 31) / 32));
 }
 inline size_t trace_ws_count_offset(long long R) { return trace_ws_key_offset(R) + trace_ws_align((size_t)((R + 31) / 32)); }
-inline size_t trace_ws_size(long long R) { return trace_ws_count_offset(R) + 2 * kOrderBuckets * sizeof(int); }
+// ... then the hits' ReLU masks (16 B per hit-list position); header word 3
+// is nonzero when the last trace recorded them
+inline size_t trace_ws_mask_offset(long long R) {
+    return trace_ws_count_offset(R) + trace_ws_align(2 * kOrderBuckets * sizeof(int));
+}
+inline size_t trace_ws_size(long long R) { return trace_ws_mask_offset(R) + 16 * (size_t)R; }
+constexpr int kWsMaskFlagWord = 3;
+// Points A at the workspace's mask region and marks it as recorded (the
+// tracers that decode one LOD per step fill it).
+int enable_hit_masks(TraceArgs& A, void* work, cudaStream_t st);
 // Enqueues the work-ordered ray-group handout of a trace (sets A.order).
 int enqueue_ray_order(TraceArgs& A, void* work, cudaStream_t st);
 int launch_trace_bf16(const nglod_svo* svo, const nglod_decoder* dec, const Tables& tb, const TraceArgs& A,
