@@ -224,7 +224,8 @@ __global__ void __launch_bounds__(kThreads) k_grad(const DecPtrs dp, const Table
     const int dcap = A.dcap > 0 ? A.dcap : kMaxDepth;
     // trace normals after a tracer that recorded its hits' ReLU masks: no z
     // gather and no forward pass, v = sum_h W2_h [mask_h] W1[h] directly
-    const bool use_mask = A.mode == 1 && A.hit_mask != nullptr && *A.mask_flag != 0;
+    const bool use_mask = A.hit_mask != nullptr && ((A.mode == 1 && *A.mask_flag == 1) ||
+                                                    (A.mode == 2 && *A.mask_flag == 2));
     for (long long base = ((long long)blockIdx.x * kWarps + warp) * 32; base < n;
          base += (long long)gridDim.x * kWarps * 32) {
         const long long it = base + lane;
@@ -599,6 +600,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_trace_blend_f32(const DecPtrs l
         const float x0 = fmaf(S.t, S.dx, S.ox), x1 = fmaf(S.t, S.dy, S.oy), x2 = fmaf(S.t, S.dz, S.oz);
         const float q0 = __fadd_rn(x0, 1.0f), q1 = __fadd_rn(x1, 1.0f), q2 = __fadd_rn(x2, 1.0f);
         float dlo = 0.0f, dhi = 0.0f;
+        uint4 mlo = make_uint4(0u, 0u, 0u, 0u), mhi = mlo;
 #pragma unroll 1
         for (int pass = 0; pass < 2; ++pass) {
             // pass 0: depths 3..D-1 into the rows; pass 1: add depth D
@@ -624,14 +626,21 @@ __global__ void __launch_bounds__(kThreads, 2) k_trace_blend_f32(const DecPtrs l
                 row[1] = zc;
             }
             __syncwarp();
-            const float dv = mlp_f32<IN>(pass ? shi : slo, pass ? hi.b2 : lo.b2, zb + lane * kZStride, x0, x1, x2);
-            if (pass) dhi = dv;
-            else dlo = dv;
+            uint4 mk;
+            const float dv = mlp_f32<IN, true>(pass ? shi : slo, pass ? hi.b2 : lo.b2, zb + lane * kZStride, x0,
+                                               x1, x2, &mk);
+            if (pass) {
+                dhi = dv;
+                mhi = mk;
+            } else {
+                dlo = dv;
+                mlo = mk;
+            }
             __syncwarp();
         }
         const float dhat = fmaf(alpha, dhi - dlo, dlo);
         if (act) step_update(S, dhat, A, tb);
-        publish_hits(S, A, lane);
+        publish_hits(S, A, lane, mlo, mhi);
     }
 }
 
@@ -892,10 +901,13 @@ int launch_normals_blend(const nglod_decoder* lo, const nglod_decoder* hi, float
     G.out = normal;
     G.dcap = A.D - 1;
     G.w = 1.0f - alpha;
+    G.hit_mask = A.hit_mask;                 // the lower LOD's masks, if the trace recorded them
+    G.mask_flag = A.hit_count + (kWsMaskFlagWord - 2);
     int rc = run_grad(lo, tb, G, f16, sms, st);
     if (rc) return rc;
     G.dcap = A.D;
     G.w = alpha;
+    G.hit_mask = A.hit_mask2;
     if ((rc = run_grad(hi, tb, G, f16, sms, st))) return rc;
     k_normalise_hits<<<std::max(1, (int)std::min<long long>((A.R + 255) / 256, (long long)sms * 8)), 256, 0, st>>>(
         A.hit_count, A.hit_list, normal);
@@ -1032,9 +1044,10 @@ __global__ void k_order_scatter(const uint8_t* __restrict__ key, long long G, in
 
 }  // namespace
 
-int enable_hit_masks(TraceArgs& A, void* work, cudaStream_t st) {
+int enable_hit_masks(TraceArgs& A, void* work, cudaStream_t st, bool two) {
     A.hit_mask = reinterpret_cast<uint4*>(static_cast<char*>(work) + trace_ws_mask_offset(A.R));
-    NGLOD_CUDA(cudaMemsetAsync(static_cast<int*>(work) + kWsMaskFlagWord, 1, 1, st));
+    A.hit_mask2 = two ? A.hit_mask + A.R : nullptr;
+    NGLOD_CUDA(cudaMemsetAsync(static_cast<int*>(work) + kWsMaskFlagWord, two ? 2 : 1, 1, st));
     return NGLOD_OK;
 }
 

@@ -570,11 +570,12 @@ __device__ __forceinline__ void gather_pair(const Tables& tb, int dd, int dlo, i
 template <int IN>
 __device__ __forceinline__ int blend_decode(BlendSmem& S, uint32_t taddr, uint32_t& ph_lo, uint32_t& ph_hi,
                                             float b2lo, float b2hi, float alpha, float x0, float x1, float x2,
-                                            bool wact, float& dhat) {
+                                            bool wact, float& dhat, uint4* mlo = nullptr,
+                                            uint4* mhi = nullptr) {
     if (!__syncthreads_and(mma_tile<false>(S.lo, taddr, ph_lo))) return 1;
-    const float dlo = wact ? epilogue<IN>(S.lo, taddr, b2lo, x0, x1, x2) : 0.0f;
+    const float dlo = wact ? epilogue<IN>(S.lo, taddr, b2lo, x0, x1, x2, mlo) : 0.0f;
     if (!__syncthreads_and(mma_tile<false>(S.hi, taddr, ph_hi))) return 2;
-    const float dhi = wact ? epilogue<IN>(S.hi, taddr, b2hi, x0, x1, x2) : 0.0f;
+    const float dhi = wact ? epilogue<IN>(S.hi, taddr, b2hi, x0, x1, x2, mhi) : 0.0f;
     dhat = fmaf(alpha, dhi - dlo, dlo);
     return 0;
 }
@@ -629,14 +630,15 @@ __global__ void __launch_bounds__(kTM, kCtasPerSm) k_trace_blend_bf16(const DecP
             }
         }
         float dhat = 0.0f;
+        uint4 mlo = make_uint4(0u, 0u, 0u, 0u), mhi = mlo;
         failed = blend_decode<IN>(S, taddr, ph_lo, ph_hi, plo.b2, phi.b2, alpha, x0, x1, x2,
-                                  __any_sync(0xffffffffu, act), dhat);
+                                  __any_sync(0xffffffffu, act), dhat, &mlo, &mhi);
         if (failed) {
             if (threadIdx.x == 0) atomicExch(err, kStatusTimeout);
             break;
         }
         if (act) step_update(st, dhat, A, tb);
-        publish_hits(st, A, lane);
+        publish_hits(st, A, lane, mlo, mhi);
     }
     teardown_blend(S, taddr, failed, ph_lo, ph_hi);
 }

@@ -114,6 +114,7 @@ struct TraceArgs {
     // at its hit-list position (null: not recorded); the normals need no
     // forward pass then
     uint4* hit_mask = nullptr;
+    uint4* hit_mask2 = nullptr;   // level blending: the second decoder's masks
 };
 
 // One ray being traced: its list cursor [cur, end) with the current entry's
@@ -151,7 +152,8 @@ __device__ __forceinline__ void finish(RaySlot& S, const TraceArgs& A, bool hit)
 // Appends the rays this warp just finished as hits to the hit list (one
 // atomic per warp and step).  Called by the whole warp, converged.
 __device__ __forceinline__ void publish_hits(RaySlot& S, const TraceArgs& A, int lane,
-                                             uint4 mask = make_uint4(0u, 0u, 0u, 0u)) {
+                                             uint4 mask = make_uint4(0u, 0u, 0u, 0u),
+                                             uint4 mask2 = make_uint4(0u, 0u, 0u, 0u)) {
     const unsigned m = __ballot_sync(0xffffffffu, S.hit_ray >= 0);
     if (m) {
         int base = 0;
@@ -161,6 +163,7 @@ __device__ __forceinline__ void publish_hits(RaySlot& S, const TraceArgs& A, int
             const int pos = base + __popc(m & ((1u << lane) - 1u));
             A.hit_list[pos] = S.hit_ray;
             if (A.hit_mask) A.hit_mask[pos] = mask;
+            if (A.hit_mask2) A.hit_mask2[pos] = mask2;
         }
     }
     S.hit_ray = -1;
@@ -369,11 +372,12 @@ inline size_t trace_ws_count_offset(long long R) { return trace_ws_key_offset(R)
 inline size_t trace_ws_mask_offset(long long R) {
     return trace_ws_count_offset(R) + trace_ws_align(2 * kOrderBuckets * sizeof(int));
 }
-inline size_t trace_ws_size(long long R) { return trace_ws_mask_offset(R) + 16 * (size_t)R; }
+inline size_t trace_ws_size(long long R) { return trace_ws_mask_offset(R) + 32 * (size_t)R; }
+// header word 3: 1 = one mask per hit (plain traces), 2 = two (blended: the
+// lower LOD's at [0, R), the upper's at [R, 2R)), 0 = none
 constexpr int kWsMaskFlagWord = 3;
-// Points A at the workspace's mask region and marks it as recorded (the
-// tracers that decode one LOD per step fill it).
-int enable_hit_masks(TraceArgs& A, void* work, cudaStream_t st);
+// Points A at the workspace's mask region(s) and marks them as recorded.
+int enable_hit_masks(TraceArgs& A, void* work, cudaStream_t st, bool two = false);
 // Enqueues the work-ordered ray-group handout of a trace (sets A.order).
 int enqueue_ray_order(TraceArgs& A, void* work, cudaStream_t st);
 int launch_trace_bf16(const nglod_svo* svo, const nglod_decoder* dec, const Tables& tb, const TraceArgs& A,
