@@ -309,6 +309,29 @@ def run_ours(args, rank, world, local_rank):
                                      hit_pixels=int(fr.out["hit"].sum().item()))
         del fr
 
+    # ---- the BF16 frame with FP16 corner features (half the gathered bytes) ----
+    if "bf16" in modes:
+        f16 = ng.Features(W["feats"], "f16")
+        fr = FrameRenderer(svo, f16, dec, o, d, W["lod"], chunks=CHUNKS, eps=W["eps"], far=W["far"],
+                           max_steps=W["max_steps"], decode="bf16", normals=True)
+        hl = []
+        for k in range(args.warmup + args.steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fr.frame()
+            e1.record()
+            e1.synchronize()
+            if k >= args.warmup:
+                hl.append(e0.elapsed_time(e1))
+        fr.check()
+        ms = max_over_ranks(statistics.mean(hl), dev)
+        results["bf16_f16features"] = dict(schedule=f"{CHUNKS} ray chunks on {CHUNKS} streams", ms_per_step=ms,
+                                           rays_per_s=job_rate(R, world, ms * 1e-3),
+                                           queries_per_frame=int(fr.out["steps"].sum().item()),
+                                           hit_pixels=int(fr.out["hit"].sum().item()))
+        del fr, f16
+
     # ---- end to end through the public API with pinned host buffers: each chunk's
     # rays copied in and its t / hit / normals copied out on the chunk's stream ----
     mode = "bf16" if "bf16" in modes else modes[0]
@@ -675,8 +698,9 @@ def main():
             # per frame: traversal (tiles, tile scan, placement) + ray-group order (keys, bucket
             # scan, scatter) + trace + normals, once in the sequential frame and once per chunk in
             # the renderer's frame; the blended frame adds a second gradient pass and the
-            # normalisation
-            "gpu_launches": args.steps * (len(modes) * 8 * (1 + CHUNKS) + ("bf16_blend" in res) * 10 * CHUNKS),
+            # normalisation; the FP16-feature frame runs the renderer's frame once more
+            "gpu_launches": args.steps * (len(modes) * 8 * (1 + CHUNKS) + ("bf16_blend" in res) * 10 * CHUNKS
+                                          + ("bf16_f16features" in res) * 8 * CHUNKS),
         }
         if "bf16" in res and "f32" in res:
             line["bf16_speedup"] = res["f32"]["ms_per_step"] / res["bf16"]["ms_per_step"]

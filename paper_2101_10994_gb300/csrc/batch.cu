@@ -20,6 +20,7 @@
 
 #include "nglod_internal.cuh"
 #include "query_common.cuh"
+#include "scan_common.cuh"
 #include "trace_common.cuh"
 
 struct nglod_batch {
@@ -119,20 +120,10 @@ __global__ void k_batch_keys(const TraceJob* __restrict__ jobs, const JobGroup* 
 
 // One block per group: cursor = exclusive sum of its bucket counts.
 __global__ void k_batch_order_scan(const int* __restrict__ hist, int* __restrict__ cursor) {
-    __shared__ int ws[kOrderBuckets / 32];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int v = hist[blockIdx.x * kOrderBuckets + threadIdx.x];
-    int incl = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += y;
-    }
-    if (lane == 31) ws[w] = incl;
-    __syncthreads();
-    int pre = 0;
-    for (int i = 0; i < w; ++i) pre += ws[i];
-    cursor[blockIdx.x * kOrderBuckets + threadIdx.x] = pre + incl - v;
+    __shared__ int ws[33];
+    int total;
+    const int i = blockIdx.x * kOrderBuckets + threadIdx.x;
+    cursor[i] = block_exclusive_sum(hist[i], ws, total);
 }
 
 __global__ void k_batch_order_scatter(const long long* __restrict__ gbase, int G, long long nchunks,

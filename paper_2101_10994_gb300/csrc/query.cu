@@ -14,6 +14,7 @@
 
 #include "nglod_internal.cuh"
 #include "query_common.cuh"
+#include "scan_common.cuh"
 #include "trace_common.cuh"
 
 namespace nglod {
@@ -1003,22 +1004,13 @@ __global__ void k_group_keys(const int32_t* __restrict__ offs, long long R, uint
         if (h[i]) atomicAdd(&hist[i], h[i]);
 }
 
-// cursor[b] = sum of hist[0..b) (one block of kOrderBuckets threads).
+// cursor[b] = sum of hist[0..b) (one block of kOrderBuckets threads per
+// histogram; block i scans histogram i).
 __global__ void k_order_scan(const int* __restrict__ hist, int* __restrict__ cursor) {
-    __shared__ int ws[kOrderBuckets / 32];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int v = hist[threadIdx.x];
-    int incl = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += y;
-    }
-    if (lane == 31) ws[w] = incl;
-    __syncthreads();
-    int pre = 0;
-    for (int i = 0; i < w; ++i) pre += ws[i];
-    cursor[threadIdx.x] = pre + incl - v;
+    __shared__ int ws[33];
+    int total;
+    const int i = blockIdx.x * kOrderBuckets + threadIdx.x;
+    cursor[i] = block_exclusive_sum(hist[i], ws, total);
 }
 
 // Places every group at its bucket's cursor; lanes of a warp with the same

@@ -16,6 +16,7 @@
 #include <algorithm>
 
 #include "nglod_internal.cuh"
+#include "scan_common.cuh"
 
 namespace nglod {
 namespace {
@@ -56,40 +57,12 @@ __global__ void k_sort_keys(const float* __restrict__ x, long long Q, int depth,
     }
 }
 
-__device__ __forceinline__ int block_scan_excl(int v, int* ws, int& total) {
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    int incl = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += y;
-    }
-    if (lane == 31) ws[w] = incl;
-    __syncthreads();
-    if (w == 0) {
-        const int s = lane < nw ? ws[lane] : 0;
-        int si = s;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, si, o);
-            if (lane >= o) si += y;
-        }
-        if (lane < nw) ws[lane] = si - s;
-        if (lane == 31) ws[32] = si;
-    }
-    __syncthreads();
-    total = ws[32];
-    const int r = ws[w] + incl - v;
-    __syncthreads();
-    return r;
-}
-
 // per block of kScanBlock counts: its sum
 __global__ void k_scan_sums(const int* __restrict__ count, long long n, int* __restrict__ bsum) {
     __shared__ int ws[33];
     const long long i = (long long)blockIdx.x * kScanBlock + threadIdx.x;
     int total;
-    block_scan_excl(i < n ? count[i] : 0, ws, total);
+    block_exclusive_sum(i < n ? count[i] : 0, ws, total);
     if (threadIdx.x == 0) bsum[blockIdx.x] = total;
 }
 
@@ -102,7 +75,7 @@ __global__ void k_scan_top(int* __restrict__ bsum, int nb) {
     for (int b0 = 0; b0 < nb; b0 += kScanBlock) {
         const int i = b0 + threadIdx.x;
         int total;
-        const int e = block_scan_excl(i < nb ? bsum[i] : 0, ws, total);
+        const int e = block_exclusive_sum(i < nb ? bsum[i] : 0, ws, total);
         if (i < nb) bsum[i] = carry + e;
         __syncthreads();
         if (threadIdx.x == 0) carry += total;
@@ -116,7 +89,7 @@ __global__ void k_scan_apply(const int* __restrict__ count, long long n, const i
     __shared__ int ws[33];
     const long long i = (long long)blockIdx.x * kScanBlock + threadIdx.x;
     int total;
-    const int e = block_scan_excl(i < n ? count[i] : 0, ws, total);
+    const int e = block_exclusive_sum(i < n ? count[i] : 0, ws, total);
     if (i < n) cursor[i] = bsum[blockIdx.x] + e;
 }
 
