@@ -309,6 +309,25 @@ def run_ours(args, rank, world, local_rank):
                                      hit_pixels=int(fr.out["hit"].sum().item()))
         del fr
 
+    # ---- standalone sdf_query: 2^22 points uniform inside the target-level voxels ----
+    from paper_2101_10994_gb300 import scenes as S
+    xq = torch.from_numpy(S.points_in_voxels(W["octree"], W["lod"] + S.FIRST_FEATURE_DEPTH - 1, 1 << 22, 21)).to(dev)
+    for qm in [m for m in ("f32", "bf16") if m in modes]:
+        ql = []
+        for k in range(args.warmup + args.steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            ng.sdf_query(svo, feats, dec, xq, W["lod"], decode=qm)
+            e1.record()
+            e1.synchronize()
+            if k >= args.warmup:
+                ql.append(e0.elapsed_time(e1))
+        ms = max_over_ranks(statistics.mean(ql), dev)
+        results[f"sdf_query_{qm}"] = dict(points=int(xq.shape[0]), ms_per_call=ms,
+                                          queries_per_s=world * xq.shape[0] / (ms * 1e-3))
+    del xq
+
     # ---- the BF16 frame with FP16 corner features (half the gathered bytes) ----
     if "bf16" in modes:
         f16 = ng.Features(W["feats"], "f16")
@@ -399,6 +418,19 @@ def traversal_bytes(W, sizes):
     return 36 * R + 16 * visits + 36 * H
 
 
+def cpu_model():
+    """The host CPU's model name (Linux /proc/cpuinfo), for the CPU baseline."""
+    try:
+        for line in open("/proc/cpuinfo"):
+            k, _, v = line.partition(":")
+            if k.strip().lower() in ("model name", "cpu model", "hardware"):
+                return v.strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
 def traversal_roofline(W, res, mode, peaks):
     """The traversal (k_traverse + tile scan + placement, 3 launches) against
     HBM; it is issue-bound on the slab tests, so this fraction is low."""
@@ -406,9 +438,13 @@ def traversal_roofline(W, res, mode, peaks):
     nbytes = traversal_bytes(W, res["level_sizes"])
     sec = res["ms_traverse"] * 1e-3
     achieved = nbytes / sec / 1e9
+    # the lower bound of any design: rays in, the final CSR lists out
+    sizes = res["level_sizes"]
+    lower = 24 * sizes[0] + 4 * (sizes[0] + 1) + 12 * sizes[-1]
     return {"bound": "hbm", "kernel": "k_traverse", "achieved": achieved, "peak": hbm, "unit": "GB/s",
             "frac": achieved / hbm, "traffic": profiled_traffic("k_traverse"),
             "bytes_per_frame": nbytes, "launches_per_frame": 3,
+            "lower_bound_bytes": lower, "lower_bound_frac": lower / sec / 1e9 / hbm,
             "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in peaks else "fallback",
             "timing": "CUDA events around svo_trace_rays (3 launches + the H read-back)",
             "note": "issue-bound on the 8-child slab tests (ncu: ~64 % issue active); node records hit L1/L2"}
@@ -485,7 +521,7 @@ def run_reference(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "csg64_seed0_lod5_1920x1080", "lod": 5, "rays": R, "max_steps": 128,
                        "eps": 1e-3, "decoder": "32->128->1 readout-embedded", "l2": "n/a (CPU)"},
-            "cpu_baseline": {"value": v, "unit": "rays/s", "cores": cores, "kind": "oracle",
+            "cpu_baseline": {"value": v, "unit": "rays/s", "cores": cores, "kind": "oracle", "cpu": cpu_model(),
                              "sample": f"per step a uniform random sample of the 1920x1080 frame's rays "
                                        f"(~{budget:.0f} s of CPU work), FP64 oracle: brute-force traversal + "
                                        f"sphere trace + normals"},
@@ -698,9 +734,11 @@ def main():
             # per frame: traversal (tiles, tile scan, placement) + ray-group order (keys, bucket
             # scan, scatter) + trace + normals, once in the sequential frame and once per chunk in
             # the renderer's frame; the blended frame adds a second gradient pass and the
-            # normalisation; the FP16-feature frame runs the renderer's frame once more
+            # normalisation; the FP16-feature frame runs the renderer's frame once more; each
+            # standalone sdf_query is one launch
             "gpu_launches": args.steps * (len(modes) * 8 * (1 + CHUNKS) + ("bf16_blend" in res) * 10 * CHUNKS
-                                          + ("bf16_f16features" in res) * 8 * CHUNKS),
+                                          + ("bf16_f16features" in res) * 8 * CHUNKS
+                                          + sum(k.startswith("sdf_query_") for k in res)),
         }
         if "bf16" in res and "f32" in res:
             line["bf16_speedup"] = res["f32"]["ms_per_step"] / res["bf16"]["ms_per_step"]
@@ -709,6 +747,7 @@ def main():
             oracle.build()
             v, n, dt = oracle_rate(W, 15.0)
             line["cpu_baseline"] = {"value": v, "unit": "rays/s", "cores": os.cpu_count(), "kind": "oracle",
+                                    "cpu": cpu_model(),
                                     "sample": f"{n} rays drawn uniformly from the frame, {dt:.1f} s, FP64 "
                                               f"brute-force traversal + sphere trace + normals"}
         print(json.dumps(line))

@@ -561,14 +561,25 @@ def surface_samples(scene: Scene, n: int, seed: int) -> np.ndarray:
     return np.concatenate(out)[:n]
 
 
-def training_batch(scene: Scene, n: int, seed: int, sigma: float = 0.01):
-    """Half near-surface (surface + N(0, sigma^2)), half uniform in [-1,1]^3,
-    with float32 targets from the exact scene SDF (Sec. 3.3 sampling)."""
+def training_batch(scene: Scene, n: int, seed: int, sigma: float = 0.01, mix: str = "half"):
+    """SDF samples with float32 targets from the exact scene SDF (Sec. 3.3
+    sampling).  mix "half": half near-surface (surface + N(0, sigma^2)), half
+    uniform in [-1,1]^3; mix "paper": surface, near-surface and uniform points
+    in the ratio 2:2:1."""
     rng = np.random.default_rng(seed + 7919)
-    n_near = n // 2
-    near = surface_samples(scene, n_near, seed) + rng.normal(0.0, sigma, (n_near, 3))
-    uni = rng.uniform(-1.0, 1.0, (n - n_near, 3))
-    x = np.clip(np.concatenate([near, uni]), -1.0, 1.0).astype(np.float32)
+    if mix == "paper":
+        n_surf, n_near = 2 * n // 5, 2 * n // 5
+        surf = surface_samples(scene, n_surf, seed)
+        near = surface_samples(scene, n_near, seed + 1) + rng.normal(0.0, sigma, (n_near, 3))
+        parts = [surf, near]
+    elif mix == "half":
+        n_near = n // 2
+        parts = [surface_samples(scene, n_near, seed) + rng.normal(0.0, sigma, (n_near, 3))]
+    else:
+        raise ValueError(f"training_batch: unknown mix {mix!r}")
+    n_uni = n - sum(len(p) for p in parts)
+    parts.append(rng.uniform(-1.0, 1.0, (n_uni, 3)))
+    x = np.clip(np.concatenate(parts), -1.0, 1.0).astype(np.float32)
     return x, scene_sdf(scene, x.astype(np.float64)).astype(np.float32)
 
 
