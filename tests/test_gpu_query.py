@@ -89,3 +89,25 @@ def test_query_rejects_bad_args(ng):
         ng.sdf_query(svo, F, bad, x, 1)
     assert e.value.code == ng.ERR_NOT_SUPPORTED
     assert ng.sdf_query(svo, F, dec, torch.zeros((0, 3), device="cuda"), 1).numel() == 0
+
+
+def test_query_full_size_sampled(ng, oracle_mod):
+    # the benchmark's standalone configuration: 2^22 points uniform inside the
+    # LOD-5 voxels of CSG-64, readout decoder, one call; 6000 sampled outputs
+    # against the oracle (FP32 within 1e-5, BF16 within its rounding bound
+    # 2^-8 |z_c| for the readout channel c)
+    sc, oc = S.csg_workload(64, seed=0, max_lod=5)
+    feats, dec = S.readout_features(oc, sc), S.readout_decoder(5)
+    svo = ng.svo_build(oc.keys)
+    ora = oracle_mod.OracleSVO(oc.keys)
+    x = S.points_in_voxels(oc, 7, 1 << 22, 21)
+    F, D = ng.Features(feats), ng.DecoderDev.from_decoder(dec)
+    xt = torch.from_numpy(x).cuda()
+    sel = np.random.default_rng(0).choice(len(x), 6000, replace=False)
+    ref, _ = ora.sdf_query(feats, dec, x[sel], 5)
+    z = ora.feature_sum(feats, x[sel], 5)[:, 4]
+    got = ng.sdf_query(svo, F, D, xt, 5).cpu().numpy()[sel].astype(np.float64)
+    assert np.abs(got - ref).max() <= TOL
+    got = ng.sdf_query(svo, F, D, xt, 5, decode="bf16").cpu().numpy()[sel].astype(np.float64)
+    assert np.all(np.abs(got - ref) <= 2.0 ** -8 * np.abs(z) + TOL)
+    svo.free()
