@@ -568,7 +568,7 @@ def run_batch(args):
         B.per_scene_frame(jobs, decode="bf16")
 
     rnd = B.BatchRenderer(jobs, decode="bf16")
-    best, tune = B.autotune(rnd, reps=3)
+    best, tune = B.autotune(rnd, streams=[0, 2, 4, 8], reps=3)
     rnd.frame()
     rnd.check()
     rnd.capture()
@@ -594,7 +594,8 @@ def run_batch(args):
                    "l2": "flushed between steps (256 MB write)", "parallelism": "single GPU"},
         "schedules_ms": {"per_scene_calls": ms_scene, "persistent_launch": ms_batch, "graph_replay": ms_graph},
         "speedup_vs_per_scene": ms_scene / ms_graph,
-        "autotune": {"best_ctas_per_sm": best, "ms": tune},
+        "autotune": {"best_ctas_per_sm": best[0], "best_traversal_streams": best[1],
+                     "ms_by_ctas_per_sm_and_streams": tune},
         "hit_pixels": hits,
         "clocks": sampler.summary(),
         # per graph replay: each job's traversal (3 launches), the reset, the chunk order

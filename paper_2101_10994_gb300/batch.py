@@ -32,7 +32,8 @@ class BatchRenderer:
         self.jobs = jobs
         # the jobs' traversals are independent: they run on a few side streams
         # (forked from and joined back into the frame's stream, also under graph capture)
-        self.tstreams = [torch.cuda.Stream(device=jobs[0].o.device) for _ in range(max(0, traversal_streams))]
+        self.stream_pool = [torch.cuda.Stream(device=jobs[0].o.device) for _ in range(max(0, traversal_streams))]
+        self.tstreams = list(self.stream_pool)
         # the batched trace leaves the normals to frame(), which spreads the jobs'
         # normal kernels over the side streams
         self.normals = bool(normals)
@@ -178,21 +179,40 @@ class BatchRenderer:
         return statistics.median(ts)
 
 
-def autotune(renderer: BatchRenderer, candidates=None, reps=3):
-    """Picks the trace kernel's CTAs per SM by timing each candidate on the
-    renderer's own batch; leaves the renderer configured with the best."""
+def set_traversal_streams(renderer: BatchRenderer, n: int):
+    """Spreads the jobs' traversals and normals over n side streams (0: the
+    frame's own stream); n is capped by the renderer's stream pool, which
+    grows on demand."""
+    import torch
+    while len(renderer.stream_pool) < n:
+        renderer.stream_pool.append(torch.cuda.Stream(device=renderer.jobs[0].o.device))
+    renderer.tstreams = renderer.stream_pool[:max(0, n)]
+    renderer.graph = None
+
+
+def autotune(renderer: BatchRenderer, candidates=None, streams=None, reps=3):
+    """Picks the trace kernel's CTAs per SM (queries in flight per SM: 128
+    per CTA) and the number of side streams for the jobs' traversals and
+    normals, by timing every pair on the renderer's own batch; leaves the
+    renderer configured with the best.  Returns ((ctas, streams), timings)
+    with timings keyed "ctas/streams"."""
     cands = candidates or ([1, 2, 3] if renderer.decode == "f32" else [1, 2, 3, 4])
+    scands = streams if streams is not None else [len(renderer.tstreams)]
     timings = {}
     for c in cands:
         renderer.ctas_per_sm = c
         renderer._create()
-        renderer.frame()
-        renderer.check()
-        timings[c] = renderer.time_frames(reps)
-    best = min(timings, key=timings.get)
-    renderer.ctas_per_sm = best
+        for n in scands:
+            set_traversal_streams(renderer, n)
+            renderer.frame()
+            renderer.check()
+            timings[f"{c}/{n}"] = renderer.time_frames(reps)
+    key = min(timings, key=timings.get)
+    c, n = (int(v) for v in key.split("/"))
+    renderer.ctas_per_sm = c
     renderer._create()
-    return best, timings
+    set_traversal_streams(renderer, n)
+    return (c, n), timings
 
 
 def per_scene_frame(jobs, eps=1e-3, far=5.0, max_steps=128, decode="bf16", normals=True):

@@ -99,8 +99,9 @@ def test_batch_graph_replay_and_autotune(ng, items):
     from paper_2101_10994_gb300 import batch as B
     jobs = make_jobs(ng, items, "bf16")
     rnd = B.BatchRenderer(jobs, decode="bf16")
-    best, timings = B.autotune(rnd, reps=2)
-    assert best in (1, 2, 3, 4) and set(timings) == {1, 2, 3, 4}
+    best, timings = B.autotune(rnd, streams=[0, 2], reps=2)
+    assert best[0] in (1, 2, 3, 4) and best[1] in (0, 2)
+    assert set(timings) == {f"{c}/{n}" for c in (1, 2, 3, 4) for n in (0, 2)}
     rnd.frame()
     rnd.check()
     first = [{k: v.clone() for k, v in rnd.outputs(i).items()} for i in range(len(jobs))]
