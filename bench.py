@@ -35,7 +35,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "sphere-traced rays/s and SDF queries/s at 1080p LOD5, bf16 vs fp32, % roofline"
-CHUNKS = 2          # ray chunks (and streams) of the frame renderer
+CHUNKS = 2          # ray chunks (and streams) of the blended frame renderer
 PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
 CSRC = os.path.join(ROOT, "paper_2101_10994_gb300", "csrc")
 KERNEL_SRC = {"k_traverse": ["traverse.cu", "nglod_internal.cuh"],
@@ -176,7 +176,7 @@ def run_ours(args, rank, world, local_rank):
     import torch
 
     from paper_2101_10994_gb300 import nglod as ng
-    from paper_2101_10994_gb300.frame import FrameRenderer
+    from paper_2101_10994_gb300.frame import FrameRenderer, autotune_frame
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     W = workload(args.width, args.height)
@@ -211,6 +211,7 @@ def run_ours(args, rank, world, local_rank):
         return lists
 
     results = {}
+    configs = {}
     clock_info = None
     for mode in modes:
         out = dict(t=torch.empty(R, device=dev), hit=torch.empty(R, dtype=torch.uint8, device=dev),
@@ -247,10 +248,11 @@ def run_ours(args, rank, world, local_rank):
         hits = int(out["hit"].sum().item())
         lists = step(mode, out, wev)
         sizes = lists.level_sizes()
-        # the frame as the library's frame renderer runs it: two chunks of rays on two
-        # streams (traversal, trace and normals of one chunk overlap the other's)
-        fr = FrameRenderer(svo, feats, dec, o, d, W["lod"], chunks=CHUNKS, eps=W["eps"], far=W["far"],
-                           max_steps=W["max_steps"], decode=mode, normals=True)
+        # the frame as the library's frame renderer runs it: the rays in chunks on as many
+        # streams (traversal, trace and normals of one chunk overlap the others'), the chunk
+        # count and the trace's CTAs per SM picked by its autotuner (untimed)
+        fr, tune = autotune_frame(svo, feats, dec, o, d, W["lod"], eps=W["eps"], far=W["far"],
+                                  max_steps=W["max_steps"], decode=mode, normals=True)
         for _ in range(args.warmup):
             flush.zero_()
             fr.frame()
@@ -274,8 +276,12 @@ def run_ours(args, rank, world, local_rank):
         ms_seq = ms_step
         ms_step = max_over_ranks(sum(a.elapsed_time(b) for a, b in fev), dev) / args.steps
         assert torch.equal(fr.out["t"], out["t"]) and torch.equal(fr.out["normal"], out["normal"])
+        chunks, ctas = len(fr.chunks), fr.ctas_per_sm
+        configs[mode] = (chunks, ctas)
         del fr
-        results[mode] = dict(level_sizes=sizes, schedule=f"{CHUNKS} ray chunks on {CHUNKS} streams",
+        results[mode] = dict(level_sizes=sizes, chunks=chunks, trace_ctas_per_sm=ctas,
+            schedule=f"{chunks} ray chunks on {chunks} streams, trace CTAs/SM {ctas or 'max'} (autotuned)",
+            autotune_ms_by_chunks_and_ctas=tune,
             ms_sequential=ms_seq, rays_per_s_sequential=job_rate(R, world, ms_seq * 1e-3),
             ms_per_step=ms_step, rays_per_s=job_rate(R, world, ms_step * 1e-3),
             queries_per_s=world * queries / args.steps / (sum(trace) / args.steps * 1e-3),
@@ -331,8 +337,8 @@ def run_ours(args, rank, world, local_rank):
     # ---- the BF16 frame with FP16 corner features (half the gathered bytes) ----
     if "bf16" in modes:
         f16 = ng.Features(W["feats"], "f16")
-        fr = FrameRenderer(svo, f16, dec, o, d, W["lod"], chunks=CHUNKS, eps=W["eps"], far=W["far"],
-                           max_steps=W["max_steps"], decode="bf16", normals=True)
+        fr = FrameRenderer(svo, f16, dec, o, d, W["lod"], chunks=configs["bf16"][0], ctas_per_sm=configs["bf16"][1],
+                           eps=W["eps"], far=W["far"], max_steps=W["max_steps"], decode="bf16", normals=True)
         hl = []
         for k in range(args.warmup + args.steps):
             flush.zero_()
@@ -345,7 +351,7 @@ def run_ours(args, rank, world, local_rank):
                 hl.append(e0.elapsed_time(e1))
         fr.check()
         ms = max_over_ranks(statistics.mean(hl), dev)
-        results["bf16_f16features"] = dict(schedule=f"{CHUNKS} ray chunks on {CHUNKS} streams", ms_per_step=ms,
+        results["bf16_f16features"] = dict(schedule="the BF16 frame's", chunks=configs["bf16"][0], ms_per_step=ms,
                                            rays_per_s=job_rate(R, world, ms * 1e-3),
                                            queries_per_frame=int(fr.out["steps"].sum().item()),
                                            hit_pixels=int(fr.out["hit"].sum().item()))
@@ -361,8 +367,9 @@ def run_ours(args, rank, world, local_rank):
              "normal": torch.empty((R, 3), dtype=torch.float32).pin_memory()}
     # the renderer sizes its lists from the rays it is built on; every timed frame then
     # brings its rays in from the host buffers (the device copies are cleared first)
-    fr = FrameRenderer(svo, feats, dec, o.clone(), d.clone(), W["lod"], chunks=CHUNKS, eps=W["eps"], far=W["far"],
-                       max_steps=W["max_steps"], decode=mode, normals=True)
+    ech, ecta = configs[mode]
+    fr = FrameRenderer(svo, feats, dec, o.clone(), d.clone(), W["lod"], chunks=ech, ctas_per_sm=ecta, eps=W["eps"],
+                       far=W["far"], max_steps=W["max_steps"], decode=mode, normals=True)
     e2e_ms = []
     for k in range(args.warmup + args.steps):
         flush.zero_()
@@ -381,7 +388,7 @@ def run_ours(args, rank, world, local_rank):
     e2e = dict(value=job_rate(R, world, e2e_ms_job * 1e-3), unit="rays/s",
                h2d_bytes_per_step=int(h_o.numel() * 4 + h_d.numel() * 4),
                d2h_bytes_per_step=int(sum(v.numel() * v.element_size() for v in h_out.values())),
-               schedule=f"{CHUNKS} chunks on {CHUNKS} streams, copies overlapped with the other chunks' work")
+               schedule=f"{ech} chunks on {ech} streams, copies overlapped with the other chunks' work")
     svo.free()
     return W, results, clock_info, e2e, modes
 
@@ -737,8 +744,9 @@ def main():
             # the renderer's frame; the blended frame adds a second gradient pass and the
             # normalisation; the FP16-feature frame runs the renderer's frame once more; each
             # standalone sdf_query is one launch
-            "gpu_launches": args.steps * (len(modes) * 8 * (1 + CHUNKS) + ("bf16_blend" in res) * 10 * CHUNKS
-                                          + ("bf16_f16features" in res) * 8 * CHUNKS
+            "gpu_launches": args.steps * (sum(8 * (1 + res[m]["chunks"]) for m in modes)
+                                          + ("bf16_blend" in res) * 10 * CHUNKS
+                                          + 8 * res.get("bf16_f16features", {}).get("chunks", 0)
                                           + sum(k.startswith("sdf_query_") for k in res)),
         }
         if "bf16" in res and "f32" in res:

@@ -789,7 +789,7 @@ __global__ void k_normalise_hits(const int* __restrict__ hit_count, const int32_
 
 int launch_trace_fp32(const nglod_decoder* dec, const Tables& tb, const TraceArgs& A, bool f16, int sms,
                       cudaStream_t st) {
-    const int grid = sms * 2;
+    const int grid = sms * (A.ctas_per_sm > 0 ? std::min(A.ctas_per_sm, 2) : 2);
     const DecPtrs P = dec_ptrs(dec);
     if (dec->in_dim == 35) {
         if (f16) launch_trace_f32<__half, 35>(P, tb, A, grid, st); else launch_trace_f32<float, 35>(P, tb, A, grid, st);
@@ -1082,6 +1082,8 @@ extern "C" int sphere_trace(const nglod_svo* svo, const nglod_features* feats, c
     if (!(params->eps > 0.0f) || !(params->far_t > 0.0f) || params->max_steps < 1)
         return fail(NGLOD_ERR_INVALID_ARG, "sphere_trace: eps, far_t and max_steps must be positive");
     if (int e = check_normal_params(params, "sphere_trace")) return e;
+    if (params->ctas_per_sm < 0 || params->ctas_per_sm > 4)
+        return fail(NGLOD_ERR_INVALID_ARG, "sphere_trace: ctas_per_sm must lie in 0..4");
     if (R == 0) return NGLOD_OK;
     if (!o || !d || !ray_offsets || !t_hit || !hit || !work)
         return fail(NGLOD_ERR_INVALID_ARG, "sphere_trace: NULL argument");
@@ -1112,6 +1114,7 @@ extern "C" int sphere_trace(const nglod_svo* svo, const nglod_features* feats, c
     A.hit_count = (int*)work + 2;
     A.hit_vox = (int32_t*)((char*)work + trace_ws_hit_vox_offset());
     A.hit_list = (int32_t*)((char*)work + trace_ws_hit_list_offset(R));
+    A.ctas_per_sm = params->ctas_per_sm;
     NGLOD_CUDA(cudaMemsetAsync(work, 0, 256, st));
     rc = check_decoder(dec);
     if (rc) return rc;

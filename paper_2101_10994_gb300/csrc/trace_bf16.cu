@@ -453,7 +453,7 @@ int launch_trace_bf16(const nglod_svo* svo, const nglod_decoder* dec, const Tabl
     static_assert(sizeof(BfSmem) <= kDynSmem, "shared layout");
     // the error word shares the workspace header with the ray queue
     int* err = A.queue + 1;
-    const int grid = svo->num_sms * kCtasPerSm;
+    const int grid = svo->num_sms * (A.ctas_per_sm > 0 ? std::min(A.ctas_per_sm, kCtasPerSm) : kCtasPerSm);
     const DecPtrsB P = bptrs(dec, fp8 ? kE4M3Max / fp8_z_absmax : 1.0f);
     if (dec->in_dim == 35) {
         if (f16) go_trace<__half, 35>(P, tb, A, err, grid, fp8, st);

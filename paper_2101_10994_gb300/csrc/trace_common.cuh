@@ -115,6 +115,7 @@ struct TraceArgs {
     // forward pass then
     uint4* hit_mask = nullptr;
     uint4* hit_mask2 = nullptr;   // level blending: the second decoder's masks
+    int ctas_per_sm = 0;          // launch width of the persistent trace (0: the most that fit)
 };
 
 // One ray being traced: its list cursor [cur, end) with the current entry's

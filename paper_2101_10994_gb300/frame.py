@@ -22,7 +22,7 @@ class FrameRenderer:
     def __init__(self, svo: ng.SVO, feats: ng.Features, dec: ng.DecoderDev, o, d, lod, chunks: int = 2,
                  eps: float = 1e-3, far: float = 5.0, max_steps: int = 128, decode: str = "bf16",
                  normals: bool = True, headroom: float = 1.25, dec_hi: ng.DecoderDev | None = None,
-                 normal_mode: str = "analytic", fd_h: float = 1e-3):
+                 normal_mode: str = "analytic", fd_h: float = 1e-3, ctas_per_sm: int = 0):
         """lod: an integer LOD, or a continuous L~ (Eq. 3) with dec = LOD floor(L~)'s decoder and
         dec_hi = LOD floor(L~) + 1's; rays then walk their lists at ceil(L~)."""
         import torch
@@ -38,6 +38,7 @@ class FrameRenderer:
         self.R = R = int(self.o.shape[0])
         self.eps, self.far, self.max_steps, self.decode, self.normals = eps, far, max_steps, decode, normals
         self.nopt = dict(normal_mode=normal_mode, fd_h=fd_h)
+        self.ctas_per_sm = int(ctas_per_sm)
         dev = self.o.device
         # chunk bounds on multiples of 128 rays (the traversal's tile)
         n = max(1, int(chunks))
@@ -82,7 +83,7 @@ class FrameRenderer:
         else:
             ng.sphere_trace(self.svo, self.feats, self.dec, oo, dd, c["lists"], eps=self.eps, far=self.far,
                             max_steps=self.max_steps, decode=self.decode, normals=self.normals, stream=st,
-                            out=c["outs"], **self.nopt)
+                            out=c["outs"], ctas_per_sm=self.ctas_per_sm, **self.nopt)
 
     def frame(self, h_in=None, h_out=None):
         """Enqueues one frame after the work already on the current stream,
@@ -117,3 +118,35 @@ class FrameRenderer:
             s = C.c_void_p(c["stream"].cuda_stream)
             ng._check(L.svo_trace_rays_check(c["twork"].data_ptr(), self.lod, stats, s))
             ng._check(L.sphere_trace_status(c["swork"].data_ptr(), s))
+
+
+def autotune_frame(svo: ng.SVO, feats: ng.Features, dec: ng.DecoderDev, o, d, lod, chunk_counts=(1, 2, 3, 4),
+                   ctas=(0, 3, 2), reps: int = 5, **kw):
+    """Times the frame renderer on these rays for every (chunk count, trace
+    CTAs per SM) pair -- fewer trace CTAs per SM leave room for the other
+    chunks' traversal and normals on the same SMs -- and returns the fastest
+    renderer with the timings (ms per frame, keyed "chunks/ctas")."""
+    import torch
+    timings, best, best_ms = {}, None, float("inf")
+    for n in chunk_counts:
+        for c in ctas:
+            fr = FrameRenderer(svo, feats, dec, o, d, lod, chunks=n, ctas_per_sm=c, **kw)
+            for _ in range(2):
+                fr.frame()
+            fr.check()
+            ts = []
+            for _ in range(reps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                fr.frame()
+                e1.record()
+                e1.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            fr.check()
+            ms = sorted(ts)[len(ts) // 2]
+            timings[f"{n}/{c}"] = ms
+            if ms < best_ms:
+                best, best_ms = fr, ms
+            else:
+                del fr
+    return best, timings

@@ -58,7 +58,7 @@ class _TraceJob(C.Structure):
 class _TraceParams(C.Structure):
     _fields_ = [("eps", C.c_float), ("far_t", C.c_float), ("max_steps", C.c_int), ("osc_check", C.c_int),
                 ("decode_dtype", C.c_int), ("want_normals", C.c_int), ("normal_mode", C.c_int),
-                ("fd_h", C.c_float)]
+                ("fd_h", C.c_float), ("ctas_per_sm", C.c_int)]
 
 NORMALS = {"analytic": 0, "fd": 1}
 
@@ -353,11 +353,13 @@ def sdf_query(svo: SVO, feats: Features, dec: DecoderDev, x, lod: int, decode: s
 
 def sphere_trace(svo: SVO, feats: Features, dec: DecoderDev, o, d, lists: RayLists, eps: float = 1e-3,
                  far: float = 5.0, max_steps: int = 128, osc: bool = False, decode: str = "f32",
-                 normals: bool = True, stream=None, out=None, normal_mode: str = "analytic", fd_h: float = 1e-3):
+                 normals: bool = True, stream=None, out=None, normal_mode: str = "analytic", fd_h: float = 1e-3,
+                 ctas_per_sm: int = 0):
     """Sphere-traces every ray through its voxel list; returns a dict of tensors.
 
     normal_mode "analytic" (gradient of the decoded SDF) or "fd" (central
-    differences with step fd_h, supplementary Sec. A.4)."""
+    differences with step fd_h, supplementary Sec. A.4).  ctas_per_sm: the
+    persistent trace's launch width (0: the most that fit)."""
     import torch
     _require_cuda(o, d)
     R = int(o.shape[0])
@@ -369,7 +371,7 @@ def sphere_trace(svo: SVO, feats: Features, dec: DecoderDev, o, d, lists: RayLis
                    normal=torch.empty((R, 3), dtype=torch.float32, device=dev) if normals else None,
                    work=torch.empty(max(lib().sphere_trace_workspace(R), 1), dtype=torch.uint8, device=dev))
     p = _TraceParams(eps, far, max_steps, int(osc), {"f32": F32, "bf16": BF16, "fp8": FP8}[decode], int(normals),
-                     NORMALS[normal_mode], fd_h)
+                     NORMALS[normal_mode], fd_h, int(ctas_per_sm))
     fc, dc = feats.c(), dec.c()
     _check(lib().sphere_trace(svo.h, C.byref(fc), C.byref(dc), o.data_ptr(), d.data_ptr(), R, lists.lod,
                               C.byref(p), lists.ray_offsets.data_ptr(), lists.voxel_id.data_ptr(),
