@@ -59,3 +59,32 @@ def test_chunked_blended_frame_equals_single_pass(ng):
     for k in ("t", "hit", "steps", "normal"):
         assert torch.equal(fr.out[k], ref[k]), k
     svo.free()
+
+
+@pytest.mark.parametrize("decode", ["bf16", "f32"])
+def test_trace_width_and_frame_autotune(ng, decode):
+    # the persistent trace's launch width changes no output; the frame
+    # autotuner returns a renderer whose frame equals the single pass
+    from paper_2101_10994_gb300.frame import autotune_frame
+    sc, oc = S.csg_workload(64, seed=0, max_lod=5)
+    svo = ng.svo_build(oc.keys)
+    F = ng.Features(S.readout_features(oc, sc))
+    D = ng.DecoderDev.from_decoder(S.readout_decoder(5))
+    o, d, _ = S.camera_rays(400, 300, tile=8)
+    to, td = torch.from_numpy(o).cuda(), torch.from_numpy(d).cuda()
+    lists = ng.svo_trace_rays(svo, to, td, 5)
+    ref = ng.sphere_trace(svo, F, D, to, td, lists, decode=decode, normals=True)
+    for c in (1, 2, 3, 4):
+        got = ng.sphere_trace(svo, F, D, to, td, lists, decode=decode, normals=True, ctas_per_sm=c)
+        for k in ("t", "hit", "steps", "normal"):
+            assert torch.equal(got[k], ref[k]), (c, k)
+    with pytest.raises(ng.NglodError) as e:
+        ng.sphere_trace(svo, F, D, to, td, lists, decode=decode, ctas_per_sm=5)
+    assert e.value.code == ng.ERR_INVALID_ARG
+    fr, timings = autotune_frame(svo, F, D, to, td, 5, chunk_counts=(1, 2), ctas=(0, 2), reps=2, decode=decode)
+    assert set(timings) == {"1/0", "1/2", "2/0", "2/2"}
+    fr.frame()
+    fr.check()
+    for k in ("t", "hit", "steps", "normal"):
+        assert torch.equal(fr.out[k], ref[k]), k
+    svo.free()
