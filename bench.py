@@ -35,7 +35,6 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "sphere-traced rays/s and SDF queries/s at 1080p LOD5, bf16 vs fp32, % roofline"
-CHUNKS = 2          # ray chunks (and streams) of the blended frame renderer
 PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
 CSRC = os.path.join(ROOT, "paper_2101_10994_gb300", "csrc")
 KERNEL_SRC = {"k_traverse": ["traverse.cu", "nglod_internal.cuh"],
@@ -295,8 +294,8 @@ def run_ours(args, rank, world, local_rank):
     if "bf16" in modes and W["lod"] >= 2:
         lt = W["lod"] - 0.5
         dlo = ng.DecoderDev.from_decoder(W["dec_lo"])
-        fr = FrameRenderer(svo, feats, dlo, o, d, lt, chunks=CHUNKS, eps=W["eps"], far=W["far"],
-                           max_steps=W["max_steps"], decode="bf16", normals=True, dec_hi=dec)
+        fr, btune = autotune_frame(svo, feats, dlo, o, d, lt, eps=W["eps"], far=W["far"], max_steps=W["max_steps"],
+                                   decode="bf16", normals=True, dec_hi=dec)
         bl = []
         for k in range(args.warmup + args.steps):
             flush.zero_()
@@ -309,7 +308,11 @@ def run_ours(args, rank, world, local_rank):
                 bl.append(e0.elapsed_time(e1))
         fr.check()
         ms = max_over_ranks(statistics.mean(bl), dev)
-        results["bf16_blend"] = dict(lod_tilde=lt, schedule=f"{CHUNKS} ray chunks on {CHUNKS} streams",
+        bch = len(fr.chunks)
+        results["bf16_blend"] = dict(lod_tilde=lt, chunks=bch, trace_ctas_per_sm=fr.ctas_per_sm,
+                                     schedule=f"{bch} ray chunks on {bch} streams, trace CTAs/SM "
+                                              f"{fr.ctas_per_sm or 'max'} (autotuned)",
+                                     autotune_ms_by_chunks_and_ctas=btune,
                                      ms_per_step=ms, rays_per_s=job_rate(R, world, ms * 1e-3),
                                      queries_per_frame=int(fr.out["steps"].sum().item()),
                                      hit_pixels=int(fr.out["hit"].sum().item()))
@@ -745,7 +748,7 @@ def main():
             # normalisation; the FP16-feature frame runs the renderer's frame once more; each
             # standalone sdf_query is one launch
             "gpu_launches": args.steps * (sum(8 * (1 + res[m]["chunks"]) for m in modes)
-                                          + ("bf16_blend" in res) * 10 * CHUNKS
+                                          + 10 * res.get("bf16_blend", {}).get("chunks", 0)
                                           + 8 * res.get("bf16_f16features", {}).get("chunks", 0)
                                           + sum(k.startswith("sdf_query_") for k in res)),
         }

@@ -97,11 +97,10 @@ typedef struct {
                               x +- fd_h e_a and n = normalise of the three
                               differences                                  */
     float fd_h;            /* FD step in scene units, in (0, 1) (FD only)     */
-    int ctas_per_sm;       /* sphere_trace: persistent trace CTAs per SM (0:
-                              the most that fit -- 4 for the tcgen05 decode,
-                              2 for FP32); fewer leave room on each SM for
-                              concurrent kernels of other streams (0..4); the
-                              blended trace always takes the most          */
+    int ctas_per_sm;       /* persistent trace CTAs per SM (0: the most that
+                              fit -- 4 for the tcgen05 decode, 2 for FP32);
+                              fewer leave room on each SM for concurrent
+                              kernels of other streams (0..4)               */
 } nglod_trace_params;
 
 #define NGLOD_NORMALS_ANALYTIC 0

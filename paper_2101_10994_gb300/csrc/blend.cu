@@ -88,6 +88,8 @@ extern "C" int sphere_trace_blend(const nglod_svo* svo, const nglod_features* fe
     if (!(params->eps > 0.0f) || !(params->far_t > 0.0f) || params->max_steps < 1)
         return fail(NGLOD_ERR_INVALID_ARG, "sphere_trace_blend: eps, far_t and max_steps must be positive");
     if ((rc = check_normal_params(params, "sphere_trace_blend"))) return rc;
+    if (params->ctas_per_sm < 0 || params->ctas_per_sm > 4)
+        return fail(NGLOD_ERR_INVALID_ARG, "sphere_trace_blend: ctas_per_sm must lie in 0..4");
     if (R == 0) return NGLOD_OK;
     if (!o || !d || !ray_offsets || !t_hit || !hit || !work)
         return fail(NGLOD_ERR_INVALID_ARG, "sphere_trace_blend: NULL argument");
@@ -118,6 +120,7 @@ extern "C" int sphere_trace_blend(const nglod_svo* svo, const nglod_features* fe
     A.hit_count = (int*)work + 2;
     A.hit_vox = (int32_t*)((char*)work + trace_ws_hit_vox_offset());
     A.hit_list = (int32_t*)((char*)work + trace_ws_hit_list_offset(R));
+    A.ctas_per_sm = params->ctas_per_sm;
     NGLOD_CUDA(cudaMemsetAsync(work, 0, 256, st));
     if ((rc = enqueue_ray_order(A, work, st))) return rc;
     if ((rc = enable_hit_masks(A, work, st, true))) return rc;

@@ -870,7 +870,7 @@ int launch_normals_blend_fd(const nglod_decoder* lo, const nglod_decoder* hi, fl
 int launch_trace_blend_f32(const nglod_decoder* lo, const nglod_decoder* hi, float alpha, const Tables& tb,
                            const TraceArgs& A, bool f16, int sms, cudaStream_t st) {
     go_blend_f32_any(true, lo->in_dim, f16, dec_ptrs(lo), dec_ptrs(hi), alpha, tb, &A, nullptr, 0, A.D, nullptr,
-                     sms * 2, st);
+                     sms * (A.ctas_per_sm > 0 ? std::min(A.ctas_per_sm, 2) : 2), st);
     NGLOD_CUDA(cudaGetLastError());
     return NGLOD_OK;
 }

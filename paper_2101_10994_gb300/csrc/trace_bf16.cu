@@ -736,7 +736,7 @@ int launch_trace_blend_bf16(const nglod_svo* svo, const nglod_decoder* lo, const
                             const Tables& tb, const TraceArgs& A, bool f16, cudaStream_t st) {
     int* err = A.queue + 1;      // the workspace header's status word
     go_blend_any(true, lo->in_dim, f16, bptrs(lo, 1.0f), bptrs(hi, 1.0f), alpha, tb, &A, nullptr, 0, A.D, nullptr,
-                 err, svo->num_sms * kCtasPerSm, st);
+                 err, svo->num_sms * (A.ctas_per_sm > 0 ? std::min(A.ctas_per_sm, kCtasPerSm) : kCtasPerSm), st);
     NGLOD_CUDA(cudaGetLastError());
     return NGLOD_OK;
 }

@@ -79,7 +79,8 @@ class FrameRenderer:
         if self.blend:
             ng.sphere_trace_blend(self.svo, self.feats, self.dec, self.dec_hi, oo, dd, c["lists"], self.lod_tilde,
                                   eps=self.eps, far=self.far, max_steps=self.max_steps, decode=self.decode,
-                                  normals=self.normals, stream=st, out=c["outs"], **self.nopt)
+                                  normals=self.normals, stream=st, out=c["outs"], ctas_per_sm=self.ctas_per_sm,
+                                  **self.nopt)
         else:
             ng.sphere_trace(self.svo, self.feats, self.dec, oo, dd, c["lists"], eps=self.eps, far=self.far,
                             max_steps=self.max_steps, decode=self.decode, normals=self.normals, stream=st,

@@ -436,7 +436,7 @@ def sdf_query_blend(svo: SVO, feats: Features, dec_lo: DecoderDev, dec_hi: Decod
 def sphere_trace_blend(svo: SVO, feats: Features, dec_lo: DecoderDev, dec_hi: DecoderDev | None, o, d,
                        lists: RayLists, lod_tilde: float, eps: float = 1e-3, far: float = 5.0, max_steps: int = 128,
                        osc: bool = False, decode: str = "f32", normals: bool = True, stream=None, out=None,
-                       normal_mode: str = "analytic", fd_h: float = 1e-3):
+                       normal_mode: str = "analytic", fd_h: float = 1e-3, ctas_per_sm: int = 0):
     """Sphere-traces the Eq. 3 blend; ``lists`` must be at LOD ceil(L~)."""
     import torch
     _require_cuda(o, d)
@@ -451,7 +451,7 @@ def sphere_trace_blend(svo: SVO, feats: Features, dec_lo: DecoderDev, dec_hi: De
                    normal=torch.empty((R, 3), dtype=torch.float32, device=dev) if normals else None,
                    work=torch.empty(max(lib().sphere_trace_workspace(R), 1), dtype=torch.uint8, device=dev))
     p = _TraceParams(eps, far, max_steps, int(osc), {"f32": F32, "bf16": BF16, "fp8": FP8}[decode], int(normals),
-                     NORMALS[normal_mode], fd_h)
+                     NORMALS[normal_mode], fd_h, int(ctas_per_sm))
     fc, lo = feats.c(), dec_lo.c()
     hi = (dec_hi or dec_lo).c()
     _check(lib().sphere_trace_blend(svo.h, C.byref(fc), C.byref(lo), C.byref(hi), o.data_ptr(), d.data_ptr(), R,
