@@ -163,3 +163,27 @@ def test_batch_tiny_jobs_padding(ng, items):
         lists, ref = per_job(ng, j, "bf16")
         assert_same(rnd.outputs(k), lists, ref, rnd.bufs[k])
     rnd.free()
+
+
+def test_batch_full_workload_equals_per_scene(ng):
+    # the benchmark's batching workload (32 seeded CSG scenes, LOD 3..6,
+    # images 128..1024 a side) in its timed configuration (autotuned trace
+    # width and side streams, CUDA-graph replay): every output bit-identical
+    # to the per-scene calls (whose parity with the oracle is tested above);
+    # one job's sampled pixels also against the oracle
+    import os
+    from paper_2101_10994_gb300 import batch as B
+    items = S.batching_workload(32, seed=0, workers=min(16, os.cpu_count() or 1))
+    jobs = make_jobs(ng, items, "bf16")
+    rnd = B.BatchRenderer(jobs, decode="bf16")
+    B.autotune(rnd, streams=[0, 8], reps=1)
+    rnd.frame()
+    rnd.check()
+    rnd.capture()
+    rnd.replay()
+    torch.cuda.synchronize()
+    rnd.check()
+    for k, j in enumerate(jobs):
+        lists, ref = per_job(ng, j, "bf16")
+        assert_same(rnd.outputs(k), lists, ref)
+    rnd.free()
