@@ -53,7 +53,7 @@ def parse():
     # itself is always the 1920x1080 LOD 5 CSG-64 frame)
     p.add_argument("--width", type=int, default=1920)
     p.add_argument("--height", type=int, default=1080)
-    p.add_argument("--decode", choices=["both", "all", "f32", "bf16", "fp8"], default="all")
+    p.add_argument("--decode", choices=["both", "all", "f32", "bf16", "fp8", "f32tc"], default="all")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--workload", choices=["frame", "batch", "train"], default="frame",
                    help="frame: the 1080p LOD5 CSG-64 frame (default); batch: 32 seeded CSG scenes of "
@@ -194,6 +194,8 @@ def run_ours(args, rank, world, local_rank):
     if args.decode in ("all", "fp8") and bf16_available():
         modes.append("fp8")
         feats.set_fp8_bound(svo, W["lod"])
+    if args.decode in ("all", "f32tc") and bf16_available():
+        modes.append("f32tc")        # FP32-accurate decode on the tensor cores (three-term BF16 splits)
     dist = world > 1
     if dist:
         import torch.distributed as td

@@ -49,7 +49,7 @@ enum {
 };
 
 /* Element types of features / decode arithmetic. */
-enum { NGLOD_F32 = 0, NGLOD_F16 = 1, NGLOD_BF16 = 2, NGLOD_FP8E4M3 = 3 };
+enum { NGLOD_F32 = 0, NGLOD_F16 = 1, NGLOD_BF16 = 2, NGLOD_FP8E4M3 = 3, NGLOD_F32_SPLIT = 4 };
 
 typedef struct nglod_svo nglod_svo;   /* opaque octree handle */
 
@@ -86,8 +86,9 @@ typedef struct {
     int max_steps;         /* miss after this many decodes (paper: 200)       */
     int osc_check;         /* 1: also stop when |d_k - d_(k-1)| < 6 eps; the
                               ray is then a hit iff |d_k| < 6 eps             */
-    int decode_dtype;      /* NGLOD_F32 (CUDA cores), NGLOD_BF16 or
-                              NGLOD_FP8E4M3 (tcgen05; see sdf_query)         */
+    int decode_dtype;      /* NGLOD_F32 (CUDA cores), NGLOD_BF16,
+                              NGLOD_FP8E4M3 or NGLOD_F32_SPLIT (tcgen05; see
+                              sdf_query)                                     */
     int want_normals;      /* 1: write normals of hit rays                    */
     int normal_mode;       /* NGLOD_NORMALS_ANALYTIC (0): normalised analytic
                               gradient of the decoded SDF (FP32);
@@ -257,7 +258,11 @@ int svo_trace_rays_sizes(const void* work, int64_t* h_sizes, int n, void* stream
  *                 (tensor cores: z scaled by 448 / feats->fp8_z_absmax and
  *                 W1's z columns by 448 / their largest |value| (a per-LOD
  *                 scale), both rounded to e4m3, FP32 accumulation, scales
- *                 undone before the bias).
+ *                 undone before the bias) or NGLOD_F32_SPLIT (tensor cores
+ *                 at FP32 accuracy: z and W1's z columns each split into
+ *                 three BF16 terms, x = x0 + x1 + x2 exactly to 24 bits,
+ *                 and the six products x_i w_j with i + j <= 2 accumulated
+ *                 in FP32; not for level blending or batches).
  * Errors: NGLOD_ERR_INVALID_ARG (lod outside 1..num_depths-3, missing
  * features), NGLOD_ERR_NOT_SUPPORTED (m != 32, hidden != 128, in_dim not 32 or
  * 35, grad with BF16 decode), NGLOD_ERR_TIMEOUT (a bounded tensor-core wait

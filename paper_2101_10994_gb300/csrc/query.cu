@@ -934,14 +934,15 @@ extern "C" int sdf_query(const nglod_svo* svo, const nglod_features* feats, cons
     int rc = fill_tables(svo, feats, lod, tb);
     if (rc) return rc;
     const bool f16 = feats->dtype == NGLOD_F16;
-    if (decode_dtype == NGLOD_BF16 || decode_dtype == NGLOD_FP8E4M3) {
+    if (decode_dtype == NGLOD_BF16 || decode_dtype == NGLOD_FP8E4M3 || decode_dtype == NGLOD_F32_SPLIT) {
         rc = check_decoder(dec);
         if (rc) return rc;
         if (grad) return fail(NGLOD_ERR_NOT_SUPPORTED, "sdf_query: grad needs the FP32 decode");
         const bool fp8 = decode_dtype == NGLOD_FP8E4M3;
         if (fp8 && !(feats->fp8_z_absmax > 0.0f))
             return fail(NGLOD_ERR_INVALID_ARG, "sdf_query: the FP8 decode needs feats->fp8_z_absmax > 0");
-        rc = launch_query_bf16(svo, tb, dec, x, Q, D, sdf, deepest, f16, fp8 ? feats->fp8_z_absmax : 0.0f, st);
+        rc = launch_query_bf16(svo, tb, dec, x, Q, D, sdf, deepest, f16, fp8 ? feats->fp8_z_absmax : 0.0f, st,
+                               decode_dtype == NGLOD_F32_SPLIT);
         if (rc) return rc;
         return NGLOD_OK;
     }
@@ -1122,13 +1123,15 @@ extern "C" int sphere_trace(const nglod_svo* svo, const nglod_features* feats, c
     if ((rc = enable_hit_masks(A, work, st))) return rc;
     if (params->decode_dtype == NGLOD_F32) {
         rc = launch_trace_fp32(dec, tb, A, f16, svo->num_sms, st);
-    } else if (params->decode_dtype == NGLOD_BF16 || params->decode_dtype == NGLOD_FP8E4M3) {
+    } else if (params->decode_dtype == NGLOD_BF16 || params->decode_dtype == NGLOD_FP8E4M3 ||
+               params->decode_dtype == NGLOD_F32_SPLIT) {
         const bool fp8 = params->decode_dtype == NGLOD_FP8E4M3;
         if (fp8 && !(feats->fp8_z_absmax > 0.0f))
             return fail(NGLOD_ERR_INVALID_ARG, "sphere_trace: the FP8 decode needs feats->fp8_z_absmax > 0");
-        rc = launch_trace_bf16(svo, dec, tb, A, f16, fp8 ? feats->fp8_z_absmax : 0.0f, st);
+        rc = launch_trace_bf16(svo, dec, tb, A, f16, fp8 ? feats->fp8_z_absmax : 0.0f, st,
+                               params->decode_dtype == NGLOD_F32_SPLIT);
     } else {
-        return fail(NGLOD_ERR_NOT_SUPPORTED, "sphere_trace: decode_dtype must be F32, BF16 or FP8E4M3");
+        return fail(NGLOD_ERR_NOT_SUPPORTED, "sphere_trace: decode_dtype must be F32, BF16, FP8E4M3 or F32_SPLIT");
     }
     if (rc) return rc;
     if (normal && params->want_normals) {

@@ -55,6 +55,33 @@ constexpr float kE4M3Max = 448.0f;
 // tcgen05.alloc until one of the four finished.
 constexpr int kDynSmem = (int)((sizeof(BfSmem) + 1023) / 1024 * 1024);
 
+// FP32-accurate decode on the tensor cores: z and W1 (z columns) each as a
+// sum of three BF16 terms (x = x0 + x1 + x2, 24 significant bits), and the
+// six products whose magnitude exceeds 2^-24 of the leading one accumulated
+// in FP32 tensor memory.
+struct BfSmem3 {
+    unsigned char A[3][kTM * kFeatDim * 2];
+    unsigned char B[3][kHidden * kFeatDim * 2];
+    float4 epi[kHidden];
+    float wx2[kHidden];
+    float amax[kTM / 32];
+    float acc_scale;
+    uint64_t bar;
+    uint32_t taddr;
+};
+constexpr int kDynSmem3 = (int)((sizeof(BfSmem3) + 1023) / 1024 * 1024);
+
+// precision mode of the tensor-core decode: 0 BF16, 1 FP8-E4M3, 2 FP32 by
+// three-term BF16 splits
+template <int PM>
+struct TcSmem {
+    using type = BfSmem;
+};
+template <>
+struct TcSmem<2> {
+    using type = BfSmem3;
+};
+
 struct DecPtrsB {
     const float* W1;
     const float* b1;
@@ -150,8 +177,8 @@ __device__ __forceinline__ bool mma_tile(BfSmem& S, uint32_t taddr, uint32_t& ph
 
 // d = b2 + sum_h W2[h] relu(acc[h] + b1[h] (+ W1x[h] . x)) for this thread's
 // row; with a mask pointer, also its ReLU mask (bit h: pre_h > 0).
-template <int IN>
-__device__ __forceinline__ float epilogue(const BfSmem& S, uint32_t taddr, float b2, float x0, float x1, float x2,
+template <int IN, class SM>
+__device__ __forceinline__ float epilogue(const SM& S, uint32_t taddr, float b2, float x0, float x1, float x2,
                                           uint4* mask = nullptr) {
     const int warp = threadIdx.x >> 5;
     float out = b2;
@@ -179,7 +206,8 @@ __device__ __forceinline__ float epilogue(const BfSmem& S, uint32_t taddr, float
     return out;
 }
 
-__device__ __forceinline__ void setup_tmem(BfSmem& S) {
+template <class SM>
+__device__ __forceinline__ void setup_tmem(SM& S) {
     if (threadIdx.x == 0) tc::mbar_init(&S.bar, 1);
     if ((threadIdx.x >> 5) == 0) {
         tc::tmem_alloc(&S.taddr, kHidden);
@@ -191,23 +219,115 @@ __device__ __forceinline__ void setup_tmem(BfSmem& S) {
     tc::fence_after_sync();
 }
 
-__device__ __forceinline__ void teardown_tmem(BfSmem& S, uint32_t taddr, bool drained, uint32_t phase) {
+template <class SM>
+__device__ __forceinline__ void teardown_tmem(SM& S, uint32_t taddr, bool drained, uint32_t phase) {
     if (!drained) tc::mbar_wait(&S.bar, phase ^ 1u, kWaitPolls);   // let an expired MMA finish
     tc::fence_before_sync();
     __syncthreads();
     if ((threadIdx.x >> 5) == 0) tc::tmem_dealloc(taddr, kHidden);
 }
 
+// Three BF16 terms of v: t0 = bf16(v), t1 = bf16(v - t0), t2 = bf16(v - t0 - t1)
+// (each difference exact in FP32).
+__device__ __forceinline__ void split3(float v, __nv_bfloat16& t0, __nv_bfloat16& t1, __nv_bfloat16& t2) {
+    t0 = __float2bfloat16_rn(v);
+    const float r1 = v - __bfloat162float(t0);
+    t1 = __float2bfloat16_rn(r1);
+    t2 = __float2bfloat16_rn(r1 - __bfloat162float(t1));
+}
+
+template <int IN>
+__device__ __forceinline__ void stage_split_decoder(BfSmem3& S, const DecPtrsB& dp) {
+    constexpr int OFF = IN - kFeatDim;
+    for (int i = threadIdx.x; i < kHidden * kFeatDim; i += blockDim.x) {
+        const int h = i / kFeatDim, k = i - h * kFeatDim;
+        __nv_bfloat16 t[3];
+        split3(dp.W1[h * IN + OFF + k], t[0], t[1], t[2]);
+        const uint32_t o = tc::kmajor_offset(h, k, kKc);
+#pragma unroll
+        for (int p = 0; p < 3; ++p) *reinterpret_cast<__nv_bfloat16*>(S.B[p] + o) = t[p];
+    }
+    if (threadIdx.x == 0) S.acc_scale = 1.0f;
+    for (int h = threadIdx.x; h < kHidden; h += blockDim.x) {
+        const float x0 = OFF ? dp.W1[h * IN] : 0.f, x1 = OFF ? dp.W1[h * IN + 1] : 0.f;
+        S.epi[h] = make_float4(dp.b1[h], dp.W2[h], x0, x1);
+        S.wx2[h] = OFF ? dp.W1[h * IN + 2] : 0.f;
+    }
+}
+
+// This lane's four z channels of A-tile row `row`, as three BF16 planes.
+__device__ __forceinline__ void put_z_split(BfSmem3& S, int row, int l, float4 z) {
+    const float zz[4] = {z.x, z.y, z.z, z.w};
+    __nv_bfloat16 t[3][4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) split3(zz[c], t[0][c], t[1][c], t[2][c]);
+    const uint32_t o = tc::kmajor_offset(row, 4 * l, kKc);
+#pragma unroll
+    for (int p = 0; p < 3; ++p) {
+        const __nv_bfloat162 lo = __halves2bfloat162(t[p][0], t[p][1]);
+        const __nv_bfloat162 hi = __halves2bfloat162(t[p][2], t[p][3]);
+        uint2 v;
+        v.x = *reinterpret_cast<const uint32_t*>(&lo);
+        v.y = *reinterpret_cast<const uint32_t*>(&hi);
+        *reinterpret_cast<uint2*>(S.A[p] + o) = v;
+    }
+}
+
+// The six products A_i B_j (i + j <= 2), smallest first, into one FP32
+// accumulator; issued by thread 0, waited for by all (bounded).
+__device__ __forceinline__ bool mma_tile_split(BfSmem3& S, uint32_t taddr, uint32_t& phase) {
+    tc::fence_proxy_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        tc::fence_after_sync();
+        constexpr int kPi[6] = {2, 1, 0, 1, 0, 0}, kPj[6] = {0, 1, 2, 0, 1, 0};
+        const uint32_t idesc = tc::idesc_bf16_f32(kTM, kHidden);
+#pragma unroll
+        for (int t = 0; t < 6; ++t) {
+            const uint32_t a0 = tc::smem_u32(S.A[kPi[t]]), b0 = tc::smem_u32(S.B[kPj[t]]);
+#pragma unroll
+            for (int ks = 0; ks < kFeatDim / 16; ++ks)
+                tc::mma_bf16(taddr, tc::smem_desc_kmajor(a0 + ks * 256, kLbo, kSbo),
+                             tc::smem_desc_kmajor(b0 + ks * 256, kLbo, kSbo), idesc, t > 0 || ks > 0);
+        }
+        tc::mma_commit(&S.bar);
+    }
+    const bool ok = tc::mbar_wait(&S.bar, phase, kWaitPolls);
+    phase ^= 1u;
+    tc::fence_after_sync();
+    return ok;
+}
+
+template <int IN, int PM>
+__device__ __forceinline__ void stage_any(typename TcSmem<PM>::type& S, const DecPtrsB& dp) {
+    if constexpr (PM == 2) stage_split_decoder<IN>(S, dp);
+    else stage_bf16_decoder<IN, PM == 1>(S, dp);
+}
+
+template <int PM>
+__device__ __forceinline__ void put_any(typename TcSmem<PM>::type& S, int row, int l, float4 z, float zs) {
+    if constexpr (PM == 2) put_z_split(S, row, l, z);
+    else put_z<PM == 1>(S, row, l, z, zs);
+}
+
+template <int PM>
+__device__ __forceinline__ bool mma_any(typename TcSmem<PM>::type& S, uint32_t taddr, uint32_t& phase) {
+    if constexpr (PM == 2) return mma_tile_split(S, taddr, phase);
+    else return mma_tile<PM == 1>(S, taddr, phase);
+}
+
 // ---------------------------------------------------------------------------
 // sphere tracing, BF16 decode
 // ---------------------------------------------------------------------------
-template <typename T, int IN, bool FP8>
+template <typename T, int IN, int PM>
 __global__ void __launch_bounds__(kTM, kCtasPerSm) k_trace_bf16(const DecPtrsB dp, const Tables tb, const TraceArgs A,
                                                       int* __restrict__ err) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    BfSmem& S = *reinterpret_cast<BfSmem*>(smem_raw);
+    using SM = typename TcSmem<PM>::type;
+    SM& S = *reinterpret_cast<SM*>(smem_raw);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    stage_bf16_decoder<IN, FP8>(S, dp);
+    stage_any<IN, PM>(S, dp);
     for (int i = threadIdx.x; i < (int)(sizeof(S.A) / 16); i += blockDim.x)
         reinterpret_cast<uint4*>(S.A)[i] = make_uint4(0u, 0u, 0u, 0u);   // rows of idle warps stay finite
     setup_tmem(S);
@@ -242,11 +362,11 @@ __global__ void __launch_bounds__(kTM, kCtasPerSm) k_trace_bf16(const DecPtrsB d
                 const float s2 = __shfl_sync(0xffffffffu, q2, s);
                 float4 za = make_float4(0.f, 0.f, 0.f, 0.f), zb = za;
                 if (sact) gather_slot4<T>(tb, A.D, svox, sijk, s0, s1, s2, gm4, gb4, l4, za, zb);
-                put_z<FP8>(S, warp * 32 + s, 2 * l4, za, dp.z_scale);
-                put_z<FP8>(S, warp * 32 + s, 2 * l4 + 1, zb, dp.z_scale);
+                put_any<PM>(S, warp * 32 + s, 2 * l4, za, dp.z_scale);
+                put_any<PM>(S, warp * 32 + s, 2 * l4 + 1, zb, dp.z_scale);
             }
         }
-        const bool ok = mma_tile<FP8>(S, taddr, phase);
+        const bool ok = mma_any<PM>(S, taddr, phase);
         if (!__syncthreads_and(ok)) {
             if (threadIdx.x == 0) atomicExch(err, kStatusTimeout);
             drained = false;
@@ -263,16 +383,17 @@ __global__ void __launch_bounds__(kTM, kCtasPerSm) k_trace_bf16(const DecPtrsB d
 // ---------------------------------------------------------------------------
 // sdf_query, BF16 decode: tiles of 128 points
 // ---------------------------------------------------------------------------
-template <typename T, int IN, bool FP8>
+template <typename T, int IN, int PM>
 __global__ void __launch_bounds__(kTM, kCtasPerSm) k_query_bf16(const DecPtrsB dp, const Tables tb, const float* __restrict__ x,
                                                       long long Q, int D, float* __restrict__ sdf,
                                                       int8_t* __restrict__ deepest, int* __restrict__ err) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    BfSmem& S = *reinterpret_cast<BfSmem*>(smem_raw);
+    using SM = typename TcSmem<PM>::type;
+    SM& S = *reinterpret_cast<SM*>(smem_raw);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int g4 = lane >> 2, l4 = lane & 3, gb4 = g4 << 2;
     const unsigned gm4 = 0xfu << gb4;
-    stage_bf16_decoder<IN, FP8>(S, dp);
+    stage_any<IN, PM>(S, dp);
     setup_tmem(S);
     const uint32_t taddr = S.taddr;
     uint32_t phase = 0;
@@ -302,10 +423,10 @@ __global__ void __launch_bounds__(kTM, kCtasPerSm) k_query_bf16(const DecPtrsB d
             const float s2 = __shfl_sync(0xffffffffu, q2, s);
             float4 za = make_float4(0.f, 0.f, 0.f, 0.f), zb = za;
             if (sdd >= kFirstFeatureDepth) gather_slot4<T>(tb, sdd, svox, sijk, s0, s1, s2, gm4, gb4, l4, za, zb);
-            put_z<FP8>(S, warp * 32 + s, 2 * l4, za, dp.z_scale);
-            put_z<FP8>(S, warp * 32 + s, 2 * l4 + 1, zb, dp.z_scale);
+            put_any<PM>(S, warp * 32 + s, 2 * l4, za, dp.z_scale);
+            put_any<PM>(S, warp * 32 + s, 2 * l4 + 1, zb, dp.z_scale);
         }
-        const bool ok = mma_tile<FP8>(S, taddr, phase);
+        const bool ok = mma_any<PM>(S, taddr, phase);
         if (!__syncthreads_and(ok)) {
             if (threadIdx.x == 0) atomicExch(err, kStatusTimeout);
             drained = false;
@@ -417,50 +538,66 @@ void prefer_l1(K kernel) {
     cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 40);
 }
 
-template <typename T, int IN, bool FP8>
+// the three-plane kernels need 52 KB of shared memory a CTA: their carveout
+// keeps two CTAs per SM with the rest of the storage as L1
+template <int PM, typename K>
+void configure_tc(K kernel) {
+    if constexpr (PM == 2) {
+        cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kDynSmem3);
+        cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 50);
+    } else {
+        prefer_l1(kernel);
+    }
+}
+
+template <typename T, int IN, int PM>
 void go_trace1(const DecPtrsB& P, const Tables& tb, const TraceArgs& A, int* err, int grid, cudaStream_t st) {
-    static bool once = (prefer_l1(k_trace_bf16<T, IN, FP8>), true);
+    static bool once = (configure_tc<PM>(k_trace_bf16<T, IN, PM>), true);
     (void)once;
-    k_trace_bf16<T, IN, FP8><<<grid, kTM, kDynSmem, st>>>(P, tb, A, err);
+    k_trace_bf16<T, IN, PM><<<grid, kTM, PM == 2 ? kDynSmem3 : kDynSmem, st>>>(P, tb, A, err);
 }
 
 template <typename T, int IN>
-void go_trace(const DecPtrsB& P, const Tables& tb, const TraceArgs& A, int* err, int grid, bool fp8, cudaStream_t st) {
-    if (fp8) go_trace1<T, IN, true>(P, tb, A, err, grid, st);
-    else go_trace1<T, IN, false>(P, tb, A, err, grid, st);
+void go_trace(const DecPtrsB& P, const Tables& tb, const TraceArgs& A, int* err, int grid, int pm, cudaStream_t st) {
+    if (pm == 2) go_trace1<T, IN, 2>(P, tb, A, err, grid, st);
+    else if (pm == 1) go_trace1<T, IN, 1>(P, tb, A, err, grid, st);
+    else go_trace1<T, IN, 0>(P, tb, A, err, grid, st);
 }
 
-template <typename T, int IN, bool FP8>
+template <typename T, int IN, int PM>
 void go_query1(const DecPtrsB& P, const Tables& tb, const float* x, long long Q, int D, float* sdf, int8_t* deep,
                int* err, int grid, cudaStream_t st) {
-    static bool once = (prefer_l1(k_query_bf16<T, IN, FP8>), true);
+    static bool once = (configure_tc<PM>(k_query_bf16<T, IN, PM>), true);
     (void)once;
-    k_query_bf16<T, IN, FP8><<<grid, kTM, kDynSmem, st>>>(P, tb, x, Q, D, sdf, deep, err);
+    k_query_bf16<T, IN, PM><<<grid, kTM, PM == 2 ? kDynSmem3 : kDynSmem, st>>>(P, tb, x, Q, D, sdf, deep, err);
 }
 
 template <typename T, int IN>
 void go_query(const DecPtrsB& P, const Tables& tb, const float* x, long long Q, int D, float* sdf, int8_t* deep,
-              int* err, int grid, bool fp8, cudaStream_t st) {
-    if (fp8) go_query1<T, IN, true>(P, tb, x, Q, D, sdf, deep, err, grid, st);
-    else go_query1<T, IN, false>(P, tb, x, Q, D, sdf, deep, err, grid, st);
+              int* err, int grid, int pm, cudaStream_t st) {
+    if (pm == 2) go_query1<T, IN, 2>(P, tb, x, Q, D, sdf, deep, err, grid, st);
+    else if (pm == 1) go_query1<T, IN, 1>(P, tb, x, Q, D, sdf, deep, err, grid, st);
+    else go_query1<T, IN, 0>(P, tb, x, Q, D, sdf, deep, err, grid, st);
 }
 
 }  // namespace
 
 int launch_trace_bf16(const nglod_svo* svo, const nglod_decoder* dec, const Tables& tb, const TraceArgs& A,
-                      bool f16, float fp8_z_absmax, cudaStream_t st) {
+                      bool f16, float fp8_z_absmax, cudaStream_t st, bool split) {
     const bool fp8 = fp8_z_absmax > 0.0f;
+    const int pm = split ? 2 : fp8 ? 1 : 0;
     static_assert(sizeof(BfSmem) <= kDynSmem, "shared layout");
     // the error word shares the workspace header with the ray queue
     int* err = A.queue + 1;
-    const int grid = svo->num_sms * (A.ctas_per_sm > 0 ? std::min(A.ctas_per_sm, kCtasPerSm) : kCtasPerSm);
+    const int most = split ? 2 : kCtasPerSm;   // the three-plane tiles fit two CTAs per SM beside L1
+    const int grid = svo->num_sms * (A.ctas_per_sm > 0 ? std::min(A.ctas_per_sm, most) : most);
     const DecPtrsB P = bptrs(dec, fp8 ? kE4M3Max / fp8_z_absmax : 1.0f);
     if (dec->in_dim == 35) {
-        if (f16) go_trace<__half, 35>(P, tb, A, err, grid, fp8, st);
-        else go_trace<float, 35>(P, tb, A, err, grid, fp8, st);
+        if (f16) go_trace<__half, 35>(P, tb, A, err, grid, pm, st);
+        else go_trace<float, 35>(P, tb, A, err, grid, pm, st);
     } else {
-        if (f16) go_trace<__half, 32>(P, tb, A, err, grid, fp8, st);
-        else go_trace<float, 32>(P, tb, A, err, grid, fp8, st);
+        if (f16) go_trace<__half, 32>(P, tb, A, err, grid, pm, st);
+        else go_trace<float, 32>(P, tb, A, err, grid, pm, st);
     }
     NGLOD_CUDA(cudaGetLastError());
     return NGLOD_OK;
@@ -468,20 +605,22 @@ int launch_trace_bf16(const nglod_svo* svo, const nglod_decoder* dec, const Tabl
 
 int launch_query_bf16(const nglod_svo* svo, const Tables& tb, const nglod_decoder* dec, const float* x,
                       long long Q, int D, float* sdf, int8_t* deepest, bool f16, float fp8_z_absmax,
-                      cudaStream_t st) {
+                      cudaStream_t st, bool split) {
     const bool fp8 = fp8_z_absmax > 0.0f;
+    const int pm = split ? 2 : fp8 ? 1 : 0;
     // the octree handle's device status word records an expired wait
     int* err = svo->dstatus;
     NGLOD_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
     const long long tiles = (Q + kTM - 1) / kTM;
-    const int grid = (int)std::max<long long>(1, std::min<long long>(tiles, (long long)svo->num_sms * kCtasPerSm));
+    const int grid = (int)std::max<long long>(1, std::min<long long>(tiles, (long long)svo->num_sms *
+                                                                                   (split ? 2 : kCtasPerSm)));
     const DecPtrsB P = bptrs(dec, fp8 ? kE4M3Max / fp8_z_absmax : 1.0f);
     if (dec->in_dim == 35) {
-        if (f16) go_query<__half, 35>(P, tb, x, Q, D, sdf, deepest, err, grid, fp8, st);
-        else go_query<float, 35>(P, tb, x, Q, D, sdf, deepest, err, grid, fp8, st);
+        if (f16) go_query<__half, 35>(P, tb, x, Q, D, sdf, deepest, err, grid, pm, st);
+        else go_query<float, 35>(P, tb, x, Q, D, sdf, deepest, err, grid, pm, st);
     } else {
-        if (f16) go_query<__half, 32>(P, tb, x, Q, D, sdf, deepest, err, grid, fp8, st);
-        else go_query<float, 32>(P, tb, x, Q, D, sdf, deepest, err, grid, fp8, st);
+        if (f16) go_query<__half, 32>(P, tb, x, Q, D, sdf, deepest, err, grid, pm, st);
+        else go_query<float, 32>(P, tb, x, Q, D, sdf, deepest, err, grid, pm, st);
     }
     NGLOD_CUDA(cudaGetLastError());
     int h = 0;

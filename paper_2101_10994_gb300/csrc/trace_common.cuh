@@ -381,11 +381,12 @@ constexpr int kWsMaskFlagWord = 3;
 int enable_hit_masks(TraceArgs& A, void* work, cudaStream_t st, bool two = false);
 // Enqueues the work-ordered ray-group handout of a trace (sets A.order).
 int enqueue_ray_order(TraceArgs& A, void* work, cudaStream_t st);
+// split = true: the FP32-accurate decode (three-term BF16 splits, six products)
 int launch_trace_bf16(const nglod_svo* svo, const nglod_decoder* dec, const Tables& tb, const TraceArgs& A,
-                      bool f16, float fp8_z_absmax, cudaStream_t st);
+                      bool f16, float fp8_z_absmax, cudaStream_t st, bool split = false);
 int launch_query_bf16(const nglod_svo* svo, const Tables& tb, const nglod_decoder* dec, const float* x,
                       long long Q, int D, float* sdf, int8_t* deepest, bool f16, float fp8_z_absmax,
-                      cudaStream_t st);
+                      cudaStream_t st, bool split = false);
 int launch_trace_batch_tc(const TraceJob* jobs, const JobGroup* groups, int ngroups, int in_dim, bool f16, bool fp8,
                           int ctas_per_sm, int sms, int* err, cudaStream_t st);
 int launch_trace_blend_f32(const nglod_decoder* lo, const nglod_decoder* hi, float alpha, const Tables& tb,

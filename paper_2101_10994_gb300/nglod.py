@@ -17,7 +17,10 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libnglod.so")
 
 NGLOD_OK, ERR_INVALID_ARG, ERR_CAPACITY, ERR_CUDA, ERR_OOM, ERR_TIMEOUT, ERR_NOT_SUPPORTED = range(7)
-F32, F16, BF16, FP8 = 0, 1, 2, 3
+F32, F16, BF16, FP8, F32_SPLIT = 0, 1, 2, 3, 4
+# decode names: "f32" CUDA cores; "bf16" / "fp8" tensor cores; "f32tc" tensor
+# cores at FP32 accuracy (three-term BF16 splits, six products)
+DECODES = {"f32": F32, "bf16": BF16, "fp8": FP8, "f32tc": F32_SPLIT}
 BF16_DECODE = True          # the tensor-core (tcgen05) decode is built
 FIRST_FEATURE_DEPTH = 3
 
@@ -341,7 +344,7 @@ def sdf_query(svo: SVO, feats: Features, dec: DecoderDev, x, lod: int, decode: s
     g = torch.empty((Q, 3), dtype=torch.float32, device=x.device) if grad else None
     fc, dc = feats.c(), dec.c()
     _check(lib().sdf_query(svo.h, C.byref(fc), C.byref(dc), x.data_ptr(), Q, lod,
-                           {"f32": F32, "bf16": BF16, "fp8": FP8}[decode], sdf.data_ptr(), _ptr(dp), _ptr(g),
+                           DECODES[decode], sdf.data_ptr(), _ptr(dp), _ptr(g),
                            C.c_void_p(_stream(stream))))
     out = [sdf]
     if deepest:
@@ -370,7 +373,7 @@ def sphere_trace(svo: SVO, feats: Features, dec: DecoderDev, o, d, lists: RayLis
                    steps=torch.empty(R, dtype=torch.int32, device=dev),
                    normal=torch.empty((R, 3), dtype=torch.float32, device=dev) if normals else None,
                    work=torch.empty(max(lib().sphere_trace_workspace(R), 1), dtype=torch.uint8, device=dev))
-    p = _TraceParams(eps, far, max_steps, int(osc), {"f32": F32, "bf16": BF16, "fp8": FP8}[decode], int(normals),
+    p = _TraceParams(eps, far, max_steps, int(osc), DECODES[decode], int(normals),
                      NORMALS[normal_mode], fd_h, int(ctas_per_sm))
     fc, dc = feats.c(), dec.c()
     _check(lib().sphere_trace(svo.h, C.byref(fc), C.byref(dc), o.data_ptr(), d.data_ptr(), R, lists.lod,
@@ -428,7 +431,7 @@ def sdf_query_blend(svo: SVO, feats: Features, dec_lo: DecoderDev, dec_hi: Decod
     fc, lo = feats.c(), dec_lo.c()
     hi = (dec_hi or dec_lo).c()
     _check(lib().sdf_query_blend(svo.h, C.byref(fc), C.byref(lo), C.byref(hi), x.data_ptr(), Q, lod_tilde,
-                                 {"f32": F32, "bf16": BF16, "fp8": FP8}[decode], out.data_ptr(),
+                                 DECODES[decode], out.data_ptr(),
                                  C.c_void_p(_stream(stream))))
     return out
 
@@ -450,7 +453,7 @@ def sphere_trace_blend(svo: SVO, feats: Features, dec_lo: DecoderDev, dec_hi: De
                    steps=torch.empty(R, dtype=torch.int32, device=dev),
                    normal=torch.empty((R, 3), dtype=torch.float32, device=dev) if normals else None,
                    work=torch.empty(max(lib().sphere_trace_workspace(R), 1), dtype=torch.uint8, device=dev))
-    p = _TraceParams(eps, far, max_steps, int(osc), {"f32": F32, "bf16": BF16, "fp8": FP8}[decode], int(normals),
+    p = _TraceParams(eps, far, max_steps, int(osc), DECODES[decode], int(normals),
                      NORMALS[normal_mode], fd_h, int(ctas_per_sm))
     fc, lo = feats.c(), dec_lo.c()
     hi = (dec_hi or dec_lo).c()

@@ -111,3 +111,28 @@ def test_query_full_size_sampled(ng, oracle_mod):
     got = ng.sdf_query(svo, F, D, xt, 5, decode="bf16").cpu().numpy()[sel].astype(np.float64)
     assert np.all(np.abs(got - ref) <= 2.0 ** -8 * np.abs(z) + TOL)
     svo.free()
+
+
+@pytest.mark.parametrize("in_dim,fdt", [(32, "f32"), (35, "f16")])
+def test_query_f32tc_vs_oracle(ng, oracle_mod, in_dim, fdt):
+    # the FP32-accurate tensor-core decode (three-term BF16 splits, six
+    # products): the FP32 tolerance 1e-5 against the FP64 oracle
+    sc, oc = S.csg_workload(64, seed=0, max_lod=5)
+    feats = S.init_features(oc, seed=0, sigma=0.1)
+    if fdt == "f16":
+        feats = [f.astype(np.float16) for f in feats]
+    svo = ng.svo_build(oc.keys)
+    ora = oracle_mod.OracleSVO(oc.keys)
+    F = ng.Features(feats, fdt)
+    x = query_points(oc, 3000, seed=7)
+    xt = torch.from_numpy(x).cuda()
+    for lod in (1, 3, 5):
+        dec = S.init_decoder(lod, in_dim)
+        dec.b1 = np.random.default_rng(lod).normal(0, 0.1, 128).astype(np.float32)
+        dec.b2 = -0.05
+        sdf, deep = ng.sdf_query(svo, F, ng.DecoderDev.from_decoder(dec), xt, lod, decode="f32tc", deepest=True)
+        ref, rdeep = ora.sdf_query(feats, dec, x, lod)
+        err = np.abs(sdf.cpu().numpy().astype(np.float64) - ref)
+        assert np.nanmax(err) <= TOL, (lod, np.nanmax(err))
+        np.testing.assert_array_equal(deep.cpu().numpy(), rdeep)
+    svo.free()

@@ -110,15 +110,17 @@ def test_plain_sphere_f32(ng, oracle_mod, decoder):
     assert c["steps_eq"] >= 0.999
 
 
-def test_csg64_lod5_1080p_sampled_f32(ng, oracle_mod):
-    # the benchmark's frame, in the benchmark's configuration
+@pytest.mark.parametrize("decode", ["f32", "f32tc"])
+def test_csg64_lod5_1080p_sampled_f32(ng, oracle_mod, decode):
+    # the benchmark's frame, in the benchmark's configuration; "f32tc" is the
+    # FP32-accurate tensor-core decode, held to the same tolerances
     sc, oc = S.csg_workload(64, seed=0, max_lod=5)
     ora = oracle_mod.OracleSVO(oc.keys)
     feats, dec = S.readout_features(oc, sc), S.readout_decoder(5)
     o, d, _ = S.camera_rays(1920, 1080, tile=8)
     rng = np.random.default_rng(1)
     sel = rng.choice(len(o), 1500, replace=False)
-    gs, ref = trace_both(ng, ora, oc, feats, "f32", dec, 5, o, d, 1e-3, 128, "f32", sample=sel)
+    gs, ref = trace_both(ng, ora, oc, feats, "f32", dec, 5, o, d, 1e-3, 128, decode, sample=sel)
     c = compare(ora, feats, dec, 5, o, d, gs, ref, 1e-3, sel=sel, oc=oc)
     assert c["mismatch"] <= 1 and c["both"] > 300
     assert c["dt"].max() <= 1e-3, c["dt"].max()
