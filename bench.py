@@ -362,6 +362,68 @@ def run_ours(args, rank, world, local_rank):
                                            hit_pixels=int(fr.out["hit"].sum().item()))
         del fr, f16
 
+    # ---- the frames reading the summed corner table of the LOD (nglod_sum_features: z at
+    # every corner of the LOD, so a query gathers 8 rows instead of 8 per level; built once per
+    # feature set, its build timed apart).  Same rays, lists and decoders; the stage times come
+    # from the sequential frame, the frame time from the autotuned renderer ----
+    for sm_mode in [m for m in ("bf16", "f32") if m in modes]:
+        b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        flush.zero_()
+        b0.record()
+        fs = feats.summed(svo, W["lod"])
+        b1.record()
+        b1.synchronize()
+        ms_build = b0.elapsed_time(b1)
+        sout = dict(t=torch.empty(R, device=dev), hit=torch.empty(R, dtype=torch.uint8, device=dev),
+                    steps=torch.empty(R, dtype=torch.int32, device=dev), normal=torch.empty((R, 3), device=dev),
+                    work=torch.empty(ng.lib().sphere_trace_workspace(R), dtype=torch.uint8, device=dev))
+        st_ms = []
+        for k in range(args.warmup + args.steps):
+            flush.zero_()
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            ev[0].record()
+            lists = ng.svo_trace_rays(svo, o, d, W["lod"])
+            ev[1].record()
+            ng.sphere_trace(svo, fs, dec, o, d, lists, eps=W["eps"], far=W["far"], max_steps=W["max_steps"],
+                            decode=sm_mode, normals=False, out=sout)
+            ev[2].record()
+            ng.trace_normals(svo, fs, dec, o, d, lists, sout)
+            ev[3].record()
+            ev[3].synchronize()
+            if k >= args.warmup:
+                st_ms.append([ev[i].elapsed_time(ev[i + 1]) for i in range(3)])
+        ng.sphere_trace_status(sout)
+        st_ms = [statistics.mean(v[i] for v in st_ms) for i in range(3)]
+        fr, stune = autotune_frame(svo, fs, dec, o, d, W["lod"], eps=W["eps"], far=W["far"],
+                                   max_steps=W["max_steps"], decode=sm_mode, normals=True)
+        sl = []
+        for k in range(args.warmup + args.steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fr.frame()
+            e1.record()
+            e1.synchronize()
+            if k >= args.warmup:
+                sl.append(e0.elapsed_time(e1))
+        fr.check()
+        assert torch.equal(fr.out["t"], sout["t"]) and torch.equal(fr.out["normal"], sout["normal"])
+        ms = max_over_ranks(statistics.mean(sl), dev)
+        sch = len(fr.chunks)
+        q = int(sout["steps"].sum().item())
+        results[f"{sm_mode}_summed"] = dict(
+            chunks=sch, trace_ctas_per_sm=fr.ctas_per_sm, autotune_ms_by_chunks_and_ctas=stune,
+            schedule=f"{sch} ray chunks on {sch} streams, trace CTAs/SM {fr.ctas_per_sm or 'max'} (autotuned)",
+            ms_per_step=ms, rays_per_s=job_rate(R, world, ms * 1e-3),
+            ms_traverse=float(st_ms[0]), ms_trace=float(st_ms[1]), ms_normals=float(st_ms[2]),
+            ms_sequential=float(sum(st_ms)), queries_per_frame=q,
+            queries_per_s=world * q / (float(st_ms[1]) * 1e-3),
+            hit_pixels=int(sout["hit"].sum().item()),
+            table_build_ms=ms_build, table_bytes=int(fs.tables[-1].numel() * 4),
+            note="the summed table replaces the multi-level gather of Eq. 2 by the trilinear "
+                 "interpolation of z's own corner values (the same function inside every voxel of the LOD)")
+        del fr, fs, sout
+
     # ---- end to end through the public API with pinned host buffers: each chunk's
     # rays copied in and its t / hit / normals copied out on the chunk's stream ----
     mode = "bf16" if "bf16" in modes else modes[0]
@@ -752,7 +814,9 @@ def main():
             "gpu_launches": args.steps * (sum(8 * (1 + res[m]["chunks"]) for m in modes)
                                           + 10 * res.get("bf16_blend", {}).get("chunks", 0)
                                           + 8 * res.get("bf16_f16features", {}).get("chunks", 0)
-                                          + sum(k.startswith("sdf_query_") for k in res)),
+                                          + sum(8 * (1 + res[k]["chunks"]) for k in res if k.endswith("_summed"))
+                                          + sum(k.startswith("sdf_query_") for k in res))
+                            + sum(k.endswith("_summed") for k in res),      # one table build each
         }
         if "bf16" in res and "f32" in res:
             line["bf16_speedup"] = res["f32"]["ms_per_step"] / res["bf16"]["ms_per_step"]

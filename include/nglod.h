@@ -64,6 +64,15 @@ typedef struct {
     float fp8_z_absmax;    /* FP8 decode only: a bound on |z| (e.g. from
                               nglod_features_absmax); z is scaled so this
                               bound maps to 448, the largest e4m3 value     */
+    int summed_lod;        /* 0: feats[l-1] are the per-LOD tables Z_l of
+                              Eq. 2's sum.  L >= 1: feats[L-1] is the
+                              summed corner table of LOD L written by
+                              nglod_sum_features (dtype NGLOD_F32) and the
+                              other entries are ignored; only sphere_trace
+                              (analytic or no normals), trace_normals and
+                              nglod_features_absmax at lod = L accept it,
+                              every other call returns
+                              NGLOD_ERR_NOT_SUPPORTED                        */
 } nglod_features;
 
 /* One LOD's decoder (Eq. 2): d = W2 . relu(W1 v + b1) + b2 with
@@ -110,9 +119,32 @@ typedef struct {
 /* nglod_features_absmax -- the sum over LODs 1..lod of each feature table's
  * largest |value|, written to *h_out (synchronises).  The trilinear weights
  * are non-negative and sum to 1, so this bounds every |z_k(x; lod)|: the
- * natural fp8_z_absmax for decoding at that LOD. */
+ * natural fp8_z_absmax for decoding at that LOD.  For a summed table
+ * (summed_lod = lod) it is that table's largest |value|. */
 int nglod_features_absmax(const nglod_svo* svo, const nglod_features* feats, int lod, float* h_out,
                           void* stream);
+
+/* nglod_sum_features -- the summed corner table of LOD `lod` (Sec. 3.2,
+ * Eq. 2's z = sum over LODs 1..lod of the trilinear interpolants psi_l).
+ * Inside one voxel V of LOD `lod` every coarser psi_l is trilinear too (V lies
+ * in one voxel of each coarser level, whose interpolant is a product of
+ * affine functions of x), so their sum equals the trilinear interpolation of
+ * its own values at V's 8 corners.  out[c] = that sum at corner c of LOD
+ * `lod` (the interpolants of the coarser levels are continuous across voxel
+ * faces, so every voxel sharing the corner gives the same value): a render
+ * then gathers 8 rows per query instead of 8 per level.  Only points inside
+ * voxels of LOD `lod` may be queried through the table, which is what the
+ * sphere tracer and its analytic normals do.
+ *   feats   per-LOD tables (summed_lod = 0), F32 or F16
+ *   out     device [C_lod, 32] FP32 (svo_info's corner count), 32-byte
+ *           aligned; every row is written
+ * The interpolation weights at the corners are exact dyadic numbers; each
+ * row is accumulated in FP64 (levels in order 1..lod, corners in index
+ * order) and rounded once to FP32, so the table is the same whichever voxel
+ * a shared corner is computed from.  Stream-ordered, no synchronisation.
+ * NGLOD_ERR_INVALID_ARG for NULL pointers, lod outside 1..svo's LODs or
+ * features not covering lod; NGLOD_ERR_NOT_SUPPORTED for summed input. */
+int nglod_sum_features(const nglod_svo* svo, const nglod_features* feats, int lod, float* out, void* stream);
 
 /* Text of the calling thread's last error ("" if none). */
 const char* nglod_last_error(void);

@@ -19,15 +19,25 @@
 
 namespace nglod {
 
-int fill_tables(const nglod_svo* svo, const nglod_features* f, int lod, Tables& tb) {
+int fill_tables(const nglod_svo* svo, const nglod_features* f, int lod, Tables& tb, bool summed_ok) {
     const int D = lod + kFirstFeatureDepth - 1;
     if (!f) return fail(NGLOD_ERR_INVALID_ARG, "NULL features");
     if (f->m != kFeatDim) return fail(NGLOD_ERR_NOT_SUPPORTED, "only m = 32 features are built");
     if (f->dtype != NGLOD_F32 && f->dtype != NGLOD_F16)
         return fail(NGLOD_ERR_NOT_SUPPORTED, "features must be F32 or F16");
     if (f->num_lods < lod) return fail(NGLOD_ERR_INVALID_ARG, "features do not cover the requested LOD");
+    if (f->summed_lod != 0) {
+        if (!summed_ok)
+            return fail(NGLOD_ERR_NOT_SUPPORTED,
+                        "a summed corner table only serves sphere_trace (analytic normals) and trace_normals");
+        if (f->summed_lod != lod)
+            return fail(NGLOD_ERR_INVALID_ARG, "a summed corner table serves only its own LOD");
+        if (f->dtype != NGLOD_F32) return fail(NGLOD_ERR_NOT_SUPPORTED, "summed corner tables are F32");
+    }
+    const int first = f->summed_lod != 0 ? lod : 1;
+    tb.first_depth = first + kFirstFeatureDepth - 1;
     for (int l = 0; l < kMaxLods; ++l) tb.feats[l] = nullptr;
-    for (int l = 1; l <= lod; ++l) {
+    for (int l = first; l <= lod; ++l) {
         if (!f->feats[l - 1]) return fail(NGLOD_ERR_INVALID_ARG, "NULL feature table for a LOD <= lod");
         // FP32 rows are read with 32-byte vector loads, FP16 rows with 16-byte ones
         if ((reinterpret_cast<uintptr_t>(f->feats[l - 1]) & (f->dtype == NGLOD_F32 ? 31u : 15u)) != 0)
@@ -351,7 +361,7 @@ __global__ void __launch_bounds__(kThreads) k_grad(const DecPtrs dp, const Table
                 int2 a = make_int2(-1, -1);
                 if (2 * l4 <= sdd - kFirstFeatureDepth)
                     a = __ldg(reinterpret_cast<const int2*>(tb.anc[sdd] + (size_t)svox * 8) + l4);
-                for (int dp2 = kFirstFeatureDepth; dp2 <= min(sdd, dcap); ++dp2) {
+                for (int dp2 = tb.first_depth; dp2 <= min(sdd, dcap); ++dp2) {
                     const int i = dp2 - kFirstFeatureDepth;
                     const int vv = __shfl_sync(gm4, (i & 1) ? a.y : a.x, gb4 + (i >> 1));
                     const int2 cc = __ldg(reinterpret_cast<const int2*>(tb.corners[dp2] + (size_t)vv * 8) + l4);
@@ -1091,7 +1101,9 @@ extern "C" int sphere_trace(const nglod_svo* svo, const nglod_features* feats, c
     if (work_bytes < sphere_trace_workspace(R)) return fail(NGLOD_ERR_CAPACITY, "sphere_trace: workspace too small");
     if (((uintptr_t)work & 255u) != 0) return fail(NGLOD_ERR_INVALID_ARG, "sphere_trace: work must be 256-B aligned");
     Tables tb;
-    int rc = fill_tables(svo, feats, lod, tb);
+    // FD normals evaluate the field off the hit voxel: per-LOD tables only
+    const bool fd = normal && params->want_normals && params->normal_mode == NGLOD_NORMALS_FD;
+    int rc = fill_tables(svo, feats, lod, tb, !fd);
     if (rc) return rc;
     if (!dec || dec->hidden != kHidden || (dec->in_dim != 32 && dec->in_dim != 35))
         return fail(NGLOD_ERR_NOT_SUPPORTED, "sphere_trace: decoder must be 32|35 -> 128 -> 1");
@@ -1161,7 +1173,7 @@ int normals_common(const nglod_svo* svo, const nglod_features* feats, const nglo
     if (!dec || dec->hidden != kHidden || (dec->in_dim != 32 && dec->in_dim != 35))
         return fail(NGLOD_ERR_NOT_SUPPORTED, "trace_normals: decoder must be 32|35 -> 128 -> 1");
     Tables tb;
-    int rc = fill_tables(svo, feats, lod, tb);
+    int rc = fill_tables(svo, feats, lod, tb, fd_h == 0.0f);
     if (rc) return rc;
     TraceArgs A{};
     A.o = o;
@@ -1228,8 +1240,11 @@ extern "C" int nglod_features_absmax(const nglod_svo* svo, const nglod_features*
         return fail(NGLOD_ERR_INVALID_ARG, "nglod_features_absmax: bad arguments");
     if (feats->dtype != NGLOD_F32 && feats->dtype != NGLOD_F16)
         return fail(NGLOD_ERR_NOT_SUPPORTED, "nglod_features_absmax: features must be F32 or F16");
+    if (feats->summed_lod != 0 && (feats->summed_lod != lod || feats->dtype != NGLOD_F32))
+        return fail(NGLOD_ERR_INVALID_ARG, "nglod_features_absmax: a summed table serves only its own LOD (F32)");
     NGLOD_CUDA(cudaMemsetAsync(svo->dscratch, 0, sizeof(unsigned) * 16, st));
-    for (int l = 1; l <= lod; ++l) {
+    const int first = feats->summed_lod != 0 ? lod : 1;   // a summed table bounds z alone
+    for (int l = first; l <= lod; ++l) {
         if (!feats->feats[l - 1]) return fail(NGLOD_ERR_INVALID_ARG, "nglod_features_absmax: NULL table");
         const long long n = svo->nc[l + kFirstFeatureDepth - 1] * (long long)feats->m;
         const int grid = (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, (long long)svo->num_sms * 8));
@@ -1243,7 +1258,7 @@ extern "C" int nglod_features_absmax(const nglod_svo* svo, const nglod_features*
     NGLOD_CUDA(cudaMemcpyAsync(h, svo->dscratch, sizeof(h), cudaMemcpyDeviceToHost, st));
     NGLOD_CUDA(cudaStreamSynchronize(st));
     float sum = 0.0f;
-    for (int l = 1; l <= lod; ++l) {
+    for (int l = first; l <= lod; ++l) {
         float v;
         memcpy(&v, &h[l], sizeof(float));
         sum += v;

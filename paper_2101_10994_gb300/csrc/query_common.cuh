@@ -23,6 +23,10 @@ constexpr int kZStride = 36;   // floats per staged z row (16-B aligned, 4-way b
 
 struct Tables {
     const void* feats[kMaxLods];             // LOD l at index l - 1
+    // first depth whose table is gathered: kFirstFeatureDepth, or the
+    // queried depth for a summed corner table (it already holds the
+    // coarser levels' sum at its corners)
+    int first_depth;
     const int32_t* corners[kMaxDepth + 1];   // [V_dp, 8]
     const int32_t* anc[kMaxDepth + 1];       // [V_dp, 8]
     const Node* node[kMaxDepth + 1];
@@ -72,7 +76,7 @@ __device__ __forceinline__ float4 gather_slot(const Tables& tb, int dd, int vox,
     float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
     const int a = (l <= dd - kFirstFeatureDepth) ? __ldg(tb.anc[dd] + (size_t)vox * 8 + l) : -1;
 #pragma unroll 1
-    for (int dp = kFirstFeatureDepth; dp <= dd; ++dp) {
+    for (int dp = tb.first_depth; dp <= dd; ++dp) {
         const int v = __shfl_sync(gmask, a, gbase + dp - kFirstFeatureDepth);
         const int cid = __ldg(tb.corners[dp] + (size_t)v * 8 + l);
         const int sh = dd - dp;
@@ -141,7 +145,7 @@ __device__ __forceinline__ void gather_slot4(const Tables& tb, int dd, int vox, 
     if (2 * l4 <= dd - kFirstFeatureDepth) a = __ldg(reinterpret_cast<const int2*>(tb.anc[dd] + (size_t)vox * 8) + l4);
     const int top = min(dd, dlast);     // only depths dfirst..dlast (level blending, Eq. 3)
 #pragma unroll 1
-    for (int dp = dfirst; dp <= top; ++dp) {
+    for (int dp = max(dfirst, tb.first_depth); dp <= top; ++dp) {
         const int i = dp - kFirstFeatureDepth;
         const int v = __shfl_sync(gmask, (i & 1) ? a.y : a.x, gbase + (i >> 1));
         const int2 cc = __ldg(reinterpret_cast<const int2*>(tb.corners[dp] + (size_t)v * 8) + l4);

@@ -341,7 +341,9 @@ __device__ __forceinline__ void publish_hits_batch(RaySlot& S, const TraceJob* _
 }
 
 // Host-side entry points implemented per translation unit.
-int fill_tables(const nglod_svo* svo, const nglod_features* f, int lod, Tables& tb);
+// summed_ok: the caller only queries points inside voxels of LOD `lod` and
+// so may take a summed corner table (nglod_features.summed_lod = lod).
+int fill_tables(const nglod_svo* svo, const nglod_features* f, int lod, Tables& tb, bool summed_ok = false);
 int check_decoder(const nglod_decoder* dec);
 int launch_trace_fp32(const nglod_decoder* dec, const Tables& tb, const TraceArgs& A, bool f16, int sms,
                       cudaStream_t st);

@@ -32,7 +32,7 @@ EXPORTS = ["nglod_last_error", "svo_build", "svo_info", "svo_device_arrays", "sv
            "sphere_trace_batch_create", "sphere_trace_batch_run", "sphere_trace_batch_status",
            "sphere_trace_batch_free", "sdf_query_blend", "sphere_trace_blend", "nglod_lod_select",
            "trace_normals_fd", "sdf_backward_bf16", "sdf_l2_backward_bf16", "nglod_sort_points_workspace",
-           "nglod_sort_points"]
+           "nglod_sort_points", "nglod_sum_features"]
 
 
 class NglodError(RuntimeError):
@@ -43,7 +43,7 @@ class NglodError(RuntimeError):
 
 class _Features(C.Structure):
     _fields_ = [("feats", C.c_void_p * 8), ("dtype", C.c_int), ("m", C.c_int), ("num_lods", C.c_int),
-                ("fp8_z_absmax", C.c_float)]
+                ("fp8_z_absmax", C.c_float), ("summed_lod", C.c_int)]
 
 
 class _Decoder(C.Structure):
@@ -104,6 +104,7 @@ def lib():
         L.nglod_sort_points.argtypes = [P, P, i64, i32, P, P, P, P, sz, P]
         L.sdf_l2_backward_bf16.argtypes = [P, P, P, P, P, i64, C.c_uint32, C.c_float, P, P, P, P, P, P, P]
         L.nglod_features_absmax.argtypes = [P, P, i32, P, P]
+        L.nglod_sum_features.argtypes = [P, P, i32, P, P]
         L.svo_trace_rays_async.argtypes = [P, P, P, i64, i32, P, sz, i64, P, P, P, i64, P]
         L.svo_trace_rays_check.argtypes = [P, i32, P, P]
         L.sphere_trace_batch_create.argtypes = [P, i32, P, i32, P, P]
@@ -208,6 +209,7 @@ class Features:
                        for t in tables]
         self.m = int(self.tables[0].shape[1])
         self.z_absmax = 0.0
+        self.summed_lod = 0
 
     @classmethod
     def from_tensors(cls, tables):
@@ -218,6 +220,28 @@ class Features:
         f.dtype = "f16" if f.tables[0].dtype == torch.float16 else "f32"
         f.m = int(f.tables[0].shape[1])
         f.z_absmax = 0.0
+        f.summed_lod = 0
+        return f
+
+    def summed(self, svo, lod: int, stream=None) -> "Features":
+        """The summed corner table of LOD ``lod`` (nglod_sum_features): per
+        corner of that LOD, the sum over LODs 1..lod of the interpolated
+        features there.  The returned Features serve sphere_trace (analytic
+        normals) and trace_normals at that LOD with 8 row gathers per query."""
+        import torch
+        if getattr(self, "summed_lod", 0):
+            raise ValueError("already a summed table")
+        ref = self.tables[lod - 1]
+        out = torch.empty((svo.corners[lod - 1], self.m), dtype=torch.float32, device=ref.device)
+        fc = self.c()
+        _check(lib().nglod_sum_features(svo.h, C.byref(fc), int(lod), out.data_ptr(),
+                                        C.c_void_p(_stream(stream))))
+        f = Features.__new__(Features)
+        f.tables = [None] * (lod - 1) + [out]
+        f.dtype = "f32"
+        f.m = self.m
+        f.z_absmax = 0.0
+        f.summed_lod = int(lod)
         return f
 
     def set_fp8_bound(self, svo, lod: int, stream=None):
@@ -231,11 +255,12 @@ class Features:
     def c(self) -> _Features:
         f = _Features()
         for i, t in enumerate(self.tables[:8]):
-            f.feats[i] = t.data_ptr()
+            f.feats[i] = t.data_ptr() if t is not None else None
         f.dtype = F32 if self.dtype == "f32" else F16
         f.m = self.m
         f.num_lods = len(self.tables)
         f.fp8_z_absmax = getattr(self, "z_absmax", 0.0)
+        f.summed_lod = getattr(self, "summed_lod", 0)
         return f
 
 
