@@ -55,6 +55,9 @@ def parse():
     p.add_argument("--height", type=int, default=1080)
     p.add_argument("--decode", choices=["both", "all", "f32", "bf16", "fp8", "f32tc"], default="all")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--features", choices=["levels", "summed"], default="levels",
+                   help="frame workload: per-level corner tables (Eq. 2's multi-level gather, the default) "
+                        "or the summed corner table of the LOD (one 8-row gather per query)")
     p.add_argument("--workload", choices=["frame", "batch", "train"], default="frame",
                    help="frame: the 1080p LOD5 CSG-64 frame (default); batch: 32 seeded CSG scenes of "
                         "U{8..256} primitives at LOD U{3..6}, images U{128..1024} a side, BF16 decode; "
@@ -191,6 +194,9 @@ def run_ours(args, rank, world, local_rank):
         modes.append("f32")
     if args.decode in ("both", "all", "bf16") and bf16_available():
         modes.append("bf16")
+    summed = getattr(args, "features", "levels") == "summed"
+    if summed:
+        feats = feats.summed(svo, W["lod"])      # the frames below read the summed table
     if args.decode in ("all", "fp8") and bf16_available():
         modes.append("fp8")
         feats.set_fp8_bound(svo, W["lod"])
@@ -293,7 +299,7 @@ def run_ours(args, rank, world, local_rank):
             clock_info = sampler.summary()
 
     # ---- continuous LOD (Eq. 3): the same frame at L~ = lod - 0.5, BF16, frame renderer ----
-    if "bf16" in modes and W["lod"] >= 2:
+    if "bf16" in modes and W["lod"] >= 2 and not summed:
         lt = W["lod"] - 0.5
         dlo = ng.DecoderDev.from_decoder(W["dec_lo"])
         fr, btune = autotune_frame(svo, feats, dlo, o, d, lt, eps=W["eps"], far=W["far"], max_steps=W["max_steps"],
@@ -323,7 +329,7 @@ def run_ours(args, rank, world, local_rank):
     # ---- standalone sdf_query: 2^22 points uniform inside the target-level voxels ----
     from paper_2101_10994_gb300 import scenes as S
     xq = torch.from_numpy(S.points_in_voxels(W["octree"], W["lod"] + S.FIRST_FEATURE_DEPTH - 1, 1 << 22, 21)).to(dev)
-    for qm in [m for m in ("f32", "bf16") if m in modes]:
+    for qm in [m for m in ("f32", "bf16") if m in modes and not summed]:
         ql = []
         for k in range(args.warmup + args.steps):
             flush.zero_()
@@ -340,7 +346,7 @@ def run_ours(args, rank, world, local_rank):
     del xq
 
     # ---- the BF16 frame with FP16 corner features (half the gathered bytes) ----
-    if "bf16" in modes:
+    if "bf16" in modes and not summed:
         f16 = ng.Features(W["feats"], "f16")
         fr = FrameRenderer(svo, f16, dec, o, d, W["lod"], chunks=configs["bf16"][0], ctas_per_sm=configs["bf16"][1],
                            eps=W["eps"], far=W["far"], max_steps=W["max_steps"], decode="bf16", normals=True)
@@ -366,7 +372,7 @@ def run_ours(args, rank, world, local_rank):
     # every corner of the LOD, so a query gathers 8 rows instead of 8 per level; built once per
     # feature set, its build timed apart).  Same rays, lists and decoders; the stage times come
     # from the sequential frame, the frame time from the autotuned renderer ----
-    for sm_mode in [m for m in ("bf16", "f32") if m in modes]:
+    for sm_mode in [m for m in ("bf16", "f32") if m in modes and not summed]:
         b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         flush.zero_()
         b0.record()
@@ -470,9 +476,11 @@ def source_hash(kernel):
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(kernel):
+def profiled_traffic(kernel, tag=""):
+    """The stored DRAM bytes per launch of ``kernel`` on the workload ``tag``
+    ("" = the default frame, "@summed" = the summed-table frame)."""
     if os.path.exists(PROFILE_TRAFFIC):
-        ent = json.load(open(PROFILE_TRAFFIC)).get(kernel)
+        ent = json.load(open(PROFILE_TRAFFIC)).get(kernel + tag)
         if ent and ent.get("source_hash") == source_hash(kernel):
             return ent.get("dram_bytes_per_launch")
     return None
@@ -524,11 +532,12 @@ def traversal_roofline(W, res, mode, peaks):
             "note": "issue-bound on the 8-child slab tests (ncu: ~64 % issue active); node records hit L1/L2"}
 
 
-def trace_roofline(W, res, mode, peaks):
+def trace_roofline(W, res, mode, peaks, levels=None):
     """Dominant kernel = the sphere tracer (largest share of the frame in the
     launch list): its decode contraction against the tensor pipe (BF16) or
     its FP32 arithmetic against the CUDA cores."""
-    interp, layer1, outl = flops_per_query(W["dec"].in_dim, W["lod"], mode)
+    levels = W["lod"] if levels is None else levels      # levels gathered per query (1: summed table)
+    interp, layer1, outl = flops_per_query(W["dec"].in_dim, levels, mode)
     q = res["queries_per_frame"]
     sec = res["ms_trace"] * 1e-3
     kern = "k_trace_f32" if mode == "f32" else "k_trace_bf16"
@@ -536,12 +545,12 @@ def trace_roofline(W, res, mode, peaks):
         tf = peaks.get("bf16_tflops", 1900.0)
         achieved = q * layer1 / sec / 1e12
         return {"bound": "tensor", "kernel": kern, "achieved": achieved, "peak": tf, "unit": "TFLOP/s",
-                "frac": achieved / tf, "traffic": profiled_traffic(kern),
+                "frac": achieved / tf, "traffic": profiled_traffic(kern, "@summed" if levels == 1 else ""),
                 "flops_per_query": layer1, "queries_per_launch": q,
                 "peak_source": "MEASURED_PEAKS.json bf16_tflops burst (of measured)",
                 "note": "the kernel is bound by feature-gather latency (L1/L2), not by the 128x32 contraction",
-                "gather_bytes_per_query": 8 * 32 * 4 * W["lod"],
-                "gather_GBps": q * 8 * 32 * 4 * W["lod"] / sec / 1e9}
+                "gather_bytes_per_query": 8 * 32 * 4 * levels,
+                "gather_GBps": q * 8 * 32 * 4 * levels / sec / 1e9}
     sm_mhz = peaks.get("sm_max_mhz", 2070.0)
     peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
     achieved = q * (interp + layer1 + outl) / sec / 1e12
@@ -798,11 +807,13 @@ def main():
             "data": "synthetic",
             "config": {"workload": f"csg64_seed0_lod5_{args.width}x{args.height}", "lod": 5,
                        "rays": int(W["o"].shape[0]), "max_steps": W["max_steps"], "eps": W["eps"],
-                       "features": "f32 m=32", "decoder": "32->128->1 readout-embedded",
+                       "features": ("summed corner table of LOD 5, f32 m=32" if args.features == "summed"
+                                    else "f32 m=32, per-level tables"),
+                       "decoder": "32->128->1 readout-embedded",
                        "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world}"},
             "queries_per_s": r["queries_per_s"],
             "modes": res,
-            "roofline": trace_roofline(W, r, head, peaks),
+            "roofline": trace_roofline(W, r, head, peaks, 1 if args.features == "summed" else None),
             "traversal_roofline": traversal_roofline(W, r, head, peaks),
             "clocks": clocks,
             "e2e": e2e,

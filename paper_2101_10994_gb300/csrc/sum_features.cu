@@ -11,13 +11,15 @@
 //
 // One warp per (voxel of LOD L, corner) pair, lane = channel.  The corner's
 // integer position P (at LOD L's resolution) gives, at each coarser depth,
-// its local coordinates in the ancestor voxel: (P - base) / 2^s, an exact
-// dyadic number, so the trilinear weights are exact in FP64 and the terms
-// with weight 0 are skipped.  A corner shared by several voxels is computed
-// by each of them with the same non-zero terms in the same order (where two
-// of them have different ancestors, the corner lies on the ancestors' common
-// face, edge or vertex, whose corners they share), so every write of a row
-// carries the same value.
+// its local coordinates in the ancestor voxel: (P - base) / 2^s with
+// s = L's depth - that depth <= 7, so u and 1 - u carry at most 8
+// significant bits and every trilinear weight (a product of three) at most
+// 24: the weights are exact in FP32, the terms with weight 0 are skipped,
+// and the sum is accumulated in FP64.  A corner shared by several voxels is
+// computed by each of them with the same non-zero terms in the same order
+// (where two of them have different ancestors, the corner lies on the
+// ancestors' common face, edge or vertex, whose corners they share), so
+// every write of a row carries the same value.
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
@@ -43,9 +45,6 @@ __device__ __forceinline__ double feat_at<__half>(const void* base, long long i)
     return (double)__half2float(static_cast<const __half*>(base)[i]);
 }
 
-// 2^-s as a double (0 <= s <= 1022).
-__device__ __forceinline__ double pow2_neg(int s) { return __longlong_as_double((long long)(1023 - s) << 52); }
-
 template <typename T>
 __global__ void __launch_bounds__(256) k_sum_features(const Tables tb, int D, long long V, float* __restrict__ out) {
     const int lane = threadIdx.x & 31;
@@ -62,18 +61,18 @@ __global__ void __launch_bounds__(256) k_sum_features(const Tables tb, int D, lo
         for (int dp = kFirstFeatureDepth; dp <= D; ++dp) {
             const int sh = D - dp;
             const int a = __ldg(tb.anc[D] + v * 8 + (dp - kFirstFeatureDepth));
-            double u[3];
+            float u[3];
 #pragma unroll
-            for (int ax = 0; ax < 3; ++ax) u[ax] = (double)(P[ax] - ((vc[ax] >> sh) << sh)) * pow2_neg(sh);
+            for (int ax = 0; ax < 3; ++ax) u[ax] = (float)(P[ax] - ((vc[ax] >> sh) << sh)) * pow2f(-sh);
             const void* fb = tb.feats[dp - kFirstFeatureDepth];
 #pragma unroll
             for (int cc = 0; cc < 8; ++cc) {
-                double w = 1.0;
+                float w = 1.0f;
 #pragma unroll
-                for (int ax = 0; ax < 3; ++ax) w *= ((cc >> ax) & 1) ? u[ax] : 1.0 - u[ax];
-                if (w != 0.0) {
+                for (int ax = 0; ax < 3; ++ax) w *= ((cc >> ax) & 1) ? u[ax] : 1.0f - u[ax];
+                if (w != 0.0f) {
                     const int row = __ldg(tb.corners[dp] + (size_t)a * 8 + cc);
-                    z = fma(w, feat_at<T>(fb, (long long)row * kFeatDim + lane), z);
+                    z = fma((double)w, feat_at<T>(fb, (long long)row * kFeatDim + lane), z);
                 }
             }
         }
