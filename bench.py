@@ -630,8 +630,11 @@ def run_batch(args):
         if lod not in decs:
             decs[lod] = ng.DecoderDev.from_decoder(S.readout_decoder(lod))
         o, d, _ = S.camera_rays(w, h, tile=8)
-        jobs.append(B.Job(ng.svo_build(oc.keys), ng.Features(feats, "f32"), decs[lod], lod,
-                          torch.from_numpy(o).to(dev), torch.from_numpy(d).to(dev)))
+        svo = ng.svo_build(oc.keys)
+        F = ng.Features(feats, "f32")
+        if args.features == "summed":
+            F = F.summed(svo, lod)       # each scene reads the summed corner table of its LOD
+        jobs.append(B.Job(svo, F, decs[lod], lod, torch.from_numpy(o).to(dev), torch.from_numpy(d).to(dev)))
     R = sum(j.R for j in jobs)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
@@ -674,6 +677,8 @@ def run_batch(args):
         "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
         "config": {"workload": "batch32_csg_u8-256_lod_u3-6_side_u128-1024_seed0", "rays": R,
                    "scenes": len(jobs), "decoder_groups": len(decs), "max_steps": 128, "eps": 1e-3,
+                   "features": ("summed corner table of each scene's LOD, f32 m=32" if args.features == "summed"
+                                else "f32 m=32, per-level tables"),
                    "l2": "flushed between steps (256 MB write)", "parallelism": "single GPU"},
         "schedules_ms": {"per_scene_calls": ms_scene, "persistent_launch": ms_batch, "graph_replay": ms_graph},
         "speedup_vs_per_scene": ms_scene / ms_graph,

@@ -69,7 +69,8 @@ typedef struct {
                               summed corner table of LOD L written by
                               nglod_sum_features (dtype NGLOD_F32) and the
                               other entries are ignored; only sphere_trace
-                              (analytic or no normals), trace_normals and
+                              and sphere_trace_batch_create (analytic or no
+                              normals), trace_normals and
                               nglod_features_absmax at lod = L accept it,
                               every other call returns
                               NGLOD_ERR_NOT_SUPPORTED                        */

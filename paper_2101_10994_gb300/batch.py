@@ -68,6 +68,7 @@ class BatchRenderer:
     def _create(self, stream=None):
         if self.handle:
             ng.lib().sphere_trace_batch_free(self.handle)
+            self.handle = None
         arr = (ng._TraceJob * len(self.jobs))()
         for k, (j, b) in enumerate(zip(self.jobs, self.bufs)):
             arr[k].svo = j.svo.h.value

@@ -209,7 +209,9 @@ extern "C" int sphere_trace_batch_create(const nglod_trace_job* jobs, int num_jo
                 break;
             }
             TraceJob tj{};
-            if ((rc = fill_tables(J.svo, &J.feats, J.lod, tj.tb))) break;
+            // a summed corner table serves a trace with analytic normals (every
+            // query inside a voxel of the job's LOD)
+            if ((rc = fill_tables(J.svo, &J.feats, J.lod, tj.tb, b->normal_mode != NGLOD_NORMALS_FD))) break;
             if ((rc = check_decoder(&J.dec))) break;
             const int D = J.lod + kFirstFeatureDepth - 1;
             if (J.lod < 1 || D >= J.svo->num_depths) {

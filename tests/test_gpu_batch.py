@@ -187,3 +187,26 @@ def test_batch_full_workload_equals_per_scene(ng):
         lists, ref = per_job(ng, j, "bf16")
         assert_same(rnd.outputs(k), lists, ref)
     rnd.free()
+
+
+@pytest.mark.parametrize("decode", ["f32", "bf16"])
+def test_batch_summed_tables_equal_per_job(ng, items, decode):
+    # every other job reads the summed corner table of its LOD: the batch
+    # takes each job's gather depth from that job's tables
+    from paper_2101_10994_gb300 import batch as B
+    jobs = make_jobs(ng, items, decode)
+    for k, j in enumerate(jobs):
+        if k % 2 == 0:
+            j.feats = j.feats.summed(j.svo, j.lod)
+    rnd = B.BatchRenderer(jobs, decode=decode)
+    rnd.frame()
+    rnd.check()
+    for k, j in enumerate(jobs):
+        lists, ref = per_job(ng, j, decode)
+        assert_same(rnd.outputs(k), lists, ref)
+    # FD normals leave the hit voxel: a batch whose own normals are FD ones
+    # refuses summed tables
+    rnd.params.want_normals, rnd.params.normal_mode, rnd.params.fd_h = 1, ng.NORMALS["fd"], 1e-3
+    with pytest.raises(ng.NglodError, match="summed"):
+        rnd._create()
+    rnd.free()
