@@ -140,9 +140,10 @@ int nglod_features_absmax(const nglod_svo* svo, const nglod_features* feats, int
  *   out     device [C_lod, 32] FP32 (svo_info's corner count), 32-byte
  *           aligned; every row is written
  * The interpolation weights at the corners are exact dyadic numbers (exact
- * in FP32 up to LOD 8); each row is accumulated in FP64 (levels in order
- * 1..lod, corners in index order) and rounded once to FP32, so the table is
- * the same whichever voxel a shared corner is computed from.
+ * in FP32 up to LOD 8); each row is accumulated with the rounding errors of
+ * every product and sum kept (an FP32 pair, levels in order 1..lod, corners
+ * in index order) and rounded once, so the table is the same whichever
+ * voxel a shared corner is computed from.
  * Stream-ordered, no synchronisation.
  * NGLOD_ERR_INVALID_ARG for NULL pointers, lod outside 1..svo's LODs or
  * features not covering lod; NGLOD_ERR_NOT_SUPPORTED for summed input. */

@@ -14,11 +14,16 @@
 // its local coordinates in the ancestor voxel: (P - base) / 2^s with
 // s = L's depth - that depth <= 7, so u and 1 - u carry at most 8
 // significant bits and every trilinear weight (a product of three) at most
-// 24: the weights are exact in FP32, the terms with weight 0 are skipped,
-// and the sum is accumulated in FP64.  A corner shared by several voxels is
-// computed by each of them with the same non-zero terms in the same order
-// (where two of them have different ancestors, the corner lies on the
-// ancestors' common face, edge or vertex, whose corners they share), so
+// 24: the weights are exact in FP32 and the terms with weight 0 are skipped.
+// The sum is carried as an unevaluated pair hi + lo of FP32 numbers: each
+// product w r splits exactly into its rounded value and fmaf's remainder,
+// each addition into its rounded value and the two-sum remainder (Knuth's
+// TwoSum), and the remainders gather in lo, so the one final rounding of
+// hi + lo dominates the error (FP64 arithmetic, the plain alternative, runs
+// at a small fraction of the FP32 rate on GB300).  A corner shared by several
+// voxels is computed by each of them with the same non-zero terms in the
+// same order (where two of them have different ancestors, the corner lies on
+// the ancestors' common face, edge or vertex, whose corners they share), so
 // every write of a row carries the same value.
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -33,16 +38,28 @@ namespace nglod {
 namespace {
 
 template <typename T>
-__device__ __forceinline__ double feat_at(const void* base, long long i);
+__device__ __forceinline__ float feat_at(const void* base, long long i);
 
 template <>
-__device__ __forceinline__ double feat_at<float>(const void* base, long long i) {
-    return (double)__ldg(static_cast<const float*>(base) + i);
+__device__ __forceinline__ float feat_at<float>(const void* base, long long i) {
+    return __ldg(static_cast<const float*>(base) + i);
 }
 
 template <>
-__device__ __forceinline__ double feat_at<__half>(const void* base, long long i) {
-    return (double)__half2float(static_cast<const __half*>(base)[i]);
+__device__ __forceinline__ float feat_at<__half>(const void* base, long long i) {
+    return __half2float(static_cast<const __half*>(base)[i]);
+}
+
+// hi + lo += w r, with the rounding errors of the product and of the sum
+// kept in lo.
+__device__ __forceinline__ void acc2(float& hi, float& lo, float w, float r) {
+    const float p = __fmul_rn(w, r);
+    const float ep = __fmaf_rn(w, r, -p);          // w r - p, exact
+    const float s = __fadd_rn(hi, p);
+    const float bb = __fsub_rn(s, hi);
+    const float es = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));   // hi + p - s, exact
+    hi = s;
+    lo = __fadd_rn(lo, __fadd_rn(es, ep));
 }
 
 template <typename T>
@@ -56,7 +73,7 @@ __global__ void __launch_bounds__(256) k_sum_features(const Tables tb, int D, lo
         const uint32_t ijk = tb.node[D][v].ijk;
         const uint32_t vc[3] = {unpack_i(ijk), unpack_j(ijk), unpack_k(ijk)};
         const uint32_t P[3] = {vc[0] + (c & 1), vc[1] + ((c >> 1) & 1), vc[2] + ((c >> 2) & 1)};
-        double z = 0.0;
+        float hi = 0.0f, lo = 0.0f;
 #pragma unroll 1
         for (int dp = kFirstFeatureDepth; dp <= D; ++dp) {
             const int sh = D - dp;
@@ -72,12 +89,12 @@ __global__ void __launch_bounds__(256) k_sum_features(const Tables tb, int D, lo
                 for (int ax = 0; ax < 3; ++ax) w *= ((cc >> ax) & 1) ? u[ax] : 1.0f - u[ax];
                 if (w != 0.0f) {
                     const int row = __ldg(tb.corners[dp] + (size_t)a * 8 + cc);
-                    z = fma((double)w, feat_at<T>(fb, (long long)row * kFeatDim + lane), z);
+                    acc2(hi, lo, w, feat_at<T>(fb, (long long)row * kFeatDim + lane));
                 }
             }
         }
         const int row = __ldg(tb.corners[D] + v * 8 + c);
-        out[(size_t)row * kFeatDim + lane] = __double2float_rn(z);
+        out[(size_t)row * kFeatDim + lane] = __fadd_rn(hi, lo);
     }
 }
 
