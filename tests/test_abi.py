@@ -49,3 +49,31 @@ def test_binding_has_no_cpu_fallback(monkeypatch, tmp_path):
     monkeypatch.setattr(nglod, "_lib", None)
     with pytest.raises(RuntimeError, match="no CPU fallback"):
         nglod.lib()
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """The ctypes structures of the binding have the header's sizes and field
+    offsets (a host C compiler lays the header's structs out; no GPU)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no host C compiler")
+    structs = {"nglod_features": nglod._Features, "nglod_decoder": nglod._Decoder,
+               "nglod_trace_params": nglod._TraceParams, "nglod_trace_job": nglod._TraceJob}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "nglod.h"', "int main(void) {"]
+    for cname, cls in structs.items():
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in cls._fields_:
+            lines.append(f'printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", "-I", B.INCLUDE, str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(line.split()[:2]): int(line.split()[2]) for line in out if line}
+    for cname, cls in structs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(cls), cname
+        for fname, _ in cls._fields_:
+            assert got[(cname, fname)] == getattr(cls, fname).offset, (cname, fname)
