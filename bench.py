@@ -603,7 +603,8 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": R / v * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "csg64_seed0_lod5_1920x1080", "lod": 5, "rays": R, "max_steps": 128,
-                       "eps": 1e-3, "decoder": "32->128->1 readout-embedded", "l2": "n/a (CPU)"},
+                       "eps": 1e-3, "features": "f32 m=32, per-level tables (promoted to f64)",
+                       "decoder": "32->128->1 readout-embedded", "l2": "n/a (CPU)"},
             "cpu_baseline": {"value": v, "unit": "rays/s", "cores": cores, "kind": "oracle", "cpu": cpu_model(),
                              "sample": f"per step a uniform random sample of the 1920x1080 frame's rays "
                                        f"(~{budget:.0f} s of CPU work), FP64 oracle: brute-force traversal + "
