@@ -173,6 +173,44 @@ def flops_per_query(in_dim, lod, decode):
     return interp, layer1, out
 
 
+def measure_ceilings(dev, reps=5):
+    """Hardware ceilings measured on this GPU with the library's probe kernels
+    (include/nglod_probe.h), CUDA events, best of ``reps`` after a warm-up:
+    L2 read bandwidth (a 40 MB buffer, well inside the L2, read 20 times with
+    L2-only loads), L1 read bandwidth (each of 4 blocks per SM re-reading its
+    own 32 KB window with the gathers' 32-byte read-only loads) and FP32 FMA
+    throughput (8 independent chains per thread); the SM count from the
+    device."""
+    import torch
+
+    from paper_2101_10994_gb300 import nglod as ng
+
+    def best(fn):
+        fn()
+        ts, work = [], 0
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            work = fn()
+            e1.record()
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1) * 1e-3)
+        return work / min(ts)
+
+    l2buf = torch.ones(40 << 20, dtype=torch.uint8, device=dev)
+    sms = ng.device_sms()
+    l1buf = torch.ones(sms * 4 * (32 << 10), dtype=torch.uint8, device=dev)
+    out = {"sms": sms,
+           "l2_read_GBps": best(lambda: ng.probe("l2", l2buf, passes=20)) / 1e9,
+           "l1_read_GBps": best(lambda: ng.probe("l1", l1buf, passes=400, window_bytes=32 << 10)) / 1e9,
+           "ffma_tflops": best(lambda: ng.probe("ffma", iters=4096)) / 1e12,
+           "how": "probe kernels of include/nglod_probe.h, CUDA events, best of 5 after a warm-up: L2 = 40 MB "
+                  "read 20x with ld.global.cg; L1 = 32 KB per block (4 blocks/SM) read 400x with "
+                  "ld.global.nc.v8; FFMA = 8 chains x 16 x 4096 steps per thread, 8 x 256 threads per SM"}
+    del l2buf, l1buf
+    return out
+
+
 def run_ours(args, rank, world, local_rank):
     import numpy as np
     import torch
@@ -463,7 +501,8 @@ def run_ours(args, rank, world, local_rank):
                d2h_bytes_per_step=int(sum(v.numel() * v.element_size() for v in h_out.values())),
                schedule=f"{ech} chunks on {ech} streams, copies overlapped with the other chunks' work")
     svo.free()
-    return W, results, clock_info, e2e, modes
+    ceilings = measure_ceilings(dev)
+    return W, results, clock_info, e2e, modes, ceilings
 
 
 def source_hash(kernel):
@@ -523,8 +562,10 @@ def traversal_roofline(W, res, mode, peaks):
     # the lower bound of any design: rays in, the final CSR lists out
     sizes = res["level_sizes"]
     lower = 24 * sizes[0] + 4 * (sizes[0] + 1) + 12 * sizes[-1]
+    traffic = profiled_traffic("k_traverse")
     return {"bound": "hbm", "kernel": "k_traverse", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-            "frac": achieved / hbm, "traffic": profiled_traffic("k_traverse"),
+            "frac": achieved / hbm, "traffic": traffic,
+            "dram_frac": (traffic / sec / 1e9 / hbm) if traffic else None,
             "bytes_per_frame": nbytes, "launches_per_frame": 3,
             "lower_bound_bytes": lower, "lower_bound_frac": lower / sec / 1e9 / hbm,
             "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in peaks else "fallback",
@@ -532,10 +573,12 @@ def traversal_roofline(W, res, mode, peaks):
             "note": "issue-bound on the 8-child slab tests (ncu: ~64 % issue active); node records hit L1/L2"}
 
 
-def trace_roofline(W, res, mode, peaks, levels=None):
+def trace_roofline(W, res, mode, peaks, levels=None, ceilings=None):
     """Dominant kernel = the sphere tracer (largest share of the frame in the
     launch list): its decode contraction against the tensor pipe (BF16) or
-    its FP32 arithmetic against the CUDA cores."""
+    its FP32 arithmetic against the CUDA cores (the measured FFMA ceiling);
+    its feature gathers against the measured L1 and L2 read bandwidth."""
+    ceilings = ceilings or {}
     levels = W["lod"] if levels is None else levels      # levels gathered per query (1: summed table)
     interp, layer1, outl = flops_per_query(W["dec"].in_dim, levels, mode)
     q = res["queries_per_frame"]
@@ -549,14 +592,29 @@ def trace_roofline(W, res, mode, peaks, levels=None):
                 "flops_per_query": layer1, "queries_per_launch": q,
                 "peak_source": "MEASURED_PEAKS.json bf16_tflops burst (of measured)",
                 "note": "the kernel is bound by feature-gather latency (L1/L2), not by the 128x32 contraction",
-                "gather_bytes_per_query": 8 * 32 * 4 * levels,
-                "gather_GBps": q * 8 * 32 * 4 * levels / sec / 1e9}
-    sm_mhz = peaks.get("sm_max_mhz", 2070.0)
-    peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+                **gather_fracs(q, levels, sec, ceilings)}
+    if "ffma_tflops" in ceilings:
+        peak, src = ceilings["ffma_tflops"], "measured FFMA probe (of measured)"
+    else:
+        sms = ceilings.get("sms", 152)
+        peak = sms * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        src = f"{sms} SMs x 128 FP32 lanes x 2 flop x sm_max_mhz (nominal)"
     achieved = q * (interp + layer1 + outl) / sec / 1e12
     return {"bound": "alu", "kernel": kern, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak, "traffic": profiled_traffic(kern),
-            "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x sm_max_mhz"}
+            "frac": achieved / peak, "traffic": profiled_traffic(kern), "flops_per_query": interp + layer1 + outl,
+            "queries_per_launch": q, "peak_source": src, **gather_fracs(q, levels, sec, ceilings)}
+
+
+def gather_fracs(q, levels, sec, ceilings):
+    """The gathers' requested bytes (8 corner rows of 32 FP32 channels per
+    level per query) per second, as a fraction of the measured L1 and L2 read
+    bandwidth (every request passes L1; what misses it is served by L2)."""
+    gbps = q * 8 * 32 * 4 * levels / sec / 1e9
+    out = {"gather_bytes_per_query": 8 * 32 * 4 * levels, "gather_GBps": gbps}
+    if "l1_read_GBps" in ceilings:
+        out["gather_frac_of_l1"] = gbps / ceilings["l1_read_GBps"]
+        out["gather_frac_of_l2"] = gbps / ceilings["l2_read_GBps"]
+    return out
 
 
 # ----------------------------------------------------------------------------
@@ -593,14 +651,20 @@ def run_reference(args):
     oracle.build()
     cores = os.cpu_count()
     budget = max(1.0, min(20.0, 100.0 / max(1, args.steps + args.warmup)))
-    rates = []
+    rates, ns, dts = [], [], []
     for k in range(args.warmup + args.steps):
         rate, n, dt = oracle_rate(W, budget, seed=k)
         if k >= args.warmup:
             rates.append(rate)
+            ns.append(n)
+            dts.append(dt)
     v = statistics.mean(rates)
+    # a step is the sampled rays of the frame: ms_per_step is the time those
+    # took; the time the whole frame would take at that rate is separate
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "rays/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": R / v * 1e3, "higher_is_better": True,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.mean(dts) * 1e3,
+            "sample_rays_per_step": statistics.mean(ns), "sample_s_per_step": statistics.mean(dts),
+            "projected_ms_per_frame": R / v * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "csg64_seed0_lod5_1920x1080", "lod": 5, "rays": R, "max_steps": 128,
                        "eps": 1e-3, "features": "f32 m=32, per-level tables (promoted to f64)",
@@ -798,7 +862,7 @@ def main():
         import torch.distributed as td
         torch.cuda.set_device(local_rank)
         td.init_process_group("nccl")
-    W, res, clocks, e2e, modes = run_ours(args, rank, world, local_rank)
+    W, res, clocks, e2e, modes, ceilings = run_ours(args, rank, world, local_rank)
     if rank == 0:
         peaks = {}
         pp = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -819,8 +883,11 @@ def main():
                        "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world}"},
             "queries_per_s": r["queries_per_s"],
             "modes": res,
-            "roofline": trace_roofline(W, r, head, peaks, 1 if args.features == "summed" else None),
+            "roofline": trace_roofline(W, r, head, peaks, 1 if args.features == "summed" else None, ceilings),
             "traversal_roofline": traversal_roofline(W, r, head, peaks),
+            "fp32_roofline": (trace_roofline(W, res["f32"], "f32", peaks, 1 if args.features == "summed" else None,
+                                             ceilings) if "f32" in res else None),
+            "ceilings": ceilings,
             "clocks": clocks,
             "e2e": e2e,
             # per frame: traversal (tiles, tile scan, placement) + ray-group order (keys, bucket

@@ -79,12 +79,16 @@ typedef struct {
 /* One LOD's decoder (Eq. 2): d = W2 . relu(W1 v + b1) + b2 with
  * v = [x, z] (in_dim = m + 3) or v = z (in_dim = m).  FP32 master weights;
  * the BF16 decode rounds W1 and z to bf16 (round-to-nearest-even) and
- * accumulates in FP32. */
+ * accumulates in FP32.  Every parameter, b2 included, is read from device
+ * memory by the kernels when they run, so an optimiser step that updates
+ * them in place (nglod_adam_step) reaches the next call, or the next replay
+ * of a captured CUDA graph, without any host copy.  NULL pointers are
+ * NGLOD_ERR_INVALID_ARG. */
 typedef struct {
     const float* W1;       /* [hidden, in_dim] row-major (device)             */
     const float* b1;       /* [hidden] (device)                               */
     const float* W2;       /* [hidden] (device)                               */
-    float b2;
+    const float* b2;       /* one float (device)                              */
     int in_dim;            /* 32 or 35                                        */
     int hidden;            /* only 128 is built                               */
 } nglod_decoder;
@@ -151,6 +155,21 @@ int nglod_sum_features(const nglod_svo* svo, const nglod_features* feats, int lo
 
 /* Text of the calling thread's last error ("" if none). */
 const char* nglod_last_error(void);
+
+/* nglod_set_wait_polls -- the poll budget of the bounded wait each
+ * tensor-core kernel (the BF16 / FP8 / FP32-split decodes of sdf_query,
+ * sphere_trace, sphere_trace_blend, sdf_query_blend and batches, and the
+ * tensor-core adjoint) takes on the completion of every tile's MMA.  The
+ * paper has no counterpart: this is a testing hook for the expiry path.
+ * polls >= 0 sets the budget of every launch that follows, process-wide
+ * (0: every such wait expires at once, so the call reports
+ * NGLOD_ERR_TIMEOUT without any GPU fault or hang); polls < 0 restores the
+ * default (2^24 polls, tens of milliseconds).  After an expiry a kernel
+ * raises its status word, waits for its MMA in flight with the default
+ * budget, frees its tensor memory and returns; outputs of that call are
+ * unspecified, and a later call with the default budget is unaffected.
+ * Always returns NGLOD_OK. */
+int nglod_set_wait_polls(int64_t polls);
 
 /* svo_build -- Sec. 3.2 (SVO over [-1,1]^3, corner features shared between
  * neighbours) and Sec. 3.4 ("pointers ... precalculated in an initialization
@@ -240,7 +259,10 @@ int svo_trace_rays(const nglod_svo* svo, const float* o, const float* d, int64_t
  * The workspace is a 32 MiB array built into the library, present on every
  * GPU that loads it until the process exits.  The first call on a device
  * (with that device current) looks up the array's device address; make it
- * before any stream capture.  The staging capacity is whatever fits in
+ * before any stream capture.  Later calls outside a capture look it up again
+ * (so a cudaDeviceReset, after which the array may move, is followed by a
+ * fresh lookup); calls inside a capture reuse the last address found on that
+ * device.  The staging capacity is whatever fits in
  * 32 MiB after the per-ray and per-tile records (about 2.1 M entries at
  * 2 M rays); R whose records alone exceed it is rejected with
  * NGLOD_ERR_CAPACITY before anything is read or launched, and more entries
@@ -331,7 +353,10 @@ size_t sphere_trace_workspace(int64_t R);
  *                       list, so long rays start early; it changes only the
  *                       schedule, never a ray's outputs) and, per hit-list
  *                       position, the ReLU mask of the hit's last decode
- *                       (128 bits), which trace_normals reuses.
+ *                       (128 bits), which trace_normals reuses (not with the
+ *                       FP8 decode, whose 4-bit z can zero or flip a
+ *                       pre-activation: its normals recompute the forward
+ *                       pass in FP32).
  * Outputs: t_hit [R] (+inf on miss), hit [R] uint8, steps [R] int32
  * (nullable: decodes taken), normal [R, 3] (nullable; normalised analytic
  * gradient of the decoded SDF at the hit point in FP32, or its central

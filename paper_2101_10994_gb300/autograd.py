@@ -37,8 +37,8 @@ class NeuralSDF:
 
 def _views(field):
     F = ng.Features.from_tensors([f.detach() for f in field.feats])
-    b2 = field.b2.detach().cpu().tolist()
-    decs = [ng.DecoderDev.from_tensors(w1.detach(), b1.detach(), w2.detach(), b2[i])
+    b2 = field.b2.detach()
+    decs = [ng.DecoderDev.from_tensors(w1.detach(), b1.detach(), w2.detach(), b2[i:i + 1])
             for i, (w1, b1, w2) in enumerate(zip(field.W1, field.b1, field.W2))]
     return F, decs
 

@@ -56,7 +56,7 @@ struct BackArgs {
     const float* g;          // [Q] upstream gradient of this LOD's output (null: L2 mode)
     const float* target;     // L2 mode: [Q] target distances
     float loss_scale;        // L2 mode: g = loss_scale * 2 (d - target)
-    float b2;                // decoder output bias (L2 mode forward)
+    const float* b2;         // decoder output bias, one float on the device (L2 mode forward)
     float* loss;             // L2 mode: += sum_q (d - target)^2 (device scalar)
     long long Q;
     int D;
@@ -184,7 +184,7 @@ __global__ void __launch_bounds__(kThreads) k_backward(const Tables tb, const Ba
         }
         if (!A.g) {
             // L2 mode: this LOD's prediction d, then g = scale * 2 (d - target)
-            float dpred = A.b2;
+            float dpred = __ldg(A.b2);
 #pragma unroll 1
             for (int h = 0; h < kHidden; ++h) {
                 const float4* w = reinterpret_cast<const float4*>(S.sd.W1 + h * K4);
@@ -411,10 +411,10 @@ __global__ void __launch_bounds__(kThreads) k_backward(const Tables tb, const Ba
 
 template <typename T, int IN, bool DET>
 void launch_back(const Tables& tb, const BackArgs& A, int grid, cudaStream_t st) {
-    static bool once = (cudaFuncSetAttribute(k_backward<T, IN, DET>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)sizeof(BackSmem)),
-                        true);
-    (void)once;
+    static std::atomic<unsigned long long> done{0};
+    once_per_device(done, [] {
+        cudaFuncSetAttribute(k_backward<T, IN, DET>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(BackSmem));
+    });
     k_backward<T, IN, DET><<<grid, kThreads, sizeof(BackSmem), st>>>(tb, A);
 }
 

@@ -41,7 +41,6 @@ namespace {
 
 constexpr int kTQ = 128;                         // queries per tile = threads per CTA
 constexpr uint32_t kColP = 0, kColG = 128, kColW = 192, kTmemCols = 256;
-constexpr long kPolls = 1l << 24;
 
 template <int KV>
 struct TcSmem {
@@ -59,7 +58,7 @@ struct TcArgs {
     const float* W1;
     const float* b1;
     const float* W2;
-    float b2;
+    const float* b2;         // one float (device)
     const float* x;          // [Q, 3]
     const float* g;          // [Q] upstream gradient of this LOD's output (null: L2 mode)
     const float* target;     // L2 mode: [Q]
@@ -73,6 +72,7 @@ struct TcArgs {
     float* gW2;
     float* gb2;
     int* err;
+    long long polls;         // poll budget of each MMA wait
 };
 
 __device__ __forceinline__ void red_add_v4(float* addr, float4 v) {
@@ -273,7 +273,7 @@ __global__ void __launch_bounds__(kTQ, 2) k_backward_tc(const Tables tb, const T
                              tc::smem_desc_kmajor(w1 + ks * 256, 128, 128 * KC), idesc, ks > 0);
             tc::mma_commit(&S.bar);
         }
-        bool ok = tc::mbar_wait(&S.bar, phase, kPolls);
+        bool ok = tc::mbar_wait(&S.bar, phase, A.polls);
         phase ^= 1u;
         tc::fence_after_sync();
         if (!__syncthreads_and(ok)) {
@@ -282,7 +282,7 @@ __global__ void __launch_bounds__(kTQ, 2) k_backward_tc(const Tables tb, const T
             break;
         }
         // (C) epilogue: the prediction, then dpre (bf16 into A2) and the row sums of db1, dW2
-        float dval = A.b2;
+        float dval = __ldg(A.b2);
 #pragma unroll 1
         for (int c0 = 0; c0 < kHidden; c0 += 32) {
             float v[32];
@@ -346,7 +346,7 @@ __global__ void __launch_bounds__(kTQ, 2) k_backward_tc(const Tables tb, const T
             tc::mma_commit(&S.bar);
         }
         any = true;
-        ok = tc::mbar_wait(&S.bar, phase, kPolls);
+        ok = tc::mbar_wait(&S.bar, phase, A.polls);
         phase ^= 1u;
         tc::fence_after_sync();
         if (!__syncthreads_and(ok)) {
@@ -409,7 +409,7 @@ __global__ void __launch_bounds__(kTQ, 2) k_backward_tc(const Tables tb, const T
             }
         }
     }
-    if (!drained) tc::mbar_wait(&S.bar, phase ^ 1u, kPolls);   // let an expired MMA finish
+    if (!drained) tc::mbar_wait(&S.bar, phase ^ 1u, kDefaultWaitPolls);   // let an expired MMA finish
     tc::fence_before_sync();
     __syncthreads();
     if (warp == 0) tc::tmem_dealloc(taddr, kTmemCols);
@@ -419,9 +419,10 @@ template <typename T, int IN>
 void launch_tc(const Tables& tb, const TcArgs& A, int grid, cudaStream_t st) {
     constexpr int KV = (IN - kFeatDim) ? 48 : 32;
     constexpr int smem = (int)((sizeof(TcSmem<KV>) + 1023) / 1024 * 1024);
-    static bool once = (cudaFuncSetAttribute(k_backward_tc<T, IN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem),
-                        true);
-    (void)once;
+    static std::atomic<unsigned long long> done{0};
+    once_per_device(done, [] {
+        cudaFuncSetAttribute(k_backward_tc<T, IN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    });
     k_backward_tc<T, IN><<<grid, kTQ, smem, st>>>(tb, A);
 }
 
@@ -476,6 +477,7 @@ int run_backward_tc(const nglod_svo* svo, const nglod_features* feats, const ngl
         A.gW2 = h_grad_W2[lod - 1];
         A.gb2 = grad_b2 + (lod - 1);
         A.err = err;
+        A.polls = mma_wait_polls();
         if (dec.in_dim == 35) {
             if (f16) launch_tc<__half, 35>(tb, A, grid, st); else launch_tc<float, 35>(tb, A, grid, st);
         } else {

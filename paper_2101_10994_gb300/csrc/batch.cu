@@ -51,7 +51,8 @@ __global__ void k_batch_reset(TraceJob* __restrict__ jobs, int njobs, int* __res
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < njobs + nwords; i += gridDim.x * blockDim.x) {
         if (i < njobs) {
             *jobs[i].A.hit_count = 0;
-            jobs[i].A.hit_count[kWsMaskFlagWord - 2] = 1;   // the batched tracers record the hits' masks
+            // the batched tracers record the hits' masks (not for the FP8 decode)
+            jobs[i].A.hit_count[kWsMaskFlagWord - 2] = jobs[i].A.hit_mask ? 1 : 0;
         }
         else words[i - njobs] = 0;
     }
@@ -237,7 +238,7 @@ extern "C" int sphere_trace_batch_create(const nglod_trace_job* jobs, int num_jo
             A.hit_count = (int*)J.work + 2;
             A.hit_vox = (int32_t*)((char*)J.work + trace_ws_hit_vox_offset());
             A.hit_list = (int32_t*)((char*)J.work + trace_ws_hit_list_offset(J.R));
-            A.hit_mask = (uint4*)((char*)J.work + trace_ws_mask_offset(J.R));
+            A.hit_mask = dec_t == NGLOD_FP8E4M3 ? nullptr : (uint4*)((char*)J.work + trace_ws_mask_offset(J.R));
             tj.ray_base = base;
             base += (J.R + 31) / 32 * 32;     // chunks of 32 never span two jobs
             b->h_jobs.push_back(tj);

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <cstdio>
 #include <string>
 
@@ -54,6 +55,28 @@ void set_error(const std::string& msg);
 int fail(int code, const std::string& msg);
 int check_cuda(cudaError_t e, const char* what);
 int device_sms();
+
+// Bounded tensor-core waits: the poll budget of the wait for each tile's
+// MMA (nglod_set_wait_polls changes it, for tests of the expiry path); the
+// wait that drains an MMA after an expiry always keeps the default, so no
+// MMA is still in flight when its tensor memory is freed.
+constexpr long long kDefaultWaitPolls = 1ll << 24;
+long long mma_wait_polls();
+
+// Runs f once for each device it is called on (the device current at the
+// call): kernel attributes such as cudaFuncSetAttribute apply to the current
+// device only, so a process that launches on several devices must set them
+// on each.  Two threads may both run f for one device; f must be idempotent.
+template <class F>
+inline void once_per_device(std::atomic<unsigned long long>& done, F&& f) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const unsigned long long bit = 1ull << (dev & 63);
+    if (!(done.load(std::memory_order_acquire) & bit)) {
+        f();
+        done.fetch_or(bit, std::memory_order_acq_rel);
+    }
+}
 
 #define NGLOD_CUDA(call)                                         \
     do {                                                         \

@@ -57,7 +57,7 @@ int check_decoder(const nglod_decoder* dec) {
     if (!dec) return fail(NGLOD_ERR_INVALID_ARG, "NULL decoder");
     if (dec->hidden != kHidden) return fail(NGLOD_ERR_NOT_SUPPORTED, "only hidden = 128 is built");
     if (dec->in_dim != 32 && dec->in_dim != 35) return fail(NGLOD_ERR_NOT_SUPPORTED, "in_dim must be 32 or 35");
-    if (!dec->W1 || !dec->b1 || !dec->W2) return fail(NGLOD_ERR_INVALID_ARG, "NULL decoder weights");
+    if (!dec->W1 || !dec->b1 || !dec->W2 || !dec->b2) return fail(NGLOD_ERR_INVALID_ARG, "NULL decoder weights");
     return NGLOD_OK;
 }
 
@@ -73,7 +73,7 @@ struct DecPtrs {
     const float* W1;
     const float* b1;
     const float* W2;
-    float b2;
+    const float* b2;      // one float, read by the kernel at launch time
 };
 
 // Finite-difference normals (supplementary Sec. A.4 takes the normals by
@@ -137,6 +137,7 @@ __global__ void __launch_bounds__(kThreads) k_sdf_query(const DecPtrs dp, const 
     __shared__ __align__(16) SmemDecoder sd;
     stage_decoder<IN>(sd, dp.W1, dp.b1, dp.W2);
     __syncthreads();
+    const float b2 = __ldg(dp.b2);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int g4 = lane >> 2, l4 = lane & 3, gb4 = g4 << 2;
     const unsigned gm4 = 0xfu << gb4;
@@ -178,7 +179,7 @@ __global__ void __launch_bounds__(kThreads) k_sdf_query(const DecPtrs dp, const 
             zr[1] = zc;
         }
         __syncwarp();
-        const float out = mlp_f32<IN>(sd, dp.b2, zb + lane * kZStride, x0, x1, x2);
+        const float out = mlp_f32<IN>(sd, b2, zb + lane * kZStride, x0, x1, x2);
         if constexpr (FD) {
             fd_write(F, lane, act, ray, out);
         } else if (act) {
@@ -441,6 +442,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_trace_f32(const DecPtrs dp, con
     __shared__ __align__(16) SmemDecoder sd;
     stage_decoder<IN>(sd, dp.W1, dp.b1, dp.W2);
     __syncthreads();
+    const float b2 = __ldg(dp.b2);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float* zb = zbuf[warp];
     RaySlot S;
@@ -475,7 +477,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_trace_f32(const DecPtrs dp, con
         }
         __syncwarp();
         uint4 mask;
-        const float dhat = mlp_f32<IN, true>(sd, dp.b2, zb + lane * kZStride, x0, x1, x2, &mask);
+        const float dhat = mlp_f32<IN, true>(sd, b2, zb + lane * kZStride, x0, x1, x2, &mask);
         __syncwarp();
         if (act) step_update(S, dhat, A, tb);
         publish_hits(S, A, lane, mask);
@@ -500,6 +502,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_trace_batch_f32(const TraceJob*
         __syncthreads();
         stage_decoder<IN>(sd, G.W1, G.b1, G.W2);
         __syncthreads();
+        const float b2 = __ldg(G.b2);
         RaySlot S;
         S.ray = -1;
         S.hit_ray = -1;
@@ -531,7 +534,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_trace_batch_f32(const TraceJob*
             }
             __syncwarp();
             uint4 mask;
-            const float dhat = mlp_f32<IN, true>(sd, G.b2, zb + lane * kZStride, x0, x1, x2, &mask);
+            const float dhat = mlp_f32<IN, true>(sd, b2, zb + lane * kZStride, x0, x1, x2, &mask);
             __syncwarp();
             if (act) step_update(S, dhat, jobs[S.job].A, jobs[S.job].tb);
             publish_hits_batch(S, jobs, mask);
@@ -595,6 +598,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_trace_blend_f32(const DecPtrs l
     stage_decoder<IN>(slo, lo.W1, lo.b1, lo.W2);
     stage_decoder<IN>(shi, hi.W1, hi.b1, hi.W2);
     __syncthreads();
+    const float b2lo = __ldg(lo.b2), b2hi = __ldg(hi.b2);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int g4 = lane >> 2, l4 = lane & 3, gb4 = g4 << 2;
     const unsigned gm4 = 0xfu << gb4;
@@ -638,7 +642,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_trace_blend_f32(const DecPtrs l
             }
             __syncwarp();
             uint4 mk;
-            const float dv = mlp_f32<IN, true>(pass ? shi : slo, pass ? hi.b2 : lo.b2, zb + lane * kZStride, x0,
+            const float dv = mlp_f32<IN, true>(pass ? shi : slo, pass ? b2hi : b2lo, zb + lane * kZStride, x0,
                                                x1, x2, &mk);
             if (pass) {
                 dhi = dv;
@@ -666,6 +670,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_query_blend_f32(const DecPtrs l
     stage_decoder<IN>(slo, lo.W1, lo.b1, lo.W2);
     stage_decoder<IN>(shi, hi.W1, hi.b1, hi.W2);
     __syncthreads();
+    const float b2lo = __ldg(lo.b2), b2hi = __ldg(hi.b2);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int g4 = lane >> 2, l4 = lane & 3, gb4 = g4 << 2;
     const unsigned gm4 = 0xfu << gb4;
@@ -720,7 +725,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_query_blend_f32(const DecPtrs l
                 }
             }
             __syncwarp();
-            const float dv = mlp_f32<IN>(pass ? shi : slo, pass ? hi.b2 : lo.b2, zb + lane * kZStride, x0, x1, x2);
+            const float dv = mlp_f32<IN>(pass ? shi : slo, pass ? b2hi : b2lo, zb + lane * kZStride, x0, x1, x2);
             if (pass) dhi = dv;
             else dlo = dv;
             __syncwarp();
@@ -741,17 +746,17 @@ void go_blend_f32(bool trace, const DecPtrs& lo, const DecPtrs& hi, float alpha,
                   const TraceArgs* A, const float* x, long long Q, int D, float* sdf, const FDArgs* F, int grid,
                   cudaStream_t st) {
     if (trace) {
-        static bool once = (allow_blend_smem(k_trace_blend_f32<T, IN>), true);
-        (void)once;
+        static std::atomic<unsigned long long> done{0};
+        once_per_device(done, [] { allow_blend_smem(k_trace_blend_f32<T, IN>); });
         k_trace_blend_f32<T, IN><<<grid, kThreads, kBlendF32Smem, st>>>(lo, hi, alpha, tb, *A);
     } else if (F) {
-        static bool once = (allow_blend_smem(k_query_blend_f32<T, IN, true>), true);
-        (void)once;
+        static std::atomic<unsigned long long> done{0};
+        once_per_device(done, [] { allow_blend_smem(k_query_blend_f32<T, IN, true>); });
         k_query_blend_f32<T, IN, true><<<grid, kThreads, kBlendF32Smem, st>>>(lo, hi, alpha, tb, nullptr, 0, D,
                                                                                 nullptr, *F);
     } else {
-        static bool once = (allow_blend_smem(k_query_blend_f32<T, IN, false>), true);
-        (void)once;
+        static std::atomic<unsigned long long> done{0};
+        once_per_device(done, [] { allow_blend_smem(k_query_blend_f32<T, IN, false>); });
         k_query_blend_f32<T, IN, false><<<grid, kThreads, kBlendF32Smem, st>>>(lo, hi, alpha, tb, x, Q, D, sdf,
                                                                                  FDArgs{});
     }
@@ -1132,7 +1137,11 @@ extern "C" int sphere_trace(const nglod_svo* svo, const nglod_features* feats, c
     rc = check_decoder(dec);
     if (rc) return rc;
     if ((rc = enqueue_ray_order(A, work, st))) return rc;
-    if ((rc = enable_hit_masks(A, work, st))) return rc;
+    // the FP8 decode's ReLU masks are not recorded: with z rounded to four
+    // significant bits a pre-activation can round to zero or flip sign (a
+    // read-out unit pair at z = 0 would give a zero gradient), so its
+    // normals recompute the forward pass in FP32
+    if (params->decode_dtype != NGLOD_FP8E4M3 && (rc = enable_hit_masks(A, work, st))) return rc;
     if (params->decode_dtype == NGLOD_F32) {
         rc = launch_trace_fp32(dec, tb, A, f16, svo->num_sms, st);
     } else if (params->decode_dtype == NGLOD_BF16 || params->decode_dtype == NGLOD_FP8E4M3 ||

@@ -13,6 +13,7 @@
 // sorted unique corner keys.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstring>
 #include <new>
 #include <string>
@@ -35,6 +36,10 @@ int check_cuda(cudaError_t e, const char* what) {
     g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
     return e == cudaErrorMemoryAllocation ? NGLOD_ERR_OOM : NGLOD_ERR_CUDA;
 }
+
+static std::atomic<long long> g_wait_polls{kDefaultWaitPolls};
+
+long long mma_wait_polls() { return g_wait_polls.load(std::memory_order_relaxed); }
 
 int device_sms() {
     int dev = 0, n = 0;
@@ -255,6 +260,11 @@ void destroy(nglod_svo* s, cudaStream_t st) {
 using namespace nglod;
 
 extern "C" const char* nglod_last_error(void) { return g_last_error.c_str(); }
+
+extern "C" int nglod_set_wait_polls(int64_t polls) {
+    g_wait_polls.store(polls < 0 ? kDefaultWaitPolls : (long long)polls, std::memory_order_relaxed);
+    return NGLOD_OK;
+}
 
 extern "C" int svo_build(const uint64_t* const* h_keys, const int64_t* h_counts, int num_depths,
                          void* stream, nglod_svo** out) {

@@ -5,9 +5,9 @@
 // contraction: pre[q][h] = sum_k z[q][k] W1[h][k], M = 128 queries,
 // N = 128 hidden units, K = 32 feature channels.  Each CTA owns 128 query
 // slots (thread i <-> A-tile row i <-> tensor-memory lane i):
-//   1. gather: 8-lane groups interpolate each slot's z (FP32) and write it as
-//      BF16 straight into the A tile, laid out as the MMA's canonical K-major
-//      operand (8-row x 16-byte core matrices);
+//   1. gather: 4-lane groups interpolate each slot's z (FP32, 8 channels a
+//      lane) and write it as BF16 straight into the A tile, laid out as the
+//      MMA's canonical K-major operand (8-row x 16-byte core matrices);
 //   2. one thread issues two K = 16 tcgen05.mma (A, B from shared memory,
 //      FP32 accumulator in 128 TMEM columns) and commits to an mbarrier;
 //   3. epilogue: every thread loads its accumulator row with tcgen05.ld and
@@ -35,7 +35,6 @@ constexpr int kTM = 128;                 // queries per tile = threads per CTA
 constexpr int kKc = kFeatDim / 8;        // 16-byte K chunks per operand row
 constexpr uint32_t kLbo = 128;           // K-adjacent core matrices
 constexpr uint32_t kSbo = 128 * kKc;     // M/N-adjacent 8-row groups
-constexpr long kWaitPolls = 1l << 24;
 constexpr int kCtasPerSm = 4;           // 4 x 128 TMEM columns = the SM's 512
 
 struct BfSmem {
@@ -86,8 +85,9 @@ struct DecPtrsB {
     const float* W1;
     const float* b1;
     const float* W2;
-    float b2;
+    const float* b2;   // one float (device), read when the kernel starts
     float z_scale;     // FP8: z is multiplied by this before rounding to e4m3
+    long long polls;   // poll budget of each tile's MMA wait
 };
 
 template <int IN, bool FP8>
@@ -148,7 +148,7 @@ __device__ __forceinline__ void put_z(BfSmem& S, int row, int l, float4 z, float
 // Issues the tile's MMA (thread 0) and waits for it (all threads); returns
 // false if the wait expired.
 template <bool FP8>
-__device__ __forceinline__ bool mma_tile(BfSmem& S, uint32_t taddr, uint32_t& phase) {
+__device__ __forceinline__ bool mma_tile(BfSmem& S, uint32_t taddr, uint32_t& phase, long long polls) {
     tc::fence_proxy_async_smem();
     tc::fence_before_sync();
     __syncthreads();
@@ -169,7 +169,7 @@ __device__ __forceinline__ bool mma_tile(BfSmem& S, uint32_t taddr, uint32_t& ph
         }
         tc::mma_commit(&S.bar);
     }
-    const bool ok = tc::mbar_wait(&S.bar, phase, kWaitPolls);
+    const bool ok = tc::mbar_wait(&S.bar, phase, polls);
     phase ^= 1u;
     tc::fence_after_sync();
     return ok;
@@ -221,7 +221,7 @@ __device__ __forceinline__ void setup_tmem(SM& S) {
 
 template <class SM>
 __device__ __forceinline__ void teardown_tmem(SM& S, uint32_t taddr, bool drained, uint32_t phase) {
-    if (!drained) tc::mbar_wait(&S.bar, phase ^ 1u, kWaitPolls);   // let an expired MMA finish
+    if (!drained) tc::mbar_wait(&S.bar, phase ^ 1u, kDefaultWaitPolls);   // let an expired MMA finish
     tc::fence_before_sync();
     __syncthreads();
     if ((threadIdx.x >> 5) == 0) tc::tmem_dealloc(taddr, kHidden);
@@ -275,7 +275,7 @@ __device__ __forceinline__ void put_z_split(BfSmem3& S, int row, int l, float4 z
 
 // The six products A_i B_j (i + j <= 2), smallest first, into one FP32
 // accumulator; issued by thread 0, waited for by all (bounded).
-__device__ __forceinline__ bool mma_tile_split(BfSmem3& S, uint32_t taddr, uint32_t& phase) {
+__device__ __forceinline__ bool mma_tile_split(BfSmem3& S, uint32_t taddr, uint32_t& phase, long long polls) {
     tc::fence_proxy_async_smem();
     tc::fence_before_sync();
     __syncthreads();
@@ -293,7 +293,7 @@ __device__ __forceinline__ bool mma_tile_split(BfSmem3& S, uint32_t taddr, uint3
         }
         tc::mma_commit(&S.bar);
     }
-    const bool ok = tc::mbar_wait(&S.bar, phase, kWaitPolls);
+    const bool ok = tc::mbar_wait(&S.bar, phase, polls);
     phase ^= 1u;
     tc::fence_after_sync();
     return ok;
@@ -312,9 +312,10 @@ __device__ __forceinline__ void put_any(typename TcSmem<PM>::type& S, int row, i
 }
 
 template <int PM>
-__device__ __forceinline__ bool mma_any(typename TcSmem<PM>::type& S, uint32_t taddr, uint32_t& phase) {
-    if constexpr (PM == 2) return mma_tile_split(S, taddr, phase);
-    else return mma_tile<PM == 1>(S, taddr, phase);
+__device__ __forceinline__ bool mma_any(typename TcSmem<PM>::type& S, uint32_t taddr, uint32_t& phase,
+                                        long long polls) {
+    if constexpr (PM == 2) return mma_tile_split(S, taddr, phase, polls);
+    else return mma_tile<PM == 1>(S, taddr, phase, polls);
 }
 
 // ---------------------------------------------------------------------------
@@ -332,6 +333,7 @@ __global__ void __launch_bounds__(kTM, kCtasPerSm) k_trace_bf16(const DecPtrsB d
         reinterpret_cast<uint4*>(S.A)[i] = make_uint4(0u, 0u, 0u, 0u);   // rows of idle warps stay finite
     setup_tmem(S);
     const uint32_t taddr = S.taddr;
+    const float b2 = __ldg(dp.b2);
     uint32_t phase = 0;
     bool drained = true;
     RaySlot st;
@@ -366,14 +368,14 @@ __global__ void __launch_bounds__(kTM, kCtasPerSm) k_trace_bf16(const DecPtrsB d
                 put_any<PM>(S, warp * 32 + s, 2 * l4 + 1, zb, dp.z_scale);
             }
         }
-        const bool ok = mma_any<PM>(S, taddr, phase);
+        const bool ok = mma_any<PM>(S, taddr, phase, dp.polls);
         if (!__syncthreads_and(ok)) {
             if (threadIdx.x == 0) atomicExch(err, kStatusTimeout);
             drained = false;
             break;
         }
         uint4 mask = make_uint4(0u, 0u, 0u, 0u);
-        const float dhat = wact ? epilogue<IN>(S, taddr, dp.b2, x0, x1, x2, &mask) : 0.0f;
+        const float dhat = wact ? epilogue<IN>(S, taddr, b2, x0, x1, x2, &mask) : 0.0f;
         if (act) step_update(st, dhat, A, tb);
         publish_hits(st, A, lane, mask);
     }
@@ -396,6 +398,7 @@ __global__ void __launch_bounds__(kTM, kCtasPerSm) k_query_bf16(const DecPtrsB d
     stage_any<IN, PM>(S, dp);
     setup_tmem(S);
     const uint32_t taddr = S.taddr;
+    const float b2 = __ldg(dp.b2);
     uint32_t phase = 0;
     bool drained = true;
     const long long ntiles = (Q + kTM - 1) / kTM;
@@ -426,13 +429,13 @@ __global__ void __launch_bounds__(kTM, kCtasPerSm) k_query_bf16(const DecPtrsB d
             put_any<PM>(S, warp * 32 + s, 2 * l4, za, dp.z_scale);
             put_any<PM>(S, warp * 32 + s, 2 * l4 + 1, zb, dp.z_scale);
         }
-        const bool ok = mma_any<PM>(S, taddr, phase);
+        const bool ok = mma_any<PM>(S, taddr, phase, dp.polls);
         if (!__syncthreads_and(ok)) {
             if (threadIdx.x == 0) atomicExch(err, kStatusTimeout);
             drained = false;
             break;
         }
-        const float out = epilogue<IN>(S, taddr, dp.b2, x0, x1, x2);
+        const float out = epilogue<IN>(S, taddr, b2, x0, x1, x2);
         if (act) {
             sdf[qi] = out;
             if (deepest) deepest[qi] = (int8_t)(dd >= kFirstFeatureDepth ? dd - kFirstFeatureDepth + 1 : 0);
@@ -451,7 +454,7 @@ void prefer_l1(K kernel);
 template <typename T, int IN, bool FP8>
 __global__ void __launch_bounds__(kTM, kCtasPerSm) k_trace_batch(const TraceJob* __restrict__ jobs,
                                                                const JobGroup* __restrict__ groups, int ngroups,
-                                                               int* __restrict__ err) {
+                                                               int* __restrict__ err, long long polls) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     BfSmem& S = *reinterpret_cast<BfSmem*>(smem_raw);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -470,11 +473,12 @@ __global__ void __launch_bounds__(kTM, kCtasPerSm) k_trace_batch(const TraceJob*
     bool drained = true;
     for (int gi = 0; gi < ngroups && drained; ++gi) {
         const JobGroup G = groups[gi];
-        const DecPtrsB dp{G.W1, G.b1, G.W2, G.b2, G.z_scale};
+        const DecPtrsB dp{G.W1, G.b1, G.W2, G.b2, G.z_scale, polls};
         __syncthreads();                      // the previous group's epilogues are done
         stage_bf16_decoder<IN, FP8>(S, dp);
         tc::fence_proxy_async_smem();
         __syncthreads();
+        const float b2 = __ldg(dp.b2);
         RaySlot st;
         st.ray = -1;
         st.hit_ray = -1;
@@ -506,14 +510,14 @@ __global__ void __launch_bounds__(kTM, kCtasPerSm) k_trace_batch(const TraceJob*
                 put_z<FP8>(S, warp * 32 + s, 2 * l4, za, dp.z_scale);
                 put_z<FP8>(S, warp * 32 + s, 2 * l4 + 1, zb, dp.z_scale);
             }
-            const bool ok = mma_tile<FP8>(S, taddr, phase);
+            const bool ok = mma_tile<FP8>(S, taddr, phase, polls);
             if (!__syncthreads_and(ok)) {
                 if (threadIdx.x == 0) atomicExch(err, kStatusTimeout);
                 drained = false;
                 break;
             }
             uint4 mask = make_uint4(0u, 0u, 0u, 0u);
-            const float dhat = wact ? epilogue<IN>(S, taddr, dp.b2, x0, x1, x2, &mask) : 0.0f;
+            const float dhat = wact ? epilogue<IN>(S, taddr, b2, x0, x1, x2, &mask) : 0.0f;
             if (act) step_update(st, dhat, jobs[st.job].A, jobs[st.job].tb);
             publish_hits_batch(st, jobs, mask);
         }
@@ -523,13 +527,13 @@ __global__ void __launch_bounds__(kTM, kCtasPerSm) k_trace_batch(const TraceJob*
 
 template <typename T, int IN, bool FP8>
 void go_batch1(const TraceJob* jobs, const JobGroup* groups, int ngroups, int* err, int grid, cudaStream_t st) {
-    static bool once = (prefer_l1(k_trace_batch<T, IN, FP8>), true);
-    (void)once;
-    k_trace_batch<T, IN, FP8><<<grid, kTM, kDynSmem, st>>>(jobs, groups, ngroups, err);
+    static std::atomic<unsigned long long> done{0};
+    once_per_device(done, [] { prefer_l1(k_trace_batch<T, IN, FP8>); });
+    k_trace_batch<T, IN, FP8><<<grid, kTM, kDynSmem, st>>>(jobs, groups, ngroups, err, mma_wait_polls());
 }
 
 DecPtrsB bptrs(const nglod_decoder* dec, float z_scale) {
-    return DecPtrsB{dec->W1, dec->b1, dec->W2, dec->b2, z_scale};
+    return DecPtrsB{dec->W1, dec->b1, dec->W2, dec->b2, z_scale, mma_wait_polls()};
 }
 
 template <typename K>
@@ -552,8 +556,8 @@ void configure_tc(K kernel) {
 
 template <typename T, int IN, int PM>
 void go_trace1(const DecPtrsB& P, const Tables& tb, const TraceArgs& A, int* err, int grid, cudaStream_t st) {
-    static bool once = (configure_tc<PM>(k_trace_bf16<T, IN, PM>), true);
-    (void)once;
+    static std::atomic<unsigned long long> done{0};
+    once_per_device(done, [] { configure_tc<PM>(k_trace_bf16<T, IN, PM>); });
     k_trace_bf16<T, IN, PM><<<grid, kTM, PM == 2 ? kDynSmem3 : kDynSmem, st>>>(P, tb, A, err);
 }
 
@@ -567,8 +571,8 @@ void go_trace(const DecPtrsB& P, const Tables& tb, const TraceArgs& A, int* err,
 template <typename T, int IN, int PM>
 void go_query1(const DecPtrsB& P, const Tables& tb, const float* x, long long Q, int D, float* sdf, int8_t* deep,
                int* err, int grid, cudaStream_t st) {
-    static bool once = (configure_tc<PM>(k_query_bf16<T, IN, PM>), true);
-    (void)once;
+    static std::atomic<unsigned long long> done{0};
+    once_per_device(done, [] { configure_tc<PM>(k_query_bf16<T, IN, PM>); });
     k_query_bf16<T, IN, PM><<<grid, kTM, PM == 2 ? kDynSmem3 : kDynSmem, st>>>(P, tb, x, Q, D, sdf, deep, err);
 }
 
@@ -709,11 +713,11 @@ __device__ __forceinline__ void gather_pair(const Tables& tb, int dd, int dlo, i
 template <int IN>
 __device__ __forceinline__ int blend_decode(BlendSmem& S, uint32_t taddr, uint32_t& ph_lo, uint32_t& ph_hi,
                                             float b2lo, float b2hi, float alpha, float x0, float x1, float x2,
-                                            bool wact, float& dhat, uint4* mlo = nullptr,
+                                            bool wact, float& dhat, long long polls, uint4* mlo = nullptr,
                                             uint4* mhi = nullptr) {
-    if (!__syncthreads_and(mma_tile<false>(S.lo, taddr, ph_lo))) return 1;
+    if (!__syncthreads_and(mma_tile<false>(S.lo, taddr, ph_lo, polls))) return 1;
     const float dlo = wact ? epilogue<IN>(S.lo, taddr, b2lo, x0, x1, x2, mlo) : 0.0f;
-    if (!__syncthreads_and(mma_tile<false>(S.hi, taddr, ph_hi))) return 2;
+    if (!__syncthreads_and(mma_tile<false>(S.hi, taddr, ph_hi, polls))) return 2;
     const float dhi = wact ? epilogue<IN>(S.hi, taddr, b2hi, x0, x1, x2, mhi) : 0.0f;
     dhat = fmaf(alpha, dhi - dlo, dlo);
     return 0;
@@ -738,6 +742,7 @@ __global__ void __launch_bounds__(kTM, kCtasPerSm) k_trace_blend_bf16(const DecP
     stage_bf16_decoder<IN, false>(S.hi, phi);
     setup_blend(S);
     const uint32_t taddr = S.lo.taddr;
+    const float b2lo = __ldg(plo.b2), b2hi = __ldg(phi.b2);
     uint32_t ph_lo = 0, ph_hi = 0;
     int failed = 0;
     RaySlot st;
@@ -770,8 +775,8 @@ __global__ void __launch_bounds__(kTM, kCtasPerSm) k_trace_blend_bf16(const DecP
         }
         float dhat = 0.0f;
         uint4 mlo = make_uint4(0u, 0u, 0u, 0u), mhi = mlo;
-        failed = blend_decode<IN>(S, taddr, ph_lo, ph_hi, plo.b2, phi.b2, alpha, x0, x1, x2,
-                                  __any_sync(0xffffffffu, act), dhat, &mlo, &mhi);
+        failed = blend_decode<IN>(S, taddr, ph_lo, ph_hi, b2lo, b2hi, alpha, x0, x1, x2,
+                                  __any_sync(0xffffffffu, act), dhat, plo.polls, &mlo, &mhi);
         if (failed) {
             if (threadIdx.x == 0) atomicExch(err, kStatusTimeout);
             break;
@@ -796,6 +801,7 @@ __global__ void __launch_bounds__(kTM, kCtasPerSm) k_query_blend_bf16(const DecP
     stage_bf16_decoder<IN, false>(S.hi, phi);
     setup_blend(S);
     const uint32_t taddr = S.lo.taddr;
+    const float b2lo = __ldg(plo.b2), b2hi = __ldg(phi.b2);
     uint32_t ph_lo = 0, ph_hi = 0;
     int failed = 0;
     const long long ntiles = (Q + kTM - 1) / kTM;
@@ -831,8 +837,8 @@ __global__ void __launch_bounds__(kTM, kCtasPerSm) k_query_blend_bf16(const DecP
             }
         }
         float out = 0.0f;
-        failed = blend_decode<IN>(S, taddr, ph_lo, ph_hi, plo.b2, phi.b2, alpha, x0, x1, x2,
-                                  __any_sync(0xffffffffu, act), out);
+        failed = blend_decode<IN>(S, taddr, ph_lo, ph_hi, b2lo, b2hi, alpha, x0, x1, x2,
+                                  __any_sync(0xffffffffu, act), out, plo.polls);
         if (failed) {
             if (threadIdx.x == 0) atomicExch(err, kStatusTimeout);
             break;
@@ -847,12 +853,12 @@ void go_blend(bool trace, const DecPtrsB& lo, const DecPtrsB& hi, float alpha, c
               const float* x, long long Q, int D, float* sdf, int* err, int grid, cudaStream_t st) {
     static_assert(sizeof(BlendSmem) <= kBlendSmem && kBlendSmem <= 48 * 1024, "shared layout");
     if (trace) {
-        static bool once = (prefer_l1(k_trace_blend_bf16<T, IN>), true);
-        (void)once;
+        static std::atomic<unsigned long long> done{0};
+        once_per_device(done, [] { prefer_l1(k_trace_blend_bf16<T, IN>); });
         k_trace_blend_bf16<T, IN><<<grid, kTM, kBlendSmem, st>>>(lo, hi, alpha, tb, *A, err);
     } else {
-        static bool once = (prefer_l1(k_query_blend_bf16<T, IN>), true);
-        (void)once;
+        static std::atomic<unsigned long long> done{0};
+        once_per_device(done, [] { prefer_l1(k_query_blend_bf16<T, IN>); });
         k_query_blend_bf16<T, IN><<<grid, kTM, kBlendSmem, st>>>(lo, hi, alpha, tb, x, Q, D, sdf, err);
     }
 }

@@ -284,7 +284,7 @@ struct JobGroup {
     const float* W1;
     const float* b1;
     const float* W2;
-    float b2;
+    const float* b2;         // one float (device)
     float z_scale;           // FP8 decode
     int* queue;
     const int32_t* order;    // handout order of the group's 32-ray chunks (longest list first)

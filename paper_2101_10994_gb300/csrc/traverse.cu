@@ -307,6 +307,9 @@ __global__ void __launch_bounds__(kThreads, 4) k_traverse(const TileParams p) {
                 ++nsub;
                 tile_total += tot2;
                 r += l;
+                // grow back after a success, so only the dense part of the
+                // tile runs at the small size
+                len = min(nr / 2, 2 * len);
             }
         }
         if (threadIdx.x == 0) {
@@ -452,15 +455,20 @@ size_t align_up(size_t v, size_t a = 256) { return (v + a - 1) / a * a; }
 
 long long num_tiles(long long R) { return (R + kTR - 1) / kTR; }
 
+// Resident traversal CTAs per SM, found (and the shared-memory opt-in set)
+// once per device.
 int traverse_ctas_per_sm() {
-    static int cached = 0;
-    if (!cached) {
+    static std::atomic<int> cached[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::atomic<int>& c = cached[dev & 63];
+    if (!c.load(std::memory_order_acquire)) {
         cudaFuncSetAttribute(k_traverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TileSmem));
         int n = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_traverse, kThreads, sizeof(TileSmem));
-        cached = n > 0 ? n : 1;
+        c.store(n > 0 ? n : 1, std::memory_order_release);
     }
-    return cached;
+    return c.load(std::memory_order_acquire);
 }
 
 }  // namespace
@@ -612,9 +620,11 @@ extern "C" int svo_trace_rays_sizes(const void* work, int64_t* h_sizes, int n, v
 // The array below, kNoAllocScratchBytes (32 MiB) long, is created on every
 // GPU that loads this library and stays there until the process exits.  Its
 // host-side name is only a stand-in; the device address is looked up with
-// cudaGetSymbolAddress once per device, the first time this entry point runs
-// with that device current (make that first call before any stream
-// capture).  All calls share the array and it keeps the previous call's
+// cudaGetSymbolAddress with the device current -- on the first call on each
+// device and on every call made outside a stream capture (make the first
+// call on a device before any stream capture; a capture reuses the address
+// of the last lookup, so a device reset followed directly by a capture is
+// not supported).  All calls share the array and it keeps the previous call's
 // contents: the traversal clears its own counters and scan state at the
 // start of every call, but two calls that overlap on the GPU (different
 // streams, or different host threads on one device) race on it.
@@ -652,10 +662,16 @@ extern "C" int svo_trace_rays_noalloc(const nglod_svo* svo, const float* o, cons
     NGLOD_CUDA(cudaGetDevice(&dev));
     if (dev < 0 || dev >= kNoAllocMaxDevices)
         return fail(NGLOD_ERR_NOT_SUPPORTED, "svo_trace_rays_noalloc: device index out of range");
+    // outside a stream capture the address is looked up on every call (cheap),
+    // so a device reset, after which the runtime loads the module again,
+    // cannot leave a stale address behind; inside a capture the address of
+    // the last lookup on this device is used
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    NGLOD_CUDA(cudaStreamIsCapturing((cudaStream_t)stream, &cap));
     void* scratch = nullptr;
     {
         std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-        if (!g_noalloc_ptr[dev]) {
+        if (!g_noalloc_ptr[dev] || cap == cudaStreamCaptureStatusNone) {
             void* p = nullptr;
             const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
             if (e != cudaSuccess || !p) {

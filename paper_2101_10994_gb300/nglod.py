@@ -32,7 +32,9 @@ EXPORTS = ["nglod_last_error", "svo_build", "svo_info", "svo_device_arrays", "sv
            "sphere_trace_batch_create", "sphere_trace_batch_run", "sphere_trace_batch_status",
            "sphere_trace_batch_free", "sdf_query_blend", "sphere_trace_blend", "nglod_lod_select",
            "trace_normals_fd", "sdf_backward_bf16", "sdf_l2_backward_bf16", "nglod_sort_points_workspace",
-           "nglod_sort_points", "nglod_sum_features"]
+           "nglod_sort_points", "nglod_sum_features", "nglod_set_wait_polls",
+           # measurement probes (include/nglod_probe.h)
+           "nglod_probe_l2_read", "nglod_probe_l1_read", "nglod_probe_ffma", "nglod_device_sms"]
 
 
 class NglodError(RuntimeError):
@@ -47,7 +49,7 @@ class _Features(C.Structure):
 
 
 class _Decoder(C.Structure):
-    _fields_ = [("W1", C.c_void_p), ("b1", C.c_void_p), ("W2", C.c_void_p), ("b2", C.c_float),
+    _fields_ = [("W1", C.c_void_p), ("b1", C.c_void_p), ("W2", C.c_void_p), ("b2", C.c_void_p),
                 ("in_dim", C.c_int), ("hidden", C.c_int)]
 
 
@@ -118,8 +120,55 @@ def lib():
         L.nglod_lod_select.restype = C.c_float
         L.nglod_adam_step.argtypes = [P, P, P, P, i64, C.c_float, C.c_float, C.c_float, C.c_float, i32, P]
         L.svo_trace_rays_noalloc.argtypes = [P, P, P, i64, i32, P, P, P, i64, P, P]
+        L.nglod_set_wait_polls.argtypes = [i64]
+        L.nglod_probe_l2_read.argtypes = [P, i64, i32, P, P, P]
+        L.nglod_probe_l1_read.argtypes = [P, i64, i64, i32, P, P, P]
+        L.nglod_probe_ffma.argtypes = [i64, P, P, P]
+        L.nglod_device_sms.argtypes = [P]
         _lib = L
     return _lib
+
+
+_probe_sink = None
+
+
+def device_sms() -> int:
+    """SMs of the current device (what the persistent launches are sized by)."""
+    n = C.c_int(0)
+    _check(lib().nglod_device_sms(C.byref(n)))
+    return int(n.value)
+
+
+def probe(kind: str, buf=None, passes: int = 20, window_bytes: int = 96 << 10, iters: int = 1 << 14,
+          stream=None) -> int:
+    """Enqueues one measurement-probe kernel (include/nglod_probe.h) and
+    returns the bytes it reads ("l2", "l1") or the flops it executes
+    ("ffma"); the caller times it with CUDA events."""
+    import torch
+    global _probe_sink
+    if _probe_sink is None:
+        _probe_sink = torch.zeros(4, dtype=torch.int32, device="cuda")
+    sink = _probe_sink
+    out = C.c_int64(0)
+    s = C.c_void_p(_stream(stream))
+    if kind == "l2":
+        _check(lib().nglod_probe_l2_read(buf.data_ptr(), buf.numel() * buf.element_size(), passes, sink.data_ptr(),
+                                         C.byref(out), s))
+    elif kind == "l1":
+        _check(lib().nglod_probe_l1_read(buf.data_ptr(), buf.numel() * buf.element_size(), window_bytes, passes,
+                                         sink.data_ptr(), C.byref(out), s))
+    elif kind == "ffma":
+        _check(lib().nglod_probe_ffma(iters, sink.data_ptr(), C.byref(out), s))
+    else:
+        raise ValueError(kind)
+    return int(out.value)
+
+
+def set_wait_polls(polls: int):
+    """Poll budget of every tensor-core kernel's per-tile MMA wait from now on
+    (0: each such wait expires at once and the call reports ERR_TIMEOUT;
+    negative: the default).  A testing hook for the expiry path."""
+    _check(lib().nglod_set_wait_polls(int(polls)))
 
 
 def _check(rc: int):
@@ -265,37 +314,51 @@ class Features:
 
 
 class DecoderDev:
-    """One LOD's decoder on the device (FP32 weights)."""
+    """One LOD's decoder on the device (FP32 weights; b2 is a one-element
+    device tensor, ``b2_t``, that the kernels read when they run)."""
 
     def __init__(self, W1, b1, W2, b2, device="cuda"):
         import torch
         self.h_W1 = np.ascontiguousarray(W1, np.float32)
         self.h_b1 = np.ascontiguousarray(b1, np.float32)
         self.h_W2 = np.ascontiguousarray(W2, np.float32)
-        self.b2 = float(b2)
         self.W1 = torch.from_numpy(self.h_W1).to(device)
         self.b1 = torch.from_numpy(self.h_b1).to(device)
         self.W2 = torch.from_numpy(self.h_W2).to(device)
+        self.b2_t = torch.tensor([float(b2)], dtype=torch.float32, device=device)
         self.in_dim = int(self.h_W1.shape[1])
         self.hidden = int(self.h_W1.shape[0])
+
+    @property
+    def b2(self) -> float:
+        """The current b2 (reads the device value: synchronises)."""
+        return float(self.b2_t.item())
 
     @classmethod
     def from_decoder(cls, dec, device="cuda"):
         return cls(dec.W1, dec.b1, dec.W2, dec.b2, device)
 
     @classmethod
-    def from_tensors(cls, W1, b1, W2, b2: float):
-        """A view on existing FP32 device tensors (no copy)."""
+    def from_tensors(cls, W1, b1, W2, b2):
+        """A view on existing FP32 device tensors (no copy).  ``b2``: a
+        one-element FP32 device tensor (viewed, e.g. one entry of a
+        per-LOD vector) or a float (uploaded)."""
+        import torch
         d = cls.__new__(cls)
         d.W1, d.b1, d.W2 = W1.contiguous(), b1.contiguous(), W2.contiguous()
-        d.b2 = float(b2)
+        if isinstance(b2, torch.Tensor):
+            if b2.numel() != 1 or b2.dtype != torch.float32 or not b2.is_cuda:
+                raise ValueError("b2 must be a one-element float32 CUDA tensor")
+            d.b2_t = b2.reshape(1)
+        else:
+            d.b2_t = torch.tensor([float(b2)], dtype=torch.float32, device=W1.device)
         d.in_dim, d.hidden = int(W1.shape[1]), int(W1.shape[0])
         return d
 
     def c(self) -> _Decoder:
         d = _Decoder()
         d.W1, d.b1, d.W2 = self.W1.data_ptr(), self.b1.data_ptr(), self.W2.data_ptr()
-        d.b2 = self.b2
+        d.b2 = self.b2_t.data_ptr()
         d.in_dim, d.hidden = self.in_dim, self.hidden
         return d
 

@@ -22,8 +22,11 @@ class Trainer:
         self.torch = torch
         self.svo = svo
         self.F = ng.Features(feats, "f32", device)
-        self.D = [ng.DecoderDev.from_decoder(d, device) for d in decoders]
-        self.b2 = torch.tensor([d.b2 for d in self.D], dtype=torch.float32, device=device)
+        D0 = [ng.DecoderDev.from_decoder(d, device) for d in decoders]
+        # one device vector of the LODs' b2; each decoder points at its entry,
+        # so Adam updates it in place and the kernels read it from there
+        self.b2 = torch.tensor([float(d.b2) for d in decoders], dtype=torch.float32, device=device)
+        self.D = [ng.DecoderDev.from_tensors(d.W1, d.b1, d.W2, self.b2[i:i + 1]) for i, d in enumerate(D0)]
         self.grads = ng.new_grads(svo, self.D, device)
         self.params = (list(self.F.tables) + [d.W1 for d in self.D] + [d.b1 for d in self.D] +
                        [d.W2 for d in self.D] + [self.b2])
@@ -50,14 +53,13 @@ class Trainer:
         self.t += 1
         for p, g, m, v in zip(self.params, self.gparams, self.m, self.v):
             ng.adam_step(p, g, m, v, self.lr, self.t)
-        b2 = self.b2.cpu().numpy()
-        for d, b in zip(self.D, b2):
-            d.b2 = float(b)
         return loss / Q
 
     def export(self):
         """Current parameters as numpy (features per LOD, scenes.Decoder list)."""
         from .scenes import Decoder
         feats = [t.cpu().numpy() for t in self.F.tables]
-        decs = [Decoder(d.W1.cpu().numpy(), d.b1.cpu().numpy(), d.W2.cpu().numpy(), d.b2, d.in_dim) for d in self.D]
+        b2 = self.b2.cpu().numpy()
+        decs = [Decoder(d.W1.cpu().numpy(), d.b1.cpu().numpy(), d.W2.cpu().numpy(), float(b2[i]), d.in_dim)
+                for i, d in enumerate(self.D)]
         return feats, decs

@@ -1,6 +1,8 @@
 """The C-ABI library builds for sm_103a, loads without a GPU, and exports
-every entry point include/nglod.h declares (no compute call is made here)."""
+every entry point the headers under include/ declare (no compute call is
+made here)."""
 import ctypes
+import glob
 import os
 import re
 
@@ -9,13 +11,14 @@ import pytest
 from paper_2101_10994_gb300 import build as B
 from paper_2101_10994_gb300 import nglod
 
-HEADER = os.path.join(B.INCLUDE, "nglod.h")
+HEADERS = sorted(glob.glob(os.path.join(B.INCLUDE, "*.h")))
 
 
 def declared_functions():
-    text = open(HEADER).read()
-    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    names = re.findall(r"^[A-Za-z_][\w\s\*]*?\b([a-z_][a-z0-9_]*)\s*\(", text, flags=re.M)
+    names = []
+    for h in HEADERS:
+        text = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        names += re.findall(r"^[A-Za-z_][\w\s\*]*?\b([a-z_][a-z0-9_]*)\s*\(", text, flags=re.M)
     return sorted(set(n for n in names if n not in ("if", "while")))
 
 
@@ -25,6 +28,7 @@ def libpath():
 
 
 def test_header_declares_the_five_calls():
+    assert any(h.endswith("nglod.h") for h in HEADERS) and any(h.endswith("nglod_probe.h") for h in HEADERS)
     names = declared_functions()
     for n in ("svo_build", "svo_trace_rays", "sdf_query", "sphere_trace"):
         assert n in names

@@ -69,3 +69,22 @@ def test_stale_traffic_is_dropped(bench, tmp_path, monkeypatch):
     assert bench.profiled_traffic("k_trace_bf16", "@summed") == 45
     assert bench.profiled_traffic("k_traverse") is None          # sources changed since the capture
     assert bench.profiled_traffic("k_trace_f32") is None          # never captured
+
+
+def test_rooflines_use_measured_ceilings(bench):
+    # with probe-measured ceilings the FP32 tracer divides by the measured FFMA
+    # rate and the gathers are reported against the measured L1 / L2 reads
+    W = {"dec": _Dec(), "lod": 5}
+    res = {"queries_per_frame": 1_000_000, "ms_trace": 1.0}
+    ceil = {"sms": 148, "ffma_tflops": 70.0, "l1_read_GBps": 40000.0, "l2_read_GBps": 20000.0}
+    f = bench.trace_roofline(W, res, "f32", {"sm_max_mhz": 2000.0}, ceilings=ceil)
+    assert f["peak"] == 70.0 and "measured" in f["peak_source"]
+    gbps = 1e6 * 8 * 32 * 4 * 5 / 1e-3 / 1e9
+    assert f["gather_GBps"] == pytest.approx(gbps)
+    assert f["gather_frac_of_l1"] == pytest.approx(gbps / 40000.0)
+    assert f["gather_frac_of_l2"] == pytest.approx(gbps / 20000.0)
+    # without a measured FFMA rate: the nominal count from the device's SMs
+    g = bench.trace_roofline(W, res, "f32", {"sm_max_mhz": 2000.0}, ceilings={"sms": 148})
+    assert g["peak"] == pytest.approx(148 * 128 * 2 * 2000e6 / 1e12)
+    b = bench.trace_roofline(W, res, "bf16", {"bf16_tflops": 2000.0}, ceilings=ceil)
+    assert b["gather_frac_of_l2"] == pytest.approx(gbps / 20000.0)

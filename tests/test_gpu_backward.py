@@ -11,10 +11,43 @@ from paper_2101_10994_gb300 import scenes as S
 pytestmark = pytest.mark.gpu
 
 
-def rel_err(a, b):
+# FP32 gradients summed by atomics: an element's error is a few FP32
+# roundings of its own terms.  Each element is held to 2e-5 of its own value
+# plus 2e-6 of the tensor's largest element (a single max-error / max-value
+# ratio would let the small gradients of corners touched by few points go
+# unchecked).
+RTOL, ATOL_FRAC = 2e-5, 2e-6
+
+
+def elem_err(a, b):
+    """max_i |a_i - b_i| / (RTOL |b_i| + ATOL_FRAC max|b|): <= 1 iff every
+    element is within its tolerance."""
     a = np.asarray(a, np.float64)
     b = np.asarray(b, np.float64)
-    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-30)
+    scale = max(np.abs(b).max(), 1e-30)
+    return float((np.abs(a - b) / (RTOL * np.abs(b) + ATOL_FRAC * scale)).max())
+
+
+def kink_x_check(ora, feats, decs, x, lods, g, gx, ref_x, step=5e-5):
+    """x gradients: every point within 1e-4 (relative to its largest
+    component) of the oracle's, except points at a ReLU kink of one of the
+    decoders, where the FP32 mask may take the other side: those must match
+    the oracle's gradient a step away on one side (x +- step e_a) within the
+    drift of the trilinear gradient over that step (5e-3).  Returns the
+    number of kink points."""
+    e = np.abs(gx - ref_x).max(axis=1) / np.maximum(np.abs(ref_x).max(axis=1), 1e-6)
+    bad = np.flatnonzero(e >= 1e-4)
+    if bad.size == 0:
+        return 0
+    best = np.full(bad.size, np.inf)
+    for a in range(3):
+        for sgn in (-1.0, 1.0):
+            xs = x[bad].copy()
+            xs[:, a] = (xs[:, a] + np.float32(sgn * step)).astype(np.float32)
+            rx = ora.sdf_backward(feats, decs, xs, lods, g[:, bad])["x"]
+            best = np.minimum(best, np.abs(gx[bad] - rx).max(axis=1) / np.maximum(np.abs(rx).max(axis=1), 1e-6))
+    assert np.all(best < 5e-3), (bad[best >= 5e-3], best.max())
+    return int(bad.size)
 
 
 @pytest.mark.parametrize("scene,in_dim", [("sphere", 32), ("sphere", 35), ("csg", 32)])
@@ -42,19 +75,20 @@ def test_backward_vs_oracle(ng, oracle_mod, scene, in_dim):
     gr = ng.sdf_backward(svo, F, D, torch.from_numpy(x).cuda(), lods, torch.from_numpy(g).cuda(), grad_x=gx)
     ref = ora = oracle_mod.OracleSVO(oc.keys).sdf_backward(feats, decs, x, lods, g)
     for li in range(L):
-        assert rel_err(gr["feats"][li].cpu().numpy(), ref["feats"][li]) < 2e-5, li
+        assert elem_err(gr["feats"][li].cpu().numpy(), ref["feats"][li]) <= 1, li
     for lod in lods:
         i = lod - 1
-        assert rel_err(gr["W1"][i].cpu().numpy(), ref["W1"][i]) < 2e-5, lod
-        assert rel_err(gr["b1"][i].cpu().numpy(), ref["b1"][i]) < 2e-5, lod
-        assert rel_err(gr["W2"][i].cpu().numpy(), ref["W2"][i]) < 2e-5, lod
+        assert elem_err(gr["W1"][i].cpu().numpy(), ref["W1"][i]) <= 1, lod
+        assert elem_err(gr["b1"][i].cpu().numpy(), ref["b1"][i]) <= 1, lod
+        assert elem_err(gr["W2"][i].cpu().numpy(), ref["W2"][i]) <= 1, lod
         assert abs(gr["b2"][i].item() - ref["b2"][i]) < 1e-3 * max(1.0, abs(ref["b2"][i]))
     for lod in range(1, L + 1):
         if lod not in lods:
             assert gr["W1"][lod - 1].abs().max().item() == 0.0
-    # x gradient: ReLU kinks can sit within rounding of a point; compare the bulk
-    e = np.abs(gx.cpu().numpy() - ref["x"]).max(axis=1) / np.maximum(np.abs(ref["x"]).max(axis=1), 1e-6)
-    assert np.mean(e < 1e-4) > 0.99, np.sort(e)[-5:]
+    # x gradient: every point, one-sided at ReLU kinks
+    nk = kink_x_check(oracle_mod.OracleSVO(oc.keys), feats, decs, x, lods, g, gx.cpu().numpy().astype(np.float64),
+                      ref["x"])
+    assert nk <= 0.01 * len(x), nk
     svo.free()
 
 
@@ -127,10 +161,10 @@ def test_l2_backward_vs_oracle(ng, oracle_mod):
         assert abs(loss[lod - 1].item() - ((pred - tgt) ** 2).sum()) < 1e-4 * ((pred - tgt) ** 2).sum()
     ref = ora.sdf_backward(feats, decs, x, lods, np.array(g))
     for li in range(4):
-        assert rel_err(grads["feats"][li].cpu().numpy(), ref["feats"][li]) < 2e-5, li
+        assert elem_err(grads["feats"][li].cpu().numpy(), ref["feats"][li]) <= 1, li
     for lod in lods:
-        assert rel_err(grads["W1"][lod - 1].cpu().numpy(), ref["W1"][lod - 1]) < 2e-5
-        assert rel_err(grads["W2"][lod - 1].cpu().numpy(), ref["W2"][lod - 1]) < 2e-5
+        assert elem_err(grads["W1"][lod - 1].cpu().numpy(), ref["W1"][lod - 1]) <= 1
+        assert elem_err(grads["W2"][lod - 1].cpu().numpy(), ref["W2"][lod - 1]) <= 1
     assert loss[1].item() == 0.0
     svo.free()
 
@@ -201,12 +235,12 @@ def test_deterministic_backward(ng, oracle_mod, fdtype, in_dim):
     ffeats = [t.astype(np.float16).astype(np.float32) for t in feats] if fdtype == "f16" else feats
     ref = oracle_mod.OracleSVO(oc.keys).sdf_backward(ffeats, decs, x, lods, g)
     for li in range(5):
-        assert rel_err(a["feats"][li].cpu().numpy(), ref["feats"][li]) < 2e-5, li
-        assert rel_err(a["feats"][li].cpu().numpy(), f["feats"][li].cpu().numpy()) < 2e-5, li
+        assert elem_err(a["feats"][li].cpu().numpy(), ref["feats"][li]) <= 1, li
+        assert elem_err(a["feats"][li].cpu().numpy(), f["feats"][li].cpu().numpy()) <= 1, li
     for lod in lods:
         i = lod - 1
         for k in ("W1", "b1", "W2"):
-            assert rel_err(a[k][i].cpu().numpy(), ref[k][i]) < 2e-5, (k, lod)
+            assert elem_err(a[k][i].cpu().numpy(), ref[k][i]) <= 1, (k, lod)
         assert abs(a["b2"][i].item() - ref["b2"][i]) < 1e-3 * max(1.0, abs(ref["b2"][i]))
     svo.free()
 

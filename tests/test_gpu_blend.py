@@ -13,8 +13,9 @@ import numpy as np
 import pytest
 import torch
 
+import parity_util as P
 from paper_2101_10994_gb300 import scenes as S
-from test_gpu_trace import oracle_decoder_for
+from test_gpu_trace import decode_bound, oracle_decoder_for
 
 pytestmark = pytest.mark.gpu
 
@@ -88,15 +89,12 @@ def test_query_blend_bf16_within_rounding_bound(ng, oracle_mod, scene):
     svo.free()
 
 
-def blended_normal_in_voxel(ora, oc, feats, dlo, dhi, lt, x, vox):
-    """Oracle gradient of the blend at x, clamped into the GPU's hit voxel
-    (depth of LOD ceil(L~)), with the kink-stability flag of test_gpu_trace."""
+def blended_unit_normal(ora, oc, feats, dlo, dhi, lt, vox):
+    """x -> the oracle's unit gradient of the blend, evaluated with x clamped
+    into the GPU's hit voxels (depth of LOD ceil(L~))."""
     ls = int(np.floor(lt))
     a = lt - ls
-    D = ls + S.FIRST_FEATURE_DEPTH
-    i, j, k = S.morton_decode(oc.keys[D][vox])
-    s = 2.0 / (1 << D)
-    lo = np.stack([-1 + i * s, -1 + j * s, -1 + k * s], axis=1)
+    lo, s = P.voxel_lo(oc, ls + S.FIRST_FEATURE_DEPTH, vox)
 
     def unit(xx):
         xc = np.clip(xx, lo + 1e-4 * s, lo + s - 1e-4 * s).astype(np.float32)
@@ -104,18 +102,13 @@ def blended_normal_in_voxel(ora, oc, feats, dlo, dhi, lt, x, vox):
         _, _, g1 = ora.sdf_query(feats, dhi, xc, ls + 1, grad=True)
         g = (1 - a) * g0 + a * g1
         return g / np.maximum(np.linalg.norm(g, axis=1, keepdims=True), 1e-300)
-    n0 = unit(x)
-    stable = np.ones(len(x), bool)
-    for ax in range(3):
-        for sgn in (-1.0, 1.0):
-            xs = x.copy()
-            xs[:, ax] += sgn * 5e-5
-            stable &= np.degrees(np.arccos(np.clip((unit(xs) * n0).sum(1), -1, 1))) <= 0.2
-    return n0, stable
+    return unit
 
 
 @pytest.mark.parametrize("decode", ["f32", "bf16"])
 def test_trace_blend_vs_oracle(ng, oracle_mod, scene, decode):
+    # hit masks, hit depth (eps straddles counted, parity_util) and every hit
+    # normal (one-sided at ReLU kinks) against the oracle's blended trace
     sc, oc = scene
     ora = oracle_mod.OracleSVO(oc.keys)
     feats = S.readout_features(oc, sc)
@@ -135,19 +128,26 @@ def test_trace_blend_vs_oracle(ng, oracle_mod, scene, decode):
     olo, ohi = oracle_decoder_for(decs[ls], decode), oracle_decoder_for(decs[ls + 1], decode)
     ref = ora.sphere_trace_blend(feats, olo, ohi, o[sel], d[sel], lt, eps=1e-3, max_steps=128)
     gh, rh = g["hit"][sel].astype(bool), ref["hit"].astype(bool)
-    assert int((gh != rh).sum()) <= 2
     both = gh & rh
     assert both.sum() > 500
-    dt = np.abs(g["t"][sel][both].astype(np.float64) - ref["t"][both])
+    xg = P.hit_points(o[sel], d[sel], g["t"][sel], gh)
+    xo = P.hit_points(o[sel], d[sel], ref["t"], rh)
+    # the blend of the two decoders' bounds on |GPU decode - oracle decode|
+    a = lt - ls
+    bound = np.maximum(*[(1 - a) * decode_bound(ora, feats, olo, ls, x, decode) +
+                         a * decode_bound(ora, feats, ohi, ls + 1, x, decode) for x in (xg, xo)])
+    strad = P.straddles(lambda x: ora.sdf_query_blend(feats, olo, ohi, x, lt), 1e-3, bound, xo, xg)
+    assert int((gh != rh).sum()) <= 2 and np.all(strad[gh != rh])
+    dt = np.abs(g["t"][sel].astype(np.float64) - ref["t"])
+    far = both & (dt > 1e-3)
+    assert np.all(strad[far]) and far.sum() <= max(2, int(0.005 * both.sum())), far.sum()
     if decode == "f32":
-        assert dt.max() <= 1e-3, dt.max()
         assert (g["steps"][sel] == ref["steps"]).mean() >= 0.999
-    else:
-        assert np.mean(dt <= 1e-3) >= 0.995 and dt.max() <= 1.2e-3, dt.max()
-    x = o[sel][gh].astype(np.float64) + g["t"][sel][gh].astype(np.float64)[:, None] * d[sel][gh].astype(np.float64)
-    nref, stable = blended_normal_in_voxel(ora, oc, feats, olo, ohi, lt, x, g["hit_voxel"][sel][gh])
-    ang = np.degrees(np.arccos(np.clip((g["normal"][sel][gh][stable] * nref[stable]).sum(1), -1, 1)))
-    assert stable.mean() >= 0.95 and ang.max() <= 0.5, (stable.mean(), ang.max())
+    unit = blended_unit_normal(ora, oc, feats, olo, ohi, lt, g["hit_voxel"][sel][gh])
+    a0, amin = P.min_normal_angle(unit, xg[gh], g["normal"][sel][gh].astype(np.float64))
+    print(f"\nBLEND PARITY {decode}: {int(both.sum())} hits, {int((gh != rh).sum())} mismatches, {int(far.sum())} "
+          f"straddles beyond 1e-3, normals max {amin.max():.3f} deg ({int((a0 > 0.5).sum())} at a kink)")
+    assert amin.max() <= 0.5, amin.max()
     svo.free()
 
 

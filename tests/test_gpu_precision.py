@@ -15,12 +15,16 @@ are reported per configuration (run with -s to see the table) and bounded:
   * frame: a decode error e moves the stop test d < eps to a neighbouring
     step, so hit masks differ only on rays whose closest approach lies
     within e of eps (a small fraction), and the hit depth moves by about
-    one step (< 2 eps) on all but grazing rays.
+    one step (< 2 eps) on all but grazing rays;
+  * normals: at the two sides' own hit points, median and 99th percentile
+    (bounds below); at the GPU's own hit point, every hit within 0.5
+    degrees of the full-precision oracle gradient there.
 """
 import numpy as np
 import pytest
 import torch
 
+import parity_util as P
 from paper_2101_10994_gb300 import scenes as S
 
 pytestmark = pytest.mark.gpu
@@ -72,16 +76,38 @@ def test_precision_vs_fp64(ng, oracle_mod, csg256, lod):
         cosang = (nn * ref["normal"][both]).sum(1) / np.maximum(np.linalg.norm(ref["normal"][both], axis=1), 1e-300)
         ang = np.degrees(np.arccos(np.clip(cosang, -1.0, 1.0)))
         mism = float((gh != rh).mean())
-        rows.append((fdt, decode, eq, mism, int(both.sum()), dt, ang))
+        # the same normals at the GPU's own hit points, in the GPU's voxels,
+        # against the oracle gradient of the full-precision model there
+        # (one-sided at ReLU kinks, parity_util): every hit within 0.5 degrees
+        ghit = out["hit"].cpu().numpy()[sel].astype(bool)
+        xg = P.hit_points(o[sel], d[sel], out["t"].cpu().numpy()[sel], ghit)[ghit]
+        lo, s = P.voxel_lo(oc, lod + S.FIRST_FEATURE_DEPTH - 1, out["work"][256:256 + 4 * len(o)].view(
+            torch.int32).cpu().numpy()[sel][ghit])
+
+        def unit(xx):
+            _, _, g = ora.sdf_query(feats, dec, np.clip(xx, lo + 1e-4 * s, lo + s - 1e-4 * s).astype(np.float32),
+                                    lod, grad=True)
+            return g / np.maximum(np.linalg.norm(g, axis=1, keepdims=True), 1e-300)
+        _, same_x = P.min_normal_angle(unit, xg, out["normal"].cpu().numpy()[sel][ghit].astype(np.float64))
+        rows.append((fdt, decode, eq, mism, int(both.sum()), dt, ang, same_x))
         assert mism <= (0.01 if decode == "fp8" else 0.003), (fdt, decode, mism)
         assert np.median(dt) <= EPS and np.percentile(dt, 99) <= 2 * EPS, (fdt, decode, np.percentile(dt, 99))
+        # normals at the two sides' own hit points: a decode error moves the
+        # stop by about one step (< 2 eps), so the points differ by up to
+        # ~2e-3 along the ray; on surfaces of curvature up to 1/0.025 (the
+        # smallest capsule radius) that turns the normal by up to ~4.6
+        # degrees, and the trilinear gradient also jumps across voxel faces.
+        # FP32 and BF16 (hit points within 1e-5 on all but straddles): median
+        # and p99 within 0.5 degrees; FP8: median 0.5, p99 3 degrees
         assert np.median(ang) <= 0.5, (fdt, decode, np.median(ang))
+        assert np.percentile(ang, 99) <= (3.0 if decode == "fp8" else 0.5), (fdt, decode, np.percentile(ang, 99))
+        assert same_x.max() <= 0.5, (fdt, decode, same_x.max())
     print(f"\nCSG-256 seed 0, LOD {lod}, 1920x1080 ({len(sel)} sampled pixels, {int(rh.sum())} oracle hits; "
           f"{len(xq)} queries), errors vs the FP64 oracle:")
     print("features decode | query |dd| median p99 max | hit-mask mismatch | hit |dt| median p99 max | "
-          "normal deg median p99")
-    for fdt, decode, eq, mism, nb, dt, ang in rows:
+          "normal deg median p99 | same-point normal deg max")
+    for fdt, decode, eq, mism, nb, dt, ang, same_x in rows:
         print(f"PRECISION lod={lod} {fdt:>4} {decode:>5} | {np.median(eq):.2e} {np.percentile(eq, 99):.2e} "
               f"{eq.max():.2e} | {mism * 100:.2f}% | {np.median(dt):.2e} {np.percentile(dt, 99):.2e} "
-              f"{dt.max():.2e} | {np.median(ang):.3f} {np.percentile(ang, 99):.3f}")
+              f"{dt.max():.2e} | {np.median(ang):.3f} {np.percentile(ang, 99):.3f} | {same_x.max():.3f}")
     svo.free()

@@ -56,3 +56,27 @@ def test_training_beats_corner_sampled_interpolant(ng):
         assert trained[l] < 0.8 * adf[l], (l + 1, trained, adf)
     assert trained[0] < 0.25 * adf[0]
     svo.free()
+
+
+def test_adam_updates_reach_the_kernels_without_host_copies(ng):
+    # every decoder parameter, b2 included, is read by the kernels from device
+    # memory: the trainer's decoders point into its parameter tensors, so an
+    # Adam step reaches the next call with no host round trip
+    sc, oc = S.csg_workload(16, seed=1, max_lod=3)
+    svo = ng.svo_build(oc.keys)
+    x, d = S.training_batch(sc, 1 << 14, 3)
+    tx, td = torch.from_numpy(x).cuda(), torch.from_numpy(d).cuda()
+    decs0 = [S.init_decoder(l) for l in (1, 2, 3)]
+    tr = Trainer(svo, S.init_features(oc, seed=0), decs0, lr=1e-2)
+    for i, dd in enumerate(tr.D):
+        assert dd.b2_t.data_ptr() == tr.b2[i:i + 1].data_ptr()
+    for _ in range(5):
+        tr.step(tx, td)
+    torch.cuda.synchronize()
+    f, decs = tr.export()
+    assert all(abs(decs[i].b2 - decs0[i].b2) > 1e-4 for i in range(3))     # Adam moved every b2
+    for lod in (1, 2, 3):
+        live = ng.sdf_query(svo, tr.F, tr.D[lod - 1], tx, lod)
+        fresh = ng.sdf_query(svo, ng.Features(f), ng.DecoderDev.from_decoder(decs[lod - 1]), tx, lod)
+        assert torch.equal(live, fresh), lod
+    svo.free()
