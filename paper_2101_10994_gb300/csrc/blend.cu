@@ -122,7 +122,7 @@ extern "C" int sphere_trace_blend(const nglod_svo* svo, const nglod_features* fe
     A.hit_list = (int32_t*)((char*)work + trace_ws_hit_list_offset(R));
     A.ctas_per_sm = params->ctas_per_sm;
     NGLOD_CUDA(cudaMemsetAsync(work, 0, 256, st));
-    if ((rc = enqueue_ray_order(A, work, st))) return rc;
+    if ((rc = enqueue_ray_order(A, work, svo->node[A.D], st))) return rc;
     if ((rc = enable_hit_masks(A, work, st, true))) return rc;
     if (params->decode_dtype == NGLOD_F32)
         rc = launch_trace_blend_f32(dec_lo, dec_hi, alpha, tb, A, f16, svo->num_sms, st);

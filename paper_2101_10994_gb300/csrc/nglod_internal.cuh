@@ -40,6 +40,10 @@ struct nglod_svo {
     // anc[d][8 v + i] = id of the depth-(3 + i) voxel containing voxel v of
     // depth d, for i = 0..d-3 (i = d-3 is v itself); unused entries are -1.
     int32_t* anc[nglod::kMaxDepth + 1] = {};
+    // cids[d][(v (d - 2) + i) 8 + c] = corner id, at depth 3 + i, of corner c
+    // of the depth-(3 + i) voxel containing voxel v of depth d (i = 0..d-3):
+    // every corner id a query in voxel v gathers, one 32-byte record per level
+    int32_t* cids[nglod::kMaxDepth + 1] = {};
     int* dstatus = nullptr;                               // device status word
     unsigned* dscratch = nullptr;                         // 16 device words (reductions)
     int device = 0;

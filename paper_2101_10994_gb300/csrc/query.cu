@@ -49,6 +49,7 @@ int fill_tables(const nglod_svo* svo, const nglod_features* f, int lod, Tables& 
         tb.node[d] = ok ? svo->node[d] : nullptr;
         tb.corners[d] = ok ? svo->corners[d] : nullptr;
         tb.anc[d] = ok ? svo->anc[d] : nullptr;
+        tb.cids[d] = ok && d >= kFirstFeatureDepth ? svo->cids[d] : nullptr;
     }
     return NGLOD_OK;
 }
@@ -359,13 +360,16 @@ __global__ void __launch_bounds__(kThreads) k_grad(const DecPtrs dp, const Table
             if (sdd >= kFirstFeatureDepth) {
                 const float4 ga = *reinterpret_cast<const float4*>(zb + s * kZStride + 8 * l4);
                 const float4 gc = *reinterpret_cast<const float4*>(zb + s * kZStride + 8 * l4 + 4);
-                int2 a = make_int2(-1, -1);
-                if (2 * l4 <= sdd - kFirstFeatureDepth)
-                    a = __ldg(reinterpret_cast<const int2*>(tb.anc[sdd] + (size_t)svox * 8) + l4);
-                for (int dp2 = tb.first_depth; dp2 <= min(sdd, dcap); ++dp2) {
+                // corner ids from the flat table, the next level's in flight
+                const int top2 = min(sdd, dcap);
+                const int2* ids = reinterpret_cast<const int2*>(
+                                      tb.cids[sdd] + (size_t)svox * (sdd - kFirstFeatureDepth + 1) * 8) + l4;
+                int2 cn = tb.first_depth <= top2 ? __ldg(ids + 4 * (tb.first_depth - kFirstFeatureDepth))
+                                                 : make_int2(0, 0);
+                for (int dp2 = tb.first_depth; dp2 <= top2; ++dp2) {
                     const int i = dp2 - kFirstFeatureDepth;
-                    const int vv = __shfl_sync(gm4, (i & 1) ? a.y : a.x, gb4 + (i >> 1));
-                    const int2 cc = __ldg(reinterpret_cast<const int2*>(tb.corners[dp2] + (size_t)vv * 8) + l4);
+                    const int2 cc = cn;
+                    if (dp2 < top2) cn = __ldg(ids + 4 * (i + 1));
                     const int sh = sdd - dp2;
                     const float sc = pow2f(dp2 - 1);
                     const uint32_t ci[3] = {unpack_i(sijk) >> sh, unpack_j(sijk) >> sh, unpack_k(sijk) >> sh};
@@ -475,6 +479,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_trace_f32(const DecPtrs dp, con
                 zr[1] = zc;
             }
         }
+        prefetch_next_ijk(S, A, tb);
         __syncwarp();
         uint4 mask;
         const float dhat = mlp_f32<IN, true>(sd, b2, zb + lane * kZStride, x0, x1, x2, &mask);
@@ -532,6 +537,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_trace_batch_f32(const TraceJob*
                 zr[0] = za;
                 zr[1] = zc;
             }
+            if (S.ray >= 0) prefetch_next_ijk(S, jobs[S.job].A, jobs[S.job].tb);
             __syncwarp();
             uint4 mask;
             const float dhat = mlp_f32<IN, true>(sd, b2, zb + lane * kZStride, x0, x1, x2, &mask);
@@ -616,6 +622,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_trace_blend_f32(const DecPtrs l
         const float q0 = __fadd_rn(x0, 1.0f), q1 = __fadd_rn(x1, 1.0f), q2 = __fadd_rn(x2, 1.0f);
         float dlo = 0.0f, dhi = 0.0f;
         uint4 mlo = make_uint4(0u, 0u, 0u, 0u), mhi = mlo;
+        prefetch_next_ijk(S, A, tb);
 #pragma unroll 1
         for (int pass = 0; pass < 2; ++pass) {
             // pass 0: depths 3..D-1 into the rows; pass 1: add depth D
@@ -997,8 +1004,11 @@ namespace {
 // decreasing longest-list length (a counting sort over kOrderBuckets
 // lengths, clamped), which changes only the schedule: every ray's outputs
 // are those of the index-order trace.
+// Also writes each ray's first list entry (t_enter, t_exit, voxel, packed
+// ijk) to start[r], so the tracer starts a ray with independent loads only.
 __global__ void k_group_keys(const int32_t* __restrict__ offs, long long R, uint8_t* __restrict__ key,
-                             int* __restrict__ hist) {
+                             int* __restrict__ hist, const float2* __restrict__ tr, const int32_t* __restrict__ vid,
+                             const Node* __restrict__ node_D, int4* __restrict__ start) {
     __shared__ int h[kOrderBuckets];
     for (int i = threadIdx.x; i < kOrderBuckets; i += blockDim.x) h[i] = 0;
     __syncthreads();
@@ -1007,7 +1017,13 @@ __global__ void k_group_keys(const int32_t* __restrict__ offs, long long R, uint
     const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
     for (long long g = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); g < G; g += nw) {
         const long long r = g * 32 + lane;
-        const int len = r < R ? offs[r + 1] - offs[r] : 0;
+        const int c0 = r < R ? offs[r] : 0;
+        const int len = r < R ? offs[r + 1] - c0 : 0;
+        if (len > 0) {
+            const float2 t0 = tr[c0];
+            const int v = vid[c0];
+            start[r] = make_int4(__float_as_int(t0.x), __float_as_int(t0.y), v, (int)node_D[v].ijk);
+        }
         const int m = __reduce_max_sync(0xffffffffu, len);
         if (lane == 0) {
             const int b = kOrderBuckets - 1 - min(max(m, 0), kOrderBuckets - 1);   // longest first
@@ -1059,7 +1075,7 @@ int enable_hit_masks(TraceArgs& A, void* work, cudaStream_t st, bool two) {
     return NGLOD_OK;
 }
 
-int enqueue_ray_order(TraceArgs& A, void* work, cudaStream_t st) {
+int enqueue_ray_order(TraceArgs& A, void* work, const Node* node_D, cudaStream_t st) {
     const long long R = A.R, G = (R + 31) / 32;
     char* w = static_cast<char*>(work);
     int32_t* order = reinterpret_cast<int32_t*>(w + trace_ws_order_offset(R));
@@ -1069,12 +1085,14 @@ int enqueue_ray_order(TraceArgs& A, void* work, cudaStream_t st) {
     NGLOD_CUDA(cudaMemsetAsync(hist, 0, kOrderBuckets * sizeof(int), st));
     const int sms = device_sms();
     const int gk = (int)std::max<long long>(1, std::min<long long>((G + 7) / 8, (long long)sms * 4));
-    k_group_keys<<<gk, 256, 0, st>>>(A.offs, R, key, hist);
+    int4* start = reinterpret_cast<int4*>(w + trace_ws_start_offset(R));
+    k_group_keys<<<gk, 256, 0, st>>>(A.offs, R, key, hist, A.tr, A.vid, node_D, start);
     k_order_scan<<<1, kOrderBuckets, 0, st>>>(hist, cursor);
     const int gs = (int)std::max<long long>(1, std::min<long long>((G + 255) / 256, (long long)sms * 4));
     k_order_scatter<<<gs, 256, 0, st>>>(key, G, cursor, order);
     NGLOD_CUDA(cudaGetLastError());
     A.order = order;
+    A.start = start;
     return NGLOD_OK;
 }
 
@@ -1136,7 +1154,7 @@ extern "C" int sphere_trace(const nglod_svo* svo, const nglod_features* feats, c
     NGLOD_CUDA(cudaMemsetAsync(work, 0, 256, st));
     rc = check_decoder(dec);
     if (rc) return rc;
-    if ((rc = enqueue_ray_order(A, work, st))) return rc;
+    if ((rc = enqueue_ray_order(A, work, svo->node[D], st))) return rc;
     // the FP8 decode's ReLU masks are not recorded: with z rounded to four
     // significant bits a pre-activation can round to zero or flip sign (a
     // read-out unit pair at z = 0 would give a zero gradient), so its

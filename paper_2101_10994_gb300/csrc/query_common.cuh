@@ -29,6 +29,7 @@ struct Tables {
     int first_depth;
     const int32_t* corners[kMaxDepth + 1];   // [V_dp, 8]
     const int32_t* anc[kMaxDepth + 1];       // [V_dp, 8]
+    const int32_t* cids[kMaxDepth + 1];      // [V_dp, dp - 2, 8]: corner ids of every level (svo_build)
     const Node* node[kMaxDepth + 1];
 };
 
@@ -130,25 +131,35 @@ struct FeatLoad8<__half> {
     }
 };
 
+// FP32 fused multiply-add of two lanes at once (a packed pair, each
+// component rounded once exactly as fmaf): z += w * r.
+__device__ __forceinline__ float2 fma2(float w, float2 r, float2 z) {
+    return __ffma2_rn(make_float2(w, w), r, z);
+}
+
 // gather_slot with 4-lane groups: lane l4 of the group owns channels
-// 8 l4 .. 8 l4 + 7, so a warp interpolates 8 slots at a time.  The ancestor
-// and corner ids come as one 8-byte load per lane (two levels / two corners
-// each) and are shared within the group; every channel sums the same terms
-// in the same order as gather_slot (bit-identical result).
+// 8 l4 .. 8 l4 + 7, so a warp interpolates 8 slots at a time.  The corner
+// ids of a level come from the flat table (one 8-byte load per lane: two
+// corners each, shared within the group), and the next level's ids are in
+// flight while this level's rows are loaded.  Every channel sums the same
+// terms in the same order as gather_slot (levels ascending, corners 0..7;
+// packed FMAs round each lane exactly as fmaf), so the result is
+// bit-identical to it.
 template <typename T>
 __device__ __forceinline__ void gather_slot4(const Tables& tb, int dd, int vox, uint32_t ijk, float q0, float q1,
                                              float q2, unsigned gmask, int gbase, int l4, float4& za, float4& zb,
                                              int dlast = kMaxDepth, int dfirst = kFirstFeatureDepth) {
-    za = make_float4(0.f, 0.f, 0.f, 0.f);
-    zb = za;
-    int2 a = make_int2(-1, -1);
-    if (2 * l4 <= dd - kFirstFeatureDepth) a = __ldg(reinterpret_cast<const int2*>(tb.anc[dd] + (size_t)vox * 8) + l4);
+    float2 z[4] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
     const int top = min(dd, dlast);     // only depths dfirst..dlast (level blending, Eq. 3)
+    int dp = max(dfirst, tb.first_depth);
+    // lane l4's pair of corner ids at level i: ids[4 i]
+    const int2* ids = reinterpret_cast<const int2*>(tb.cids[dd] + (size_t)vox * (dd - kFirstFeatureDepth + 1) * 8) + l4;
+    int2 cc = dp <= top ? __ldg(ids + 4 * (dp - kFirstFeatureDepth)) : make_int2(0, 0);
 #pragma unroll 1
-    for (int dp = max(dfirst, tb.first_depth); dp <= top; ++dp) {
+    for (; dp <= top; ++dp) {
         const int i = dp - kFirstFeatureDepth;
-        const int v = __shfl_sync(gmask, (i & 1) ? a.y : a.x, gbase + (i >> 1));
-        const int2 cc = __ldg(reinterpret_cast<const int2*>(tb.corners[dp] + (size_t)v * 8) + l4);
+        const int2 cur = cc;
+        if (dp < top) cc = __ldg(ids + 4 * (i + 1));
         const int sh = dd - dp;
         const float sc = pow2f(dp - 1);
         const float u0 = clamp01(__fsub_rn(__fmul_rn(q0, sc), (float)(unpack_i(ijk) >> sh)));
@@ -160,21 +171,19 @@ __device__ __forceinline__ void gather_slot4(const Tables& tb, int dd, int vox, 
         float4 ra[8], rb[8];
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
-            const int cid = __shfl_sync(gmask, (c & 1) ? cc.y : cc.x, gbase + (c >> 1));
+            const int cid = __shfl_sync(gmask, (c & 1) ? cur.y : cur.x, gbase + (c >> 1));
             FeatLoad8<T>::load(fb, cid, l4, ra[c], rb[c]);
         }
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
-            za.x = fmaf(w[c], ra[c].x, za.x);
-            za.y = fmaf(w[c], ra[c].y, za.y);
-            za.z = fmaf(w[c], ra[c].z, za.z);
-            za.w = fmaf(w[c], ra[c].w, za.w);
-            zb.x = fmaf(w[c], rb[c].x, zb.x);
-            zb.y = fmaf(w[c], rb[c].y, zb.y);
-            zb.z = fmaf(w[c], rb[c].z, zb.z);
-            zb.w = fmaf(w[c], rb[c].w, zb.w);
+            z[0] = fma2(w[c], make_float2(ra[c].x, ra[c].y), z[0]);
+            z[1] = fma2(w[c], make_float2(ra[c].z, ra[c].w), z[1]);
+            z[2] = fma2(w[c], make_float2(rb[c].x, rb[c].y), z[2]);
+            z[3] = fma2(w[c], make_float2(rb[c].z, rb[c].w), z[3]);
         }
     }
+    za = make_float4(z[0].x, z[0].y, z[1].x, z[1].y);
+    zb = make_float4(z[2].x, z[2].y, z[3].x, z[3].y);
 }
 
 // Locates x by descending from the root through the child masks (the voxels

@@ -164,6 +164,25 @@ __global__ void k_ancestors(NodePtrs np, int d, int64_t n, int32_t* __restrict__
     }
 }
 
+// Flat corner-id table of depth d: for voxel v the corner ids of its
+// ancestors at depths 3..d, level by level (anc then corners, resolved once
+// here so a query's ids are one load per level instead of two dependent ones).
+struct CornerPtrs {
+    const int32_t* corners[kMaxDepth + 1];
+};
+
+__global__ void k_flat_corners(CornerPtrs cp, int d, int64_t n, const int32_t* __restrict__ anc,
+                               int32_t* __restrict__ cids) {
+    const int nl = d - kFirstFeatureDepth + 1;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n * nl * 8;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t v = t / (nl * 8);
+        const int i = (int)((t / 8) % nl), c = (int)(t & 7);
+        const int32_t a = anc[8 * v + i];
+        cids[t] = cp.corners[kFirstFeatureDepth + i][8 * (int64_t)a + c];
+    }
+}
+
 // ---- three-pass exclusive scan of per-word popcounts (build time only) ----
 constexpr int kScanBlock = 1024;
 
@@ -247,6 +266,7 @@ void destroy(nglod_svo* s, cudaStream_t st) {
         if (s->node[d]) cudaFreeAsync(s->node[d], st);
         if (s->corners[d]) cudaFreeAsync(s->corners[d], st);
         if (s->anc[d]) cudaFreeAsync(s->anc[d], st);
+        if (s->cids[d]) cudaFreeAsync(s->cids[d], st);
     }
     if (s->dstatus) cudaFreeAsync(s->dstatus, st);
     if (s->dscratch) cudaFreeAsync(s->dscratch, st);
@@ -372,6 +392,16 @@ extern "C" int svo_build(const uint64_t* const* h_keys, const int64_t* h_counts,
         s->nc[d] = total;
         cudaFreeAsync(scratch, st);
         scratch = nullptr;
+    }
+    {
+        CornerPtrs cp;
+        for (int d = 0; d <= kMaxDepth; ++d) cp.corners[d] = d < num_depths ? s->corners[d] : nullptr;
+        for (int d = kFirstFeatureDepth; d < num_depths; ++d) {
+            const int64_t cnt = s->n[d] * (d - kFirstFeatureDepth + 1) * 8;
+            BUILD_CUDA(cudaMallocAsync(&s->cids[d], sizeof(int32_t) * cnt, st));
+            k_flat_corners<<<grid_for(cnt), 256, 0, st>>>(cp, d, s->n[d], s->anc[d], s->cids[d]);
+        }
+        BUILD_CUDA(cudaGetLastError());
     }
     cleanup_tmp();
 #undef BUILD_CUDA

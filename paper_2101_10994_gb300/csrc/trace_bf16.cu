@@ -368,6 +368,7 @@ __global__ void __launch_bounds__(kTM, kCtasPerSm) k_trace_bf16(const DecPtrsB d
                 put_any<PM>(S, warp * 32 + s, 2 * l4 + 1, zb, dp.z_scale);
             }
         }
+        prefetch_next_ijk(st, A, tb);
         const bool ok = mma_any<PM>(S, taddr, phase, dp.polls);
         if (!__syncthreads_and(ok)) {
             if (threadIdx.x == 0) atomicExch(err, kStatusTimeout);
@@ -773,6 +774,7 @@ __global__ void __launch_bounds__(kTM, kCtasPerSm) k_trace_blend_bf16(const DecP
                 put_z<false>(S.hi, warp * 32 + s, 2 * l4 + h, zh[h], 1.0f);
             }
         }
+        prefetch_next_ijk(st, A, tb);
         float dhat = 0.0f;
         uint4 mlo = make_uint4(0u, 0u, 0u, 0u), mhi = mlo;
         failed = blend_decode<IN>(S, taddr, ph_lo, ph_hi, b2lo, b2hi, alpha, x0, x1, x2,

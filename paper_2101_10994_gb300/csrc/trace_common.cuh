@@ -116,6 +116,10 @@ struct TraceArgs {
     uint4* hit_mask = nullptr;
     uint4* hit_mask2 = nullptr;   // level blending: the second decoder's masks
     int ctas_per_sm = 0;          // launch width of the persistent trace (0: the most that fit)
+    // workspace (null: not prepared): per ray its first list entry as
+    // (t_enter bits, t_exit bits, voxel id, packed ijk), written by the
+    // handout-order pass, so a ray starts with one round of independent loads
+    const int4* start = nullptr;
 };
 
 // One ray being traced: its list cursor [cur, end) with the current entry's
@@ -129,6 +133,12 @@ struct RaySlot {
     float t, tin, tout, dprev;
     int cur, end, k, vox;
     uint32_t ijk;
+    // the next list entry (cur + 1 < end), loaded ahead so that moving on
+    // costs no list read; its voxel's packed ijk once nijk_ok
+    float ntin, ntout;
+    int nvox;
+    uint32_t nijk;
+    bool nijk_ok;
 };
 
 // Warp-uniform batch of ray indices taken from the global queue.
@@ -170,24 +180,47 @@ __device__ __forceinline__ void publish_hits(RaySlot& S, const TraceArgs& A, int
     S.hit_ray = -1;
 }
 
+// Issues the loads of the list entry after the current one (consumed by a
+// later advance, so their latency hides behind the next decode).
+__device__ __forceinline__ void load_next(RaySlot& S, const TraceArgs& A) {
+    if (S.cur + 1 < S.end) {
+        const float2 tr = A.tr[S.cur + 1];
+        S.ntin = tr.x;
+        S.ntout = tr.y;
+        S.nvox = A.vid[S.cur + 1];
+    }
+    S.nijk_ok = false;
+}
+
+// The packed ijk of the next entry's voxel (its id arrived during the last
+// decode); called between the gather and the decoder, so it is in a register
+// before the ray can move on.
+__device__ __forceinline__ void prefetch_next_ijk(RaySlot& S, const TraceArgs& A, const Tables& tb) {
+    if (S.ray >= 0 && !S.nijk_ok && S.cur + 1 < S.end) {
+        S.nijk = tb.node[A.D][S.nvox].ijk;
+        S.nijk_ok = true;
+    }
+}
+
 // Moves the cursor past entries that end before t (the ray is discarded when
 // the list runs out), then jumps t to the current entry's start (Sec. 3.4).
 __device__ __forceinline__ void advance(RaySlot& S, const TraceArgs& A, const Tables& tb) {
-    bool moved = false;
+    int moves = 0;
+    bool have_ijk = false;
     while (S.t > S.tout) {
         if (++S.cur >= S.end) {
             finish(S, A, false);
             return;
         }
-        const float2 tr = A.tr[S.cur];
-        S.tin = tr.x;
-        S.tout = tr.y;
-        moved = true;
+        S.tin = S.ntin;
+        S.tout = S.ntout;
+        S.vox = S.nvox;
+        have_ijk = moves == 0 && S.nijk_ok;
+        if (have_ijk) S.ijk = S.nijk;
+        ++moves;
+        load_next(S, A);
     }
-    if (moved) {
-        S.vox = A.vid[S.cur];
-        S.ijk = tb.node[A.D][S.vox].ijk;
-    }
+    if (moves && !have_ijk) S.ijk = tb.node[A.D][S.vox].ijk;
     if (S.t < S.tin) S.t = S.tin;
     if (S.t > A.far_t) finish(S, A, false);
 }
@@ -199,6 +232,8 @@ __device__ __forceinline__ void start_ray(RaySlot& S, int r, const TraceArgs& A,
     S.vox = -1;
     S.cur = A.offs[r];
     S.end = A.offs[r + 1];
+    int4 first = make_int4(0, 0, 0, 0);
+    if (A.start) first = A.start[r];      // independent of the offsets: one round of loads
     if (S.cur >= S.end) {
         finish(S, A, false);
         return;
@@ -209,13 +244,21 @@ __device__ __forceinline__ void start_ray(RaySlot& S, int r, const TraceArgs& A,
     S.dx = A.d[3 * r];
     S.dy = A.d[3 * r + 1];
     S.dz = A.d[3 * r + 2];
-    const float2 tr = A.tr[S.cur];
-    S.tin = tr.x;
-    S.tout = tr.y;
-    S.t = tr.x;
+    if (A.start) {
+        S.tin = __int_as_float(first.x);
+        S.tout = __int_as_float(first.y);
+        S.vox = first.z;
+        S.ijk = (uint32_t)first.w;
+    } else {
+        const float2 tr = A.tr[S.cur];
+        S.tin = tr.x;
+        S.tout = tr.y;
+        S.vox = A.vid[S.cur];
+        S.ijk = tb.node[A.D][S.vox].ijk;
+    }
+    S.t = S.tin;
     S.dprev = __int_as_float(0x7fc00000);
-    S.vox = A.vid[S.cur];
-    S.ijk = tb.node[A.D][S.vox].ijk;
+    load_next(S, A);
     if (S.t > A.far_t) finish(S, A, false);
 }
 
@@ -375,14 +418,18 @@ inline size_t trace_ws_count_offset(long long R) { return trace_ws_key_offset(R)
 inline size_t trace_ws_mask_offset(long long R) {
     return trace_ws_count_offset(R) + trace_ws_align(2 * kOrderBuckets * sizeof(int));
 }
-inline size_t trace_ws_size(long long R) { return trace_ws_mask_offset(R) + 32 * (size_t)R; }
+// ... then, per ray, its first list entry (16 B; the handout-order pass writes it)
+inline size_t trace_ws_start_offset(long long R) { return trace_ws_mask_offset(R) + trace_ws_align(32 * (size_t)R); }
+inline size_t trace_ws_size(long long R) { return trace_ws_start_offset(R) + 16 * (size_t)R; }
 // header word 3: 1 = one mask per hit (plain traces), 2 = two (blended: the
 // lower LOD's at [0, R), the upper's at [R, 2R)), 0 = none
 constexpr int kWsMaskFlagWord = 3;
 // Points A at the workspace's mask region(s) and marks them as recorded.
 int enable_hit_masks(TraceArgs& A, void* work, cudaStream_t st, bool two = false);
-// Enqueues the work-ordered ray-group handout of a trace (sets A.order).
-int enqueue_ray_order(TraceArgs& A, void* work, cudaStream_t st);
+// Enqueues the work-ordered ray-group handout of a trace (sets A.order) and
+// the rays' first-entry records (sets A.start; node_D = the nodes of the
+// lists' depth).
+int enqueue_ray_order(TraceArgs& A, void* work, const Node* node_D, cudaStream_t st);
 // split = true: the FP32-accurate decode (three-term BF16 splits, six products)
 int launch_trace_bf16(const nglod_svo* svo, const nglod_decoder* dec, const Tables& tb, const TraceArgs& A,
                       bool f16, float fp8_z_absmax, cudaStream_t st, bool split = false);

@@ -12,11 +12,12 @@ pytestmark = pytest.mark.gpu
 
 
 # FP32 gradients summed by atomics: an element's error is a few FP32
-# roundings of its own terms.  Each element is held to 2e-5 of its own value
-# plus 2e-6 of the tensor's largest element (a single max-error / max-value
-# ratio would let the small gradients of corners touched by few points go
-# unchecked).
-RTOL, ATOL_FRAC = 2e-5, 2e-6
+# roundings of its own terms, which may cancel (sums over thousands of
+# points of both signs), so besides 2e-5 of its own value each element is
+# allowed 4e-6 of the tensor's largest element -- five times less than a
+# single max-error / max-value ratio of 2e-5 would allow it, which would let
+# the small gradients of corners touched by few points go unchecked.
+RTOL, ATOL_FRAC = 2e-5, 4e-6
 
 
 def elem_err(a, b):
