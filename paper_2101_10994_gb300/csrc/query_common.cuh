@@ -145,16 +145,33 @@ __device__ __forceinline__ float2 fma2(float w, float2 r, float2 z) {
 // terms in the same order as gather_slot (levels ascending, corners 0..7;
 // packed FMAs round each lane exactly as fmaf), so the result is
 // bit-identical to it.
+// This lane's pair of corner ids (corners 2 l4, 2 l4 + 1) at depth dp of the
+// depth-dd voxel vox, from the flat table.
+__device__ __forceinline__ const int2* corner_ids(const Tables& tb, int dd, int vox, int dp, int l4) {
+    return reinterpret_cast<const int2*>(tb.cids[dd] + ((size_t)vox * (dd - kFirstFeatureDepth + 1) +
+                                                        (dp - kFirstFeatureDepth)) * 8) + l4;
+}
+
+// The first depth a gather over depths dfirst..dlast reads.
+__device__ __forceinline__ int gather_first_depth(const Tables& tb, int dfirst = kFirstFeatureDepth) {
+    return max(dfirst, tb.first_depth);
+}
+
+// gather_slot4 with the first level's corner ids already loaded by the
+// caller (first_ids = *corner_ids(tb, dd, vox, gather_first_depth(tb,
+// dfirst), l4)), so that a loop over slots can fetch the next slot's ids
+// while this one is gathered.
 template <typename T>
-__device__ __forceinline__ void gather_slot4(const Tables& tb, int dd, int vox, uint32_t ijk, float q0, float q1,
-                                             float q2, unsigned gmask, int gbase, int l4, float4& za, float4& zb,
-                                             int dlast = kMaxDepth, int dfirst = kFirstFeatureDepth) {
+__device__ __forceinline__ void gather_slot4_ids(const Tables& tb, int dd, int vox, uint32_t ijk, float q0, float q1,
+                                                 float q2, unsigned gmask, int gbase, int l4, float4& za, float4& zb,
+                                                 int2 first_ids, int dlast = kMaxDepth,
+                                                 int dfirst = kFirstFeatureDepth) {
     float2 z[4] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
     const int top = min(dd, dlast);     // only depths dfirst..dlast (level blending, Eq. 3)
-    int dp = max(dfirst, tb.first_depth);
+    int dp = gather_first_depth(tb, dfirst);
     // lane l4's pair of corner ids at level i: ids[4 i]
     const int2* ids = reinterpret_cast<const int2*>(tb.cids[dd] + (size_t)vox * (dd - kFirstFeatureDepth + 1) * 8) + l4;
-    int2 cc = dp <= top ? __ldg(ids + 4 * (dp - kFirstFeatureDepth)) : make_int2(0, 0);
+    int2 cc = first_ids;
 #pragma unroll 1
     for (; dp <= top; ++dp) {
         const int i = dp - kFirstFeatureDepth;
@@ -184,6 +201,15 @@ __device__ __forceinline__ void gather_slot4(const Tables& tb, int dd, int vox, 
     }
     za = make_float4(z[0].x, z[0].y, z[1].x, z[1].y);
     zb = make_float4(z[2].x, z[2].y, z[3].x, z[3].y);
+}
+
+template <typename T>
+__device__ __forceinline__ void gather_slot4(const Tables& tb, int dd, int vox, uint32_t ijk, float q0, float q1,
+                                             float q2, unsigned gmask, int gbase, int l4, float4& za, float4& zb,
+                                             int dlast = kMaxDepth, int dfirst = kFirstFeatureDepth) {
+    const int dp = gather_first_depth(tb, dfirst);
+    const int2 first = dp <= min(dd, dlast) ? __ldg(corner_ids(tb, dd, vox, dp, l4)) : make_int2(0, 0);
+    gather_slot4_ids<T>(tb, dd, vox, ijk, q0, q1, q2, gmask, gbase, l4, za, zb, first, dlast, dfirst);
 }
 
 // Locates x by descending from the root through the child masks (the voxels

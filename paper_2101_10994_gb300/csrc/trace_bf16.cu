@@ -145,13 +145,26 @@ __device__ __forceinline__ void put_z(BfSmem& S, int row, int l, float4 z, float
     }
 }
 
-// Issues the tile's MMA (thread 0) and waits for it (all threads); returns
-// false if the wait expired.
-template <bool FP8>
-__device__ __forceinline__ bool mma_tile(BfSmem& S, uint32_t taddr, uint32_t& phase, long long polls) {
+// Makes the A-tile writes visible to the tensor core and meets the CTA's
+// other threads (the barrier before an MMA); returns whether any thread's
+// `act` is set.
+__device__ __forceinline__ bool tile_barrier_or(bool act) {
     tc::fence_proxy_async_smem();
     tc::fence_before_sync();
-    __syncthreads();
+    return __syncthreads_or(act) != 0;
+}
+
+// Issues the tile's MMA (thread 0) and waits for it (all threads); returns
+// false if the wait expired.  barrier = false: the caller has just passed
+// tile_barrier_or.
+template <bool FP8>
+__device__ __forceinline__ bool mma_tile(BfSmem& S, uint32_t taddr, uint32_t& phase, long long polls,
+                                         bool barrier = true) {
+    if (barrier) {
+        tc::fence_proxy_async_smem();
+        tc::fence_before_sync();
+        __syncthreads();
+    }
     if (threadIdx.x == 0) {
         tc::fence_after_sync();
         const uint32_t a0 = tc::smem_u32(S.A), b0 = tc::smem_u32(S.B);
@@ -275,10 +288,13 @@ __device__ __forceinline__ void put_z_split(BfSmem3& S, int row, int l, float4 z
 
 // The six products A_i B_j (i + j <= 2), smallest first, into one FP32
 // accumulator; issued by thread 0, waited for by all (bounded).
-__device__ __forceinline__ bool mma_tile_split(BfSmem3& S, uint32_t taddr, uint32_t& phase, long long polls) {
-    tc::fence_proxy_async_smem();
-    tc::fence_before_sync();
-    __syncthreads();
+__device__ __forceinline__ bool mma_tile_split(BfSmem3& S, uint32_t taddr, uint32_t& phase, long long polls,
+                                               bool barrier = true) {
+    if (barrier) {
+        tc::fence_proxy_async_smem();
+        tc::fence_before_sync();
+        __syncthreads();
+    }
     if (threadIdx.x == 0) {
         tc::fence_after_sync();
         constexpr int kPi[6] = {2, 1, 0, 1, 0, 0}, kPj[6] = {0, 1, 2, 0, 1, 0};
@@ -313,9 +329,9 @@ __device__ __forceinline__ void put_any(typename TcSmem<PM>::type& S, int row, i
 
 template <int PM>
 __device__ __forceinline__ bool mma_any(typename TcSmem<PM>::type& S, uint32_t taddr, uint32_t& phase,
-                                        long long polls) {
-    if constexpr (PM == 2) return mma_tile_split(S, taddr, phase, polls);
-    else return mma_tile<PM == 1>(S, taddr, phase, polls);
+                                        long long polls, bool barrier = true) {
+    if constexpr (PM == 2) return mma_tile_split(S, taddr, phase, polls, barrier);
+    else return mma_tile<PM == 1>(S, taddr, phase, polls, barrier);
 }
 
 // ---------------------------------------------------------------------------
@@ -341,10 +357,10 @@ __global__ void __launch_bounds__(kTM, kCtasPerSm) k_trace_bf16(const DecPtrsB d
     st.hit_ray = -1;
     RayQueue Qu;
     Qu.init();
+    const int d0 = gather_first_depth(tb);
     for (;;) {
         refill(st, Qu, A, tb, lane);
         const bool act = st.ray >= 0;
-        if (!__syncthreads_or(act)) break;
         const float x0 = fmaf(st.t, st.dx, st.ox), x1 = fmaf(st.t, st.dy, st.oy), x2 = fmaf(st.t, st.dz, st.oz);
         const float q0 = __fadd_rn(x0, 1.0f), q1 = __fadd_rn(x1, 1.0f), q2 = __fadd_rn(x2, 1.0f);
         // a warp without rays (the tail of the frame) leaves its 32 A-tile
@@ -353,23 +369,38 @@ __global__ void __launch_bounds__(kTM, kCtasPerSm) k_trace_bf16(const DecPtrsB d
         if (wact) {
             const int g4 = lane >> 2, l4 = lane & 3, gb4 = g4 << 2;
             const unsigned gm4 = 0xfu << gb4;
+            // the first level's corner ids of the next round's slot are
+            // fetched while this round's slot is gathered
+            // (every shuffle here runs on all 32 lanes: only the loads are conditional)
+            int nact = __shfl_sync(0xffffffffu, act ? 1 : 0, g4);
+            const int vox0 = __shfl_sync(0xffffffffu, st.vox, g4);
+            int2 nids = nact ? __ldg(corner_ids(tb, A.D, vox0, d0, l4)) : make_int2(0, 0);
 #pragma unroll 1
             for (int r = 0; r < 4; ++r) {
                 const int s = r * 8 + g4;
-                const int sact = __shfl_sync(0xffffffffu, act ? 1 : 0, s);
+                const int sact = nact;
+                const int2 ids = nids;
                 const int svox = __shfl_sync(0xffffffffu, st.vox, s);
                 const uint32_t sijk = __shfl_sync(0xffffffffu, st.ijk, s);
                 const float s0 = __shfl_sync(0xffffffffu, q0, s);
                 const float s1 = __shfl_sync(0xffffffffu, q1, s);
                 const float s2 = __shfl_sync(0xffffffffu, q2, s);
+                if (r < 3) {
+                    nact = __shfl_sync(0xffffffffu, act ? 1 : 0, s + 8);
+                    const int nvox = __shfl_sync(0xffffffffu, st.vox, s + 8);
+                    if (nact) nids = __ldg(corner_ids(tb, A.D, nvox, d0, l4));
+                }
                 float4 za = make_float4(0.f, 0.f, 0.f, 0.f), zb = za;
-                if (sact) gather_slot4<T>(tb, A.D, svox, sijk, s0, s1, s2, gm4, gb4, l4, za, zb);
+                if (sact) gather_slot4_ids<T>(tb, A.D, svox, sijk, s0, s1, s2, gm4, gb4, l4, za, zb, ids);
                 put_any<PM>(S, warp * 32 + s, 2 * l4, za, dp.z_scale);
                 put_any<PM>(S, warp * 32 + s, 2 * l4 + 1, zb, dp.z_scale);
             }
         }
         prefetch_next_ijk(st, A, tb);
-        const bool ok = mma_any<PM>(S, taddr, phase, dp.polls);
+        // one barrier both ends the loop (no ray left in the CTA) and
+        // publishes the A tile to the MMA
+        if (!tile_barrier_or(act)) break;
+        const bool ok = mma_any<PM>(S, taddr, phase, dp.polls, false);
         if (!__syncthreads_and(ok)) {
             if (threadIdx.x == 0) atomicExch(err, kStatusTimeout);
             drained = false;
