@@ -41,6 +41,7 @@ struct BfSmem {
     unsigned char A[kTM * kFeatDim * 2];      // z tile, bf16 or e4m3, K-major
     unsigned char B[kHidden * kFeatDim * 2];  // W1 (z columns), bf16 or e4m3, K-major
     float4 epi[kHidden];                      // (b1, W2, W1x_0, W1x_1)
+    float4 bw[kHidden / 2];                   // (b1, W2) of units 2j and 2j + 1
     float wx2[kHidden];                       // W1x_2
     float amax[kTM / 32];                     // FP8: per-warp |W1z| maxima
     float acc_scale;                          // FP8: 1 / (W1 scale * z scale)
@@ -62,6 +63,7 @@ struct BfSmem3 {
     unsigned char A[3][kTM * kFeatDim * 2];
     unsigned char B[3][kHidden * kFeatDim * 2];
     float4 epi[kHidden];
+    float4 bw[kHidden / 2];
     float wx2[kHidden];
     float amax[kTM / 32];
     float acc_scale;
@@ -125,6 +127,8 @@ __device__ __forceinline__ void stage_bf16_decoder(BfSmem& S, const DecPtrsB& dp
         S.epi[h] = make_float4(dp.b1[h], dp.W2[h], x0, x1);
         S.wx2[h] = OFF ? dp.W1[h * IN + 2] : 0.f;
     }
+    for (int j = threadIdx.x; j < kHidden / 2; j += blockDim.x)
+        S.bw[j] = make_float4(dp.b1[2 * j], dp.W2[2 * j], dp.b1[2 * j + 1], dp.W2[2 * j + 1]);
 }
 
 // Writes this lane's four z channels of A-tile row `row` as bf16 or, scaled,
@@ -194,6 +198,7 @@ template <int IN, class SM>
 __device__ __forceinline__ float epilogue(const SM& S, uint32_t taddr, float b2, float x0, float x1, float x2,
                                           uint4* mask = nullptr) {
     const int warp = threadIdx.x >> 5;
+    const float sc = S.acc_scale;
     float out = b2;
     uint32_t m0 = 0u, m1 = 0u, m2 = 0u, m3 = 0u;
 #pragma unroll 1
@@ -202,13 +207,26 @@ __device__ __forceinline__ float epilogue(const SM& S, uint32_t taddr, float b2,
         tc::tmem_ld32(taddr + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
         tc::tmem_wait_ld();
         uint32_t bits = 0u;
+        if constexpr (IN == kFeatDim) {
+            // (b1, W2) of two units per 16-byte shared load
 #pragma unroll
-        for (int i = 0; i < 32; ++i) {
-            const float4 e = S.epi[c0 + i];
-            float pre = fmaf(v[i], S.acc_scale, e.x);
-            if constexpr (IN != kFeatDim) pre = fmaf(e.z, x0, fmaf(e.w, x1, fmaf(S.wx2[c0 + i], x2, pre)));
-            out = fmaf(e.y, fmaxf(pre, 0.0f), out);
-            bits |= (pre > 0.0f ? 1u : 0u) << i;
+            for (int i = 0; i < 32; i += 2) {
+                const float4 e = S.bw[(c0 + i) >> 1];
+                const float p0 = fmaf(v[i], sc, e.x), p1 = fmaf(v[i + 1], sc, e.z);
+                out = fmaf(e.y, fmaxf(p0, 0.0f), out);
+                out = fmaf(e.w, fmaxf(p1, 0.0f), out);
+                bits |= (p0 > 0.0f ? 1u : 0u) << i;
+                bits |= (p1 > 0.0f ? 1u : 0u) << (i + 1);
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < 32; ++i) {
+                const float4 e = S.epi[c0 + i];
+                float pre = fmaf(v[i], sc, e.x);
+                pre = fmaf(e.z, x0, fmaf(e.w, x1, fmaf(S.wx2[c0 + i], x2, pre)));
+                out = fmaf(e.y, fmaxf(pre, 0.0f), out);
+                bits |= (pre > 0.0f ? 1u : 0u) << i;
+            }
         }
         m0 = c0 == 0 ? bits : m0;
         m1 = c0 == 32 ? bits : m1;
@@ -266,6 +284,8 @@ __device__ __forceinline__ void stage_split_decoder(BfSmem3& S, const DecPtrsB& 
         S.epi[h] = make_float4(dp.b1[h], dp.W2[h], x0, x1);
         S.wx2[h] = OFF ? dp.W1[h * IN + 2] : 0.f;
     }
+    for (int j = threadIdx.x; j < kHidden / 2; j += blockDim.x)
+        S.bw[j] = make_float4(dp.b1[2 * j], dp.W2[2 * j], dp.b1[2 * j + 1], dp.W2[2 * j + 1]);
 }
 
 // This lane's four z channels of A-tile row `row`, as three BF16 planes.

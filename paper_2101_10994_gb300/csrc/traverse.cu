@@ -23,7 +23,9 @@
 //
 // A tile whose frontier would outgrow shared memory at some level is
 // re-run over halves of its rays (recursively); a single ray always fits,
-// since a ray crosses at most 3 * 2^dp - 2 voxels of depth dp.
+// since a ray crosses at most 3 * 2^dp - 2 voxels of depth dp.  Each such
+// sub-range stages its entries as soon as its levels are done, and records
+// each ray's first staging slot, so no sub-range is run twice.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -49,7 +51,8 @@ struct Counters {
 };
 
 struct TileInfo {
-    long long stage;                   // first staging slot of the tile's entries
+    long long stage;                   // first staging slot of the tile's entries (-1: staged per
+                                       // sub-range, each ray's first slot in ray_src)
     long long count;                   // entries of the tile
 };
 
@@ -64,6 +67,7 @@ struct TileParams {
     long long R, ntiles, stage_cap;
     int D;
     int32_t* ray_cnt;                  // [R] entries per ray (k_place turns them into offsets)
+    int32_t* ray_src;                  // [R] staging slot of each ray's first entry (sub-range tiles)
     int32_t* stage_vid;                // [stage_cap] staged entries
     float2* stage_tr;
     TileInfo* tiles;                   // [ntiles]
@@ -77,7 +81,6 @@ struct TileSmem {
     uint16_t rec[kFCap];               // decisions: hit children by rank | octant << 8
     int ray_cnt[kTR];                  // entries per ray at the target depth
     long long lvl[kMaxDepth + 2];      // level sizes of the current pass
-    int sub_len[kTR];                  // fallback: lengths of the sub-ranges run
     int warp_sums[kThreads / 32 + 1];
     long long tile;
     long long stage;
@@ -263,6 +266,16 @@ __device__ bool run_levels(TileSmem& S, const TileParams& p, int r0, int nr, boo
     return true;
 }
 
+// Reserves n staging slots (one atomic, thread 0) into S.stage; flags an
+// overflow of the staging capacity.  The caller syncs before reading S.stage.
+__device__ __forceinline__ void reserve_stage(TileSmem& S, const TileParams& p, long long n) {
+    if (threadIdx.x == 0) {
+        const long long st = (long long)atomicAdd(&p.ctr->stage_top, (unsigned long long)n);
+        S.stage = st;
+        if (st + n > p.stage_cap) atomicCAS(&p.ctr->status, kStatusOk, kStatusOverflow);
+    }
+}
+
 __device__ __forceinline__ void commit_levels(TileSmem& S, const TileParams& p) {
     if (threadIdx.x >= 1 && threadIdx.x <= p.D && S.lvl[threadIdx.x])
         atomicAdd((unsigned long long*)&p.ctr->count[threadIdx.x], (unsigned long long)S.lvl[threadIdx.x]);
@@ -287,13 +300,17 @@ __global__ void __launch_bounds__(kThreads, 4) k_traverse(const TileParams p) {
         __syncthreads();
         int cur, c0, c1, base, total;
         const bool whole = run_levels(S, p, 0, nr, true, cur, c0, c1, base, total);
-        long long tile_total = 0;
-        int nsub = 0;
         if (whole) {
             commit_levels(S, p);
-            tile_total = total;
+            reserve_stage(S, p, total);
+            if (threadIdx.x == 0) p.tiles[t] = TileInfo{S.stage, (long long)total};
+            __syncthreads();
+            write_final(S, p, p.D - 1, cur, c0, c1, S.stage + base);
         } else {
-            // halve until every sub-range fits; per-ray counts accumulate
+            // halve until every sub-range fits; each sub-range reserves its
+            // own staging slots and writes its entries at once (each ray's
+            // first slot goes to ray_src for the placement)
+            long long tile_total = 0;
             int r = 0, len = nr / 2;
             while (r < nr) {
                 const int l = min(len, nr - r);
@@ -303,39 +320,22 @@ __global__ void __launch_bounds__(kThreads, 4) k_traverse(const TileParams p) {
                     continue;
                 }
                 commit_levels(S, p);
-                if (threadIdx.x == 0) S.sub_len[nsub] = l;
-                ++nsub;
+                reserve_stage(S, p, tot2);
+                __syncthreads();
+                write_final(S, p, p.D - 1, cu2, a0, a1, S.stage + b2);
+                const int j = (int)threadIdx.x;
+                int sum;
+                const int pre = block_exclusive_sum(j < l ? S.ray_cnt[r + j] : 0, S.warp_sums, sum);
+                if (j < l) p.ray_src[ra + r + j] = (int32_t)(S.stage + pre);
                 tile_total += tot2;
                 r += l;
                 // grow back after a success, so only the dense part of the
                 // tile runs at the small size
                 len = min(nr / 2, 2 * len);
             }
-        }
-        if (threadIdx.x == 0) {
-            const long long st = (long long)atomicAdd(&p.ctr->stage_top, (unsigned long long)tile_total);
-            S.stage = st;
-            p.tiles[t] = TileInfo{st, tile_total};
-            if (st + tile_total > p.stage_cap) atomicCAS(&p.ctr->status, kStatusOk, kStatusOverflow);
+            if (threadIdx.x == 0) p.tiles[t] = TileInfo{-1, tile_total};
         }
         if ((int)threadIdx.x < nr) p.ray_cnt[ra + threadIdx.x] = S.ray_cnt[threadIdx.x];
-        __syncthreads();
-        const long long st = S.stage;
-        if (whole) {
-            write_final(S, p, p.D - 1, cur, c0, c1, st + base);
-        } else {
-            long long run = st;
-            int r = 0;
-            for (int k = 0; k < nsub; ++k) {
-                const int l = S.sub_len[k];
-                int cu2, a0, a1, b2, tot2;
-                run_levels(S, p, r, l, false, cu2, a0, a1, b2, tot2);
-                write_final(S, p, p.D - 1, cu2, a0, a1, run + b2);
-                __syncthreads();
-                run += tot2;
-                r += l;
-            }
-        }
         __syncthreads();   // shared state is reused by the next tile
     }
 }
@@ -399,6 +399,7 @@ __global__ void __launch_bounds__(kPlaceThreads) k_place(const TileInfo* __restr
         const int nr = (int)min((long long)kTR, p.R - ra);
         const long long off = tiles[t].count;           // exclusive prefix (k_tile_scan)
         const long long st = tiles[t].stage;
+        long long my_dst = 0;                           // this thread's ray's first final position
         if (threadIdx.x < kTR) {
             const int v = (int)threadIdx.x < nr ? ray_cnt[ra + threadIdx.x] : 0;
             const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -420,13 +421,27 @@ __global__ void __launch_bounds__(kPlaceThreads) k_place(const TileInfo* __restr
                 warp_sums[kTR / 32] = a;
             }
             asm volatile("bar.sync 1, %0;" ::"r"(kTR));
-            if ((int)threadIdx.x < nr) ray_offsets[ra + threadIdx.x] = (int32_t)(off + warp_sums[warp] + incl - v);
+            my_dst = off + warp_sums[warp] + incl - v;
+            if ((int)threadIdx.x < nr) ray_offsets[ra + threadIdx.x] = (int32_t)my_dst;
         }
         __syncthreads();
         // staged entries -> final positions (within both capacities: the
         // status checked above covers the staging list and H <= hit_cap)
         const int cnt = warp_sums[kTR / 32];
         if (t == p.ntiles - 1 && threadIdx.x == 0) ray_offsets[p.R] = (int32_t)(off + cnt);
+        if (st < 0) {
+            // staged per sub-range: each ray's entries from its own first slot
+            if ((int)threadIdx.x < nr) {
+                const int32_t n = ray_cnt[ra + threadIdx.x];
+                const long long src = p.ray_src[ra + threadIdx.x];
+                for (int i = 0; i < n; ++i) {
+                    voxel_id[my_dst + i] = p.stage_vid[src + i];
+                    t_range[my_dst + i] = p.stage_tr[src + i];
+                }
+            }
+            __syncthreads();
+            continue;
+        }
         for (int i0 = threadIdx.x; i0 < cnt; i0 += 4 * kPlaceThreads) {
             int32_t v[4];
             float2 tr[4];
@@ -479,7 +494,7 @@ using namespace nglod;
 extern "C" size_t svo_trace_rays_workspace(int64_t R, int64_t pair_capacity) {
     if (R < 0 || pair_capacity < 0) return 0;
     return align_up(sizeof(Counters)) + align_up(sizeof(TileInfo) * (size_t)(num_tiles(R) + 1)) +
-           align_up(sizeof(int32_t) * (size_t)(R + 1)) + align_up(sizeof(int32_t) * (size_t)pair_capacity) +
+           2 * align_up(sizeof(int32_t) * (size_t)(R + 1)) + align_up(sizeof(int32_t) * (size_t)pair_capacity) +
            align_up(sizeof(float2) * (size_t)pair_capacity);
 }
 
@@ -496,7 +511,8 @@ int enqueue_traversal(const nglod_svo* svo, const float* o, const float* d, int6
     if (target_lod < 1 || D >= svo->num_depths)
         return fail(NGLOD_ERR_INVALID_ARG, w + ": target_lod outside 1.." +
                                                std::to_string(svo->num_depths - kFirstFeatureDepth));
-    if (R < 0 || R >= (1ll << 31) - 1 || pair_capacity < 0 || hit_capacity < 0)
+    if (R < 0 || R >= (1ll << 31) - 1 || pair_capacity < 0 || pair_capacity >= (1ll << 31) - 1 ||
+        hit_capacity < 0)
         return fail(NGLOD_ERR_INVALID_ARG, w + ": bad R or capacity");
     if (!ray_offsets) return fail(NGLOD_ERR_INVALID_ARG, w + ": NULL ray_offsets");
     if (!work) return fail(NGLOD_ERR_INVALID_ARG, w + ": NULL workspace");
@@ -519,6 +535,8 @@ int enqueue_traversal(const nglod_svo* svo, const float* o, const float* d, int6
     wp += align_up(sizeof(TileInfo) * (size_t)(ntiles + 1));
     int32_t* ray_cnt = (int32_t*)wp;
     wp += align_up(sizeof(int32_t) * (size_t)(R + 1));
+    int32_t* ray_src = (int32_t*)wp;
+    wp += align_up(sizeof(int32_t) * (size_t)(R + 1));
     int32_t* stage_vid = (int32_t*)wp;
     wp += align_up(sizeof(int32_t) * (size_t)pair_capacity);
     float2* stage_tr = (float2*)wp;
@@ -532,6 +550,7 @@ int enqueue_traversal(const nglod_svo* svo, const float* o, const float* d, int6
     p.stage_cap = pair_capacity;
     p.D = D;
     p.ray_cnt = ray_cnt;
+    p.ray_src = ray_src;
     p.stage_vid = stage_vid;
     p.stage_tr = stage_tr;
     p.tiles = tiles;
