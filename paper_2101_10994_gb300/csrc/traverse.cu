@@ -37,6 +37,7 @@ namespace nglod {
 namespace {
 
 constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
 constexpr int kTR = 128;                 // rays per tile
 constexpr int kFCap = 4096;              // frontier capacity (pairs) of one buffer
 static_assert(kFCap >= 3 * (1 << (kMaxDepth - 1)), "one ray's frontier must fit");
@@ -82,6 +83,8 @@ struct TileSmem {
     int ray_cnt[kTR];                  // entries per ray at the target depth
     long long lvl[kMaxDepth + 2];      // level sizes of the current pass
     int warp_sums[kThreads / 32 + 1];
+    int wtot[kThreads / 32];           // per-warp totals of a level ...
+    int wbase[kThreads / 32 + 1];      // ... their exclusive prefix and sum
     long long tile;
     long long stage;
     uint8_t rank_lut[8 * 256];         // rank_mask(m, oct) at [oct * 256 + m]
@@ -140,109 +143,161 @@ __device__ __forceinline__ RayPrep prep_ray(const float* o, const float* d, long
     return p;
 }
 
+// The pairs [0, n) of a level are split into kWarps contiguous ranges, one
+// per warp; lane l of a warp takes pairs w0 + 32 j + l (rows of 32), so
+// neighbouring lanes read neighbouring shared-memory words and write
+// neighbouring outputs, and a warp-wide scan per row keeps every output in
+// pair order.
+__device__ __forceinline__ void warp_range(int n, int& w0, int& w1) {
+    const int q = (n + kWarps - 1) / kWarps;
+    w0 = min((int)(threadIdx.x >> 5) * q, n);
+    w1 = min(w0 + q, n);
+}
+
+__device__ __forceinline__ int warp_incl_scan(int v, int lane) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += y;
+    }
+    return v;
+}
+
+// S.wbase[w] = exclusive prefix of the warps' totals; returns the sum.
+__device__ __forceinline__ int warp_bases(TileSmem& S, int wsum) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) S.wtot[warp] = wsum;
+    __syncthreads();
+    if (warp == 0) {
+        const int v = lane < kWarps ? S.wtot[lane] : 0;
+        const int incl = warp_incl_scan(v, lane);
+        if (lane < kWarps) S.wbase[lane] = incl - v;
+        if (lane == kWarps - 1) S.wbase[kWarps] = incl;
+    }
+    __syncthreads();
+    return S.wbase[kWarps];
+}
+
 // Decide at depth dp for the n pairs of frontier buffer `cur`: each pair's
 // occupied children are slab-tested (all 8 from the 3 shared plane crossings
-// per axis) and recorded by front-to-back rank.  Thread t owns the pairs
-// [c0, c1) (contiguous, so the block scan keeps list order); `base` is its
-// first output position.  Returns the number of children hit.
-__device__ __forceinline__ int decide(TileSmem& S, const TileParams& p, int dp, int cur, int n, bool per_ray,
-                                      int& c0, int& c1, int& base) {
-    const int k = (n + kThreads - 1) / kThreads;
-    c0 = min((int)threadIdx.x * k, n);
-    c1 = min(c0 + k, n);
-    int cnt = 0;
+// per axis) and recorded by front-to-back rank in S.rec (hit ranks | origin
+// octant << 8).  Returns the number of children hit; S.wbase holds each
+// warp's first output position.
+__device__ __forceinline__ int decide(TileSmem& S, const TileParams& p, int dp, int cur, int n) {
+    const int lane = threadIdx.x & 31;
+    int w0, w1;
+    warp_range(n, w0, w1);
     const Node* nodes = p.nt.node[dp];
-    for (int i0 = c0; i0 < c1; i0 += 4) {
-        // the next four pairs' nodes are loaded together, then decided one
-        // after the other (one copy of the decision code)
-        Node nd0 = nodes[S.vox[cur][i0]];
-        Node nd1 = nodes[S.vox[cur][min(i0 + 1, c1 - 1)]];
-        Node nd2 = nodes[S.vox[cur][min(i0 + 2, c1 - 1)]];
-        Node nd3 = nodes[S.vox[cur][min(i0 + 3, c1 - 1)]];
-        const int iend = min(i0 + 4, c1);
-#pragma unroll 1
-        for (int i = i0; i < iend; ++i) {
-            const int rl = S.rl[cur][i];
-            const RayPrep ray = S.ray[rl];
-            uint32_t o8, h = 0;
+    int cnt = 0;
+    for (int rb = w0; rb < w1; rb += 32) {
+        const int i = rb + lane;
+        if (i < w1) {
+            const Node nd = nodes[S.vox[cur][i]];
+            const RayPrep ray = S.ray[S.rl[cur][i]];
+            uint32_t o8 = 0, h = 0;
             bool live = true;
             if (dp == 0) {
                 float t0, t1;   // the root is the only undecided input
-                live = ray.valid && slab_test(ray, nd0.ijk, 0, t0, t1, &o8);
+                live = ray.valid && slab_test(ray, nd.ijk, 0, t0, t1, &o8);
             }
-            if (live && nd0.childmask) {
-                const uint32_t hs = child_hits8<false>(ray, nd0.ijk, dp, o8);
-                h = S.rank_lut[(o8 << 8) | (hs & nd0.childmask)];
-            } else if (dp != 0) {
-                o8 = origin_octant(ray, nd0.ijk, dp);
+            if (live && nd.childmask) {
+                const uint32_t hs = child_hits8<false>(ray, nd.ijk, dp, o8);
+                h = S.rank_lut[(o8 << 8) | (hs & nd.childmask)];
             }
-            S.rec[i] = (uint16_t)(h | (live ? (o8 << 8) : 0u));
+            // (the octant is read only where a child was hit)
+            S.rec[i] = (uint16_t)(h | (o8 << 8));
             cnt += __popc(h);
-            if (per_ray && h) atomicAdd(&S.ray_cnt[rl], __popc(h));
-            nd0 = nd1;
-            nd1 = nd2;
-            nd2 = nd3;
         }
     }
-    int total;
-    base = block_exclusive_sum(cnt, S.warp_sums, total);
-    return total;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    return warp_bases(S, cnt);
 }
 
-// Subdivide: the hit children of the owned pairs, front to back, into `nxt`.
-__device__ __forceinline__ void subdivide(TileSmem& S, const TileParams& p, int dp, int cur, int c0, int c1,
-                                          int base) {
+// Subdivide: the hit children of the n pairs, front to back, into `cur ^ 1`.
+__device__ __forceinline__ void subdivide(TileSmem& S, const TileParams& p, int dp, int cur, int n) {
+    const int lane = threadIdx.x & 31;
+    int w0, w1;
+    warp_range(n, w0, w1);
     const Node* nodes = p.nt.node[dp];
-    int pos = base;
-    for (int i = c0; i < c1; ++i) {
-        const uint32_t h0 = S.rec[i] & 0xffu;
-        if (!h0) continue;
-        const Node nd = nodes[S.vox[cur][i]];
-        const uint32_t o8 = S.rec[i] >> 8;
-        const uint8_t rl = S.rl[cur][i];
-        for (uint32_t h = h0; h; h &= h - 1u) {
-            const uint32_t c = (uint32_t)(__ffs(h) - 1) ^ o8;
-            S.vox[cur ^ 1][pos] = nd.childbase + __popc(nd.childmask & ((1u << c) - 1u));
-            S.rl[cur ^ 1][pos] = rl;
-            ++pos;
-        }
-    }
-}
-
-// Compactify at the target depth: the hit children of the owned pairs with
-// their (t_enter, t_exit), written to their final list positions.
-__device__ __forceinline__ void write_final(TileSmem& S, const TileParams& p, int dp, int cur, int c0, int c1,
-                                            long long pos) {
-    const Node* nodes = p.nt.node[dp];
-    for (int i = c0; i < c1; ++i) {
-        const uint32_t h0 = S.rec[i] & 0xffu;
-        if (!h0) continue;
-        const Node nd = nodes[S.vox[cur][i]];
-        const uint32_t o8 = S.rec[i] >> 8;
-        // the exact (t_enter, t_exit) of the hit children only (about one
-        // per pair at the target depth)
-        ChildSlabs cs;
-        child_slabs(S.ray[S.rl[cur][i]], nd.ijk, dp, cs);
-        for (uint32_t h = h0; h; h &= h - 1u) {
-            const uint32_t c = (uint32_t)(__ffs(h) - 1) ^ o8;
-            float a0 = 0.f, a1 = 0.f;
-            child_hit(cs, c, a0, a1);
-            if (pos < p.stage_cap) {
-                p.stage_vid[pos] = nd.childbase + __popc(nd.childmask & ((1u << c) - 1u));
-                p.stage_tr[pos] = make_float2(a0, a1);
+    int run = S.wbase[threadIdx.x >> 5];
+    for (int rb = w0; rb < w1; rb += 32) {
+        const int i = rb + lane;
+        const uint32_t r = i < w1 ? S.rec[i] : 0u;
+        const uint32_t h0 = r & 0xffu;
+        const int c = __popc(h0);
+        const int incl = warp_incl_scan(c, lane);
+        int pos = run + incl - c;
+        run += __shfl_sync(0xffffffffu, incl, 31);
+        if (h0) {
+            const Node nd = nodes[S.vox[cur][i]];
+            const uint32_t o8 = r >> 8;
+            const uint8_t rl = S.rl[cur][i];
+            for (uint32_t h = h0; h; h &= h - 1u) {
+                const uint32_t cs = (uint32_t)(__ffs(h) - 1) ^ o8;
+                S.vox[cur ^ 1][pos] = nd.childbase + __popc(nd.childmask & ((1u << cs) - 1u));
+                S.rl[cur ^ 1][pos] = rl;
+                ++pos;
             }
-            ++pos;
+        }
+    }
+}
+
+// Compactify at the target depth: the hit children of the n pairs with their
+// (t_enter, t_exit), written to their staging slots from `base` on, and each
+// ray's entry count added to S.ray_cnt (pairs are grouped by ray, so the
+// last lane of each run of one ray in a row adds the run's sum).
+__device__ __forceinline__ void write_final(TileSmem& S, const TileParams& p, int dp, int cur, int n,
+                                            long long base) {
+    const int lane = threadIdx.x & 31;
+    int w0, w1;
+    warp_range(n, w0, w1);
+    const Node* nodes = p.nt.node[dp];
+    long long run = base + S.wbase[threadIdx.x >> 5];
+    for (int rb = w0; rb < w1; rb += 32) {
+        const int i = rb + lane;
+        const bool valid = i < w1;
+        const uint32_t r = valid ? S.rec[i] : 0u;
+        const int rl = valid ? (int)S.rl[cur][i] : -1;
+        const uint32_t h0 = r & 0xffu;
+        const int c = __popc(h0);
+        const int incl = warp_incl_scan(c, lane);
+        long long pos = run + incl - c;
+        run += __shfl_sync(0xffffffffu, incl, 31);
+        // runs of equal rays in the row: heads, and each lane's run head
+        const int rl_prev = __shfl_up_sync(0xffffffffu, rl, 1);
+        const int rl_next = __shfl_down_sync(0xffffffffu, rl, 1);
+        const unsigned heads = __ballot_sync(0xffffffffu, lane == 0 || rl_prev != rl);
+        const int head = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
+        const int excl_head = __shfl_sync(0xffffffffu, incl - c, head);
+        if (valid && (lane == 31 || rl_next != rl) && incl > excl_head) atomicAdd(&S.ray_cnt[rl], incl - excl_head);
+        if (h0) {
+            const Node nd = nodes[S.vox[cur][i]];
+            const uint32_t o8 = r >> 8;
+            // the exact (t_enter, t_exit) of the hit children only (about one
+            // per pair at the target depth)
+            ChildSlabs cs;
+            child_slabs(S.ray[rl], nd.ijk, dp, cs);
+            for (uint32_t h = h0; h; h &= h - 1u) {
+                const uint32_t cc = (uint32_t)(__ffs(h) - 1) ^ o8;
+                float a0 = 0.f, a1 = 0.f;
+                child_hit(cs, cc, a0, a1);
+                if (pos < p.stage_cap) {
+                    p.stage_vid[pos] = nd.childbase + __popc(nd.childmask & ((1u << cc) - 1u));
+                    p.stage_tr[pos] = make_float2(a0, a1);
+                }
+                ++pos;
+            }
         }
     }
 }
 
 // Levels 0..D-1 for the tile-local rays [r0, r0 + nr).  Returns false if a
 // frontier would exceed kFCap (block-uniform).  On success the target
-// depth's decisions stay in S.rec with the thread's chunk [c0, c1) and
-// output base, and `total` is the number of entries; S.lvl holds the level
-// sizes of this pass.
-__device__ bool run_levels(TileSmem& S, const TileParams& p, int r0, int nr, bool per_ray, int& cur, int& c0,
-                           int& c1, int& base, int& total) {
+// depth's decisions stay in S.rec over the nfin pairs of frontier buffer
+// `cur` (S.wbase: each warp's first output), and `total` is the number of
+// entries; S.lvl holds the level sizes of this pass.
+__device__ bool run_levels(TileSmem& S, const TileParams& p, int r0, int nr, int& cur, int& nfin, int& total) {
     for (int i = threadIdx.x; i < nr; i += kThreads) {
         S.vox[0][i] = 0;
         S.rl[0][i] = (uint8_t)(r0 + i);
@@ -253,15 +308,16 @@ __device__ bool run_levels(TileSmem& S, const TileParams& p, int r0, int nr, boo
     int n = nr;
     for (int dp = 0; dp < p.D; ++dp) {
         const bool fin = dp + 1 == p.D;
-        total = decide(S, p, dp, cur, n, fin && per_ray, c0, c1, base);
+        total = decide(S, p, dp, cur, n);
         if (threadIdx.x == 0) S.lvl[dp + 1] = total;
         if (fin) break;
         if (total > kFCap) return false;
-        subdivide(S, p, dp, cur, c0, c1, base);
+        subdivide(S, p, dp, cur, n);
         __syncthreads();
         cur ^= 1;
         n = total;
     }
+    nfin = n;
     __syncthreads();
     return true;
 }
@@ -298,14 +354,14 @@ __global__ void __launch_bounds__(kThreads, 4) k_traverse(const TileParams p) {
             S.ray_cnt[i] = 0;
         }
         __syncthreads();
-        int cur, c0, c1, base, total;
-        const bool whole = run_levels(S, p, 0, nr, true, cur, c0, c1, base, total);
+        int cur, nfin, total;
+        const bool whole = run_levels(S, p, 0, nr, cur, nfin, total);
         if (whole) {
             commit_levels(S, p);
             reserve_stage(S, p, total);
             if (threadIdx.x == 0) p.tiles[t] = TileInfo{S.stage, (long long)total};
             __syncthreads();
-            write_final(S, p, p.D - 1, cur, c0, c1, S.stage + base);
+            write_final(S, p, p.D - 1, cur, nfin, S.stage);
         } else {
             // halve until every sub-range fits; each sub-range reserves its
             // own staging slots and writes its entries at once (each ray's
@@ -314,15 +370,16 @@ __global__ void __launch_bounds__(kThreads, 4) k_traverse(const TileParams p) {
             int r = 0, len = nr / 2;
             while (r < nr) {
                 const int l = min(len, nr - r);
-                int cu2, a0, a1, b2, tot2;
-                if (!run_levels(S, p, r, l, true, cu2, a0, a1, b2, tot2)) {
+                int cu2, nf2, tot2;
+                if (!run_levels(S, p, r, l, cu2, nf2, tot2)) {
                     len = max(1, l / 2);
                     continue;
                 }
                 commit_levels(S, p);
                 reserve_stage(S, p, tot2);
                 __syncthreads();
-                write_final(S, p, p.D - 1, cu2, a0, a1, S.stage + b2);
+                write_final(S, p, p.D - 1, cu2, nf2, S.stage);
+                __syncthreads();           // the sub-range's per-ray counts are complete
                 const int j = (int)threadIdx.x;
                 int sum;
                 const int pre = block_exclusive_sum(j < l ? S.ray_cnt[r + j] : 0, S.warp_sums, sum);
@@ -335,6 +392,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_traverse(const TileParams p) {
             }
             if (threadIdx.x == 0) p.tiles[t] = TileInfo{-1, tile_total};
         }
+        __syncthreads();                   // per-ray counts complete
         if ((int)threadIdx.x < nr) p.ray_cnt[ra + threadIdx.x] = S.ray_cnt[threadIdx.x];
         __syncthreads();   // shared state is reused by the next tile
     }
