@@ -451,6 +451,8 @@ __global__ void __launch_bounds__(kPlaceThreads) k_place(const TileInfo* __restr
                                                         int32_t* __restrict__ ray_offsets,
                                                         int32_t* __restrict__ voxel_id, float2* __restrict__ t_range) {
     __shared__ int warp_sums[kTR / 32 + 1];
+    __shared__ int ray_pre[kTR + 1];                // sub-range tiles: each ray's first entry in the tile
+    __shared__ int32_t ray_from[kTR];               // ... and its first staging slot
     if (p.ctr->status != kStatusOk) return;
     for (long long t = blockIdx.x; t < p.ntiles; t += gridDim.x) {
         const long long ra = t * kTR;
@@ -488,14 +490,25 @@ __global__ void __launch_bounds__(kPlaceThreads) k_place(const TileInfo* __restr
         const int cnt = warp_sums[kTR / 32];
         if (t == p.ntiles - 1 && threadIdx.x == 0) ray_offsets[p.R] = (int32_t)(off + cnt);
         if (st < 0) {
-            // staged per sub-range: each ray's entries from its own first slot
-            if ((int)threadIdx.x < nr) {
-                const int32_t n = ray_cnt[ra + threadIdx.x];
-                const long long src = p.ray_src[ra + threadIdx.x];
-                for (int i = 0; i < n; ++i) {
-                    voxel_id[my_dst + i] = p.stage_vid[src + i];
-                    t_range[my_dst + i] = p.stage_tr[src + i];
+            // staged per sub-range: entry e of the tile belongs to the ray j
+            // with ray_pre[j] <= e < ray_pre[j + 1] and sits at staging slot
+            // ray_from[j] + e - ray_pre[j]; the threads take consecutive
+            // entries (coalesced writes), each finding its ray by bisection
+            if ((int)threadIdx.x < kTR) {
+                ray_pre[threadIdx.x] = (int)threadIdx.x < nr ? (int)(my_dst - off) : cnt;
+                ray_from[threadIdx.x] = (int)threadIdx.x < nr ? p.ray_src[ra + threadIdx.x] : 0;
+            }
+            if (threadIdx.x == 0) ray_pre[kTR] = cnt;
+            __syncthreads();
+            for (int e = threadIdx.x; e < cnt; e += kPlaceThreads) {
+                int lo = 0, hi = nr - 1;          // the last ray j with ray_pre[j] <= e
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (ray_pre[mid] <= e) lo = mid; else hi = mid - 1;
                 }
+                const long long src = (long long)ray_from[lo] + (e - ray_pre[lo]);
+                voxel_id[off + e] = p.stage_vid[src];
+                t_range[off + e] = p.stage_tr[src];
             }
             __syncthreads();
             continue;
