@@ -321,11 +321,12 @@ def run_ours(args, rank, world, local_rank):
         ms_seq = ms_step
         ms_step = max_over_ranks(sum(a.elapsed_time(b) for a, b in fev), dev) / args.steps
         assert torch.equal(fr.out["t"], out["t"]) and torch.equal(fr.out["normal"], out["normal"])
-        chunks, ctas = len(fr.chunks), fr.ctas_per_sm
-        configs[mode] = (chunks, ctas)
+        chunks, ctas, tctas = len(fr.chunks), fr.ctas_per_sm, fr.trav_ctas_per_sm
+        configs[mode] = (chunks, ctas, tctas)
         del fr
-        results[mode] = dict(level_sizes=sizes, chunks=chunks, trace_ctas_per_sm=ctas,
-            schedule=f"{chunks} ray chunks on {chunks} streams, trace CTAs/SM {ctas or 'max'} (autotuned)",
+        results[mode] = dict(level_sizes=sizes, chunks=chunks, trace_ctas_per_sm=ctas, traversal_ctas_per_sm=tctas,
+            schedule=f"{chunks} ray chunks on {chunks} streams, trace CTAs/SM {ctas or 'max'}, traversal "
+                     f"CTAs/SM {tctas or 'max'} (autotuned)",
             autotune_ms_by_chunks_and_ctas=tune,
             ms_sequential=ms_seq, rays_per_s_sequential=job_rate(R, world, ms_seq * 1e-3),
             ms_per_step=ms_step, rays_per_s=job_rate(R, world, ms_step * 1e-3),
@@ -356,6 +357,7 @@ def run_ours(args, rank, world, local_rank):
         ms = max_over_ranks(statistics.mean(bl), dev)
         bch = len(fr.chunks)
         results["bf16_blend"] = dict(lod_tilde=lt, chunks=bch, trace_ctas_per_sm=fr.ctas_per_sm,
+                                     traversal_ctas_per_sm=fr.trav_ctas_per_sm,
                                      schedule=f"{bch} ray chunks on {bch} streams, trace CTAs/SM "
                                               f"{fr.ctas_per_sm or 'max'} (autotuned)",
                                      autotune_ms_by_chunks_and_ctas=btune,
@@ -387,7 +389,8 @@ def run_ours(args, rank, world, local_rank):
     if "bf16" in modes and not summed:
         f16 = ng.Features(W["feats"], "f16")
         fr = FrameRenderer(svo, f16, dec, o, d, W["lod"], chunks=configs["bf16"][0], ctas_per_sm=configs["bf16"][1],
-                           eps=W["eps"], far=W["far"], max_steps=W["max_steps"], decode="bf16", normals=True)
+                           trav_ctas_per_sm=configs["bf16"][2], eps=W["eps"], far=W["far"],
+                           max_steps=W["max_steps"], decode="bf16", normals=True)
         hl = []
         for k in range(args.warmup + args.steps):
             flush.zero_()
@@ -456,7 +459,8 @@ def run_ours(args, rank, world, local_rank):
         sch = len(fr.chunks)
         q = int(sout["steps"].sum().item())
         results[f"{sm_mode}_summed"] = dict(
-            chunks=sch, trace_ctas_per_sm=fr.ctas_per_sm, autotune_ms_by_chunks_and_ctas=stune,
+            chunks=sch, trace_ctas_per_sm=fr.ctas_per_sm, traversal_ctas_per_sm=fr.trav_ctas_per_sm,
+            autotune_ms_by_chunks_and_ctas=stune,
             schedule=f"{sch} ray chunks on {sch} streams, trace CTAs/SM {fr.ctas_per_sm or 'max'} (autotuned)",
             ms_per_step=ms, rays_per_s=job_rate(R, world, ms * 1e-3),
             ms_traverse=float(st_ms[0]), ms_trace=float(st_ms[1]), ms_normals=float(st_ms[2]),
@@ -478,9 +482,10 @@ def run_ours(args, rank, world, local_rank):
              "normal": torch.empty((R, 3), dtype=torch.float32).pin_memory()}
     # the renderer sizes its lists from the rays it is built on; every timed frame then
     # brings its rays in from the host buffers (the device copies are cleared first)
-    ech, ecta = configs[mode]
-    fr = FrameRenderer(svo, feats, dec, o.clone(), d.clone(), W["lod"], chunks=ech, ctas_per_sm=ecta, eps=W["eps"],
-                       far=W["far"], max_steps=W["max_steps"], decode=mode, normals=True)
+    ech, ecta, etcta = configs[mode]
+    fr = FrameRenderer(svo, feats, dec, o.clone(), d.clone(), W["lod"], chunks=ech, ctas_per_sm=ecta,
+                       trav_ctas_per_sm=etcta, eps=W["eps"], far=W["far"], max_steps=W["max_steps"], decode=mode,
+                       normals=True)
     e2e_ms = []
     for k in range(args.warmup + args.steps):
         flush.zero_()

@@ -287,6 +287,19 @@ int svo_trace_rays_async(const nglod_svo* svo, const float* o, const float* d, i
                          int32_t* ray_offsets, int32_t* voxel_id, float* t_range,
                          int64_t hit_capacity, void* stream);
 
+/* svo_trace_rays_async_width -- svo_trace_rays_async with the persistent
+ * traversal kernel launched at ctas_per_sm resident CTAs per SM (1..4; 0:
+ * the most that fit, as svo_trace_rays_async).  A traversal CTA holds ~56 KB
+ * of shared memory, so at the full width no tracer CTA of a concurrent
+ * stream fits beside it; a narrower traversal leaves room on every SM for
+ * another stream's sphere trace (the frame renderer tunes this).  Changes
+ * only the schedule: the lists are identical.  NGLOD_ERR_INVALID_ARG for
+ * ctas_per_sm outside 0..4; otherwise as svo_trace_rays_async. */
+int svo_trace_rays_async_width(const nglod_svo* svo, const float* o, const float* d, int64_t R,
+                               int target_lod, void* work, size_t work_bytes, int64_t pair_capacity,
+                               int32_t* ray_offsets, int32_t* voxel_id, float* t_range,
+                               int64_t hit_capacity, int ctas_per_sm, void* stream);
+
 /* svo_trace_rays_check -- synchronises and reports the status of the last
  * traversal enqueued in this workspace (as svo_trace_rays would have): OK,
  * NGLOD_ERR_CAPACITY (h_stats = sizes needed) or NGLOD_ERR_TIMEOUT. */

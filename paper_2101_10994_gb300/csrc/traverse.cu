@@ -575,7 +575,7 @@ namespace {
 // Enqueues the whole traversal on the stream (no host synchronisation).
 int enqueue_traversal(const nglod_svo* svo, const float* o, const float* d, int64_t R, int target_lod, void* work,
                       size_t work_bytes, int64_t pair_capacity, int32_t* ray_offsets, int32_t* voxel_id,
-                      float* t_range, int64_t hit_capacity, cudaStream_t st, const char* who) {
+                      float* t_range, int64_t hit_capacity, cudaStream_t st, const char* who, int ctas_per_sm = 0) {
     const std::string w(who);
     if (!svo) return fail(NGLOD_ERR_INVALID_ARG, w + ": NULL octree");
     const int D = target_lod + kFirstFeatureDepth - 1;
@@ -627,7 +627,8 @@ int enqueue_traversal(const nglod_svo* svo, const float* o, const float* d, int6
     p.tiles = tiles;
     p.ctr = ctr;
     const int sms = svo->num_sms;
-    const long long grid = std::min<long long>(ntiles, (long long)sms * traverse_ctas_per_sm());
+    const int occ = traverse_ctas_per_sm();
+    const long long grid = std::min<long long>(ntiles, (long long)sms * (ctas_per_sm > 0 ? std::min(ctas_per_sm, occ) : occ));
     k_traverse<<<(unsigned)grid, kThreads, sizeof(TileSmem), st>>>(p);
     k_tile_scan<<<1, kScanThreads, 0, st>>>(tiles, ntiles, ctr, hit_capacity, D);
     k_place<<<(unsigned)std::min<long long>(ntiles, (long long)sms * 8), kPlaceThreads, 0, st>>>(
@@ -676,6 +677,16 @@ extern "C" int svo_trace_rays_async(const nglod_svo* svo, const float* o, const 
                                     int32_t* voxel_id, float* t_range, int64_t hit_capacity, void* stream) {
     return enqueue_traversal(svo, o, d, R, target_lod, work, work_bytes, pair_capacity, ray_offsets, voxel_id,
                              t_range, hit_capacity, (cudaStream_t)stream, "svo_trace_rays_async");
+}
+
+extern "C" int svo_trace_rays_async_width(const nglod_svo* svo, const float* o, const float* d, int64_t R,
+                                          int target_lod, void* work, size_t work_bytes, int64_t pair_capacity,
+                                          int32_t* ray_offsets, int32_t* voxel_id, float* t_range,
+                                          int64_t hit_capacity, int ctas_per_sm, void* stream) {
+    if (ctas_per_sm < 0 || ctas_per_sm > 4)
+        return fail(NGLOD_ERR_INVALID_ARG, "svo_trace_rays_async_width: ctas_per_sm must lie in 0..4");
+    return enqueue_traversal(svo, o, d, R, target_lod, work, work_bytes, pair_capacity, ray_offsets, voxel_id,
+                             t_range, hit_capacity, (cudaStream_t)stream, "svo_trace_rays_async_width", ctas_per_sm);
 }
 
 extern "C" int svo_trace_rays_check(const void* work, int target_lod, int64_t* h_stats, void* stream) {

@@ -22,9 +22,13 @@ class FrameRenderer:
     def __init__(self, svo: ng.SVO, feats: ng.Features, dec: ng.DecoderDev, o, d, lod, chunks: int = 2,
                  eps: float = 1e-3, far: float = 5.0, max_steps: int = 128, decode: str = "bf16",
                  normals: bool = True, headroom: float = 1.25, dec_hi: ng.DecoderDev | None = None,
-                 normal_mode: str = "analytic", fd_h: float = 1e-3, ctas_per_sm: int = 0):
+                 normal_mode: str = "analytic", fd_h: float = 1e-3, ctas_per_sm: int = 0,
+                 trav_ctas_per_sm: int = 0):
         """lod: an integer LOD, or a continuous L~ (Eq. 3) with dec = LOD floor(L~)'s decoder and
-        dec_hi = LOD floor(L~) + 1's; rays then walk their lists at ceil(L~)."""
+        dec_hi = LOD floor(L~) + 1's; rays then walk their lists at ceil(L~).
+        ctas_per_sm / trav_ctas_per_sm: resident CTAs per SM of the persistent trace / traversal
+        kernels (0: the most that fit); narrower launches leave room on each SM for the other
+        chunks' kernels."""
         import torch
         self.torch = torch
         self.lod_tilde = float(lod)
@@ -39,6 +43,7 @@ class FrameRenderer:
         self.eps, self.far, self.max_steps, self.decode, self.normals = eps, far, max_steps, decode, normals
         self.nopt = dict(normal_mode=normal_mode, fd_h=fd_h)
         self.ctas_per_sm = int(ctas_per_sm)
+        self.trav_ctas_per_sm = int(trav_ctas_per_sm)
         dev = self.o.device
         # chunk bounds on multiples of 128 rays (the traversal's tile)
         n = max(1, int(chunks))
@@ -72,10 +77,10 @@ class FrameRenderer:
         st = c["stream"]
         rs, re_ = c["rs"], c["rs"] + c["n"]
         oo, dd = self.o[rs:re_], self.d[rs:re_]
-        ng._check(L.svo_trace_rays_async(self.svo.h, oo.data_ptr(), dd.data_ptr(), c["n"], self.lod,
-                                         c["twork"].data_ptr(), c["twork"].numel(), c["cap"], c["offs"].data_ptr(),
-                                         c["vid"].data_ptr(), c["tr"].data_ptr(), c["cap"],
-                                         C.c_void_p(st.cuda_stream)))
+        ng._check(L.svo_trace_rays_async_width(self.svo.h, oo.data_ptr(), dd.data_ptr(), c["n"], self.lod,
+                                               c["twork"].data_ptr(), c["twork"].numel(), c["cap"],
+                                               c["offs"].data_ptr(), c["vid"].data_ptr(), c["tr"].data_ptr(), c["cap"],
+                                               self.trav_ctas_per_sm, C.c_void_p(st.cuda_stream)))
         if self.blend:
             ng.sphere_trace_blend(self.svo, self.feats, self.dec, self.dec_hi, oo, dd, c["lists"], self.lod_tilde,
                                   eps=self.eps, far=self.far, max_steps=self.max_steps, decode=self.decode,
@@ -122,32 +127,35 @@ class FrameRenderer:
 
 
 def autotune_frame(svo: ng.SVO, feats: ng.Features, dec: ng.DecoderDev, o, d, lod, chunk_counts=(1, 2, 3, 4),
-                   ctas=(0, 3, 2), reps: int = 5, **kw):
+                   ctas=(0, 3, 2), trav_ctas=(0, 2), reps: int = 5, **kw):
     """Times the frame renderer on these rays for every (chunk count, trace
-    CTAs per SM) pair -- fewer trace CTAs per SM leave room for the other
-    chunks' traversal and normals on the same SMs -- and returns the fastest
-    renderer with the timings (ms per frame, keyed "chunks/ctas")."""
+    CTAs per SM, traversal CTAs per SM) triple -- narrower persistent
+    launches leave room on each SM for the other chunks' kernels, so the
+    chunks' stages share SMs instead of taking turns -- and returns the
+    fastest renderer with the timings (ms per frame, keyed
+    "chunks/trace ctas" for the widest traversal, "chunks/trace ctas/t<n>"
+    for a traversal of n CTAs per SM)."""
     import torch
     timings, best, best_ms = {}, None, float("inf")
-    for n in chunk_counts:
-        for c in ctas:
-            fr = FrameRenderer(svo, feats, dec, o, d, lod, chunks=n, ctas_per_sm=c, **kw)
-            for _ in range(2):
-                fr.frame()
-            fr.check()
-            ts = []
-            for _ in range(reps):
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record()
-                fr.frame()
-                e1.record()
-                e1.synchronize()
-                ts.append(e0.elapsed_time(e1))
-            fr.check()
-            ms = sorted(ts)[len(ts) // 2]
-            timings[f"{n}/{c}"] = ms
-            if ms < best_ms:
-                best, best_ms = fr, ms
-            else:
-                del fr
+    configs = [(n, c, t) for n in chunk_counts for c in ctas for t in (trav_ctas if n > 1 else (0,))]
+    for n, c, t in configs:
+        fr = FrameRenderer(svo, feats, dec, o, d, lod, chunks=n, ctas_per_sm=c, trav_ctas_per_sm=t, **kw)
+        for _ in range(2):
+            fr.frame()
+        fr.check()
+        ts = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fr.frame()
+            e1.record()
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        fr.check()
+        ms = sorted(ts)[len(ts) // 2]
+        timings[f"{n}/{c}/t{t}" if t else f"{n}/{c}"] = ms
+        if ms < best_ms:
+            best, best_ms = fr, ms
+        else:
+            del fr
     return best, timings

@@ -32,7 +32,7 @@ EXPORTS = ["nglod_last_error", "svo_build", "svo_info", "svo_device_arrays", "sv
            "sphere_trace_batch_create", "sphere_trace_batch_run", "sphere_trace_batch_status",
            "sphere_trace_batch_free", "sdf_query_blend", "sphere_trace_blend", "nglod_lod_select",
            "trace_normals_fd", "sdf_backward_bf16", "sdf_l2_backward_bf16", "nglod_sort_points_workspace",
-           "nglod_sort_points", "nglod_sum_features", "nglod_set_wait_polls",
+           "nglod_sort_points", "nglod_sum_features", "nglod_set_wait_polls", "svo_trace_rays_async_width",
            # measurement probes (include/nglod_probe.h)
            "nglod_probe_l2_read", "nglod_probe_l1_read", "nglod_probe_ffma", "nglod_device_sms"]
 
@@ -109,6 +109,7 @@ def lib():
         L.nglod_sum_features.argtypes = [P, P, i32, P, P]
         L.svo_trace_rays_async.argtypes = [P, P, P, i64, i32, P, sz, i64, P, P, P, i64, P]
         L.svo_trace_rays_check.argtypes = [P, i32, P, P]
+        L.svo_trace_rays_async_width.argtypes = [P, P, P, i64, i32, P, sz, i64, P, P, P, i64, i32, P]
         L.sphere_trace_batch_create.argtypes = [P, i32, P, i32, P, P]
         L.sphere_trace_batch_run.argtypes = [P, P]
         L.sphere_trace_batch_status.argtypes = [P, P]

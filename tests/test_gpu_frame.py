@@ -30,6 +30,18 @@ def test_chunked_frame_equals_single_pass(ng, decode, chunks):
         fr.check()
         for k in ("t", "hit", "steps", "normal"):
             assert torch.equal(fr.out[k], ref[k]), k
+    # narrower traversal and trace launches change only the schedule
+    fn = FrameRenderer(svo, F, D, to, td, 5, chunks=chunks, decode=decode, ctas_per_sm=2, trav_ctas_per_sm=1)
+    fn.frame()
+    fn.check()
+    for k in ("t", "hit", "steps", "normal"):
+        assert torch.equal(fn.out[k], ref[k]), k
+    for c in fn.chunks:                    # and the lists are those of svo_trace_rays
+        n = c["n"]
+        L = ng.svo_trace_rays(svo, to[c["rs"]:c["rs"] + n], td[c["rs"]:c["rs"] + n], 5)
+        H = L.voxel_id.numel()
+        assert torch.equal(c["offs"], L.ray_offsets) and torch.equal(c["vid"][:H], L.voxel_id)
+        assert torch.equal(c["tr"][:H].view(torch.int32), L.t_range.view(torch.int32))
     # rays and results through pinned host buffers, copied chunk by chunk
     h_in = (torch.from_numpy(o).pin_memory(), torch.from_numpy(d).pin_memory())
     h_out = {"t": torch.empty(len(o)).pin_memory(), "hit": torch.empty(len(o), dtype=torch.uint8).pin_memory(),
@@ -82,7 +94,7 @@ def test_trace_width_and_frame_autotune(ng, decode):
         ng.sphere_trace(svo, F, D, to, td, lists, decode=decode, ctas_per_sm=5)
     assert e.value.code == ng.ERR_INVALID_ARG
     fr, timings = autotune_frame(svo, F, D, to, td, 5, chunk_counts=(1, 2), ctas=(0, 2), reps=2, decode=decode)
-    assert set(timings) == {"1/0", "1/2", "2/0", "2/2"}
+    assert set(timings) == {"1/0", "1/2", "2/0", "2/2", "2/0/t2", "2/2/t2"}
     fr.frame()
     fr.check()
     for k in ("t", "hit", "steps", "normal"):

@@ -125,3 +125,23 @@ def test_dense_grid_frontier_overflow_path(ng, oracle_mod):
     assert_same_lists(g, ora.trace_rays(o, d, 4))
     sizes = g[3].level_sizes()
     assert sizes[-1] == len(g[1]) and sizes[0] == n
+
+
+def test_async_width_rejects_bad_width(ng):
+    import ctypes as C
+    sc, oc = S.plain_sphere(3)
+    svo = ng.svo_build(oc.keys)
+    o, d, _ = S.camera_rays(16, 16)
+    to, td = torch.from_numpy(o).cuda(), torch.from_numpy(d).cuda()
+    L = ng.lib()
+    R, cap = len(o), 1 << 14
+    work = torch.empty(L.svo_trace_rays_workspace(R, cap), dtype=torch.uint8, device="cuda")
+    offs = torch.empty(R + 1, dtype=torch.int32, device="cuda")
+    vid = torch.empty(cap, dtype=torch.int32, device="cuda")
+    tr = torch.empty((cap, 2), dtype=torch.float32, device="cuda")
+    for w in (-1, 5):
+        rc = L.svo_trace_rays_async_width(svo.h, to.data_ptr(), td.data_ptr(), R, 3, work.data_ptr(), work.numel(),
+                                          cap, offs.data_ptr(), vid.data_ptr(), tr.data_ptr(), cap, w,
+                                          C.c_void_p(torch.cuda.current_stream().cuda_stream))
+        assert rc == ng.ERR_INVALID_ARG
+    svo.free()
