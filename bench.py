@@ -575,7 +575,7 @@ def traversal_roofline(W, res, mode, peaks):
             "lower_bound_bytes": lower, "lower_bound_frac": lower / sec / 1e9 / hbm,
             "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in peaks else "fallback",
             "timing": "CUDA events around svo_trace_rays (3 launches + the H read-back)",
-            "note": "issue-bound on the 8-child slab tests (ncu: ~64 % issue active); node records hit L1/L2"}
+            "note": "issue-bound on the 8-child slab tests (ncu: ~71 % issue active, ALU pipe ~66 %); node records hit L1/L2"}
 
 
 def trace_roofline(W, res, mode, peaks, levels=None, ceilings=None):
