@@ -21,11 +21,14 @@
 // scans keep pairs in (ray, front to back) order, and tiles are placed in
 // ray order.
 //
-// A tile whose frontier would outgrow shared memory at some level is
-// re-run over halves of its rays (recursively); a single ray always fits,
-// since a ray crosses at most 3 * 2^dp - 2 voxels of depth dp.  Each such
-// sub-range stages its entries as soon as its levels are done, and records
-// each ray's first staging slot, so no sub-range is run twice.
+// A tile whose frontier would outgrow shared memory at some depth keeps the
+// last level that fits (already decided) and continues from it in chunks of
+// whole rays, each small enough for the rest of the pool; each chunk stages
+// its entries as soon as its levels are done and records each ray's first
+// staging slot, so nothing above that level is run twice.  A chunk that
+// overflows again further down hands its rays (and the tile's later ones) to
+// runs from the root over halving ray ranges; a single ray always fits,
+// since a ray crosses at most 3 * 2^dp - 2 voxels of depth dp.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -77,8 +80,8 @@ struct TileParams {
 
 struct TileSmem {
     RayPrep ray[kTR];
-    int32_t vox[2][kFCap];             // frontier: voxel ids at the current depth
-    uint8_t rl[2][kFCap];              // ... and the tile-local ray of each pair
+    int32_t vox[2 * kFCap];            // frontier pool: voxel ids ...
+    uint8_t rl[2 * kFCap];             // ... and the tile-local ray of each pair
     uint16_t rec[kFCap];               // decisions: hit children by rank | octant << 8
     int ray_cnt[kTR];                  // entries per ray at the target depth
     long long lvl[kMaxDepth + 2];      // level sizes of the current pass
@@ -87,8 +90,16 @@ struct TileSmem {
     int wbase[kThreads / 32 + 1];      // ... their exclusive prefix and sum
     long long tile;
     long long stage;
+    // continuation after an overflow: per ray its children at the next depth
+    // | its pairs at the kept depth << 16, and the chunks' first rays / pairs
+    int ray_chpc[kTR];
+    uint16_t chunk_pair[kTR + 1];
+    uint8_t chunk_ray[kTR + 1];
+    int nchunks;
     uint8_t rank_lut[8 * 256];         // rank_mask(m, oct) at [oct * 256 + m]
 };
+// four CTAs per SM: 4 x (shared memory + the 1 KB reserved per CTA) <= 228 KB
+static_assert(sizeof(TileSmem) + 1024 <= 233472 / 4, "traversal tile state must allow 4 CTAs per SM");
 
 __device__ __forceinline__ int block_exclusive_sum(int v, int* warp_sums, int& total) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -178,12 +189,12 @@ __device__ __forceinline__ int warp_bases(TileSmem& S, int wsum) {
     return S.wbase[kWarps];
 }
 
-// Decide at depth dp for the n pairs of frontier buffer `cur`: each pair's
+// Decide at depth dp for the n pairs at pool offset src: each pair's
 // occupied children are slab-tested (all 8 from the 3 shared plane crossings
 // per axis) and recorded by front-to-back rank in S.rec (hit ranks | origin
 // octant << 8).  Returns the number of children hit; S.wbase holds each
 // warp's first output position.
-__device__ __forceinline__ int decide(TileSmem& S, const TileParams& p, int dp, int cur, int n) {
+__device__ __forceinline__ int decide(TileSmem& S, const TileParams& p, int dp, int src, int n) {
     const int lane = threadIdx.x & 31;
     int w0, w1;
     warp_range(n, w0, w1);
@@ -192,8 +203,8 @@ __device__ __forceinline__ int decide(TileSmem& S, const TileParams& p, int dp, 
     for (int rb = w0; rb < w1; rb += 32) {
         const int i = rb + lane;
         if (i < w1) {
-            const Node nd = nodes[S.vox[cur][i]];
-            const RayPrep ray = S.ray[S.rl[cur][i]];
+            const Node nd = nodes[S.vox[src + i]];
+            const RayPrep ray = S.ray[S.rl[src + i]];
             uint32_t o8 = 0, h = 0;
             bool live = true;
             if (dp == 0) {
@@ -214,8 +225,8 @@ __device__ __forceinline__ int decide(TileSmem& S, const TileParams& p, int dp, 
     return warp_bases(S, cnt);
 }
 
-// Subdivide: the hit children of the n pairs, front to back, into `cur ^ 1`.
-__device__ __forceinline__ void subdivide(TileSmem& S, const TileParams& p, int dp, int cur, int n) {
+// Subdivide: the hit children of the n pairs at src, front to back, to dst.
+__device__ __forceinline__ void subdivide(TileSmem& S, const TileParams& p, int dp, int src, int dst, int n) {
     const int lane = threadIdx.x & 31;
     int w0, w1;
     warp_range(n, w0, w1);
@@ -230,24 +241,24 @@ __device__ __forceinline__ void subdivide(TileSmem& S, const TileParams& p, int 
         int pos = run + incl - c;
         run += __shfl_sync(0xffffffffu, incl, 31);
         if (h0) {
-            const Node nd = nodes[S.vox[cur][i]];
+            const Node nd = nodes[S.vox[src + i]];
             const uint32_t o8 = r >> 8;
-            const uint8_t rl = S.rl[cur][i];
+            const uint8_t rl = S.rl[src + i];
             for (uint32_t h = h0; h; h &= h - 1u) {
                 const uint32_t cs = (uint32_t)(__ffs(h) - 1) ^ o8;
-                S.vox[cur ^ 1][pos] = nd.childbase + __popc(nd.childmask & ((1u << cs) - 1u));
-                S.rl[cur ^ 1][pos] = rl;
+                S.vox[dst + pos] = nd.childbase + __popc(nd.childmask & ((1u << cs) - 1u));
+                S.rl[dst + pos] = rl;
                 ++pos;
             }
         }
     }
 }
 
-// Compactify at the target depth: the hit children of the n pairs with their
+// Compactify at the target depth: the hit children of the n pairs at src with their
 // (t_enter, t_exit), written to their staging slots from `base` on, and each
 // ray's entry count added to S.ray_cnt (pairs are grouped by ray, so the
 // last lane of each run of one ray in a row adds the run's sum).
-__device__ __forceinline__ void write_final(TileSmem& S, const TileParams& p, int dp, int cur, int n,
+__device__ __forceinline__ void write_final(TileSmem& S, const TileParams& p, int dp, int src, int n,
                                             long long base) {
     const int lane = threadIdx.x & 31;
     int w0, w1;
@@ -258,7 +269,7 @@ __device__ __forceinline__ void write_final(TileSmem& S, const TileParams& p, in
         const int i = rb + lane;
         const bool valid = i < w1;
         const uint32_t r = valid ? S.rec[i] : 0u;
-        const int rl = valid ? (int)S.rl[cur][i] : -1;
+        const int rl = valid ? (int)S.rl[src + i] : -1;
         const uint32_t h0 = r & 0xffu;
         const int c = __popc(h0);
         const int incl = warp_incl_scan(c, lane);
@@ -272,7 +283,7 @@ __device__ __forceinline__ void write_final(TileSmem& S, const TileParams& p, in
         const int excl_head = __shfl_sync(0xffffffffu, incl - c, head);
         if (valid && (lane == 31 || rl_next != rl) && incl > excl_head) atomicAdd(&S.ray_cnt[rl], incl - excl_head);
         if (h0) {
-            const Node nd = nodes[S.vox[cur][i]];
+            const Node nd = nodes[S.vox[src + i]];
             const uint32_t o8 = r >> 8;
             // the exact (t_enter, t_exit) of the hit children only (about one
             // per pair at the target depth)
@@ -292,34 +303,45 @@ __device__ __forceinline__ void write_final(TileSmem& S, const TileParams& p, in
     }
 }
 
-// Levels 0..D-1 for the tile-local rays [r0, r0 + nr).  Returns false if a
-// frontier would exceed kFCap (block-uniform).  On success the target
-// depth's decisions stay in S.rec over the nfin pairs of frontier buffer
-// `cur` (S.wbase: each warp's first output), and `total` is the number of
-// entries; S.lvl holds the level sizes of this pass.
-__device__ bool run_levels(TileSmem& S, const TileParams& p, int r0, int nr, int& cur, int& nfin, int& total) {
+// Root pairs of the tile-local rays [r0, r0 + nr) at the pool's start.
+__device__ __forceinline__ void init_roots(TileSmem& S, int r0, int nr) {
     for (int i = threadIdx.x; i < nr; i += kThreads) {
-        S.vox[0][i] = 0;
-        S.rl[0][i] = (uint8_t)(r0 + i);
+        S.vox[i] = 0;
+        S.rl[i] = (uint8_t)(r0 + i);
     }
-    if (threadIdx.x <= kMaxDepth + 1) S.lvl[threadIdx.x] = 0;
-    __syncthreads();
-    cur = 0;
-    int n = nr;
-    for (int dp = 0; dp < p.D; ++dp) {
-        const bool fin = dp + 1 == p.D;
-        total = decide(S, p, dp, cur, n);
+}
+
+// Where a sweep of levels stopped: the n pairs of depth dp at pool offset
+// src, decided (S.rec; S.wbase holds each warp's first output), and the
+// number of pairs (or entries, at the target depth) their decisions make.
+struct LevelRun {
+    int src, n, dp, total;
+};
+
+// Decide / Subdivide from depth dp0 for the n pairs at pool offset a, the
+// levels alternating between offsets a and b, each holding at most cap
+// pairs.  Returns true at the target depth (lr: its decided pairs and the
+// entry count) or false (block-uniform) when the Decide at depth lr.dp would
+// make a frontier of lr.total > cap pairs (lr: that depth's pairs, kept in
+// place).  S.lvl[dp + 1] receives the size every decided level makes.  The
+// caller syncs after placing the first level's pairs.
+__device__ bool run_from(TileSmem& S, const TileParams& p, int dp0, int a, int b, int n, int cap, LevelRun& lr) {
+    for (int dp = dp0;; ++dp) {
+        const int total = decide(S, p, dp, a, n);
         if (threadIdx.x == 0) S.lvl[dp + 1] = total;
-        if (fin) break;
-        if (total > kFCap) return false;
-        subdivide(S, p, dp, cur, n);
+        lr = LevelRun{a, n, dp, total};
+        if (dp + 1 == p.D) {
+            __syncthreads();
+            return true;
+        }
+        if (total > cap) return false;
+        subdivide(S, p, dp, a, b, n);
         __syncthreads();
-        cur ^= 1;
+        const int t = a;
+        a = b;
+        b = t;
         n = total;
     }
-    nfin = n;
-    __syncthreads();
-    return true;
 }
 
 // Reserves n staging slots (one atomic, thread 0) into S.stage; flags an
@@ -332,9 +354,122 @@ __device__ __forceinline__ void reserve_stage(TileSmem& S, const TileParams& p, 
     }
 }
 
-__device__ __forceinline__ void commit_levels(TileSmem& S, const TileParams& p) {
-    if (threadIdx.x >= 1 && threadIdx.x <= p.D && S.lvl[threadIdx.x])
-        atomicAdd((unsigned long long*)&p.ctr->count[threadIdx.x], (unsigned long long)S.lvl[threadIdx.x]);
+// Adds the level sizes S.lvl[lo..hi] of the last sweep to the counters.
+__device__ __forceinline__ void commit_levels(TileSmem& S, const TileParams& p, int lo, int hi) {
+    const int l = (int)threadIdx.x;
+    if (l >= lo && l <= hi && S.lvl[l])
+        atomicAdd((unsigned long long*)&p.ctr->count[l], (unsigned long long)S.lvl[l]);
+}
+
+// Stages the entries of a finished sweep whose decisions (at the target
+// depth) are lr's, covering the tile-local rays [r_lo, r_hi): one
+// reservation, the entries written, and each ray's first staging slot.
+__device__ __forceinline__ void stage_sweep(TileSmem& S, const TileParams& p, long long ra, int r_lo, int r_hi,
+                                            const LevelRun& lr) {
+    reserve_stage(S, p, lr.total);
+    __syncthreads();
+    write_final(S, p, p.D - 1, lr.src, lr.n, S.stage);
+    __syncthreads();                       // the rays' counts are complete
+    const int j = (int)threadIdx.x, l = r_hi - r_lo;
+    int sum;
+    const int pre = block_exclusive_sum(j < l ? S.ray_cnt[r_lo + j] : 0, S.warp_sums, sum);
+    if (j < l) p.ray_src[ra + r_lo + j] = (int32_t)(S.stage + pre);
+}
+
+// Runs the tile-local rays [r, nr) from the root over ranges that fit,
+// halving a range that overflows and growing back after a success; level
+// sizes from depth lmin on are counted.  Returns the entries staged.
+__device__ long long sweep_halving(TileSmem& S, const TileParams& p, long long ra, int r, int nr, int lmin) {
+    long long staged = 0;
+    const int half = max(1, (nr - r) / 2);
+    int len = half;
+    while (r < nr) {
+        const int l = min(len, nr - r);
+        init_roots(S, r, l);
+        __syncthreads();
+        LevelRun lr;
+        if (!run_from(S, p, 0, 0, kFCap, l, kFCap, lr)) {
+            len = max(1, l / 2);
+            __syncthreads();               // the pool is refilled next
+            continue;
+        }
+        commit_levels(S, p, lmin, p.D);
+        stage_sweep(S, p, ra, r, r + l, lr);
+        staged += lr.total;
+        r += l;
+        len = min(half, 2 * len);
+    }
+    return staged;
+}
+
+// A tile whose frontier at depth lr0.dp + 1 would overflow.  The lr0.n pairs
+// of depth lr0.dp (decided: S.rec) move to the pool's start and are split at
+// ray boundaries into chunks whose pairs fit one of two buffers after them
+// and whose children fit too (half a buffer where deeper frontiers follow);
+// each chunk is decided again at that depth, swept down to the target depth
+// in those buffers and staged.  Returns the tile's entry count.
+__device__ long long sweep_chunks(TileSmem& S, const TileParams& p, long long ra, int nr, const LevelRun& lr0) {
+    const int dp = lr0.dp, n = lr0.n;
+    for (int i = threadIdx.x; i < kTR; i += kThreads) S.ray_chpc[i] = 0;
+    __syncthreads();
+    commit_levels(S, p, 1, dp + 1);        // those levels are complete for the tile
+    for (int i = threadIdx.x; i < n; i += kThreads)
+        atomicAdd(&S.ray_chpc[S.rl[lr0.src + i]], __popc(S.rec[i] & 0xffu) | (1 << 16));
+    __syncthreads();
+    if (lr0.src != 0) {                    // [kFCap, kFCap + n) -> [0, n): disjoint
+        for (int i = threadIdx.x; i < n; i += kThreads) {
+            S.vox[i] = S.vox[lr0.src + i];
+            S.rl[i] = S.rl[lr0.src + i];
+        }
+    }
+    const int F = min(kFCap, (2 * kFCap - n) / 2);     // >= kFCap / 2: a single ray always fits
+    const int A = n, B = n + F;
+    const int budget = dp + 2 == p.D ? F : F / 2;
+    if (threadIdx.x == 0) {
+        // a chunk's own pairs must fit one buffer too
+        int nch = 0, acc = 0, pairs = 0, first = 0;
+        S.chunk_ray[0] = 0;
+        S.chunk_pair[0] = 0;
+        for (int r = 0; r < nr; ++r) {
+            const int v = S.ray_chpc[r];
+            const int c = v & 0xffff, pc = v >> 16;
+            if (r > first && (acc + c > budget || pairs + pc - (int)S.chunk_pair[nch] > F)) {
+                ++nch;
+                S.chunk_ray[nch] = (uint8_t)r;
+                S.chunk_pair[nch] = (uint16_t)pairs;
+                first = r;
+                acc = 0;
+            }
+            acc += c;
+            pairs += pc;
+        }
+        ++nch;
+        S.chunk_ray[nch] = (uint8_t)nr;
+        S.chunk_pair[nch] = (uint16_t)pairs;
+        S.nchunks = nch;
+    }
+    __syncthreads();
+    const int nch = S.nchunks;
+    long long staged = 0;
+    for (int k = 0; k < nch; ++k) {
+        const int r_lo = S.chunk_ray[k], r_hi = S.chunk_ray[k + 1];
+        const int pa = S.chunk_pair[k], m = (int)S.chunk_pair[k + 1] - pa;
+        for (int i = threadIdx.x; i < m; i += kThreads) {
+            S.vox[A + i] = S.vox[pa + i];
+            S.rl[A + i] = S.rl[pa + i];
+        }
+        __syncthreads();
+        LevelRun lr;
+        if (!run_from(S, p, dp, A, B, m, F, lr)) {
+            __syncthreads();
+            return staged + sweep_halving(S, p, ra, r_lo, nr, dp + 2);
+        }
+        commit_levels(S, p, dp + 2, p.D);
+        stage_sweep(S, p, ra, r_lo, r_hi, lr);
+        staged += lr.total;
+        __syncthreads();                   // the chunk's buffers are reused next
+    }
+    return staged;
 }
 
 __global__ void __launch_bounds__(kThreads, 4) k_traverse(const TileParams p) {
@@ -353,44 +488,19 @@ __global__ void __launch_bounds__(kThreads, 4) k_traverse(const TileParams p) {
             if (i < nr) S.ray[i] = prep_ray(p.o, p.d, ra + i);
             S.ray_cnt[i] = 0;
         }
+        init_roots(S, 0, nr);
         __syncthreads();
-        int cur, nfin, total;
-        const bool whole = run_levels(S, p, 0, nr, cur, nfin, total);
-        if (whole) {
-            commit_levels(S, p);
-            reserve_stage(S, p, total);
-            if (threadIdx.x == 0) p.tiles[t] = TileInfo{S.stage, (long long)total};
+        LevelRun lr;
+        if (run_from(S, p, 0, 0, kFCap, nr, kFCap, lr)) {
+            commit_levels(S, p, 1, p.D);
+            reserve_stage(S, p, lr.total);
+            if (threadIdx.x == 0) p.tiles[t] = TileInfo{S.stage, (long long)lr.total};
             __syncthreads();
-            write_final(S, p, p.D - 1, cur, nfin, S.stage);
+            write_final(S, p, p.D - 1, lr.src, lr.n, S.stage);
         } else {
-            // halve until every sub-range fits; each sub-range reserves its
-            // own staging slots and writes its entries at once (each ray's
-            // first slot goes to ray_src for the placement)
-            long long tile_total = 0;
-            int r = 0, len = nr / 2;
-            while (r < nr) {
-                const int l = min(len, nr - r);
-                int cu2, nf2, tot2;
-                if (!run_levels(S, p, r, l, cu2, nf2, tot2)) {
-                    len = max(1, l / 2);
-                    continue;
-                }
-                commit_levels(S, p);
-                reserve_stage(S, p, tot2);
-                __syncthreads();
-                write_final(S, p, p.D - 1, cu2, nf2, S.stage);
-                __syncthreads();           // the sub-range's per-ray counts are complete
-                const int j = (int)threadIdx.x;
-                int sum;
-                const int pre = block_exclusive_sum(j < l ? S.ray_cnt[r + j] : 0, S.warp_sums, sum);
-                if (j < l) p.ray_src[ra + r + j] = (int32_t)(S.stage + pre);
-                tile_total += tot2;
-                r += l;
-                // grow back after a success, so only the dense part of the
-                // tile runs at the small size
-                len = min(nr / 2, 2 * len);
-            }
-            if (threadIdx.x == 0) p.tiles[t] = TileInfo{-1, tile_total};
+            __syncthreads();               // S.lvl of the overflowing level
+            const long long staged = sweep_chunks(S, p, ra, nr, lr);
+            if (threadIdx.x == 0) p.tiles[t] = TileInfo{-1, staged};
         }
         __syncthreads();                   // per-ray counts complete
         if ((int)threadIdx.x < nr) p.ray_cnt[ra + threadIdx.x] = S.ray_cnt[threadIdx.x];

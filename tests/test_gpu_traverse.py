@@ -6,6 +6,8 @@ import torch
 
 from paper_2101_10994_gb300 import scenes as S
 
+from traverse_paths import pairs_by_depth, tile_paths
+
 pytestmark = pytest.mark.gpu
 
 
@@ -109,7 +111,7 @@ def test_full_size_1080p_lod5_sampled(ng, oracle_mod):
 def test_dense_grid_frontier_overflow_path(ng, oracle_mod):
     # every voxel of a dense depth-6 grid is occupied: a ray crossing the cube
     # meets ~100-190 voxels per level, so 128 rays overflow the on-chip
-    # frontier and the traversal re-runs the tile over halves of its rays;
+    # frontier and the traversal continues those tiles in chunks of rays;
     # the lists must still equal the brute-force ones bit for bit
     dense = S.full_octree(6)
     svo = ng.svo_build(dense.keys)
@@ -120,11 +122,40 @@ def test_dense_grid_frontier_overflow_path(ng, oracle_mod):
     tgt = rng.uniform(-0.6, 0.6, (n, 3))
     d = (tgt - o).astype(np.float64)
     d = (d / np.linalg.norm(d, axis=1, keepdims=True)).astype(np.float32)
+    assert tile_paths(pairs_by_depth(ora, o, d, 6), 6) == ["chunks", "chunks", "whole"]
     g = gpu_lists(ng, svo, o, d, 4)
     assert np.diff(g[0]).mean() > 60
     assert_same_lists(g, ora.trace_rays(o, d, 4))
     sizes = g[3].level_sizes()
     assert sizes[-1] == len(g[1]) and sizes[0] == n
+
+
+def test_dense_grid_every_overflow_path(ng, oracle_mod):
+    # rays near the cube's main diagonal cross ~3 x 2^dp voxels per depth: the
+    # first tile overflows early, and one of its chunks overflows again
+    # further down (its rays then run from the root over halving ranges); the
+    # second continues in chunks; the third (rays running along one edge of
+    # the cube) fits whole.  Lists bit-exact, and every depth's pair count (each
+    # counted once whatever the path) equal to the brute-force list lengths.
+    dense = S.full_octree(6)
+    svo = ng.svo_build(dense.keys)
+    ora = oracle_mod.OracleSVO(dense.keys)
+    rng = np.random.default_rng(1)
+    o = np.full((256, 3), -2.0, np.float32) + rng.uniform(-0.2, 0.2, (256, 3)).astype(np.float32)
+    d = rng.uniform(-0.2, 0.2, (256, 3)) - o
+    o2 = np.tile(np.array([[-2.0, 0.97, 0.97]], np.float32), (70, 1))
+    d2 = np.stack([np.ones(70), rng.uniform(-0.01, 0.01, 70), rng.uniform(-0.01, 0.01, 70)], 1)
+    o = np.concatenate([o, o2])
+    d = np.concatenate([d, d2])
+    d = (d / np.linalg.norm(d, axis=1, keepdims=True)).astype(np.float32)
+    P = pairs_by_depth(ora, o, d, 6)
+    assert tile_paths(P, 6) == ["halving", "chunks", "whole"]
+    g = gpu_lists(ng, svo, o, d, 4)
+    assert_same_lists(g, ora.trace_rays(o, d, 4))
+    sizes = g[3].level_sizes()
+    assert sizes[0] == len(o)
+    assert sizes[3:] == [int(v) for v in P.sum(0)[3:]]
+    svo.free()
 
 
 def test_async_width_rejects_bad_width(ng):
