@@ -246,7 +246,7 @@ def run_ours(args, rank, world, local_rank):
 
     def step(mode, out, ev):
         ev[0].record()
-        lists = ng.svo_trace_rays(svo, o, d, W["lod"])
+        lists = ng.svo_trace_rays(svo, o, d, W["lod"], t_range=False)
         ev[1].record()
         ng.sphere_trace(svo, feats, dec, o, d, lists, eps=W["eps"], far=W["far"], max_steps=W["max_steps"],
                         decode=mode, normals=False, out=out)
@@ -429,7 +429,7 @@ def run_ours(args, rank, world, local_rank):
             flush.zero_()
             ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
             ev[0].record()
-            lists = ng.svo_trace_rays(svo, o, d, W["lod"])
+            lists = ng.svo_trace_rays(svo, o, d, W["lod"], t_range=False)
             ev[1].record()
             ng.sphere_trace(svo, fs, dec, o, d, lists, eps=W["eps"], far=W["far"], max_steps=W["max_steps"],
                             decode=sm_mode, normals=False, out=sout)
@@ -532,16 +532,17 @@ def profiled_traffic(kernel, tag=""):
 
 def traversal_bytes(W, sizes):
     """Algorithmic bytes of one frame's traversal as this design runs it
-    (tiles of rays swept level by level on chip): every ray read once (24 B)
-    with its count written and read back and its CSR offset written
-    (3 x 4 B); one node record (16 B) per ray/voxel pair Decide visits at
-    depths 0..D-1; every final entry (voxel id 4 B + t range 8 B) staged,
-    read back and written to its final position (3 x 12 B)."""
+    (tiles of rays swept level by level on chip; the frame asks for no t
+    ranges, which the tracers recompute): every ray read once (24 B) with
+    its count written and read back and its CSR offset written (3 x 4 B);
+    one node record (16 B) per ray/voxel pair Decide visits at depths
+    0..D-1; every final entry (voxel id, 4 B) staged, read back and written
+    to its final position (3 x 4 B)."""
     R = sizes[0]
     D = len(sizes) - 1
     H = sizes[D]
     visits = sum(sizes[:D])
-    return 36 * R + 16 * visits + 36 * H
+    return 36 * R + 16 * visits + 12 * H
 
 
 def cpu_model():
@@ -564,9 +565,9 @@ def traversal_roofline(W, res, mode, peaks):
     nbytes = traversal_bytes(W, res["level_sizes"])
     sec = res["ms_traverse"] * 1e-3
     achieved = nbytes / sec / 1e9
-    # the lower bound of any design: rays in, the final CSR lists out
+    # the lower bound of any design: rays in, the final CSR lists (voxel ids) out
     sizes = res["level_sizes"]
-    lower = 24 * sizes[0] + 4 * (sizes[0] + 1) + 12 * sizes[-1]
+    lower = 24 * sizes[0] + 4 * (sizes[0] + 1) + 4 * sizes[-1]
     traffic = profiled_traffic("k_traverse")
     return {"bound": "hbm", "kernel": "k_traverse", "achieved": achieved, "peak": hbm, "unit": "GB/s",
             "frac": achieved / hbm, "traffic": traffic,

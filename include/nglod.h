@@ -226,8 +226,9 @@ size_t svo_trace_rays_workspace(int64_t R, int64_t pair_capacity);
  * in magnitude makes that axis parallel.
  * The levels run per tile of 128 consecutive rays inside one persistent
  * kernel, each tile's frontier in shared memory (Decide, the block-wide
- * ExclusiveSum and Subdivide on chip; a tile whose frontier outgrows it is
- * re-run over halves of its rays).  Tiles stage their entries in any order;
+ * ExclusiveSum and Subdivide on chip; a tile whose frontier outgrows it
+ * continues from its last level that fits in chunks of whole rays).  Tiles
+ * stage their entries in any order;
  * a scan of the tile counts then places them in ray order, so the result
  * equals the global level-by-level sequence entry for entry.
  *   o, d          [R, 3] float32 origins / directions (device).
@@ -238,7 +239,9 @@ size_t svo_trace_rays_workspace(int64_t R, int64_t pair_capacity);
  *   ray_offsets   [R + 1] int32; hits of ray i are [ray_offsets[i],
  *                 ray_offsets[i+1]).
  *   voxel_id      [hit_capacity] int32 voxel ids at the target depth.
- *   t_range       [hit_capacity, 2] float32 (t_enter, t_exit) per hit.
+ *   t_range       [hit_capacity, 2] float32 (t_enter, t_exit) per hit, or
+ *                 NULL: not written (the tracers recompute each entry's
+ *                 interval from its voxel with the same FP32 slab test).
  *   h_stats       host int64[2] (nullable): [0] = total hits H, [1] = largest
  *                 number of pairs Decide kept at any depth.
  * Errors: NGLOD_ERR_CAPACITY if H > hit_capacity or H > pair_capacity
@@ -354,7 +357,10 @@ size_t sphere_trace_workspace(int64_t R);
  * x = o + t d from that voxel and its ancestors, and counts one step; d < eps
  * is a hit, otherwise t += d; t > far_t or max_steps reached is a miss.
  *   o, d, R, lod        as for svo_trace_rays (same rays, same LOD).
- *   ray_offsets, voxel_id, t_range   the CSR lists of svo_trace_rays.
+ *   ray_offsets, voxel_id   the CSR lists of svo_trace_rays.
+ *   t_range             not read (may be NULL): each entry's [t_enter,
+ *                       t_exit] is recomputed from its voxel by the slab
+ *                       test svo_trace_rays uses, which gives the same bits.
  *   work                device workspace >= sphere_trace_workspace(R).  After
  *                       the call, bytes [256, 256 + 4R) hold the int32 id (at
  *                       the target depth) of the voxel each hit ray stopped in,
@@ -497,8 +503,8 @@ int sdf_query_blend(const nglod_svo* svo, const nglod_features* feats,
                     float* sdf, void* stream);
 
 /* sphere_trace_blend -- sphere_trace (Sec. 3.4 / A.4 stepping) of the
- * blended field d_L~.  The lists (ray_offsets, voxel_id, t_range) are those
- * of svo_trace_rays at LOD ceil(L~): at L* + 1 when alpha > 0 (rays walk the
+ * blended field d_L~.  The lists (ray_offsets, voxel_id; t_range is not
+ * read and may be NULL) are those of svo_trace_rays at LOD ceil(L~): at L* + 1 when alpha > 0 (rays walk the
  * finer voxels, inside which both terms are defined; every step decodes
  * both LODs at the same point), at L* when alpha = 0 (the plain trace).
  * normal: the normalised blend (1 - alpha) grad d_L* + alpha grad d_(L*+1)
@@ -531,7 +537,7 @@ typedef struct {
     int64_t R;
     const int32_t* ray_offsets;
     const int32_t* voxel_id;
-    const float* t_range;
+    const float* t_range;     /* not read (may be NULL), as for sphere_trace */
     void* work;
     size_t work_bytes;
     float* t_hit;

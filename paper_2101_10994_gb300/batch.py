@@ -45,7 +45,7 @@ class BatchRenderer:
         # sizing pass: one synchronous traversal per job fixes the list capacities
         self.bufs = []
         for j in jobs:
-            lists = ng.svo_trace_rays(j.svo, j.o, j.d, j.lod)
+            lists = ng.svo_trace_rays(j.svo, j.o, j.d, j.lod, t_range=False)
             cap = max(int(lists.max_pairs * headroom) + 1024, j.R + 1024)
             hcap = max(int(lists.voxel_id.numel() * headroom) + 1024, 1024)
             tw = L.svo_trace_rays_workspace(j.R, cap)
@@ -53,7 +53,6 @@ class BatchRenderer:
                      twork=torch.empty(tw, dtype=torch.uint8, device=dev),
                      offs=torch.empty(j.R + 1, dtype=torch.int32, device=dev),
                      vid=torch.empty(hcap, dtype=torch.int32, device=dev),
-                     tr=torch.empty((hcap, 2), dtype=torch.float32, device=dev),
                      swork=torch.empty(L.sphere_trace_workspace(j.R), dtype=torch.uint8, device=dev),
                      t=torch.empty(j.R, dtype=torch.float32, device=dev),
                      hit=torch.empty(j.R, dtype=torch.uint8, device=dev),
@@ -76,8 +75,8 @@ class BatchRenderer:
             arr[k].dec = j.dec.c()
             arr[k].lod = j.lod
             arr[k].o, arr[k].d, arr[k].R = j.o.data_ptr(), j.d.data_ptr(), j.R
-            arr[k].ray_offsets, arr[k].voxel_id, arr[k].t_range = (b["offs"].data_ptr(), b["vid"].data_ptr(),
-                                                                    b["tr"].data_ptr())
+            # no t ranges: the tracers recompute each entry's interval
+            arr[k].ray_offsets, arr[k].voxel_id, arr[k].t_range = b["offs"].data_ptr(), b["vid"].data_ptr(), None
             arr[k].work, arr[k].work_bytes = b["swork"].data_ptr(), b["swork"].numel()
             arr[k].t_hit, arr[k].hit, arr[k].steps = b["t"].data_ptr(), b["hit"].data_ptr(), b["steps"].data_ptr()
             arr[k].normal = ng._ptr(b["normal"])
@@ -113,7 +112,7 @@ class BatchRenderer:
             st = self.tstreams[i % len(self.tstreams)] if self.tstreams else main
             ng._check(L.svo_trace_rays_async(j.svo.h, j.o.data_ptr(), j.d.data_ptr(), j.R, j.lod,
                                              b["twork"].data_ptr(), b["twork"].numel(), b["cap"],
-                                             b["offs"].data_ptr(), b["vid"].data_ptr(), b["tr"].data_ptr(),
+                                             b["offs"].data_ptr(), b["vid"].data_ptr(), None,
                                              b["hcap"], C.c_void_p(st.cuda_stream)))
         for st in self.tstreams:
             main.wait_stream(st)

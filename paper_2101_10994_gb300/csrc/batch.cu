@@ -230,7 +230,6 @@ extern "C" int sphere_trace_batch_create(const nglod_trace_job* jobs, int num_jo
             A.osc = params->osc_check;
             A.offs = J.ray_offsets;
             A.vid = J.voxel_id;
-            A.tr = (const float2*)J.t_range;
             A.t_hit = J.t_hit;
             A.hit = J.hit;
             A.steps = J.steps;

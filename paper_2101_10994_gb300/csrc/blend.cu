@@ -112,7 +112,6 @@ extern "C" int sphere_trace_blend(const nglod_svo* svo, const nglod_features* fe
     A.osc = params->osc_check;
     A.offs = ray_offsets;
     A.vid = voxel_id;
-    A.tr = (const float2*)t_range;
     A.t_hit = t_hit;
     A.hit = hit;
     A.steps = steps;

@@ -111,6 +111,34 @@ struct __align__(16) RayPrep {
     int par;                  // bit a set: axis a parallel
 };
 
+// Prepares a ray: IEEE reciprocals of the direction components (0 for an
+// axis below FLT_MIN in magnitude, which is then parallel) and the validity
+// flag (finite components, not all axes parallel).
+__device__ __forceinline__ RayPrep make_ray_prep(float ox, float oy, float oz, float dx, float dy, float dz) {
+    RayPrep p;
+    p.ox = ox;
+    p.oy = oy;
+    p.oz = oz;
+    const float dd[3] = {dx, dy, dz};
+    const float oo[3] = {ox, oy, oz};
+    int ok = 1, par = 0;
+    float inv[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (!isfinite(oo[a]) || !isfinite(dd[a])) ok = 0;
+        const bool pa = fabsf(dd[a]) < 1.17549435e-38f;
+        par |= pa ? (1 << a) : 0;
+        inv[a] = pa ? 0.0f : __fdiv_rn(1.0f, dd[a]);
+    }
+    if (par == 7) ok = 0;
+    p.ix = inv[0];
+    p.iy = inv[1];
+    p.iz = inv[2];
+    p.par = par;
+    p.valid = ok;
+    return p;
+}
+
 // FP32 slab test of a prepared ray against voxel (i,j,k) at depth dp, all in
 // round-to-nearest with no contraction of the rounded steps.  Voxel bounds
 // lo = -1 + i 2^(1-dp) and hi = lo + 2^(1-dp) are exact (a single fused
@@ -151,6 +179,19 @@ __device__ __forceinline__ bool slab_test(const RayPrep& r, uint32_t ijk, int dp
     tout = tf;
     if (oct) *oct = octant;
     return true;
+}
+
+// [t_enter, t_exit] of ray (o, d) in voxel (i,j,k) at depth dp by the slab
+// test above -- the bits the traversal writes for a listed voxel (its
+// child_slabs + child_hit are equal to slab_test bit for bit); an interval
+// that does not hit (never the case for a listed voxel) comes back empty.
+__device__ __forceinline__ void voxel_interval(float ox, float oy, float oz, float dx, float dy, float dz,
+                                               uint32_t ijk, int dp, float& tin, float& tout) {
+    const RayPrep r = make_ray_prep(ox, oy, oz, dx, dy, dz);
+    if (!slab_test(r, ijk, dp, tin, tout)) {
+        tin = INFINITY;
+        tout = -INFINITY;
+    }
 }
 
 // Octant of the ray origin relative to the centre lo + 2^(-dp) of voxel

@@ -1005,10 +1005,12 @@ namespace {
 // lengths, clamped), which changes only the schedule: every ray's outputs
 // are those of the index-order trace.
 // Also writes each ray's first list entry (t_enter, t_exit, voxel, packed
-// ijk) to start[r], so the tracer starts a ray with independent loads only.
+// ijk; the interval by the traversal's slab test at depth D) to start[r], so
+// the tracer starts a ray with independent loads only.
 __global__ void k_group_keys(const int32_t* __restrict__ offs, long long R, uint8_t* __restrict__ key,
-                             int* __restrict__ hist, const float2* __restrict__ tr, const int32_t* __restrict__ vid,
-                             const Node* __restrict__ node_D, int4* __restrict__ start) {
+                             int* __restrict__ hist, const float* __restrict__ o, const float* __restrict__ d,
+                             const int32_t* __restrict__ vid, const Node* __restrict__ node_D, int D,
+                             int4* __restrict__ start) {
     __shared__ int h[kOrderBuckets];
     for (int i = threadIdx.x; i < kOrderBuckets; i += blockDim.x) h[i] = 0;
     __syncthreads();
@@ -1020,9 +1022,12 @@ __global__ void k_group_keys(const int32_t* __restrict__ offs, long long R, uint
         const int c0 = r < R ? offs[r] : 0;
         const int len = r < R ? offs[r + 1] - c0 : 0;
         if (len > 0) {
-            const float2 t0 = tr[c0];
             const int v = vid[c0];
-            start[r] = make_int4(__float_as_int(t0.x), __float_as_int(t0.y), v, (int)node_D[v].ijk);
+            const uint32_t ijk = node_D[v].ijk;
+            float tin, tout;
+            voxel_interval(o[3 * r], o[3 * r + 1], o[3 * r + 2], d[3 * r], d[3 * r + 1], d[3 * r + 2], ijk, D, tin,
+                           tout);
+            start[r] = make_int4(__float_as_int(tin), __float_as_int(tout), v, (int)ijk);
         }
         const int m = __reduce_max_sync(0xffffffffu, len);
         if (lane == 0) {
@@ -1086,7 +1091,7 @@ int enqueue_ray_order(TraceArgs& A, void* work, const Node* node_D, cudaStream_t
     const int sms = device_sms();
     const int gk = (int)std::max<long long>(1, std::min<long long>((G + 7) / 8, (long long)sms * 4));
     int4* start = reinterpret_cast<int4*>(w + trace_ws_start_offset(R));
-    k_group_keys<<<gk, 256, 0, st>>>(A.offs, R, key, hist, A.tr, A.vid, node_D, start);
+    k_group_keys<<<gk, 256, 0, st>>>(A.offs, R, key, hist, A.o, A.d, A.vid, node_D, A.D, start);
     k_order_scan<<<1, kOrderBuckets, 0, st>>>(hist, cursor);
     const int gs = (int)std::max<long long>(1, std::min<long long>((G + 255) / 256, (long long)sms * 4));
     k_order_scatter<<<gs, 256, 0, st>>>(key, G, cursor, order);
@@ -1142,7 +1147,6 @@ extern "C" int sphere_trace(const nglod_svo* svo, const nglod_features* feats, c
     A.osc = params->osc_check;
     A.offs = ray_offsets;
     A.vid = voxel_id;
-    A.tr = (const float2*)t_range;
     A.t_hit = t_hit;
     A.hit = hit;
     A.steps = steps;

@@ -97,9 +97,10 @@ struct TraceArgs {
     int D;
     float eps, far_t;
     int max_steps, osc;
+    // the rays' voxel lists (CSR); each entry's interval [t_enter, t_exit]
+    // is recomputed from its voxel by the traversal's slab test (same bits)
     const int32_t* offs;
     const int32_t* vid;
-    const float2* tr;
     float* t_hit;
     uint8_t* hit;
     int32_t* steps;       // nullable
@@ -133,13 +134,17 @@ struct RaySlot {
     float t, tin, tout, dprev;
     int cur, end, k, vox;
     uint32_t ijk;
-    // the next list entry (cur + 1 < end), loaded ahead so that moving on
-    // costs no list read; its voxel's packed ijk once nijk_ok
-    float ntin, ntout;
+    // the next list entry's voxel (cur + 1 < end), loaded ahead so that moving
+    // on costs no list read; its packed ijk once nijk_ok
     int nvox;
     uint32_t nijk;
     bool nijk_ok;
 };
+
+// The current entry's interval from its voxel S.ijk at depth D.
+__device__ __forceinline__ void entry_interval(RaySlot& S, int D) {
+    voxel_interval(S.ox, S.oy, S.oz, S.dx, S.dy, S.dz, S.ijk, D, S.tin, S.tout);
+}
 
 // Warp-uniform batch of ray indices taken from the global queue.
 struct RayQueue {
@@ -180,15 +185,10 @@ __device__ __forceinline__ void publish_hits(RaySlot& S, const TraceArgs& A, int
     S.hit_ray = -1;
 }
 
-// Issues the loads of the list entry after the current one (consumed by a
-// later advance, so their latency hides behind the next decode).
+// Issues the load of the list entry after the current one (consumed by a
+// later advance, so its latency hides behind the next decode).
 __device__ __forceinline__ void load_next(RaySlot& S, const TraceArgs& A) {
-    if (S.cur + 1 < S.end) {
-        const float2 tr = A.tr[S.cur + 1];
-        S.ntin = tr.x;
-        S.ntout = tr.y;
-        S.nvox = A.vid[S.cur + 1];
-    }
+    if (S.cur + 1 < S.end) S.nvox = A.vid[S.cur + 1];
     S.nijk_ok = false;
 }
 
@@ -205,22 +205,18 @@ __device__ __forceinline__ void prefetch_next_ijk(RaySlot& S, const TraceArgs& A
 // Moves the cursor past entries that end before t (the ray is discarded when
 // the list runs out), then jumps t to the current entry's start (Sec. 3.4).
 __device__ __forceinline__ void advance(RaySlot& S, const TraceArgs& A, const Tables& tb) {
-    int moves = 0;
-    bool have_ijk = false;
+    bool first = true;
     while (S.t > S.tout) {
         if (++S.cur >= S.end) {
             finish(S, A, false);
             return;
         }
-        S.tin = S.ntin;
-        S.tout = S.ntout;
         S.vox = S.nvox;
-        have_ijk = moves == 0 && S.nijk_ok;
-        if (have_ijk) S.ijk = S.nijk;
-        ++moves;
+        S.ijk = first && S.nijk_ok ? S.nijk : tb.node[A.D][S.vox].ijk;
+        first = false;
         load_next(S, A);
+        entry_interval(S, A.D);
     }
-    if (moves && !have_ijk) S.ijk = tb.node[A.D][S.vox].ijk;
     if (S.t < S.tin) S.t = S.tin;
     if (S.t > A.far_t) finish(S, A, false);
 }
@@ -250,11 +246,9 @@ __device__ __forceinline__ void start_ray(RaySlot& S, int r, const TraceArgs& A,
         S.vox = first.z;
         S.ijk = (uint32_t)first.w;
     } else {
-        const float2 tr = A.tr[S.cur];
-        S.tin = tr.x;
-        S.tout = tr.y;
         S.vox = A.vid[S.cur];
         S.ijk = tb.node[A.D][S.vox].ijk;
+        entry_interval(S, A.D);
     }
     S.t = S.tin;
     S.dprev = __int_as_float(0x7fc00000);

@@ -73,7 +73,7 @@ struct TileParams {
     int32_t* ray_cnt;                  // [R] entries per ray (k_place turns them into offsets)
     int32_t* ray_src;                  // [R] staging slot of each ray's first entry (sub-range tiles)
     int32_t* stage_vid;                // [stage_cap] staged entries
-    float2* stage_tr;
+    float2* stage_tr;                  // ... and their t ranges (null: not wanted)
     TileInfo* tiles;                   // [ntiles]
     Counters* ctr;
 };
@@ -130,28 +130,7 @@ __device__ __forceinline__ int block_exclusive_sum(int v, int* warp_sums, int& t
 }
 
 __device__ __forceinline__ RayPrep prep_ray(const float* o, const float* d, long long r) {
-    RayPrep p;
-    p.ox = o[3 * r];
-    p.oy = o[3 * r + 1];
-    p.oz = o[3 * r + 2];
-    const float dd[3] = {d[3 * r], d[3 * r + 1], d[3 * r + 2]};
-    const float oo[3] = {p.ox, p.oy, p.oz};
-    int ok = 1, par = 0;
-    float inv[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        if (!isfinite(oo[a]) || !isfinite(dd[a])) ok = 0;
-        const bool pa = fabsf(dd[a]) < 1.17549435e-38f;
-        par |= pa ? (1 << a) : 0;
-        inv[a] = pa ? 0.0f : __fdiv_rn(1.0f, dd[a]);
-    }
-    if (par == 7) ok = 0;
-    p.ix = inv[0];
-    p.iy = inv[1];
-    p.iz = inv[2];
-    p.par = par;
-    p.valid = ok;
-    return p;
+    return make_ray_prep(o[3 * r], o[3 * r + 1], o[3 * r + 2], d[3 * r], d[3 * r + 1], d[3 * r + 2]);
 }
 
 // The pairs [0, n) of a level are split into kWarps contiguous ranges, one
@@ -258,6 +237,7 @@ __device__ __forceinline__ void subdivide(TileSmem& S, const TileParams& p, int 
 // (t_enter, t_exit), written to their staging slots from `base` on, and each
 // ray's entry count added to S.ray_cnt (pairs are grouped by ray, so the
 // last lane of each run of one ray in a row adds the run's sum).
+template <bool WT>
 __device__ __forceinline__ void write_final(TileSmem& S, const TileParams& p, int dp, int src, int n,
                                             long long base) {
     const int lane = threadIdx.x & 31;
@@ -286,16 +266,18 @@ __device__ __forceinline__ void write_final(TileSmem& S, const TileParams& p, in
             const Node nd = nodes[S.vox[src + i]];
             const uint32_t o8 = r >> 8;
             // the exact (t_enter, t_exit) of the hit children only (about one
-            // per pair at the target depth)
+            // per pair at the target depth), when the caller wants them
             ChildSlabs cs;
-            child_slabs(S.ray[rl], nd.ijk, dp, cs);
+            if constexpr (WT) child_slabs(S.ray[rl], nd.ijk, dp, cs);
             for (uint32_t h = h0; h; h &= h - 1u) {
                 const uint32_t cc = (uint32_t)(__ffs(h) - 1) ^ o8;
-                float a0 = 0.f, a1 = 0.f;
-                child_hit(cs, cc, a0, a1);
                 if (pos < p.stage_cap) {
                     p.stage_vid[pos] = nd.childbase + __popc(nd.childmask & ((1u << cc) - 1u));
-                    p.stage_tr[pos] = make_float2(a0, a1);
+                    if constexpr (WT) {
+                        float a0 = 0.f, a1 = 0.f;
+                        child_hit(cs, cc, a0, a1);
+                        p.stage_tr[pos] = make_float2(a0, a1);
+                    }
                 }
                 ++pos;
             }
@@ -364,11 +346,12 @@ __device__ __forceinline__ void commit_levels(TileSmem& S, const TileParams& p, 
 // Stages the entries of a finished sweep whose decisions (at the target
 // depth) are lr's, covering the tile-local rays [r_lo, r_hi): one
 // reservation, the entries written, and each ray's first staging slot.
+template <bool WT>
 __device__ __forceinline__ void stage_sweep(TileSmem& S, const TileParams& p, long long ra, int r_lo, int r_hi,
                                             const LevelRun& lr) {
     reserve_stage(S, p, lr.total);
     __syncthreads();
-    write_final(S, p, p.D - 1, lr.src, lr.n, S.stage);
+    write_final<WT>(S, p, p.D - 1, lr.src, lr.n, S.stage);
     __syncthreads();                       // the rays' counts are complete
     const int j = (int)threadIdx.x, l = r_hi - r_lo;
     int sum;
@@ -379,6 +362,7 @@ __device__ __forceinline__ void stage_sweep(TileSmem& S, const TileParams& p, lo
 // Runs the tile-local rays [r, nr) from the root over ranges that fit,
 // halving a range that overflows and growing back after a success; level
 // sizes from depth lmin on are counted.  Returns the entries staged.
+template <bool WT>
 __device__ long long sweep_halving(TileSmem& S, const TileParams& p, long long ra, int r, int nr, int lmin) {
     long long staged = 0;
     const int half = max(1, (nr - r) / 2);
@@ -394,7 +378,7 @@ __device__ long long sweep_halving(TileSmem& S, const TileParams& p, long long r
             continue;
         }
         commit_levels(S, p, lmin, p.D);
-        stage_sweep(S, p, ra, r, r + l, lr);
+        stage_sweep<WT>(S, p, ra, r, r + l, lr);
         staged += lr.total;
         r += l;
         len = min(half, 2 * len);
@@ -408,6 +392,7 @@ __device__ long long sweep_halving(TileSmem& S, const TileParams& p, long long r
 // and whose children fit too (half a buffer where deeper frontiers follow);
 // each chunk is decided again at that depth, swept down to the target depth
 // in those buffers and staged.  Returns the tile's entry count.
+template <bool WT>
 __device__ long long sweep_chunks(TileSmem& S, const TileParams& p, long long ra, int nr, const LevelRun& lr0) {
     const int dp = lr0.dp, n = lr0.n;
     for (int i = threadIdx.x; i < kTR; i += kThreads) S.ray_chpc[i] = 0;
@@ -462,16 +447,18 @@ __device__ long long sweep_chunks(TileSmem& S, const TileParams& p, long long ra
         LevelRun lr;
         if (!run_from(S, p, dp, A, B, m, F, lr)) {
             __syncthreads();
-            return staged + sweep_halving(S, p, ra, r_lo, nr, dp + 2);
+            return staged + sweep_halving<WT>(S, p, ra, r_lo, nr, dp + 2);
         }
         commit_levels(S, p, dp + 2, p.D);
-        stage_sweep(S, p, ra, r_lo, r_hi, lr);
+        stage_sweep<WT>(S, p, ra, r_lo, r_hi, lr);
         staged += lr.total;
         __syncthreads();                   // the chunk's buffers are reused next
     }
     return staged;
 }
 
+// WT: the entries' t ranges are staged too (the caller asked for them).
+template <bool WT>
 __global__ void __launch_bounds__(kThreads, 4) k_traverse(const TileParams p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TileSmem& S = *reinterpret_cast<TileSmem*>(smem_raw);
@@ -496,10 +483,10 @@ __global__ void __launch_bounds__(kThreads, 4) k_traverse(const TileParams p) {
             reserve_stage(S, p, lr.total);
             if (threadIdx.x == 0) p.tiles[t] = TileInfo{S.stage, (long long)lr.total};
             __syncthreads();
-            write_final(S, p, p.D - 1, lr.src, lr.n, S.stage);
+            write_final<WT>(S, p, p.D - 1, lr.src, lr.n, S.stage);
         } else {
             __syncthreads();               // S.lvl of the overflowing level
-            const long long staged = sweep_chunks(S, p, ra, nr, lr);
+            const long long staged = sweep_chunks<WT>(S, p, ra, nr, lr);
             if (threadIdx.x == 0) p.tiles[t] = TileInfo{-1, staged};
         }
         __syncthreads();                   // per-ray counts complete
@@ -618,28 +605,44 @@ __global__ void __launch_bounds__(kPlaceThreads) k_place(const TileInfo* __restr
                 }
                 const long long src = (long long)ray_from[lo] + (e - ray_pre[lo]);
                 voxel_id[off + e] = p.stage_vid[src];
-                t_range[off + e] = p.stage_tr[src];
+                if (t_range) t_range[off + e] = p.stage_tr[src];
             }
             __syncthreads();
             continue;
         }
-        for (int i0 = threadIdx.x; i0 < cnt; i0 += 4 * kPlaceThreads) {
-            int32_t v[4];
-            float2 tr[4];
+        if (t_range) {
+            for (int i0 = threadIdx.x; i0 < cnt; i0 += 4 * kPlaceThreads) {
+                int32_t v[4];
+                float2 tr[4];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int i = i0 + u * kPlaceThreads;
-                if (i < cnt) {
-                    v[u] = p.stage_vid[st + i];
-                    tr[u] = p.stage_tr[st + i];
+                for (int u = 0; u < 4; ++u) {
+                    const int i = i0 + u * kPlaceThreads;
+                    if (i < cnt) {
+                        v[u] = p.stage_vid[st + i];
+                        tr[u] = p.stage_tr[st + i];
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int i = i0 + u * kPlaceThreads;
+                    if (i < cnt) {
+                        voxel_id[off + i] = v[u];
+                        t_range[off + i] = tr[u];
+                    }
                 }
             }
+        } else {
+            for (int i0 = threadIdx.x; i0 < cnt; i0 += 8 * kPlaceThreads) {
+                int32_t v[8];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int i = i0 + u * kPlaceThreads;
-                if (i < cnt) {
-                    voxel_id[off + i] = v[u];
-                    t_range[off + i] = tr[u];
+                for (int u = 0; u < 8; ++u) {
+                    const int i = i0 + u * kPlaceThreads;
+                    if (i < cnt) v[u] = p.stage_vid[st + i];
+                }
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int i = i0 + u * kPlaceThreads;
+                    if (i < cnt) voxel_id[off + i] = v[u];
                 }
             }
         }
@@ -659,9 +662,12 @@ int traverse_ctas_per_sm() {
     cudaGetDevice(&dev);
     std::atomic<int>& c = cached[dev & 63];
     if (!c.load(std::memory_order_acquire)) {
-        cudaFuncSetAttribute(k_traverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TileSmem));
-        int n = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_traverse, kThreads, sizeof(TileSmem));
+        cudaFuncSetAttribute(k_traverse<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TileSmem));
+        cudaFuncSetAttribute(k_traverse<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TileSmem));
+        int n = 0, n2 = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_traverse<true>, kThreads, sizeof(TileSmem));
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n2, k_traverse<false>, kThreads, sizeof(TileSmem));
+        n = std::min(n, n2);
         c.store(n > 0 ? n : 1, std::memory_order_release);
     }
     return c.load(std::memory_order_acquire);
@@ -707,8 +713,7 @@ int enqueue_traversal(const nglod_svo* svo, const float* o, const float* d, int6
         return NGLOD_OK;
     }
     if (!o || !d) return fail(NGLOD_ERR_INVALID_ARG, w + ": NULL rays");
-    if ((hit_capacity > 0 && (!voxel_id || !t_range)))
-        return fail(NGLOD_ERR_INVALID_ARG, w + ": NULL voxel_id / t_range");
+    if (hit_capacity > 0 && !voxel_id) return fail(NGLOD_ERR_INVALID_ARG, w + ": NULL voxel_id");
 
     const long long ntiles = num_tiles(R);
     char* wp = (char*)work + align_up(sizeof(Counters));
@@ -733,13 +738,16 @@ int enqueue_traversal(const nglod_svo* svo, const float* o, const float* d, int6
     p.ray_cnt = ray_cnt;
     p.ray_src = ray_src;
     p.stage_vid = stage_vid;
-    p.stage_tr = stage_tr;
+    p.stage_tr = t_range ? stage_tr : nullptr;
     p.tiles = tiles;
     p.ctr = ctr;
     const int sms = svo->num_sms;
     const int occ = traverse_ctas_per_sm();
     const long long grid = std::min<long long>(ntiles, (long long)sms * (ctas_per_sm > 0 ? std::min(ctas_per_sm, occ) : occ));
-    k_traverse<<<(unsigned)grid, kThreads, sizeof(TileSmem), st>>>(p);
+    if (t_range)
+        k_traverse<true><<<(unsigned)grid, kThreads, sizeof(TileSmem), st>>>(p);
+    else
+        k_traverse<false><<<(unsigned)grid, kThreads, sizeof(TileSmem), st>>>(p);
     k_tile_scan<<<1, kScanThreads, 0, st>>>(tiles, ntiles, ctr, hit_capacity, D);
     k_place<<<(unsigned)std::min<long long>(ntiles, (long long)sms * 8), kPlaceThreads, 0, st>>>(
         tiles, p, ray_cnt, ray_offsets, voxel_id, (float2*)t_range);

@@ -59,15 +59,15 @@ class FrameRenderer:
         for rs, re_ in zip(self.bounds[:-1], self.bounds[1:]):
             m = re_ - rs
             # sizing pass: the lists of this chunk fix its capacities
-            lists = ng.svo_trace_rays(svo, self.o[rs:re_], self.d[rs:re_], self.lod)
+            lists = ng.svo_trace_rays(svo, self.o[rs:re_], self.d[rs:re_], self.lod, t_range=False)
             cap = int(lists.voxel_id.numel() * headroom) + 4096
             c = dict(rs=rs, n=m, cap=cap, stream=torch.cuda.Stream(device=dev),
                      twork=torch.empty(L.svo_trace_rays_workspace(m, cap), dtype=torch.uint8, device=dev),
                      offs=torch.empty(m + 1, dtype=torch.int32, device=dev),
                      vid=torch.empty(cap, dtype=torch.int32, device=dev),
-                     tr=torch.empty((cap, 2), dtype=torch.float32, device=dev),
                      swork=torch.empty(L.sphere_trace_workspace(m), dtype=torch.uint8, device=dev))
-            c["lists"] = ng.RayLists(c["offs"], c["vid"], c["tr"], 0, self.lod, c["twork"])
+            # no t ranges in the lists: the tracers recompute each entry's interval
+            c["lists"] = ng.RayLists(c["offs"], c["vid"], None, 0, self.lod, c["twork"])
             c["outs"] = dict(t=self.out["t"][rs:re_], hit=self.out["hit"][rs:re_], steps=self.out["steps"][rs:re_],
                              normal=self.out["normal"][rs:re_] if normals else None, work=c["swork"])
             self.chunks.append(c)
@@ -79,7 +79,7 @@ class FrameRenderer:
         oo, dd = self.o[rs:re_], self.d[rs:re_]
         ng._check(L.svo_trace_rays_async_width(self.svo.h, oo.data_ptr(), dd.data_ptr(), c["n"], self.lod,
                                                c["twork"].data_ptr(), c["twork"].numel(), c["cap"],
-                                               c["offs"].data_ptr(), c["vid"].data_ptr(), c["tr"].data_ptr(), c["cap"],
+                                               c["offs"].data_ptr(), c["vid"].data_ptr(), None, c["cap"],
                                                self.trav_ctas_per_sm, C.c_void_p(st.cuda_stream)))
         if self.blend:
             ng.sphere_trace_blend(self.svo, self.feats, self.dec, self.dec_hi, oo, dd, c["lists"], self.lod_tilde,

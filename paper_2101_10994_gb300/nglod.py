@@ -371,7 +371,7 @@ class DecoderDev:
 class RayLists:
     ray_offsets: object      # int32 [R + 1]
     voxel_id: object         # int32 [H]
-    t_range: object          # float32 [H, 2]
+    t_range: object          # float32 [H, 2], or None (not asked for: the tracers do not read it)
     max_pairs: int
     lod: int
     work: object = None      # the workspace the lists were built in
@@ -385,8 +385,9 @@ class RayLists:
 
 
 def svo_trace_rays(svo: SVO, o, d, lod: int, stream=None, pair_capacity: int | None = None,
-                   workspace=None) -> RayLists:
-    """Per-ray front-to-back voxel lists at LOD ``lod`` (CSR).
+                   workspace=None, t_range: bool = True) -> RayLists:
+    """Per-ray front-to-back voxel lists at LOD ``lod`` (CSR), with each
+    entry's (t_enter, t_exit) unless ``t_range`` is False.
 
     Grows the intermediate-list capacity and retries when the library reports
     NGLOD_ERR_CAPACITY; the capacity that worked is remembered per (R, lod).
@@ -408,9 +409,9 @@ def svo_trace_rays(svo: SVO, o, d, lod: int, stream=None, pair_capacity: int | N
             work = torch.empty(max(wbytes, 1), dtype=torch.uint8, device=o.device)
         offs = torch.empty(R + 1, dtype=torch.int32, device=o.device)
         vid = torch.empty(max(cap, 1), dtype=torch.int32, device=o.device)
-        tr = torch.empty((max(cap, 1), 2), dtype=torch.float32, device=o.device)
+        tr = torch.empty((max(cap, 1), 2), dtype=torch.float32, device=o.device) if t_range else None
         rc = L.svo_trace_rays(svo.h, o.data_ptr(), d.data_ptr(), R, lod, work.data_ptr(), wbytes, cap,
-                              offs.data_ptr(), vid.data_ptr(), tr.data_ptr(), cap, stats,
+                              offs.data_ptr(), vid.data_ptr(), _ptr(tr), cap, stats,
                               C.c_void_p(_stream(stream)))
         if rc == ERR_CAPACITY:
             cap = int(max(2 * cap, 1.25 * max(stats[0], stats[1])))
@@ -418,7 +419,7 @@ def svo_trace_rays(svo: SVO, o, d, lod: int, stream=None, pair_capacity: int | N
         _check(rc)
         svo._cap[key] = cap
         H = int(stats[0])
-        return RayLists(offs, vid[:H], tr[:H], int(stats[1]), lod, work)
+        return RayLists(offs, vid[:H], tr[:H] if t_range else None, int(stats[1]), lod, work)
     raise NglodError(ERR_CAPACITY, "svo_trace_rays: capacity growth did not converge")
 
 
@@ -467,7 +468,7 @@ def sphere_trace(svo: SVO, feats: Features, dec: DecoderDev, o, d, lists: RayLis
     fc, dc = feats.c(), dec.c()
     _check(lib().sphere_trace(svo.h, C.byref(fc), C.byref(dc), o.data_ptr(), d.data_ptr(), R, lists.lod,
                               C.byref(p), lists.ray_offsets.data_ptr(), lists.voxel_id.data_ptr(),
-                              lists.t_range.data_ptr(), out["work"].data_ptr(), out["work"].numel(),
+                              _ptr(lists.t_range), out["work"].data_ptr(), out["work"].numel(),
                               out["t"].data_ptr(), out["hit"].data_ptr(), _ptr(out["steps"]),
                               _ptr(out["normal"]), C.c_void_p(_stream(stream))))
     out["hit_voxel"] = out["work"][256:256 + 4 * R].view(torch.int32)
@@ -548,7 +549,7 @@ def sphere_trace_blend(svo: SVO, feats: Features, dec_lo: DecoderDev, dec_hi: De
     hi = (dec_hi or dec_lo).c()
     _check(lib().sphere_trace_blend(svo.h, C.byref(fc), C.byref(lo), C.byref(hi), o.data_ptr(), d.data_ptr(), R,
                                     lod_tilde, C.byref(p), lists.ray_offsets.data_ptr(), lists.voxel_id.data_ptr(),
-                                    lists.t_range.data_ptr(), out["work"].data_ptr(), out["work"].numel(),
+                                    _ptr(lists.t_range), out["work"].data_ptr(), out["work"].numel(),
                                     out["t"].data_ptr(), out["hit"].data_ptr(), _ptr(out["steps"]),
                                     _ptr(out["normal"]), C.c_void_p(_stream(stream))))
     out["hit_voxel"] = out["work"][256:256 + 4 * R].view(torch.int32)

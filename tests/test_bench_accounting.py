@@ -31,9 +31,10 @@ def test_flops_per_query(bench):
 
 
 def test_traversal_bytes(bench):
-    # 2 rays; Decide visits 2 + 3 pairs at depths 0..1; 4 final entries at depth 2
+    # 2 rays; Decide visits 2 + 3 pairs at depths 0..1; 4 final entries (voxel
+    # ids only: the frame's lists carry no t ranges) at depth 2
     sizes = [2, 3, 4]
-    assert bench.traversal_bytes(None, sizes) == 36 * 2 + 16 * (2 + 3) + 36 * 4
+    assert bench.traversal_bytes(None, sizes) == 36 * 2 + 16 * (2 + 3) + 12 * 4
 
 
 def test_job_rate(bench):

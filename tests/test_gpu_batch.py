@@ -59,7 +59,6 @@ def assert_same(r, lists, ref, bufs=None):
         H = lists.voxel_id.numel()
         assert torch.equal(bufs["offs"].cpu(), lists.ray_offsets.cpu())
         assert torch.equal(bufs["vid"][:H].cpu(), lists.voxel_id.cpu())
-        assert torch.equal(bufs["tr"][:H].cpu().view(torch.int32), lists.t_range.cpu().view(torch.int32))
 
 
 @pytest.fixture(scope="module")

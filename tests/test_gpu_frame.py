@@ -41,7 +41,6 @@ def test_chunked_frame_equals_single_pass(ng, decode, chunks):
         L = ng.svo_trace_rays(svo, to[c["rs"]:c["rs"] + n], td[c["rs"]:c["rs"] + n], 5)
         H = L.voxel_id.numel()
         assert torch.equal(c["offs"], L.ray_offsets) and torch.equal(c["vid"][:H], L.voxel_id)
-        assert torch.equal(c["tr"][:H].view(torch.int32), L.t_range.view(torch.int32))
     # rays and results through pinned host buffers, copied chunk by chunk
     h_in = (torch.from_numpy(o).pin_memory(), torch.from_numpy(d).pin_memory())
     h_out = {"t": torch.empty(len(o)).pin_memory(), "hit": torch.empty(len(o), dtype=torch.uint8).pin_memory(),

@@ -228,3 +228,39 @@ def test_bf16_query_within_rounding_bound(ng, oracle_mod):
         assert np.all(err <= bound + 1e-5), (err - bound).max()
         assert bound.max() < 0.05
     svo.free()
+
+
+@pytest.mark.parametrize("decode", ["f32", "bf16", "f32tc"])
+def test_entry_intervals_recomputed_bit_exact(ng, decode):
+    # The tracers do not read the lists' t ranges: each entry's [t_enter,
+    # t_exit] is recomputed from its voxel with the traversal's FP32 slab
+    # test.  With eps above every distance a ray stops at its first decode,
+    # i.e. at t = its first entry's t_enter (Sec. 3.4: t starts at the first
+    # voxel), so t_hit must equal the traversal's t_range bit for bit; rays
+    # starting inside occupied voxels (t_enter = 0) are included.
+    sc, oc = S.csg_workload(64, seed=0, max_lod=5)
+    svo = ng.svo_build(oc.keys)
+    F = ng.Features(S.readout_features(oc, sc))
+    dec = ng.DecoderDev.from_decoder(S.readout_decoder(5))
+    o, d, _ = S.camera_rays(256, 256, tile=8)
+    rng = np.random.default_rng(4)
+    inside = S.points_in_voxels(oc, 7, 4000, 5).astype(np.float32)
+    dirs = rng.normal(size=(4000, 3))
+    dirs = (dirs / np.linalg.norm(dirs, axis=1, keepdims=True)).astype(np.float32)
+    o = np.concatenate([o, inside])
+    d = np.concatenate([d, dirs])
+    to, td = torch.from_numpy(o).cuda(), torch.from_numpy(d).cuda()
+    lists = ng.svo_trace_rays(svo, to, td, 5)
+    out = ng.sphere_trace(svo, F, dec, to, td, lists, eps=1e9, far=1e9, max_steps=1, decode=decode, normals=False)
+    ng.sphere_trace_status(out)
+    offs = lists.ray_offsets.cpu().numpy()
+    tr = lists.t_range.cpu().numpy()
+    nonempty = offs[1:] > offs[:-1]
+    assert nonempty.sum() > 20000 and nonempty[-4000:].sum() > 3000
+    hit = out["hit"].cpu().numpy().astype(bool)
+    assert np.array_equal(hit, nonempty)
+    t = out["t"].cpu().numpy()
+    first = tr[offs[:-1][nonempty], 0]
+    assert np.array_equal(t[nonempty].view(np.uint32), first.view(np.uint32))
+    assert np.sum(first == 0) > 3000           # the rays starting inside occupied voxels
+    svo.free()

@@ -106,6 +106,10 @@ def test_full_size_1080p_lod5_sampled(ng, oracle_mod):
     assert np.all(np.diff(g[0]) >= 0) and g[0][-1] == len(g[1])
     assert g[1].min() >= 0 and g[1].max() < oc.counts()[7]
     assert np.all(g[2][:, 0] <= g[2][:, 1])
+    # the frame renderer's variant (no t ranges): identical CSR lists
+    L2 = ng.svo_trace_rays(svo, torch.from_numpy(o).cuda(), torch.from_numpy(d).cuda(), 5, t_range=False)
+    np.testing.assert_array_equal(L2.ray_offsets.cpu().numpy(), g[0])
+    np.testing.assert_array_equal(L2.voxel_id.cpu().numpy(), g[1])
 
 
 def test_dense_grid_frontier_overflow_path(ng, oracle_mod):
@@ -155,6 +159,13 @@ def test_dense_grid_every_overflow_path(ng, oracle_mod):
     sizes = g[3].level_sizes()
     assert sizes[0] == len(o)
     assert sizes[3:] == [int(v) for v in P.sum(0)[3:]]
+    # without t ranges (the kernel variant the frame renderer runs): the same
+    # lists and level sizes on every path
+    L2 = ng.svo_trace_rays(svo, torch.from_numpy(o).cuda(), torch.from_numpy(d).cuda(), 4, t_range=False)
+    assert L2.t_range is None
+    np.testing.assert_array_equal(L2.ray_offsets.cpu().numpy(), g[0])
+    np.testing.assert_array_equal(L2.voxel_id.cpu().numpy(), g[1])
+    assert L2.level_sizes() == sizes
     svo.free()
 
 
