@@ -389,16 +389,22 @@ __global__ void __launch_bounds__(kTM, kCtasPerSm) k_trace_bf16(const DecPtrsB d
         if (wact) {
             const int g4 = lane >> 2, l4 = lane & 3, gb4 = g4 << 2;
             const unsigned gm4 = 0xfu << gb4;
+            // the warp's active slots, compacted: group g4 of round r takes
+            // the (8 r + g4)-th, so a warp with na rays gathers in
+            // ceil(na / 8) rounds (the rows of idle slots keep their last,
+            // finite values; their results are not used)
+            const unsigned am = __ballot_sync(0xffffffffu, act);
             // the first level's corner ids of the next round's slot are
-            // fetched while this round's slot is gathered
+            // fetched while this round's slot is gathered (ns = 32: no slot)
             // (every shuffle here runs on all 32 lanes: only the loads are conditional)
-            int nact = __shfl_sync(0xffffffffu, act ? 1 : 0, g4);
-            const int vox0 = __shfl_sync(0xffffffffu, st.vox, g4);
-            int2 nids = nact ? __ldg(corner_ids(tb, A.D, vox0, d0, l4)) : make_int2(0, 0);
+            int ns = g4 < __popc(am) ? kth_set_bit(am, g4) : 32;
+            const int vox0 = __shfl_sync(0xffffffffu, st.vox, ns & 31);
+            int2 nids = ns < 32 ? __ldg(corner_ids(tb, A.D, vox0, d0, l4)) : make_int2(0, 0);
 #pragma unroll 1
             for (int r = 0; r < 4; ++r) {
-                const int s = r * 8 + g4;
-                const int sact = nact;
+                if (8 * r >= __popc(am)) break;
+                const int s = ns & 31;
+                const bool sact = ns < 32;
                 const int2 ids = nids;
                 const int svox = __shfl_sync(0xffffffffu, st.vox, s);
                 const uint32_t sijk = __shfl_sync(0xffffffffu, st.ijk, s);
@@ -406,14 +412,17 @@ __global__ void __launch_bounds__(kTM, kCtasPerSm) k_trace_bf16(const DecPtrsB d
                 const float s1 = __shfl_sync(0xffffffffu, q1, s);
                 const float s2 = __shfl_sync(0xffffffffu, q2, s);
                 if (r < 3) {
-                    nact = __shfl_sync(0xffffffffu, act ? 1 : 0, s + 8);
-                    const int nvox = __shfl_sync(0xffffffffu, st.vox, s + 8);
-                    if (nact) nids = __ldg(corner_ids(tb, A.D, nvox, d0, l4));
+                    const int k = 8 * (r + 1) + g4;
+                    ns = k < __popc(am) ? kth_set_bit(am, k) : 32;
+                    const int nvox = __shfl_sync(0xffffffffu, st.vox, ns & 31);
+                    if (ns < 32) nids = __ldg(corner_ids(tb, A.D, nvox, d0, l4));
                 }
-                float4 za = make_float4(0.f, 0.f, 0.f, 0.f), zb = za;
-                if (sact) gather_slot4_ids<T>(tb, A.D, svox, sijk, s0, s1, s2, gm4, gb4, l4, za, zb, ids);
-                put_any<PM>(S, warp * 32 + s, 2 * l4, za, dp.z_scale);
-                put_any<PM>(S, warp * 32 + s, 2 * l4 + 1, zb, dp.z_scale);
+                if (sact) {
+                    float4 za, zb;
+                    gather_slot4_ids<T>(tb, A.D, svox, sijk, s0, s1, s2, gm4, gb4, l4, za, zb, ids);
+                    put_any<PM>(S, warp * 32 + s, 2 * l4, za, dp.z_scale);
+                    put_any<PM>(S, warp * 32 + s, 2 * l4 + 1, zb, dp.z_scale);
+                }
             }
         }
         prefetch_next_ijk(st, A, tb);
@@ -808,21 +817,27 @@ __global__ void __launch_bounds__(kTM, kCtasPerSm) k_trace_blend_bf16(const DecP
         if (!__syncthreads_or(act)) break;
         const float x0 = fmaf(st.t, st.dx, st.ox), x1 = fmaf(st.t, st.dy, st.oy), x2 = fmaf(st.t, st.dz, st.oz);
         const float q0 = __fadd_rn(x0, 1.0f), q1 = __fadd_rn(x1, 1.0f), q2 = __fadd_rn(x2, 1.0f);
+        // the warp's active slots, compacted (as in k_trace_bf16); the rows
+        // of idle slots keep finite values whose results are not used
+        const unsigned am = __ballot_sync(0xffffffffu, act);
 #pragma unroll 1
         for (int r = 0; r < 4; ++r) {
-            const int s = r * 8 + g4;
-            const int sact = __shfl_sync(0xffffffffu, act ? 1 : 0, s);
+            if (8 * r >= __popc(am)) break;
+            const bool sact = 8 * r + g4 < __popc(am);
+            const int s = sact ? kth_set_bit(am, 8 * r + g4) : 0;
             const int svox = __shfl_sync(0xffffffffu, st.vox, s);
             const uint32_t sijk = __shfl_sync(0xffffffffu, st.ijk, s);
             const float s0 = __shfl_sync(0xffffffffu, q0, s);
             const float s1 = __shfl_sync(0xffffffffu, q1, s);
             const float s2 = __shfl_sync(0xffffffffu, q2, s);
-            float4 zl[2] = {make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f)}, zh[2] = {zl[0], zl[1]};
-            if (sact) gather_pair<T>(tb, A.D, A.D - 1, svox, sijk, s0, s1, s2, gm4, gb4, l4, zl, zh);
+            if (sact) {
+                float4 zl[2], zh[2];
+                gather_pair<T>(tb, A.D, A.D - 1, svox, sijk, s0, s1, s2, gm4, gb4, l4, zl, zh);
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                put_z<false>(S.lo, warp * 32 + s, 2 * l4 + h, zl[h], 1.0f);
-                put_z<false>(S.hi, warp * 32 + s, 2 * l4 + h, zh[h], 1.0f);
+                for (int h = 0; h < 2; ++h) {
+                    put_z<false>(S.lo, warp * 32 + s, 2 * l4 + h, zl[h], 1.0f);
+                    put_z<false>(S.hi, warp * 32 + s, 2 * l4 + h, zh[h], 1.0f);
+                }
             }
         }
         prefetch_next_ijk(st, A, tb);

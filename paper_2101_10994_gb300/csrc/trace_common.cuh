@@ -90,6 +90,21 @@ __device__ __forceinline__ float mlp_f32(const SmemDecoder& sd, float b2, const 
     return out;
 }
 
+// Position of the k-th (0-based) set bit of m; k < popc(m).
+__device__ __forceinline__ int kth_set_bit(unsigned m, int k) {
+    int pos = 0;
+#pragma unroll
+    for (int w = 16; w > 0; w >>= 1) {
+        const int c = __popc(m & ((1u << w) - 1u));
+        if (k >= c) {
+            k -= c;
+            m >>= w;
+            pos += w;
+        }
+    }
+    return pos;
+}
+
 struct TraceArgs {
     const float* o;
     const float* d;
