@@ -365,13 +365,14 @@ size_t sphere_trace_workspace(int64_t R);
  *                       the call, bytes [256, 256 + 4R) hold the int32 id (at
  *                       the target depth) of the voxel each hit ray stopped in,
  *                       -1 for misses, and int32 word 2 counts the hit rays,
- *                       whose ids follow (in no particular order) from byte
+ *                       whose ids follow (in increasing order, so that the
+ *                       normals visit neighbouring hits together) from byte
  *                       256 + 4R rounded up to 256; trace_normals reads them.
  *                       The rest holds the order in which 32-ray groups are
  *                       handed to the persistent trace (by decreasing longest
  *                       list, so long rays start early; it changes only the
- *                       schedule, never a ray's outputs) and, per hit-list
- *                       position, the ReLU mask of the hit's last decode
+ *                       schedule, never a ray's outputs) and, per ray, the
+ *                       ReLU mask of a hit's last decode
  *                       (128 bits), which trace_normals reuses (not with the
  *                       FP8 decode, whose 4-bit z can zero or flip a
  *                       pre-activation: its normals recompute the forward

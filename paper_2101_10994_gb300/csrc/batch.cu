@@ -330,6 +330,10 @@ extern "C" int sphere_trace_batch_run(nglod_batch* b, void* stream) {
         rc = launch_trace_batch_tc(b->d_jobs, b->d_groups, b->ngroups, b->in_dim, b->f16, b->decode == NGLOD_FP8E4M3,
                                    b->ctas_per_sm, b->sms, b->d_words + b->ngroups, st);
     if (rc) return rc;
+    // each job's hit list in ray order (A.queue is the start of the job's
+    // trace workspace)
+    for (int j = 0; j < b->njobs; ++j)
+        if (b->h_jobs[j].A.R > 0 && (rc = enqueue_hit_order(b->h_jobs[j].A, b->h_jobs[j].A.queue, st))) return rc;
     if (b->want_normals) {
         for (int j = 0; j < b->njobs; ++j) {
             if (!b->normals[j] || b->h_jobs[j].A.R == 0) continue;

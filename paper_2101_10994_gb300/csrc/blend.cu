@@ -130,6 +130,7 @@ extern "C" int sphere_trace_blend(const nglod_svo* svo, const nglod_features* fe
     else
         return fail(NGLOD_ERR_NOT_SUPPORTED, "sphere_trace_blend: decode_dtype must be F32 or BF16 when blending");
     if (rc) return rc;
+    if ((rc = enqueue_hit_order(A, work, st))) return rc;
     if (normal && params->want_normals)
         return params->normal_mode == NGLOD_NORMALS_FD
                    ? launch_normals_blend_fd(dec_lo, dec_hi, alpha, tb, A, params->fd_h, normal, f16, svo->num_sms, st)

@@ -211,7 +211,7 @@ struct GradArgs {
     const int32_t* hit_vox;
     const int* hit_count;  // mode 1: number of entries in hit_list
     const int32_t* hit_list;
-    const uint4* hit_mask;  // mode 1: the tracer's ReLU mask per hit-list position (used if *mask_flag)
+    const uint4* hit_mask;  // modes 1, 2: the tracer's ReLU mask per ray (used if *mask_flag)
     const int* mask_flag;
     long long n;           // mode 0: Q
     int D;
@@ -297,7 +297,7 @@ __global__ void __launch_bounds__(kThreads) k_grad(const DecPtrs dp, const Table
 #pragma unroll
         for (int k = 0; k < K4; ++k) gv[k] = 0.0f;
         if (use_mask) {
-            const uint4 mk = act ? A.hit_mask[it] : make_uint4(0u, 0u, 0u, 0u);
+            const uint4 mk = act ? A.hit_mask[ray] : make_uint4(0u, 0u, 0u, 0u);
 #pragma unroll 1
             for (int c = 0; c < 4; ++c) {
                 const uint32_t bits = c == 0 ? mk.x : c == 1 ? mk.y : c == 2 ? mk.z : mk.w;
@@ -1080,6 +1080,76 @@ int enable_hit_masks(TraceArgs& A, void* work, cudaStream_t st, bool two) {
     return NGLOD_OK;
 }
 
+namespace {
+
+// Hit list in ray order: blocks of kHitBlock rays, 16 consecutive rays a
+// thread; k_hit_counts counts each block's hits, k_hit_scan turns the
+// counts into block offsets, k_hit_place writes the hit rays' ids.
+constexpr int kHitThreads = 256;
+constexpr int kHitPerThread = 16;
+constexpr long long kHitBlock = (long long)kHitThreads * kHitPerThread;
+
+__device__ __forceinline__ int thread_hits(const uint8_t* __restrict__ hit, long long R, long long r0) {
+    int c = 0;
+#pragma unroll
+    for (int j = 0; j < kHitPerThread; ++j) c += (r0 + j < R && hit[r0 + j]) ? 1 : 0;
+    return c;
+}
+
+__global__ void __launch_bounds__(kHitThreads) k_hit_counts(const uint8_t* __restrict__ hit, long long R,
+                                                            int* __restrict__ cnt) {
+    __shared__ int ws[33];
+    const long long r0 = (long long)blockIdx.x * kHitBlock + (long long)threadIdx.x * kHitPerThread;
+    int total;
+    block_exclusive_sum(thread_hits(hit, R, r0), ws, total);
+    if (threadIdx.x == 0) cnt[blockIdx.x] = total;
+}
+
+// Exclusive prefix of the n block counts, in place (one block).
+__global__ void __launch_bounds__(1024) k_hit_scan(int* __restrict__ cnt, long long n) {
+    __shared__ int ws[33];
+    __shared__ int carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (long long b0 = 0; b0 < n; b0 += blockDim.x) {
+        const long long i = b0 + threadIdx.x;
+        const int v = i < n ? cnt[i] : 0;
+        int total;
+        const int e = block_exclusive_sum(v, ws, total);
+        if (i < n) cnt[i] = carry + e;
+        __syncthreads();
+        if (threadIdx.x == 0) carry += total;
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(kHitThreads) k_hit_place(const uint8_t* __restrict__ hit, long long R,
+                                                           const int* __restrict__ off, int32_t* __restrict__ list) {
+    __shared__ int ws[33];
+    const long long r0 = (long long)blockIdx.x * kHitBlock + (long long)threadIdx.x * kHitPerThread;
+    int total;
+    int pos = off[blockIdx.x] + block_exclusive_sum(thread_hits(hit, R, r0), ws, total);
+#pragma unroll
+    for (int j = 0; j < kHitPerThread; ++j)
+        if (r0 + j < R && hit[r0 + j]) list[pos++] = (int32_t)(r0 + j);
+}
+
+}  // namespace
+
+int enqueue_hit_order(const TraceArgs& A, void* work, cudaStream_t st) {
+    const long long R = A.R;
+    if (R <= 0) return NGLOD_OK;
+    const long long nb = (R + kHitBlock - 1) / kHitBlock;
+    // the ray-group order of the finished trace is no longer needed: its
+    // region (R / 32 ints) holds the block counts
+    int* cnt = reinterpret_cast<int*>(static_cast<char*>(work) + trace_ws_order_offset(R));
+    k_hit_counts<<<(unsigned)nb, kHitThreads, 0, st>>>(A.hit, R, cnt);
+    k_hit_scan<<<1, 1024, 0, st>>>(cnt, nb);
+    k_hit_place<<<(unsigned)nb, kHitThreads, 0, st>>>(A.hit, R, cnt, A.hit_list);
+    NGLOD_CUDA(cudaGetLastError());
+    return NGLOD_OK;
+}
+
 int enqueue_ray_order(TraceArgs& A, void* work, const Node* node_D, cudaStream_t st) {
     const long long R = A.R, G = (R + 31) / 32;
     char* w = static_cast<char*>(work);
@@ -1177,6 +1247,7 @@ extern "C" int sphere_trace(const nglod_svo* svo, const nglod_features* feats, c
         return fail(NGLOD_ERR_NOT_SUPPORTED, "sphere_trace: decode_dtype must be F32, BF16, FP8E4M3 or F32_SPLIT");
     }
     if (rc) return rc;
+    if ((rc = enqueue_hit_order(A, work, st))) return rc;
     if (normal && params->want_normals) {
         rc = params->normal_mode == NGLOD_NORMALS_FD
                  ? launch_normals_fd(dec, tb, A, params->fd_h, normal, f16, svo->num_sms, st)

@@ -127,8 +127,8 @@ struct TraceArgs {
     // index order); longest-working groups first shortens the frame's tail
     const int32_t* order = nullptr;
     // workspace: the ReLU mask (bit h: pre_h > 0) of each hit's last decode,
-    // at its hit-list position (null: not recorded); the normals need no
-    // forward pass then
+    // indexed by ray (null: not recorded); the normals need no forward pass
+    // then
     uint4* hit_mask = nullptr;
     uint4* hit_mask2 = nullptr;   // level blending: the second decoder's masks
     int ctas_per_sm = 0;          // launch width of the persistent trace (0: the most that fit)
@@ -193,8 +193,8 @@ __device__ __forceinline__ void publish_hits(RaySlot& S, const TraceArgs& A, int
         if (S.hit_ray >= 0) {
             const int pos = base + __popc(m & ((1u << lane) - 1u));
             A.hit_list[pos] = S.hit_ray;
-            if (A.hit_mask) A.hit_mask[pos] = mask;
-            if (A.hit_mask2) A.hit_mask2[pos] = mask2;
+            if (A.hit_mask) A.hit_mask[S.hit_ray] = mask;
+            if (A.hit_mask2) A.hit_mask2[S.hit_ray] = mask2;
         }
     }
     S.hit_ray = -1;
@@ -387,7 +387,7 @@ __device__ __forceinline__ void publish_hits_batch(RaySlot& S, const TraceJob* _
         const TraceArgs& A = jobs[S.job].A;
         const int pos = atomicAdd(A.hit_count, 1);
         A.hit_list[pos] = S.hit_ray;
-        if (A.hit_mask) A.hit_mask[pos] = mask;
+        if (A.hit_mask) A.hit_mask[S.hit_ray] = mask;
     }
     S.hit_ray = -1;
 }
@@ -422,7 +422,7 @@ inline size_t trace_ws_key_offset(long long R) {
     return trace_ws_order_offset(R) + trace_ws_align(sizeof(int32_t) * (size_t)((R + 31) / 32));
 }
 inline size_t trace_ws_count_offset(long long R) { return trace_ws_key_offset(R) + trace_ws_align((size_t)((R + 31) / 32)); }
-// ... then the hits' ReLU masks (16 B per hit-list position); header word 3
+// ... then the hits' ReLU masks (16 B per ray); header word 3
 // is nonzero when the last trace recorded them
 inline size_t trace_ws_mask_offset(long long R) {
     return trace_ws_count_offset(R) + trace_ws_align(2 * kOrderBuckets * sizeof(int));
@@ -435,6 +435,10 @@ inline size_t trace_ws_size(long long R) { return trace_ws_start_offset(R) + 16 
 constexpr int kWsMaskFlagWord = 3;
 // Points A at the workspace's mask region(s) and marks them as recorded.
 int enable_hit_masks(TraceArgs& A, void* work, cudaStream_t st, bool two = false);
+// Rewrites the finished trace's hit list (hit_count ids) in ray order from
+// the per-ray hit flags A.hit, so that the normals visit neighbouring hits
+// together (the ray-order scratch of the workspace holds the block counts).
+int enqueue_hit_order(const TraceArgs& A, void* work, cudaStream_t st);
 // Enqueues the work-ordered ray-group handout of a trace (sets A.order) and
 // the rays' first-entry records (sets A.start; node_D = the nodes of the
 // lists' depth).

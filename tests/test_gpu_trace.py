@@ -264,3 +264,33 @@ def test_entry_intervals_recomputed_bit_exact(ng, decode):
     assert np.array_equal(t[nonempty].view(np.uint32), first.view(np.uint32))
     assert np.sum(first == 0) > 3000           # the rays starting inside occupied voxels
     svo.free()
+
+
+@pytest.mark.parametrize("decode", ["f32", "bf16", "fp8"])
+def test_hit_list_in_ray_order(ng, decode):
+    # after a trace the workspace holds the hit rays' ids in increasing order
+    # (int32 word 2 = their count; the list starts at 256 + 4R rounded up to
+    # 256), and the normals computed from it equal the ones of a second
+    # trace_normals call over the same workspace
+    sc, oc = S.csg_workload(64, seed=0, max_lod=5)
+    svo = ng.svo_build(oc.keys)
+    F = ng.Features(S.readout_features(oc, sc))
+    if decode == "fp8":
+        F.set_fp8_bound(svo, 5)
+    dec = ng.DecoderDev.from_decoder(S.readout_decoder(5))
+    o, d, _ = S.camera_rays(300, 200, tile=8)
+    to, td = torch.from_numpy(o).cuda(), torch.from_numpy(d).cuda()
+    lists = ng.svo_trace_rays(svo, to, td, 5, t_range=False)
+    out = ng.sphere_trace(svo, F, dec, to, td, lists, decode=decode, normals=True)
+    ng.sphere_trace_status(out)
+    R = len(o)
+    w = out["work"].cpu().numpy().view(np.int32)
+    n = int(w[2])
+    start = (256 + 4 * R + 255) // 256 * 256 // 4
+    hit = out["hit"].cpu().numpy().astype(bool)
+    assert n == hit.sum() > 1000
+    np.testing.assert_array_equal(w[start:start + n], np.flatnonzero(hit))
+    again = dict(out, normal=torch.empty_like(out["normal"]))
+    ng.trace_normals(svo, F, dec, to, td, lists, again)
+    assert torch.equal(again["normal"], out["normal"])
+    svo.free()
