@@ -1089,11 +1089,22 @@ constexpr int kHitThreads = 256;
 constexpr int kHitPerThread = 16;
 constexpr long long kHitBlock = (long long)kHitThreads * kHitPerThread;
 
-__device__ __forceinline__ int thread_hits(const uint8_t* __restrict__ hit, long long R, long long r0) {
-    int c = 0;
+// Bit j of the result is set iff ray r0 + j (< R) hit; one 16-byte load
+// where the 16 flags are aligned and in range.
+__device__ __forceinline__ uint32_t thread_hit_bits(const uint8_t* __restrict__ hit, long long R, long long r0) {
+    uint32_t bits = 0u;
+    if (r0 + kHitPerThread <= R && ((reinterpret_cast<uintptr_t>(hit + r0) & 15u) == 0)) {
+        const uint4 v = *reinterpret_cast<const uint4*>(hit + r0);
+        const uint32_t w[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-    for (int j = 0; j < kHitPerThread; ++j) c += (r0 + j < R && hit[r0 + j]) ? 1 : 0;
-    return c;
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) bits |= (((w[q] >> (8 * b)) & 0xffu) ? 1u : 0u) << (4 * q + b);
+    } else {
+#pragma unroll
+        for (int j = 0; j < kHitPerThread; ++j) bits |= (r0 + j < R && hit[r0 + j]) ? (1u << j) : 0u;
+    }
+    return bits;
 }
 
 __global__ void __launch_bounds__(kHitThreads) k_hit_counts(const uint8_t* __restrict__ hit, long long R,
@@ -1101,7 +1112,7 @@ __global__ void __launch_bounds__(kHitThreads) k_hit_counts(const uint8_t* __res
     __shared__ int ws[33];
     const long long r0 = (long long)blockIdx.x * kHitBlock + (long long)threadIdx.x * kHitPerThread;
     int total;
-    block_exclusive_sum(thread_hits(hit, R, r0), ws, total);
+    block_exclusive_sum(__popc(thread_hit_bits(hit, R, r0)), ws, total);
     if (threadIdx.x == 0) cnt[blockIdx.x] = total;
 }
 
@@ -1128,10 +1139,9 @@ __global__ void __launch_bounds__(kHitThreads) k_hit_place(const uint8_t* __rest
     __shared__ int ws[33];
     const long long r0 = (long long)blockIdx.x * kHitBlock + (long long)threadIdx.x * kHitPerThread;
     int total;
-    int pos = off[blockIdx.x] + block_exclusive_sum(thread_hits(hit, R, r0), ws, total);
-#pragma unroll
-    for (int j = 0; j < kHitPerThread; ++j)
-        if (r0 + j < R && hit[r0 + j]) list[pos++] = (int32_t)(r0 + j);
+    uint32_t bits = thread_hit_bits(hit, R, r0);
+    int pos = off[blockIdx.x] + block_exclusive_sum(__popc(bits), ws, total);
+    for (; bits; bits &= bits - 1u) list[pos++] = (int32_t)(r0 + __ffs(bits) - 1);
 }
 
 }  // namespace

@@ -495,8 +495,19 @@ __global__ void __launch_bounds__(kThreads, 4) k_traverse(const TileParams p) {
     }
 }
 
-// Exclusive sum of the tile counts, in place over TileInfo::count (one CTA);
-// the grand total is the hit count H.
+// Exclusive sum of the tile counts, in place over TileInfo::count (one CTA,
+// kScanPer consecutive tiles a thread); the grand total is the hit count H.
+constexpr int kScanPer = 16;
+
+__device__ __forceinline__ long long warp_incl_scan_ll(long long v, int lane) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long y = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += y;
+    }
+    return v;
+}
+
 __global__ void __launch_bounds__(kScanThreads) k_tile_scan(TileInfo* __restrict__ tiles, long long ntiles,
                                                             Counters* __restrict__ ctr, long long hit_cap, int D) {
     __shared__ long long warp_sums[kScanThreads / 32 + 1];
@@ -504,30 +515,31 @@ __global__ void __launch_bounds__(kScanThreads) k_tile_scan(TileInfo* __restrict
     if (threadIdx.x == 0) carry = 0;
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (long long b0 = 0; b0 < ntiles; b0 += kScanThreads) {
-        const long long i = b0 + threadIdx.x;
-        const long long v = i < ntiles ? tiles[i].count : 0;
-        long long incl = v;
+    for (long long b0 = 0; b0 < ntiles; b0 += (long long)kScanThreads * kScanPer) {
+        const long long i0 = b0 + (long long)threadIdx.x * kScanPer;
+        long long c[kScanPer];
+        long long sum = 0;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const long long y = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += y;
+        for (int j = 0; j < kScanPer; ++j) {
+            c[j] = i0 + j < ntiles ? tiles[i0 + j].count : 0;
+            sum += c[j];
         }
+        const long long incl = warp_incl_scan_ll(sum, lane);
         if (lane == 31) warp_sums[warp] = incl;
         __syncthreads();
         if (warp == 0) {
             const long long s = warp_sums[lane];
-            long long si = s;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const long long y = __shfl_up_sync(0xffffffffu, si, o);
-                if (lane >= o) si += y;
-            }
+            const long long si = warp_incl_scan_ll(s, lane);
             warp_sums[lane] = si - s;
             if (lane == 31) warp_sums[32] = si;
         }
         __syncthreads();
-        if (i < ntiles) tiles[i].count = carry + warp_sums[warp] + incl - v;   // now the exclusive prefix
+        long long run = carry + warp_sums[warp] + incl - sum;     // this thread's first tile's prefix
+#pragma unroll
+        for (int j = 0; j < kScanPer; ++j) {
+            if (i0 + j < ntiles) tiles[i0 + j].count = run;        // now the exclusive prefix
+            run += c[j];
+        }
         __syncthreads();
         if (threadIdx.x == 0) carry += warp_sums[32];
         __syncthreads();
