@@ -287,11 +287,27 @@ __device__ __forceinline__ uint32_t child_hits8(const RayPrep& r, uint32_t ijk, 
     uint32_t allow = 0xffu;
     oct = 0;
     constexpr uint32_t kSide[3][2] = {{0x55u, 0xaau}, {0x33u, 0xccu}, {0x0fu, 0xf0u}};
+    // the planes and crossings of x and y as packed pairs (each lane
+    // rounded once, as the scalar operations)
+    const float2 lo_xy = __ffma2_rn(make_float2((float)c[0], (float)c[1]), make_float2(s, s), make_float2(-1.0f, -1.0f));
+    const float2 mid_xy = __fadd2_rn(lo_xy, make_float2(hs, hs));
+    const float2 hi_xy = __fadd2_rn(mid_xy, make_float2(hs, hs));
+    const float lo_z = __fmaf_rn((float)c[2], s, -1.0f);
+    const float mid_z = __fadd_rn(lo_z, hs);
+    const float hi_z = __fadd_rn(mid_z, hs);
+    const float2 no_xy = make_float2(-o[0], -o[1]), inv_xy = make_float2(inv[0], inv[1]);
+    const float2 tlo_xy = __fmul2_rn(__fadd2_rn(lo_xy, no_xy), inv_xy);
+    const float2 tmid_xy = __fmul2_rn(__fadd2_rn(mid_xy, no_xy), inv_xy);
+    const float2 thi_xy = __fmul2_rn(__fadd2_rn(hi_xy, no_xy), inv_xy);
+    const float2 tlm_z = __fmul2_rn(__fadd2_rn(make_float2(lo_z, mid_z), make_float2(-o[2], -o[2])),
+                                    make_float2(inv[2], inv[2]));
+    const float thi_z = __fmul_rn(__fsub_rn(hi_z, o[2]), inv[2]);
+    const float LO[3] = {lo_xy.x, lo_xy.y, lo_z}, MID[3] = {mid_xy.x, mid_xy.y, mid_z}, HI[3] = {hi_xy.x, hi_xy.y, hi_z};
+    const float TLO[3] = {tlo_xy.x, tlo_xy.y, tlm_z.x}, TMID[3] = {tmid_xy.x, tmid_xy.y, tlm_z.y},
+                THI[3] = {thi_xy.x, thi_xy.y, thi_z};
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        const float lo = __fmaf_rn((float)c[a], s, -1.0f);
-        const float mid = __fadd_rn(lo, hs);
-        const float hi = __fadd_rn(mid, hs);
+        const float lo = LO[a], mid = MID[a], hi = HI[a];
         oct |= (o[a] >= mid) ? (1u << a) : 0u;
         if ((r.par >> a) & 1) {
             allow &= ((lo <= o[a] && o[a] <= mid) ? kSide[a][0] : 0u) | ((mid <= o[a] && o[a] <= hi) ? kSide[a][1] : 0u);
@@ -299,9 +315,7 @@ __device__ __forceinline__ uint32_t child_hits8(const RayPrep& r, uint32_t ijk, 
             fr[a][0] = fr[a][1] = INFINITY;
             continue;
         }
-        const float t_lo = __fmul_rn(__fsub_rn(lo, o[a]), inv[a]);
-        const float t_mid = __fmul_rn(__fsub_rn(mid, o[a]), inv[a]);
-        const float t_hi = __fmul_rn(__fsub_rn(hi, o[a]), inv[a]);
+        const float t_lo = TLO[a], t_mid = TMID[a], t_hi = THI[a];
         if (WANT_T) {
             nr[a][0] = t_lo < t_mid ? t_lo : t_mid;
             fr[a][0] = t_lo < t_mid ? t_mid : t_lo;

@@ -495,9 +495,11 @@ __global__ void __launch_bounds__(kThreads, 4) k_traverse(const TileParams p) {
     }
 }
 
-// Exclusive sum of the tile counts, in place over TileInfo::count (one CTA,
-// kScanPer consecutive tiles a thread); the grand total is the hit count H.
-constexpr int kScanPer = 16;
+// Exclusive sum of the tile counts, in place over TileInfo::count (one CTA):
+// chunks of kScanChunk tiles staged in shared memory with coalesced loads,
+// kScanPer consecutive tiles a thread.
+constexpr int kScanPer = 4;
+constexpr int kScanChunk = kScanThreads * kScanPer;
 
 __device__ __forceinline__ long long warp_incl_scan_ll(long long v, int lane) {
 #pragma unroll
@@ -510,18 +512,22 @@ __device__ __forceinline__ long long warp_incl_scan_ll(long long v, int lane) {
 
 __global__ void __launch_bounds__(kScanThreads) k_tile_scan(TileInfo* __restrict__ tiles, long long ntiles,
                                                             Counters* __restrict__ ctr, long long hit_cap, int D) {
+    __shared__ long long buf[kScanChunk];
     __shared__ long long warp_sums[kScanThreads / 32 + 1];
     __shared__ long long carry;
     if (threadIdx.x == 0) carry = 0;
-    __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (long long b0 = 0; b0 < ntiles; b0 += (long long)kScanThreads * kScanPer) {
-        const long long i0 = b0 + (long long)threadIdx.x * kScanPer;
-        long long c[kScanPer];
-        long long sum = 0;
+    for (long long b0 = 0; b0 < ntiles; b0 += kScanChunk) {
 #pragma unroll
         for (int j = 0; j < kScanPer; ++j) {
-            c[j] = i0 + j < ntiles ? tiles[i0 + j].count : 0;
+            const long long i = b0 + j * kScanThreads + threadIdx.x;
+            buf[j * kScanThreads + threadIdx.x] = i < ntiles ? tiles[i].count : 0;
+        }
+        __syncthreads();
+        long long c[kScanPer], sum = 0;
+#pragma unroll
+        for (int j = 0; j < kScanPer; ++j) {
+            c[j] = buf[threadIdx.x * kScanPer + j];
             sum += c[j];
         }
         const long long incl = warp_incl_scan_ll(sum, lane);
@@ -534,13 +540,18 @@ __global__ void __launch_bounds__(kScanThreads) k_tile_scan(TileInfo* __restrict
             if (lane == 31) warp_sums[32] = si;
         }
         __syncthreads();
-        long long run = carry + warp_sums[warp] + incl - sum;     // this thread's first tile's prefix
+        long long run = carry + warp_sums[warp] + incl - sum;
 #pragma unroll
         for (int j = 0; j < kScanPer; ++j) {
-            if (i0 + j < ntiles) tiles[i0 + j].count = run;        // now the exclusive prefix
+            buf[threadIdx.x * kScanPer + j] = run;
             run += c[j];
         }
         __syncthreads();
+#pragma unroll
+        for (int j = 0; j < kScanPer; ++j) {
+            const long long i = b0 + j * kScanThreads + threadIdx.x;
+            if (i < ntiles) tiles[i].count = buf[j * kScanThreads + threadIdx.x];   // now the exclusive prefix
+        }
         if (threadIdx.x == 0) carry += warp_sums[32];
         __syncthreads();
     }
