@@ -139,7 +139,7 @@ __device__ __forceinline__ RayPrep prep_ray(const float* o, const float* d, long
 // neighbouring outputs, and a warp-wide scan per row keeps every output in
 // pair order.
 __device__ __forceinline__ void warp_range(int n, int& w0, int& w1) {
-    const int q = (n + kWarps - 1) / kWarps;
+    const int q = ((n + kWarps - 1) / kWarps + 31) & ~31;   // whole rows: idle warps issue nothing
     w0 = min((int)(threadIdx.x >> 5) * q, n);
     w1 = min(w0 + q, n);
 }
