@@ -481,11 +481,12 @@ def run_ours(args, rank, world, local_rank):
              "hit": torch.empty(R, dtype=torch.uint8).pin_memory(),
              "normal": torch.empty((R, 3), dtype=torch.float32).pin_memory()}
     # the renderer sizes its lists from the rays it is built on; every timed frame then
-    # brings its rays in from the host buffers (the device copies are cleared first)
-    ech, ecta, etcta = configs[mode]
-    fr = FrameRenderer(svo, feats, dec, o.clone(), d.clone(), W["lod"], chunks=ech, ctas_per_sm=ecta,
-                       trav_ctas_per_sm=etcta, eps=W["eps"], far=W["far"], max_steps=W["max_steps"], decode=mode,
-                       normals=True)
+    # brings its rays in from the host buffers (the device copies are cleared first).
+    # The schedule is tuned with the copies in (untimed): the one that hides them best
+    # can differ from the device-only frame's
+    fr, etune = autotune_frame(svo, feats, dec, o.clone(), d.clone(), W["lod"], host=((h_o, h_d), h_out),
+                               eps=W["eps"], far=W["far"], max_steps=W["max_steps"], decode=mode, normals=True)
+    ech, ecta, etcta = len(fr.chunks), fr.ctas_per_sm, fr.trav_ctas_per_sm
     e2e_ms = []
     for k in range(args.warmup + args.steps):
         flush.zero_()
@@ -504,7 +505,9 @@ def run_ours(args, rank, world, local_rank):
     e2e = dict(value=job_rate(R, world, e2e_ms_job * 1e-3), unit="rays/s",
                h2d_bytes_per_step=int(h_o.numel() * 4 + h_d.numel() * 4),
                d2h_bytes_per_step=int(sum(v.numel() * v.element_size() for v in h_out.values())),
-               schedule=f"{ech} chunks on {ech} streams, copies overlapped with the other chunks' work")
+               schedule=f"{ech} chunks on {ech} streams, trace CTAs/SM {ecta or 'max'}, traversal CTAs/SM "
+                        f"{etcta or 'max'}, copies overlapped with the other chunks' work (autotuned with the copies)",
+               autotune_ms_by_chunks_and_ctas=etune)
     svo.free()
     ceilings = measure_ceilings(dev)
     return W, results, clock_info, e2e, modes, ceilings

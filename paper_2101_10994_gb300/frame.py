@@ -23,12 +23,13 @@ class FrameRenderer:
                  eps: float = 1e-3, far: float = 5.0, max_steps: int = 128, decode: str = "bf16",
                  normals: bool = True, headroom: float = 1.25, dec_hi: ng.DecoderDev | None = None,
                  normal_mode: str = "analytic", fd_h: float = 1e-3, ctas_per_sm: int = 0,
-                 trav_ctas_per_sm: int = 0):
+                 trav_ctas_per_sm: int = 0, weights=None):
         """lod: an integer LOD, or a continuous L~ (Eq. 3) with dec = LOD floor(L~)'s decoder and
         dec_hi = LOD floor(L~) + 1's; rays then walk their lists at ceil(L~).
         ctas_per_sm / trav_ctas_per_sm: resident CTAs per SM of the persistent trace / traversal
         kernels (0: the most that fit); narrower launches leave room on each SM for the other
-        chunks' kernels."""
+        chunks' kernels.  weights: relative chunk sizes (default equal); smaller first and last
+        chunks shorten the stretches where only one chunk's stage runs."""
         import torch
         self.torch = torch
         self.lod_tilde = float(lod)
@@ -47,7 +48,11 @@ class FrameRenderer:
         dev = self.o.device
         # chunk bounds on multiples of 128 rays (the traversal's tile)
         n = max(1, int(chunks))
-        self.bounds = sorted(set([min(R, R * i // n // 128 * 128) for i in range(n)] + [R]))
+        w = [1.0] * n if weights is None else [float(x) for x in weights]
+        if len(w) != n or min(w) <= 0:
+            raise ValueError("FrameRenderer: weights must be chunks positive numbers")
+        cum = [sum(w[:i]) / sum(w) for i in range(n)]
+        self.bounds = sorted(set([min(R, int(R * f) // 128 * 128) for f in cum] + [R]))
         if self.bounds[0] != 0:
             self.bounds = [0] + self.bounds
         self.out = dict(t=torch.empty(R, dtype=torch.float32, device=dev),
@@ -127,27 +132,30 @@ class FrameRenderer:
 
 
 def autotune_frame(svo: ng.SVO, feats: ng.Features, dec: ng.DecoderDev, o, d, lod, chunk_counts=(1, 2, 3, 4),
-                   ctas=(0, 3, 2), trav_ctas=(0, 2), reps: int = 5, **kw):
+                   ctas=(0, 3, 2), trav_ctas=(0, 2), reps: int = 5, host=None, **kw):
     """Times the frame renderer on these rays for every (chunk count, trace
     CTAs per SM, traversal CTAs per SM) triple -- narrower persistent
     launches leave room on each SM for the other chunks' kernels, so the
     chunks' stages share SMs instead of taking turns -- and returns the
     fastest renderer with the timings (ms per frame, keyed
     "chunks/trace ctas" for the widest traversal, "chunks/trace ctas/t<n>"
-    for a traversal of n CTAs per SM)."""
+    for a traversal of n CTAs per SM).  host = (h_in, h_out): time frames
+    that copy their rays in from and their results out to these pinned
+    host buffers (the schedule that hides the copies best can differ)."""
     import torch
     timings, best, best_ms = {}, None, float("inf")
     configs = [(n, c, t) for n in chunk_counts for c in ctas for t in (trav_ctas if n > 1 else (0,))]
     for n, c, t in configs:
         fr = FrameRenderer(svo, feats, dec, o, d, lod, chunks=n, ctas_per_sm=c, trav_ctas_per_sm=t, **kw)
+        args = () if host is None else host
         for _ in range(2):
-            fr.frame()
+            fr.frame(*args)
         fr.check()
         ts = []
         for _ in range(reps):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
-            fr.frame()
+            fr.frame(*args)
             e1.record()
             e1.synchronize()
             ts.append(e0.elapsed_time(e1))

@@ -25,6 +25,16 @@ def test_chunked_frame_equals_single_pass(ng, decode, chunks):
     ref = ng.sphere_trace(svo, F, D, to, td, lists, decode=decode, normals=True)
     fr = FrameRenderer(svo, F, D, to, td, 5, chunks=chunks, decode=decode)
     assert len(fr.chunks) == chunks
+    # uneven chunk sizes change only the schedule
+    fw = FrameRenderer(svo, F, D, to, td, 5, chunks=chunks, decode=decode, weights=list(range(1, chunks + 1)))
+    sizes = [c["n"] for c in fw.chunks]
+    assert sum(sizes) == len(o) and sizes == sorted(sizes)
+    fw.frame()
+    fw.check()
+    for k in ("t", "hit", "steps", "normal"):
+        assert torch.equal(fw.out[k], ref[k]), k
+    with pytest.raises(ValueError):
+        FrameRenderer(svo, F, D, to, td, 5, chunks=chunks, decode=decode, weights=[1.0] * (chunks + 1))
     for _ in range(2):                     # a second frame reuses every buffer
         fr.frame()
         fr.check()
@@ -98,4 +108,17 @@ def test_trace_width_and_frame_autotune(ng, decode):
     fr.check()
     for k in ("t", "hit", "steps", "normal"):
         assert torch.equal(fr.out[k], ref[k]), k
+    # tuned with the host copies in: the frames it times copy rays in and
+    # results out, and the returned renderer's copies equal the single pass
+    h_in = (torch.from_numpy(o).pin_memory(), torch.from_numpy(d).pin_memory())
+    h_out = {"t": torch.empty(len(o)).pin_memory(), "hit": torch.empty(len(o), dtype=torch.uint8).pin_memory(),
+             "normal": torch.empty((len(o), 3)).pin_memory()}
+    fh, th = autotune_frame(svo, F, D, to.clone(), td.clone(), 5, chunk_counts=(1, 2), ctas=(0,), reps=2,
+                            decode=decode, host=(h_in, h_out))
+    assert set(th) == {"1/0", "2/0", "2/0/t2"}
+    fh.o.zero_()
+    fh.frame(h_in, h_out)
+    torch.cuda.synchronize()
+    fh.check()
+    assert torch.equal(h_out["t"], ref["t"].cpu()) and torch.equal(h_out["normal"], ref["normal"].cpu())
     svo.free()
