@@ -306,13 +306,16 @@ __global__ void __launch_bounds__(kThreads) k_grad(const DecPtrs dp, const Table
                     const int h = c * 32 + hh;
                     const float4* w = reinterpret_cast<const float4*>(sd.W1 + h * K4);
                     const float gh = ((bits >> hh) & 1u) ? sd.bw[h].y : 0.0f;
+                    // packed pairs: each lane rounded once, as fmaf
 #pragma unroll
                     for (int j = 0; j < K4 / 4; ++j) {
                         const float4 ww = w[j];
-                        gv[4 * j] = fmaf(gh, ww.x, gv[4 * j]);
-                        gv[4 * j + 1] = fmaf(gh, ww.y, gv[4 * j + 1]);
-                        gv[4 * j + 2] = fmaf(gh, ww.z, gv[4 * j + 2]);
-                        gv[4 * j + 3] = fmaf(gh, ww.w, gv[4 * j + 3]);
+                        const float2 lo = fma2(gh, make_float2(ww.x, ww.y), make_float2(gv[4 * j], gv[4 * j + 1]));
+                        const float2 hi = fma2(gh, make_float2(ww.z, ww.w), make_float2(gv[4 * j + 2], gv[4 * j + 3]));
+                        gv[4 * j] = lo.x;
+                        gv[4 * j + 1] = lo.y;
+                        gv[4 * j + 2] = hi.x;
+                        gv[4 * j + 3] = hi.y;
                     }
                 }
             }
@@ -320,24 +323,25 @@ __global__ void __launch_bounds__(kThreads) k_grad(const DecPtrs dp, const Table
 #pragma unroll 1
         for (int h = 0; h < (use_mask ? 0 : kHidden); ++h) {
             const float4* w = reinterpret_cast<const float4*>(sd.W1 + h * K4);
-            float a0 = 0.0f, a1 = 0.0f;
+            // the two partial sums as one packed pair (each lane rounded once, as fmaf)
+            float2 a = make_float2(0.0f, 0.0f);
 #pragma unroll
             for (int j = 0; j < K4 / 4; ++j) {
                 const float4 ww = w[j];
-                a0 = fmaf(ww.x, v[4 * j], a0);
-                a1 = fmaf(ww.y, v[4 * j + 1], a1);
-                a0 = fmaf(ww.z, v[4 * j + 2], a0);
-                a1 = fmaf(ww.w, v[4 * j + 3], a1);
+                a = __ffma2_rn(make_float2(ww.x, ww.y), make_float2(v[4 * j], v[4 * j + 1]), a);
+                a = __ffma2_rn(make_float2(ww.z, ww.w), make_float2(v[4 * j + 2], v[4 * j + 3]), a);
             }
             const float2 bw = sd.bw[h];
-            const float gh = (a0 + a1 + bw.x) > 0.0f ? bw.y : 0.0f;
+            const float gh = (a.x + a.y + bw.x) > 0.0f ? bw.y : 0.0f;
 #pragma unroll
             for (int j = 0; j < K4 / 4; ++j) {
                 const float4 ww = w[j];
-                gv[4 * j] = fmaf(gh, ww.x, gv[4 * j]);
-                gv[4 * j + 1] = fmaf(gh, ww.y, gv[4 * j + 1]);
-                gv[4 * j + 2] = fmaf(gh, ww.z, gv[4 * j + 2]);
-                gv[4 * j + 3] = fmaf(gh, ww.w, gv[4 * j + 3]);
+                const float2 lo = fma2(gh, make_float2(ww.x, ww.y), make_float2(gv[4 * j], gv[4 * j + 1]));
+                const float2 hi = fma2(gh, make_float2(ww.z, ww.w), make_float2(gv[4 * j + 2], gv[4 * j + 3]));
+                gv[4 * j] = lo.x;
+                gv[4 * j + 1] = lo.y;
+                gv[4 * j + 2] = hi.x;
+                gv[4 * j + 3] = hi.y;
             }
         }
         __syncwarp();
