@@ -371,12 +371,13 @@ size_t sphere_trace_workspace(int64_t R);
  *                       The rest holds the order in which 32-ray groups are
  *                       handed to the persistent trace (by decreasing longest
  *                       list, so long rays start early; it changes only the
- *                       schedule, never a ray's outputs) and, per ray, the
- *                       ReLU mask of a hit's last decode
+ *                       schedule, never a ray's outputs), per ray the ReLU
+ *                       mask of a hit's last decode
  *                       (128 bits), which trace_normals reuses (not with the
  *                       FP8 decode, whose 4-bit z can zero or flip a
  *                       pre-activation: its normals recompute the forward
- *                       pass in FP32).
+ *                       pass in FP32), and last the normals' scratch (their
+ *                       masked-sum operand, 30 KB).
  * Outputs: t_hit [R] (+inf on miss), hit [R] uint8, steps [R] int32
  * (nullable: decodes taken), normal [R, 3] (nullable; normalised analytic
  * gradient of the decoded SDF at the hit point in FP32, or its central
@@ -577,8 +578,12 @@ void sphere_trace_batch_free(nglod_batch* batch);
  * the normalised analytic gradient of the decoded SDF (Eq. 2 chain rule
  * through the trilinear weights, Sec. 3.2) in FP32 at the hit point
  * x = o + t_hit d, using the hit voxel and the ReLU mask of the hit's last
- * decode recorded by sphere_trace (a blended trace records no masks: the
- * forward pass is then recomputed in FP32).  The paper
+ * decode recorded by sphere_trace (a blended trace records no masks for it:
+ * the forward pass is then recomputed in FP32).  The masked sum
+ * sum_h W2_h [mask_h] W1[h] runs as warp-level tensor-core products of the
+ * 0/1 masks with W2 W1 split into three BF16 terms (exact products, FP32
+ * sums); its operand is built in the workspace's last region, the only
+ * bytes of work this call writes.  The paper
  * takes normals by finite differences (supplementary Sec. A.4); the analytic
  * gradient is their limit.  normal [R, 3]; zero for misses.  Does not
  * synchronise. */

@@ -237,6 +237,7 @@ extern "C" int sphere_trace_batch_create(const nglod_trace_job* jobs, int num_jo
             A.hit_count = (int*)J.work + 2;
             A.hit_vox = (int32_t*)((char*)J.work + trace_ws_hit_vox_offset());
             A.hit_list = (int32_t*)((char*)J.work + trace_ws_hit_list_offset(J.R));
+            A.wfrag = (uint2*)((char*)J.work + trace_ws_wfrag_offset(J.R));
             A.hit_mask = dec_t == NGLOD_FP8E4M3 ? nullptr : (uint4*)((char*)J.work + trace_ws_mask_offset(J.R));
             tj.ray_base = base;
             base += (J.R + 31) / 32 * 32;     // chunks of 32 never span two jobs

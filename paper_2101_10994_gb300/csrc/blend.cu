@@ -119,6 +119,7 @@ extern "C" int sphere_trace_blend(const nglod_svo* svo, const nglod_features* fe
     A.hit_count = (int*)work + 2;
     A.hit_vox = (int32_t*)((char*)work + trace_ws_hit_vox_offset());
     A.hit_list = (int32_t*)((char*)work + trace_ws_hit_list_offset(R));
+    A.wfrag = (uint2*)((char*)work + trace_ws_wfrag_offset(R));
     A.ctas_per_sm = params->ctas_per_sm;
     NGLOD_CUDA(cudaMemsetAsync(work, 0, 256, st));
     if ((rc = enqueue_ray_order(A, work, svo->node[A.D], st))) return rc;

@@ -4,6 +4,7 @@
 // 35(32) -> 128 -> 1 MLP with the decoder staged once per CTA in shared
 // memory; all lanes of a warp read the same weight row, so the loads are
 // broadcasts and each 16-byte load feeds four FFMAs.
+#include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
@@ -203,6 +204,35 @@ __global__ void __launch_bounds__(kThreads) k_sdf_query(const DecPtrs dp, const 
 // corner by corner, and reduce.  The trace normals run over the compact list
 // of hit rays the tracer recorded.
 // ---------------------------------------------------------------------------
+// The masked sum v = sum_h W2_h [mask_h] W1[h] of the normals as a product
+// of the warp's 32 x 128 mask matrix A (entries 0 or 1, exact in BF16) with
+// W' = diag(W2) W1 (128 x 8 NT, the z columns and, for in_dim 35, the x
+// columns), W' split into three BF16 terms (w0 + w1 + w2 = W' exactly):
+// every product is exact and the sums are FP32, as in the CUDA-core form.
+// Warp-level tensor-core MMAs (m16n8k16, FP32 accumulate): the operands
+// live in registers, so no block barrier and no shared memory.
+// B fragments in the order the MMA wants them: entry ((s * 8 + ks) * NT +
+// nt) * 32 + lane holds lane's (b0, b1) for split s, K step ks (hidden units
+// 16 ks ..), N tile nt: b0 = (W'_s[k0][n], W'_s[k0 + 1][n]), b1 = the same
+// at k0 + 8, with k0 = 16 ks + 2 (lane % 4), n = 8 nt + lane / 4.
+constexpr int kFragSplits = 3;
+constexpr int kFragKSteps = kHidden / 16;
+constexpr int kFragNTMax = 5;                   // in_dim 35: 35 columns in 5 tiles of 8
+static_assert(sizeof(uint2) * kFragSplits * kFragKSteps * kFragNTMax * 32 == kWsFragBytes, "workspace region");
+
+__device__ __forceinline__ void mma_bf16_16816(float (&c)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                               uint2 b) {
+    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, "
+                 "{%8, %9}, {%0, %1, %2, %3};"
+                 : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+                 : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b.x), "r"(b.y));
+}
+
+// Two mask bits as a pair of BF16 (lower bit in the lower half): 1.0 or 0.
+__device__ __forceinline__ uint32_t bits_bf16x2(uint32_t m, int j) {
+    return (((m >> j) & 1u) ? 0x3f80u : 0u) | (((m >> (j + 1)) & 1u) ? 0x3f800000u : 0u);
+}
+
 struct GradArgs {
     const float* x;        // mode 0: [Q, 3] points
     const float* o;        // mode 1: rays
@@ -212,6 +242,7 @@ struct GradArgs {
     const int* hit_count;  // mode 1: number of entries in hit_list
     const int32_t* hit_list;
     const uint4* hit_mask;  // modes 1, 2: the tracer's ReLU mask per ray (used if *mask_flag)
+    const uint2* wfrag;     // with masks: B operand of the masked sum (k_wfrag), in fragment order
     const int* mask_flag;
     long long n;           // mode 0: Q
     int D;
@@ -237,8 +268,8 @@ __global__ void __launch_bounds__(kThreads) k_grad(const DecPtrs dp, const Table
     const int dcap = A.dcap > 0 ? A.dcap : kMaxDepth;
     // trace normals after a tracer that recorded its hits' ReLU masks: no z
     // gather and no forward pass, v = sum_h W2_h [mask_h] W1[h] directly
-    const bool use_mask = A.hit_mask != nullptr && ((A.mode == 1 && *A.mask_flag == 1) ||
-                                                    (A.mode == 2 && *A.mask_flag == 2));
+    const bool use_mask = A.hit_mask != nullptr && A.wfrag != nullptr &&
+                          ((A.mode == 1 && *A.mask_flag == 1) || (A.mode == 2 && *A.mask_flag == 2));
     for (long long base = ((long long)blockIdx.x * kWarps + warp) * 32; base < n;
          base += (long long)gridDim.x * kWarps * 32) {
         const long long it = base + lane;
@@ -297,28 +328,64 @@ __global__ void __launch_bounds__(kThreads) k_grad(const DecPtrs dp, const Table
 #pragma unroll
         for (int k = 0; k < K4; ++k) gv[k] = 0.0f;
         if (use_mask) {
+            // v of the warp's 32 items by MMAs (see mma_bf16_16816): item i's
+            // mask is lane i's; the accumulators c[mt][nt] hold rows 16 mt +
+            // lane / 4 (+ 8) and columns 8 nt + 2 (lane % 4) (+ 1) of v
+            constexpr int NT = OFF ? 5 : 4;
             const uint4 mk = act ? A.hit_mask[ray] : make_uint4(0u, 0u, 0u, 0u);
-#pragma unroll 1
-            for (int c = 0; c < 4; ++c) {
-                const uint32_t bits = c == 0 ? mk.x : c == 1 ? mk.y : c == 2 ? mk.z : mk.w;
-#pragma unroll 2
-                for (int hh = 0; hh < 32; ++hh) {
-                    const int h = c * 32 + hh;
-                    const float4* w = reinterpret_cast<const float4*>(sd.W1 + h * K4);
-                    const float gh = ((bits >> hh) & 1u) ? sd.bw[h].y : 0.0f;
-                    // packed pairs: each lane rounded once, as fmaf
+            const int g = lane >> 2, cq = 2 * (lane & 3);
+            float acc[2][NT][4];
 #pragma unroll
-                    for (int j = 0; j < K4 / 4; ++j) {
-                        const float4 ww = w[j];
-                        const float2 lo = fma2(gh, make_float2(ww.x, ww.y), make_float2(gv[4 * j], gv[4 * j + 1]));
-                        const float2 hi = fma2(gh, make_float2(ww.z, ww.w), make_float2(gv[4 * j + 2], gv[4 * j + 3]));
-                        gv[4 * j] = lo.x;
-                        gv[4 * j + 1] = lo.y;
-                        gv[4 * j + 2] = hi.x;
-                        gv[4 * j + 3] = hi.y;
+            for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+                for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) acc[mt][nt][e] = 0.0f;
+#pragma unroll 1
+            for (int w = 0; w < 4; ++w) {
+                const uint32_t word = w == 0 ? mk.x : w == 1 ? mk.y : w == 2 ? mk.z : mk.w;
+                uint32_t m0[2], m1[2];
+#pragma unroll
+                for (int mt = 0; mt < 2; ++mt) {
+                    m0[mt] = __shfl_sync(0xffffffffu, word, 16 * mt + g);
+                    m1[mt] = __shfl_sync(0xffffffffu, word, 16 * mt + g + 8);
+                }
+#pragma unroll
+                for (int half = 0; half < 2; ++half) {
+                    const int ks = 2 * w + half, sh = 16 * half;
+                    uint2 bf[kFragSplits][NT];
+#pragma unroll
+                    for (int sp = 0; sp < kFragSplits; ++sp)
+#pragma unroll
+                        for (int nt = 0; nt < NT; ++nt)
+                            bf[sp][nt] = __ldg(A.wfrag + ((sp * kFragKSteps + ks) * NT + nt) * 32 + lane);
+#pragma unroll
+                    for (int mt = 0; mt < 2; ++mt) {
+                        const uint32_t r0 = m0[mt] >> sh, r1 = m1[mt] >> sh;
+                        const uint32_t a0 = bits_bf16x2(r0, cq), a1 = bits_bf16x2(r1, cq);
+                        const uint32_t a2 = bits_bf16x2(r0, cq + 8), a3 = bits_bf16x2(r1, cq + 8);
+#pragma unroll
+                        for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+                            for (int sp = kFragSplits - 1; sp >= 0; --sp)   // smallest terms first
+                                mma_bf16_16816(acc[mt][nt], a0, a1, a2, a3, bf[sp][nt]);
                     }
                 }
             }
+            __syncwarp();
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+                for (int nt = 0; nt < NT; ++nt) {
+                    const int col = 8 * nt + cq;
+                    if (col < kZStride) {
+                        *reinterpret_cast<float2*>(zb + (16 * mt + g) * kZStride + col) =
+                            make_float2(acc[mt][nt][0], acc[mt][nt][1]);
+                        *reinterpret_cast<float2*>(zb + (16 * mt + g + 8) * kZStride + col) =
+                            make_float2(acc[mt][nt][2], acc[mt][nt][3]);
+                    }
+                }
+            __syncwarp();
         }
 #pragma unroll 1
         for (int h = 0; h < (use_mask ? 0 : kHidden); ++h) {
@@ -344,12 +411,14 @@ __global__ void __launch_bounds__(kThreads) k_grad(const DecPtrs dp, const Table
                 gv[4 * j + 3] = hi.y;
             }
         }
-        __syncwarp();
+        if (!use_mask) {
+            __syncwarp();
 #pragma unroll
-        for (int j = 0; j < 8; ++j)
-            reinterpret_cast<float4*>(zb + lane * kZStride)[j] =
-                make_float4(gv[4 * j], gv[4 * j + 1], gv[4 * j + 2], gv[4 * j + 3]);
-        __syncwarp();
+            for (int j = 0; j < K4 / 4; ++j)
+                reinterpret_cast<float4*>(zb + lane * kZStride)[j] =
+                    make_float4(gv[4 * j], gv[4 * j + 1], gv[4 * j + 2], gv[4 * j + 3]);
+            __syncwarp();
+        }
         // (C) J^T v_z: the trilinear derivative weights of every level and corner
         // (4-lane groups: lane l4 dots its 8 channels of each corner row with v_z)
 #pragma unroll 1
@@ -414,10 +483,10 @@ __global__ void __launch_bounds__(kThreads) k_grad(const DecPtrs dp, const Table
         __syncwarp();
         if (act) {
             float gx[3] = {gb[lane * 4], gb[lane * 4 + 1], gb[lane * 4 + 2]};
-            if constexpr (OFF == 3) {
-                gx[0] += gv[32];
-                gx[1] += gv[33];
-                gx[2] += gv[34];
+            if constexpr (OFF == 3) {   // the x columns of v (x concatenated in Eq. 2)
+                gx[0] += zb[lane * kZStride + 32];
+                gx[1] += zb[lane * kZStride + 33];
+                gx[2] += zb[lane * kZStride + 34];
             }
             const long long oi = A.mode >= 1 ? (long long)ray : it;
             if (A.mode == 2) {
@@ -811,6 +880,52 @@ __global__ void k_normalise_hits(const int* __restrict__ hit_count, const int32_
     }
 }
 
+// B fragments of W' = diag(W2) W1 for the normals' masked sum (layout at
+// mma_bf16_16816): one thread per (split, K step, N tile, lane) entry.
+__device__ __forceinline__ float wprime(const float* __restrict__ W1, const float* __restrict__ W2, int in_dim, int h,
+                                        int n) {
+    const int off = in_dim - kFeatDim;
+    if (n < kFeatDim) return W2[h] * W1[h * in_dim + off + n];
+    if (n < kFeatDim + off) return W2[h] * W1[h * in_dim + (n - kFeatDim)];
+    return 0.0f;
+}
+
+// Term sp of the three-term BF16 split of v (v = t0 + t1 + t2; each
+// difference exact in FP32), as raw bits.
+__device__ __forceinline__ uint32_t split_bits(float v, int sp) {
+    const __nv_bfloat16 t0 = __float2bfloat16_rn(v);
+    const float r1 = v - __bfloat162float(t0);
+    const __nv_bfloat16 t1 = __float2bfloat16_rn(r1);
+    const __nv_bfloat16 t2 = __float2bfloat16_rn(r1 - __bfloat162float(t1));
+    const __nv_bfloat16 t = sp == 0 ? t0 : sp == 1 ? t1 : t2;
+    return (uint32_t)*reinterpret_cast<const unsigned short*>(&t);
+}
+
+__global__ void k_wfrag(const float* __restrict__ W1, const float* __restrict__ W2, int in_dim,
+                        uint2* __restrict__ out) {
+    const int NT = in_dim == 35 ? 5 : 4;
+    const int total = kFragSplits * kFragKSteps * NT * 32;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+        const int lane = e & 31, rest = e >> 5;
+        const int nt = rest % NT, ks = (rest / NT) % kFragKSteps, sp = rest / (NT * kFragKSteps);
+        const int n = 8 * nt + (lane >> 2), k0 = 16 * ks + 2 * (lane & 3);
+        const uint32_t b0 = split_bits(wprime(W1, W2, in_dim, k0, n), sp) |
+                            (split_bits(wprime(W1, W2, in_dim, k0 + 1, n), sp) << 16);
+        const uint32_t b1 = split_bits(wprime(W1, W2, in_dim, k0 + 8, n), sp) |
+                            (split_bits(wprime(W1, W2, in_dim, k0 + 9, n), sp) << 16);
+        out[e] = make_uint2(b0, b1);
+    }
+}
+
+// The masked-sum operand of decoder dec, when the trace recorded masks.
+int enqueue_wfrag(const nglod_decoder* dec, const TraceArgs& A, cudaStream_t st) {
+    if (!A.hit_mask || !A.wfrag) return NGLOD_OK;
+    k_wfrag<<<(kFragSplits * kFragKSteps * kFragNTMax * 32 + 255) / 256, 256, 0, st>>>(
+        static_cast<const float*>(dec->W1), static_cast<const float*>(dec->W2), dec->in_dim, A.wfrag);
+    NGLOD_CUDA(cudaGetLastError());
+    return NGLOD_OK;
+}
+
 }  // namespace
 
 int launch_trace_fp32(const nglod_decoder* dec, const Tables& tb, const TraceArgs& A, bool f16, int sms,
@@ -852,11 +967,13 @@ int launch_normals(const nglod_decoder* dec, const Tables& tb, const TraceArgs& 
     G.hit_count = A.hit_count;
     G.hit_list = A.hit_list;
     G.hit_mask = A.hit_mask;
+    G.wfrag = A.wfrag;
     G.mask_flag = A.hit_count + (kWsMaskFlagWord - 2);
     G.n = A.R;
     G.D = A.D;
     G.mode = 1;
     G.out = normal;
+    if (int rc = enqueue_wfrag(dec, A, st)) return rc;
     return run_grad(dec, tb, G, f16, sms, st);
 }
 
@@ -929,13 +1046,14 @@ int launch_normals_blend(const nglod_decoder* lo, const nglod_decoder* hi, float
     G.dcap = A.D - 1;
     G.w = 1.0f - alpha;
     G.hit_mask = A.hit_mask;                 // the lower LOD's masks, if the trace recorded them
+    G.wfrag = A.wfrag;
     G.mask_flag = A.hit_count + (kWsMaskFlagWord - 2);
-    int rc = run_grad(lo, tb, G, f16, sms, st);
-    if (rc) return rc;
+    int rc = enqueue_wfrag(lo, A, st);
+    if (rc || (rc = run_grad(lo, tb, G, f16, sms, st))) return rc;
     G.dcap = A.D;
     G.w = alpha;
     G.hit_mask = A.hit_mask2;
-    if ((rc = run_grad(hi, tb, G, f16, sms, st))) return rc;
+    if ((rc = enqueue_wfrag(hi, A, st)) || (rc = run_grad(hi, tb, G, f16, sms, st))) return rc;
     k_normalise_hits<<<std::max(1, (int)std::min<long long>((A.R + 255) / 256, (long long)sms * 8)), 256, 0, st>>>(
         A.hit_count, A.hit_list, normal);
     NGLOD_CUDA(cudaGetLastError());
@@ -1238,6 +1356,7 @@ extern "C" int sphere_trace(const nglod_svo* svo, const nglod_features* feats, c
     A.hit_count = (int*)work + 2;
     A.hit_vox = (int32_t*)((char*)work + trace_ws_hit_vox_offset());
     A.hit_list = (int32_t*)((char*)work + trace_ws_hit_list_offset(R));
+    A.wfrag = (uint2*)((char*)work + trace_ws_wfrag_offset(R));
     A.ctas_per_sm = params->ctas_per_sm;
     NGLOD_CUDA(cudaMemsetAsync(work, 0, 256, st));
     rc = check_decoder(dec);
@@ -1301,6 +1420,8 @@ int normals_common(const nglod_svo* svo, const nglod_features* feats, const nglo
     A.hit_count = (int*)const_cast<void*>(work) + 2;
     A.hit_vox = (int32_t*)((char*)work + trace_ws_hit_vox_offset());
     A.hit_list = (int32_t*)((char*)work + trace_ws_hit_list_offset(R));
+    // the masked-sum operand is scratch of the normals themselves
+    A.wfrag = (uint2*)((char*)const_cast<void*>(work) + trace_ws_wfrag_offset(R));
     A.hit_mask = (uint4*)((char*)work + trace_ws_mask_offset(R));   // used if the header flag says recorded
     const bool f16 = feats->dtype == NGLOD_F16;
     return fd_h > 0.0f ? launch_normals_fd(dec, tb, A, fd_h, normal, f16, svo->num_sms, st)

@@ -131,6 +131,9 @@ struct TraceArgs {
     // then
     uint4* hit_mask = nullptr;
     uint4* hit_mask2 = nullptr;   // level blending: the second decoder's masks
+    // workspace: the normals' masked-sum operand (B fragments of diag(W2) W1,
+    // rebuilt for each decoder by launch_normals*)
+    uint2* wfrag = nullptr;
     int ctas_per_sm = 0;          // launch width of the persistent trace (0: the most that fit)
     // workspace (null: not prepared): per ray its first list entry as
     // (t_enter bits, t_exit bits, voxel id, packed ijk), written by the
@@ -429,7 +432,10 @@ inline size_t trace_ws_mask_offset(long long R) {
 }
 // ... then, per ray, its first list entry (16 B; the handout-order pass writes it)
 inline size_t trace_ws_start_offset(long long R) { return trace_ws_mask_offset(R) + trace_ws_align(32 * (size_t)R); }
-inline size_t trace_ws_size(long long R) { return trace_ws_start_offset(R) + 16 * (size_t)R; }
+// ... then the normals' masked-sum operand: 3 splits x 8 K steps x 5 N tiles x 32 lanes x 8 B
+constexpr size_t kWsFragBytes = 3 * 8 * 5 * 32 * 8;
+inline size_t trace_ws_wfrag_offset(long long R) { return trace_ws_align(trace_ws_start_offset(R) + 16 * (size_t)R); }
+inline size_t trace_ws_size(long long R) { return trace_ws_wfrag_offset(R) + kWsFragBytes; }
 // header word 3: 1 = one mask per hit (plain traces), 2 = two (blended: the
 // lower LOD's at [0, R), the upper's at [R, 2R)), 0 = none
 constexpr int kWsMaskFlagWord = 3;
