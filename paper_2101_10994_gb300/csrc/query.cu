@@ -327,12 +327,43 @@ __global__ void __launch_bounds__(kThreads) k_grad(const DecPtrs dp, const Table
         }
 #pragma unroll
         for (int k = 0; k < K4; ++k) gv[k] = 0.0f;
-        if (use_mask) {
+        // the normals (modes 1, 2) form v by MMAs from the recorded masks, or
+        // from the masks of an FP32 forward pass run here for them
+        const bool mma_sum = A.wfrag != nullptr && A.mode >= 1;
+        if (mma_sum) {
+            uint4 mk = make_uint4(0u, 0u, 0u, 0u);
+            if (use_mask) {
+                if (act) mk = A.hit_mask[ray];
+            } else {
+                uint32_t m0 = 0u, m1 = 0u, m2 = 0u, m3 = 0u;
+#pragma unroll 1
+                for (int c = 0; c < 4; ++c) {
+                    uint32_t bits = 0u;
+#pragma unroll 2
+                    for (int hh = 0; hh < 32; ++hh) {
+                        const int h = c * 32 + hh;
+                        const float4* w = reinterpret_cast<const float4*>(sd.W1 + h * K4);
+                        // the two partial sums as one packed pair (each lane rounded once, as fmaf)
+                        float2 a = make_float2(0.0f, 0.0f);
+#pragma unroll
+                        for (int j = 0; j < K4 / 4; ++j) {
+                            const float4 ww = w[j];
+                            a = __ffma2_rn(make_float2(ww.x, ww.y), make_float2(v[4 * j], v[4 * j + 1]), a);
+                            a = __ffma2_rn(make_float2(ww.z, ww.w), make_float2(v[4 * j + 2], v[4 * j + 3]), a);
+                        }
+                        bits |= ((a.x + a.y + sd.bw[h].x) > 0.0f ? 1u : 0u) << hh;
+                    }
+                    m0 = c == 0 ? bits : m0;
+                    m1 = c == 1 ? bits : m1;
+                    m2 = c == 2 ? bits : m2;
+                    m3 = c == 3 ? bits : m3;
+                }
+                if (act) mk = make_uint4(m0, m1, m2, m3);
+            }
             // v of the warp's 32 items by MMAs (see mma_bf16_16816): item i's
             // mask is lane i's; the accumulators c[mt][nt] hold rows 16 mt +
             // lane / 4 (+ 8) and columns 8 nt + 2 (lane % 4) (+ 1) of v
             constexpr int NT = OFF ? 5 : 4;
-            const uint4 mk = act ? A.hit_mask[ray] : make_uint4(0u, 0u, 0u, 0u);
             const int g = lane >> 2, cq = 2 * (lane & 3);
             float acc[2][NT][4];
 #pragma unroll
@@ -388,7 +419,7 @@ __global__ void __launch_bounds__(kThreads) k_grad(const DecPtrs dp, const Table
             __syncwarp();
         }
 #pragma unroll 1
-        for (int h = 0; h < (use_mask ? 0 : kHidden); ++h) {
+        for (int h = 0; h < (mma_sum ? 0 : kHidden); ++h) {
             const float4* w = reinterpret_cast<const float4*>(sd.W1 + h * K4);
             // the two partial sums as one packed pair (each lane rounded once, as fmaf)
             float2 a = make_float2(0.0f, 0.0f);
@@ -411,7 +442,7 @@ __global__ void __launch_bounds__(kThreads) k_grad(const DecPtrs dp, const Table
                 gv[4 * j + 3] = hi.y;
             }
         }
-        if (!use_mask) {
+        if (!mma_sum) {
             __syncwarp();
 #pragma unroll
             for (int j = 0; j < K4 / 4; ++j)
@@ -917,9 +948,10 @@ __global__ void k_wfrag(const float* __restrict__ W1, const float* __restrict__ 
     }
 }
 
-// The masked-sum operand of decoder dec, when the trace recorded masks.
+// The masked-sum operand of decoder dec for the normals of a trace whose
+// workspace holds one.
 int enqueue_wfrag(const nglod_decoder* dec, const TraceArgs& A, cudaStream_t st) {
-    if (!A.hit_mask || !A.wfrag) return NGLOD_OK;
+    if (!A.wfrag) return NGLOD_OK;
     k_wfrag<<<(kFragSplits * kFragKSteps * kFragNTMax * 32 + 255) / 256, 256, 0, st>>>(
         static_cast<const float*>(dec->W1), static_cast<const float*>(dec->W2), dec->in_dim, A.wfrag);
     NGLOD_CUDA(cudaGetLastError());
