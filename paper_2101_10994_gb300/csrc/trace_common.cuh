@@ -65,17 +65,16 @@ __device__ __forceinline__ float mlp_f32(const SmemDecoder& sd, float b2, const 
         for (int hh = 0; hh < 32; ++hh) {
             const int h = c * 32 + hh;
             const float4* w = reinterpret_cast<const float4*>(sd.W1 + h * K4);
-            float a0 = 0.0f, a1 = 0.0f;
+            // two partial sums as one packed pair (each lane rounded once, as fmaf)
+            float2 a = make_float2(0.0f, 0.0f);
 #pragma unroll
             for (int j = 0; j < K4 / 4; ++j) {
                 const float4 ww = w[j];
-                a0 = fmaf(ww.x, v[4 * j], a0);
-                a1 = fmaf(ww.y, v[4 * j + 1], a1);
-                a0 = fmaf(ww.z, v[4 * j + 2], a0);
-                a1 = fmaf(ww.w, v[4 * j + 3], a1);
+                a = __ffma2_rn(make_float2(ww.x, ww.y), make_float2(v[4 * j], v[4 * j + 1]), a);
+                a = __ffma2_rn(make_float2(ww.z, ww.w), make_float2(v[4 * j + 2], v[4 * j + 3]), a);
             }
             const float2 bw = sd.bw[h];
-            const float pre = a0 + a1 + bw.x;
+            const float pre = a.x + a.y + bw.x;
             out = fmaf(bw.y, fmaxf(pre, 0.0f), out);
             if constexpr (MASK) bits |= (pre > 0.0f ? 1u : 0u) << hh;
         }
