@@ -297,7 +297,7 @@ def run_ours(args, rank, world, local_rank):
         # streams (traversal, trace and normals of one chunk overlap the others'), the chunk
         # count and the trace's CTAs per SM picked by its autotuner (untimed)
         fr, tune = autotune_frame(svo, feats, dec, o, d, W["lod"], eps=W["eps"], far=W["far"],
-                                  max_steps=W["max_steps"], decode=mode, normals=True)
+                                  max_steps=W["max_steps"], decode=mode, normals=True, flush=flush)
         for _ in range(args.warmup):
             flush.zero_()
             fr.frame()
@@ -342,7 +342,7 @@ def run_ours(args, rank, world, local_rank):
         lt = W["lod"] - 0.5
         dlo = ng.DecoderDev.from_decoder(W["dec_lo"])
         fr, btune = autotune_frame(svo, feats, dlo, o, d, lt, eps=W["eps"], far=W["far"], max_steps=W["max_steps"],
-                                   decode="bf16", normals=True, dec_hi=dec)
+                                   decode="bf16", normals=True, dec_hi=dec, flush=flush)
         bl = []
         for k in range(args.warmup + args.steps):
             flush.zero_()
@@ -442,7 +442,7 @@ def run_ours(args, rank, world, local_rank):
         ng.sphere_trace_status(sout)
         st_ms = [statistics.mean(v[i] for v in st_ms) for i in range(3)]
         fr, stune = autotune_frame(svo, fs, dec, o, d, W["lod"], eps=W["eps"], far=W["far"],
-                                   max_steps=W["max_steps"], decode=sm_mode, normals=True)
+                                   max_steps=W["max_steps"], decode=sm_mode, normals=True, flush=flush)
         sl = []
         for k in range(args.warmup + args.steps):
             flush.zero_()
@@ -485,7 +485,8 @@ def run_ours(args, rank, world, local_rank):
     # The schedule is tuned with the copies in (untimed): the one that hides them best
     # can differ from the device-only frame's
     fr, etune = autotune_frame(svo, feats, dec, o.clone(), d.clone(), W["lod"], host=((h_o, h_d), h_out),
-                               eps=W["eps"], far=W["far"], max_steps=W["max_steps"], decode=mode, normals=True)
+                               eps=W["eps"], far=W["far"], max_steps=W["max_steps"], decode=mode, normals=True,
+                               flush=flush)
     ech, ecta, etcta = len(fr.chunks), fr.ctas_per_sm, fr.trav_ctas_per_sm
     e2e_ms = []
     for k in range(args.warmup + args.steps):

@@ -132,7 +132,7 @@ class FrameRenderer:
 
 
 def autotune_frame(svo: ng.SVO, feats: ng.Features, dec: ng.DecoderDev, o, d, lod, chunk_counts=(1, 2, 3, 4),
-                   ctas=(0, 3, 2), trav_ctas=(0, 2), reps: int = 5, host=None, **kw):
+                   ctas=(0, 3, 2), trav_ctas=(0, 2), reps: int = 5, host=None, flush=None, **kw):
     """Times the frame renderer on these rays for every (chunk count, trace
     CTAs per SM, traversal CTAs per SM) triple -- narrower persistent
     launches leave room on each SM for the other chunks' kernels, so the
@@ -141,7 +141,9 @@ def autotune_frame(svo: ng.SVO, feats: ng.Features, dec: ng.DecoderDev, o, d, lo
     "chunks/trace ctas" for the widest traversal, "chunks/trace ctas/t<n>"
     for a traversal of n CTAs per SM).  host = (h_in, h_out): time frames
     that copy their rays in from and their results out to these pinned
-    host buffers (the schedule that hides the copies best can differ)."""
+    host buffers (the schedule that hides the copies best can differ).
+    flush: a device buffer zeroed before every timed frame (larger than the
+    L2, so each frame starts cold, as in a timed loop that flushes)."""
     import torch
     timings, best, best_ms = {}, None, float("inf")
     configs = [(n, c, t) for n in chunk_counts for c in ctas for t in (trav_ctas if n > 1 else (0,))]
@@ -153,6 +155,8 @@ def autotune_frame(svo: ng.SVO, feats: ng.Features, dec: ng.DecoderDev, o, d, lo
         fr.check()
         ts = []
         for _ in range(reps):
+            if flush is not None:
+                flush.zero_()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
             fr.frame(*args)
