@@ -197,12 +197,14 @@ __global__ void __launch_bounds__(kThreads) k_sdf_query(const DecPtrs dp, const 
 //
 // d sdf/dx = W1x^T g + J^T W1z^T g with g_h = W2_h [pre_h > 0] and J = dz/dx
 // (chain rule through Eq. 2 and the trilinear weights of Sec. 3.2).  Per warp
-// of 32 items: (A) 8-lane groups gather z into shared memory; (B) each lane
-// runs its item's forward pass and accumulates v = sum_h g_h W1[h] in the
-// same loop over hidden units (each W1 row read once as broadcast 16-byte
-// loads); (C) groups apply the trilinear derivative weights to v's z part,
-// corner by corner, and reduce.  The trace normals run over the compact list
-// of hit rays the tracer recorded.
+// of 32 items: (A) without a recorded ReLU mask, 4-lane groups gather z into
+// shared memory and each lane runs its item's forward pass for the mask;
+// (B) v = sum_h g_h W1[h], either as tensor-core MMAs of the mask matrix
+// with the split-BF16 W' below, or per lane in the loop over hidden units
+// (each W1 row read once as broadcast 16-byte loads); (C) 4-lane groups apply
+// the trilinear derivative weights to v's z part, corner by corner, and
+// reduce.  The trace normals run over the ray-ordered list of hit rays the
+// tracer recorded.
 // ---------------------------------------------------------------------------
 // The masked sum v = sum_h W2_h [mask_h] W1[h] of the normals as a product
 // of the warp's 32 x 128 mask matrix A (entries 0 or 1, exact in BF16) with
@@ -219,14 +221,6 @@ constexpr int kFragSplits = 3;
 constexpr int kFragKSteps = kHidden / 16;
 constexpr int kFragNTMax = 5;                   // in_dim 35: 35 columns in 5 tiles of 8
 static_assert(sizeof(uint2) * kFragSplits * kFragKSteps * kFragNTMax * 32 == kWsFragBytes, "workspace region");
-
-__device__ __forceinline__ void mma_bf16_16816(float (&c)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
-                                               uint2 b) {
-    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, "
-                 "{%8, %9}, {%0, %1, %2, %3};"
-                 : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-                 : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b.x), "r"(b.y));
-}
 
 // Two mask bits as a pair of BF16 (lower bit in the lower half): 1.0 or 0.
 __device__ __forceinline__ uint32_t bits_bf16x2(uint32_t m, int j) {

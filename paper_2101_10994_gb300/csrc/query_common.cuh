@@ -137,6 +137,19 @@ __device__ __forceinline__ float2 fma2(float w, float2 r, float2 z) {
     return __ffma2_rn(make_float2(w, w), r, z);
 }
 
+// One warp-level tensor-core MMA, D = A B + D, m16n8k16, BF16 operands and
+// FP32 accumulation.  With g = lane / 4 and c = 2 (lane % 4): a0 holds
+// A[g][c..c+1], a1 A[g+8][c..c+1], a2 A[g][c+8..c+9], a3 A[g+8][c+8..c+9]
+// (two BF16, the lower column in the lower half); b.x holds B[c..c+1][g],
+// b.y B[c+8..c+9][g]; c[0..1] = D[g][c..c+1], c[2..3] = D[g+8][c..c+1].
+__device__ __forceinline__ void mma_bf16_16816(float (&c)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                               uint2 b) {
+    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, "
+                 "{%8, %9}, {%0, %1, %2, %3};"
+                 : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+                 : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b.x), "r"(b.y));
+}
+
 // gather_slot with 4-lane groups: lane l4 of the group owns channels
 // 8 l4 .. 8 l4 + 7, so a warp interpolates 8 slots at a time.  The corner
 // ids of a level come from the flat table (one 8-byte load per lane: two

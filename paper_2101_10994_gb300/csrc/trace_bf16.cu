@@ -1,22 +1,29 @@
-// BF16 decode on the fifth-generation tensor cores (tcgen05), for the sphere
-// tracer and for sdf_query.
+// Tensor-core decodes for the sphere tracer and for sdf_query.
 //
-// The decoder's first layer over a batch of 128 queries is a dense
-// contraction: pre[q][h] = sum_k z[q][k] W1[h][k], M = 128 queries,
-// N = 128 hidden units, K = 32 feature channels.  Each CTA owns 128 query
-// slots (thread i <-> A-tile row i <-> tensor-memory lane i):
+// The decoder's first layer over a batch of queries is a dense contraction:
+// pre[q][h] = sum_k z[q][k] W1[h][k], N = 128 hidden units, K = 32 feature
+// channels.
+//
+// BF16 sphere tracing (k_trace_warp_bf16): each warp decodes its own 32
+// slots with warp-level MMAs (mma.sync m16n8k16, BF16 operands, FP32
+// accumulation), the A operand taken from the registers the 4-lane gather
+// groups filled, so no warp waits for another.
+//
+// tcgen05 (the FP8 and three-term FP32 decodes of the tracer, sdf_query,
+// batches and level blending): each CTA owns 128 query slots (thread i <->
+// A-tile row i <-> tensor-memory lane i):
 //   1. gather: 4-lane groups interpolate each slot's z (FP32, 8 channels a
-//      lane) and write it as BF16 straight into the A tile, laid out as the
-//      MMA's canonical K-major operand (8-row x 16-byte core matrices);
-//   2. one thread issues two K = 16 tcgen05.mma (A, B from shared memory,
-//      FP32 accumulator in 128 TMEM columns) and commits to an mbarrier;
+//      lane) and write it straight into the A tile, laid out as the MMA's
+//      canonical K-major operand (8-row x 16-byte core matrices);
+//   2. one thread issues the tcgen05.mma (A, B from shared memory, FP32
+//      accumulator in 128 TMEM columns) and commits to an mbarrier;
 //   3. epilogue: every thread loads its accumulator row with tcgen05.ld and
 //      applies b1 (+ the FP32 x-term when in_dim = 35), ReLU and the W2 dot
 //      product in FP32 on the CUDA cores.
-// W1 (z part) is converted to BF16 once per CTA and stays resident.  Several
-// CTAs share an SM (4 x 128 TMEM columns), so one CTA's gathers overlap
-// another's MMA and epilogue.  Every wait is bounded: on expiry the kernel
-// raises an error flag, drains its MMA, frees its tensor memory and returns.
+// W1 (z part) is converted once per CTA and stays resident.  Several CTAs
+// share an SM (4 x 128 TMEM columns), so one CTA's gathers overlap another's
+// MMA and epilogue.  Every wait is bounded: on expiry the kernel raises an
+// error flag, drains its MMA, frees its tensor memory and returns.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_fp8.h>
@@ -355,7 +362,7 @@ __device__ __forceinline__ bool mma_any(typename TcSmem<PM>::type& S, uint32_t t
 }
 
 // ---------------------------------------------------------------------------
-// sphere tracing, BF16 decode
+// sphere tracing, FP8 (PM = 1) or three-term FP32 (PM = 2) decode on tcgen05
 // ---------------------------------------------------------------------------
 template <typename T, int IN, int PM>
 __global__ void __launch_bounds__(kTM, kCtasPerSm) k_trace_bf16(const DecPtrsB dp, const Tables tb, const TraceArgs A,
@@ -441,6 +448,327 @@ __global__ void __launch_bounds__(kTM, kCtasPerSm) k_trace_bf16(const DecPtrsB d
         publish_hits(st, A, lane, mask);
     }
     teardown_tmem(S, taddr, drained, phase);
+}
+
+// ---------------------------------------------------------------------------
+// sphere tracing, BF16 decode on warp-level MMAs
+//
+// The same contraction per step, but each warp decodes its own 32 slots:
+// pre = z W1^T as 2 M tiles (16 slots each) x 16 N tiles (8 hidden units)
+// x 2 K steps of mma.sync m16n8k16 (BF16 operands, FP32 accumulation), with
+// A taken from the slots' gathered z and B (W1, BF16) from shared memory.
+// No warp waits for another: a tcgen05 tile needs all 128 slots of the CTA
+// gathered before its MMA, and that barrier waited for the slowest warp's
+// gather at every step.  The K order of the tile is permuted so that every
+// lane's fragment holds the channels it gathered: channel 8 l + 4 ks + c
+// (lane l of a 4-lane group, c = 0..3) sits at K index 16 ks + 2 l + (c & 1)
+// + 8 (c >> 1) of K step ks, and W1's columns follow the same order, which
+// makes a lane's B fragment of an N tile one 16-byte load of its W1 row.
+// ---------------------------------------------------------------------------
+template <int IN>
+struct WarpSmem {
+    uint4 w1[kHidden * kFeatDim / 8];   // W1 (z columns) as BF16: channels 8 j .. 8 j + 7 of unit h at [4 h + j]
+    float4 bw[kHidden / 2];             // (b1, W2) of units 2 j and 2 j + 1
+    float4 ex[kHidden];                 // in_dim 35: (W1x_0, W1x_1, W1x_2, 0) per unit
+    uint4 zs[kTM / 32][4][32];          // per warp, gather round and lane: the lane's BF16 z channels
+    float4 xs[kTM / 32][4][IN == kFeatDim ? 1 : 32];   // in_dim 35: x of the slot the lane gathered
+};
+
+__device__ __forceinline__ uint32_t bf16x2_bits(float lo, float hi) {
+    const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+// Bits 2 q and 2 q + 1 of x (q = 0..3) moved to bits 8 q and 8 q + 1.
+__device__ __forceinline__ uint32_t spread_pairs(uint32_t x) {
+    return (x & 3u) | ((x & 0xcu) << 6) | ((x & 0x30u) << 12) | ((x & 0xc0u) << 18);
+}
+
+template <int IN>
+__device__ __forceinline__ void stage_warp_decoder(WarpSmem<IN>& S, const DecPtrsB& dp) {
+    constexpr int OFF = IN - kFeatDim;
+    for (int i = threadIdx.x; i < kHidden * kFeatDim / 8; i += blockDim.x) {
+        const float* w = dp.W1 + (i >> 2) * IN + OFF + 8 * (i & 3);
+        S.w1[i] = make_uint4(bf16x2_bits(w[0], w[1]), bf16x2_bits(w[2], w[3]), bf16x2_bits(w[4], w[5]),
+                             bf16x2_bits(w[6], w[7]));
+    }
+    for (int j = threadIdx.x; j < kHidden / 2; j += blockDim.x)
+        S.bw[j] = make_float4(dp.b1[2 * j], dp.W2[2 * j], dp.b1[2 * j + 1], dp.W2[2 * j + 1]);
+    for (int h = threadIdx.x; h < kHidden; h += blockDim.x)
+        S.ex[h] = OFF ? make_float4(dp.W1[h * IN], dp.W1[h * IN + 1], dp.W1[h * IN + 2], 0.f)
+                      : make_float4(0.f, 0.f, 0.f, 0.f);
+    // rows of idle slots stay finite
+    for (int i = threadIdx.x; i < (int)(sizeof(S.zs) / 16); i += blockDim.x)
+        (&S.zs[0][0][0])[i] = make_uint4(0u, 0u, 0u, 0u);
+    for (int i = threadIdx.x; i < (int)(sizeof(S.xs) / 16); i += blockDim.x)
+        (&S.xs[0][0][0])[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+// One row's terms of units u and u + 1: pre = acc + b1 (+ W1x . x), the
+// W2-weighted ReLU added to part, the ReLU bits set at sh and sh + 1.
+template <int IN>
+__device__ __forceinline__ void warp_unit2(const WarpSmem<IN>& S, int u, const float4& e, float c0, float c1,
+                                           const float (&x)[3], float& part, uint32_t& bits, int sh) {
+    float p0 = c0 + e.x, p1 = c1 + e.z;
+    if constexpr (IN != kFeatDim) {
+        const float4 w0 = S.ex[u], w1 = S.ex[u + 1];
+        p0 = fmaf(w0.x, x[0], fmaf(w0.y, x[1], fmaf(w0.z, x[2], p0)));
+        p1 = fmaf(w1.x, x[0], fmaf(w1.y, x[1], fmaf(w1.z, x[2], p1)));
+    }
+    part = fmaf(e.y, fmaxf(p0, 0.0f), part);
+    part = fmaf(e.w, fmaxf(p1, 0.0f), part);
+    bits |= (p0 > 0.0f ? 1u : 0u) << sh;
+    bits |= (p1 > 0.0f ? 1u : 0u) << (sh + 1);
+}
+
+// Decodes the warp's gathered rows (S.zs / S.xs of this warp; row h = 0..3
+// of a lane is the slot its group gathered in round h, and the active slots
+// were handed out in rank order, the (8 r + g)-th to group g of round r):
+// returns sum_h W2_h relu(pre_h) (without b2) of this lane's slot, and in
+// cm[h] the ReLU bits this lane holds of row h (bit 2 nt (+ 1) for unit
+// 8 nt + 2 (lane % 4) (+ 1)).  Called by the whole warp, converged.
+template <int IN>
+__device__ __forceinline__ float warp_decode(const WarpSmem<IN>& S, int warp, int lane, unsigned am,
+                                             uint32_t (&cm)[4]) {
+    const int g4 = lane >> 2, l4 = lane & 3;
+    const bool two = __popc(am) > 16;
+    // A fragments af[8 mt + 4 ks + e] (e as in mma_bf16_16816): rows g4 and
+    // g4 + 8 of M tile mt are rows 2 mt and 2 mt + 1 of the lane
+    uint32_t af[16];
+    float rx[4][3];
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+        const uint4 z = (h < 2 || two) ? S.zs[warp][h][lane] : make_uint4(0u, 0u, 0u, 0u);
+        const int b = 8 * (h >> 1) + (h & 1);
+        af[b] = z.x;
+        af[b + 2] = z.y;
+        af[b + 4] = z.z;
+        af[b + 6] = z.w;
+        if constexpr (IN != kFeatDim) {
+            const float4 xv = (h < 2 || two) ? S.xs[warp][h][lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+            rx[h][0] = xv.x;
+            rx[h][1] = xv.y;
+            rx[h][2] = xv.z;
+        } else {
+            rx[h][0] = rx[h][1] = rx[h][2] = 0.f;
+        }
+    }
+    // 16 N tiles: lane (g4, l4) sums units 8 nt + 2 l4 (+ 1) of its rows
+    float part[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int h = 0; h < 4; ++h) cm[h] = 0u;
+#pragma unroll
+    for (int nt = 0; nt < kHidden / 8; ++nt) {
+        const uint4 bb = S.w1[(8 * nt + g4) * 4 + l4];
+        const int u = 8 * nt + 2 * l4;
+        const float4 e = S.bw[u >> 1];
+        float c[4] = {0.f, 0.f, 0.f, 0.f};
+        mma_bf16_16816(c, af[0], af[1], af[2], af[3], make_uint2(bb.x, bb.y));
+        mma_bf16_16816(c, af[4], af[5], af[6], af[7], make_uint2(bb.z, bb.w));
+        warp_unit2<IN>(S, u, e, c[0], c[1], rx[0], part[0], cm[0], 2 * nt);
+        warp_unit2<IN>(S, u, e, c[2], c[3], rx[1], part[1], cm[1], 2 * nt);
+        if (two) {
+            float c2[4] = {0.f, 0.f, 0.f, 0.f};
+            mma_bf16_16816(c2, af[8], af[9], af[10], af[11], make_uint2(bb.x, bb.y));
+            mma_bf16_16816(c2, af[12], af[13], af[14], af[15], make_uint2(bb.z, bb.w));
+            warp_unit2<IN>(S, u, e, c2[0], c2[1], rx[2], part[2], cm[2], 2 * nt);
+            warp_unit2<IN>(S, u, e, c2[2], c2[3], rx[3], part[3], cm[3], 2 * nt);
+        }
+    }
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+        part[h] += __shfl_xor_sync(0xffffffffu, part[h], 1);
+        part[h] += __shfl_xor_sync(0xffffffffu, part[h], 2);
+    }
+    // this lane's slot: round rank / 8 of group rank % 8
+    const int rank = __popc(am & ((1u << lane) - 1u));
+    const int src = 4 * (rank & 7), rsel = rank >> 3;
+    float dsum = 0.f;
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+        const float v = __shfl_sync(0xffffffffu, part[h], src);
+        dsum = rsel == h ? v : dsum;
+    }
+    return dsum;
+}
+
+// The 128-bit ReLU mask (bit h: pre_h > 0) of this lane's slot from the
+// warp_decode bits: word w of a row (units 32 w ..) has lane j of the group
+// holding its bits 8 q + 2 j (+ 1) at bits 8 w + 2 q (+ 1) of cm; lane l4
+// assembles word l4 of each row, then the slot's lane collects its row.
+// Called by the whole warp, converged.
+__device__ __forceinline__ uint4 warp_row_mask(const uint32_t (&cm)[4], int lane, unsigned am) {
+    const int l4 = lane & 3, gb4 = (lane >> 2) << 2;
+    uint32_t wd[4];
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+        uint32_t acc = 0u;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const uint32_t o = __shfl_sync(0xffffffffu, cm[h], gb4 + j);
+            acc |= spread_pairs((o >> (8 * l4)) & 0xffu) << (2 * j);
+        }
+        wd[h] = acc;
+    }
+    const int rank = __popc(am & ((1u << lane) - 1u));
+    const int src = 4 * (rank & 7), rsel = rank >> 3;
+    uint32_t m[4];
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+        uint32_t v = 0u;
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            const uint32_t o = __shfl_sync(0xffffffffu, wd[h], src + w);
+            v = rsel == h ? o : v;
+        }
+        m[w] = v;
+    }
+    return make_uint4(m[0], m[1], m[2], m[3]);
+}
+
+template <typename T, int IN>
+__global__ void __launch_bounds__(kTM, kCtasPerSm) k_trace_warp_bf16(const DecPtrsB dp, const Tables tb,
+                                                                     const TraceArgs A) {
+    __shared__ __align__(16) WarpSmem<IN> S;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    stage_warp_decoder<IN>(S, dp);
+    __syncthreads();
+    const float b2 = __ldg(dp.b2);
+    const bool want_mask = A.hit_mask != nullptr;
+    RaySlot st;
+    st.ray = -1;
+    st.hit_ray = -1;
+    RayQueue Qu;
+    Qu.init();
+    const int d0 = gather_first_depth(tb);
+    const int g4 = lane >> 2, l4 = lane & 3, gb4 = g4 << 2;
+    const unsigned gm4 = 0xfu << gb4;
+    for (;;) {
+        refill(st, Qu, A, tb, lane);
+        const bool act = st.ray >= 0;
+        const unsigned am = __ballot_sync(0xffffffffu, act);
+        if (am == 0u) break;   // the queue is exhausted and the warp has no ray left
+        const int na = __popc(am);
+        const float x0 = fmaf(st.t, st.dx, st.ox), x1 = fmaf(st.t, st.dy, st.oy), x2 = fmaf(st.t, st.dz, st.oz);
+        const float q0 = __fadd_rn(x0, 1.0f), q1 = __fadd_rn(x1, 1.0f), q2 = __fadd_rn(x2, 1.0f);
+        // gather, with the warp's active slots compacted: group g4 of round
+        // r takes the (8 r + g4)-th, whose z becomes row g4 (r even) or
+        // g4 + 8 (r odd) of M tile r / 2; the first level's corner ids of the
+        // next round's slot load while this round's slot is gathered
+        int ns = g4 < na ? kth_set_bit(am, g4) : 32;
+        const int vox0 = __shfl_sync(0xffffffffu, st.vox, ns & 31);
+        int2 nids = ns < 32 ? __ldg(corner_ids(tb, A.D, vox0, d0, l4)) : make_int2(0, 0);
+#pragma unroll 1
+        for (int r = 0; r < 4; ++r) {
+            if (8 * r >= na) break;
+            const int s = ns & 31;
+            const bool sact = ns < 32;
+            const int2 ids = nids;
+            const int svox = __shfl_sync(0xffffffffu, st.vox, s);
+            const uint32_t sijk = __shfl_sync(0xffffffffu, st.ijk, s);
+            const float s0 = __shfl_sync(0xffffffffu, q0, s);
+            const float s1 = __shfl_sync(0xffffffffu, q1, s);
+            const float s2 = __shfl_sync(0xffffffffu, q2, s);
+            float sx0 = 0.f, sx1 = 0.f, sx2 = 0.f;
+            if constexpr (IN != kFeatDim) {
+                sx0 = __shfl_sync(0xffffffffu, x0, s);
+                sx1 = __shfl_sync(0xffffffffu, x1, s);
+                sx2 = __shfl_sync(0xffffffffu, x2, s);
+            }
+            if (r < 3) {
+                const int k = 8 * (r + 1) + g4;
+                ns = k < na ? kth_set_bit(am, k) : 32;
+                const int nvox = __shfl_sync(0xffffffffu, st.vox, ns & 31);
+                if (ns < 32) nids = __ldg(corner_ids(tb, A.D, nvox, d0, l4));
+            }
+            if (sact) {
+                float4 za, zb;
+                gather_slot4_ids<T>(tb, A.D, svox, sijk, s0, s1, s2, gm4, gb4, l4, za, zb, ids);
+                // kept lane-private in shared memory until the MMAs (the
+                // gather needs the registers)
+                S.zs[warp][r][lane] = make_uint4(bf16x2_bits(za.x, za.y), bf16x2_bits(za.z, za.w),
+                                                 bf16x2_bits(zb.x, zb.y), bf16x2_bits(zb.z, zb.w));
+                if constexpr (IN != kFeatDim) S.xs[warp][r][lane] = make_float4(sx0, sx1, sx2, 0.f);
+            }
+        }
+        prefetch_next_ijk(st, A, tb);
+        uint32_t cm[4];
+        const float dsum = warp_decode<IN>(S, warp, lane, am, cm);
+        if (act) step_update(st, b2 + dsum, A, tb);
+        const uint4 mask = want_mask && __any_sync(0xffffffffu, st.hit_ray >= 0) ? warp_row_mask(cm, lane, am)
+                                                                                : make_uint4(0u, 0u, 0u, 0u);
+        publish_hits(st, A, lane, mask);
+    }
+}
+
+// Batched tracing with the BF16 warp-level decode (the decode of
+// k_trace_warp_bf16, so every output is bit-identical to per-image calls):
+// the groups one after another, each warp taking rays from the group's queue
+// until it is empty; the CTA meets only to stage the next group's decoder.
+template <typename T, int IN>
+__global__ void __launch_bounds__(kTM, kCtasPerSm) k_trace_batch_warp(const TraceJob* __restrict__ jobs,
+                                                                    const JobGroup* __restrict__ groups,
+                                                                    int ngroups) {
+    __shared__ __align__(16) WarpSmem<IN> S;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g4 = lane >> 2, l4 = lane & 3, gb4 = g4 << 2;
+    const unsigned gm4 = 0xfu << gb4;
+    for (int gi = 0; gi < ngroups; ++gi) {
+        const JobGroup G = groups[gi];
+        const DecPtrsB dp{G.W1, G.b1, G.W2, G.b2, G.z_scale, 0};
+        __syncthreads();                      // every warp is done with the previous group's decoder
+        stage_warp_decoder<IN>(S, dp);
+        __syncthreads();
+        const float b2 = __ldg(dp.b2);
+        RaySlot st;
+        st.ray = -1;
+        st.hit_ray = -1;
+        st.job = G.j0;
+        RayQueue Qu;
+        Qu.init();
+        for (;;) {
+            refill_batch(st, Qu, G, jobs, lane);
+            const bool act = st.ray >= 0;
+            const unsigned am = __ballot_sync(0xffffffffu, act);
+            if (am == 0u) break;              // the group's queue is exhausted and the warp has no ray left
+            const int na = __popc(am);
+            const float x0 = fmaf(st.t, st.dx, st.ox), x1 = fmaf(st.t, st.dy, st.oy), x2 = fmaf(st.t, st.dz, st.oz);
+            const float q0 = __fadd_rn(x0, 1.0f), q1 = __fadd_rn(x1, 1.0f), q2 = __fadd_rn(x2, 1.0f);
+            // the active slots in rank order, the (8 r + g4)-th to group g4 of round r
+#pragma unroll 1
+            for (int r = 0; r < 4; ++r) {
+                if (8 * r >= na) break;
+                const int k = 8 * r + g4;
+                const int ns = k < na ? kth_set_bit(am, k) : 32;
+                const int s = ns & 31;
+                const int sjob = __shfl_sync(0xffffffffu, st.job, s);
+                const int svox = __shfl_sync(0xffffffffu, st.vox, s);
+                const uint32_t sijk = __shfl_sync(0xffffffffu, st.ijk, s);
+                const float s0 = __shfl_sync(0xffffffffu, q0, s);
+                const float s1 = __shfl_sync(0xffffffffu, q1, s);
+                const float s2 = __shfl_sync(0xffffffffu, q2, s);
+                float sx0 = 0.f, sx1 = 0.f, sx2 = 0.f;
+                if constexpr (IN != kFeatDim) {
+                    sx0 = __shfl_sync(0xffffffffu, x0, s);
+                    sx1 = __shfl_sync(0xffffffffu, x1, s);
+                    sx2 = __shfl_sync(0xffffffffu, x2, s);
+                }
+                if (ns < 32) {
+                    float4 za, zb;
+                    gather_slot4<T>(jobs[sjob].tb, jobs[sjob].A.D, svox, sijk, s0, s1, s2, gm4, gb4, l4, za, zb);
+                    S.zs[warp][r][lane] = make_uint4(bf16x2_bits(za.x, za.y), bf16x2_bits(za.z, za.w),
+                                                     bf16x2_bits(zb.x, zb.y), bf16x2_bits(zb.z, zb.w));
+                    if constexpr (IN != kFeatDim) S.xs[warp][r][lane] = make_float4(sx0, sx1, sx2, 0.f);
+                }
+            }
+            uint32_t cm[4];
+            const float dsum = warp_decode<IN>(S, warp, lane, am, cm);
+            if (act) step_update(st, b2 + dsum, jobs[st.job].A, jobs[st.job].tb);
+            const uint4 mask = __any_sync(0xffffffffu, st.hit_ray >= 0) ? warp_row_mask(cm, lane, am)
+                                                                        : make_uint4(0u, 0u, 0u, 0u);
+            publish_hits_batch(st, jobs, mask);
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -589,8 +917,14 @@ __global__ void __launch_bounds__(kTM, kCtasPerSm) k_trace_batch(const TraceJob*
 template <typename T, int IN, bool FP8>
 void go_batch1(const TraceJob* jobs, const JobGroup* groups, int ngroups, int* err, int grid, cudaStream_t st) {
     static std::atomic<unsigned long long> done{0};
-    once_per_device(done, [] { prefer_l1(k_trace_batch<T, IN, FP8>); });
-    k_trace_batch<T, IN, FP8><<<grid, kTM, kDynSmem, st>>>(jobs, groups, ngroups, err, mma_wait_polls());
+    if constexpr (FP8) {
+        once_per_device(done, [] { prefer_l1(k_trace_batch<T, IN, true>); });
+        k_trace_batch<T, IN, true><<<grid, kTM, kDynSmem, st>>>(jobs, groups, ngroups, err, mma_wait_polls());
+    } else {
+        // BF16: the warp-level decode, as in per-image tracing
+        once_per_device(done, [] { prefer_l1(k_trace_batch_warp<T, IN>); });
+        k_trace_batch_warp<T, IN><<<grid, kTM, 0, st>>>(jobs, groups, ngroups);
+    }
 }
 
 DecPtrsB bptrs(const nglod_decoder* dec, float z_scale) {
@@ -618,8 +952,15 @@ void configure_tc(K kernel) {
 template <typename T, int IN, int PM>
 void go_trace1(const DecPtrsB& P, const Tables& tb, const TraceArgs& A, int* err, int grid, cudaStream_t st) {
     static std::atomic<unsigned long long> done{0};
-    once_per_device(done, [] { configure_tc<PM>(k_trace_bf16<T, IN, PM>); });
-    k_trace_bf16<T, IN, PM><<<grid, kTM, PM == 2 ? kDynSmem3 : kDynSmem, st>>>(P, tb, A, err);
+    if constexpr (PM == 0) {
+        // BF16: the warp-level decode (its shared memory, ~20 KB a CTA, leaves
+        // the rest of the storage to L1)
+        once_per_device(done, [] { prefer_l1(k_trace_warp_bf16<T, IN>); });
+        k_trace_warp_bf16<T, IN><<<grid, kTM, 0, st>>>(P, tb, A);
+    } else {
+        once_per_device(done, [] { configure_tc<PM>(k_trace_bf16<T, IN, PM>); });
+        k_trace_bf16<T, IN, PM><<<grid, kTM, PM == 2 ? kDynSmem3 : kDynSmem, st>>>(P, tb, A, err);
+    }
 }
 
 template <typename T, int IN>
