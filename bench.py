@@ -595,8 +595,8 @@ def trace_roofline(W, res, mode, peaks, levels=None, ceilings=None):
     interp, layer1, outl = flops_per_query(W["dec"].in_dim, levels, mode)
     q = res["queries_per_frame"]
     sec = res["ms_trace"] * 1e-3
-    # BF16: warp-level MMAs (k_trace_warp_bf16); FP8 and three-term FP32: tcgen05 (k_trace_bf16)
-    kern = {"f32": "k_trace_f32", "bf16": "k_trace_warp_bf16"}.get(mode, "k_trace_bf16")
+    # BF16 and three-term FP32: warp-level MMAs (k_trace_warp_bf16); FP8: tcgen05 (k_trace_bf16)
+    kern = {"f32": "k_trace_f32", "fp8": "k_trace_bf16"}.get(mode, "k_trace_warp_bf16")
     if mode != "f32":
         tf = peaks.get("bf16_tflops", 1900.0)
         achieved = q * layer1 / sec / 1e12
@@ -605,7 +605,7 @@ def trace_roofline(W, res, mode, peaks, levels=None, ceilings=None):
                 "flops_per_query": layer1, "queries_per_launch": q,
                 "peak_source": "MEASURED_PEAKS.json bf16_tflops burst (of measured)",
                 "note": "the kernel is bound by feature-gather latency (L1/L2), not by the 128x32 contraction"
-                        + (" (decoded per warp with mma.sync m16n8k16, no CTA-wide tile)" if mode == "bf16" else ""),
+                        + (" (decoded per warp with mma.sync m16n8k16, no CTA-wide tile)" if mode != "fp8" else ""),
                 **gather_fracs(q, levels, sec, ceilings)}
     if "ffma_tflops" in ceilings:
         peak, src = ceilings["ffma_tflops"], "measured FFMA probe (of measured)"

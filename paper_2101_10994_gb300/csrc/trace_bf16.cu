@@ -4,14 +4,15 @@
 // pre[q][h] = sum_k z[q][k] W1[h][k], N = 128 hidden units, K = 32 feature
 // channels.
 //
-// BF16 sphere tracing (k_trace_warp_bf16): each warp decodes its own 32
-// slots with warp-level MMAs (mma.sync m16n8k16, BF16 operands, FP32
-// accumulation), the A operand taken from the registers the 4-lane gather
-// groups filled, so no warp waits for another.
+// Sphere tracing with the BF16 or the three-term FP32 decode, per image or
+// batched (k_trace_warp_bf16, k_trace_batch_warp): each warp decodes its own
+// 32 slots with warp-level MMAs (mma.sync m16n8k16, BF16 operands, FP32
+// accumulation), the A operand built from the z the lane gathered itself, so
+// no warp waits for another.
 //
-// tcgen05 (the FP8 and three-term FP32 decodes of the tracer, sdf_query,
-// batches and level blending): each CTA owns 128 query slots (thread i <->
-// A-tile row i <-> tensor-memory lane i):
+// tcgen05 (the FP8 tracer, sdf_query, FP8 batches and level blending): each
+// CTA owns 128 query slots (thread i <-> A-tile row i <-> tensor-memory lane
+// i):
 //   1. gather: 4-lane groups interpolate each slot's z (FP32, 8 channels a
 //      lane) and write it straight into the A tile, laid out as the MMA's
 //      canonical K-major operand (8-row x 16-byte core matrices);
@@ -29,6 +30,7 @@
 #include <cuda_fp8.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "nglod_internal.cuh"
 #include "query_common.cuh"
@@ -362,7 +364,7 @@ __device__ __forceinline__ bool mma_any(typename TcSmem<PM>::type& S, uint32_t t
 }
 
 // ---------------------------------------------------------------------------
-// sphere tracing, FP8 (PM = 1) or three-term FP32 (PM = 2) decode on tcgen05
+// sphere tracing on tcgen05 (the FP8 decode, PM = 1, is the one launched)
 // ---------------------------------------------------------------------------
 template <typename T, int IN, int PM>
 __global__ void __launch_bounds__(kTM, kCtasPerSm) k_trace_bf16(const DecPtrsB dp, const Tables tb, const TraceArgs A,
@@ -466,12 +468,26 @@ __global__ void __launch_bounds__(kTM, kCtasPerSm) k_trace_bf16(const DecPtrsB d
 // makes a lane's B fragment of an N tile one 16-byte load of its W1 row.
 // ---------------------------------------------------------------------------
 template <int IN>
-struct WarpSmem {
+struct WarpDec {
     uint4 w1[kHidden * kFeatDim / 8];   // W1 (z columns) as BF16: channels 8 j .. 8 j + 7 of unit h at [4 h + j]
     float4 bw[kHidden / 2];             // (b1, W2) of units 2 j and 2 j + 1
-    float4 ex[kHidden];                 // in_dim 35: (W1x_0, W1x_1, W1x_2, 0) per unit
-    uint4 zs[kTM / 32][4][32];          // per warp, gather round and lane: the lane's BF16 z channels
-    float4 xs[kTM / 32][4][IN == kFeatDim ? 1 : 32];   // in_dim 35: x of the slot the lane gathered
+    float4 ex[IN == kFeatDim ? 1 : kHidden];   // in_dim 35: (W1x_0, W1x_1, W1x_2, 0) per unit
+};
+// Per warp, gather round and lane: the lane's BF16 z channels (lane-private:
+// kept here between the gather and the MMAs, which need the registers).
+struct WarpZ {
+    uint4 zs[kTM / 32][4][32];
+};
+// in_dim 35: the x of the slot each lane gathered in each round.
+template <int IN>
+struct WarpX {
+    float4 xs[kTM / 32][4][IN == kFeatDim ? 1 : 32];
+};
+template <int IN>
+struct WarpSmem {
+    WarpDec<IN> dec;
+    WarpZ z;
+    WarpX<IN> x;
 };
 
 __device__ __forceinline__ uint32_t bf16x2_bits(float lo, float hi) {
@@ -485,7 +501,7 @@ __device__ __forceinline__ uint32_t spread_pairs(uint32_t x) {
 }
 
 template <int IN>
-__device__ __forceinline__ void stage_warp_decoder(WarpSmem<IN>& S, const DecPtrsB& dp) {
+__device__ __forceinline__ void stage_warp_decoder(WarpDec<IN>& S, const DecPtrsB& dp) {
     constexpr int OFF = IN - kFeatDim;
     for (int i = threadIdx.x; i < kHidden * kFeatDim / 8; i += blockDim.x) {
         const float* w = dp.W1 + (i >> 2) * IN + OFF + 8 * (i & 3);
@@ -494,20 +510,29 @@ __device__ __forceinline__ void stage_warp_decoder(WarpSmem<IN>& S, const DecPtr
     }
     for (int j = threadIdx.x; j < kHidden / 2; j += blockDim.x)
         S.bw[j] = make_float4(dp.b1[2 * j], dp.W2[2 * j], dp.b1[2 * j + 1], dp.W2[2 * j + 1]);
-    for (int h = threadIdx.x; h < kHidden; h += blockDim.x)
-        S.ex[h] = OFF ? make_float4(dp.W1[h * IN], dp.W1[h * IN + 1], dp.W1[h * IN + 2], 0.f)
-                      : make_float4(0.f, 0.f, 0.f, 0.f);
-    // rows of idle slots stay finite
-    for (int i = threadIdx.x; i < (int)(sizeof(S.zs) / 16); i += blockDim.x)
-        (&S.zs[0][0][0])[i] = make_uint4(0u, 0u, 0u, 0u);
-    for (int i = threadIdx.x; i < (int)(sizeof(S.xs) / 16); i += blockDim.x)
-        (&S.xs[0][0][0])[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if constexpr (OFF != 0)
+        for (int h = threadIdx.x; h < kHidden; h += blockDim.x)
+            S.ex[h] = make_float4(dp.W1[h * IN], dp.W1[h * IN + 1], dp.W1[h * IN + 2], 0.f);
+}
+
+// Rows of idle slots stay finite.
+template <int IN>
+__device__ __forceinline__ void clear_warp_stash(WarpZ& Z, WarpX<IN>& X) {
+    for (int i = threadIdx.x; i < (int)(sizeof(Z.zs) / 16); i += blockDim.x)
+        (&Z.zs[0][0][0])[i] = make_uint4(0u, 0u, 0u, 0u);
+    for (int i = threadIdx.x; i < (int)(sizeof(X.xs) / 16); i += blockDim.x)
+        (&X.xs[0][0][0])[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+// The lane's 8 gathered channels as BF16 pairs (channels 8 l4 + 0..7).
+__device__ __forceinline__ uint4 pack_bf16x8(float4 a, float4 b) {
+    return make_uint4(bf16x2_bits(a.x, a.y), bf16x2_bits(a.z, a.w), bf16x2_bits(b.x, b.y), bf16x2_bits(b.z, b.w));
 }
 
 // One row's terms of units u and u + 1: pre = acc + b1 (+ W1x . x), the
 // W2-weighted ReLU added to part, the ReLU bits set at sh and sh + 1.
-template <int IN>
-__device__ __forceinline__ void warp_unit2(const WarpSmem<IN>& S, int u, const float4& e, float c0, float c1,
+template <int IN, class Dec>
+__device__ __forceinline__ void warp_unit2(const Dec& S, int u, const float4& e, float c0, float c1,
                                            const float (&x)[3], float& part, uint32_t& bits, int sh) {
     float p0 = c0 + e.x, p1 = c1 + e.z;
     if constexpr (IN != kFeatDim) {
@@ -521,15 +546,15 @@ __device__ __forceinline__ void warp_unit2(const WarpSmem<IN>& S, int u, const f
     bits |= (p1 > 0.0f ? 1u : 0u) << (sh + 1);
 }
 
-// Decodes the warp's gathered rows (S.zs / S.xs of this warp; row h = 0..3
+// Decodes the warp's gathered rows (Z.zs / X.xs of this warp; row h = 0..3
 // of a lane is the slot its group gathered in round h, and the active slots
 // were handed out in rank order, the (8 r + g)-th to group g of round r):
 // returns sum_h W2_h relu(pre_h) (without b2) of this lane's slot, and in
 // cm[h] the ReLU bits this lane holds of row h (bit 2 nt (+ 1) for unit
 // 8 nt + 2 (lane % 4) (+ 1)).  Called by the whole warp, converged.
 template <int IN>
-__device__ __forceinline__ float warp_decode(const WarpSmem<IN>& S, int warp, int lane, unsigned am,
-                                             uint32_t (&cm)[4]) {
+__device__ __forceinline__ float warp_decode(const WarpDec<IN>& S, const WarpZ& Z, const WarpX<IN>& X, int warp,
+                                             int lane, unsigned am, uint32_t (&cm)[4]) {
     const int g4 = lane >> 2, l4 = lane & 3;
     const bool two = __popc(am) > 16;
     // A fragments af[8 mt + 4 ks + e] (e as in mma_bf16_16816): rows g4 and
@@ -538,14 +563,14 @@ __device__ __forceinline__ float warp_decode(const WarpSmem<IN>& S, int warp, in
     float rx[4][3];
 #pragma unroll
     for (int h = 0; h < 4; ++h) {
-        const uint4 z = (h < 2 || two) ? S.zs[warp][h][lane] : make_uint4(0u, 0u, 0u, 0u);
+        const uint4 z = (h < 2 || two) ? Z.zs[warp][h][lane] : make_uint4(0u, 0u, 0u, 0u);
         const int b = 8 * (h >> 1) + (h & 1);
         af[b] = z.x;
         af[b + 2] = z.y;
         af[b + 4] = z.z;
         af[b + 6] = z.w;
         if constexpr (IN != kFeatDim) {
-            const float4 xv = (h < 2 || two) ? S.xs[warp][h][lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float4 xv = (h < 2 || two) ? X.xs[warp][h][lane] : make_float4(0.f, 0.f, 0.f, 0.f);
             rx[h][0] = xv.x;
             rx[h][1] = xv.y;
             rx[h][2] = xv.z;
@@ -626,12 +651,166 @@ __device__ __forceinline__ uint4 warp_row_mask(const uint32_t (&cm)[4], int lane
     return make_uint4(m[0], m[1], m[2], m[3]);
 }
 
-template <typename T, int IN>
+// ---------------------------------------------------------------------------
+// sphere tracing, FP32-accurate decode on warp-level MMAs: z and W1 (z
+// columns) each as three BF16 terms (split3), the six products A_i B_j with
+// i + j <= 2 accumulated smallest first in FP32, as in the tcgen05 form, per
+// warp with mma.sync.  The gathered z waits in shared memory as FP32 and is
+// split when its fragments are built.
+// ---------------------------------------------------------------------------
+template <int IN>
+struct WarpDec3 {
+    uint4 w1[3][kHidden * kFeatDim / 8];   // the three BF16 terms of W1, each laid out as WarpDec::w1
+    float4 bw[kHidden / 2];
+    float4 ex[IN == kFeatDim ? 1 : kHidden];
+};
+struct WarpZF {
+    float4 zs[kTM / 32][4][32][2];         // per warp, round and lane: the lane's 8 FP32 z channels
+};
+template <int IN>
+struct WarpSmem3 {
+    WarpDec3<IN> dec;
+    WarpZF z;
+    WarpX<IN> x;
+};
+
+template <int IN>
+__device__ __forceinline__ void stage_warp_decoder3(WarpDec3<IN>& S, const DecPtrsB& dp) {
+    constexpr int OFF = IN - kFeatDim;
+    for (int i = threadIdx.x; i < kHidden * kFeatDim / 8; i += blockDim.x) {
+        const float* w = dp.W1 + (i >> 2) * IN + OFF + 8 * (i & 3);
+        __nv_bfloat16 t[3][8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) split3(w[c], t[0][c], t[1][c], t[2][c]);
+#pragma unroll
+        for (int p = 0; p < 3; ++p) {
+            uint32_t u[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const __nv_bfloat162 v = __halves2bfloat162(t[p][2 * c], t[p][2 * c + 1]);
+                u[c] = *reinterpret_cast<const uint32_t*>(&v);
+            }
+            S.w1[p][i] = make_uint4(u[0], u[1], u[2], u[3]);
+        }
+    }
+    for (int j = threadIdx.x; j < kHidden / 2; j += blockDim.x)
+        S.bw[j] = make_float4(dp.b1[2 * j], dp.W2[2 * j], dp.b1[2 * j + 1], dp.W2[2 * j + 1]);
+    if constexpr (OFF != 0)
+        for (int h = threadIdx.x; h < kHidden; h += blockDim.x)
+            S.ex[h] = make_float4(dp.W1[h * IN], dp.W1[h * IN + 1], dp.W1[h * IN + 2], 0.f);
+}
+
+// The three BF16 terms of a pair of FP32 values, as BF16 pairs.
+__device__ __forceinline__ void split3_pair(float a, float b, uint32_t& p0, uint32_t& p1, uint32_t& p2) {
+    __nv_bfloat16 a0, a1, a2, b0, b1, b2;
+    split3(a, a0, a1, a2);
+    split3(b, b0, b1, b2);
+    const __nv_bfloat162 v0 = __halves2bfloat162(a0, b0), v1 = __halves2bfloat162(a1, b1),
+                         v2 = __halves2bfloat162(a2, b2);
+    p0 = *reinterpret_cast<const uint32_t*>(&v0);
+    p1 = *reinterpret_cast<const uint32_t*>(&v1);
+    p2 = *reinterpret_cast<const uint32_t*>(&v2);
+}
+
+// warp_decode with the three-term products (same rows, results and bits).
+template <int IN>
+__device__ __forceinline__ float warp_decode3(const WarpDec3<IN>& S, const WarpZF& Z, const WarpX<IN>& X, int warp,
+                                              int lane, unsigned am, uint32_t (&cm)[4]) {
+    const int g4 = lane >> 2, l4 = lane & 3;
+    const bool two = __popc(am) > 16;
+    // af[p][8 mt + 4 ks + e]: term p of the A fragments
+    uint32_t af[3][16];
+    float rx[4][3];
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+        float4 za = make_float4(0.f, 0.f, 0.f, 0.f), zb = za;
+        if (h < 2 || two) {
+            za = Z.zs[warp][h][lane][0];
+            zb = Z.zs[warp][h][lane][1];
+        }
+        const int b = 8 * (h >> 1) + (h & 1);
+        split3_pair(za.x, za.y, af[0][b], af[1][b], af[2][b]);
+        split3_pair(za.z, za.w, af[0][b + 2], af[1][b + 2], af[2][b + 2]);
+        split3_pair(zb.x, zb.y, af[0][b + 4], af[1][b + 4], af[2][b + 4]);
+        split3_pair(zb.z, zb.w, af[0][b + 6], af[1][b + 6], af[2][b + 6]);
+        if constexpr (IN != kFeatDim) {
+            const float4 xv = (h < 2 || two) ? X.xs[warp][h][lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+            rx[h][0] = xv.x;
+            rx[h][1] = xv.y;
+            rx[h][2] = xv.z;
+        } else {
+            rx[h][0] = rx[h][1] = rx[h][2] = 0.f;
+        }
+    }
+    constexpr int kPi[6] = {2, 1, 0, 1, 0, 0}, kPj[6] = {0, 1, 2, 0, 1, 0};
+    float part[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int h = 0; h < 4; ++h) cm[h] = 0u;
+#pragma unroll
+    for (int nt = 0; nt < kHidden / 8; ++nt) {
+        const int wi = (8 * nt + g4) * 4 + l4;
+        const uint4 bb[3] = {S.w1[0][wi], S.w1[1][wi], S.w1[2][wi]};
+        const int u = 8 * nt + 2 * l4;
+        const float4 e = S.bw[u >> 1];
+        float c[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int t = 0; t < 6; ++t) {
+            const uint32_t* a = af[kPi[t]];
+            const uint4& w = bb[kPj[t]];
+            mma_bf16_16816(c, a[0], a[1], a[2], a[3], make_uint2(w.x, w.y));
+            mma_bf16_16816(c, a[4], a[5], a[6], a[7], make_uint2(w.z, w.w));
+        }
+        warp_unit2<IN>(S, u, e, c[0], c[1], rx[0], part[0], cm[0], 2 * nt);
+        warp_unit2<IN>(S, u, e, c[2], c[3], rx[1], part[1], cm[1], 2 * nt);
+        if (two) {
+            float c2[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int t = 0; t < 6; ++t) {
+                const uint32_t* a = af[kPi[t]];
+                const uint4& w = bb[kPj[t]];
+                mma_bf16_16816(c2, a[8], a[9], a[10], a[11], make_uint2(w.x, w.y));
+                mma_bf16_16816(c2, a[12], a[13], a[14], a[15], make_uint2(w.z, w.w));
+            }
+            warp_unit2<IN>(S, u, e, c2[0], c2[1], rx[2], part[2], cm[2], 2 * nt);
+            warp_unit2<IN>(S, u, e, c2[2], c2[3], rx[3], part[3], cm[3], 2 * nt);
+        }
+    }
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+        part[h] += __shfl_xor_sync(0xffffffffu, part[h], 1);
+        part[h] += __shfl_xor_sync(0xffffffffu, part[h], 2);
+    }
+    const int rank = __popc(am & ((1u << lane) - 1u));
+    const int src = 4 * (rank & 7), rsel = rank >> 3;
+    float dsum = 0.f;
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+        const float v = __shfl_sync(0xffffffffu, part[h], src);
+        dsum = rsel == h ? v : dsum;
+    }
+    return dsum;
+}
+
+template <int IN, bool SPLIT>
+using WarpSmemT = std::conditional_t<SPLIT, WarpSmem3<IN>, WarpSmem<IN>>;
+
+// SPLIT: the three-term FP32-accurate decode (warp_decode3), else BF16.
+template <typename T, int IN, bool SPLIT>
 __global__ void __launch_bounds__(kTM, kCtasPerSm) k_trace_warp_bf16(const DecPtrsB dp, const Tables tb,
                                                                      const TraceArgs A) {
-    __shared__ __align__(16) WarpSmem<IN> S;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    WarpSmemT<IN, SPLIT>& S = *reinterpret_cast<WarpSmemT<IN, SPLIT>*>(smem_raw);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    stage_warp_decoder<IN>(S, dp);
+    if constexpr (SPLIT) {
+        stage_warp_decoder3<IN>(S.dec, dp);
+        for (int i = threadIdx.x; i < (int)(sizeof(S.z.zs) / 16); i += blockDim.x)
+            (&S.z.zs[0][0][0][0])[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int i = threadIdx.x; i < (int)(sizeof(S.x.xs) / 16); i += blockDim.x)
+            (&S.x.xs[0][0][0])[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    } else {
+        stage_warp_decoder<IN>(S.dec, dp);
+        clear_warp_stash<IN>(S.z, S.x);
+    }
     __syncthreads();
     const float b2 = __ldg(dp.b2);
     const bool want_mask = A.hit_mask != nullptr;
@@ -684,16 +863,20 @@ __global__ void __launch_bounds__(kTM, kCtasPerSm) k_trace_warp_bf16(const DecPt
             if (sact) {
                 float4 za, zb;
                 gather_slot4_ids<T>(tb, A.D, svox, sijk, s0, s1, s2, gm4, gb4, l4, za, zb, ids);
-                // kept lane-private in shared memory until the MMAs (the
-                // gather needs the registers)
-                S.zs[warp][r][lane] = make_uint4(bf16x2_bits(za.x, za.y), bf16x2_bits(za.z, za.w),
-                                                 bf16x2_bits(zb.x, zb.y), bf16x2_bits(zb.z, zb.w));
-                if constexpr (IN != kFeatDim) S.xs[warp][r][lane] = make_float4(sx0, sx1, sx2, 0.f);
+                if constexpr (SPLIT) {
+                    S.z.zs[warp][r][lane][0] = za;
+                    S.z.zs[warp][r][lane][1] = zb;
+                } else {
+                    S.z.zs[warp][r][lane] = pack_bf16x8(za, zb);
+                }
+                if constexpr (IN != kFeatDim) S.x.xs[warp][r][lane] = make_float4(sx0, sx1, sx2, 0.f);
             }
         }
         prefetch_next_ijk(st, A, tb);
         uint32_t cm[4];
-        const float dsum = warp_decode<IN>(S, warp, lane, am, cm);
+        float dsum;
+        if constexpr (SPLIT) dsum = warp_decode3<IN>(S.dec, S.z, S.x, warp, lane, am, cm);
+        else dsum = warp_decode<IN>(S.dec, S.z, S.x, warp, lane, am, cm);
         if (act) step_update(st, b2 + dsum, A, tb);
         const uint4 mask = want_mask && __any_sync(0xffffffffu, st.hit_ray >= 0) ? warp_row_mask(cm, lane, am)
                                                                                 : make_uint4(0u, 0u, 0u, 0u);
@@ -717,7 +900,8 @@ __global__ void __launch_bounds__(kTM, kCtasPerSm) k_trace_batch_warp(const Trac
         const JobGroup G = groups[gi];
         const DecPtrsB dp{G.W1, G.b1, G.W2, G.b2, G.z_scale, 0};
         __syncthreads();                      // every warp is done with the previous group's decoder
-        stage_warp_decoder<IN>(S, dp);
+        stage_warp_decoder<IN>(S.dec, dp);
+        clear_warp_stash<IN>(S.z, S.x);
         __syncthreads();
         const float b2 = __ldg(dp.b2);
         RaySlot st;
@@ -756,13 +940,12 @@ __global__ void __launch_bounds__(kTM, kCtasPerSm) k_trace_batch_warp(const Trac
                 if (ns < 32) {
                     float4 za, zb;
                     gather_slot4<T>(jobs[sjob].tb, jobs[sjob].A.D, svox, sijk, s0, s1, s2, gm4, gb4, l4, za, zb);
-                    S.zs[warp][r][lane] = make_uint4(bf16x2_bits(za.x, za.y), bf16x2_bits(za.z, za.w),
-                                                     bf16x2_bits(zb.x, zb.y), bf16x2_bits(zb.z, zb.w));
-                    if constexpr (IN != kFeatDim) S.xs[warp][r][lane] = make_float4(sx0, sx1, sx2, 0.f);
+                    S.z.zs[warp][r][lane] = pack_bf16x8(za, zb);
+                    if constexpr (IN != kFeatDim) S.x.xs[warp][r][lane] = make_float4(sx0, sx1, sx2, 0.f);
                 }
             }
             uint32_t cm[4];
-            const float dsum = warp_decode<IN>(S, warp, lane, am, cm);
+            const float dsum = warp_decode<IN>(S.dec, S.z, S.x, warp, lane, am, cm);
             if (act) step_update(st, b2 + dsum, jobs[st.job].A, jobs[st.job].tb);
             const uint4 mask = __any_sync(0xffffffffu, st.hit_ray >= 0) ? warp_row_mask(cm, lane, am)
                                                                         : make_uint4(0u, 0u, 0u, 0u);
@@ -949,14 +1132,29 @@ void configure_tc(K kernel) {
     }
 }
 
+// The warp-level tracers' shared memory: ~20 KB a CTA (BF16), leaving the
+// rest of the storage to L1; the three-term form holds three W1 terms and
+// FP32 z (~41 KB, 53 KB with in_dim 35): a carveout for 4 CTAs.
+template <bool SPLIT, typename K>
+void configure_warp(K kernel, int smem) {
+    if constexpr (SPLIT) {
+        cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             std::min(100, (4 * (smem + 1024) * 100 + 233471) / 233472));
+    } else {
+        prefer_l1(kernel);
+    }
+}
+
 template <typename T, int IN, int PM>
 void go_trace1(const DecPtrsB& P, const Tables& tb, const TraceArgs& A, int* err, int grid, cudaStream_t st) {
     static std::atomic<unsigned long long> done{0};
-    if constexpr (PM == 0) {
-        // BF16: the warp-level decode (its shared memory, ~20 KB a CTA, leaves
-        // the rest of the storage to L1)
-        once_per_device(done, [] { prefer_l1(k_trace_warp_bf16<T, IN>); });
-        k_trace_warp_bf16<T, IN><<<grid, kTM, 0, st>>>(P, tb, A);
+    if constexpr (PM != 1) {
+        // BF16 and three-term FP32: the warp-level decode
+        constexpr bool SPLIT = PM == 2;
+        constexpr int smem = (int)sizeof(WarpSmemT<IN, SPLIT>);
+        once_per_device(done, [] { configure_warp<SPLIT>(k_trace_warp_bf16<T, IN, SPLIT>, smem); });
+        k_trace_warp_bf16<T, IN, SPLIT><<<grid, kTM, smem, st>>>(P, tb, A);
     } else {
         once_per_device(done, [] { configure_tc<PM>(k_trace_bf16<T, IN, PM>); });
         k_trace_bf16<T, IN, PM><<<grid, kTM, PM == 2 ? kDynSmem3 : kDynSmem, st>>>(P, tb, A, err);
@@ -995,7 +1193,7 @@ int launch_trace_bf16(const nglod_svo* svo, const nglod_decoder* dec, const Tabl
     static_assert(sizeof(BfSmem) <= kDynSmem, "shared layout");
     // the error word shares the workspace header with the ray queue
     int* err = A.queue + 1;
-    const int most = split ? 2 : kCtasPerSm;   // the three-plane tiles fit two CTAs per SM beside L1
+    const int most = kCtasPerSm;
     const int grid = svo->num_sms * (A.ctas_per_sm > 0 ? std::min(A.ctas_per_sm, most) : most);
     const DecPtrsB P = bptrs(dec, fp8 ? kE4M3Max / fp8_z_absmax : 1.0f);
     if (dec->in_dim == 35) {
