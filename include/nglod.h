@@ -113,9 +113,16 @@ typedef struct {
                               differences                                  */
     float fd_h;            /* FD step in scene units, in (0, 1) (FD only)     */
     int ctas_per_sm;       /* persistent trace CTAs per SM (0: the most that
-                              fit -- 4 for the tcgen05 decode, 2 for FP32);
-                              fewer leave room on each SM for concurrent
-                              kernels of other streams (0..4)               */
+                              fit -- 4 for the tensor-core decodes, 2 for
+                              FP32); fewer leave room on each SM for
+                              concurrent kernels of other streams (0..4)    */
+    const int32_t* ray_counts; /* NULL: the lists are CSR (ray_offsets has
+                              R + 1 entries).  Else the lists as
+                              svo_trace_rays_staged_async left them: ray i's
+                              entries are voxel_id[ray_offsets[i] ..
+                              ray_offsets[i] + ray_counts[i]) (device, R
+                              int32 each; sphere_trace and
+                              sphere_trace_blend only, not batches)         */
 } nglod_trace_params;
 
 #define NGLOD_NORMALS_ANALYTIC 0
@@ -303,6 +310,28 @@ int svo_trace_rays_async_width(const nglod_svo* svo, const float* o, const float
                                int32_t* ray_offsets, int32_t* voxel_id, float* t_range,
                                int64_t hit_capacity, int ctas_per_sm, void* stream);
 
+/* svo_trace_rays_staged_async -- svo_trace_rays_async without its placement
+ * pass: the lists stay where the persistent traversal staged them in the
+ * workspace (each ray's entries contiguous and front to back, the same
+ * entries as the CSR lists; the rays' lists in no particular order), so the
+ * traversal is one launch.  The paper's Compactify writes CSR; this form
+ * exists for the renderer, whose tracer reads a ray's list by its first
+ * entry and count (nglod_trace_params.ray_counts).
+ *   svo, o, d, R, target_lod, work, work_bytes, pair_capacity, ctas_per_sm
+ *                 as svo_trace_rays_async_width.
+ *   ray_first, ray_count, voxel_id  host pointers that receive device
+ *                 addresses inside work: [R] int32 index of each ray's first
+ *                 entry in voxel_id, [R] int32 its entry count, and the
+ *                 [pair_capacity] int32 staged voxel ids.  Valid until the
+ *                 workspace is reused.
+ * Overflow of pair_capacity is reported by svo_trace_rays_check (outputs
+ * then unspecified).  NGLOD_ERR_INVALID_ARG as svo_trace_rays_async_width.
+ * Does not synchronise. */
+int svo_trace_rays_staged_async(const nglod_svo* svo, const float* o, const float* d, int64_t R,
+                                int target_lod, void* work, size_t work_bytes, int64_t pair_capacity,
+                                int ctas_per_sm, const int32_t** ray_first, const int32_t** ray_count,
+                                const int32_t** voxel_id, void* stream);
+
 /* svo_trace_rays_check -- synchronises and reports the status of the last
  * traversal enqueued in this workspace (as svo_trace_rays would have): OK,
  * NGLOD_ERR_CAPACITY (h_stats = sizes needed) or NGLOD_ERR_TIMEOUT. */
@@ -357,7 +386,10 @@ size_t sphere_trace_workspace(int64_t R);
  * x = o + t d from that voxel and its ancestors, and counts one step; d < eps
  * is a hit, otherwise t += d; t > far_t or max_steps reached is a miss.
  *   o, d, R, lod        as for svo_trace_rays (same rays, same LOD).
- *   ray_offsets, voxel_id   the CSR lists of svo_trace_rays.
+ *   ray_offsets, voxel_id   the CSR lists of svo_trace_rays, or with
+ *                       params->ray_counts the staged lists of
+ *                       svo_trace_rays_staged_async (ray_offsets = its
+ *                       ray_first).
  *   t_range             not read (may be NULL): each entry's [t_enter,
  *                       t_exit] is recomputed from its voxel by the slab
  *                       test svo_trace_rays uses, which gives the same bits.

@@ -111,6 +111,7 @@ extern "C" int sphere_trace_blend(const nglod_svo* svo, const nglod_features* fe
     A.max_steps = params->max_steps;
     A.osc = params->osc_check;
     A.offs = ray_offsets;
+    A.cnt = params->ray_counts;
     A.vid = voxel_id;
     A.t_hit = t_hit;
     A.hit = hit;

@@ -1155,7 +1155,8 @@ namespace {
 // Also writes each ray's first list entry (t_enter, t_exit, voxel, packed
 // ijk; the interval by the traversal's slab test at depth D) to start[r], so
 // the tracer starts a ray with independent loads only.
-__global__ void k_group_keys(const int32_t* __restrict__ offs, long long R, uint8_t* __restrict__ key,
+__global__ void k_group_keys(const int32_t* __restrict__ offs, const int32_t* __restrict__ cnt, long long R,
+                             uint8_t* __restrict__ key,
                              int* __restrict__ hist, const float* __restrict__ o, const float* __restrict__ d,
                              const int32_t* __restrict__ vid, const Node* __restrict__ node_D, int D,
                              int4* __restrict__ start) {
@@ -1168,7 +1169,7 @@ __global__ void k_group_keys(const int32_t* __restrict__ offs, long long R, uint
     for (long long g = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); g < G; g += nw) {
         const long long r = g * 32 + lane;
         const int c0 = r < R ? offs[r] : 0;
-        const int len = r < R ? offs[r + 1] - c0 : 0;
+        const int len = r < R ? (cnt ? cnt[r] : offs[r + 1] - c0) : 0;
         if (len > 0) {
             const int v = vid[c0];
             const uint32_t ijk = node_D[v].ijk;
@@ -1319,7 +1320,7 @@ int enqueue_ray_order(TraceArgs& A, void* work, const Node* node_D, cudaStream_t
     const int sms = device_sms();
     const int gk = (int)std::max<long long>(1, std::min<long long>((G + 7) / 8, (long long)sms * 4));
     int4* start = reinterpret_cast<int4*>(w + trace_ws_start_offset(R));
-    k_group_keys<<<gk, 256, 0, st>>>(A.offs, R, key, hist, A.o, A.d, A.vid, node_D, A.D, start);
+    k_group_keys<<<gk, 256, 0, st>>>(A.offs, A.cnt, R, key, hist, A.o, A.d, A.vid, node_D, A.D, start);
     k_order_scan<<<1, kOrderBuckets, 0, st>>>(hist, cursor);
     const int gs = (int)std::max<long long>(1, std::min<long long>((G + 255) / 256, (long long)sms * 4));
     k_order_scatter<<<gs, 256, 0, st>>>(key, G, cursor, order);
@@ -1374,6 +1375,7 @@ extern "C" int sphere_trace(const nglod_svo* svo, const nglod_features* feats, c
     A.max_steps = params->max_steps;
     A.osc = params->osc_check;
     A.offs = ray_offsets;
+    A.cnt = params->ray_counts;
     A.vid = voxel_id;
     A.t_hit = t_hit;
     A.hit = hit;

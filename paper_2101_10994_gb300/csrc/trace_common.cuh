@@ -115,6 +115,10 @@ struct TraceArgs {
     // is recomputed from its voxel by the traversal's slab test (same bits)
     const int32_t* offs;
     const int32_t* vid;
+    // with cnt, the lists as the traversal staged them: ray r's entries are
+    // vid[offs[r] .. offs[r] + cnt[r]) (each ray's contiguous, front to
+    // back; rays in no particular order), and offs has R entries
+    const int32_t* cnt = nullptr;
     float* t_hit;
     uint8_t* hit;
     int32_t* steps;       // nullable
@@ -244,7 +248,7 @@ __device__ __forceinline__ void start_ray(RaySlot& S, int r, const TraceArgs& A,
     S.t = 0.0f;
     S.vox = -1;
     S.cur = A.offs[r];
-    S.end = A.offs[r + 1];
+    S.end = A.cnt ? S.cur + A.cnt[r] : A.offs[r + 1];
     int4 first = make_int4(0, 0, 0, 0);
     if (A.start) first = A.start[r];      // independent of the offsets: one round of loads
     if (S.cur >= S.end) {

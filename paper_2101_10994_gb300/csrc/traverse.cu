@@ -71,7 +71,9 @@ struct TileParams {
     long long R, ntiles, stage_cap;
     int D;
     int32_t* ray_cnt;                  // [R] entries per ray (k_place turns them into offsets)
-    int32_t* ray_src;                  // [R] staging slot of each ray's first entry (sub-range tiles)
+    int32_t* ray_src;                  // [R] staging slot of each ray's first entry (sub-range tiles;
+                                       // every tile's with first_all)
+    bool first_all;                    // staged lists wanted (no placement follows)
     int32_t* stage_vid;                // [stage_cap] staged entries
     float2* stage_tr;                  // ... and their t ranges (null: not wanted)
     TileInfo* tiles;                   // [ntiles]
@@ -478,7 +480,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_traverse(const TileParams p) {
         init_roots(S, 0, nr);
         __syncthreads();
         LevelRun lr;
-        if (run_from(S, p, 0, 0, kFCap, nr, kFCap, lr)) {
+        const bool whole = run_from(S, p, 0, 0, kFCap, nr, kFCap, lr);
+        if (whole) {
             commit_levels(S, p, 1, p.D);
             reserve_stage(S, p, lr.total);
             if (threadIdx.x == 0) p.tiles[t] = TileInfo{S.stage, (long long)lr.total};
@@ -491,6 +494,13 @@ __global__ void __launch_bounds__(kThreads, 4) k_traverse(const TileParams p) {
         }
         __syncthreads();                   // per-ray counts complete
         if ((int)threadIdx.x < nr) p.ray_cnt[ra + threadIdx.x] = S.ray_cnt[threadIdx.x];
+        if (whole && p.first_all) {
+            // the tile was staged in one piece, its rays in order
+            int sum;
+            const int pre = block_exclusive_sum((int)threadIdx.x < nr ? S.ray_cnt[threadIdx.x] : 0, S.warp_sums,
+                                                sum);
+            if ((int)threadIdx.x < nr) p.ray_src[ra + threadIdx.x] = (int32_t)(S.stage + pre);
+        }
         __syncthreads();   // shared state is reused by the next tile
     }
 }
@@ -712,9 +722,39 @@ namespace nglod {
 namespace {
 
 // Enqueues the whole traversal on the stream (no host synchronisation).
+// The workspace's regions (svo_trace_rays_workspace).
+struct TraversalWs {
+    Counters* ctr;
+    TileInfo* tiles;
+    int32_t* ray_cnt;
+    int32_t* ray_src;
+    int32_t* stage_vid;
+    float2* stage_tr;
+};
+
+TraversalWs traversal_ws(void* work, int64_t R, int64_t pair_capacity) {
+    TraversalWs w;
+    char* wp = (char*)work;
+    w.ctr = (Counters*)wp;
+    wp += align_up(sizeof(Counters));
+    w.tiles = (TileInfo*)wp;
+    wp += align_up(sizeof(TileInfo) * (size_t)(num_tiles(R) + 1));
+    w.ray_cnt = (int32_t*)wp;
+    wp += align_up(sizeof(int32_t) * (size_t)(R + 1));
+    w.ray_src = (int32_t*)wp;
+    wp += align_up(sizeof(int32_t) * (size_t)(R + 1));
+    w.stage_vid = (int32_t*)wp;
+    wp += align_up(sizeof(int32_t) * (size_t)pair_capacity);
+    w.stage_tr = (float2*)wp;
+    return w;
+}
+
+// staged: the lists stay in the staging list (svo_trace_rays_staged_async):
+// no placement, every ray's first staging slot recorded, no CSR outputs.
 int enqueue_traversal(const nglod_svo* svo, const float* o, const float* d, int64_t R, int target_lod, void* work,
                       size_t work_bytes, int64_t pair_capacity, int32_t* ray_offsets, int32_t* voxel_id,
-                      float* t_range, int64_t hit_capacity, cudaStream_t st, const char* who, int ctas_per_sm = 0) {
+                      float* t_range, int64_t hit_capacity, cudaStream_t st, const char* who, int ctas_per_sm = 0,
+                      bool staged = false) {
     const std::string w(who);
     if (!svo) return fail(NGLOD_ERR_INVALID_ARG, w + ": NULL octree");
     const int D = target_lod + kFirstFeatureDepth - 1;
@@ -724,7 +764,7 @@ int enqueue_traversal(const nglod_svo* svo, const float* o, const float* d, int6
     if (R < 0 || R >= (1ll << 31) - 1 || pair_capacity < 0 || pair_capacity >= (1ll << 31) - 1 ||
         hit_capacity < 0)
         return fail(NGLOD_ERR_INVALID_ARG, w + ": bad R or capacity");
-    if (!ray_offsets) return fail(NGLOD_ERR_INVALID_ARG, w + ": NULL ray_offsets");
+    if (!ray_offsets && !staged) return fail(NGLOD_ERR_INVALID_ARG, w + ": NULL ray_offsets");
     if (!work) return fail(NGLOD_ERR_INVALID_ARG, w + ": NULL workspace");
     if (work_bytes < svo_trace_rays_workspace(R, pair_capacity))
         return fail(NGLOD_ERR_CAPACITY, w + ": workspace smaller than svo_trace_rays_workspace()");
@@ -732,23 +772,19 @@ int enqueue_traversal(const nglod_svo* svo, const float* o, const float* d, int6
     Counters* ctr = (Counters*)work;
     if (R == 0) {
         NGLOD_CUDA(cudaMemsetAsync(ctr, 0, sizeof(Counters), st));
-        NGLOD_CUDA(cudaMemsetAsync(ray_offsets, 0, sizeof(int32_t), st));
+        if (!staged) NGLOD_CUDA(cudaMemsetAsync(ray_offsets, 0, sizeof(int32_t), st));
         return NGLOD_OK;
     }
     if (!o || !d) return fail(NGLOD_ERR_INVALID_ARG, w + ": NULL rays");
-    if (hit_capacity > 0 && !voxel_id) return fail(NGLOD_ERR_INVALID_ARG, w + ": NULL voxel_id");
+    if (!staged && hit_capacity > 0 && !voxel_id) return fail(NGLOD_ERR_INVALID_ARG, w + ": NULL voxel_id");
 
     const long long ntiles = num_tiles(R);
-    char* wp = (char*)work + align_up(sizeof(Counters));
-    TileInfo* tiles = (TileInfo*)wp;
-    wp += align_up(sizeof(TileInfo) * (size_t)(ntiles + 1));
-    int32_t* ray_cnt = (int32_t*)wp;
-    wp += align_up(sizeof(int32_t) * (size_t)(R + 1));
-    int32_t* ray_src = (int32_t*)wp;
-    wp += align_up(sizeof(int32_t) * (size_t)(R + 1));
-    int32_t* stage_vid = (int32_t*)wp;
-    wp += align_up(sizeof(int32_t) * (size_t)pair_capacity);
-    float2* stage_tr = (float2*)wp;
+    const TraversalWs ws = traversal_ws(work, R, pair_capacity);
+    TileInfo* tiles = ws.tiles;
+    int32_t* ray_cnt = ws.ray_cnt;
+    int32_t* ray_src = ws.ray_src;
+    int32_t* stage_vid = ws.stage_vid;
+    float2* stage_tr = ws.stage_tr;
     NGLOD_CUDA(cudaMemsetAsync(ctr, 0, sizeof(Counters), st));
     TileParams p;
     for (int dp = 0; dp <= kMaxDepth; ++dp) p.nt.node[dp] = dp < svo->num_depths ? svo->node[dp] : nullptr;
@@ -760,17 +796,22 @@ int enqueue_traversal(const nglod_svo* svo, const float* o, const float* d, int6
     p.D = D;
     p.ray_cnt = ray_cnt;
     p.ray_src = ray_src;
+    p.first_all = staged;
     p.stage_vid = stage_vid;
-    p.stage_tr = t_range ? stage_tr : nullptr;
+    p.stage_tr = t_range && !staged ? stage_tr : nullptr;
     p.tiles = tiles;
     p.ctr = ctr;
     const int sms = svo->num_sms;
     const int occ = traverse_ctas_per_sm();
     const long long grid = std::min<long long>(ntiles, (long long)sms * (ctas_per_sm > 0 ? std::min(ctas_per_sm, occ) : occ));
-    if (t_range)
+    if (p.stage_tr)
         k_traverse<true><<<(unsigned)grid, kThreads, sizeof(TileSmem), st>>>(p);
     else
         k_traverse<false><<<(unsigned)grid, kThreads, sizeof(TileSmem), st>>>(p);
+    if (staged) {
+        NGLOD_CUDA(cudaGetLastError());
+        return NGLOD_OK;
+    }
     k_tile_scan<<<1, kScanThreads, 0, st>>>(tiles, ntiles, ctr, hit_capacity, D);
     k_place<<<(unsigned)std::min<long long>(ntiles, (long long)sms * 8), kPlaceThreads, 0, st>>>(
         tiles, p, ray_cnt, ray_offsets, voxel_id, (float2*)t_range);
@@ -828,6 +869,25 @@ extern "C" int svo_trace_rays_async_width(const nglod_svo* svo, const float* o, 
         return fail(NGLOD_ERR_INVALID_ARG, "svo_trace_rays_async_width: ctas_per_sm must lie in 0..4");
     return enqueue_traversal(svo, o, d, R, target_lod, work, work_bytes, pair_capacity, ray_offsets, voxel_id,
                              t_range, hit_capacity, (cudaStream_t)stream, "svo_trace_rays_async_width", ctas_per_sm);
+}
+
+extern "C" int svo_trace_rays_staged_async(const nglod_svo* svo, const float* o, const float* d, int64_t R,
+                                           int target_lod, void* work, size_t work_bytes, int64_t pair_capacity,
+                                           int ctas_per_sm, const int32_t** ray_first, const int32_t** ray_count,
+                                           const int32_t** voxel_id, void* stream) {
+    if (ctas_per_sm < 0 || ctas_per_sm > 4)
+        return fail(NGLOD_ERR_INVALID_ARG, "svo_trace_rays_staged_async: ctas_per_sm must lie in 0..4");
+    if (!ray_first || !ray_count || !voxel_id)
+        return fail(NGLOD_ERR_INVALID_ARG, "svo_trace_rays_staged_async: NULL output pointer");
+    const int rc = enqueue_traversal(svo, o, d, R, target_lod, work, work_bytes, pair_capacity, nullptr, nullptr,
+                                     nullptr, 0, (cudaStream_t)stream, "svo_trace_rays_staged_async", ctas_per_sm,
+                                     true);
+    if (rc) return rc;
+    const TraversalWs ws = traversal_ws(work, R, pair_capacity);
+    *ray_first = ws.ray_src;
+    *ray_count = ws.ray_cnt;
+    *voxel_id = ws.stage_vid;
+    return NGLOD_OK;
 }
 
 extern "C" int svo_trace_rays_check(const void* work, int target_lod, int64_t* h_stats, void* stream) {

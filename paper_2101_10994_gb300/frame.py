@@ -1,8 +1,9 @@
 """One image per frame with its stages overlapped across CUDA streams.
 
 The rays of the image are split into a few consecutive chunks; each chunk's
-traversal (svo_trace_rays_async), sphere trace and normals are enqueued on
-its own stream, so the tail of one chunk's trace -- the few long rays that
+traversal (svo_trace_rays_staged_async: one launch, the lists left where the
+traversal staged them and read by each ray's first entry and count), sphere
+trace and normals are enqueued on its own stream, so the tail of one chunk's trace -- the few long rays that
 keep a persistent launch busy while most SMs idle -- overlaps the next
 chunk's traversal and trace, and one chunk's normals overlap another's
 trace.  No kernel waits for another; the chunks only share the GPU.  The
@@ -68,11 +69,12 @@ class FrameRenderer:
             cap = int(lists.voxel_id.numel() * headroom) + 4096
             c = dict(rs=rs, n=m, cap=cap, stream=torch.cuda.Stream(device=dev),
                      twork=torch.empty(L.svo_trace_rays_workspace(m, cap), dtype=torch.uint8, device=dev),
-                     offs=torch.empty(m + 1, dtype=torch.int32, device=dev),
-                     vid=torch.empty(cap, dtype=torch.int32, device=dev),
-                     swork=torch.empty(L.sphere_trace_workspace(m), dtype=torch.uint8, device=dev))
-            # no t ranges in the lists: the tracers recompute each entry's interval
-            c["lists"] = ng.RayLists(c["offs"], c["vid"], None, 0, self.lod, c["twork"])
+                     swork=torch.empty(L.sphere_trace_workspace(m), dtype=torch.uint8, device=dev),
+                     ptrs=[C.c_void_p() for _ in range(3)])
+            # the staged lists (views into twork, the same every frame); no t
+            # ranges: the tracers recompute each entry's interval
+            c["lists"] = ng.svo_trace_rays_staged(svo, self.o[rs:re_], self.d[rs:re_], self.lod, c["twork"], cap,
+                                                  self.trav_ctas_per_sm)
             c["outs"] = dict(t=self.out["t"][rs:re_], hit=self.out["hit"][rs:re_], steps=self.out["steps"][rs:re_],
                              normal=self.out["normal"][rs:re_] if normals else None, work=c["swork"])
             self.chunks.append(c)
@@ -82,10 +84,11 @@ class FrameRenderer:
         st = c["stream"]
         rs, re_ = c["rs"], c["rs"] + c["n"]
         oo, dd = self.o[rs:re_], self.d[rs:re_]
-        ng._check(L.svo_trace_rays_async_width(self.svo.h, oo.data_ptr(), dd.data_ptr(), c["n"], self.lod,
-                                               c["twork"].data_ptr(), c["twork"].numel(), c["cap"],
-                                               c["offs"].data_ptr(), c["vid"].data_ptr(), None, c["cap"],
-                                               self.trav_ctas_per_sm, C.c_void_p(st.cuda_stream)))
+        p = c["ptrs"]
+        ng._check(L.svo_trace_rays_staged_async(self.svo.h, oo.data_ptr(), dd.data_ptr(), c["n"], self.lod,
+                                                c["twork"].data_ptr(), c["twork"].numel(), c["cap"],
+                                                self.trav_ctas_per_sm, C.byref(p[0]), C.byref(p[1]), C.byref(p[2]),
+                                                C.c_void_p(st.cuda_stream)))
         if self.blend:
             ng.sphere_trace_blend(self.svo, self.feats, self.dec, self.dec_hi, oo, dd, c["lists"], self.lod_tilde,
                                   eps=self.eps, far=self.far, max_steps=self.max_steps, decode=self.decode,

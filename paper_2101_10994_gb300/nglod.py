@@ -33,6 +33,7 @@ EXPORTS = ["nglod_last_error", "svo_build", "svo_info", "svo_device_arrays", "sv
            "sphere_trace_batch_free", "sdf_query_blend", "sphere_trace_blend", "nglod_lod_select",
            "trace_normals_fd", "sdf_backward_bf16", "sdf_l2_backward_bf16", "nglod_sort_points_workspace",
            "nglod_sort_points", "nglod_sum_features", "nglod_set_wait_polls", "svo_trace_rays_async_width",
+           "svo_trace_rays_staged_async",
            # measurement probes (include/nglod_probe.h)
            "nglod_probe_l2_read", "nglod_probe_l1_read", "nglod_probe_ffma", "nglod_device_sms"]
 
@@ -63,7 +64,7 @@ class _TraceJob(C.Structure):
 class _TraceParams(C.Structure):
     _fields_ = [("eps", C.c_float), ("far_t", C.c_float), ("max_steps", C.c_int), ("osc_check", C.c_int),
                 ("decode_dtype", C.c_int), ("want_normals", C.c_int), ("normal_mode", C.c_int),
-                ("fd_h", C.c_float), ("ctas_per_sm", C.c_int)]
+                ("fd_h", C.c_float), ("ctas_per_sm", C.c_int), ("ray_counts", C.c_void_p)]
 
 NORMALS = {"analytic": 0, "fd": 1}
 
@@ -110,6 +111,7 @@ def lib():
         L.svo_trace_rays_async.argtypes = [P, P, P, i64, i32, P, sz, i64, P, P, P, i64, P]
         L.svo_trace_rays_check.argtypes = [P, i32, P, P]
         L.svo_trace_rays_async_width.argtypes = [P, P, P, i64, i32, P, sz, i64, P, P, P, i64, i32, P]
+        L.svo_trace_rays_staged_async.argtypes = [P, P, P, i64, i32, P, sz, i64, i32, P, P, P, P]
         L.sphere_trace_batch_create.argtypes = [P, i32, P, i32, P, P]
         L.sphere_trace_batch_run.argtypes = [P, P]
         L.sphere_trace_batch_status.argtypes = [P, P]
@@ -375,6 +377,9 @@ class RayLists:
     max_pairs: int
     lod: int
     work: object = None      # the workspace the lists were built in
+    # staged lists (svo_trace_rays_staged): ray_offsets is then each ray's
+    # first entry [R] and ray_counts its entry count [R]
+    ray_counts: object = None
 
     def level_sizes(self, stream=None):
         """Pairs kept by Decide at each depth 0..target (entry 0 = R)."""
@@ -423,6 +428,30 @@ def svo_trace_rays(svo: SVO, o, d, lod: int, stream=None, pair_capacity: int | N
     raise NglodError(ERR_CAPACITY, "svo_trace_rays: capacity growth did not converge")
 
 
+def svo_trace_rays_staged(svo: SVO, o, d, lod: int, work, pair_capacity: int, ctas_per_sm: int = 0,
+                          stream=None) -> RayLists:
+    """Enqueues the traversal without its placement pass (no host
+    synchronisation): each ray's front-to-back entries stay where the
+    traversal staged them in ``work`` (a uint8 tensor of at least
+    svo_trace_rays_workspace(R, pair_capacity) bytes, 256-B aligned).
+    Returns views into ``work``: ray_offsets = each ray's first entry,
+    ray_counts = its count, voxel_id = the staging list.  Overflow is
+    reported by svo_trace_rays_check on ``work``."""
+    _require_cuda(o, d)
+    import torch
+    R = int(o.shape[0])
+    first, cnt, vid = C.c_void_p(), C.c_void_p(), C.c_void_p()
+    _check(lib().svo_trace_rays_staged_async(svo.h, o.data_ptr(), d.data_ptr(), R, lod, work.data_ptr(),
+                                             work.numel(), int(pair_capacity), int(ctas_per_sm), C.byref(first),
+                                             C.byref(cnt), C.byref(vid), C.c_void_p(_stream(stream))))
+    base = work.data_ptr()
+
+    def view(ptr, n):
+        off = int(ptr.value or base) - base
+        return work[off:off + 4 * n].view(torch.int32)
+    return RayLists(view(first, R), view(vid, int(pair_capacity)), None, -1, lod, work, view(cnt, R))
+
+
 def sdf_query(svo: SVO, feats: Features, dec: DecoderDev, x, lod: int, decode: str = "f32",
               grad: bool = False, deepest: bool = False, stream=None):
     import torch
@@ -464,7 +493,7 @@ def sphere_trace(svo: SVO, feats: Features, dec: DecoderDev, o, d, lists: RayLis
                    normal=torch.empty((R, 3), dtype=torch.float32, device=dev) if normals else None,
                    work=torch.empty(max(lib().sphere_trace_workspace(R), 1), dtype=torch.uint8, device=dev))
     p = _TraceParams(eps, far, max_steps, int(osc), DECODES[decode], int(normals),
-                     NORMALS[normal_mode], fd_h, int(ctas_per_sm))
+                     NORMALS[normal_mode], fd_h, int(ctas_per_sm), _ptr(lists.ray_counts))
     fc, dc = feats.c(), dec.c()
     _check(lib().sphere_trace(svo.h, C.byref(fc), C.byref(dc), o.data_ptr(), d.data_ptr(), R, lists.lod,
                               C.byref(p), lists.ray_offsets.data_ptr(), lists.voxel_id.data_ptr(),
@@ -544,7 +573,7 @@ def sphere_trace_blend(svo: SVO, feats: Features, dec_lo: DecoderDev, dec_hi: De
                    normal=torch.empty((R, 3), dtype=torch.float32, device=dev) if normals else None,
                    work=torch.empty(max(lib().sphere_trace_workspace(R), 1), dtype=torch.uint8, device=dev))
     p = _TraceParams(eps, far, max_steps, int(osc), DECODES[decode], int(normals),
-                     NORMALS[normal_mode], fd_h, int(ctas_per_sm))
+                     NORMALS[normal_mode], fd_h, int(ctas_per_sm), _ptr(lists.ray_counts))
     fc, lo = feats.c(), dec_lo.c()
     hi = (dec_hi or dec_lo).c()
     _check(lib().sphere_trace_blend(svo.h, C.byref(fc), C.byref(lo), C.byref(hi), o.data_ptr(), d.data_ptr(), R,

@@ -10,6 +10,18 @@ from paper_2101_10994_gb300 import scenes as S
 pytestmark = pytest.mark.gpu
 
 
+def assert_staged_equal(staged, L):
+    """Ray by ray, the staged lists (first entry, count, staging list) equal
+    the CSR lists L of svo_trace_rays, entry for entry."""
+    offs = L.ray_offsets.long()
+    cnt = staged.ray_counts.long()
+    assert torch.equal(cnt, offs[1:] - offs[:-1])
+    H = int(offs[-1])
+    start = torch.repeat_interleave(staged.ray_offsets.long(), cnt)
+    within = torch.arange(H, device=cnt.device) - torch.repeat_interleave(offs[:-1], cnt)
+    assert torch.equal(staged.voxel_id[start + within], L.voxel_id)
+
+
 @pytest.mark.parametrize("decode,chunks", [("bf16", 2), ("f32", 3), ("fp8", 2)])
 def test_chunked_frame_equals_single_pass(ng, decode, chunks):
     from paper_2101_10994_gb300.frame import FrameRenderer
@@ -46,11 +58,10 @@ def test_chunked_frame_equals_single_pass(ng, decode, chunks):
     fn.check()
     for k in ("t", "hit", "steps", "normal"):
         assert torch.equal(fn.out[k], ref[k]), k
-    for c in fn.chunks:                    # and the lists are those of svo_trace_rays
+    for c in fn.chunks:                    # and the staged lists hold those of svo_trace_rays
         n = c["n"]
         L = ng.svo_trace_rays(svo, to[c["rs"]:c["rs"] + n], td[c["rs"]:c["rs"] + n], 5)
-        H = L.voxel_id.numel()
-        assert torch.equal(c["offs"], L.ray_offsets) and torch.equal(c["vid"][:H], L.voxel_id)
+        assert_staged_equal(c["lists"], L)
     # rays and results through pinned host buffers, copied chunk by chunk
     h_in = (torch.from_numpy(o).pin_memory(), torch.from_numpy(d).pin_memory())
     h_out = {"t": torch.empty(len(o)).pin_memory(), "hit": torch.empty(len(o), dtype=torch.uint8).pin_memory(),

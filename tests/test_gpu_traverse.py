@@ -1,5 +1,7 @@
 """svo_trace_rays (Algorithm 1 on the GPU) vs the oracle's brute-force lists:
 bit-exact voxel ids, order and FP32 (t_enter, t_exit) bits."""
+import ctypes as C
+
 import numpy as np
 import pytest
 import torch
@@ -166,6 +168,57 @@ def test_dense_grid_every_overflow_path(ng, oracle_mod):
     np.testing.assert_array_equal(L2.ray_offsets.cpu().numpy(), g[0])
     np.testing.assert_array_equal(L2.voxel_id.cpu().numpy(), g[1])
     assert L2.level_sizes() == sizes
+    # staged (no placement pass): each ray's entries where the traversal
+    # staged them -- the same entries on every path, the same level sizes
+    assert_staged_lists(ng, svo, o, d, 4, L2)
+    svo.free()
+
+
+def assert_staged_lists(ng, svo, o, d, lod, L):
+    """svo_trace_rays_staged: ray by ray equal to the CSR lists L, with the
+    same level sizes and status, and a trace over them bit-identical to one
+    over L."""
+    to, td = torch.from_numpy(o).cuda(), torch.from_numpy(d).cuda()
+    cap = int(L.voxel_id.numel()) + 1024
+    work = torch.empty(ng.lib().svo_trace_rays_workspace(len(o), cap), dtype=torch.uint8, device="cuda")
+    St = ng.svo_trace_rays_staged(svo, to, td, lod, work, cap)
+    stats = (C.c_int64 * 2)()
+    ng._check(ng.lib().svo_trace_rays_check(work.data_ptr(), lod, stats, None))
+    assert stats[0] == L.voxel_id.numel()
+    assert St.level_sizes() == L.level_sizes()
+    offs = L.ray_offsets.long()
+    cnt = St.ray_counts.long()
+    assert torch.equal(cnt, offs[1:] - offs[:-1])
+    H = int(offs[-1])
+    start = torch.repeat_interleave(St.ray_offsets.long(), cnt)
+    within = torch.arange(H, device="cuda") - torch.repeat_interleave(offs[:-1], cnt)
+    assert torch.equal(St.voxel_id[start + within], L.voxel_id)
+    return St
+
+
+def test_staged_lists_and_trace(ng, oracle_mod):
+    # the 1080p-style camera on the CSG scene (tiles staged whole) and a
+    # trace over the staged lists: every output bit-identical to CSR lists
+    sc, oc = S.csg_workload(16, seed=2, max_lod=4)
+    svo = ng.svo_build(oc.keys)
+    o, d, _ = S.camera_rays(320, 200, tile=8)
+    L = ng.svo_trace_rays(svo, torch.from_numpy(o).cuda(), torch.from_numpy(d).cuda(), 4, t_range=False)
+    St = assert_staged_lists(ng, svo, o, d, 4, L)
+    F = ng.Features(S.readout_features(oc, sc))
+    D = ng.DecoderDev.from_decoder(S.readout_decoder(4))
+    to, td = torch.from_numpy(o).cuda(), torch.from_numpy(d).cuda()
+    for decode in ("f32", "bf16"):
+        a = ng.sphere_trace(svo, F, D, to, td, L, decode=decode, normals=True)
+        b = ng.sphere_trace(svo, F, D, to, td, St, decode=decode, normals=True)
+        assert int(a["hit"].sum()) > 1000
+        for k in ("t", "hit", "steps", "normal"):
+            assert torch.equal(a[k], b[k]), (decode, k)
+    # a capacity below the entries is reported, not overrun
+    small = 64
+    work = torch.empty(ng.lib().svo_trace_rays_workspace(len(o), small), dtype=torch.uint8, device="cuda")
+    ng.svo_trace_rays_staged(svo, to, td, 4, work, small)
+    stats = (C.c_int64 * 2)()
+    assert ng.lib().svo_trace_rays_check(work.data_ptr(), 4, stats, None) == ng.ERR_CAPACITY
     svo.free()
 
 
