@@ -10,9 +10,8 @@
 // accumulation), the A operand built from the z the lane gathered itself, so
 // no warp waits for another.
 //
-// tcgen05 (the FP8 tracer, sdf_query, FP8 batches and level blending): each
-// CTA owns 128 query slots (thread i <-> A-tile row i <-> tensor-memory lane
-// i):
+// tcgen05 (sdf_query, the FP8 tracer and batches, level blending): each CTA
+// owns 128 query slots (thread i <-> A-tile row i <-> tensor-memory lane i):
 //   1. gather: 4-lane groups interpolate each slot's z (FP32, 8 channels a
 //      lane) and write it straight into the A tile, laid out as the MMA's
 //      canonical K-major operand (8-row x 16-byte core matrices);
@@ -897,7 +896,8 @@ __global__ void __launch_bounds__(kTM, kCtasPerSm) k_trace_batch_warp(const Trac
     const int g4 = lane >> 2, l4 = lane & 3, gb4 = g4 << 2;
     const unsigned gm4 = 0xfu << gb4;
     for (int gi = 0; gi < ngroups; ++gi) {
-        const JobGroup G = groups[gi];
+        // read in place (a register copy of the group spilled)
+        const JobGroup& G = groups[gi];
         const DecPtrsB dp{G.W1, G.b1, G.W2, G.b2, G.z_scale, 0};
         __syncthreads();                      // every warp is done with the previous group's decoder
         stage_warp_decoder<IN>(S.dec, dp);
