@@ -149,6 +149,35 @@ def test_plain_sphere_f32(ng, oracle_mod, decoder):
     assert c["steps_eq"] >= 0.999
 
 
+@pytest.mark.parametrize("decode,fdt", [("bf16", "f32"), ("bf16", "f16"), ("f32tc", "f32")])
+def test_plain_sphere_in35_tensor_decodes(ng, oracle_mod, decode, fdt):
+    # the warp-level tracers with the x-concatenated decoder (in_dim 35: the
+    # x term added in FP32 to each unit's accumulator) against the oracle.
+    # FP32-accurate: a random decoder.  BF16: the read-out decoder (a
+    # distance-like field: on a random decoder, which is none, BF16 rounding
+    # sends sphere-tracing trajectories elsewhere) with two more units that
+    # read x, adding 0.05 w.x to the field, so the x term reaches the output
+    sc, oc = S.plain_sphere(3)
+    ora = oracle_mod.OracleSVO(oc.keys)
+    if decode == "bf16":
+        feats, dec = S.readout_features(oc, sc), S.readout_decoder(3, in_dim=35)
+        w = np.array([0.3, -0.2, 0.1], np.float32)
+        for u, sgn in ((2, 1.0), (3, -1.0)):
+            dec.W1[u, :] = 0.0
+            dec.W1[u, 0:3] = sgn * w
+            dec.b1[u] = 0.0
+            dec.W2[u] = sgn * 0.05
+    else:
+        feats, dec = S.init_features(oc, sigma=0.1), S.init_decoder(3, 35)
+        dec.b1 = np.random.default_rng(0).normal(0, 0.05, 128).astype(np.float32)
+    if fdt == "f16":
+        feats = [f.astype(np.float16) for f in feats]
+    o, d, _ = S.camera_rays(128, 128)
+    gs, ref = trace_both(ng, ora, oc, feats, fdt, dec, 3, o, d, 1e-3, 32, decode)
+    c = compare(ora, feats, dec, 3, o, d, gs, ref, 1e-3, decode=decode, oc=oc)
+    assert_parity(c, max_mismatch=2, min_both=1500)
+
+
 @pytest.mark.parametrize("decode,chunks,ctas", [("f32", 0, 0), ("f32tc", 0, 0), ("bf16", 4, 2), ("bf16", 0, 0)])
 def test_csg64_lod5_1080p_sampled(ng, oracle_mod, decode, chunks, ctas):
     # the benchmark's frame: CSG-64 seed 0, LOD 5, 1920x1080 tile-ordered
