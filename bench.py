@@ -904,17 +904,19 @@ def main():
             "ceilings": ceilings,
             "clocks": clocks,
             "e2e": e2e,
-            # per frame: traversal (tiles, tile scan, placement) + ray-group order (keys, bucket
-            # scan, scatter) + trace + normals, once in the sequential frame and once per chunk in
-            # the renderer's frame; the blended frame adds a second gradient pass and the
-            # normalisation; the FP16-feature frame runs the renderer's frame once more; each
-            # standalone sdf_query is one launch
-            "gpu_launches": args.steps * (sum(8 * (1 + res[m]["chunks"]) for m in modes)
-                                          + 10 * res.get("bf16_blend", {}).get("chunks", 0)
-                                          + 8 * res.get("bf16_f16features", {}).get("chunks", 0)
-                                          + sum(8 * (1 + res[k]["chunks"]) for k in res if k.endswith("_summed"))
+            # the library's kernels per timed frame: the sequential frame runs the CSR traversal
+            # (tiles, tile scan, placement: 3), the ray-group order (keys, bucket scan, scatter: 3),
+            # the tracer (1), the hit list in ray order (counts, scan, placement: 3) and the normals
+            # (masked-sum operand, gradient: 2) = 12; each chunk of the renderer's frame the same
+            # with the staged traversal (1) = 10; a blended chunk two operand builds and gradient
+            # passes and the normalisation (13); the FP16-feature frame the renderer's frame once
+            # more; each standalone sdf_query one launch; each summed table's timed build one
+            "gpu_launches": args.steps * (sum(12 + 10 * res[m]["chunks"] for m in modes)
+                                          + 13 * res.get("bf16_blend", {}).get("chunks", 0)
+                                          + 10 * res.get("bf16_f16features", {}).get("chunks", 0)
+                                          + sum(12 + 10 * res[k]["chunks"] for k in res if k.endswith("_summed"))
                                           + sum(k.startswith("sdf_query_") for k in res))
-                            + sum(k.endswith("_summed") for k in res),      # one table build each
+                            + sum(k.endswith("_summed") for k in res),
         }
         if "bf16" in res and "f32" in res:
             line["bf16_speedup"] = res["f32"]["ms_per_step"] / res["bf16"]["ms_per_step"]
