@@ -339,6 +339,30 @@ def run_ours(args, rank, world, local_rank):
         if clock_info is None or mode == "bf16":
             clock_info = sampler.summary()
 
+    # ---- the traversal as the frame renderer runs it: staged lists (one launch, no tile scan or
+    # placement), whole frame, CUDA events; decode-independent, so measured once ----
+    if modes:
+        Lc = ng.svo_trace_rays(svo, o, d, W["lod"], t_range=False)
+        cap_st = int(Lc.voxel_id.numel() * 1.25) + 4096
+        del Lc
+        twork = torch.empty(ng.lib().svo_trace_rays_workspace(R, cap_st), dtype=torch.uint8, device=dev)
+        tst = []
+        for k in range(args.warmup + args.steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            ng.svo_trace_rays_staged(svo, o, d, W["lod"], twork, cap_st)
+            e1.record()
+            torch.cuda.synchronize()
+            if k >= args.warmup:
+                tst.append(e0.elapsed_time(e1))
+        ng._check(ng.lib().svo_trace_rays_check(twork.data_ptr(), W["lod"], None, None))
+        results["traversal_staged"] = dict(
+            ms_per_frame=max_over_ranks(sum(tst), dev) / args.steps, launches_per_frame=1,
+            note="svo_trace_rays_staged_async: the frame renderer's traversal (each ray's entries left "
+                 "where the traversal staged them)")
+        del twork
+
     # ---- continuous LOD (Eq. 3): the same frame at L~ = lod - 0.5, BF16, frame renderer ----
     if "bf16" in modes and W["lod"] >= 2 and not summed:
         lt = W["lod"] - 0.5
@@ -564,9 +588,10 @@ def cpu_model():
     return platform.processor() or platform.machine()
 
 
-def traversal_roofline(W, res, mode, peaks):
+def traversal_roofline(W, res, mode, peaks, staged=None):
     """The traversal (k_traverse + tile scan + placement, 3 launches) against
-    HBM; it is issue-bound on the slab tests, so this fraction is low."""
+    HBM; it is issue-bound on the slab tests, so this fraction is low.
+    staged: the renderer's one-launch form (staged lists), timed beside it."""
     hbm = peaks.get("hbm_gbs", 6800.0)
     nbytes = traversal_bytes(W, res["level_sizes"])
     sec = res["ms_traverse"] * 1e-3
@@ -579,6 +604,7 @@ def traversal_roofline(W, res, mode, peaks):
             "frac": achieved / hbm, "traffic": traffic,
             "dram_frac": (traffic / sec / 1e9 / hbm) if traffic else None,
             "bytes_per_frame": nbytes, "launches_per_frame": 3,
+            "ms_staged_lists": staged["ms_per_frame"] if staged else None,
             "lower_bound_bytes": lower, "lower_bound_frac": lower / sec / 1e9 / hbm,
             "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in peaks else "fallback",
             "timing": "CUDA events around svo_trace_rays (3 launches + the H read-back)",
@@ -898,7 +924,7 @@ def main():
             "queries_per_s": r["queries_per_s"],
             "modes": res,
             "roofline": trace_roofline(W, r, head, peaks, 1 if args.features == "summed" else None, ceilings),
-            "traversal_roofline": traversal_roofline(W, r, head, peaks),
+            "traversal_roofline": traversal_roofline(W, r, head, peaks, res.get("traversal_staged")),
             "fp32_roofline": (trace_roofline(W, res["f32"], "f32", peaks, 1 if args.features == "summed" else None,
                                              ceilings) if "f32" in res else None),
             "ceilings": ceilings,
@@ -910,12 +936,14 @@ def main():
             # (masked-sum operand, gradient: 2) = 12; each chunk of the renderer's frame the same
             # with the staged traversal (1) = 10; a blended chunk two operand builds and gradient
             # passes and the normalisation (13); the FP16-feature frame the renderer's frame once
-            # more; each standalone sdf_query one launch; each summed table's timed build one
+            # more; each standalone sdf_query and the staged traversal one launch; each summed
+            # table's timed build one
             "gpu_launches": args.steps * (sum(12 + 10 * res[m]["chunks"] for m in modes)
                                           + 13 * res.get("bf16_blend", {}).get("chunks", 0)
                                           + 10 * res.get("bf16_f16features", {}).get("chunks", 0)
                                           + sum(12 + 10 * res[k]["chunks"] for k in res if k.endswith("_summed"))
-                                          + sum(k.startswith("sdf_query_") for k in res))
+                                          + sum(k.startswith("sdf_query_") for k in res)
+                                          + ("traversal_staged" in res))
                             + sum(k.endswith("_summed") for k in res),
         }
         if "bf16" in res and "f32" in res:
