@@ -81,3 +81,22 @@ def test_binding_structs_match_the_header(tmp_path):
         assert got[(cname, "size")] == ctypes.sizeof(cls), cname
         for fname, _ in cls._fields_:
             assert got[(cname, fname)] == getattr(cls, fname).offset, (cname, fname)
+
+
+def test_staged_traversal_rejects_bad_arguments_on_the_host(libpath):
+    """svo_trace_rays_staged_async checks its arguments before any device
+    work: a width outside 0..4, a NULL output pointer or a NULL octree each
+    return NGLOD_ERR_INVALID_ARG and name the call (no GPU touched)."""
+    lib = ctypes.CDLL(libpath)
+    f = lib.svo_trace_rays_staged_async
+    P, i32, i64, sz = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t
+    f.argtypes = [P, P, P, i64, i32, P, sz, i64, i32, P, P, P, P]
+    lib.nglod_last_error.restype = ctypes.c_char_p
+    outs = [ctypes.c_void_p() for _ in range(3)]
+    refs = [ctypes.byref(x) for x in outs]
+    assert f(None, None, None, 16, 3, None, 0, 64, 5, *refs, None) == nglod.ERR_INVALID_ARG
+    assert b"ctas_per_sm" in lib.nglod_last_error()
+    assert f(None, None, None, 16, 3, None, 0, 64, 0, refs[0], None, refs[2], None) == nglod.ERR_INVALID_ARG
+    assert b"NULL output" in lib.nglod_last_error()
+    assert f(None, None, None, 16, 3, None, 0, 64, 0, *refs, None) == nglod.ERR_INVALID_ARG
+    assert b"svo_trace_rays_staged_async" in lib.nglod_last_error()
