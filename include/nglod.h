@@ -101,8 +101,10 @@ typedef struct {
     int osc_check;         /* 1: also stop when |d_k - d_(k-1)| < 6 eps; the
                               ray is then a hit iff |d_k| < 6 eps             */
     int decode_dtype;      /* NGLOD_F32 (CUDA cores), NGLOD_BF16,
-                              NGLOD_FP8E4M3 or NGLOD_F32_SPLIT (tcgen05; see
-                              sdf_query)                                     */
+                              NGLOD_FP8E4M3 or NGLOD_F32_SPLIT (tensor cores,
+                              numerics as sdf_query; the tracers decode BF16
+                              and F32_SPLIT per warp with mma.sync, FP8 and
+                              blending on tcgen05)                          */
     int want_normals;      /* 1: write normals of hit rays                    */
     int normal_mode;       /* NGLOD_NORMALS_ANALYTIC (0): normalised analytic
                               gradient of the decoded SDF (FP32);
@@ -163,11 +165,13 @@ int nglod_sum_features(const nglod_svo* svo, const nglod_features* feats, int lo
 /* Text of the calling thread's last error ("" if none). */
 const char* nglod_last_error(void);
 
-/* nglod_set_wait_polls -- the poll budget of the bounded wait each
- * tensor-core kernel (the BF16 / FP8 / FP32-split decodes of sdf_query,
- * sphere_trace, sphere_trace_blend, sdf_query_blend and batches, and the
+/* nglod_set_wait_polls -- the poll budget of the bounded wait each tcgen05
+ * kernel (the BF16 / FP8 / FP32-split decodes of sdf_query, the FP8 decode
+ * of sphere_trace and batches, sphere_trace_blend, sdf_query_blend, and the
  * tensor-core adjoint) takes on the completion of every tile's MMA.  The
- * paper has no counterpart: this is a testing hook for the expiry path.
+ * BF16 and FP32-split decodes of sphere_trace and the BF16 batches run
+ * warp-level MMAs, which complete in the issuing warp: no wait, no budget.
+ * The paper has no counterpart: this is a testing hook for the expiry path.
  * polls >= 0 sets the budget of every launch that follows, process-wide
  * (0: every such wait expires at once, so the call reports
  * NGLOD_ERR_TIMEOUT without any GPU fault or hang); polls < 0 restores the
@@ -510,9 +514,9 @@ int nglod_adam_step(float* param, float* grad, float* m, float* v, int64_t n, fl
                     float beta1, float beta2, float eps, int step, void* stream);
 
 /* sphere_trace_status -- synchronises the stream and reports whether the
- * last sphere_trace that used this workspace completed: NGLOD_OK, or
- * NGLOD_ERR_TIMEOUT if a bounded tensor-core wait of the BF16 decode expired
- * (its outputs are then invalid). */
+ * last sphere_trace (or sphere_trace_blend) that used this workspace
+ * completed: NGLOD_OK, or NGLOD_ERR_TIMEOUT if a bounded wait of a tcgen05
+ * decode (FP8, blending) expired (its outputs are then invalid). */
 int sphere_trace_status(const void* work, void* stream);
 
 /* ---- Continuous LOD: level blending (Sec. 3.2, Eq. 3) ---------------------
