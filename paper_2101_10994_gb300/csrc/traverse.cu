@@ -493,13 +493,30 @@ __global__ void __launch_bounds__(kThreads, 4) k_traverse(const TileParams p) {
             if (threadIdx.x == 0) p.tiles[t] = TileInfo{-1, staged};
         }
         __syncthreads();                   // per-ray counts complete
-        if ((int)threadIdx.x < nr) p.ray_cnt[ra + threadIdx.x] = S.ray_cnt[threadIdx.x];
-        if (whole && p.first_all) {
-            // the tile was staged in one piece, its rays in order
-            int sum;
-            const int pre = block_exclusive_sum((int)threadIdx.x < nr ? S.ray_cnt[threadIdx.x] : 0, S.warp_sums,
-                                                sum);
-            if ((int)threadIdx.x < nr) p.ray_src[ra + threadIdx.x] = (int32_t)(S.stage + pre);
+        if (!p.first_all) {
+            if ((int)threadIdx.x < nr) p.ray_cnt[ra + threadIdx.x] = S.ray_cnt[threadIdx.x];
+        } else {
+            // staged lists: each ray's first staging slot (a tile staged in one
+            // piece holds its rays in order; sub-range tiles recorded theirs
+            // while staging).  A list that does not lie whole inside the
+            // staging capacity (the staging list overflowed: the status says
+            // so) gets no entries, so a reader sees a miss, never an unwritten
+            // slot.
+            long long first = 0;
+            if (whole) {
+                int sum;
+                const int pre = block_exclusive_sum((int)threadIdx.x < nr ? S.ray_cnt[threadIdx.x] : 0,
+                                                    S.warp_sums, sum);
+                first = S.stage + pre;
+            } else if ((int)threadIdx.x < nr) {
+                first = p.ray_src[ra + threadIdx.x];
+            }
+            if ((int)threadIdx.x < nr) {
+                const int c = S.ray_cnt[threadIdx.x];
+                const bool inside = first >= 0 && first + c <= p.stage_cap;
+                p.ray_cnt[ra + threadIdx.x] = inside ? c : 0;
+                p.ray_src[ra + threadIdx.x] = inside ? (int32_t)first : 0;
+            }
         }
         __syncthreads();   // shared state is reused by the next tile
     }
@@ -583,7 +600,14 @@ __global__ void __launch_bounds__(kPlaceThreads) k_place(const TileInfo* __restr
     __shared__ int warp_sums[kTR / 32 + 1];
     __shared__ int ray_pre[kTR + 1];                // sub-range tiles: each ray's first entry in the tile
     __shared__ int32_t ray_from[kTR];               // ... and its first staging slot
-    if (p.ctr->status != kStatusOk) return;
+    if (p.ctr->status != kStatusOk) {
+        // overflow: no lists are placed, so every ray's list is left empty
+        // (a reader sees misses, never stale offsets)
+        for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i <= p.R;
+             i += (long long)gridDim.x * blockDim.x)
+            ray_offsets[i] = 0;
+        return;
+    }
     for (long long t = blockIdx.x; t < p.ntiles; t += gridDim.x) {
         const long long ra = t * kTR;
         const int nr = (int)min((long long)kTR, p.R - ra);

@@ -219,6 +219,34 @@ def test_staged_lists_and_trace(ng, oracle_mod):
     ng.svo_trace_rays_staged(svo, to, td, 4, work, small)
     stats = (C.c_int64 * 2)()
     assert ng.lib().svo_trace_rays_check(work.data_ptr(), 4, stats, None) == ng.ERR_CAPACITY
+    # after an overflow every list a reader sees is whole: the rays whose
+    # lists did not fit get none (misses), the others trace as before
+    half = int(L.voxel_id.numel()) // 2
+    work = torch.empty(ng.lib().svo_trace_rays_workspace(len(o), half), dtype=torch.uint8, device="cuda")
+    Sh = ng.svo_trace_rays_staged(svo, to, td, 4, work, half)
+    assert ng.lib().svo_trace_rays_check(work.data_ptr(), 4, stats, None) == ng.ERR_CAPACITY
+    cnt, first = Sh.ray_counts.long(), Sh.ray_offsets.long()
+    full = (L.ray_offsets[1:] - L.ray_offsets[:-1]).long()
+    kept = cnt > 0
+    assert torch.all(first[kept] + cnt[kept] <= half)
+    assert torch.equal(cnt[kept], full[kept]) and 0 < int(kept.sum()) < int((full > 0).sum())
+    a = ng.sphere_trace(svo, F, D, to, td, L, decode="bf16", normals=True)
+    b = ng.sphere_trace(svo, F, D, to, td, Sh, decode="bf16", normals=True)
+    ng.sphere_trace_status(b)
+    for k in ("t", "hit", "steps", "normal"):
+        assert torch.equal(a[k][kept], b[k][kept]), k
+    assert int(b["hit"][~kept].sum()) == 0
+    # the CSR lists of an overflowed asynchronous traversal are empty
+    R = len(o)
+    work = torch.empty(ng.lib().svo_trace_rays_workspace(R, 2 * int(L.voxel_id.numel())), dtype=torch.uint8,
+                       device="cuda")
+    offs = torch.full((R + 1,), 7, dtype=torch.int32, device="cuda")
+    vid = torch.empty(half, dtype=torch.int32, device="cuda")
+    ng._check(ng.lib().svo_trace_rays_async(svo.h, to.data_ptr(), td.data_ptr(), R, 4, work.data_ptr(), work.numel(),
+                                            2 * int(L.voxel_id.numel()), offs.data_ptr(), vid.data_ptr(), None,
+                                            half, None))
+    assert ng.lib().svo_trace_rays_check(work.data_ptr(), 4, stats, None) == ng.ERR_CAPACITY
+    assert int(offs.abs().sum()) == 0
     svo.free()
 
 
