@@ -452,7 +452,8 @@ __global__ void __launch_bounds__(kTM, kCtasPerSm) k_trace_bf16(const DecPtrsB d
 }
 
 // ---------------------------------------------------------------------------
-// sphere tracing, BF16 decode on warp-level MMAs
+// sphere tracing, BF16 decode on warp-level MMAs (the three-term FP32
+// decode, further below, shares the gather, stash and epilogue)
 //
 // The same contraction per step, but each warp decodes its own 32 slots:
 // pre = z W1^T as 2 M tiles (16 slots each) x 16 N tiles (8 hidden units)
