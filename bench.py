@@ -25,6 +25,7 @@ import hashlib
 import json
 import math
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -541,12 +542,15 @@ def run_ours(args, rank, world, local_rank):
 
 
 def source_hash(kernel):
-    """Hash of the sources a kernel is built from (stale traffic is dropped)."""
+    """Hash of the code a kernel is built from, comments left out (traffic
+    taken from other code is dropped; a comment edit keeps it)."""
     h = hashlib.sha256()
     for f in KERNEL_SRC[kernel]:
         p = os.path.join(CSRC, f)
         if os.path.exists(p):
-            h.update(open(p, "rb").read())
+            code = re.sub(r"/\*.*?\*/", "", open(p).read(), flags=re.S)
+            code = re.sub(r"//[^\n]*", "", code)
+            h.update("\n".join(line.rstrip() for line in code.splitlines() if line.strip()).encode())
     return h.hexdigest()[:16]
 
 

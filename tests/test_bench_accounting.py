@@ -89,3 +89,17 @@ def test_rooflines_use_measured_ceilings(bench):
     assert g["peak"] == pytest.approx(148 * 128 * 2 * 2000e6 / 1e12)
     b = bench.trace_roofline(W, res, "bf16", {"bf16_tflops": 2000.0}, ceilings=ceil)
     assert b["gather_frac_of_l2"] == pytest.approx(gbps / 20000.0)
+
+
+def test_source_hash_ignores_comments_only(tmp_path, monkeypatch):
+    """Stored DRAM traffic is kept across comment edits and dropped when the
+    code changes."""
+    src = tmp_path / "k.cu"
+    src.write_text("// kernel\n__global__ void k(int* p) { p[0] = 1; }\n")
+    monkeypatch.setattr(bench, "CSRC", str(tmp_path))
+    monkeypatch.setitem(bench.KERNEL_SRC, "k_probe_hash", ["k.cu"])
+    h0 = bench.source_hash("k_probe_hash")
+    src.write_text("/* the same kernel,\n   documented */\n__global__ void k(int* p) { p[0] = 1; }  // store\n")
+    assert bench.source_hash("k_probe_hash") == h0
+    src.write_text("__global__ void k(int* p) { p[0] = 2; }\n")
+    assert bench.source_hash("k_probe_hash") != h0
