@@ -91,7 +91,7 @@ def test_rooflines_use_measured_ceilings(bench):
     assert b["gather_frac_of_l2"] == pytest.approx(gbps / 20000.0)
 
 
-def test_source_hash_ignores_comments_only(tmp_path, monkeypatch):
+def test_source_hash_ignores_comments_only(bench, tmp_path, monkeypatch):
     """Stored DRAM traffic is kept across comment edits and dropped when the
     code changes."""
     src = tmp_path / "k.cu"
