@@ -124,7 +124,8 @@ typedef struct {
                               entries are voxel_id[ray_offsets[i] ..
                               ray_offsets[i] + ray_counts[i]) (device, R
                               int32 each; sphere_trace and
-                              sphere_trace_blend only, not batches)         */
+                              sphere_trace_blend; batches take theirs per
+                              job, nglod_trace_job.ray_counts)             */
 } nglod_trace_params;
 
 #define NGLOD_NORMALS_ANALYTIC 0
@@ -582,6 +583,9 @@ typedef struct {
     uint8_t* hit;
     int32_t* steps;           /* nullable */
     float* normal;            /* nullable */
+    const int32_t* ray_counts; /* NULL: CSR lists; else the staged lists of
+                                  svo_trace_rays_staged_async (ray_offsets =
+                                  its ray_first), as nglod_trace_params */
 } nglod_trace_job;
 
 typedef struct nglod_batch nglod_batch;   /* opaque */

@@ -1,7 +1,8 @@
 """Batched rendering: many scenes and images of uneven size per frame.
 
 Each job is one image of one scene at one LOD.  A frame enqueues every job's
-traversal (svo_trace_rays_async) and one persistent sphere-trace launch over
+traversal (svo_trace_rays_staged_async: one launch, each ray's list read
+where the traversal staged it) and one persistent sphere-trace launch over
 all jobs (sphere_trace_batch_run), with no host synchronisation, so the
 whole frame is captured once in a CUDA graph and replayed.  The trace
 kernel's residency (CTAs per SM) is chosen by a small autotuner that times
@@ -47,17 +48,18 @@ class BatchRenderer:
         for j in jobs:
             lists = ng.svo_trace_rays(j.svo, j.o, j.d, j.lod, t_range=False)
             cap = max(int(lists.max_pairs * headroom) + 1024, j.R + 1024)
-            hcap = max(int(lists.voxel_id.numel() * headroom) + 1024, 1024)
             tw = L.svo_trace_rays_workspace(j.R, cap)
-            b = dict(cap=cap, hcap=hcap,
+            b = dict(cap=cap,
                      twork=torch.empty(tw, dtype=torch.uint8, device=dev),
-                     offs=torch.empty(j.R + 1, dtype=torch.int32, device=dev),
-                     vid=torch.empty(hcap, dtype=torch.int32, device=dev),
+                     ptrs=[C.c_void_p() for _ in range(3)],
                      swork=torch.empty(L.sphere_trace_workspace(j.R), dtype=torch.uint8, device=dev),
                      t=torch.empty(j.R, dtype=torch.float32, device=dev),
                      hit=torch.empty(j.R, dtype=torch.uint8, device=dev),
                      steps=torch.empty(j.R, dtype=torch.int32, device=dev),
                      normal=torch.empty((j.R, 3), dtype=torch.float32, device=dev) if normals else None)
+            # the staged lists (views into twork, the same every frame): each
+            # job's tracer reads a ray's entries where its traversal left them
+            b["lists"] = ng.svo_trace_rays_staged(j.svo, j.o, j.d, j.lod, b["twork"], cap)
             self.bufs.append(b)
         self.ctas_per_sm = ctas_per_sm
         self.handle = None
@@ -75,8 +77,11 @@ class BatchRenderer:
             arr[k].dec = j.dec.c()
             arr[k].lod = j.lod
             arr[k].o, arr[k].d, arr[k].R = j.o.data_ptr(), j.d.data_ptr(), j.R
-            # no t ranges: the tracers recompute each entry's interval
-            arr[k].ray_offsets, arr[k].voxel_id, arr[k].t_range = b["offs"].data_ptr(), b["vid"].data_ptr(), None
+            # staged lists, no t ranges: the tracers recompute each entry's interval
+            lists = b["lists"]
+            arr[k].ray_offsets, arr[k].voxel_id, arr[k].t_range = (lists.ray_offsets.data_ptr(),
+                                                                   lists.voxel_id.data_ptr(), None)
+            arr[k].ray_counts = lists.ray_counts.data_ptr()
             arr[k].work, arr[k].work_bytes = b["swork"].data_ptr(), b["swork"].numel()
             arr[k].t_hit, arr[k].hit, arr[k].steps = b["t"].data_ptr(), b["hit"].data_ptr(), b["steps"].data_ptr()
             arr[k].normal = ng._ptr(b["normal"])
@@ -110,10 +115,11 @@ class BatchRenderer:
                 st.wait_event(start)
         for i, (j, b) in enumerate(zip(self.jobs, self.bufs)):
             st = self.tstreams[i % len(self.tstreams)] if self.tstreams else main
-            ng._check(L.svo_trace_rays_async(j.svo.h, j.o.data_ptr(), j.d.data_ptr(), j.R, j.lod,
-                                             b["twork"].data_ptr(), b["twork"].numel(), b["cap"],
-                                             b["offs"].data_ptr(), b["vid"].data_ptr(), None,
-                                             b["hcap"], C.c_void_p(st.cuda_stream)))
+            p = b["ptrs"]
+            ng._check(L.svo_trace_rays_staged_async(j.svo.h, j.o.data_ptr(), j.d.data_ptr(), j.R, j.lod,
+                                                    b["twork"].data_ptr(), b["twork"].numel(), b["cap"], 0,
+                                                    C.byref(p[0]), C.byref(p[1]), C.byref(p[2]),
+                                                    C.c_void_p(st.cuda_stream)))
         for st in self.tstreams:
             main.wait_stream(st)
         ng._check(L.sphere_trace_batch_run(self.handle, s))

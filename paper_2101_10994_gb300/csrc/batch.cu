@@ -105,7 +105,7 @@ __global__ void k_batch_keys(const TraceJob* __restrict__ jobs, const JobGroup* 
         }
         const TraceArgs& A = jobs[lo].A;
         const long long r = gi - jobs[lo].ray_base + lane;
-        const int len = r < A.R ? A.offs[r + 1] - A.offs[r] : 0;
+        const int len = r < A.R ? (A.cnt ? A.cnt[r] : A.offs[r + 1] - A.offs[r]) : 0;
         const int m = __reduce_max_sync(0xffffffffu, len);
         if (lane == 0) {
             const int b = kOrderBuckets - 1 - min(max(m, 0), kOrderBuckets - 1);
@@ -229,6 +229,7 @@ extern "C" int sphere_trace_batch_create(const nglod_trace_job* jobs, int num_jo
             A.max_steps = params->max_steps;
             A.osc = params->osc_check;
             A.offs = J.ray_offsets;
+            A.cnt = J.ray_counts;
             A.vid = J.voxel_id;
             A.t_hit = J.t_hit;
             A.hit = J.hit;

@@ -58,7 +58,8 @@ class _TraceJob(C.Structure):
     _fields_ = [("svo", C.c_void_p), ("feats", _Features), ("dec", _Decoder), ("lod", C.c_int),
                 ("o", C.c_void_p), ("d", C.c_void_p), ("R", C.c_int64), ("ray_offsets", C.c_void_p),
                 ("voxel_id", C.c_void_p), ("t_range", C.c_void_p), ("work", C.c_void_p), ("work_bytes", C.c_size_t),
-                ("t_hit", C.c_void_p), ("hit", C.c_void_p), ("steps", C.c_void_p), ("normal", C.c_void_p)]
+                ("t_hit", C.c_void_p), ("hit", C.c_void_p), ("steps", C.c_void_p), ("normal", C.c_void_p),
+                ("ray_counts", C.c_void_p)]
 
 
 class _TraceParams(C.Structure):

@@ -5,7 +5,8 @@ captured in a CUDA graph) against per-image calls.
 The batched path runs the same per-ray arithmetic as sphere_trace (the
 stepping rules of Sec. 3.4 / A.4) and differs only in which CTA takes which
 ray, so every output -- hit mask, hit depth, step count, normal, and the
-traversal lists -- must be bit-identical to the per-image calls.  Per-image
+traversal lists (staged; the same entries ray by ray) -- must be
+bit-identical to the per-image calls.  Per-image
 sphere_trace itself is checked against the oracle elsewhere; one job here is
 also checked against the oracle directly.
 """
@@ -56,9 +57,14 @@ def assert_same(r, lists, ref, bufs=None):
         assert torch.equal(a.view(torch.uint8) if a.dtype == torch.float32 else a,
                            b.view(torch.uint8) if b.dtype == torch.float32 else b), k
     if bufs is not None:
-        H = lists.voxel_id.numel()
-        assert torch.equal(bufs["offs"].cpu(), lists.ray_offsets.cpu())
-        assert torch.equal(bufs["vid"][:H].cpu(), lists.voxel_id.cpu())
+        # the job's staged lists hold, ray by ray, the CSR lists' entries
+        St = bufs["lists"]
+        offs = lists.ray_offsets.long()
+        cnt = St.ray_counts.long()
+        assert torch.equal(cnt, offs[1:] - offs[:-1])
+        start = torch.repeat_interleave(St.ray_offsets.long(), cnt)
+        within = torch.arange(int(offs[-1]), device=cnt.device) - torch.repeat_interleave(offs[:-1], cnt)
+        assert torch.equal(St.voxel_id[start + within], lists.voxel_id)
 
 
 @pytest.fixture(scope="module")
