@@ -320,8 +320,10 @@ int svo_trace_rays_async_width(const nglod_svo* svo, const float* o, const float
  * workspace (each ray's entries contiguous and front to back, the same
  * entries as the CSR lists; the rays' lists in no particular order), so the
  * traversal is one launch.  The paper's Compactify writes CSR; this form
- * exists for the renderer, whose tracer reads a ray's list by its first
- * entry and count (nglod_trace_params.ray_counts).
+ * exists for the renderers, whose tracers read a ray's list by its first
+ * entry and count (nglod_trace_params.ray_counts, nglod_trace_job.ray_counts).
+ * After a staging overflow a ray whose list did not fit whole gets count 0,
+ * so a tracer reads only written entries.
  *   svo, o, d, R, target_lod, work, work_bytes, pair_capacity, ctas_per_sm
  *                 as svo_trace_rays_async_width.
  *   ray_first, ray_count, voxel_id  host pointers that receive device
