@@ -795,9 +795,10 @@ def run_batch(args):
                      "ms_by_ctas_per_sm_and_streams": tune},
         "hit_pixels": hits,
         "clocks": sampler.summary(),
-        # per graph replay: each job's traversal (3 launches), the reset, the chunk order
-        # (keys, bucket scan, scatter) and the persistent trace kernel, each job's normals
-        "gpu_launches": args.steps * (3 * len(jobs) + 5 + len(jobs)),
+        # per graph replay: the reset, the chunk order (keys, bucket scan, scatter) and the
+        # persistent trace kernel; per job its staged traversal (1), its hit list in ray order
+        # (counts, scan, placement: 3) and its normals (masked-sum operand, gradient: 2)
+        "gpu_launches": args.steps * (5 + 6 * len(jobs)),
     }
     print(json.dumps(line))
 
